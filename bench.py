@@ -1,0 +1,312 @@
+#!/usr/bin/env python
+"""Benchmark: FMM solve throughput (particles/s) on the uniform 1M workload.
+
+Workload: N = 1,048,576 points uniform in the unit cube, charges U[-1,1],
+p = 10, theta = 0.4, ncrit = 64, depth <= 10 (synthetic, SplitMix64 seed 1002).
+A step is one whole solve (box, keys, sort, tree, traversal, P2M/M2M, M2L,
+L2L/L2P, P2P, combine) from device-resident inputs to device-resident outputs.
+The inputs (16 MB) fit in L2, so a 512 MB buffer is written between timed steps
+to flush it; each step is bracketed by CUDA events on the solve's stream.
+
+Also reported:
+  e2e          the same solve through fmm_laplace3d_host (pinned host buffers,
+               host->device and device->host copies inside the timed region)
+  roofline     the dominant kernel against the measured/derived peak
+  cpu_baseline the FP64 oracle on the host cores on a bounded sample
+  clocks       nvidia-smi SM clock samples during the timed region
+
+--impl reference times the oracle (the reference arm of this project).
+Multi-GPU (torchrun): every rank solves its own replica (the single system is
+not sharded), the reported value is the sum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+P2P_FLOPS = 23          # counted flops per P2P interaction (FMA = 2)
+SMS = 152
+FP32_LANES = 128
+SM_MAX_MHZ = 2070.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="uniform1m")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32x3", "bf16x3"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload(name):
+    from paper_1108_5815_gb300 import inputs
+    w = dict(inputs.WORKLOADS[name])
+    x, q = inputs.make(w["kind"], w["n"], w["seed"])
+    return w, x, q
+
+
+def config_of(w, args):
+    return {"workload": f"{args.workload}: N={w['n']} {w['kind']} cube, q~U[-1,1]",
+            "N": w["n"], "p": w["p"], "theta": w["theta"], "ncrit": w["ncrit"],
+            "max_depth": w["max_depth"], "m2l": args.precision,
+            "l2_policy": "512 MB buffer written between timed steps (inputs 16 MB < L2)"}
+
+
+# ------------------------------------------------------------------ oracle timing
+
+def oracle_sample(x, q, w, leaf_stride=128):
+    """Oracle FMM on the full workload with the far/near evaluation restricted to
+    every `leaf_stride`-th leaf; the evaluation time is scaled to all leaves.
+    Returns (particles_per_s, seconds, description)."""
+    import numpy as np
+    from oracle import oracle as O
+    t0 = time.perf_counter()
+    f = O.Fmm(x, q, w["p"], w["theta"], w["ncrit"], max_depth=w["max_depth"])
+    f.upward()
+    t1 = time.perf_counter()
+    c = f.cells()
+    leaves = np.flatnonzero(c["nchild"] == 0)
+    pick = leaves[::leaf_stride]
+    f.evaluate_leaves(pick)
+    t2 = time.perf_counter()
+    t_total = (t1 - t0) + (t2 - t1) * (len(leaves) / len(pick))
+    desc = (f"oracle FMM on the full workload (keys, sort, tree, traversal, P2M/M2M over all "
+            f"{f.ncells} cells), M2L/L2L/L2P/P2P on {len(pick)} of {len(leaves)} leaves, "
+            f"evaluation time scaled by {len(leaves) / len(pick):.1f}")
+    return w["n"] / t_total, t2 - t0, desc
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    w, x, q = workload(args.workload)
+    for _ in range(args.warmup):
+        oracle_sample(x, q, w)
+    vals = []
+    wall = 0.0
+    desc = ""
+    for _ in range(args.steps):
+        v, t, desc = oracle_sample(x, q, w)
+        vals.append(v)
+        wall += t
+    value = statistics.mean(vals)
+    line = {"impl": "reference", "metric": "FMM particles/s", "value": value,
+            "unit": "particles/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * w["n"] / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_of(w, args),
+            "cpu_baseline": {"value": value, "unit": "particles/s", "cores": O.num_threads(),
+                             "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": "particles/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    def __init__(self, index):
+        self.proc = None
+        self.path = None
+        self.index = index
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if getattr(self, "fh", None):
+            self.fh.close()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return None
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[4 + i]
+                          and "Not" not in r[4 + i]})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ main arm
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1108_5815_gb300 import build, fmm
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    build.build()
+
+    w, x, q = workload(args.workload)
+    n = w["n"]
+    xd = torch.from_numpy(x).to(dev)
+    qd = torch.from_numpy(q).to(dev)
+    phi = torch.empty(n, device=dev)
+    grad = torch.empty(n, 3, device=dev)
+    flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device=dev)  # 512 MB > L2
+    kw = dict(max_depth=w["max_depth"], precision=args.precision)
+
+    def solve(stats=False):
+        return fmm.laplace3d(xd, qd, w["p"], w["theta"], w["ncrit"], stats=stats,
+                             out=(phi, grad), **kw)
+
+    for _ in range(args.warmup):
+        solve()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream(dev)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    st_list = []
+    with ClockSampler(local) as clk:
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            starts[k].record(stream)
+            st_list.append(solve(stats=True)[2])
+            ends[k].record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * n / (ms_per_step / 1e3)
+    clocks = clk.summary()
+
+    # roofline of the dominant kernel, from the library's event timing of each phase
+    st0 = st_list[-1]
+    ms_p2p = statistics.mean(s["ms_p2p"] for s in st_list)
+    ms_m2l = statistics.mean(s["ms_m2l"] for s in st_list)
+    P2 = (w["p"] + 1) ** 2
+    fp32_peak = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    p2p_tf = st0["n_p2p_interactions"] * P2P_FLOPS / (ms_p2p * 1e-3) / 1e12
+    m2l_tf = st0["n_m2l_pairs"] * 2 * P2 * P2 / (ms_m2l * 1e-3) / 1e12
+    if ms_p2p >= ms_m2l:
+        roof = {"kernel": "k_p2p", "bound": "alu", "achieved": p2p_tf, "peak": fp32_peak,
+                "unit": "TFLOP/s", "frac": p2p_tf / fp32_peak, "traffic": None,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+                "work": f"{st0['n_p2p_interactions']} interactions x {P2P_FLOPS} flop"}
+    else:
+        roof = {"kernel": "k_m2l_simt", "bound": "alu", "achieved": m2l_tf, "peak": fp32_peak,
+                "unit": "TFLOP/s", "frac": m2l_tf / fp32_peak, "traffic": None,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+                "work": f"{st0['n_m2l_pairs']} M2L pairs x 2 (p+1)^4 flop"}
+    phases = {k: round(statistics.mean(s[k] for s in st_list), 4)
+              for k in ("ms_tree", "ms_traverse", "ms_upward", "ms_m2l", "ms_downward", "ms_p2p",
+                        "ms_total")}
+
+    # end to end through the host-pointer entry point
+    e2e = None
+    if not args.no_e2e:
+        xh = torch.from_numpy(x).pin_memory().numpy()
+        qh = torch.from_numpy(q).pin_memory().numpy()
+        ph = torch.empty(n, dtype=torch.float32).pin_memory().numpy()
+        gh = torch.empty(n, 3, dtype=torch.float32).pin_memory().numpy()
+        sp = stream.cuda_stream
+        for _ in range(2):
+            fmm.laplace3d_host(xh, qh, w["p"], w["theta"], w["ncrit"], out=(ph, gh), stream=sp, **kw)
+        t_e2e = 0.0
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            fmm.laplace3d_host(xh, qh, w["p"], w["theta"], w["ncrit"], out=(ph, gh), stream=sp, **kw)
+            t_e2e += time.perf_counter() - t0
+        e2e_ms = 1e3 * t_e2e / args.steps
+        if world > 1:
+            t = torch.tensor([e2e_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        e2e = {"value": world * n / (e2e_ms / 1e3), "unit": "particles/s",
+               "h2d_bytes_per_step": int(x.nbytes + q.nbytes),
+               "d2h_bytes_per_step": int(ph.nbytes + gh.nbytes), "ms_per_step": e2e_ms}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import oracle as O
+        v, _, desc = oracle_sample(x, q, w)
+        cpu = {"value": v, "unit": "particles/s", "cores": O.num_threads(), "kind": "oracle",
+               "sample": desc}
+
+    if rank == 0:
+        line = {"metric": "FMM particles/s", "value": value, "unit": "particles/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": config_of(w, args), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": int(sum(s["n_launches"] for s in st_list)),
+                "clocks": clocks, "phases_ms": phases,
+                "counts": {k: st0[k] for k in ("ncells", "nleaves", "depth", "n_p2p_pairs",
+                                               "n_p2p_interactions", "n_m2l_pairs",
+                                               "n_offset_classes", "n_m2l_blocks")}}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,144 @@
+/*
+ * fmm.h -- C ABI of the GB300 fast multipole library for the 3-D Laplace
+ * potential and gradient (Yokota & Barba, "Hierarchical N-body simulations with
+ * auto-tuning for heterogeneous systems").
+ *
+ * The problem (Results section: "Laplace kernel potential and force", targets
+ * equal to sources): for N charges q_j at x_j,
+ *     phi_i  = sum_{j, r_ij > 0} q_j / r_ij
+ *     grad_i = -sum_{j, r_ij > 0} q_j (x_i - x_j) / r_ij^3      (grad_i = del phi(x_i))
+ * The paper's force on particle i is -q_i grad_i.  Pairs at zero distance
+ * (including i = j) contribute nothing.
+ *
+ * The method (sections "Hybrid treecode/FMM algorithm" and "Dual tree
+ * traversal"): an adaptive octree with at most ncrit particles per leaf, a
+ * stack-based dual tree traversal with the multipole acceptance criterion
+ * theta = (r_t + r_s)/R, spherical-harmonic expansions of order p with
+ * cell-cell (M2L) far-field and particle-particle (P2P) near-field
+ * interactions, plus the P2M/M2M upward and L2L/L2P downward passes.
+ *
+ * Conventions for every entry point:
+ *   * Coordinates are float32, row-major [N][3] (x, y, z interleaved); charges
+ *     float32 [N]; phi float32 [N]; grad float32 [N][3].  Outputs are in the
+ *     caller's particle order.  Inputs are never modified.
+ *   * Pointers are DEVICE pointers of the current CUDA device unless the name
+ *     says _host.  The caller owns all buffers; the library keeps no pointer
+ *     after returning.
+ *   * Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
+ *     stream).  The plain path synchronises `stream` where it must read sizes
+ *     back (once per tree level); on return the outputs are complete.
+ *   * Internal scratch comes from a library-owned pool per device, grown on
+ *     demand and kept until process exit.  Calls on one device are serialised
+ *     by a lock; calls on different devices may run concurrently.
+ *   * On any status other than FMM_OK the outputs are unspecified and
+ *     fmm_last_error() describes the failure.  Invalid arguments are detected
+ *     before any device work is enqueued.
+ */
+#ifndef GB300_FMM_H
+#define GB300_FMM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FMM_OK = 0,
+    FMM_ERR_ARG = 1,       /* an argument is out of range or a pointer is NULL */
+    FMM_ERR_NONFINITE = 2, /* a coordinate is NaN or infinite (found while bounding the box) */
+    FMM_ERR_CAPACITY = 3,  /* an interaction list outgrew its bound after one regrow */
+    FMM_ERR_CUDA = 4,      /* a CUDA call failed; fmm_last_error() has the message */
+    FMM_ERR_TIMEOUT = 5,   /* a bounded device-side wait gave up */
+    FMM_ERR_NOMEM = 6      /* device or pinned host memory could not be allocated */
+} fmm_status;
+
+/* Arithmetic of the M2L translations (the other steps are fixed: FP32
+ * particle/expansion arithmetic, FP64 box quantisation and operator tables). */
+enum {
+    FMM_PREC_FP32 = 0,   /* FP32 FMA on the CUDA cores */
+    FMM_PREC_TF32X3 = 1, /* tensor cores, operands split hi+lo in TF32, FP32 accumulate */
+    FMM_PREC_BF16X3 = 2  /* tensor cores, operands split hi+lo in BF16, FP32 accumulate */
+};
+
+typedef struct {
+    int max_depth;      /* deepest tree level, 1..21 (0 selects 21) */
+    int precision_mode; /* FMM_PREC_* */
+    int select_mode;    /* 0 = plain FMM (cell-cell far field everywhere) */
+    int deterministic;  /* 1 = bitwise-reproducible results (the only mode implemented) */
+} fmm_options;
+
+typedef struct {
+    int64_t ncells, nleaves, depth;
+    int64_t n_p2p_pairs, n_p2p_interactions; /* leaf pairs; sum over pairs of n_t * n_s */
+    int64_t n_m2l_pairs, n_offset_classes;   /* cell pairs; distinct translation offsets */
+    int64_t n_m2l_blocks;                    /* (target tile, offset class) GEMM blocks */
+    int64_t n_launches;                      /* kernels this library launched for the solve */
+    /* per-phase device time in ms (measured with events when stats are requested) */
+    float ms_tree, ms_upward, ms_traverse, ms_m2l, ms_downward, ms_p2p, ms_total;
+} fmm_stats;
+
+/* Fills *opt with the defaults (max_depth 21, FP32 M2L, plain, deterministic). */
+void fmm_default_options(fmm_options *opt);
+
+/* The FMM solve.  Arguments must satisfy N >= 1, 1 <= p <= 20, 0 < theta < 1,
+ * ncrit >= 1 and N < 2^31; otherwise FMM_ERR_ARG.  p is the expansion order
+ * (section "Hybrid treecode/FMM algorithm"), theta the MAC (Results section),
+ * ncrit the maximum number of particles per leaf (Results section). */
+fmm_status fmm_laplace3d(const float *xyz, const float *q, int64_t N, int p, double theta,
+                         int ncrit, float *phi, float *grad, void *stream);
+
+/* As fmm_laplace3d with options (NULL = defaults) and optional statistics
+ * (NULL = none; non-NULL adds event timing and one extra synchronisation). */
+fmm_status fmm_laplace3d_ex(const float *xyz, const float *q, int64_t N, int p, double theta,
+                            int ncrit, float *phi, float *grad, void *stream,
+                            const fmm_options *opt, fmm_stats *stats);
+
+/* As fmm_laplace3d_ex but every array is in HOST memory (pageable or pinned):
+ * the library copies the inputs to the device, solves on `stream` and copies
+ * the results back before returning. */
+fmm_status fmm_laplace3d_host(const float *xyz_host, const float *q_host, int64_t N, int p,
+                              double theta, int ncrit, float *phi_host, float *grad_host,
+                              void *stream, const fmm_options *opt, fmm_stats *stats);
+
+/* Exact all-pairs sum on the GPU (the O(N^2) direct summation of the paper's
+ * Introduction): FP32 arithmetic, same conventions as fmm_laplace3d. */
+fmm_status fmm_direct(const float *xyz, const float *q, int64_t N, float *phi, float *grad,
+                      void *stream);
+
+/* Copies an intermediate array of the most recent successful solve on the
+ * current device into host memory `dst` of `capacity` bytes; *needed (may be
+ * NULL) receives the byte size.  Returns FMM_ERR_ARG if no solve has run or
+ * capacity is too small.  Cells are in the library's order (level by level,
+ * Morton order within a level); cell-index arrays refer to that order.
+ *   FMM_EXPORT_BOX        double[4]: lo_x, lo_y, lo_z, side
+ *   FMM_EXPORT_KEYS       uint64[N] Morton keys in sorted order
+ *   FMM_EXPORT_ORDER      int32[N]  original index of each sorted position
+ *   FMM_EXPORT_CELLS      int64[ncells][6]: level, key prefix, begin, end, parent, nchild
+ *   FMM_EXPORT_P2P        int32[n][2]: target leaf, source leaf
+ *   FMM_EXPORT_M2L        int32[n][3]: target cell, source cell, offset class
+ *   FMM_EXPORT_MULTIPOLE  float[ncells][P2pad] unit-scaled multipoles (see below)
+ *   FMM_EXPORT_LOCAL      float[ncells][P2pad] unit-scaled local expansions
+ * Expansion rows hold, for n = 0..p, Re c_n^0 then (Re c_n^m, Im c_n^m) for
+ * m = 1..n ((p+1)^2 values, zero-padded to P2pad = a multiple of 32), scaled
+ * by s^-n (multipoles) or s^(n+1) (locals) with s the cell side. */
+enum {
+    FMM_EXPORT_BOX = 0,
+    FMM_EXPORT_KEYS = 1,
+    FMM_EXPORT_ORDER = 2,
+    FMM_EXPORT_CELLS = 3,
+    FMM_EXPORT_P2P = 4,
+    FMM_EXPORT_M2L = 5,
+    FMM_EXPORT_MULTIPOLE = 6,
+    FMM_EXPORT_LOCAL = 7
+};
+fmm_status fmm_export(int what, void *dst, int64_t capacity, int64_t *needed);
+
+/* Message for the last non-OK status returned on this thread ("" if none). */
+const char *fmm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GB300_FMM_H */

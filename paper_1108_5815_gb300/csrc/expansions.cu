@@ -1,0 +1,485 @@
+// expansions.cu -- spherical-harmonic expansions on the GPU: operator tables
+// (FP64 -> FP32), P2M, M2M, L2L and L2P (FP32).
+//
+// The paper's kernels are "based on spherical harmonic expansions" of order p
+// (section "Hybrid treecode/FMM algorithm").  With the solid harmonics
+//   R_n^m(x) = r^n P_n^m(cos t) e^{imf} / (n+m)!,
+//   I_n^m(x) = (n-m)! P_n^m(cos t) e^{imf} / r^{n+1},
+// 1/|x-y| = sum conj(R_n^m(y)) I_n^m(x) and the operators are
+//   P2M  M_n^m  = sum q conj(R_n^m(y - c))
+//   M2M  M'_n^m = sum conj(R_k^l(c - c')) M_{n-k}^{m-l}
+//   M2L  L_j^l  = (-1)^{j+l} sum M_n^m I_{n+j}^{m-l}(c_t - c_s)
+//   L2L  L'_j^l = sum L_n^m R_{n-j}^{m-l}(c' - c)
+//   L2P  phi = sum L_n^m R_n^m(x - c), (d/dz) phi = sum L_n^m R_{n-1}^m,
+//        (d/dx + i d/dy) phi = sum L_n^m R_{n-1}^{m+1}.
+// Storage on the GPU (documented in fmm.h): m >= 0 only, real layout
+// [Re c_n^0, Re c_n^1, Im c_n^1, ...] per degree, each cell's row padded to
+// P2pad floats, and two rescalings that keep every quantity O(1) in FP32:
+//   * unit scaling by the cell side s: M~_n = M_n s^-n, L~_j = L_j s^{j+1},
+//     which makes every operator matrix independent of the level;
+//   * the order normalisation nu_n^m = sqrt((n-m)!(n+m)!):
+//     M^_n^m = nu_n^m M~_n^m and L^_n^m = L~_n^m / nu_n^m, i.e. the expansions
+//     are taken in the basis R^ = nu R, whose recurrence
+//       R^_m^m = -(x+iy) sqrt((2m-1)/(2m)) R^_{m-1}^{m-1}
+//       R^_n^m = ((2n-1) z R^_{n-1}^m - r^2 sqrt((n-m-1)(n+m-1)) R^_{n-2}^m)
+//                / sqrt((n+m)(n-m))
+//     stays bounded by |x|^n.
+// The M2L/M2M/L2L operators become real (P2 x P2) matrices, computed in FP64
+// from the complex formulas and stored in FP32.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace fmm {
+
+namespace {
+
+struct cd {
+    double re, im;
+};
+
+__device__ __forceinline__ cd cmul(cd a, cd b)
+{
+    return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+
+__device__ __forceinline__ int tri(int n, int m) { return n * (n + 1) / 2 + m; }
+
+// log-free sqrt((n-m)!(n+m)!) in FP64 (n <= 40).
+__device__ double nu(int n, int m)
+{
+    m = m < 0 ? -m : m;
+    double f = 1.0;
+    for (int k = 2; k <= n - m; ++k) f *= k;
+    for (int k = 2; k <= n + m; ++k) f *= k;
+    return sqrt(f);
+}
+
+// Plain (un-normalised) regular harmonics R_n^m, m >= 0, n <= P, in FP64.
+__device__ void regular_fp64(double x, double y, double z, int P, cd *R)
+{
+    const double r2 = x * x + y * y + z * z;
+    for (int m = 0; m <= P; ++m) {
+        cd rmm;
+        if (m == 0) {
+            rmm = {1.0, 0.0};
+        } else {
+            const cd prev = R[tri(m - 1, m - 1)];
+            const cd u = {-x / (2.0 * m), -y / (2.0 * m)};
+            rmm = cmul(u, prev);
+        }
+        R[tri(m, m)] = rmm;
+        cd p2 = {0.0, 0.0}, p1 = rmm;
+        for (int n = m + 1; n <= P; ++n) {
+            const double inv = 1.0 / ((double)(n + m) * (double)(n - m));
+            cd rn = {((2.0 * n - 1.0) * z * p1.re - r2 * p2.re) * inv,
+                     ((2.0 * n - 1.0) * z * p1.im - r2 * p2.im) * inv};
+            R[tri(n, m)] = rn;
+            p2 = p1;
+            p1 = rn;
+        }
+    }
+}
+
+// Plain irregular harmonics I_n^m, m >= 0, n <= P, in FP64.
+__device__ void irregular_fp64(double x, double y, double z, int P, cd *Ih)
+{
+    const double r2 = x * x + y * y + z * z;
+    const double ir2 = 1.0 / r2;
+    for (int m = 0; m <= P; ++m) {
+        cd imm;
+        if (m == 0) {
+            imm = {1.0 / sqrt(r2), 0.0};
+        } else {
+            const cd prev = Ih[tri(m - 1, m - 1)];
+            const double f = -(2.0 * m - 1.0) * ir2;
+            imm = cmul({f * x, f * y}, prev);
+        }
+        Ih[tri(m, m)] = imm;
+        cd p2 = {0.0, 0.0}, p1 = imm;
+        for (int n = m + 1; n <= P; ++n) {
+            const double a = (2.0 * n - 1.0) * z, b = (double)(n + m - 1) * (double)(n - m - 1);
+            cd in = {(a * p1.re - b * p2.re) * ir2, (a * p1.im - b * p2.im) * ir2};
+            Ih[tri(n, m)] = in;
+            p2 = p1;
+            p1 = in;
+        }
+    }
+}
+
+// Signed-m access to a harmonic table with H_n^{-m} = (-1)^m conj(H_n^m).
+__device__ __forceinline__ cd hsigned(const cd *H, int n, int m)
+{
+    if (m >= 0) return H[tri(n, m)];
+    const cd v = H[tri(n, -m)];
+    return (m & 1) ? cd{-v.re, v.im} : cd{v.re, -v.im};
+}
+
+
+enum { kOpM2L = 0, kOpM2M = 1, kOpL2L = 2 };
+
+// Complex coefficient of input coefficient (n, m) [signed m] in output (j, l)
+// [l >= 0], in the normalised unit-scaled basis.
+__device__ cd op_coef(int op, const cd *H, int j, int l, int n, int m, double rho, int p)
+{
+    if (op == kOpM2L) {
+        // L_j^l = (-1)^{j+l} rho^n sum M_n^m I_{n+j}^{m-l}
+        const cd v = hsigned(H, n + j, m - l);
+        double f = (((j + l) & 1) ? -1.0 : 1.0) * pow(rho, (double)n) / (nu(j, l) * nu(n, m));
+        return {v.re * f, v.im * f};
+    }
+    if (op == kOpM2M) {
+        // M'_j^l = sum conj(R_k^d) 2^{-n} M_n^m, k = j - n, d = l - m
+        const int k = j - n, d = l - m;
+        if (k < 0 || (d < 0 ? -d : d) > k) return {0.0, 0.0};
+        const cd v = hsigned(H, k, d);
+        const double f = ldexp(1.0, -n) * nu(j, l) / nu(n, m);
+        return {v.re * f, -v.im * f};
+    }
+    // L2L: L'_j^l = sum 2^{-n-1} R_{n-j}^{m-l} L_n^m
+    const int k = n - j, d = m - l;
+    if (k < 0 || (d < 0 ? -d : d) > k) return {0.0, 0.0};
+    const cd v = hsigned(H, k, d);
+    const double f = ldexp(1.0, -n - 1) * nu(n, m) / nu(j, l);
+    return {v.re * f, v.im * f};
+}
+
+// Real matrix entry: output real index `row` <- input real index `col`.
+__device__ double real_entry(int op, const cd *H, int row, int col, double rho, int p)
+{
+    int j = 0;
+    while ((j + 1) * (j + 1) <= row) ++j;
+    int rr = row - j * j;
+    const int l = (rr + 1) / 2;
+    const int rim = (rr == 0) ? 0 : ((rr & 1) ? 0 : 1);
+    int n = 0;
+    while ((n + 1) * (n + 1) <= col) ++n;
+    int cc = col - n * n;
+    const int mm = (cc + 1) / 2;
+    const int cim = (cc == 0) ? 0 : ((cc & 1) ? 0 : 1);
+    const cd A = op_coef(op, H, j, l, n, mm, rho, p);
+    cd B = {0.0, 0.0};
+    if (mm > 0) {
+        const cd b = op_coef(op, H, j, l, n, -mm, rho, p);
+        const double s = (mm & 1) ? -1.0 : 1.0;
+        B = {b.re * s, b.im * s};
+    }
+    if (rim == 0) return cim == 0 ? A.re + B.re : -A.im + B.im;
+    return cim == 0 ? A.im + B.im : A.re - B.re;
+}
+
+}  // namespace
+
+// One block per new offset class: decode (dl, d), compute I^(delta) in FP64
+// and write the P2pad x P2pad matrix (row = output, col = input) at its cache slot.
+__global__ void k_build_m2l_tables(const uint64_t *__restrict__ class_keys,
+                                   const int *__restrict__ cache_slot, int nnew, int p, int P2pad,
+                                   float *__restrict__ table)
+{
+    extern __shared__ cd sh_h[];
+    const int ci = blockIdx.x;
+    if (ci >= nnew) return;
+    const uint64_t key = class_keys[ci];
+    const int dl = (int)(key >> 57) - 64;  // level(S) - level(T)
+    int64_t d[3];
+    for (int a = 0; a < 3; ++a) d[a] = (int64_t)((key >> (38 - 19 * a)) & 0x7ffff) - (1 << 18);
+    // delta = d / s_T and rho = s_S / s_T, both powers of two times d
+    const int fine_shift = dl >= 0 ? dl + 1 : 1;
+    const double rho = ldexp(1.0, -dl);
+    const double dx = ldexp((double)d[0], -fine_shift), dy = ldexp((double)d[1], -fine_shift),
+                 dz = ldexp((double)d[2], -fine_shift);
+    if (threadIdx.x == 0) irregular_fp64(dx, dy, dz, 2 * p, sh_h);
+    __syncthreads();
+    const int P2 = nterms(p);
+    float *out = table + (int64_t)cache_slot[ci] * P2pad * P2pad;
+    for (int e = threadIdx.x; e < P2pad * P2pad; e += blockDim.x) {
+        const int row = e / P2pad, col = e % P2pad;
+        double v = 0.0;
+        if (row < P2 && col < P2) v = real_entry(kOpM2L, sh_h, row, col, rho, p);
+        out[e] = (float)v;
+    }
+}
+
+// Blocks 0..7: M2M matrices per child octant; blocks 8..15: L2L.  Stored
+// transposed (input-major): t[o][col][row] so that consecutive threads (rows)
+// read consecutive addresses.
+__global__ void k_build_shift_tables(int p, int P2pad, float *__restrict__ m2m,
+                                     float *__restrict__ l2l)
+{
+    extern __shared__ cd sh_h[];
+    const int op = blockIdx.x < 8 ? kOpM2M : kOpL2L;
+    const int o = blockIdx.x & 7;
+    const double sgn[3] = {(o & 1) ? 1.0 : -1.0, (o & 2) ? 1.0 : -1.0, (o & 4) ? 1.0 : -1.0};
+    // M2M: (child - parent) / parent side = +-1/4; L2L: (child - parent) / child side = +-1/2
+    const double f = op == kOpM2M ? 0.25 : 0.5;
+    if (threadIdx.x == 0) regular_fp64(sgn[0] * f, sgn[1] * f, sgn[2] * f, p, sh_h);
+    __syncthreads();
+    const int P2 = nterms(p);
+    float *out = (op == kOpM2M ? m2m : l2l) + (int64_t)o * P2pad * P2pad;
+    for (int e = threadIdx.x; e < P2pad * P2pad; e += blockDim.x) {
+        const int col = e / P2pad, row = e % P2pad;
+        double v = 0.0;
+        if (row < P2 && col < P2) v = real_entry(op, sh_h, row, col, 1.0, p);
+        out[e] = (float)v;
+    }
+}
+
+// ---------------------------------------------------------------- P2M / L2P
+
+namespace {
+
+__device__ __forceinline__ void cell_centre_side(const CellArrays &c, int cell,
+                                                 const double *__restrict__ box, double cen[3],
+                                                 double &s)
+{
+    const int l = c.level[cell];
+    const uint64_t pre = c.prefix[cell];
+    s = ldexp(box[3], -l);
+    const double half = ldexp(box[3], -l - 1);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) cen[a] = box[a] + (double)(2 * (int64_t)compact3_dev(pre >> a) + 1) * half;
+}
+
+constexpr int kMaxChunks = 14;  // ceil(448 / 32): p <= 20
+
+}  // namespace
+
+// One warp per leaf.  Each lane evaluates R^(xi) of one particle into its
+// shared-memory row; the lanes then sum the rows column by column.
+__global__ void __launch_bounds__(32)
+    k_p2m(CellArrays c, const int *__restrict__ leaves, int nleaves, const float4 *__restrict__ pts,
+          const double *__restrict__ box, int p, int P2pad, float *__restrict__ M)
+{
+    extern __shared__ float rows[];  // 32 x (P2pad + 1)
+    const int li = blockIdx.x;
+    if (li >= nleaves) return;
+    const int cell = leaves[li];
+    const int lane = threadIdx.x;
+    const int stride = P2pad + 1;
+    double cen[3], s;
+    cell_centre_side(c, cell, box, cen, s);
+    const double is = 1.0 / s;
+    const int b = c.begin[cell], e = c.end[cell];
+    float acc[kMaxChunks];
+#pragma unroll
+    for (int j = 0; j < kMaxChunks; ++j) acc[j] = 0.f;
+    float *row = rows + lane * stride;
+    for (int base = b; base < e; base += 32) {
+        const int i = base + lane;
+        for (int k = 0; k < P2pad; ++k) row[k] = 0.f;
+        if (i < e) {
+            const float4 pt = pts[i];
+            const float x = (float)(((double)pt.x - cen[0]) * is);
+            const float y = (float)(((double)pt.y - cen[1]) * is);
+            const float z = (float)(((double)pt.z - cen[2]) * is);
+            const float q = pt.w;
+            const float r2 = x * x + y * y + z * z;
+            float mre = 1.f, mim = 0.f;  // R^_m^m
+            for (int m = 0; m <= p; ++m) {
+                if (m > 0) {
+                    const float f = -sqrtf((2.f * m - 1.f) / (2.f * m));
+                    const float nre = f * (x * mre - y * mim), nim = f * (x * mim + y * mre);
+                    mre = nre;
+                    mim = nim;
+                }
+                float p2r = 0.f, p2i = 0.f, p1r = mre, p1i = mim;
+                for (int n = m; n <= p; ++n) {
+                    float rr, ri;
+                    if (n == m) {
+                        rr = mre;
+                        ri = mim;
+                    } else {
+                        const float a = (2.f * n - 1.f) * z;
+                        const float bb = r2 * sqrtf((float)((n - m - 1) * (n + m - 1)));
+                        const float inv = rsqrtf((float)((n + m) * (n - m)));
+                        rr = (a * p1r - bb * p2r) * inv;
+                        ri = (a * p1i - bb * p2i) * inv;
+                        p2r = p1r;
+                        p2i = p1i;
+                        p1r = rr;
+                        p1i = ri;
+                    }
+                    if (m == 0) {
+                        row[n * n] = q * rr;
+                    } else {
+                        row[n * n + 2 * m - 1] = q * rr;
+                        row[n * n + 2 * m] = -q * ri;
+                    }
+                }
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < kMaxChunks; ++j) {
+            const int k = lane + 32 * j;
+            if (k < P2pad) {
+                float sum = 0.f;
+                for (int r = 0; r < 32; ++r) sum += rows[r * stride + k];
+                acc[j] += sum;
+            }
+        }
+        __syncwarp();
+    }
+#pragma unroll
+    for (int j = 0; j < kMaxChunks; ++j) {
+        const int k = lane + 32 * j;
+        if (k < P2pad) M[(int64_t)cell * P2pad + k] = acc[j];
+    }
+}
+
+// Parents [a, b) (one level): M^_P = sum over children of A_octant M^_child.
+// Block per parent, thread per output row; the matrices are stored input-major.
+__global__ void k_m2m(CellArrays c, int a, int b, const float *__restrict__ m2m, int P2, int P2pad,
+                      float *__restrict__ M)
+{
+    extern __shared__ float sm_child[];  // P2pad
+    const int cell = a + blockIdx.x;
+    if (cell >= b) return;
+    const int nch = c.nchild[cell];
+    if (nch == 0) return;
+    const int c0 = c.child0[cell];
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int k = 0; k < nch; ++k) {
+        const int ch = c0 + k;
+        const int o = (int)(c.prefix[ch] & 7ull);
+        __syncthreads();
+        for (int i = threadIdx.x; i < P2pad; i += blockDim.x) sm_child[i] = M[(int64_t)ch * P2pad + i];
+        __syncthreads();
+        const float *A = m2m + (int64_t)o * P2pad * P2pad;
+#pragma unroll
+        for (int rr = 0; rr < 4; ++rr) {
+            const int row = threadIdx.x + rr * blockDim.x;
+            if (row < P2) {
+                float s = 0.f;
+                for (int col = 0; col < P2; ++col) s = fmaf(A[(int64_t)col * P2pad + row], sm_child[col], s);
+                acc[rr] += s;
+            }
+        }
+    }
+#pragma unroll
+    for (int rr = 0; rr < 4; ++rr) {
+        const int row = threadIdx.x + rr * blockDim.x;
+        if (row < P2pad) M[(int64_t)cell * P2pad + row] = row < P2 ? acc[rr] : 0.f;
+    }
+}
+
+// Children [a, b) (one level): L^_child += A_octant L^_parent.
+__global__ void k_l2l(CellArrays c, int a, int b, const float *__restrict__ l2l, int P2, int P2pad,
+                      float *__restrict__ L)
+{
+    extern __shared__ float sm_par[];
+    const int cell = a + blockIdx.x;
+    if (cell >= b) return;
+    const int par = c.parent[cell];
+    const int o = (int)(c.prefix[cell] & 7ull);
+    for (int i = threadIdx.x; i < P2pad; i += blockDim.x) sm_par[i] = L[(int64_t)par * P2pad + i];
+    __syncthreads();
+    const float *A = l2l + (int64_t)o * P2pad * P2pad;
+    for (int row = threadIdx.x; row < P2; row += blockDim.x) {
+        float s = 0.f;
+        for (int col = 0; col < P2; ++col) s = fmaf(A[(int64_t)col * P2pad + row], sm_par[col], s);
+        L[(int64_t)cell * P2pad + row] += s;
+    }
+}
+
+// One warp per leaf: far-field potential and gradient from the leaf's local
+// expansion.  Shared memory holds the expansion and three rescaled copies that
+// fold in the normalisation ratios of the derivative ladder.
+__global__ void __launch_bounds__(32)
+    k_l2p(CellArrays c, const int *__restrict__ leaves, int nleaves, const float4 *__restrict__ pts,
+          const double *__restrict__ box, int p, int P2pad, const float *__restrict__ L,
+          float4 *__restrict__ far)
+{
+    extern __shared__ float sl[];  // 4 x P2pad: L, Lz, Lx1, Lx2
+    const int li = blockIdx.x;
+    if (li >= nleaves) return;
+    const int cell = leaves[li];
+    const int lane = threadIdx.x;
+    float *Lh = sl, *Lz = sl + P2pad, *Lx1 = sl + 2 * P2pad, *Lx2 = sl + 3 * P2pad;
+    const int P2 = nterms(p);
+    for (int k = lane; k < P2pad; k += 32) {
+        float v = k < P2 ? L[(int64_t)cell * P2pad + k] : 0.f;
+        int n = 0;
+        while ((n + 1) * (n + 1) <= k) ++n;
+        const int m = (k - n * n + 1) / 2;
+        Lh[k] = v;
+        Lz[k] = v * sqrtf((float)((n - m) * (n + m)));
+        Lx1[k] = v * sqrtf((float)max(0, (n - m) * (n - m - 1)));
+        Lx2[k] = v * sqrtf((float)((n + m) * (n + m - 1)));
+    }
+    __syncwarp();
+    double cen[3], s;
+    cell_centre_side(c, cell, box, cen, s);
+    const double is = 1.0 / s;
+    const float inv_s = (float)is, inv_s2 = (float)(is * is);
+    const int b = c.begin[cell], e = c.end[cell];
+    for (int i = b + lane; i < e; i += 32) {
+        const float4 pt = pts[i];
+        const float x = (float)(((double)pt.x - cen[0]) * is);
+        const float y = (float)(((double)pt.y - cen[1]) * is);
+        const float z = (float)(((double)pt.z - cen[2]) * is);
+        const float r2 = x * x + y * y + z * z;
+        float phi = 0.f, dz = 0.f, dpr = 0.f, dpi = 0.f;
+        float mre = 1.f, mim = 0.f;
+        for (int m = 0; m <= p; ++m) {
+            if (m > 0) {
+                const float f = -sqrtf((2.f * m - 1.f) / (2.f * m));
+                const float nre = f * (x * mre - y * mim), nim = f * (x * mim + y * mre);
+                mre = nre;
+                mim = nim;
+            }
+            const float w = m == 0 ? 1.f : 2.f;
+            float p2r = 0.f, p2i = 0.f, p1r = mre, p1i = mim;
+            for (int n = m; n <= p; ++n) {
+                float rr, ri;
+                if (n == m) {
+                    rr = mre;
+                    ri = mim;
+                } else {
+                    const float a = (2.f * n - 1.f) * z;
+                    const float bb = r2 * sqrtf((float)((n - m - 1) * (n + m - 1)));
+                    const float inv = rsqrtf((float)((n + m) * (n - m)));
+                    rr = (a * p1r - bb * p2r) * inv;
+                    ri = (a * p1i - bb * p2i) * inv;
+                    p2r = p1r;
+                    p2i = p1i;
+                    p1r = rr;
+                    p1i = ri;
+                }
+                // phi += w Re(L_n^m R_n^m)
+                {
+                    const int k = n * n + (m == 0 ? 0 : 2 * m - 1);
+                    const float lr = Lh[k], lim = m == 0 ? 0.f : Lh[k + 1];
+                    phi += w * (lr * rr - lim * ri);
+                }
+                if (n + 1 <= p) {
+                    const int n1 = n + 1, base = n1 * n1;
+                    // dz += w Re(Lz_{n+1}^m R_n^m)
+                    {
+                        const int k = base + (m == 0 ? 0 : 2 * m - 1);
+                        const float lr = Lz[k], lim = m == 0 ? 0.f : Lz[k + 1];
+                        dz += w * (lr * rr - lim * ri);
+                    }
+                    // D+ += Lx1_{n+1}^{m-1} R_n^m  (m >= 1)
+                    if (m >= 1) {
+                        const int mm = m - 1;
+                        const int k = base + (mm == 0 ? 0 : 2 * mm - 1);
+                        const float lr = Lx1[k], lim = mm == 0 ? 0.f : Lx1[k + 1];
+                        dpr += lr * rr - lim * ri;
+                        dpi += lr * ri + lim * rr;
+                    }
+                    // D+ -= conj(Lx2_{n+1}^{m+1} R_n^m)
+                    {
+                        const int mm = m + 1;
+                        const int k = base + 2 * mm - 1;
+                        const float lr = Lx2[k], lim = Lx2[k + 1];
+                        dpr -= lr * rr - lim * ri;
+                        dpi += lr * ri + lim * rr;
+                    }
+                }
+            }
+        }
+        far[i] = make_float4(phi * inv_s, dpr * inv_s2, dpi * inv_s2, dz * inv_s2);
+    }
+}
+
+}  // namespace fmm

@@ -1,0 +1,792 @@
+// fmm_api.cu -- C ABI entry points and the host orchestration of one solve.
+//
+// One solve, on the caller's stream (declared in include/fmm.h):
+//   box -> Morton keys -> radix sort -> permute         (tree build: the paper
+//   -> adaptive octree level by level                     runs it on the CPU)
+//   -> dual tree traversal level by level -> offset classes and M2L tiles
+//   -> P2M, M2M (upward) -> M2L -> L2L, L2P (downward) -> P2P -> combine.
+// Sizes that depend on the data (cells per level, list lengths, classes) are
+// read back once per level through a pinned buffer; every buffer is sized
+// exactly from those counts, so no list can overflow.
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <unordered_map>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace fmm {
+
+static thread_local std::string g_last_error;
+thread_local int64_t g_launch_count = 0;
+void set_last_error(const std::string &msg) { g_last_error = msg; }
+
+namespace {
+
+struct Buf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+struct Workspace {
+    int device = 0;
+    std::mutex mu;
+    std::map<std::string, Buf> bufs;
+    void *pinned = nullptr;
+    size_t pinned_bytes = 0;
+    // operator caches
+    int cache_p = -1;
+    std::unordered_map<uint64_t, int> class_cache;
+    int table_slots = 0;
+    // last solve (for fmm_export)
+    bool have_solve = false;
+    int64_t N = 0;
+    int ncells = 0, nleaves = 0, depth = 0, P2pad = 0, nclass = 0;
+    int64_t nm2l = 0, np2p = 0;
+};
+
+std::mutex g_ws_mu;
+std::map<int, std::unique_ptr<Workspace>> g_ws;
+
+Workspace &workspace_for_current_device()
+{
+    int dev = 0;
+    FMM_CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_ws_mu);
+    auto &w = g_ws[dev];
+    if (!w) {
+        w.reset(new Workspace());
+        w->device = dev;
+    }
+    return *w;
+}
+
+template <typename T>
+T *need(Workspace &ws, const char *name, size_t n, cudaStream_t st, bool keep = false)
+{
+    Buf &b = ws.bufs[name];
+    const size_t bytes = std::max<size_t>(n, 1) * sizeof(T);
+    if (bytes > b.bytes) {
+        size_t nb = std::max(bytes, b.bytes + b.bytes / 2);
+        nb = (nb + 255) & ~(size_t)255;
+        void *np = nullptr;
+        cudaError_t e = cudaMalloc(&np, nb);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            throw Error{FMM_ERR_NOMEM, std::string("cudaMalloc(") + std::to_string(nb) +
+                                           ") for " + name + ": " + cudaGetErrorString(e)};
+        }
+        if (keep && b.p) FMM_CUDA_TRY(cudaMemcpyAsync(np, b.p, b.bytes, cudaMemcpyDeviceToDevice, st));
+        if (b.p) {
+            FMM_CUDA_TRY(cudaStreamSynchronize(st));
+            FMM_CUDA_TRY(cudaFree(b.p));
+        }
+        b.p = np;
+        b.bytes = nb;
+    }
+    return static_cast<T *>(b.p);
+}
+
+template <typename T>
+T *get(Workspace &ws, const char *name)
+{
+    return static_cast<T *>(ws.bufs[name].p);
+}
+
+void *pinned(Workspace &ws, size_t bytes)
+{
+    if (bytes > ws.pinned_bytes) {
+        if (ws.pinned) cudaFreeHost(ws.pinned);
+        ws.pinned = nullptr;
+        size_t nb = std::max<size_t>(bytes, 4096);
+        if (cudaMallocHost(&ws.pinned, nb) != cudaSuccess) {
+            cudaGetLastError();
+            ws.pinned_bytes = 0;
+            throw Error{FMM_ERR_NOMEM, "cudaMallocHost failed"};
+        }
+        ws.pinned_bytes = nb;
+    }
+    return ws.pinned;
+}
+
+// Copies the device flags plus `n` extra (dev -> host) items and synchronises.
+void sync_point(Workspace &ws, cudaStream_t st, const int *flags_dev,
+                std::initializer_list<std::pair<const void *, size_t>> items, void *host_out)
+{
+    size_t total = sizeof(int) * kNumFlags;
+    for (auto &it : items) total += it.second;
+    char *h = static_cast<char *>(pinned(ws, total));
+    FMM_CUDA_TRY(cudaMemcpyAsync(h, flags_dev, sizeof(int) * kNumFlags, cudaMemcpyDeviceToHost, st));
+    size_t off = sizeof(int) * kNumFlags;
+    for (auto &it : items) {
+        FMM_CUDA_TRY(cudaMemcpyAsync(h + off, it.first, it.second, cudaMemcpyDeviceToHost, st));
+        off += it.second;
+    }
+    FMM_CUDA_TRY(cudaStreamSynchronize(st));
+    const int *f = reinterpret_cast<const int *>(h);
+    if (f[kFlagNonfinite]) throw Error{FMM_ERR_NONFINITE, "a coordinate is NaN or infinite"};
+    if (f[kFlagHashFull]) throw Error{FMM_ERR_CAPACITY, "offset-class table is full"};
+    if (f[kFlagClassRange])
+        throw Error{FMM_ERR_CAPACITY, "an M2L offset exceeds the class key range (2^18 cells)"};
+    if (f[kFlagStack]) throw Error{FMM_ERR_CAPACITY, "traversal stack overflow"};
+    if (host_out) std::memcpy(host_out, h + sizeof(int) * kNumFlags, total - sizeof(int) * kNumFlags);
+}
+
+struct Events {
+    bool on = false;
+    cudaEvent_t ev[8] = {};
+    void init(bool enable)
+    {
+        on = enable;
+        if (on)
+            for (auto &e : ev) FMM_CUDA_TRY(cudaEventCreate(&e));
+    }
+    void rec(int i, cudaStream_t st)
+    {
+        if (on) FMM_CUDA_TRY(cudaEventRecord(ev[i], st));
+    }
+    float ms(int a, int b)
+    {
+        float v = 0.f;
+        if (on) FMM_CUDA_TRY(cudaEventElapsedTime(&v, ev[a], ev[b]));
+        return v;
+    }
+    ~Events()
+    {
+        if (on)
+            for (auto &e : ev) cudaEventDestroy(e);
+    }
+};
+
+__global__ void k_root_lists(ListArrays L, int root_is_leaf)
+{
+    L.m2l_off[0] = 0;
+    L.m2l_cnt[0] = 0;
+    L.p2p_off[0] = 0;
+    if (root_is_leaf) {
+        L.p2p_src[0] = 0;
+        L.p2p_tgt[0] = 0;
+        L.p2p_cnt[0] = 1;
+        L.def_off[0] = 0;
+        L.def_cnt[0] = 0;
+    } else {
+        L.p2p_cnt[0] = 0;
+        L.def_src[0] = 0;
+        L.def_off[0] = 0;
+        L.def_cnt[0] = 1;
+    }
+}
+
+__global__ void k_p2p_interactions(const int *__restrict__ tgt, const int *__restrict__ src,
+                                   int64_t n, CellArrays c, unsigned long long *out)
+{
+    unsigned long long s = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int t = tgt[i], so = src[i];
+        s += (unsigned long long)(c.end[t] - c.begin[t]) * (unsigned long long)(c.end[so] - c.begin[so]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(out, s);
+}
+
+inline unsigned grid_for(int64_t n, int threads, int64_t cap = 152 * 16)
+{
+    int64_t g = ceil_div(std::max<int64_t>(n, 1), threads);
+    return (unsigned)std::min(g, cap);
+}
+
+void validate(const void *xyz, const void *q, int64_t N, int p, double theta, int ncrit,
+              const void *phi, const void *grad, const fmm_options &o)
+{
+    if (!xyz || !q || !phi || !grad) throw Error{FMM_ERR_ARG, "null pointer argument"};
+    if (N < 1 || N >= (int64_t(1) << 31)) throw Error{FMM_ERR_ARG, "N must be in [1, 2^31)"};
+    if (p < 1 || p > 20) throw Error{FMM_ERR_ARG, "p must be in [1, 20]"};
+    if (!(theta > 0.0 && theta < 1.0)) throw Error{FMM_ERR_ARG, "theta must be in (0, 1)"};
+    if (ncrit < 1) throw Error{FMM_ERR_ARG, "ncrit must be >= 1"};
+    if (o.max_depth < 0 || o.max_depth > kMaxLevel) throw Error{FMM_ERR_ARG, "max_depth must be in [0, 21]"};
+    if (o.precision_mode != FMM_PREC_FP32)
+        throw Error{FMM_ERR_ARG, "precision_mode: only FMM_PREC_FP32 is available in this build"};
+    if (o.select_mode != 0) throw Error{FMM_ERR_ARG, "select_mode: only the plain FMM (0) is available"};
+}
+
+// The solve on device buffers; the caller holds ws.mu.
+void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, int p,
+                  double theta, int ncrit, float *phi, float *grad, cudaStream_t st,
+                  const fmm_options &o, fmm_stats *stats)
+{
+    const int N = (int)N64;
+    const int max_depth = o.max_depth == 0 ? kMaxLevel : o.max_depth;
+    const int P2 = nterms(p), P2pad = nterms_pad(p);
+    Events ev;
+    ev.init(stats != nullptr);
+    ws.have_solve = false;
+    g_launch_count = 0;
+    ev.rec(0, st);
+
+    // ---------------------------------------------------------- box, keys, sort
+    int *flags = need<int>(ws, "flags", kNumFlags, st);
+    uint32_t *bbox_u = need<uint32_t>(ws, "bbox_u", 6, st);
+    double *box = need<double>(ws, "box", 4, st);
+    uint64_t *keys = need<uint64_t>(ws, "keys", N, st);
+    uint64_t *keys_alt = need<uint64_t>(ws, "keys_alt", N, st);
+    uint32_t *idx = need<uint32_t>(ws, "idx", N, st);
+    uint32_t *idx_alt = need<uint32_t>(ws, "idx_alt", N, st);
+    const int64_t nh = radix_hist_elems(N);
+    uint32_t *hist = need<uint32_t>(ws, "hist", nh, st);
+    uint32_t *tmp_u32 = need<uint32_t>(ws, "scan_u32", scan_temp_elems(nh), st);
+    float4 *pts = need<float4>(ws, "pts", N, st);
+    FMM_CUDA_TRY(cudaMemsetAsync(flags, 0, sizeof(int) * kNumFlags, st));
+    FMM_CUDA_TRY(cudaMemsetAsync(bbox_u, 0xff, 3 * sizeof(uint32_t), st));
+    FMM_CUDA_TRY(cudaMemsetAsync(bbox_u + 3, 0, 3 * sizeof(uint32_t), st));
+    k_bbox<<<grid_for(N, 256), 256, 0, st>>>(xyz, N, bbox_u, flags);
+    FMM_LAUNCH_CHECK();
+    k_morton<<<grid_for(N, 256), 256, 0, st>>>(xyz, N, bbox_u, box, keys, idx);
+    FMM_LAUNCH_CHECK();
+    radix_sort_pairs(keys, idx, keys_alt, idx_alt, N, 63, hist, tmp_u32, st);
+    k_permute<<<grid_for(N, 256), 256, 0, st>>>(xyz, q, idx, N, pts);
+    FMM_LAUNCH_CHECK();
+
+    // ---------------------------------------------------------- tree
+    int cell_cap = std::max(1024, N / 8 + 64);
+    auto cells = [&](int cap, bool keep) {
+        CellArrays c;
+        c.level = need<int>(ws, "c_level", cap, st, keep);
+        c.prefix = need<uint64_t>(ws, "c_prefix", cap, st, keep);
+        c.begin = need<int>(ws, "c_begin", cap, st, keep);
+        c.end = need<int>(ws, "c_end", cap, st, keep);
+        c.parent = need<int>(ws, "c_parent", cap, st, keep);
+        c.child0 = need<int>(ws, "c_child0", cap, st, keep);
+        c.nchild = need<int>(ws, "c_nchild", cap, st, keep);
+        c.tile = need<int>(ws, "c_tile", cap, st, keep);
+        c.lane = need<int>(ws, "c_lane", cap, st, keep);
+        return c;
+    };
+    CellArrays c = cells(cell_cap, false);
+    k_init_root<<<1, 1, 0, st>>>(c, N);
+    FMM_LAUNCH_CHECK();
+    std::vector<int> lstart = {0, 1};
+    int tiles_total = 1;
+    int64_t *i64_tmp = need<int64_t>(ws, "scan_i64", scan_temp_elems(std::max(N, 1 << 16)), st);
+    for (int l = 0;; ++l) {
+        const int a = lstart[l], b = lstart[l + 1];
+        const int nl = b - a;
+        if (nl == 0) break;
+        int64_t *packed = need<int64_t>(ws, "packed", nl, st);
+        int64_t *packed_ex = need<int64_t>(ws, "packed_ex", nl + 1, st);
+        i64_tmp = need<int64_t>(ws, "scan_i64", scan_temp_elems(nl), st);
+        k_split_count<<<(unsigned)ceil_div(nl, 128), 128, 0, st>>>(c, keys, a, b, l, ncrit, max_depth,
+                                                                  packed);
+        FMM_LAUNCH_CHECK();
+        scan_exclusive<int64_t>(packed, packed_ex, nl, packed_ex + nl, i64_tmp, st);
+        int64_t total = 0;
+        sync_point(ws, st, flags, {{packed_ex + nl, sizeof(int64_t)}}, &total);
+        const int nch = (int)(total & 0xffffffffll);
+        const int nsplit = (int)(total >> 32);
+        if (nch == 0) break;
+        if (b + nch > cell_cap) {
+            cell_cap = std::max(b + nch, cell_cap + cell_cap / 2);
+            c = cells(cell_cap, true);
+        }
+        k_split_emit<<<(unsigned)ceil_div(nl, 128), 128, 0, st>>>(c, keys, a, b, l, packed, packed_ex,
+                                                                 tiles_total);
+        FMM_LAUNCH_CHECK();
+        tiles_total += 8 * (int)ceil_div(nsplit, kTile);
+        lstart.push_back(b + nch);
+    }
+    const int depth = (int)lstart.size() - 2;
+    const int ncells = lstart.back();
+    int nleaves = 0;
+    int *leaves;
+    {
+        int *lflag = need<int>(ws, "leaf_flag", ncells, st);
+        int *lex = need<int>(ws, "leaf_ex", ncells + 1, st);
+        int *i32_tmp = need<int>(ws, "scan_i32", scan_temp_elems(ncells), st);
+        leaves = need<int>(ws, "leaves", ncells, st);
+        k_leaf_flags<<<(unsigned)ceil_div(ncells, 256), 256, 0, st>>>(c, ncells, lflag);
+        FMM_LAUNCH_CHECK();
+        scan_exclusive<int>(lflag, lex, ncells, lex + ncells, i32_tmp, st);
+        k_leaf_compact<<<(unsigned)ceil_div(ncells, 256), 256, 0, st>>>(c, ncells, lex, leaves);
+        FMM_LAUNCH_CHECK();
+        sync_point(ws, st, flags, {{lex + ncells, sizeof(int)}}, &nleaves);
+    }
+    ev.rec(1, st);
+
+    // ---------------------------------------------------------- traversal
+    const double theta2 = theta * theta;
+    ListArrays L;
+    L.m2l_off = need<int>(ws, "m2l_off", ncells, st);
+    L.m2l_cnt = need<int>(ws, "m2l_cnt", ncells, st);
+    L.p2p_off = need<int>(ws, "p2p_off", ncells, st);
+    L.p2p_cnt = need<int>(ws, "p2p_cnt", ncells, st);
+    L.def_off = need<int>(ws, "def_off", ncells, st);
+    L.def_cnt = need<int>(ws, "def_cnt", ncells, st);
+    int64_t m2l_cap = std::max<int64_t>(1024, (int64_t)ncells * 16);
+    int64_t p2p_cap = std::max<int64_t>(1024, (int64_t)ncells * 8);
+    int64_t def_cap = std::max<int64_t>(1024, (int64_t)ncells * 8);
+    auto lists = [&](bool keep) {
+        L.m2l_src = need<int>(ws, "m2l_src", m2l_cap, st, keep);
+        L.m2l_tgt = need<int>(ws, "m2l_tgt", m2l_cap, st, keep);
+        L.m2l_slot = need<uint32_t>(ws, "m2l_slot", m2l_cap, st, keep);
+        L.p2p_src = need<int>(ws, "p2p_src", p2p_cap, st, keep);
+        L.p2p_tgt = need<int>(ws, "p2p_tgt", p2p_cap, st, keep);
+        L.def_src = need<int>(ws, "def_src", def_cap, st, keep);
+    };
+    lists(false);
+    uint64_t *hash_keys = need<uint64_t>(ws, "hash_keys", kHashCap, st);
+    FMM_CUDA_TRY(cudaMemsetAsync(hash_keys, 0xff, sizeof(uint64_t) * kHashCap, st));
+    const bool root_leaf = ncells == 1;
+    k_root_lists<<<1, 1, 0, st>>>(L, root_leaf ? 1 : 0);
+    FMM_LAUNCH_CHECK();
+    int64_t m2l_total = 0, p2p_total = root_leaf ? 1 : 0;
+    int def_total = root_leaf ? 0 : 1;
+    for (int l = 1; l <= depth; ++l) {
+        const int a = lstart[l], b = lstart[l + 1];
+        const int nl = b - a;
+        int64_t *cnt_mp = need<int64_t>(ws, "cnt_mp", nl, st);
+        int64_t *off_mp = need<int64_t>(ws, "off_mp", nl + 1, st);
+        int *cnt_d = need<int>(ws, "cnt_d", nl, st);
+        int *off_d = need<int>(ws, "off_d", nl + 1, st);
+        int *i32_tmp = need<int>(ws, "scan_i32", scan_temp_elems(nl), st);
+        i64_tmp = need<int64_t>(ws, "scan_i64", scan_temp_elems(nl), st);
+        const unsigned blocks = (unsigned)ceil_div((int64_t)nl * 32, 128);
+        k_traverse_count<<<blocks, 128, 0, st>>>(c, L, a, b, theta2, cnt_mp, cnt_d, flags);
+        FMM_LAUNCH_CHECK();
+        scan_exclusive<int64_t>(cnt_mp, off_mp, nl, off_mp + nl, i64_tmp, st);
+        scan_exclusive<int>(cnt_d, off_d, nl, off_d + nl, i32_tmp, st);
+        struct {
+            int64_t mp;
+            int d;
+        } tot;
+        int64_t tmp_mp = 0;
+        int tmp_d = 0;
+        {
+            char hb[16];
+            sync_point(ws, st, flags, {{off_mp + nl, sizeof(int64_t)}, {off_d + nl, sizeof(int)}}, hb);
+            std::memcpy(&tmp_mp, hb, 8);
+            std::memcpy(&tmp_d, hb + 8, 4);
+        }
+        tot.mp = tmp_mp;
+        tot.d = tmp_d;
+        const int64_t add_m = tot.mp >> 32, add_p = tot.mp & 0xffffffffll;
+        const int add_d = tot.d;
+        bool grow = false;
+        if (m2l_total + add_m > m2l_cap) {
+            m2l_cap = std::max(m2l_total + add_m, m2l_cap + m2l_cap / 2);
+            grow = true;
+        }
+        if (p2p_total + add_p > p2p_cap) {
+            p2p_cap = std::max(p2p_total + add_p, p2p_cap + p2p_cap / 2);
+            grow = true;
+        }
+        if ((int64_t)def_total + add_d > def_cap) {
+            def_cap = std::max<int64_t>(def_total + add_d, def_cap + def_cap / 2);
+            grow = true;
+        }
+        if (grow) lists(true);
+        k_traverse_write<<<blocks, 128, 0, st>>>(c, L, a, b, theta2, off_mp, off_d, m2l_total,
+                                                 p2p_total, def_total, hash_keys, flags);
+        FMM_LAUNCH_CHECK();
+        m2l_total += add_m;
+        p2p_total += add_p;
+        def_total += add_d;
+    }
+
+    // ---------------------------------------------------------- offset classes
+    int nclass = 0;
+    {
+        int *hflag = need<int>(ws, "hflag", kHashCap, st);
+        int *hex = need<int>(ws, "hex", kHashCap + 1, st);
+        int *i32_tmp = need<int>(ws, "scan_i32", scan_temp_elems(kHashCap), st);
+        k_hash_flags<<<kHashCap / 256, 256, 0, st>>>(hash_keys, hflag);
+        FMM_LAUNCH_CHECK();
+        scan_exclusive<int>(hflag, hex, kHashCap, hex + kHashCap, i32_tmp, st);
+        sync_point(ws, st, flags, {{hex + kHashCap, sizeof(int)}}, &nclass);
+        uint64_t *ukeys = need<uint64_t>(ws, "ukeys", nclass, st);
+        uint64_t *ukeys_alt = need<uint64_t>(ws, "ukeys_alt", nclass, st);
+        uint32_t *uslot = need<uint32_t>(ws, "uslot", nclass, st);
+        uint32_t *uslot_alt = need<uint32_t>(ws, "uslot_alt", nclass, st);
+        int *slot_class = need<int>(ws, "slot_class", kHashCap, st);
+        k_hash_compact<<<kHashCap / 256, 256, 0, st>>>(hash_keys, hex, ukeys, uslot);
+        FMM_LAUNCH_CHECK();
+        if (nclass > 0) {
+            const int64_t nh2 = radix_hist_elems(nclass);
+            uint32_t *h2 = need<uint32_t>(ws, "hist", std::max(nh, nh2), st);
+            uint32_t *t2 = need<uint32_t>(ws, "scan_u32", scan_temp_elems(std::max(nh, nh2)), st);
+            radix_sort_pairs(ukeys, uslot, ukeys_alt, uslot_alt, nclass, 64, h2, t2, st);
+            k_slot_to_class<<<(unsigned)ceil_div(nclass, 256), 256, 0, st>>>(uslot, nclass, slot_class);
+            FMM_LAUNCH_CHECK();
+            if (m2l_total > 0) {
+                k_m2l_class<<<grid_for(m2l_total, 256), 256, 0, st>>>(L.m2l_slot, m2l_total, slot_class);
+                FMM_LAUNCH_CHECK();
+            }
+        }
+        // operator tables: shift matrices per p, M2L matrices cached per class key
+        if (ws.cache_p != p) {
+            ws.class_cache.clear();
+            ws.table_slots = 0;
+            ws.cache_p = p;
+            float *m2m = need<float>(ws, "m2m", (size_t)8 * P2pad * P2pad, st);
+            float *l2l = need<float>(ws, "l2l", (size_t)8 * P2pad * P2pad, st);
+            const size_t sh = sizeof(double) * 2 * (size_t)(p + 1) * (p + 2) / 2;
+            k_build_shift_tables<<<16, 256, sh, st>>>(p, P2pad, m2m, l2l);
+            FMM_LAUNCH_CHECK();
+        }
+        std::vector<uint64_t> hkeys(nclass);
+        if (nclass > 0) {
+            FMM_CUDA_TRY(cudaMemcpyAsync(hkeys.data(), ukeys, sizeof(uint64_t) * nclass,
+                                         cudaMemcpyDeviceToHost, st));
+            FMM_CUDA_TRY(cudaStreamSynchronize(st));
+        }
+        std::vector<int> cls_slot(nclass);
+        std::vector<uint64_t> new_keys;
+        std::vector<int> new_slots;
+        for (int i = 0; i < nclass; ++i) {
+            auto it = ws.class_cache.find(hkeys[i]);
+            if (it == ws.class_cache.end()) {
+                const int s = ws.table_slots++;
+                ws.class_cache.emplace(hkeys[i], s);
+                new_keys.push_back(hkeys[i]);
+                new_slots.push_back(s);
+                cls_slot[i] = s;
+            } else {
+                cls_slot[i] = it->second;
+            }
+        }
+        need<float>(ws, "table", (size_t)std::max(ws.table_slots, 1) * P2pad * P2pad, st, true);
+        int *class_slot = need<int>(ws, "class_slot", nclass, st);
+        if (nclass > 0)
+            FMM_CUDA_TRY(cudaMemcpyAsync(class_slot, cls_slot.data(), sizeof(int) * nclass,
+                                         cudaMemcpyHostToDevice, st));
+        if (!new_keys.empty()) {
+            const int nnew = (int)new_keys.size();
+            uint64_t *nk = need<uint64_t>(ws, "new_keys", nnew, st);
+            int *ns = need<int>(ws, "new_slots", nnew, st);
+            FMM_CUDA_TRY(cudaMemcpyAsync(nk, new_keys.data(), sizeof(uint64_t) * nnew,
+                                         cudaMemcpyHostToDevice, st));
+            FMM_CUDA_TRY(cudaMemcpyAsync(ns, new_slots.data(), sizeof(int) * nnew,
+                                         cudaMemcpyHostToDevice, st));
+            const size_t sh = sizeof(double) * 2 * (size_t)(2 * p + 1) * (2 * p + 2) / 2;
+            k_build_m2l_tables<<<nnew, 256, sh, st>>>(nk, ns, nnew, p, P2pad, get<float>(ws, "table"));
+            FMM_LAUNCH_CHECK();
+            // host vectors must outlive the async copies
+            FMM_CUDA_TRY(cudaStreamSynchronize(st));
+        } else if (nclass > 0) {
+            FMM_CUDA_TRY(cudaStreamSynchronize(st));
+        }
+    }
+
+    // ---------------------------------------------------------- M2L tiles
+    const int ntiles = tiles_total;
+    const int nwords = std::max(1, (int)ceil_div(nclass, 32));
+    int *tile_cells = need<int>(ws, "tile_cells", (size_t)ntiles * kTile, st);
+    uint32_t *bitmap = need<uint32_t>(ws, "bitmap", (size_t)ntiles * nwords, st);
+    int *tile_cnt = need<int>(ws, "tile_cnt", ntiles, st);
+    int *entry_base = need<int>(ws, "entry_base", ntiles + 1, st);
+    int *word_prefix = need<int>(ws, "word_prefix", (size_t)ntiles * nwords, st);
+    FMM_CUDA_TRY(cudaMemsetAsync(tile_cells, 0xff, sizeof(int) * (size_t)ntiles * kTile, st));
+    FMM_CUDA_TRY(cudaMemsetAsync(bitmap, 0, sizeof(uint32_t) * (size_t)ntiles * nwords, st));
+    k_fill_tile_cells<<<(unsigned)ceil_div(ncells, 256), 256, 0, st>>>(c, ncells, tile_cells);
+    FMM_LAUNCH_CHECK();
+    if (m2l_total > 0) {
+        k_tile_bitmap<<<grid_for(m2l_total, 256), 256, 0, st>>>(L.m2l_tgt, L.m2l_slot, m2l_total,
+                                                              c.tile, nwords, bitmap);
+        FMM_LAUNCH_CHECK();
+    }
+    k_tile_popc<<<(unsigned)ceil_div(ntiles, 4), 128, 0, st>>>(bitmap, ntiles, nwords, tile_cnt);
+    FMM_LAUNCH_CHECK();
+    {
+        int *i32_tmp = need<int>(ws, "scan_i32", scan_temp_elems(ntiles), st);
+        scan_exclusive<int>(tile_cnt, entry_base, ntiles, entry_base + ntiles, i32_tmp, st);
+    }
+    int nent = 0;
+    sync_point(ws, st, flags, {{entry_base + ntiles, sizeof(int)}}, &nent);
+    int *entry_class = need<int>(ws, "entry_class", nent, st);
+    int *src = need<int>(ws, "src", (size_t)nent * kTile, st);
+    FMM_CUDA_TRY(cudaMemsetAsync(src, 0xff, sizeof(int) * (size_t)nent * kTile, st));
+    k_tile_entries<<<(unsigned)ceil_div(ntiles, 4), 128, 0, st>>>(bitmap, ntiles, nwords, entry_base,
+                                                                  word_prefix, entry_class,
+                                                                  get<int>(ws, "class_slot"));
+    FMM_LAUNCH_CHECK();
+    if (m2l_total > 0) {
+        k_tile_src<<<grid_for(m2l_total, 256), 256, 0, st>>>(L.m2l_tgt, L.m2l_src, L.m2l_slot,
+                                                           m2l_total, c.tile, c.lane, nwords,
+                                                           bitmap, word_prefix, entry_base, src);
+        FMM_LAUNCH_CHECK();
+    }
+    ev.rec(2, st);
+
+    // ---------------------------------------------------------- upward pass
+    float *M = need<float>(ws, "M", (size_t)ncells * P2pad, st);
+    float *Lx = need<float>(ws, "L", (size_t)ncells * P2pad, st);
+    float4 *far = need<float4>(ws, "far", N, st);
+    float4 *near = need<float4>(ws, "near", N, st);
+    {
+        const size_t sh = (size_t)32 * (P2pad + 1) * sizeof(float);
+        if (sh > 48 * 1024)
+            FMM_CUDA_TRY(cudaFuncSetAttribute(k_p2m, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+        k_p2m<<<nleaves, 32, sh, st>>>(c, leaves, nleaves, pts, box, p, P2pad, M);
+        FMM_LAUNCH_CHECK();
+    }
+    for (int l = depth - 1; l >= 0; --l) {
+        const int a = lstart[l], b = lstart[l + 1];
+        k_m2m<<<b - a, 128, P2pad * sizeof(float), st>>>(c, a, b, get<float>(ws, "m2m"), P2, P2pad, M);
+        FMM_LAUNCH_CHECK();
+    }
+    ev.rec(3, st);
+
+    // ---------------------------------------------------------- M2L
+    launch_m2l_simt(ntiles, entry_base, entry_class, src, tile_cells, M, get<float>(ws, "table"),
+                    P2pad, Lx, st);
+    ev.rec(4, st);
+
+    // ---------------------------------------------------------- downward pass
+    for (int l = 1; l <= depth; ++l) {
+        const int a = lstart[l], b = lstart[l + 1];
+        k_l2l<<<b - a, 128, P2pad * sizeof(float), st>>>(c, a, b, get<float>(ws, "l2l"), P2, P2pad, Lx);
+        FMM_LAUNCH_CHECK();
+    }
+    k_l2p<<<nleaves, 32, 4 * P2pad * sizeof(float), st>>>(c, leaves, nleaves, pts, box, p, P2pad, Lx,
+                                                          far);
+    FMM_LAUNCH_CHECK();
+    ev.rec(5, st);
+
+    // ---------------------------------------------------------- near field
+    k_p2p<<<(unsigned)ceil_div(nleaves, 4), 128, 0, st>>>(c, L, leaves, nleaves, pts, near);
+    FMM_LAUNCH_CHECK();
+    k_combine<<<grid_for(N, 256), 256, 0, st>>>(far, near, idx, N, phi, grad);
+    FMM_LAUNCH_CHECK();
+    ev.rec(6, st);
+
+    unsigned long long *inter = nullptr;
+    if (stats) {
+        inter = need<unsigned long long>(ws, "inter", 1, st);
+        FMM_CUDA_TRY(cudaMemsetAsync(inter, 0, sizeof(unsigned long long), st));
+        if (p2p_total > 0) {
+            k_p2p_interactions<<<grid_for(p2p_total, 256), 256, 0, st>>>(L.p2p_tgt, L.p2p_src,
+                                                                       p2p_total, c, inter);
+            FMM_LAUNCH_CHECK();
+        }
+    }
+    unsigned long long ninter = 0;
+    if (stats)
+        sync_point(ws, st, flags, {{inter, sizeof(unsigned long long)}}, &ninter);
+    else
+        sync_point(ws, st, flags, {}, nullptr);
+
+    ws.have_solve = true;
+    ws.N = N;
+    ws.ncells = ncells;
+    ws.nleaves = nleaves;
+    ws.depth = depth;
+    ws.P2pad = P2pad;
+    ws.nclass = nclass;
+    ws.nm2l = m2l_total;
+    ws.np2p = p2p_total;
+    if (stats) {
+        stats->ncells = ncells;
+        stats->nleaves = nleaves;
+        stats->depth = depth;
+        stats->n_p2p_pairs = p2p_total;
+        stats->n_p2p_interactions = (int64_t)ninter;
+        stats->n_m2l_pairs = m2l_total;
+        stats->n_offset_classes = nclass;
+        stats->n_m2l_blocks = nent;
+        stats->n_launches = g_launch_count - 1;  // minus the statistics kernel
+        stats->ms_tree = ev.ms(0, 1);
+        stats->ms_traverse = ev.ms(1, 2);
+        stats->ms_upward = ev.ms(2, 3);
+        stats->ms_m2l = ev.ms(3, 4);
+        stats->ms_downward = ev.ms(4, 5);
+        stats->ms_p2p = ev.ms(5, 6);
+        stats->ms_total = ev.ms(0, 6);
+    }
+}
+
+fmm_options resolve_opts(const fmm_options *opt)
+{
+    fmm_options o;
+    fmm_default_options(&o);
+    if (opt) o = *opt;
+    return o;
+}
+
+template <typename F>
+fmm_status guarded(F &&f)
+{
+    try {
+        f();
+        set_last_error("");
+        return FMM_OK;
+    } catch (const Error &e) {
+        set_last_error(e.msg);
+        return e.code;
+    } catch (const std::bad_alloc &) {
+        set_last_error("host allocation failed");
+        return FMM_ERR_NOMEM;
+    } catch (...) {
+        set_last_error("unexpected exception");
+        return FMM_ERR_CUDA;
+    }
+}
+
+}  // namespace
+}  // namespace fmm
+
+using namespace fmm;
+
+extern "C" {
+
+void fmm_default_options(fmm_options *opt)
+{
+    if (!opt) return;
+    opt->max_depth = 0;
+    opt->precision_mode = FMM_PREC_FP32;
+    opt->select_mode = 0;
+    opt->deterministic = 1;
+}
+
+fmm_status fmm_laplace3d_ex(const float *xyz, const float *q, int64_t N, int p, double theta,
+                            int ncrit, float *phi, float *grad, void *stream,
+                            const fmm_options *opt, fmm_stats *stats)
+{
+    return guarded([&] {
+        const fmm_options o = resolve_opts(opt);
+        validate(xyz, q, N, p, theta, ncrit, phi, grad, o);
+        Workspace &ws = workspace_for_current_device();
+        std::lock_guard<std::mutex> lk(ws.mu);
+        solve_locked(ws, xyz, q, N, p, theta, ncrit, phi, grad, (cudaStream_t)stream, o, stats);
+    });
+}
+
+fmm_status fmm_laplace3d(const float *xyz, const float *q, int64_t N, int p, double theta,
+                         int ncrit, float *phi, float *grad, void *stream)
+{
+    return fmm_laplace3d_ex(xyz, q, N, p, theta, ncrit, phi, grad, stream, nullptr, nullptr);
+}
+
+fmm_status fmm_laplace3d_host(const float *xyz_host, const float *q_host, int64_t N, int p,
+                              double theta, int ncrit, float *phi_host, float *grad_host,
+                              void *stream, const fmm_options *opt, fmm_stats *stats)
+{
+    return guarded([&] {
+        const fmm_options o = resolve_opts(opt);
+        validate(xyz_host, q_host, N, p, theta, ncrit, phi_host, grad_host, o);
+        Workspace &ws = workspace_for_current_device();
+        std::lock_guard<std::mutex> lk(ws.mu);
+        cudaStream_t st = (cudaStream_t)stream;
+        float *xd = need<float>(ws, "host_xyz", 3 * (size_t)N, st);
+        float *qd = need<float>(ws, "host_q", (size_t)N, st);
+        float *pd = need<float>(ws, "host_phi", (size_t)N, st);
+        float *gd = need<float>(ws, "host_grad", 3 * (size_t)N, st);
+        FMM_CUDA_TRY(cudaMemcpyAsync(xd, xyz_host, sizeof(float) * 3 * N, cudaMemcpyHostToDevice, st));
+        FMM_CUDA_TRY(cudaMemcpyAsync(qd, q_host, sizeof(float) * N, cudaMemcpyHostToDevice, st));
+        solve_locked(ws, xd, qd, N, p, theta, ncrit, pd, gd, st, o, stats);
+        FMM_CUDA_TRY(cudaMemcpyAsync(phi_host, pd, sizeof(float) * N, cudaMemcpyDeviceToHost, st));
+        FMM_CUDA_TRY(cudaMemcpyAsync(grad_host, gd, sizeof(float) * 3 * N, cudaMemcpyDeviceToHost, st));
+        FMM_CUDA_TRY(cudaStreamSynchronize(st));
+    });
+}
+
+fmm_status fmm_direct(const float *xyz, const float *q, int64_t N, float *phi, float *grad,
+                      void *stream)
+{
+    return guarded([&] {
+        if (!xyz || !q || !phi || !grad) throw Error{FMM_ERR_ARG, "null pointer argument"};
+        if (N < 1 || N >= (int64_t(1) << 31)) throw Error{FMM_ERR_ARG, "N must be in [1, 2^31)"};
+        cudaStream_t st = (cudaStream_t)stream;
+        k_direct<<<(unsigned)ceil_div(N, 256), 256, 0, st>>>(xyz, q, N, phi, grad);
+        FMM_LAUNCH_CHECK();
+        FMM_CUDA_TRY(cudaStreamSynchronize(st));
+    });
+}
+
+fmm_status fmm_export(int what, void *dst, int64_t capacity, int64_t *needed)
+{
+    return guarded([&] {
+        Workspace &ws = workspace_for_current_device();
+        std::lock_guard<std::mutex> lk(ws.mu);
+        if (!ws.have_solve) throw Error{FMM_ERR_ARG, "no solve has completed on this device"};
+        int64_t bytes = 0;
+        switch (what) {
+            case FMM_EXPORT_BOX: bytes = 4 * sizeof(double); break;
+            case FMM_EXPORT_KEYS: bytes = ws.N * sizeof(uint64_t); break;
+            case FMM_EXPORT_ORDER: bytes = ws.N * sizeof(int32_t); break;
+            case FMM_EXPORT_CELLS: bytes = (int64_t)ws.ncells * 6 * sizeof(int64_t); break;
+            case FMM_EXPORT_P2P: bytes = ws.np2p * 2 * sizeof(int32_t); break;
+            case FMM_EXPORT_M2L: bytes = ws.nm2l * 3 * sizeof(int32_t); break;
+            case FMM_EXPORT_MULTIPOLE:
+            case FMM_EXPORT_LOCAL: bytes = (int64_t)ws.ncells * ws.P2pad * sizeof(float); break;
+            default: throw Error{FMM_ERR_ARG, "unknown export kind"};
+        }
+        if (needed) *needed = bytes;
+        if (!dst) return;
+        if (capacity < bytes) throw Error{FMM_ERR_ARG, "export buffer too small"};
+        auto d2h = [](void *h, const void *d, size_t n) {
+            if (n) FMM_CUDA_TRY(cudaMemcpy(h, d, n, cudaMemcpyDeviceToHost));
+        };
+        switch (what) {
+            case FMM_EXPORT_BOX: d2h(dst, get<double>(ws, "box"), bytes); break;
+            case FMM_EXPORT_KEYS: d2h(dst, get<uint64_t>(ws, "keys"), bytes); break;
+            case FMM_EXPORT_ORDER: d2h(dst, get<uint32_t>(ws, "idx"), bytes); break;
+            case FMM_EXPORT_MULTIPOLE: d2h(dst, get<float>(ws, "M"), bytes); break;
+            case FMM_EXPORT_LOCAL: d2h(dst, get<float>(ws, "L"), bytes); break;
+            case FMM_EXPORT_CELLS: {
+                const int n = ws.ncells;
+                std::vector<int> lv(n), b(n), e(n), par(n), nch(n);
+                std::vector<uint64_t> pre(n);
+                d2h(lv.data(), get<int>(ws, "c_level"), n * sizeof(int));
+                d2h(pre.data(), get<uint64_t>(ws, "c_prefix"), n * sizeof(uint64_t));
+                d2h(b.data(), get<int>(ws, "c_begin"), n * sizeof(int));
+                d2h(e.data(), get<int>(ws, "c_end"), n * sizeof(int));
+                d2h(par.data(), get<int>(ws, "c_parent"), n * sizeof(int));
+                d2h(nch.data(), get<int>(ws, "c_nchild"), n * sizeof(int));
+                int64_t *o = static_cast<int64_t *>(dst);
+                for (int i = 0; i < n; ++i) {
+                    o[6 * i] = lv[i];
+                    o[6 * i + 1] = (int64_t)pre[i];
+                    o[6 * i + 2] = b[i];
+                    o[6 * i + 3] = e[i];
+                    o[6 * i + 4] = par[i];
+                    o[6 * i + 5] = nch[i];
+                }
+                break;
+            }
+            case FMM_EXPORT_P2P: {
+                const int64_t n = ws.np2p;
+                std::vector<int> t(n), s(n);
+                d2h(t.data(), get<int>(ws, "p2p_tgt"), n * sizeof(int));
+                d2h(s.data(), get<int>(ws, "p2p_src"), n * sizeof(int));
+                int32_t *o = static_cast<int32_t *>(dst);
+                for (int64_t i = 0; i < n; ++i) {
+                    o[2 * i] = t[i];
+                    o[2 * i + 1] = s[i];
+                }
+                break;
+            }
+            case FMM_EXPORT_M2L: {
+                const int64_t n = ws.nm2l;
+                std::vector<int> t(n), s(n), k(n);
+                d2h(t.data(), get<int>(ws, "m2l_tgt"), n * sizeof(int));
+                d2h(s.data(), get<int>(ws, "m2l_src"), n * sizeof(int));
+                d2h(k.data(), get<uint32_t>(ws, "m2l_slot"), n * sizeof(int));
+                int32_t *o = static_cast<int32_t *>(dst);
+                for (int64_t i = 0; i < n; ++i) {
+                    o[3 * i] = t[i];
+                    o[3 * i + 1] = s[i];
+                    o[3 * i + 2] = k[i];
+                }
+                break;
+            }
+        }
+    });
+}
+
+const char *fmm_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,103 @@
+// kernels.cuh -- kernel declarations and the device-side data layout shared by
+// the translation units of the CUDA path.
+#pragma once
+
+#include "common.cuh"
+
+namespace fmm {
+
+// Device error flags (int[kNumFlags]).
+enum {
+    kFlagNonfinite = 0,   // NaN/Inf coordinate
+    kFlagHashFull = 1,    // offset-class hash table full
+    kFlagClassRange = 2,  // an offset component does not fit the class key
+    kFlagStack = 3,       // traversal stack overflow
+    kNumFlags = 8
+};
+
+// Structure-of-arrays cells, level by level (Morton order within a level).
+struct CellArrays {
+    int *level;
+    uint64_t *prefix;  // top 3*level key bits, right-aligned
+    int *begin, *end;  // sorted particle range
+    int *parent, *child0, *nchild;
+    int *tile, *lane;  // M2L GEMM tile of this cell as a target
+};
+
+// Interaction lists written by the traversal (CSR per target cell).
+struct ListArrays {
+    int *m2l_src;         // source cell per M2L pair
+    int *m2l_tgt;         // target cell per M2L pair
+    uint32_t *m2l_slot;   // class hash slot, later replaced by the class id
+    int *p2p_src, *p2p_tgt;
+    int *m2l_off, *m2l_cnt, *p2p_off, *p2p_cnt;  // per cell
+    int *def_off, *def_cnt;                      // per cell: deferred sources
+    int *def_src;
+};
+
+constexpr int kHashBits = 18;
+constexpr uint32_t kHashCap = 1u << kHashBits;
+constexpr uint64_t kHashEmpty = ~0ull;
+
+// tree.cu
+__global__ void k_bbox(const float *xyz, int64_t n, uint32_t *bbox_u, int *flags);
+__global__ void k_morton(const float *xyz, int64_t n, const uint32_t *bbox_u, double *box,
+                         uint64_t *keys, uint32_t *idx);
+__global__ void k_permute(const float *xyz, const float *q, const uint32_t *idx, int64_t n,
+                          float4 *out);
+__global__ void k_init_root(CellArrays c, int n);
+__global__ void k_split_count(CellArrays c, const uint64_t *keys, int a, int b, int level,
+                              int ncrit, int max_depth, int64_t *packed);
+__global__ void k_split_emit(CellArrays c, const uint64_t *keys, int a, int b, int level,
+                             const int64_t *packed, const int64_t *ex, int tile_base);
+__global__ void k_fill_tile_cells(CellArrays c, int ncells, int *tile_cells);
+__global__ void k_leaf_flags(CellArrays c, int ncells, int *flag);
+__global__ void k_leaf_compact(CellArrays c, int ncells, const int *ex, int *leaves);
+
+// traverse.cu
+__global__ void k_traverse_count(CellArrays c, ListArrays L, int a, int b, double theta2,
+                                 int64_t *cnt_mp, int *cnt_d, int *flags);
+__global__ void k_traverse_write(CellArrays c, ListArrays L, int a, int b, double theta2,
+                                 const int64_t *off_mp, const int *off_d, int64_t m2l_base,
+                                 int64_t p2p_base, int def_base, uint64_t *hash_keys,
+                                 int *flags);
+__global__ void k_hash_flags(const uint64_t *hash_keys, int *flag);
+__global__ void k_hash_compact(const uint64_t *hash_keys, const int *ex, uint64_t *ukeys,
+                               uint32_t *uslot);
+__global__ void k_slot_to_class(const uint32_t *uslot, int nclass, int *slot_class);
+__global__ void k_m2l_class(uint32_t *m2l_slot, int64_t n, const int *slot_class);
+__global__ void k_tile_bitmap(const int *m2l_tgt, const uint32_t *m2l_class, int64_t n,
+                              const int *cell_tile, int nwords, uint32_t *bitmap);
+__global__ void k_tile_popc(const uint32_t *bitmap, int ntiles, int nwords, int *cnt);
+__global__ void k_tile_entries(const uint32_t *bitmap, int ntiles, int nwords,
+                               const int *entry_base, int *word_prefix, int *entry_class,
+                               const int *class_slot);
+__global__ void k_tile_src(const int *m2l_tgt, const int *m2l_src, const uint32_t *m2l_class,
+                           int64_t n, const int *cell_tile, const int *cell_lane, int nwords,
+                           const uint32_t *bitmap, const int *word_prefix,
+                           const int *entry_base, int *src);
+
+// expansions.cu
+__global__ void k_build_m2l_tables(const uint64_t *class_keys, const int *cache_slot, int nnew,
+                                   int p, int P2pad, float *table);
+__global__ void k_build_shift_tables(int p, int P2pad, float *m2m, float *l2l);
+__global__ void k_p2m(CellArrays c, const int *leaves, int nleaves, const float4 *pts,
+                      const double *box, int p, int P2pad, float *M);
+__global__ void k_m2m(CellArrays c, int a, int b, const float *m2m, int P2, int P2pad, float *M);
+__global__ void k_l2l(CellArrays c, int a, int b, const float *l2l, int P2, int P2pad, float *L);
+__global__ void k_l2p(CellArrays c, const int *leaves, int nleaves, const float4 *pts,
+                      const double *box, int p, int P2pad, const float *L, float4 *far);
+
+// m2l.cu
+void launch_m2l_simt(int ntiles, const int *entry_base, const int *entry_class, const int *src,
+                     const int *tile_cells, const float *M, const float *table, int P2pad,
+                     float *L, cudaStream_t st);
+
+// p2p.cu
+__global__ void k_p2p(CellArrays c, ListArrays L, const int *leaves, int nleaves,
+                      const float4 *pts, float4 *near);
+__global__ void k_direct(const float *xyz, const float *q, int64_t n, float *phi, float *grad);
+__global__ void k_combine(const float4 *far, const float4 *near, const uint32_t *idx, int64_t n,
+                          float *phi, float *grad);
+
+}  // namespace fmm

@@ -1,0 +1,349 @@
+// traverse.cu -- dual tree traversal on the GPU and the M2L offset-class tiles.
+//
+// The paper's traversal (section "Dual tree traversal") pops (target, source)
+// pairs from a LIFO stack, splits the larger cell, and for every new pair
+// either evaluates it (far: MAC accepted -> cell-cell; both leaves ->
+// particle-particle) or pushes it back.  The fate of a pair depends only on
+// the pair, so the same set of interactions is produced by processing targets
+// level by level: a target T receives from its parent the sources that were
+// pending with the decision "split the target" (the paper: "target cells
+// inherit a unique stack of source cells from their parents"), and resolves
+// each inherited source S by
+//     interact(T,S): MAC -> M2L;  else T,S leaves -> P2P;
+//                    else split S (S larger, or T a leaf) and interact with
+//                    its children, or defer S to T's children.
+// One warp handles one target; lanes take inherited sources in order and
+// resolve each with a small depth-first stack.  Outputs are written in a
+// deterministic order (count pass, scan, write pass), grouped by target.
+//
+// MAC (reading R3 of the oracle): r = half side, accept iff R > 0 and
+// (r_t + r_s)^2 <= theta^2 R^2, evaluated in integer units of side/2^22 so the
+// decision is exact and identical to an FP64 CPU evaluation.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace fmm {
+
+namespace {
+
+constexpr int kStack = 192;
+
+struct TargetInfo {
+    int t, level;
+    bool leaf;
+    int64_t C[3], h;
+};
+
+__device__ __forceinline__ bool mac_accept(const TargetInfo &T, const int64_t Cs[3], int64_t hs,
+                                           double theta2)
+{
+    int64_t R2 = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int64_t d = T.C[a] - Cs[a];
+        R2 += d * d;
+    }
+    if (R2 == 0) return false;
+    const int64_t rs = T.h + hs;
+    return (double)(rs * rs) <= __dmul_rn(theta2, (double)R2);
+}
+
+__device__ __forceinline__ uint64_t mix64(uint64_t z)
+{
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+__device__ uint32_t hash_insert(uint64_t *table, uint64_t key, int *flags)
+{
+    uint32_t h = (uint32_t)mix64(key) & (kHashCap - 1);
+    for (uint32_t probe = 0; probe < kHashCap; ++probe) {
+        uint64_t cur = table[h];
+        if (cur == key) return h;
+        if (cur == kHashEmpty) {
+            uint64_t old = atomicCAS((unsigned long long *)&table[h], (unsigned long long)kHashEmpty,
+                                     (unsigned long long)key);
+            if (old == kHashEmpty || old == key) return h;
+        }
+        h = (h + 1) & (kHashCap - 1);
+    }
+    atomicOr(&flags[kFlagHashFull], 1);
+    return 0;
+}
+
+// Offset class of an accepted pair: level difference and the centre offset in
+// units of the finer cell's half side.
+__device__ __forceinline__ uint64_t class_key(const TargetInfo &T, int ls, const int64_t Cs[3],
+                                              int *flags)
+{
+    const int lf = max(T.level, ls);
+    const int64_t u = (int64_t)1 << (kKeyBits - lf);
+    uint64_t key = (uint64_t)(ls - T.level + 64) << 57;
+    const int64_t lim = (int64_t)1 << 18;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int64_t d = (T.C[a] - Cs[a]) / u;
+        if (d <= -lim || d >= lim) atomicOr(&flags[kFlagClassRange], 1);
+        key |= (uint64_t)((d + lim) & 0x7ffff) << (38 - 19 * a);
+    }
+    return key;
+}
+
+struct Counts {
+    int m, p, d;
+};
+
+// Resolves one inherited source S0 for target T.  WRITE = false only counts.
+template <bool WRITE>
+__device__ Counts resolve(const TargetInfo &T, int S0, const CellArrays &c, const ListArrays &L,
+                          double theta2, int64_t m_pos, int64_t p_pos, int d_pos,
+                          uint64_t *hash_keys, int *flags)
+{
+    Counts n = {0, 0, 0};
+    int stk[kStack];
+    int sp = 0;
+    stk[sp++] = S0;
+    while (sp > 0) {
+        const int S = stk[--sp];
+        const int ls = c.level[S];
+        const int nchS = c.nchild[S];
+        int64_t Cs[3], hs;
+        cell_int_geom(ls, c.prefix[S], Cs, hs);
+        if (mac_accept(T, Cs, hs, theta2)) {
+            if (WRITE) {
+                L.m2l_src[m_pos + n.m] = S;
+                L.m2l_tgt[m_pos + n.m] = T.t;
+                L.m2l_slot[m_pos + n.m] = hash_insert(hash_keys, class_key(T, ls, Cs, flags), flags);
+            }
+            ++n.m;
+        } else if (T.leaf && nchS == 0) {
+            if (WRITE) {
+                L.p2p_src[p_pos + n.p] = S;
+                L.p2p_tgt[p_pos + n.p] = T.t;
+            }
+            ++n.p;
+        } else if (T.leaf || (ls < T.level && nchS > 0)) {
+            if (sp + nchS > kStack) {
+                atomicOr(&flags[kFlagStack], 1);
+                break;
+            }
+            const int c0 = c.child0[S];
+            for (int k = nchS - 1; k >= 0; --k) stk[sp++] = c0 + k;
+        } else {
+            if (WRITE) L.def_src[d_pos + n.d] = S;
+            ++n.d;
+        }
+    }
+    return n;
+}
+
+__device__ __forceinline__ TargetInfo load_target(const CellArrays &c, int t)
+{
+    TargetInfo T;
+    T.t = t;
+    T.level = c.level[t];
+    T.leaf = c.nchild[t] == 0;
+    cell_int_geom(T.level, c.prefix[t], T.C, T.h);
+    return T;
+}
+
+__device__ __forceinline__ int warp_sum(int v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ int warp_excl(int v)
+{
+    const int lane = threadIdx.x & 31;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    return x - v;
+}
+
+}  // namespace
+
+// Count pass for the targets [a, b) (one warp each).
+__global__ void k_traverse_count(CellArrays c, ListArrays L, int a, int b, double theta2,
+                                 int64_t *__restrict__ cnt_mp, int *__restrict__ cnt_d,
+                                 int *__restrict__ flags)
+{
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int t = a + warp;
+    if (t >= b) return;
+    const TargetInfo T = load_target(c, t);
+    const int P = c.parent[t];
+    const int i0 = L.def_off[P], ni = L.def_cnt[P];
+    int m = 0, p = 0, d = 0;
+    for (int k = lane; k < ni; k += 32) {
+        Counts n = resolve<false>(T, L.def_src[i0 + k], c, L, theta2, 0, 0, 0, nullptr, flags);
+        m += n.m;
+        p += n.p;
+        d += n.d;
+    }
+    m = warp_sum(m);
+    p = warp_sum(p);
+    d = warp_sum(d);
+    if (lane == 0) {
+        cnt_mp[t - a] = ((int64_t)m << 32) | (int64_t)p;
+        cnt_d[t - a] = d;
+    }
+}
+
+// Write pass: same resolution order, outputs at the scanned offsets.
+__global__ void k_traverse_write(CellArrays c, ListArrays L, int a, int b, double theta2,
+                                 const int64_t *__restrict__ off_mp, const int *__restrict__ off_d,
+                                 int64_t m2l_base, int64_t p2p_base, int def_base,
+                                 uint64_t *__restrict__ hash_keys, int *__restrict__ flags)
+{
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int t = a + warp;
+    if (t >= b) return;
+    const TargetInfo T = load_target(c, t);
+    const int P = c.parent[t];
+    const int i0 = L.def_off[P], ni = L.def_cnt[P];
+    const int64_t om = m2l_base + (off_mp[t - a] >> 32);
+    const int64_t op = p2p_base + (off_mp[t - a] & 0xffffffffll);
+    const int od = def_base + off_d[t - a];
+    int64_t rm = 0, rp = 0;
+    int rd = 0;
+    for (int k0 = 0; k0 < ni; k0 += 32) {
+        const int k = k0 + lane;
+        const int S0 = k < ni ? L.def_src[i0 + k] : -1;
+        Counts n = {0, 0, 0};
+        if (S0 >= 0) n = resolve<false>(T, S0, c, L, theta2, 0, 0, 0, nullptr, flags);
+        const int em = warp_excl(n.m), ep = warp_excl(n.p), ed = warp_excl(n.d);
+        if (S0 >= 0)
+            resolve<true>(T, S0, c, L, theta2, om + rm + em, op + rp + ep, od + rd + ed, hash_keys,
+                          flags);
+        rm += warp_sum(n.m);
+        rp += warp_sum(n.p);
+        rd += warp_sum(n.d);
+    }
+    if (lane == 0) {
+        L.m2l_off[t] = (int)om;
+        L.m2l_cnt[t] = (int)rm;
+        L.p2p_off[t] = (int)op;
+        L.p2p_cnt[t] = (int)rp;
+        L.def_off[t] = od;
+        L.def_cnt[t] = rd;
+    }
+}
+
+// ---------------------------------------------------------------- classes
+
+__global__ void k_hash_flags(const uint64_t *__restrict__ hash_keys, int *__restrict__ flag)
+{
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < kHashCap) flag[i] = hash_keys[i] != kHashEmpty;
+}
+
+__global__ void k_hash_compact(const uint64_t *__restrict__ hash_keys, const int *__restrict__ ex,
+                               uint64_t *__restrict__ ukeys, uint32_t *__restrict__ uslot)
+{
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < kHashCap && hash_keys[i] != kHashEmpty) {
+        ukeys[ex[i]] = hash_keys[i];
+        uslot[ex[i]] = i;
+    }
+}
+
+__global__ void k_slot_to_class(const uint32_t *__restrict__ uslot, int nclass,
+                                int *__restrict__ slot_class)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < nclass) slot_class[uslot[r]] = r;
+}
+
+__global__ void k_m2l_class(uint32_t *__restrict__ m2l_slot, int64_t n,
+                            const int *__restrict__ slot_class)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        m2l_slot[i] = (uint32_t)slot_class[m2l_slot[i]];
+}
+
+// ---------------------------------------------------------------- tiles
+
+__global__ void k_tile_bitmap(const int *__restrict__ m2l_tgt, const uint32_t *__restrict__ m2l_class,
+                              int64_t n, const int *__restrict__ cell_tile, int nwords,
+                              uint32_t *__restrict__ bitmap)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t cl = m2l_class[i];
+        const int tile = cell_tile[m2l_tgt[i]];
+        uint32_t *w = &bitmap[(int64_t)tile * nwords + (cl >> 5)];
+        const uint32_t bit = 1u << (cl & 31);
+        if (!(__ldg(w) & bit)) atomicOr(w, bit);
+    }
+}
+
+__global__ void k_tile_popc(const uint32_t *__restrict__ bitmap, int ntiles, int nwords,
+                            int *__restrict__ cnt)
+{
+    const int tile = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (tile >= ntiles) return;
+    int s = 0;
+    for (int w = lane; w < nwords; w += 32) s += __popc(bitmap[(int64_t)tile * nwords + w]);
+    s = warp_sum(s);
+    if (lane == 0) cnt[tile] = s;
+}
+
+// One warp per tile: word prefix counts and the list of (cache slot of) classes.
+__global__ void k_tile_entries(const uint32_t *__restrict__ bitmap, int ntiles, int nwords,
+                               const int *__restrict__ entry_base, int *__restrict__ word_prefix,
+                               int *__restrict__ entry_class, const int *__restrict__ class_slot)
+{
+    const int tile = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (tile >= ntiles) return;
+    int run = entry_base[tile];
+    for (int w0 = 0; w0 < nwords; w0 += 32) {
+        const int w = w0 + lane;
+        const uint32_t bits = w < nwords ? bitmap[(int64_t)tile * nwords + w] : 0u;
+        const int pc = __popc(bits);
+        const int ex = warp_excl(pc);
+        if (w < nwords) {
+            word_prefix[(int64_t)tile * nwords + w] = run + ex;
+            uint32_t rem = bits;
+            int e = run + ex;
+            while (rem) {
+                const int bpos = __ffs(rem) - 1;
+                rem &= rem - 1;
+                entry_class[e++] = class_slot[w * 32 + bpos];
+            }
+        }
+        run += warp_sum(pc);
+    }
+}
+
+__global__ void k_tile_src(const int *__restrict__ m2l_tgt, const int *__restrict__ m2l_src,
+                           const uint32_t *__restrict__ m2l_class, int64_t n,
+                           const int *__restrict__ cell_tile, const int *__restrict__ cell_lane,
+                           int nwords, const uint32_t *__restrict__ bitmap,
+                           const int *__restrict__ word_prefix, const int *__restrict__ entry_base,
+                           int *__restrict__ src)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int t = m2l_tgt[i];
+        const uint32_t cl = m2l_class[i];
+        const int tile = cell_tile[t];
+        const int64_t wi = (int64_t)tile * nwords + (cl >> 5);
+        const uint32_t below = bitmap[wi] & ((1u << (cl & 31)) - 1u);
+        const int e = word_prefix[wi] + __popc(below);
+        src[(int64_t)e * kTile + cell_lane[t]] = m2l_src[i];
+    }
+}
+
+}  // namespace fmm

@@ -1,0 +1,230 @@
+// tree.cu -- bounding box, Morton keys, particle permutation and the adaptive
+// octree, built level by level on the GPU.
+//
+// The paper builds its adaptive tree (at most N_crit particles per cell,
+// Results section) on the host CPU; here every step runs on the device.
+// Quantisation follows the FP64 reading documented in the header: the box is
+// the cube [lo, lo + side) with side the largest extent, a coordinate maps to
+// k = min(2^21 - 1, floor((x - lo) * (2^21 / side))) with each operation a single
+// IEEE round-to-nearest FP64 operation (__dsub_rn/__dmul_rn/__ddiv_rn, no
+// contraction), so keys match an FP64 CPU computation bit for bit.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace fmm {
+
+namespace {
+
+__device__ __forceinline__ uint32_t float_to_ordered(float f)
+{
+    uint32_t u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+__device__ __forceinline__ float ordered_to_float(uint32_t u)
+{
+    return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+
+}  // namespace
+
+// bbox_u[0..2] = ordered min, [3..5] = ordered max; flags[kFlagNonfinite] set on NaN/Inf.
+__global__ void k_bbox(const float *__restrict__ xyz, int64_t n, uint32_t *__restrict__ bbox_u,
+                       int *__restrict__ flags)
+{
+    float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    bool bad = false;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            float v = xyz[3 * i + a];
+            bad |= !isfinite(v);
+            mn[a] = fminf(mn[a], v);
+            mx[a] = fmaxf(mx[a], v);
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            mn[a] = fminf(mn[a], __shfl_xor_sync(0xffffffffu, mn[a], o));
+            mx[a] = fmaxf(mx[a], __shfl_xor_sync(0xffffffffu, mx[a], o));
+        }
+    }
+    bad = __any_sync(0xffffffffu, bad);
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            atomicMin(&bbox_u[a], float_to_ordered(mn[a]));
+            atomicMax(&bbox_u[3 + a], float_to_ordered(mx[a]));
+        }
+        if (bad) atomicOr(&flags[kFlagNonfinite], 1);
+    }
+}
+
+// Decodes the box into box[0..2] = lo, box[3] = side (FP64), then writes keys
+// and the identity permutation.
+__global__ void k_morton(const float *__restrict__ xyz, int64_t n,
+                         const uint32_t *__restrict__ bbox_u, double *__restrict__ box,
+                         uint64_t *__restrict__ keys, uint32_t *__restrict__ idx)
+{
+    double lo[3], side = 0.0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = (double)ordered_to_float(bbox_u[a]);
+        double hi = (double)ordered_to_float(bbox_u[3 + a]);
+        double ext = __dsub_rn(hi, lo[a]);
+        side = ext > side ? ext : side;
+    }
+    if (!(side > 0.0)) side = 1.0;
+    const double s = __ddiv_rn(2097152.0, side);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        box[0] = lo[0];
+        box[1] = lo[1];
+        box[2] = lo[2];
+        box[3] = side;
+    }
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t k[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            double t = __dsub_rn((double)xyz[3 * i + a], lo[a]);
+            double f = floor(__dmul_rn(t, s));
+            // NaN/Inf inputs are reported through the flag; keep the key in range.
+            if (!(f >= 0.0)) f = 0.0;
+            if (f > 2097151.0) f = 2097151.0;
+            k[a] = (uint32_t)f;
+        }
+        keys[i] = spread3_dev(k[0]) | (spread3_dev(k[1]) << 1) | (spread3_dev(k[2]) << 2);
+        idx[i] = (uint32_t)i;
+    }
+}
+
+// Sorted particles as float4 (x, y, z, q).
+__global__ void k_permute(const float *__restrict__ xyz, const float *__restrict__ q,
+                          const uint32_t *__restrict__ idx, int64_t n, float4 *__restrict__ out)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t o = idx[i];
+        out[i] = make_float4(xyz[3 * o], xyz[3 * o + 1], xyz[3 * o + 2], q[o]);
+    }
+}
+
+__global__ void k_init_root(CellArrays c, int n)
+{
+    c.level[0] = 0;
+    c.prefix[0] = 0;
+    c.begin[0] = 0;
+    c.end[0] = n;
+    c.parent[0] = -1;
+    c.child0[0] = -1;
+    c.nchild[0] = 0;
+    c.tile[0] = 0;
+    c.lane[0] = 0;
+}
+
+// First index in keys[b, e) whose level-(l+1) octant digit is >= o.
+__device__ __forceinline__ int lower_octant(const uint64_t *__restrict__ keys, int b, int e,
+                                            int shift, uint32_t o)
+{
+    while (b < e) {
+        int mid = (b + e) >> 1;
+        if ((uint32_t)((keys[mid] >> shift) & 7ull) < o)
+            b = mid + 1;
+        else
+            e = mid;
+    }
+    return b;
+}
+
+// For the cells [a, b) at level l: packed[c-a] = nchild | (split ? 1 << 32 : 0).
+__global__ void k_split_count(CellArrays c, const uint64_t *__restrict__ keys, int a, int b,
+                              int level, int ncrit, int max_depth, int64_t *__restrict__ packed)
+{
+    const int i = a + blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= b) return;
+    const int cb = c.begin[i], ce = c.end[i];
+    int64_t v = 0;
+    if (ce - cb > ncrit && level < max_depth) {
+        const int shift = 3 * (kKeyBits - level - 1);
+        int nch = 0;
+        int lo = cb;
+#pragma unroll
+        for (int o = 0; o < 8; ++o) {
+            int hi = lower_octant(keys, lo, ce, shift, (uint32_t)o + 1);
+            nch += hi > lo;
+            lo = hi;
+        }
+        v = (int64_t)nch | ((int64_t)1 << 32);
+    }
+    packed[i - a] = v;
+}
+
+// Writes the children of the cells [a, b) (level l) starting at cell index b,
+// using the exclusive scan `ex` of the packed counts; assigns each child its
+// M2L tile (parent window of kTile split parents x octant) and lane.
+__global__ void k_split_emit(CellArrays c, const uint64_t *__restrict__ keys, int a, int b,
+                             int level, const int64_t *__restrict__ packed,
+                             const int64_t *__restrict__ ex, int tile_base)
+{
+    const int i = a + blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= b) return;
+    const int64_t v = packed[i - a];
+    if (v == 0) {
+        c.child0[i] = -1;
+        c.nchild[i] = 0;
+        return;
+    }
+    const int64_t e = ex[i - a];
+    const int first = b + (int)(e & 0xffffffffll);
+    const int rank = (int)(e >> 32);
+    const int window = rank / kTile, lane = rank % kTile;
+    const int cb = c.begin[i], ce = c.end[i];
+    const int shift = 3 * (kKeyBits - level - 1);
+    const uint64_t pre = c.prefix[i];
+    int lo = cb, k = 0;
+    for (int o = 0; o < 8; ++o) {
+        int hi = lower_octant(keys, lo, ce, shift, (uint32_t)o + 1);
+        if (hi > lo) {
+            const int ch = first + k++;
+            c.level[ch] = level + 1;
+            c.prefix[ch] = (pre << 3) | (uint64_t)o;
+            c.begin[ch] = lo;
+            c.end[ch] = hi;
+            c.parent[ch] = i;
+            c.child0[ch] = -1;
+            c.nchild[ch] = 0;
+            c.tile[ch] = tile_base + window * 8 + o;
+            c.lane[ch] = lane;
+        }
+        lo = hi;
+    }
+    c.child0[i] = first;
+    c.nchild[i] = k;
+}
+
+__global__ void k_fill_tile_cells(CellArrays c, int ncells, int *__restrict__ tile_cells)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ncells) return;
+    tile_cells[(int64_t)c.tile[i] * kTile + c.lane[i]] = i;
+}
+
+// Compact list of leaf cells (order preserved) via a precomputed exclusive scan.
+__global__ void k_leaf_flags(CellArrays c, int ncells, int *__restrict__ flag)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < ncells) flag[i] = c.nchild[i] == 0;
+}
+
+__global__ void k_leaf_compact(CellArrays c, int ncells, const int *__restrict__ ex,
+                               int *__restrict__ leaves)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < ncells && c.nchild[i] == 0) leaves[ex[i]] = i;
+}
+
+}  // namespace fmm

@@ -1,0 +1,193 @@
+"""Python binding of the C ABI in ``include/fmm.h`` (argument marshalling only).
+
+Every step of the solve runs in the CUDA library ``libfmm.so``; this module
+passes device pointers and the current torch stream.  There is no CPU
+fallback: if the library is missing or the tensors are not CUDA float32, the
+call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libfmm.so")
+
+FMM_OK, FMM_ERR_ARG, FMM_ERR_NONFINITE, FMM_ERR_CAPACITY, FMM_ERR_CUDA, FMM_ERR_TIMEOUT, \
+    FMM_ERR_NOMEM = range(7)
+PRECISION = {"fp32": 0, "tf32x3": 1, "bf16x3": 2}
+EXPORT = {"box": 0, "keys": 1, "order": 2, "cells": 3, "p2p": 4, "m2l": 5, "multipole": 6,
+          "local": 7}
+
+# every symbol the header declares
+ABI_SYMBOLS = ("fmm_default_options", "fmm_laplace3d", "fmm_laplace3d_ex", "fmm_laplace3d_host",
+               "fmm_direct", "fmm_export", "fmm_last_error")
+
+
+class FmmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"fmm status {status}: {msg}")
+        self.status = status
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("max_depth", ctypes.c_int), ("precision_mode", ctypes.c_int),
+                ("select_mode", ctypes.c_int), ("deterministic", ctypes.c_int)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("ncells", "nleaves", "depth", "n_p2p_pairs",
+                                              "n_p2p_interactions", "n_m2l_pairs",
+                                              "n_offset_classes", "n_m2l_blocks",
+                                              "n_launches")] + \
+               [(n, ctypes.c_float) for n in ("ms_tree", "ms_upward", "ms_traverse", "ms_m2l",
+                                              "ms_downward", "ms_p2p", "ms_total")]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libfmm.so (built in-tree by ``paper_1108_5815_gb300.build``)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = path or LIB_PATH
+        if not os.path.exists(path):
+            raise FmmError(FMM_ERR_CUDA, f"CUDA library not built: {path} is missing "
+                                         "(run paper_1108_5815_gb300.build.build())")
+        L = ctypes.CDLL(path)
+        vp, i64, f32p = ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p
+        L.fmm_default_options.argtypes = [ctypes.POINTER(Options)]
+        L.fmm_default_options.restype = None
+        L.fmm_laplace3d.argtypes = [vp, vp, i64, ctypes.c_int, ctypes.c_double, ctypes.c_int, vp, vp, vp]
+        L.fmm_laplace3d_ex.argtypes = L.fmm_laplace3d.argtypes + [ctypes.POINTER(Options),
+                                                                  ctypes.POINTER(Stats)]
+        L.fmm_laplace3d_host.argtypes = L.fmm_laplace3d_ex.argtypes
+        L.fmm_direct.argtypes = [vp, vp, i64, vp, vp, vp]
+        L.fmm_export.argtypes = [ctypes.c_int, vp, i64, ctypes.POINTER(i64)]
+        L.fmm_last_error.restype = ctypes.c_char_p
+        for name in ("fmm_laplace3d", "fmm_laplace3d_ex", "fmm_laplace3d_host", "fmm_direct",
+                     "fmm_export"):
+            getattr(L, name).restype = ctypes.c_int
+        _lib = L
+        return L
+
+
+def last_error() -> str:
+    return load().fmm_last_error().decode()
+
+
+def _check(status: int):
+    if status != FMM_OK:
+        raise FmmError(status, last_error())
+
+
+def _options(max_depth=0, precision="fp32", select_mode=0):
+    o = Options()
+    load().fmm_default_options(ctypes.byref(o))
+    o.max_depth = max_depth
+    o.precision_mode = PRECISION[precision]
+    o.select_mode = select_mode
+    return o
+
+
+def _stream_ptr(torch, device):
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _dev_f32(t, shape, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise FmmError(FMM_ERR_ARG, f"{name} must be a CUDA tensor")
+    if t.dtype != torch.float32:
+        raise FmmError(FMM_ERR_ARG, f"{name} must be float32")
+    if tuple(t.shape) != shape:
+        raise FmmError(FMM_ERR_ARG, f"{name} must have shape {shape}, got {tuple(t.shape)}")
+    return t.contiguous()
+
+
+def laplace3d(xyz, q, p: int, theta: float, ncrit: int, *, max_depth: int = 0,
+              precision: str = "fp32", stats: bool = False, out=None):
+    """FMM potential and gradient for CUDA float32 xyz[N,3], q[N].
+
+    Returns (phi[N], grad[N,3]) as CUDA tensors (and a stats dict if ``stats``)."""
+    import torch
+    n = int(xyz.shape[0]) if hasattr(xyz, "shape") else 0
+    xyz = _dev_f32(xyz, (n, 3), "xyz")
+    q = _dev_f32(q, (n,), "q")
+    with torch.cuda.device(xyz.device):
+        if out is None:
+            phi = torch.empty(n, device=xyz.device, dtype=torch.float32)
+            grad = torch.empty(n, 3, device=xyz.device, dtype=torch.float32)
+        else:
+            phi, grad = out
+        o = _options(max_depth, precision)
+        st = Stats()
+        _check(load().fmm_laplace3d_ex(xyz.data_ptr(), q.data_ptr(), n, p, float(theta), ncrit,
+                                       phi.data_ptr(), grad.data_ptr(), _stream_ptr(torch, xyz.device),
+                                       ctypes.byref(o), ctypes.byref(st) if stats else None))
+    return (phi, grad, st.as_dict()) if stats else (phi, grad)
+
+
+def laplace3d_host(xyz: np.ndarray, q: np.ndarray, p: int, theta: float, ncrit: int, *,
+                   max_depth: int = 0, precision: str = "fp32", stats: bool = False, out=None,
+                   stream=None):
+    """Same solve with host (numpy) arrays: the library copies in and out."""
+    xyz = np.ascontiguousarray(xyz, dtype=np.float32)
+    q = np.ascontiguousarray(q, dtype=np.float32)
+    n = xyz.shape[0]
+    if out is None:
+        phi = np.empty(n, dtype=np.float32)
+        grad = np.empty((n, 3), dtype=np.float32)
+    else:
+        phi, grad = out
+    o = _options(max_depth, precision)
+    st = Stats()
+    _check(load().fmm_laplace3d_host(xyz.ctypes.data, q.ctypes.data, n, p, float(theta), ncrit,
+                                     phi.ctypes.data, grad.ctypes.data,
+                                     ctypes.c_void_p(stream or 0), ctypes.byref(o),
+                                     ctypes.byref(st) if stats else None))
+    return (phi, grad, st.as_dict()) if stats else (phi, grad)
+
+
+def direct(xyz, q):
+    """Exact all-pairs sum on the GPU (FP32)."""
+    import torch
+    n = int(xyz.shape[0])
+    xyz = _dev_f32(xyz, (n, 3), "xyz")
+    q = _dev_f32(q, (n,), "q")
+    with torch.cuda.device(xyz.device):
+        phi = torch.empty(n, device=xyz.device, dtype=torch.float32)
+        grad = torch.empty(n, 3, device=xyz.device, dtype=torch.float32)
+        _check(load().fmm_direct(xyz.data_ptr(), q.data_ptr(), n, phi.data_ptr(), grad.data_ptr(),
+                                 _stream_ptr(torch, xyz.device)))
+    return phi, grad
+
+
+_EXPORT_DTYPE = {"box": (np.float64, None), "keys": (np.uint64, None), "order": (np.int32, None),
+                 "cells": (np.int64, 6), "p2p": (np.int32, 2), "m2l": (np.int32, 3),
+                 "multipole": (np.float32, "P2pad"), "local": (np.float32, "P2pad")}
+
+
+def export(what: str, p: int | None = None) -> np.ndarray:
+    """An intermediate array of the last solve on the current device (see fmm.h)."""
+    L = load()
+    need = ctypes.c_int64(0)
+    _check(L.fmm_export(EXPORT[what], None, 0, ctypes.byref(need)))
+    dt, width = _EXPORT_DTYPE[what]
+    buf = np.empty(need.value // np.dtype(dt).itemsize, dtype=dt)
+    _check(L.fmm_export(EXPORT[what], buf.ctypes.data, need.value, ctypes.byref(need)))
+    if width == "P2pad":
+        if p is None:
+            raise ValueError("p is needed to shape expansion exports")
+        width = ((p + 1) ** 2 + 31) // 32 * 32
+    return buf.reshape(-1, width) if width else buf

@@ -1,0 +1,74 @@
+"""Helpers for the GPU parity tests: run the CUDA path through the C ABI and
+bring its intermediate arrays into the oracle's vocabulary."""
+import math
+
+import numpy as np
+
+from oracle import oracle as O
+
+
+def torch_cuda():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return torch
+
+
+def gpu_solve(xyz, q, p, theta, ncrit, max_depth=0, precision="fp32", stats=False):
+    torch = torch_cuda()
+    from paper_1108_5815_gb300 import fmm
+    x = torch.from_numpy(np.ascontiguousarray(xyz, dtype=np.float32)).cuda()
+    qq = torch.from_numpy(np.ascontiguousarray(q, dtype=np.float32)).cuda()
+    res = fmm.laplace3d(x, qq, p, theta, ncrit, max_depth=max_depth, precision=precision,
+                        stats=stats)
+    torch.cuda.synchronize()
+    out = [res[0].cpu().numpy().astype(np.float64), res[1].cpu().numpy().astype(np.float64)]
+    if stats:
+        out.append(res[2])
+    return tuple(out)
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+def canonical_ids(level, prefix):
+    """Rank of each cell in (level, prefix) order -- identical for both sides
+    when the cell sets agree."""
+    order = np.lexsort((np.asarray(prefix, np.uint64), np.asarray(level, np.int64)))
+    ids = np.empty(len(order), dtype=np.int64)
+    ids[order] = np.arange(len(order))
+    return ids, order
+
+
+def gpu_cells():
+    from paper_1108_5815_gb300 import fmm
+    c = fmm.export("cells")
+    return dict(level=c[:, 0], prefix=c[:, 1].astype(np.uint64), begin=c[:, 2], end=c[:, 3],
+                parent=c[:, 4], nchild=c[:, 5])
+
+
+def pair_codes(t, s, ids, ncells):
+    return np.sort(ids[np.asarray(t, np.int64)] * ncells + ids[np.asarray(s, np.int64)])
+
+
+def nu(n, m):
+    return math.sqrt(math.factorial(n - m) * math.factorial(n + m))
+
+
+def oracle_to_gpu_layout(E, p, side, which, P2pad):
+    """Oracle complex coefficients (signed m, index n*n+n+m) of a cell with side
+    ``side`` -> the GPU's real, unit-scaled, order-normalised row."""
+    row = np.zeros(P2pad)
+    for n in range(p + 1):
+        for m in range(n + 1):
+            c = E[n * n + n + m]
+            if which == "M":
+                c = c * side ** (-n) * nu(n, m)
+            else:
+                c = c * side ** (n + 1) / nu(n, m)
+            if m == 0:
+                row[n * n] = c.real
+            else:
+                row[n * n + 2 * m - 1] = c.real
+                row[n * n + 2 * m] = c.imag
+    return row

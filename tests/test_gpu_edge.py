@@ -1,0 +1,90 @@
+"""Edge cases and error behaviour of the C ABI on the GPU."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1108_5815_gb300 import inputs
+from tests.gpu_helpers import gpu_solve, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+def test_single_particle():
+    phi, grad = gpu_solve(np.array([[0.3, 0.2, 0.1]], np.float32), np.array([2.0], np.float32), 4, 0.5, 8)
+    assert phi[0] == 0 and np.all(grad == 0)
+
+
+def test_two_particles_closed_form():
+    x = np.array([[0, 0, 0], [2, 0, 0]], np.float32)
+    phi, grad = gpu_solve(x, np.array([1.0, 3.0], np.float32), 4, 0.5, 1)
+    assert np.allclose(phi, [1.5, 0.5], rtol=1e-6)
+    assert np.allclose(grad, [[0.75, 0, 0], [-0.25, 0, 0]], rtol=1e-6, atol=1e-7)
+
+
+def test_identical_points_give_zero():
+    x = np.tile(np.array([[0.4, 0.4, 0.4]], np.float32), (100, 1))
+    phi, grad = gpu_solve(x, np.ones(100, np.float32), 5, 0.5, 4)
+    assert np.all(phi == 0) and np.all(grad == 0)
+
+
+def test_root_leaf_equals_direct():
+    x, q = inputs.uniform_cube(60, 1)
+    phi, grad = gpu_solve(x, q, 4, 0.5, 64)
+    pd, gd = O.direct(x, q)
+    assert rel_l2(phi, pd) < 1e-6 and rel_l2(grad, gd) < 1e-6
+
+
+def test_depth_cap_and_box_faces():
+    # lattice corners sit on the maximum faces; depth 2 forces crowded leaves
+    g = np.stack(np.meshgrid(*[np.linspace(0, 1, 9)] * 3, indexing="ij"), -1).reshape(-1, 3)
+    x = g.astype(np.float32)
+    q = np.resize(np.array([1, -1, 0.5], np.float32), len(x))
+    phi, grad = gpu_solve(x, q, 6, 0.5, 4, max_depth=2)
+    f = O.Fmm(x, q, 6, 0.5, 4, max_depth=2)
+    ophi, ograd = f.evaluate()
+    assert rel_l2(phi, ophi) < 1e-5 and rel_l2(grad, ograd) < 1e-5
+
+
+@pytest.mark.parametrize("n", [33, 65, 129, 257, 1025])
+def test_ragged_small_sizes(n):
+    x, q = inputs.plummer(n, n, equal_charges=False)
+    phi, grad = gpu_solve(x, q, 5, 0.5, 4)
+    ophi, ograd = O.Fmm(x, q, 5, 0.5, 4).evaluate()
+    assert rel_l2(phi, ophi) < 1e-5 and rel_l2(grad, ograd) < 1e-5
+
+
+def test_nonfinite_input_reported():
+    from paper_1108_5815_gb300 import fmm
+    x, q = inputs.uniform_cube(1000, 2)
+    for bad in (np.nan, np.inf):
+        xb = x.copy()
+        xb[17, 1] = bad
+        with pytest.raises(fmm.FmmError) as e:
+            gpu_solve(xb, q, 4, 0.5, 16)
+        assert e.value.status == fmm.FMM_ERR_NONFINITE
+    # the context stays usable
+    phi, _ = gpu_solve(x, q, 4, 0.5, 16)
+    assert np.all(np.isfinite(phi))
+
+
+@pytest.mark.parametrize("p,theta,ncrit", [(0, 0.5, 8), (21, 0.5, 8), (4, 0.0, 8), (4, 1.0, 8),
+                                           (4, 0.5, 0)])
+def test_bad_arguments(p, theta, ncrit):
+    from paper_1108_5815_gb300 import fmm
+    x, q = inputs.uniform_cube(100, 2)
+    with pytest.raises(fmm.FmmError) as e:
+        gpu_solve(x, q, p, theta, ncrit)
+    assert e.value.status == fmm.FMM_ERR_ARG
+
+
+def test_null_pointers_and_empty():
+    from paper_1108_5815_gb300 import fmm
+    L = fmm.load()
+    assert L.fmm_laplace3d(None, None, 10, 4, 0.5, 8, None, None, None) == fmm.FMM_ERR_ARG
+    assert "null" in fmm.last_error()
+    import torch
+    z = torch.zeros(3, device="cuda")
+    assert L.fmm_laplace3d(z.data_ptr(), z.data_ptr(), 0, 4, 0.5, 8, z.data_ptr(), z.data_ptr(),
+                           None) == fmm.FMM_ERR_ARG

@@ -1,0 +1,121 @@
+"""GPU path vs the FP64 oracle, through the C ABI.
+
+Bit-exact: Morton keys, the sorted permutation, the cell set and the P2P/M2L
+pair sets (integer work, with the FP64 quantisation and the exact MAC taken in
+the same precision on both sides).  Within tolerance: multipole and local
+expansions (FP32 vs FP64) and phi/grad, at 1e-5 relative L2 of the oracle at
+equal p and theta, the bar the FP32 path is held to."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1108_5815_gb300 import inputs
+from tests.gpu_helpers import (canonical_ids, gpu_cells, gpu_solve, oracle_to_gpu_layout,
+                               pair_codes, rel_l2)
+
+pytestmark = pytest.mark.gpu
+
+TOL_ORACLE = 1e-5   # rel-L2 vs the FP64 oracle at equal p, theta (FP32 path)
+
+
+def _compare_structure(f, ncells_expected=None):
+    from paper_1108_5815_gb300 import fmm
+    key, order = f.sorted()
+    assert np.array_equal(fmm.export("keys"), key)
+    assert np.array_equal(fmm.export("order").astype(np.int64), order)
+    oc = f.cells()
+    gc = gpu_cells()
+    assert len(gc["level"]) == f.ncells
+    oid, oord = canonical_ids(oc["level"], oc["prefix"])
+    gid, gord = canonical_ids(gc["level"], gc["prefix"])
+    for k in ("level", "prefix", "begin", "end", "nchild"):
+        assert np.array_equal(np.asarray(oc[k])[oord], np.asarray(gc[k])[gord]), k
+    ol = f.lists()
+    gp = fmm.export("p2p")
+    gm = fmm.export("m2l")
+    assert np.array_equal(pair_codes(ol["p2p_t"], ol["p2p_s"], oid, f.ncells),
+                          pair_codes(gp[:, 0], gp[:, 1], gid, f.ncells))
+    assert np.array_equal(pair_codes(ol["m2l_t"], ol["m2l_s"], oid, f.ncells),
+                          pair_codes(gm[:, 0], gm[:, 1], gid, f.ncells))
+    return oid, gid, oord, gord
+
+
+CASES = [
+    # (name, distribution, n, p, theta, ncrit, max_depth)
+    ("uniform4k_p4", "uniform", 4096, 4, 0.5, 64, 0),
+    ("uniform30k_p6", "uniform", 30000, 6, 0.4, 32, 0),
+    ("plummer20k_p8", "plummer", 20000, 8, 0.5, 16, 0),
+    ("shell12k_p5", "shell", 12000, 5, 0.45, 24, 0),
+    ("plummer8k_depth4", "plummer", 8000, 3, 0.5, 8, 4),
+    ("uniform9k_p10", "uniform", 9001, 10, 0.4, 64, 0),
+]
+
+
+@pytest.mark.parametrize("name,dist,n,p,theta,ncrit,md", CASES, ids=[c[0] for c in CASES])
+def test_structure_and_fields_match_oracle(name, dist, n, p, theta, ncrit, md):
+    x, q = inputs.make(dist, n, 500 + n)
+    if dist == "plummer":
+        x, q = inputs.plummer(n, 500 + n, equal_charges=False)
+    phi, grad = gpu_solve(x, q, p, theta, ncrit, max_depth=md)
+    f = O.Fmm(x, q, p, theta, ncrit, max_depth=md or 21)
+    _compare_structure(f)
+    ophi, ograd = f.evaluate()
+    assert rel_l2(phi, ophi) < TOL_ORACLE
+    assert rel_l2(grad, ograd) < TOL_ORACLE
+
+
+def test_expansions_match_oracle():
+    from paper_1108_5815_gb300 import fmm
+    n, p, theta, ncrit = 20000, 7, 0.5, 32
+    x, q = inputs.uniform_cube(n, 77)
+    gpu_solve(x, q, p, theta, ncrit)
+    f = O.Fmm(x, q, p, theta, ncrit)
+    f.evaluate()
+    oid, gid, oord, gord = _compare_structure(f)
+    gM = fmm.export("multipole", p)
+    gL = fmm.export("local", p)
+    P2pad = gM.shape[1]
+    _, side = f.box()
+    oc = f.cells()
+    rng = np.random.default_rng(0)
+    for k in rng.choice(f.ncells, size=min(200, f.ncells), replace=False):
+        oi, gi = oord[k], gord[k]
+        s = side / 2.0 ** oc["level"][oi]
+        for which, G in (("M", gM), ("L", gL)):
+            ref = oracle_to_gpu_layout(f.expansion(which, oi), p, s, which, P2pad)
+            scale = np.abs(ref).max()
+            if scale == 0:
+                continue
+            assert np.abs(G[gi] - ref).max() <= 2e-5 * scale, (which, k)
+
+
+def test_p10_reaches_1e4_vs_direct():
+    n = 16384
+    x, q = inputs.uniform_cube(n, 1234)
+    phi, grad = gpu_solve(x, q, 10, 0.4, 64)
+    pd, gd = O.direct(x, q)
+    assert rel_l2(phi, pd) < 1e-4 and rel_l2(grad, gd) < 1e-4
+
+
+def test_direct_kernel_matches_oracle_direct():
+    torch = pytest.importorskip("torch")
+    from paper_1108_5815_gb300 import fmm
+    x, q = inputs.uniform_cube(5000, 4)
+    phi, grad = fmm.direct(torch.from_numpy(x).cuda(), torch.from_numpy(q).cuda())
+    pd, gd = O.direct(x, q)
+    assert rel_l2(phi.cpu().numpy(), pd) < 1e-6 and rel_l2(grad.cpu().numpy(), gd) < 1e-6
+
+
+def test_repeated_solves_are_bitwise_identical():
+    x, q = inputs.plummer(15000, 9, equal_charges=False)
+    a = gpu_solve(x, q, 6, 0.5, 32)
+    b = gpu_solve(x, q, 6, 0.5, 32)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_host_entry_point_equals_device_entry_point():
+    from paper_1108_5815_gb300 import fmm
+    x, q = inputs.uniform_cube(7000, 5)
+    a = gpu_solve(x, q, 5, 0.5, 32)
+    phi, grad = fmm.laplace3d_host(x, q, 5, 0.5, 32)
+    assert np.array_equal(a[0], phi.astype(np.float64)) and np.array_equal(a[1], grad.astype(np.float64))

@@ -103,7 +103,8 @@ def test_direct_kernel_matches_oracle_direct():
     x, q = inputs.uniform_cube(5000, 4)
     phi, grad = fmm.direct(torch.from_numpy(x).cuda(), torch.from_numpy(q).cuda())
     pd, gd = O.direct(x, q)
-    assert rel_l2(phi.cpu().numpy(), pd) < 1e-6 and rel_l2(grad.cpu().numpy(), gd) < 1e-6
+    # FP32 accumulation over 5000 sources: ~sqrt(N) * 2^-24 relative
+    assert rel_l2(phi.cpu().numpy(), pd) < 1e-5 and rel_l2(grad.cpu().numpy(), gd) < 1e-5
 
 
 def test_repeated_solves_are_bitwise_identical():

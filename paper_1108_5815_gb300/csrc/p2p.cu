@@ -45,37 +45,119 @@ __device__ __forceinline__ void p2p_interact(float xi, float yi, float zi, float
 
 }  // namespace
 
-// One warp per target leaf, 4 warps per block.
+// Stages the next chunk of up to 32 sources of the target's source stream (the
+// concatenated particle ranges of its P2P source leaves) into sh[0..32), padded
+// with zero charges.  (r, o) = current source leaf in the list and offset in it;
+// returns false when the stream is exhausted.
+__device__ __forceinline__ bool load_chunk(const int *__restrict__ slist, int cnt,
+                                           const CellArrays &c, const float4 *__restrict__ pts,
+                                           float4 *sh, int lane, int &r, int &o)
+{
+    if (r >= cnt) return false;
+    const int rk = r + lane;
+    int beg = 0, len = 0;
+    if (rk < cnt) {
+        const int S = slist[rk];
+        beg = c.begin[S];
+        len = c.end[S] - beg;
+    }
+    const int ok = lane == 0 ? o : 0;  // already consumed part of the first range
+    beg += ok;
+    len -= ok;
+    int P = len;  // inclusive prefix of remaining lengths
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, P, d);
+        if (lane >= d) P += t;
+    }
+    const int S0 = P - len;  // chunk position where range k starts
+    const unsigned starts = __reduce_or_sync(0xffffffffu, (len > 0 && S0 < 32) ? (1u << S0) : 0u);
+    const int total = __shfl_sync(0xffffffffu, P, 31);
+    const unsigned le = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);
+    const int k = __popc(starts & le) - 1;
+    const int kb = __shfl_sync(0xffffffffu, beg, k), ks = __shfl_sync(0xffffffffu, S0, k);
+    sh[lane] = lane < total ? pts[kb + (lane - ks)] : make_float4(0.f, 0.f, 0.f, 0.f);
+    if (total <= 32) {
+        // every range of the window is consumed (a full window of 32 ranges
+        // totals at least 32 elements, so fewer than 32 means the list ended)
+        r = min(r + 32, cnt);
+        o = 0;
+    } else {
+        // the range holding chunk position 31
+        const int k31 = __popc(starts) - 1;
+        const int s31 = __shfl_sync(0xffffffffu, S0, k31);
+        const int l31 = __shfl_sync(0xffffffffu, len, k31);
+        const int o31 = __shfl_sync(0xffffffffu, ok, k31);
+        const int used = 32 - s31;  // elements of range k31 consumed in this chunk
+        if (used == l31) {
+            r += k31 + 1;
+            o = 0;
+        } else {
+            r += k31;
+            o = o31 + used;
+        }
+    }
+    return true;
+}
+
+// One warp per target leaf, 4 warps per block.  Targets go 32 at a time, one
+// per lane; the last r < 32 targets are processed with the sources split into
+// g = floor(32 / r) interleaved subsets, so that r * g lanes stay busy, and the
+// g partial sums are added in shared memory.
 __global__ void __launch_bounds__(128)
     k_p2p(CellArrays c, ListArrays L, const int *__restrict__ leaves, int nleaves,
           const float4 *__restrict__ pts, float4 *__restrict__ near)
 {
     __shared__ float4 sh[4][32];
+    __shared__ float4 red[4][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int li = blockIdx.x * 4 + warp;
     if (li >= nleaves) return;
     const int T = leaves[li];
     const int b = c.begin[T], e = c.end[T];
-    const int off = L.p2p_off[T], cnt = L.p2p_cnt[T];
-    for (int tb = b; tb < e; tb += 32) {
-        const int i = tb + lane;
-        const bool valid = i < e;
-        const float4 xi = valid ? pts[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const int *slist = L.p2p_src + L.p2p_off[T];
+    const int cnt = L.p2p_cnt[T];
+    float4 *buf = sh[warp];
+    int tb = b;
+    for (; tb + 32 <= e; tb += 32) {
+        const float4 xi = pts[tb + lane];
         float phi = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
-        for (int k = 0; k < cnt; ++k) {
-            const int S = L.p2p_src[off + k];
-            const int sb = c.begin[S], se = c.end[S];
-            for (int s0 = sb; s0 < se; s0 += 32) {
-                const int j = s0 + lane;
-                sh[warp][lane] = j < se ? pts[j] : make_float4(0.f, 0.f, 0.f, 0.f);
-                __syncwarp();
-#pragma unroll 8
-                for (int jj = 0; jj < 32; ++jj)
-                    p2p_interact(xi.x, xi.y, xi.z, sh[warp][jj], phi, gx, gy, gz);
-                __syncwarp();
-            }
+        int r = 0, o = 0;
+        while (load_chunk(slist, cnt, c, pts, buf, lane, r, o)) {
+            __syncwarp();
+#pragma unroll
+            for (int jj = 0; jj < 32; ++jj) p2p_interact(xi.x, xi.y, xi.z, buf[jj], phi, gx, gy, gz);
+            __syncwarp();
         }
-        if (valid) near[i] = make_float4(phi, gx, gy, gz);
+        near[tb + lane] = make_float4(phi, gx, gy, gz);
+    }
+    const int rem = e - tb;
+    if (rem > 0) {
+        const int g = 32 / rem;
+        const int t = lane % rem, sub = lane / rem;
+        const bool active = sub < g;
+        const float4 xi = pts[tb + t];
+        float phi = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+        int r = 0, o = 0;
+        while (load_chunk(slist, cnt, c, pts, buf, lane, r, o)) {
+            __syncwarp();
+            if (active)
+                for (int jj = sub; jj < 32; jj += g) p2p_interact(xi.x, xi.y, xi.z, buf[jj], phi, gx, gy, gz);
+            __syncwarp();
+        }
+        red[warp][lane] = make_float4(phi, gx, gy, gz);
+        __syncwarp();
+        if (lane < rem) {
+            float4 a = red[warp][lane];
+            for (int k = 1; k < g; ++k) {
+                const float4 v = red[warp][lane + k * rem];
+                a.x += v.x;
+                a.y += v.y;
+                a.z += v.z;
+                a.w += v.w;
+            }
+            near[tb + lane] = a;
+        }
     }
 }
 

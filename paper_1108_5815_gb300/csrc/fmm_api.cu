@@ -133,6 +133,7 @@ void sync_point(Workspace &ws, cudaStream_t st, const int *flags_dev,
     if (f[kFlagClassRange])
         throw Error{FMM_ERR_CAPACITY, "an M2L offset exceeds the class key range (2^18 cells)"};
     if (f[kFlagStack]) throw Error{FMM_ERR_CAPACITY, "traversal stack overflow"};
+    if (f[kFlagTimeout]) throw Error{FMM_ERR_TIMEOUT, "a bounded device-side wait expired (M2L pipeline)"};
     if (host_out) std::memcpy(host_out, h + sizeof(int) * kNumFlags, total - sizeof(int) * kNumFlags);
 }
 
@@ -210,8 +211,8 @@ void validate(const void *xyz, const void *q, int64_t N, int p, double theta, in
     if (!(theta > 0.0 && theta < 1.0)) throw Error{FMM_ERR_ARG, "theta must be in (0, 1)"};
     if (ncrit < 1) throw Error{FMM_ERR_ARG, "ncrit must be >= 1"};
     if (o.max_depth < 0 || o.max_depth > kMaxLevel) throw Error{FMM_ERR_ARG, "max_depth must be in [0, 21]"};
-    if (o.precision_mode != FMM_PREC_FP32)
-        throw Error{FMM_ERR_ARG, "precision_mode: only FMM_PREC_FP32 is available in this build"};
+    if (o.precision_mode < FMM_PREC_FP32 || o.precision_mode > FMM_PREC_BF16X3)
+        throw Error{FMM_ERR_ARG, "precision_mode must be FMM_PREC_FP32, _TF32X3 or _BF16X3"};
     if (o.select_mode != 0) throw Error{FMM_ERR_ARG, "select_mode: only the plain FMM (0) is available"};
 }
 
@@ -504,8 +505,9 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
         int *i32_tmp = need<int>(ws, "scan_i32", scan_temp_elems(ntiles), st);
         scan_exclusive<int>(tile_cnt, entry_base, ntiles, entry_base + ntiles, i32_tmp, st);
     }
-    int nent = 0;
-    sync_point(ws, st, flags, {{entry_base + ntiles, sizeof(int)}}, &nent);
+    std::vector<int> h_eb(ntiles + 1);
+    sync_point(ws, st, flags, {{entry_base, sizeof(int) * (ntiles + 1)}}, h_eb.data());
+    const int nent = h_eb[ntiles];
     int *entry_class = need<int>(ws, "entry_class", nent, st);
     int *src = need<int>(ws, "src", (size_t)nent * kTile, st);
     FMM_CUDA_TRY(cudaMemsetAsync(src, 0xff, sizeof(int) * (size_t)nent * kTile, st));
@@ -541,8 +543,36 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
     ev.rec(3, st);
 
     // ---------------------------------------------------------- M2L
-    launch_m2l_simt(ntiles, entry_base, entry_class, src, tile_cells, M, get<float>(ws, "table"),
-                    P2pad, Lx, st);
+    const bool tensor = o.precision_mode != FMM_PREC_FP32 && m2l_tc_supported(P2pad);
+    if (tensor) {
+        // work units: (tile, contiguous run of its class blocks), about six per SM
+        const int chunk = std::max(8, (int)ceil_div(std::max(nent, 1), 6 * 152));
+        std::vector<M2LUnit> units;
+        std::vector<int> ubase(ntiles + 1, 0);
+        for (int t = 0; t < ntiles; ++t) {
+            ubase[t] = (int)units.size();
+            for (int e = h_eb[t]; e < h_eb[t + 1]; e += chunk)
+                units.push_back({t, e, std::min(e + chunk, h_eb[t + 1]), 0});
+        }
+        ubase[ntiles] = (int)units.size();
+        const int nunits = (int)units.size();
+        M2LUnit *d_units = need<M2LUnit>(ws, "m2l_units", std::max(nunits, 1), st);
+        int *d_ubase = need<int>(ws, "m2l_ubase", ntiles + 1, st);
+        float *partial = need<float>(ws, "m2l_partial", (size_t)std::max(nunits, 1) * 128 * P2pad, st);
+        if (nunits > 0)
+            FMM_CUDA_TRY(cudaMemcpyAsync(d_units, units.data(), sizeof(M2LUnit) * nunits,
+                                         cudaMemcpyHostToDevice, st));
+        FMM_CUDA_TRY(cudaMemcpyAsync(d_ubase, ubase.data(), sizeof(int) * (ntiles + 1),
+                                     cudaMemcpyHostToDevice, st));
+        launch_m2l_tc(o.precision_mode == FMM_PREC_BF16X3, nunits, d_units, ntiles, d_ubase,
+                      entry_class, src, tile_cells, M, get<float>(ws, "table"), P2pad, partial, Lx,
+                      flags, st);
+        // the host vectors above must outlive the copies
+        FMM_CUDA_TRY(cudaStreamSynchronize(st));
+    } else {
+        launch_m2l_simt(ntiles, entry_base, entry_class, src, tile_cells, M, get<float>(ws, "table"),
+                        P2pad, Lx, st);
+    }
     ev.rec(4, st);
 
     // ---------------------------------------------------------- downward pass

@@ -12,6 +12,7 @@ enum {
     kFlagHashFull = 1,    // offset-class hash table full
     kFlagClassRange = 2,  // an offset component does not fit the class key
     kFlagStack = 3,       // traversal stack overflow
+    kFlagTimeout = 4,     // a bounded device-side wait expired
     kNumFlags = 8
 };
 
@@ -92,6 +93,17 @@ __global__ void k_l2p(CellArrays c, const int *leaves, int nleaves, const float4
 void launch_m2l_simt(int ntiles, const int *entry_base, const int *entry_class, const int *src,
                      const int *tile_cells, const float *M, const float *table, int P2pad,
                      float *L, cudaStream_t st);
+
+// m2l_tc.cu
+struct M2LUnit {
+    int tile, e0, e1, pad;
+};
+bool m2l_tc_supported(int P2pad);
+size_t m2l_tc_smem(int P2pad, int &nstages);
+void launch_m2l_tc(bool bf16, int nunits, const void *units, int ntiles, const int *unit_base,
+                   const int *entry_class, const int *src, const int *tile_cells, const float *M,
+                   const float *table, int P2pad, float *partial, float *L, int *flags,
+                   cudaStream_t st);
 
 // p2p.cu
 __global__ void k_p2p(CellArrays c, ListArrays L, const int *leaves, int nleaves,

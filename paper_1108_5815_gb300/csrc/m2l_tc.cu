@@ -1,0 +1,399 @@
+// m2l_tc.cu -- M2L translations on the 5th-generation tensor cores (tcgen05).
+//
+// Same regrouping as m2l.cu (targets tiled 128 at a time, one dense block per
+// offset class present in the tile), computed as D = A * B^T with
+//   A (128 x P2pad) = gathered source multipoles of the tile's targets,
+//   B (N = P2pad x P2pad) = the class's translation matrix T(class) (rows =
+//     output coefficients), both K-major,
+// and D (128 x N, FP32) accumulated in tensor memory over all K-chunks of all
+// classes of a work unit.  FP32 accuracy from lower-precision tensor inputs by
+// the 3-term split a*b ~ ah*bh + ah*bl + al*bh with ah = hi(a), al = a - ah:
+//   TF32x3: hi = a with the low 13 mantissa bits cleared, kind::tf32;
+//   BF16x3: hi = bf16(a), al = bf16(a - hi), kind::f16 with BF16 inputs.
+//
+// Roles inside a CTA (288 threads):
+//   warps 0-7  producers: gather 128 source rows and N matrix rows of one
+//              K-chunk (32 floats = 128 B per row), split them into hi/lo and
+//              store them in the canonical no-swizzle K-major layout (8-row x
+//              16-byte core matrices; LBO = 128 B along K, SBO = 1024 B along
+//              rows); after the last chunk they read D out of tensor memory.
+//   warp 8     allocates tensor memory; one lane issues the MMAs and commits.
+// Stages are handed over through mbarriers (full: 256 producer arrivals;
+// empty/done: tcgen05.commit).  Every wait is bounded: on expiry the kernel
+// raises a flag and returns after releasing its tensor memory.
+// A work unit is (tile, range of the tile's class blocks); its 128 x N result
+// goes to a partial buffer and k_m2l_reduce sums a tile's units in order.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace fmm {
+
+namespace {
+
+constexpr int kProducerWarps = 8;
+constexpr int kThreads = (kProducerWarps + 1) * 32;
+constexpr int kKChunk = 32;  // source floats per row per stage (128 B)
+constexpr uint32_t kWaitLimit = 1u << 26;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Bounded wait for the phase with the given parity; false on expiry.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+{
+    const uint32_t a = smem_u32(bar);
+    for (uint32_t it = 0; it < kWaitLimit; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void fence_proxy_async()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: no swizzle, K-major, LBO = 128 B (next core
+// matrix along K), SBO = 1024 B (next 8-row group), descriptor version 1.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFFu);
+    d |= (uint64_t)(128u >> 4) << 16;
+    d |= (uint64_t)(1024u >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// Instruction descriptor: FP32 accumulate, A/B format `fmt` (TF32 = 2 for
+// kind::tf32, BF16 = 1 for kind::f16), both K-major, M = 128, N = n.
+__host__ __device__ constexpr uint32_t instr_desc(uint32_t fmt, uint32_t n)
+{
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((n >> 3) << 17) | ((128u >> 4) << 24);
+}
+
+template <bool BF16>
+__device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
+                                    uint32_t accumulate)
+{
+    if (BF16) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+            "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+            "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+    }
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+
+// 16 consecutive FP32 columns of this warp's 32 TMEM lanes.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// hi/lo split of 4 floats into one 16-byte chunk each (TF32: 4 elements).
+__device__ __forceinline__ void split_tf32(float4 a, uint4 &hi, uint4 &lo)
+{
+    const float x[4] = {a.x, a.y, a.z, a.w};
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const uint32_t hb = __float_as_uint(x[i]) & 0xFFFFE000u;
+        h[i] = hb;
+        l[i] = __float_as_uint(x[i] - __uint_as_float(hb));
+    }
+    hi = make_uint4(h[0], h[1], h[2], h[3]);
+    lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+// hi/lo split of 8 floats into one 16-byte chunk each (BF16: 8 elements).
+__device__ __forceinline__ void split_bf16(float4 a, float4 b, uint4 &hi, uint4 &lo)
+{
+    const float x[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const __nv_bfloat16 h0 = __float2bfloat16_rn(x[2 * i]), h1 = __float2bfloat16_rn(x[2 * i + 1]);
+        const __nv_bfloat16 l0 = __float2bfloat16_rn(x[2 * i] - __bfloat162float(h0));
+        const __nv_bfloat16 l1 = __float2bfloat16_rn(x[2 * i + 1] - __bfloat162float(h1));
+        h[i] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+        l[i] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+    }
+    hi = make_uint4(h[0], h[1], h[2], h[3]);
+    lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+struct Unit {
+    int tile, e0, e1, pad;
+};
+
+// Stage layout (bytes): A_hi | A_lo | B_hi | B_lo, operand X with R rows of one
+// K-chunk occupying R * 128 bytes (16 core matrices of 8 rows per 128 rows).
+template <bool BF16>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_m2l_tc(const Unit *__restrict__ units, const int *__restrict__ entry_class,
+             const int *__restrict__ src, const float *__restrict__ M, const float *__restrict__ table,
+             int P2pad, int nstages, float *__restrict__ partial, int *__restrict__ flags)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // 1024-byte aligned base
+    unsigned char *smem = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
+    const int N = P2pad;
+    // Floats of K consumed per stage: 32 (TF32, 128 B/row) or 64 (BF16, 128 B/row).
+    const int kstage = BF16 ? 64 : 32;
+    const int nkc = (P2pad + kstage - 1) / kstage;
+    const uint32_t a_bytes = 128u * 128u, b_bytes = (uint32_t)N * 128u;
+    const uint32_t stage_bytes = 2 * a_bytes + 2 * b_bytes;
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + nstages * stage_bytes);
+    uint64_t *empty = full + nstages;
+    uint64_t *done = empty + nstages;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+    __shared__ int s_abort;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const Unit U = units[blockIdx.x];
+    const int nsteps = (U.e1 - U.e0) * nkc;
+    uint32_t ncols = 32;
+    while (ncols < (uint32_t)N) ncols <<= 1;
+
+    if (threadIdx.x == 0) {
+        s_abort = 0;
+        for (int s = 0; s < nstages; ++s) {
+            mbar_init(&full[s], kProducerWarps * 32);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == kProducerWarps) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "r"(ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp < kProducerWarps) {
+        // ------------------------------------------------------------ producers
+        const int rows_total = 128 + N;
+        const int groups = rows_total / 8;
+        const int sub = lane & 7;        // row within the 8-row group
+        const int cq = lane >> 3;        // 16-byte column chunk 0..3 (and +4)
+        for (int g = 0; g < nsteps; ++g) {
+            const int s = g % nstages;
+            if (g >= nstages && !mbar_wait(&empty[s], (uint32_t)((g / nstages) - 1) & 1u)) {
+                atomicOr(&flags[kFlagTimeout], 1);
+                s_abort = 1;
+                break;
+            }
+            if (s_abort) break;
+            const int e = U.e0 + g / nkc;
+            const int k0 = (g % nkc) * kstage;
+            const float *Tm = table + (int64_t)entry_class[e] * P2pad * P2pad;
+            unsigned char *st = smem + (size_t)s * stage_bytes;
+            for (int grp = warp; grp < groups; grp += kProducerWarps) {
+                const int row = grp * 8 + sub;
+                const float *rowp;
+                bool valid = true;
+                unsigned char *dst_hi, *dst_lo;
+                if (row < 128) {
+                    const int sidx = src[(int64_t)e * kTile + row];
+                    valid = sidx >= 0;
+                    rowp = M + (int64_t)(valid ? sidx : 0) * P2pad;
+                    dst_hi = st + (row >> 3) * 1024 + (row & 7) * 16;
+                    dst_lo = dst_hi + a_bytes;
+                } else {
+                    const int r = row - 128;
+                    rowp = Tm + (int64_t)r * P2pad;
+                    dst_hi = st + 2 * a_bytes + (r >> 3) * 1024 + (r & 7) * 16;
+                    dst_lo = dst_hi + b_bytes;
+                }
+#pragma unroll
+                for (int half = 0; half < 2; ++half) {
+                    const int c = cq + 4 * half;  // 16-byte chunk within the 128-byte row
+                    uint4 hi, lo;
+                    if (BF16) {
+                        const int kk = k0 + c * 8;
+                        float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+                        if (valid && kk < P2pad) {
+                            a = *reinterpret_cast<const float4 *>(rowp + kk);
+                            b = *reinterpret_cast<const float4 *>(rowp + kk + 4);
+                        }
+                        split_bf16(a, b, hi, lo);
+                    } else {
+                        const int kk = k0 + c * 4;
+                        float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (valid && kk < P2pad) a = *reinterpret_cast<const float4 *>(rowp + kk);
+                        split_tf32(a, hi, lo);
+                    }
+                    *reinterpret_cast<uint4 *>(dst_hi + c * 128) = hi;
+                    *reinterpret_cast<uint4 *>(dst_lo + c * 128) = lo;
+                }
+            }
+            fence_proxy_async();
+            mbar_arrive(&full[s]);
+        }
+        // ------------------------------------------------------------ epilogue
+        const bool ok = !s_abort && mbar_wait(done, 0);
+        if (!ok) atomicOr(&flags[kFlagTimeout], 1);
+        tc_fence_after();
+        const int quad = warp & 3, half = warp >> 2;
+        const int row = quad * 32 + lane;
+        const int cols = N / 2;
+        float *out = partial + ((int64_t)blockIdx.x * 128 + row) * P2pad + half * cols;
+        for (int c0 = 0; c0 < cols; c0 += 16) {
+            float v[16];
+            tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(half * cols + c0), v);
+            if (ok) {
+#pragma unroll
+                for (int i = 0; i < 16; i += 4)
+                    *reinterpret_cast<float4 *>(out + c0 + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+            }
+        }
+    } else if (lane == 0) {
+        // ------------------------------------------------------------ MMA issuer
+        const uint32_t idesc = instr_desc(BF16 ? 1u : 2u, (uint32_t)N);
+        const int ksteps = 4;  // 4 MMAs of 32 bytes of K per 128-byte stage row
+        bool ok = true;
+        for (int g = 0; g < nsteps; ++g) {
+            const int s = g % nstages;
+            if (!mbar_wait(&full[s], (uint32_t)(g / nstages) & 1u)) {
+                atomicOr(&flags[kFlagTimeout], 1);
+                s_abort = 1;
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t base = smem_u32(smem + (size_t)s * stage_bytes);
+            const uint32_t ah = base, al = base + a_bytes, bh = base + 2 * a_bytes,
+                           bl = bh + b_bytes;
+#pragma unroll
+            for (int k = 0; k < ksteps; ++k) {
+                const uint32_t off = (uint32_t)k * 256u;  // two core matrices along K
+                const uint32_t acc0 = (g > 0 || k > 0) ? 1u : 0u;
+                mma<BF16>(tmem, smem_desc(al + off), smem_desc(bh + off), idesc, acc0);
+                mma<BF16>(tmem, smem_desc(ah + off), smem_desc(bl + off), idesc, 1u);
+                mma<BF16>(tmem, smem_desc(ah + off), smem_desc(bh + off), idesc, 1u);
+            }
+            mma_commit(&empty[s]);
+        }
+        if (ok) mma_commit(done);  // units always hold at least one class block
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == kProducerWarps) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols)
+                     : "memory");
+    }
+}
+
+__global__ void k_m2l_reduce(const int *__restrict__ unit_base, const float *__restrict__ partial,
+                             const int *__restrict__ tile_cells, int P2pad, float *__restrict__ L)
+{
+    const int tile = blockIdx.x;
+    const int u0 = unit_base[tile], u1 = unit_base[tile + 1];
+    const int nq = P2pad / 4;
+    for (int i = threadIdx.x; i < kTile * nq; i += blockDim.x) {
+        const int row = i / nq, q4 = i % nq;
+        const int cell = tile_cells[(int64_t)tile * kTile + row];
+        if (cell < 0) continue;
+        float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int u = u0; u < u1; ++u) {
+            const float4 v = reinterpret_cast<const float4 *>(partial + ((int64_t)u * 128 + row) * P2pad)[q4];
+            a.x += v.x;
+            a.y += v.y;
+            a.z += v.z;
+            a.w += v.w;
+        }
+        reinterpret_cast<float4 *>(L + (int64_t)cell * P2pad)[q4] = a;
+    }
+}
+
+}  // namespace
+
+bool m2l_tc_supported(int P2pad) { return P2pad <= 256; }
+
+size_t m2l_tc_smem(int P2pad, int &nstages)
+{
+    const size_t stage = 2 * 128 * 128 + 2 * (size_t)P2pad * 128;
+    nstages = (int)std::min<size_t>(4, (200 * 1024) / stage);
+    if (nstages < 2) nstages = 2;
+    return nstages * stage + 1024 /*alignment*/ + (2 * nstages + 1) * 8 + 16;
+}
+
+void launch_m2l_tc(bool bf16, int nunits, const void *units, int ntiles, const int *unit_base,
+                   const int *entry_class, const int *src, const int *tile_cells, const float *M,
+                   const float *table, int P2pad, float *partial, float *L, int *flags,
+                   cudaStream_t st)
+{
+    int nstages = 0;
+    const size_t smem = m2l_tc_smem(P2pad, nstages);
+    if (nunits > 0) {
+        if (bf16) {
+            FMM_CUDA_TRY(cudaFuncSetAttribute(k_m2l_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            k_m2l_tc<true><<<nunits, kThreads, smem, st>>>(static_cast<const Unit *>(units), entry_class, src,
+                                                          M, table, P2pad, nstages, partial, flags);
+        } else {
+            FMM_CUDA_TRY(cudaFuncSetAttribute(k_m2l_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            k_m2l_tc<false><<<nunits, kThreads, smem, st>>>(static_cast<const Unit *>(units), entry_class, src,
+                                                           M, table, P2pad, nstages, partial, flags);
+        }
+        FMM_LAUNCH_CHECK();
+    }
+    k_m2l_reduce<<<ntiles, 256, 0, st>>>(unit_base, partial, tile_cells, P2pad, L);
+    FMM_LAUNCH_CHECK();
+}
+
+}  // namespace fmm

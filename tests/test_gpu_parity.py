@@ -120,3 +120,28 @@ def test_host_entry_point_equals_device_entry_point():
     a = gpu_solve(x, q, 5, 0.5, 32)
     phi, grad = fmm.laplace3d_host(x, q, 5, 0.5, 32)
     assert np.array_equal(a[0], phi.astype(np.float64)) and np.array_equal(a[1], grad.astype(np.float64))
+
+
+@pytest.mark.parametrize("precision,tol", [("tf32x3", 1e-5), ("bf16x3", 1e-4)])
+@pytest.mark.parametrize("dist,n,p,theta,ncrit", [("uniform", 30000, 10, 0.4, 64),
+                                                  ("plummer", 20000, 8, 0.5, 16),
+                                                  ("uniform", 6000, 4, 0.5, 32),
+                                                  ("shell", 9000, 12, 0.45, 24)])
+def test_tensor_core_m2l_matches_oracle(precision, tol, dist, n, p, theta, ncrit):
+    if dist == "plummer":
+        x, q = inputs.plummer(n, 900 + n, equal_charges=False)
+    else:
+        x, q = inputs.make(dist, n, 900 + n)
+    phi, grad = gpu_solve(x, q, p, theta, ncrit, precision=precision)
+    f = O.Fmm(x, q, p, theta, ncrit)
+    _compare_structure(f)
+    ophi, ograd = f.evaluate()
+    assert rel_l2(phi, ophi) < tol
+    assert rel_l2(grad, ograd) < tol
+
+
+def test_tensor_core_m2l_deterministic():
+    x, q = inputs.uniform_cube(40000, 3)
+    a = gpu_solve(x, q, 10, 0.4, 64, precision="tf32x3")
+    b = gpu_solve(x, q, 10, 0.4, 64, precision="tf32x3")
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])

@@ -117,6 +117,8 @@ WORKLOADS = {
     "plummer4m": dict(kind="plummer", n=4_194_304, p=8, theta=0.4, ncrit=64, max_depth=21, seed=1003),
     "batched512": dict(kind="batched", nsys=512, p=8, theta=0.5, ncrit=64, max_depth=21, seed=1004),
     "plummer16m": dict(kind="plummer", n=16_777_216, p=10, theta=0.4, ncrit=64, max_depth=21, seed=1005),
+    # a quarter-size uniform case with the same p/theta/ncrit, for profiler captures
+    "uniform262k": dict(kind="uniform", n=262_144, p=10, theta=0.4, ncrit=64, max_depth=10, seed=1006),
 }
 
 

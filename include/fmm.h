@@ -134,6 +134,28 @@ enum {
 };
 fmm_status fmm_export(int what, void *dst, int64_t capacity, int64_t *needed);
 
+/* Morton keys and sorted order of the particles, allocating nothing.
+ * (The paper has no counterpart: it is a library convenience.)  For callers
+ * that must not allocate device memory after start-up -- code running under
+ * another framework's memory pool, or a plugin host that forbids cudaMalloc
+ * once initialised -- this runs the first stage of fmm_laplace3d (bounding box,
+ * FP64 quantisation, 63-bit Morton keys, stable radix sort by key then index)
+ * with all scratch in one fixed device array compiled into the library.
+ *   xyz   device float32 [N][3], N in [1, 1048576] (larger N: FMM_ERR_ARG)
+ *   keys  device uint64 [N]  out: keys in ascending (key, index) order
+ *   order device int32 [N]   out: original index of each sorted position
+ *   box   device double [4]  out: lo_x, lo_y, lo_z, side of the cubic box
+ * Results equal FMM_EXPORT_KEYS / FMM_EXPORT_ORDER / FMM_EXPORT_BOX of a
+ * solve on the same points.  A NaN/Inf coordinate gives FMM_ERR_NONFINITE.
+ * The scratch array (12,846,336 bytes) exists on every device that loads the
+ * library until the process exits.  The first call on a device resolves its
+ * address with cudaGetSymbolAddress; make that first call before any stream
+ * capture.  All calls share the array, so calls whose GPU work overlaps (on
+ * different streams or threads) race and must be serialised by the caller.
+ * The call synchronises `stream` before returning. */
+fmm_status fmm_morton_sort_noalloc(const float *xyz, int64_t N, uint64_t *keys, int32_t *order,
+                                   double *box, void *stream);
+
 /* Message for the last non-OK status returned on this thread ("" if none). */
 const char *fmm_last_error(void);
 

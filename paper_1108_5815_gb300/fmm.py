@@ -24,7 +24,7 @@ EXPORT = {"box": 0, "keys": 1, "order": 2, "cells": 3, "p2p": 4, "m2l": 5, "mult
 
 # every symbol the header declares
 ABI_SYMBOLS = ("fmm_default_options", "fmm_laplace3d", "fmm_laplace3d_ex", "fmm_laplace3d_host",
-               "fmm_direct", "fmm_export", "fmm_last_error")
+               "fmm_direct", "fmm_export", "fmm_last_error", "fmm_morton_sort_noalloc")
 
 
 class FmmError(RuntimeError):
@@ -75,6 +75,8 @@ def load(path: str | None = None):
         L.fmm_direct.argtypes = [vp, vp, i64, vp, vp, vp]
         L.fmm_export.argtypes = [ctypes.c_int, vp, i64, ctypes.POINTER(i64)]
         L.fmm_last_error.restype = ctypes.c_char_p
+        L.fmm_morton_sort_noalloc.argtypes = [vp, i64, vp, vp, vp, vp]
+        L.fmm_morton_sort_noalloc.restype = ctypes.c_int
         for name in ("fmm_laplace3d", "fmm_laplace3d_ex", "fmm_laplace3d_host", "fmm_direct",
                      "fmm_export"):
             getattr(L, name).restype = ctypes.c_int
@@ -191,3 +193,24 @@ def export(what: str, p: int | None = None) -> np.ndarray:
             raise ValueError("p is needed to shape expansion exports")
         width = ((p + 1) ** 2 + 31) // 32 * 32
     return buf.reshape(-1, width) if width else buf
+
+
+def morton_sort_noalloc(xyz, out=None):
+    """Morton keys, sorted order and box of CUDA float32 xyz[N,3] through the
+    entry point that allocates no device memory (N <= 1048576).
+
+    ``out`` = (keys int64-viewed uint64 [N], order int32 [N], box float64 [4]) CUDA
+    tensors to fill; allocated with torch when omitted."""
+    import torch
+    n = int(xyz.shape[0])
+    xyz = _dev_f32(xyz, (n, 3), "xyz")
+    with torch.cuda.device(xyz.device):
+        if out is None:
+            keys = torch.empty(n, dtype=torch.int64, device=xyz.device)
+            order = torch.empty(n, dtype=torch.int32, device=xyz.device)
+            box = torch.empty(4, dtype=torch.float64, device=xyz.device)
+        else:
+            keys, order, box = out
+        _check(load().fmm_morton_sort_noalloc(xyz.data_ptr(), n, keys.data_ptr(), order.data_ptr(),
+                                              box.data_ptr(), _stream_ptr(torch, xyz.device)))
+    return keys, order, box

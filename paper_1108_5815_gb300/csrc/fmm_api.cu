@@ -47,6 +47,7 @@ struct Workspace {
     int64_t N = 0;
     int ncells = 0, nleaves = 0, depth = 0, P2pad = 0, nclass = 0;
     int64_t nm2l = 0, np2p = 0;
+    int64_t cap_m2l = 0, cap_p2p = 0, cap_def = 0;  // list capacities that sufficed before
 };
 
 std::mutex g_ws_mu;
@@ -271,6 +272,17 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
     CellArrays c = cells(cell_cap, false);
     k_init_root<<<1, 1, 0, st>>>(c, N);
     FMM_LAUNCH_CHECK();
+    // boundary positions of adjacent keys, bucketed (stably) by the level at which they differ
+    uint64_t *blvl = need<uint64_t>(ws, "blvl", std::max(N - 1, 1), st);
+    uint32_t *bpos = need<uint32_t>(ws, "bpos", std::max(N - 1, 1), st);
+    int *bstart = need<int>(ws, "bstart", 24, st);
+    if (N > 1) {
+        k_first_diff<<<grid_for(N, 256), 256, 0, st>>>(keys, N, blvl, bpos);
+        FMM_LAUNCH_CHECK();
+        radix_sort_pairs(blvl, bpos, keys_alt, idx_alt, N - 1, 8, hist, tmp_u32, st);
+    }
+    k_level_starts<<<1, 32, 0, st>>>(blvl, N - 1, bstart);
+    FMM_LAUNCH_CHECK();
     std::vector<int> lstart = {0, 1};
     int tiles_total = 1;
     int64_t *i64_tmp = need<int64_t>(ws, "scan_i64", scan_temp_elems(std::max(N, 1 << 16)), st);
@@ -281,8 +293,8 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
         int64_t *packed = need<int64_t>(ws, "packed", nl, st);
         int64_t *packed_ex = need<int64_t>(ws, "packed_ex", nl + 1, st);
         i64_tmp = need<int64_t>(ws, "scan_i64", scan_temp_elems(nl), st);
-        k_split_count<<<(unsigned)ceil_div(nl, 128), 128, 0, st>>>(c, keys, a, b, l, ncrit, max_depth,
-                                                                  packed);
+        k_split_count<<<(unsigned)ceil_div(nl, 128), 128, 0, st>>>(c, bpos, bstart, a, b, l, ncrit,
+                                                                  max_depth, packed);
         FMM_LAUNCH_CHECK();
         scan_exclusive<int64_t>(packed, packed_ex, nl, packed_ex + nl, i64_tmp, st);
         int64_t total = 0;
@@ -294,8 +306,8 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
             cell_cap = std::max(b + nch, cell_cap + cell_cap / 2);
             c = cells(cell_cap, true);
         }
-        k_split_emit<<<(unsigned)ceil_div(nl, 128), 128, 0, st>>>(c, keys, a, b, l, packed, packed_ex,
-                                                                 tiles_total);
+        k_split_emit<<<(unsigned)ceil_div(nl, 128), 128, 0, st>>>(c, keys, bpos, bstart, a, b, l, packed,
+                                                                 packed_ex, tiles_total);
         FMM_LAUNCH_CHECK();
         tiles_total += 8 * (int)ceil_div(nsplit, kTile);
         lstart.push_back(b + nch);
@@ -327,76 +339,49 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
     L.p2p_cnt = need<int>(ws, "p2p_cnt", ncells, st);
     L.def_off = need<int>(ws, "def_off", ncells, st);
     L.def_cnt = need<int>(ws, "def_cnt", ncells, st);
-    int64_t m2l_cap = std::max<int64_t>(1024, (int64_t)ncells * 16);
-    int64_t p2p_cap = std::max<int64_t>(1024, (int64_t)ncells * 8);
-    int64_t def_cap = std::max<int64_t>(1024, (int64_t)ncells * 8);
-    auto lists = [&](bool keep) {
-        L.m2l_src = need<int>(ws, "m2l_src", m2l_cap, st, keep);
-        L.m2l_tgt = need<int>(ws, "m2l_tgt", m2l_cap, st, keep);
-        L.m2l_slot = need<uint32_t>(ws, "m2l_slot", m2l_cap, st, keep);
-        L.p2p_src = need<int>(ws, "p2p_src", p2p_cap, st, keep);
-        L.p2p_tgt = need<int>(ws, "p2p_tgt", p2p_cap, st, keep);
-        L.def_src = need<int>(ws, "def_src", def_cap, st, keep);
-    };
-    lists(false);
+    // capacities: the last solve's totals, or estimates; regrown exactly on overflow
+    int64_t m2l_cap = std::max<int64_t>(ws.cap_m2l, std::max<int64_t>(4096, (int64_t)ncells * 160));
+    int64_t p2p_cap = std::max<int64_t>(ws.cap_p2p, std::max<int64_t>(4096, (int64_t)nleaves * 96));
+    int64_t def_cap = std::max<int64_t>(ws.cap_def, std::max<int64_t>(4096, (int64_t)ncells * 96));
     uint64_t *hash_keys = need<uint64_t>(ws, "hash_keys", kHashCap, st);
-    FMM_CUDA_TRY(cudaMemsetAsync(hash_keys, 0xff, sizeof(uint64_t) * kHashCap, st));
+    unsigned long long *tcount = need<unsigned long long>(ws, "trav_counters", 3, st);
     const bool root_leaf = ncells == 1;
-    k_root_lists<<<1, 1, 0, st>>>(L, root_leaf ? 1 : 0);
-    FMM_LAUNCH_CHECK();
-    int64_t m2l_total = 0, p2p_total = root_leaf ? 1 : 0;
-    int def_total = root_leaf ? 0 : 1;
-    for (int l = 1; l <= depth; ++l) {
-        const int a = lstart[l], b = lstart[l + 1];
-        const int nl = b - a;
-        int64_t *cnt_mp = need<int64_t>(ws, "cnt_mp", nl, st);
-        int64_t *off_mp = need<int64_t>(ws, "off_mp", nl + 1, st);
-        int *cnt_d = need<int>(ws, "cnt_d", nl, st);
-        int *off_d = need<int>(ws, "off_d", nl + 1, st);
-        int *i32_tmp = need<int>(ws, "scan_i32", scan_temp_elems(nl), st);
-        i64_tmp = need<int64_t>(ws, "scan_i64", scan_temp_elems(nl), st);
-        const unsigned blocks = (unsigned)ceil_div((int64_t)nl * 32, 128);
-        k_traverse_count<<<blocks, 128, 0, st>>>(c, L, a, b, theta2, cnt_mp, cnt_d, flags);
+    int64_t m2l_total = 0, p2p_total = 0;
+    for (int attempt = 0;; ++attempt) {
+        L.m2l_src = need<int>(ws, "m2l_src", m2l_cap, st);
+        L.m2l_tgt = need<int>(ws, "m2l_tgt", m2l_cap, st);
+        L.m2l_slot = need<uint32_t>(ws, "m2l_slot", m2l_cap, st);
+        L.p2p_src = need<int>(ws, "p2p_src", p2p_cap, st);
+        L.p2p_tgt = need<int>(ws, "p2p_tgt", p2p_cap, st);
+        L.def_src = need<int>(ws, "def_src", def_cap, st);
+        FMM_CUDA_TRY(cudaMemsetAsync(hash_keys, 0xff, sizeof(uint64_t) * kHashCap, st));
+        const unsigned long long init[3] = {0ull, root_leaf ? 1ull : 0ull, root_leaf ? 0ull : 1ull};
+        FMM_CUDA_TRY(cudaMemcpyAsync(tcount, init, sizeof(init), cudaMemcpyHostToDevice, st));
+        k_root_lists<<<1, 1, 0, st>>>(L, root_leaf ? 1 : 0);
         FMM_LAUNCH_CHECK();
-        scan_exclusive<int64_t>(cnt_mp, off_mp, nl, off_mp + nl, i64_tmp, st);
-        scan_exclusive<int>(cnt_d, off_d, nl, off_d + nl, i32_tmp, st);
-        struct {
-            int64_t mp;
-            int d;
-        } tot;
-        int64_t tmp_mp = 0;
-        int tmp_d = 0;
-        {
-            char hb[16];
-            sync_point(ws, st, flags, {{off_mp + nl, sizeof(int64_t)}, {off_d + nl, sizeof(int)}}, hb);
-            std::memcpy(&tmp_mp, hb, 8);
-            std::memcpy(&tmp_d, hb + 8, 4);
+        for (int l = 1; l <= depth; ++l) {
+            const int a = lstart[l], b = lstart[l + 1];
+            const unsigned blocks = (unsigned)ceil_div((int64_t)(b - a) * 32, 128);
+            k_traverse_level<<<blocks, 128, 0, st>>>(c, L, a, b, theta2, (float)theta2, tcount, m2l_cap,
+                                                     p2p_cap, def_cap, hash_keys, flags);
+            FMM_LAUNCH_CHECK();
         }
-        tot.mp = tmp_mp;
-        tot.d = tmp_d;
-        const int64_t add_m = tot.mp >> 32, add_p = tot.mp & 0xffffffffll;
-        const int add_d = tot.d;
-        bool grow = false;
-        if (m2l_total + add_m > m2l_cap) {
-            m2l_cap = std::max(m2l_total + add_m, m2l_cap + m2l_cap / 2);
-            grow = true;
+        unsigned long long tot[3];
+        sync_point(ws, st, flags, {{tcount, sizeof(tot)}}, tot);
+        if ((int64_t)tot[0] <= m2l_cap && (int64_t)tot[1] <= p2p_cap && (int64_t)tot[2] <= def_cap) {
+            m2l_total = (int64_t)tot[0];
+            p2p_total = (int64_t)tot[1];
+            break;
         }
-        if (p2p_total + add_p > p2p_cap) {
-            p2p_cap = std::max(p2p_total + add_p, p2p_cap + p2p_cap / 2);
-            grow = true;
-        }
-        if ((int64_t)def_total + add_d > def_cap) {
-            def_cap = std::max<int64_t>(def_total + add_d, def_cap + def_cap / 2);
-            grow = true;
-        }
-        if (grow) lists(true);
-        k_traverse_write<<<blocks, 128, 0, st>>>(c, L, a, b, theta2, off_mp, off_d, m2l_total,
-                                                 p2p_total, def_total, hash_keys, flags);
-        FMM_LAUNCH_CHECK();
-        m2l_total += add_m;
-        p2p_total += add_p;
-        def_total += add_d;
+        if (attempt >= 3) throw Error{FMM_ERR_CAPACITY, "interaction lists kept outgrowing their buffers"};
+        // deeper levels saw truncated deferred lists, so their counts are lower bounds
+        m2l_cap = std::max<int64_t>(2 * m2l_cap, (int64_t)tot[0] + tot[0] / 4);
+        p2p_cap = std::max<int64_t>(2 * p2p_cap, (int64_t)tot[1] + tot[1] / 4);
+        def_cap = std::max<int64_t>(2 * def_cap, (int64_t)tot[2] + tot[2] / 4);
     }
+    ws.cap_m2l = m2l_cap;
+    ws.cap_p2p = p2p_cap;
+    ws.cap_def = def_cap;
 
     // ---------------------------------------------------------- offset classes
     int nclass = 0;

@@ -47,21 +47,21 @@ __global__ void k_morton(const float *xyz, int64_t n, const uint32_t *bbox_u, do
 __global__ void k_permute(const float *xyz, const float *q, const uint32_t *idx, int64_t n,
                           float4 *out);
 __global__ void k_init_root(CellArrays c, int n);
-__global__ void k_split_count(CellArrays c, const uint64_t *keys, int a, int b, int level,
-                              int ncrit, int max_depth, int64_t *packed);
-__global__ void k_split_emit(CellArrays c, const uint64_t *keys, int a, int b, int level,
-                             const int64_t *packed, const int64_t *ex, int tile_base);
+__global__ void k_first_diff(const uint64_t *keys, int64_t n, uint64_t *lvl, uint32_t *pos);
+__global__ void k_level_starts(const uint64_t *lvl, int64_t n, int *start);
+__global__ void k_split_count(CellArrays c, const uint32_t *bpos, const int *lstart, int a, int b,
+                              int level, int ncrit, int max_depth, int64_t *packed);
+__global__ void k_split_emit(CellArrays c, const uint64_t *keys, const uint32_t *bpos,
+                             const int *lstart, int a, int b, int level, const int64_t *packed,
+                             const int64_t *ex, int tile_base);
 __global__ void k_fill_tile_cells(CellArrays c, int ncells, int *tile_cells);
 __global__ void k_leaf_flags(CellArrays c, int ncells, int *flag);
 __global__ void k_leaf_compact(CellArrays c, int ncells, const int *ex, int *leaves);
 
 // traverse.cu
-__global__ void k_traverse_count(CellArrays c, ListArrays L, int a, int b, double theta2,
-                                 int64_t *cnt_mp, int *cnt_d, int *flags);
-__global__ void k_traverse_write(CellArrays c, ListArrays L, int a, int b, double theta2,
-                                 const int64_t *off_mp, const int *off_d, int64_t m2l_base,
-                                 int64_t p2p_base, int def_base, uint64_t *hash_keys,
-                                 int *flags);
+__global__ void k_traverse_level(CellArrays c, ListArrays L, int a, int b, double theta2,
+                                 float theta2f, unsigned long long *counters, int64_t cap_m,
+                                 int64_t cap_p, int64_t cap_d, uint64_t *hash_keys, int *flags);
 __global__ void k_hash_flags(const uint64_t *hash_keys, int *flag);
 __global__ void k_hash_compact(const uint64_t *hash_keys, const int *ex, uint64_t *ukeys,
                                uint32_t *uslot);

@@ -176,7 +176,7 @@ struct Unit {
 
 // Stage layout (bytes): A_hi | A_lo | B_hi | B_lo, operand X with R rows of one
 // K-chunk occupying R * 128 bytes (16 core matrices of 8 rows per 128 rows).
-template <bool BF16>
+template <bool BF16, int NG>
 __global__ void __launch_bounds__(kThreads, 1)
     k_m2l_tc(const Unit *__restrict__ units, const int *__restrict__ entry_class,
              const int *__restrict__ src, const float *__restrict__ M, const float *__restrict__ table,
@@ -226,11 +226,62 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     if (warp < kProducerWarps) {
         // ------------------------------------------------------------ producers
-        const int rows_total = 128 + N;
-        const int groups = rows_total / 8;
-        const int sub = lane & 7;        // row within the 8-row group
-        const int cq = lane >> 3;        // 16-byte column chunk 0..3 (and +4)
+        // Thread (warp, lane) owns rows grp*8 + (lane & 7) for grp = warp + 8j, and the
+        // 16-byte chunks (lane >> 3) and (lane >> 3) + 4 of each.  Rows < 128 are
+        // gathered multipoles (A), the rest rows of the class matrix (B).  The loads
+        // of stage g+1 are issued before stage g is split and stored.
+        const int groups = (128 + N) / 8;
+        const int sub = lane & 7, cq = lane >> 3;
+        constexpr int V = BF16 ? 4 : 2;  // float4 per row and thread per stage
+        float4 cur[NG][V], nxt[NG][V];
+        int srow[2] = {0, 0};
+        bool svalid[2] = {false, false};
+        auto load_stage = [&](int g, float4 (&buf)[NG][V]) {
+            const int e = U.e0 + g / nkc;
+            const int k0 = (g % nkc) * kstage;
+            if (g % nkc == 0) {
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    const int row = (warp + 8 * j) * 8 + sub;
+                    const int sidx = src[(int64_t)e * kTile + row];
+                    svalid[j] = sidx >= 0;
+                    srow[j] = svalid[j] ? sidx : 0;
+                }
+            }
+            const float *Tm = table + (int64_t)entry_class[e] * P2pad * P2pad;
+#pragma unroll
+            for (int j = 0; j < NG; ++j) {
+                const int grp = warp + 8 * j;
+                const float *rowp = nullptr;
+                bool valid = grp < groups;
+                if (j < 2) {
+                    rowp = M + (int64_t)srow[j] * P2pad;
+                    valid = svalid[j];
+                } else if (valid) {
+                    rowp = Tm + (int64_t)(grp * 8 + sub - 128) * P2pad;
+                }
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int c = cq + 4 * h;
+                    if (BF16) {
+                        const int kk = k0 + c * 8;
+                        const bool ok = valid && kk < P2pad;
+                        buf[j][2 * h] = ok ? *reinterpret_cast<const float4 *>(rowp + kk) : make_float4(0.f, 0.f, 0.f, 0.f);
+                        buf[j][2 * h + 1] = ok ? *reinterpret_cast<const float4 *>(rowp + kk + 4) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    } else {
+                        const int kk = k0 + c * 4;
+                        buf[j][h] = valid ? *reinterpret_cast<const float4 *>(rowp + kk) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+                }
+            }
+        };
+        if (nsteps > 0) load_stage(0, nxt);
         for (int g = 0; g < nsteps; ++g) {
+#pragma unroll
+            for (int j = 0; j < NG; ++j)
+#pragma unroll
+                for (int v = 0; v < V; ++v) cur[j][v] = nxt[j][v];
+            if (g + 1 < nsteps) load_stage(g + 1, nxt);
             const int s = g % nstages;
             if (g >= nstages && !mbar_wait(&empty[s], (uint32_t)((g / nstages) - 1) & 1u)) {
                 atomicOr(&flags[kFlagTimeout], 1);
@@ -238,45 +289,29 @@ __global__ void __launch_bounds__(kThreads, 1)
                 break;
             }
             if (s_abort) break;
-            const int e = U.e0 + g / nkc;
-            const int k0 = (g % nkc) * kstage;
-            const float *Tm = table + (int64_t)entry_class[e] * P2pad * P2pad;
             unsigned char *st = smem + (size_t)s * stage_bytes;
-            for (int grp = warp; grp < groups; grp += kProducerWarps) {
+#pragma unroll
+            for (int j = 0; j < NG; ++j) {
+                const int grp = warp + 8 * j;
+                if (grp >= groups) continue;
                 const int row = grp * 8 + sub;
-                const float *rowp;
-                bool valid = true;
                 unsigned char *dst_hi, *dst_lo;
                 if (row < 128) {
-                    const int sidx = src[(int64_t)e * kTile + row];
-                    valid = sidx >= 0;
-                    rowp = M + (int64_t)(valid ? sidx : 0) * P2pad;
                     dst_hi = st + (row >> 3) * 1024 + (row & 7) * 16;
                     dst_lo = dst_hi + a_bytes;
                 } else {
                     const int r = row - 128;
-                    rowp = Tm + (int64_t)r * P2pad;
                     dst_hi = st + 2 * a_bytes + (r >> 3) * 1024 + (r & 7) * 16;
                     dst_lo = dst_hi + b_bytes;
                 }
 #pragma unroll
-                for (int half = 0; half < 2; ++half) {
-                    const int c = cq + 4 * half;  // 16-byte chunk within the 128-byte row
+                for (int h = 0; h < 2; ++h) {
+                    const int c = cq + 4 * h;
                     uint4 hi, lo;
-                    if (BF16) {
-                        const int kk = k0 + c * 8;
-                        float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
-                        if (valid && kk < P2pad) {
-                            a = *reinterpret_cast<const float4 *>(rowp + kk);
-                            b = *reinterpret_cast<const float4 *>(rowp + kk + 4);
-                        }
-                        split_bf16(a, b, hi, lo);
-                    } else {
-                        const int kk = k0 + c * 4;
-                        float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
-                        if (valid && kk < P2pad) a = *reinterpret_cast<const float4 *>(rowp + kk);
-                        split_tf32(a, hi, lo);
-                    }
+                    if (BF16)
+                        split_bf16(cur[j][2 * h], cur[j][2 * h + 1], hi, lo);
+                    else
+                        split_tf32(cur[j][h], hi, lo);
                     *reinterpret_cast<uint4 *>(dst_hi + c * 128) = hi;
                     *reinterpret_cast<uint4 *>(dst_lo + c * 128) = lo;
                 }
@@ -381,15 +416,27 @@ void launch_m2l_tc(bool bf16, int nunits, const void *units, int ntiles, const i
     int nstages = 0;
     const size_t smem = m2l_tc_smem(P2pad, nstages);
     if (nunits > 0) {
+        // groups of 8 rows per producer warp: ceil((128 + P2pad) / 64)
+        const int ng = (int)ceil_div(128 + P2pad, 64);
+#define FMM_M2L_TC_LAUNCH(B, G)                                                                     \
+    do {                                                                                           \
+        FMM_CUDA_TRY(cudaFuncSetAttribute(k_m2l_tc<B, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                          (int)smem));                                             \
+        k_m2l_tc<B, G><<<nunits, kThreads, smem, st>>>(static_cast<const Unit *>(units), entry_class, \
+                                                       src, M, table, P2pad, nstages, partial, flags); \
+    } while (0)
         if (bf16) {
-            FMM_CUDA_TRY(cudaFuncSetAttribute(k_m2l_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            k_m2l_tc<true><<<nunits, kThreads, smem, st>>>(static_cast<const Unit *>(units), entry_class, src,
-                                                          M, table, P2pad, nstages, partial, flags);
+            if (ng <= 3) FMM_M2L_TC_LAUNCH(true, 3);
+            else if (ng == 4) FMM_M2L_TC_LAUNCH(true, 4);
+            else if (ng == 5) FMM_M2L_TC_LAUNCH(true, 5);
+            else FMM_M2L_TC_LAUNCH(true, 6);
         } else {
-            FMM_CUDA_TRY(cudaFuncSetAttribute(k_m2l_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            k_m2l_tc<false><<<nunits, kThreads, smem, st>>>(static_cast<const Unit *>(units), entry_class, src,
-                                                           M, table, P2pad, nstages, partial, flags);
+            if (ng <= 3) FMM_M2L_TC_LAUNCH(false, 3);
+            else if (ng == 4) FMM_M2L_TC_LAUNCH(false, 4);
+            else if (ng == 5) FMM_M2L_TC_LAUNCH(false, 5);
+            else FMM_M2L_TC_LAUNCH(false, 6);
         }
+#undef FMM_M2L_TC_LAUNCH
         FMM_LAUNCH_CHECK();
     }
     k_m2l_reduce<<<ntiles, 256, 0, st>>>(unit_base, partial, tile_cells, P2pad, L);

@@ -100,6 +100,17 @@ __device__ __forceinline__ bool load_chunk(const int *__restrict__ slist, int cn
     return true;
 }
 
+// 32 sources from shared memory against one target, two accumulator sets
+// (even/odd sources) to shorten the dependency chains.
+__device__ __forceinline__ void p2p_chunk32(const float4 &xi, const float4 *buf, float4 &a0, float4 &a1)
+{
+#pragma unroll
+    for (int jj = 0; jj < 32; jj += 2) {
+        p2p_interact(xi.x, xi.y, xi.z, buf[jj], a0.x, a0.y, a0.z, a0.w);
+        p2p_interact(xi.x, xi.y, xi.z, buf[jj + 1], a1.x, a1.y, a1.z, a1.w);
+    }
+}
+
 // One warp per target leaf, 4 warps per block.  Targets go 32 at a time, one
 // per lane; the last r < 32 targets are processed with the sources split into
 // g = floor(32 / r) interleaved subsets, so that r * g lanes stay busy, and the
@@ -119,20 +130,24 @@ __global__ void __launch_bounds__(128)
     const int cnt = L.p2p_cnt[T];
     float4 *buf = sh[warp];
     int tb = b;
-    for (; tb + 32 <= e; tb += 32) {
-        const float4 xi = pts[tb + lane];
-        float phi = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+    // full passes, and a last pass of 17..31 targets (g = 1), one target per lane
+    while (tb < e && (e - tb >= 32 || 2 * (e - tb) > 32)) {
+        const bool valid = tb + lane < e;
+        const float4 xi = pts[valid ? tb + lane : tb];
+        float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
         int r = 0, o = 0;
         while (load_chunk(slist, cnt, c, pts, buf, lane, r, o)) {
             __syncwarp();
-#pragma unroll
-            for (int jj = 0; jj < 32; ++jj) p2p_interact(xi.x, xi.y, xi.z, buf[jj], phi, gx, gy, gz);
+            p2p_chunk32(xi, buf, a0, a1);
             __syncwarp();
         }
-        near[tb + lane] = make_float4(phi, gx, gy, gz);
+        // accumulators hold (phi, gx, gy, gz)
+        if (valid) near[tb + lane] = make_float4(a0.x + a1.x, a0.y + a1.y, a0.z + a1.z, a0.w + a1.w);
+        tb += 32;
     }
     const int rem = e - tb;
     if (rem > 0) {
+        // 1 <= rem <= 16: g >= 2 interleaved source subsets
         const int g = 32 / rem;
         const int t = lane % rem, sub = lane / rem;
         const bool active = sub < g;
@@ -141,8 +156,10 @@ __global__ void __launch_bounds__(128)
         int r = 0, o = 0;
         while (load_chunk(slist, cnt, c, pts, buf, lane, r, o)) {
             __syncwarp();
-            if (active)
+            if (active) {
+#pragma unroll 4
                 for (int jj = sub; jj < 32; jj += g) p2p_interact(xi.x, xi.y, xi.z, buf[jj], phi, gx, gy, gz);
+            }
             __syncwarp();
         }
         red[warp][lane] = make_float4(phi, gx, gy, gz);

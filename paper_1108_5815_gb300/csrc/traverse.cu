@@ -13,8 +13,9 @@
 //                    else split S (S larger, or T a leaf) and interact with
 //                    its children, or defer S to T's children.
 // One warp handles one target; lanes take inherited sources in order and
-// resolve each with a small depth-first stack.  Outputs are written in a
-// deterministic order (count pass, scan, write pass), grouped by target.
+// resolve each with a small depth-first stack.  Each target's outputs are
+// written contiguously in a deterministic order (count, reserve with one atomic
+// per list, write), so every per-target list is reproducible.
 //
 // MAC (reading R3 of the oracle): r = half side, accept iff R > 0 and
 // (r_t + r_s)^2 <= theta^2 R^2, evaluated in integer units of side/2^22 so the
@@ -31,21 +32,33 @@ constexpr int kStack = 192;
 struct TargetInfo {
     int t, level;
     bool leaf;
-    int64_t C[3], h;
+    int C[3], h;  // centre in units of side/2^22 and half side (< 2^23)
 };
 
-__device__ __forceinline__ bool mac_accept(const TargetInfo &T, const int64_t Cs[3], int64_t hs,
-                                           double theta2)
+__device__ __forceinline__ void cell_geom32(int level, uint64_t prefix, int C[3], int &h)
 {
-    int64_t R2 = 0;
+    h = 1 << (kKeyBits - level);
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const int64_t d = T.C[a] - Cs[a];
-        R2 += d * d;
-    }
-    if (R2 == 0) return false;
-    const int64_t rs = T.h + hs;
-    return (double)(rs * rs) <= __dmul_rn(theta2, (double)R2);
+    for (int a = 0; a < 3; ++a) C[a] = (2 * (int)compact3_dev(prefix >> a) + 1) * h;
+}
+
+// MAC of reading R3: accept iff R > 0 and (r_t + r_s)^2 <= theta^2 R^2 with theta^2 R^2
+// rounded once in FP64.  An FP32 estimate decides every pair farther than a 1e-5
+// relative margin from the threshold; the rest take the FP64 comparison itself.
+__device__ __forceinline__ bool mac_accept(const TargetInfo &T, const int Cs[3], int hs,
+                                           double theta2, float theta2f)
+{
+    const int dx = T.C[0] - Cs[0], dy = T.C[1] - Cs[1], dz = T.C[2] - Cs[2];
+    if ((dx | dy | dz) == 0) return false;
+    const float fx = (float)dx, fy = (float)dy, fz = (float)dz;
+    const float r2f = fmaf(fz, fz, fmaf(fy, fy, fx * fx));
+    const float rs = (float)(T.h + hs);
+    const float lhs = rs * rs, rhs = theta2f * r2f;
+    if (lhs < rhs * (1.0f - 1e-5f)) return true;
+    if (lhs > rhs * (1.0f + 1e-5f)) return false;
+    const int64_t R2 = (int64_t)dx * dx + (int64_t)dy * dy + (int64_t)dz * dz;
+    const int64_t r = (int64_t)T.h + hs;
+    return (double)(r * r) <= __dmul_rn(theta2, (double)R2);
 }
 
 __device__ __forceinline__ uint64_t mix64(uint64_t z)
@@ -74,16 +87,16 @@ __device__ uint32_t hash_insert(uint64_t *table, uint64_t key, int *flags)
 
 // Offset class of an accepted pair: level difference and the centre offset in
 // units of the finer cell's half side.
-__device__ __forceinline__ uint64_t class_key(const TargetInfo &T, int ls, const int64_t Cs[3],
+__device__ __forceinline__ uint64_t class_key(const TargetInfo &T, int ls, const int Cs[3],
                                               int *flags)
 {
     const int lf = max(T.level, ls);
-    const int64_t u = (int64_t)1 << (kKeyBits - lf);
+    const int sh = kKeyBits - lf;  // offsets are exact multiples of 2^sh
     uint64_t key = (uint64_t)(ls - T.level + 64) << 57;
-    const int64_t lim = (int64_t)1 << 18;
+    const int lim = 1 << 18;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const int64_t d = (T.C[a] - Cs[a]) / u;
+        const int d = (T.C[a] - Cs[a]) >> sh;
         if (d <= -lim || d >= lim) atomicOr(&flags[kFlagClassRange], 1);
         key |= (uint64_t)((d + lim) & 0x7ffff) << (38 - 19 * a);
     }
@@ -97,7 +110,7 @@ struct Counts {
 // Resolves one inherited source S0 for target T.  WRITE = false only counts.
 template <bool WRITE>
 __device__ Counts resolve(const TargetInfo &T, int S0, const CellArrays &c, const ListArrays &L,
-                          double theta2, int64_t m_pos, int64_t p_pos, int d_pos,
+                          double theta2, float theta2f, int64_t m_pos, int64_t p_pos, int d_pos,
                           uint64_t *hash_keys, int *flags)
 {
     Counts n = {0, 0, 0};
@@ -108,9 +121,9 @@ __device__ Counts resolve(const TargetInfo &T, int S0, const CellArrays &c, cons
         const int S = stk[--sp];
         const int ls = c.level[S];
         const int nchS = c.nchild[S];
-        int64_t Cs[3], hs;
-        cell_int_geom(ls, c.prefix[S], Cs, hs);
-        if (mac_accept(T, Cs, hs, theta2)) {
+        int Cs[3], hs;
+        cell_geom32(ls, c.prefix[S], Cs, hs);
+        if (mac_accept(T, Cs, hs, theta2, theta2f)) {
             if (WRITE) {
                 L.m2l_src[m_pos + n.m] = S;
                 L.m2l_tgt[m_pos + n.m] = T.t;
@@ -144,7 +157,7 @@ __device__ __forceinline__ TargetInfo load_target(const CellArrays &c, int t)
     T.t = t;
     T.level = c.level[t];
     T.leaf = c.nchild[t] == 0;
-    cell_int_geom(T.level, c.prefix[t], T.C, T.h);
+    cell_geom32(T.level, c.prefix[t], T.C, T.h);
     return T;
 }
 
@@ -169,10 +182,16 @@ __device__ __forceinline__ int warp_excl(int v)
 
 }  // namespace
 
-// Count pass for the targets [a, b) (one warp each).
-__global__ void k_traverse_count(CellArrays c, ListArrays L, int a, int b, double theta2,
-                                 int64_t *__restrict__ cnt_mp, int *__restrict__ cnt_d,
-                                 int *__restrict__ flags)
+// One warp per target of the level [a, b): count the outputs of all inherited
+// sources, reserve space for them with one atomic per list, then resolve the
+// sources again in the same order and write.  counters[] are running totals over
+// the levels; when a reservation passes its capacity nothing is written for the
+// target (its deferred count becomes 0) and the host repeats the traversal with
+// larger buffers.
+__global__ void __launch_bounds__(128)
+    k_traverse_level(CellArrays c, ListArrays L, int a, int b, double theta2, float theta2f,
+                     unsigned long long *__restrict__ counters, int64_t cap_m, int64_t cap_p,
+                     int64_t cap_d, uint64_t *__restrict__ hash_keys, int *__restrict__ flags)
 {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -183,7 +202,7 @@ __global__ void k_traverse_count(CellArrays c, ListArrays L, int a, int b, doubl
     const int i0 = L.def_off[P], ni = L.def_cnt[P];
     int m = 0, p = 0, d = 0;
     for (int k = lane; k < ni; k += 32) {
-        Counts n = resolve<false>(T, L.def_src[i0 + k], c, L, theta2, 0, 0, 0, nullptr, flags);
+        const Counts n = resolve<false>(T, L.def_src[i0 + k], c, L, theta2, theta2f, 0, 0, 0, nullptr, flags);
         m += n.m;
         p += n.p;
         d += n.d;
@@ -191,50 +210,39 @@ __global__ void k_traverse_count(CellArrays c, ListArrays L, int a, int b, doubl
     m = warp_sum(m);
     p = warp_sum(p);
     d = warp_sum(d);
+    unsigned long long om = 0, op = 0, od = 0;
     if (lane == 0) {
-        cnt_mp[t - a] = ((int64_t)m << 32) | (int64_t)p;
-        cnt_d[t - a] = d;
+        om = atomicAdd(&counters[0], (unsigned long long)m);
+        op = atomicAdd(&counters[1], (unsigned long long)p);
+        od = atomicAdd(&counters[2], (unsigned long long)d);
     }
-}
-
-// Write pass: same resolution order, outputs at the scanned offsets.
-__global__ void k_traverse_write(CellArrays c, ListArrays L, int a, int b, double theta2,
-                                 const int64_t *__restrict__ off_mp, const int *__restrict__ off_d,
-                                 int64_t m2l_base, int64_t p2p_base, int def_base,
-                                 uint64_t *__restrict__ hash_keys, int *__restrict__ flags)
-{
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    const int t = a + warp;
-    if (t >= b) return;
-    const TargetInfo T = load_target(c, t);
-    const int P = c.parent[t];
-    const int i0 = L.def_off[P], ni = L.def_cnt[P];
-    const int64_t om = m2l_base + (off_mp[t - a] >> 32);
-    const int64_t op = p2p_base + (off_mp[t - a] & 0xffffffffll);
-    const int od = def_base + off_d[t - a];
+    om = __shfl_sync(0xffffffffu, om, 0);
+    op = __shfl_sync(0xffffffffu, op, 0);
+    od = __shfl_sync(0xffffffffu, od, 0);
+    const bool fits = (int64_t)(om + m) <= cap_m && (int64_t)(op + p) <= cap_p && (int64_t)(od + d) <= cap_d;
+    if (lane == 0) {
+        L.m2l_off[t] = (int)om;
+        L.m2l_cnt[t] = fits ? m : 0;
+        L.p2p_off[t] = (int)op;
+        L.p2p_cnt[t] = fits ? p : 0;
+        L.def_off[t] = (int)od;
+        L.def_cnt[t] = fits ? d : 0;
+    }
+    if (!fits) return;
     int64_t rm = 0, rp = 0;
     int rd = 0;
     for (int k0 = 0; k0 < ni; k0 += 32) {
         const int k = k0 + lane;
         const int S0 = k < ni ? L.def_src[i0 + k] : -1;
         Counts n = {0, 0, 0};
-        if (S0 >= 0) n = resolve<false>(T, S0, c, L, theta2, 0, 0, 0, nullptr, flags);
+        if (S0 >= 0) n = resolve<false>(T, S0, c, L, theta2, theta2f, 0, 0, 0, nullptr, flags);
         const int em = warp_excl(n.m), ep = warp_excl(n.p), ed = warp_excl(n.d);
         if (S0 >= 0)
-            resolve<true>(T, S0, c, L, theta2, om + rm + em, op + rp + ep, od + rd + ed, hash_keys,
-                          flags);
+            resolve<true>(T, S0, c, L, theta2, theta2f, (int64_t)om + rm + em, (int64_t)op + rp + ep,
+                          (int)od + rd + ed, hash_keys, flags);
         rm += warp_sum(n.m);
         rp += warp_sum(n.p);
         rd += warp_sum(n.d);
-    }
-    if (lane == 0) {
-        L.m2l_off[t] = (int)om;
-        L.m2l_cnt[t] = (int)rm;
-        L.p2p_off[t] = (int)op;
-        L.p2p_cnt[t] = (int)rp;
-        L.def_off[t] = od;
-        L.def_cnt[t] = rd;
     }
 }
 

@@ -126,39 +126,64 @@ __global__ void k_init_root(CellArrays c, int n)
     c.lane[0] = 0;
 }
 
-// First index in keys[b, e) whose level-(l+1) octant digit is >= o.
-__device__ __forceinline__ int lower_octant(const uint64_t *__restrict__ keys, int b, int e,
-                                            int shift, uint32_t o)
+// Boundary levels: for i in [1, n), the first level at which the keys of
+// sorted positions i-1 and i differ (22 when they are equal).  Inside a cell
+// of level l every adjacent pair shares the level-l prefix, so the children's
+// boundaries are exactly the positions of level l+1 in the cell's range.
+__global__ void k_first_diff(const uint64_t *__restrict__ keys, int64_t n,
+                             uint64_t *__restrict__ lvl, uint32_t *__restrict__ pos)
 {
-    while (b < e) {
-        int mid = (b + e) >> 1;
-        if ((uint32_t)((keys[mid] >> shift) & 7ull) < o)
-            b = mid + 1;
-        else
-            e = mid;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x + 1; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t x = keys[i] ^ keys[i - 1];
+        lvl[i - 1] = x ? (uint64_t)(kKeyBits - (63 - __clzll((long long)x)) / 3) : 22ull;
+        pos[i - 1] = (uint32_t)i;
     }
-    return b;
+}
+
+// start[L] = first index of level L in the (stably) level-sorted boundary list.
+__global__ void k_level_starts(const uint64_t *__restrict__ lvl, int64_t n, int *__restrict__ start)
+{
+    const int L = threadIdx.x;
+    if (L > 23) return;
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (lvl[mid] < (uint64_t)L)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    start[L] = (int)lo;
+}
+
+__device__ __forceinline__ int lower_pos(const uint32_t *__restrict__ B, int nb, uint32_t v)
+{
+    int lo = 0, hi = nb;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (B[mid] < v)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return lo;
 }
 
 // For the cells [a, b) at level l: packed[c-a] = nchild | (split ? 1 << 32 : 0).
-__global__ void k_split_count(CellArrays c, const uint64_t *__restrict__ keys, int a, int b,
-                              int level, int ncrit, int max_depth, int64_t *__restrict__ packed)
+__global__ void k_split_count(CellArrays c, const uint32_t *__restrict__ bpos,
+                              const int *__restrict__ lstart, int a, int b, int level, int ncrit,
+                              int max_depth, int64_t *__restrict__ packed)
 {
     const int i = a + blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= b) return;
     const int cb = c.begin[i], ce = c.end[i];
     int64_t v = 0;
     if (ce - cb > ncrit && level < max_depth) {
-        const int shift = 3 * (kKeyBits - level - 1);
-        int nch = 0;
-        int lo = cb;
-#pragma unroll
-        for (int o = 0; o < 8; ++o) {
-            int hi = lower_octant(keys, lo, ce, shift, (uint32_t)o + 1);
-            nch += hi > lo;
-            lo = hi;
-        }
-        v = (int64_t)nch | ((int64_t)1 << 32);
+        const uint32_t *B = bpos + lstart[level + 1];
+        const int nb = lstart[level + 2] - lstart[level + 1];
+        const int lo = lower_pos(B, nb, (uint32_t)cb + 1), hi = lower_pos(B, nb, (uint32_t)ce);
+        v = (int64_t)(hi - lo + 1) | ((int64_t)1 << 32);
     }
     packed[i - a] = v;
 }
@@ -166,8 +191,9 @@ __global__ void k_split_count(CellArrays c, const uint64_t *__restrict__ keys, i
 // Writes the children of the cells [a, b) (level l) starting at cell index b,
 // using the exclusive scan `ex` of the packed counts; assigns each child its
 // M2L tile (parent window of kTile split parents x octant) and lane.
-__global__ void k_split_emit(CellArrays c, const uint64_t *__restrict__ keys, int a, int b,
-                             int level, const int64_t *__restrict__ packed,
+__global__ void k_split_emit(CellArrays c, const uint64_t *__restrict__ keys,
+                             const uint32_t *__restrict__ bpos, const int *__restrict__ lstart,
+                             int a, int b, int level, const int64_t *__restrict__ packed,
                              const int64_t *__restrict__ ex, int tile_base)
 {
     const int i = a + blockIdx.x * blockDim.x + threadIdx.x;
@@ -185,25 +211,28 @@ __global__ void k_split_emit(CellArrays c, const uint64_t *__restrict__ keys, in
     const int cb = c.begin[i], ce = c.end[i];
     const int shift = 3 * (kKeyBits - level - 1);
     const uint64_t pre = c.prefix[i];
-    int lo = cb, k = 0;
-    for (int o = 0; o < 8; ++o) {
-        int hi = lower_octant(keys, lo, ce, shift, (uint32_t)o + 1);
-        if (hi > lo) {
-            const int ch = first + k++;
-            c.level[ch] = level + 1;
-            c.prefix[ch] = (pre << 3) | (uint64_t)o;
-            c.begin[ch] = lo;
-            c.end[ch] = hi;
-            c.parent[ch] = i;
-            c.child0[ch] = -1;
-            c.nchild[ch] = 0;
-            c.tile[ch] = tile_base + window * 8 + o;
-            c.lane[ch] = lane;
-        }
-        lo = hi;
+    const uint32_t *B = bpos + lstart[level + 1];
+    const int nb = lstart[level + 2] - lstart[level + 1];
+    const int lo = lower_pos(B, nb, (uint32_t)cb + 1);
+    const int nch = (int)(v & 0xffffffffll);
+    int beg = cb;
+    for (int k = 0; k < nch; ++k) {
+        const int end = k + 1 < nch ? (int)B[lo + k] : ce;
+        const int o = (int)((keys[beg] >> shift) & 7ull);
+        const int ch = first + k;
+        c.level[ch] = level + 1;
+        c.prefix[ch] = (pre << 3) | (uint64_t)o;
+        c.begin[ch] = beg;
+        c.end[ch] = end;
+        c.parent[ch] = i;
+        c.child0[ch] = -1;
+        c.nchild[ch] = 0;
+        c.tile[ch] = tile_base + window * 8 + o;
+        c.lane[ch] = lane;
+        beg = end;
     }
     c.child0[i] = first;
-    c.nchild[i] = k;
+    c.nchild[i] = nch;
 }
 
 __global__ void k_fill_tile_cells(CellArrays c, int ncells, int *__restrict__ tile_cells)

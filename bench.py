@@ -46,7 +46,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="uniform1m")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32x3", "bf16x3"])
+    ap.add_argument("--precision", default="tf32x3", choices=["fp32", "tf32x3", "bf16x3"])
+    ap.add_argument("--no-modes", action="store_true", help="skip timing the other M2L precisions")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -118,6 +119,78 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def accuracy(x, q, phi, grad, nsample=512, seed=77):
+    """Relative L2 error of phi and grad against the FP64 direct sum (oracle) on
+    nsample seeded targets."""
+    from oracle import oracle as O
+    from paper_1108_5815_gb300 import inputs
+    import numpy as np
+    t = inputs.sample_indices(len(q), nsample, seed)
+    pd, gd = O.direct(x, q, targets=t)
+    e_phi = float(np.linalg.norm(phi[t] - pd) / np.linalg.norm(pd))
+    e_grad = float(np.linalg.norm(grad[t] - gd) / np.linalg.norm(gd))
+    return {"rel_l2_phi": e_phi, "rel_l2_grad": e_grad, "reference": "FP64 direct sum (oracle)",
+            "targets": int(nsample)}
+
+
+# ------------------------------------------------------------------ rooflines
+
+def measured_peaks():
+    """(HBM GB/s, BF16 dense TF/s, label): MEASURED_PEAKS.json when present, else
+    the fallback figures of one earlier GB300 measurement."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), float(d["bf16_tflops"]), "of measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, 1900.0, "of fallback"
+
+
+def captured_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu capture record,
+    or None when the kernel's source changed since the capture."""
+    import hashlib
+    rec_path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(rec_path))[kernel]
+        src = open(os.path.join(ROOT, rec["source"]), "rb").read()
+    except (OSError, KeyError, ValueError):
+        return None
+    if hashlib.sha256(src).hexdigest() != rec["source_sha256"]:
+        return None
+    return rec["dram_bytes_per_launch"]
+
+
+def hot_kernel_rooflines(st, ms_p2p, ms_m2l, p, precision):
+    """P2P against the FP32 pipe (derived peak) and M2L against its own pipe.
+
+    P2P work: interactions x 23 flop.  M2L work: M2L pairs x 2 (p+1)^4 flop, the
+    useful flops of the dense translation (the 3-way split, padding to 128 and
+    empty rows of a tile are not counted)."""
+    _, bf16_tf, label = measured_peaks()
+    fp32_peak = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    out = []
+    p2p_tf = st["n_p2p_interactions"] * P2P_FLOPS / (ms_p2p * 1e-3) / 1e12
+    out.append({"kernel": "k_p2p", "bound": "alu", "achieved": p2p_tf, "peak": fp32_peak,
+                "unit": "TFLOP/s", "frac": p2p_tf / fp32_peak, "traffic": captured_traffic("k_p2p"),
+                "ms": ms_p2p, "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+                "work": f"{st['n_p2p_interactions']} interactions x {P2P_FLOPS} flop"})
+    P2 = (p + 1) ** 2
+    m2l_tf = st["n_m2l_pairs"] * 2 * P2 * P2 / (ms_m2l * 1e-3) / 1e12
+    if precision == "fp32":
+        kern, bound, peak, src = "k_m2l_simt", "alu", fp32_peak, "derived FP32 peak (as for P2P)"
+    elif precision == "tf32x3":
+        kern, bound, peak = "k_m2l_tc<tf32x3>", "tensor", bf16_tf * 1.1 / 2.25
+        src = f"TF32 = BF16 dense {label} x nominal ratio 1.1/2.25"
+    else:
+        kern, bound, peak, src = "k_m2l_tc<bf16x3>", "tensor", bf16_tf, f"BF16 dense {label}"
+    out.append({"kernel": kern, "bound": bound, "achieved": m2l_tf, "peak": peak,
+                "unit": "TFLOP/s", "frac": m2l_tf / peak, "traffic": captured_traffic(kern),
+                "ms": ms_m2l, "peak_source": src,
+                "work": f"{st['n_m2l_pairs']} M2L pairs x 2 (p+1)^4 = {2 * P2 * P2} flop"})
+    return out
+
+
 # ------------------------------------------------------------------ clocks
 
 class ClockSampler:
@@ -136,7 +209,7 @@ class ClockSampler:
                  "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                  "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                  "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=self.fh, stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
@@ -237,24 +310,12 @@ def main():
     value = world * n / (ms_per_step / 1e3)
     clocks = clk.summary()
 
-    # roofline of the dominant kernel, from the library's event timing of each phase
+    # rooflines of the two hot kernels, from the library's event timing of each phase
     st0 = st_list[-1]
     ms_p2p = statistics.mean(s["ms_p2p"] for s in st_list)
     ms_m2l = statistics.mean(s["ms_m2l"] for s in st_list)
-    P2 = (w["p"] + 1) ** 2
-    fp32_peak = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    p2p_tf = st0["n_p2p_interactions"] * P2P_FLOPS / (ms_p2p * 1e-3) / 1e12
-    m2l_tf = st0["n_m2l_pairs"] * 2 * P2 * P2 / (ms_m2l * 1e-3) / 1e12
-    if ms_p2p >= ms_m2l:
-        roof = {"kernel": "k_p2p", "bound": "alu", "achieved": p2p_tf, "peak": fp32_peak,
-                "unit": "TFLOP/s", "frac": p2p_tf / fp32_peak, "traffic": None,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
-                "work": f"{st0['n_p2p_interactions']} interactions x {P2P_FLOPS} flop"}
-    else:
-        roof = {"kernel": "k_m2l_simt", "bound": "alu", "achieved": m2l_tf, "peak": fp32_peak,
-                "unit": "TFLOP/s", "frac": m2l_tf / fp32_peak, "traffic": None,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
-                "work": f"{st0['n_m2l_pairs']} M2L pairs x 2 (p+1)^4 flop"}
+    rooflines = hot_kernel_rooflines(st0, ms_p2p, ms_m2l, w["p"], args.precision)
+    roof = max(rooflines, key=lambda r: r["ms"])
     phases = {k: round(statistics.mean(s[k] for s in st_list), 4)
               for k in ("ms_tree", "ms_traverse", "ms_upward", "ms_m2l", "ms_downward", "ms_p2p",
                         "ms_total")}
@@ -285,6 +346,33 @@ def main():
                "h2d_bytes_per_step": int(x.nbytes + q.nbytes),
                "d2h_bytes_per_step": int(ph.nbytes + gh.nbytes), "ms_per_step": e2e_ms}
 
+    # accuracy of this very solve against the FP64 direct sum on sampled targets
+    acc = None
+    if rank == 0:
+        acc = accuracy(x, q, phi.cpu().numpy(), grad.cpu().numpy())
+
+    # the other M2L precisions, timed the same way (value and accuracy)
+    modes = {}
+    if rank == 0 and not args.no_modes:
+        for prec in ("fp32", "tf32x3", "bf16x3"):
+            if prec == args.precision:
+                continue
+            kw2 = dict(max_depth=w["max_depth"], precision=prec)
+            for _ in range(2):
+                fmm.laplace3d(xd, qd, w["p"], w["theta"], w["ncrit"], out=(phi, grad), **kw2)
+            ms = []
+            for k in range(args.steps):
+                flush.fill_(float(k))
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                fmm.laplace3d(xd, qd, w["p"], w["theta"], w["ncrit"], out=(phi, grad), **kw2)
+                b.record(stream)
+                b.synchronize()
+                ms.append(a.elapsed_time(b))
+            m = statistics.mean(ms)
+            modes[prec] = {"value": n / (m / 1e3), "ms_per_step": m,
+                           "accuracy": accuracy(x, q, phi.cpu().numpy(), grad.cpu().numpy())}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         from oracle import oracle as O
@@ -297,8 +385,10 @@ def main():
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": config_of(w, args), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "config": config_of(w, args), "roofline": roof, "rooflines": rooflines,
+                "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(sum(s["n_launches"] for s in st_list)),
+                "accuracy": acc, "m2l_modes": modes,
                 "clocks": clocks, "phases_ms": phases,
                 "counts": {k: st0[k] for k in ("ncells", "nleaves", "depth", "n_p2p_pairs",
                                                "n_p2p_interactions", "n_m2l_pairs",

@@ -45,6 +45,12 @@ extern thread_local int64_t g_launch_count;
     } while (0)
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Raises a kernel's dynamic shared memory limit once per device and value
+// (cudaFuncSetAttribute may synchronise, so it stays out of the per-solve path).
+void set_smem_limit_once(const void *func, int bytes);
+// Sets a kernel's preferred L1/shared carveout once per device.
+void set_carveout_once(const void *func, int carveout);
 inline int64_t round_up(int64_t a, int64_t b) { return ceil_div(a, b) * b; }
 
 // (p+1)^2 real coefficients, padded to a multiple of 32.

@@ -65,6 +65,8 @@ __global__ void k_traverse_level(CellArrays c, ListArrays L, int a, int b, doubl
 __global__ void k_hash_flags(const uint64_t *hash_keys, int *flag);
 __global__ void k_hash_compact(const uint64_t *hash_keys, const int *ex, uint64_t *ukeys,
                                uint32_t *uslot);
+__global__ void k_rank_classes(const uint64_t *ukeys, const uint32_t *uslot, int n,
+                               uint64_t *sorted_keys, int *slot_class);
 __global__ void k_slot_to_class(const uint32_t *uslot, int nclass, int *slot_class);
 __global__ void k_m2l_class(uint32_t *m2l_slot, int64_t n, const int *slot_class);
 __global__ void k_tile_bitmap(const int *m2l_tgt, const uint32_t *m2l_class, int64_t n,
@@ -107,7 +109,7 @@ void launch_m2l_tc(bool bf16, int nunits, const void *units, int ntiles, const i
 
 // p2p.cu
 __global__ void k_p2p(CellArrays c, ListArrays L, const int *leaves, int nleaves,
-                      const float4 *pts, float4 *near);
+                      const float4 *pts, float4 *near, int *counter);
 __global__ void k_direct(const float *xyz, const float *q, int64_t n, float *phi, float *grad);
 __global__ void k_combine(const float4 *far, const float4 *near, const uint32_t *idx, int64_t n,
                           float *phi, float *grad);

@@ -420,8 +420,7 @@ void launch_m2l_tc(bool bf16, int nunits, const void *units, int ntiles, const i
         const int ng = (int)ceil_div(128 + P2pad, 64);
 #define FMM_M2L_TC_LAUNCH(B, G)                                                                     \
     do {                                                                                           \
-        FMM_CUDA_TRY(cudaFuncSetAttribute(k_m2l_tc<B, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                          (int)smem));                                             \
+        set_smem_limit_once((const void *)k_m2l_tc<B, G>, (int)smem);                               \
         k_m2l_tc<B, G><<<nunits, kThreads, smem, st>>>(static_cast<const Unit *>(units), entry_class, \
                                                        src, M, table, P2pad, nstages, partial, flags); \
     } while (0)

@@ -111,24 +111,17 @@ __device__ __forceinline__ void p2p_chunk32(const float4 &xi, const float4 *buf,
     }
 }
 
-// One warp per target leaf, 4 warps per block.  Targets go 32 at a time, one
-// per lane; the last r < 32 targets are processed with the sources split into
-// g = floor(32 / r) interleaved subsets, so that r * g lanes stay busy, and the
-// g partial sums are added in shared memory.
-__global__ void __launch_bounds__(128)
-    k_p2p(CellArrays c, ListArrays L, const int *__restrict__ leaves, int nleaves,
-          const float4 *__restrict__ pts, float4 *__restrict__ near)
+// One warp per target leaf.  Targets go 32 at a time, one per lane; the last
+// r <= 16 targets are processed with the sources split into g = floor(32 / r)
+// interleaved subsets, so that r * g lanes stay busy, and the g partial sums are
+// added in shared memory.
+__device__ __forceinline__ void p2p_leaf(const CellArrays &c, const ListArrays &L, int T,
+                                         const float4 *__restrict__ pts, float4 *__restrict__ near,
+                                         float4 *buf, float4 *redbuf, int lane)
 {
-    __shared__ float4 sh[4][32];
-    __shared__ float4 red[4][32];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int li = blockIdx.x * 4 + warp;
-    if (li >= nleaves) return;
-    const int T = leaves[li];
     const int b = c.begin[T], e = c.end[T];
     const int *slist = L.p2p_src + L.p2p_off[T];
     const int cnt = L.p2p_cnt[T];
-    float4 *buf = sh[warp];
     int tb = b;
     // full passes, and a last pass of 17..31 targets (g = 1), one target per lane
     while (tb < e && (e - tb >= 32 || 2 * (e - tb) > 32)) {
@@ -162,12 +155,12 @@ __global__ void __launch_bounds__(128)
             }
             __syncwarp();
         }
-        red[warp][lane] = make_float4(phi, gx, gy, gz);
+        redbuf[lane] = make_float4(phi, gx, gy, gz);
         __syncwarp();
         if (lane < rem) {
-            float4 a = red[warp][lane];
+            float4 a = redbuf[lane];
             for (int k = 1; k < g; ++k) {
-                const float4 v = red[warp][lane + k * rem];
+                const float4 v = redbuf[lane + k * rem];
                 a.x += v.x;
                 a.y += v.y;
                 a.z += v.z;
@@ -175,6 +168,26 @@ __global__ void __launch_bounds__(128)
             }
             near[tb + lane] = a;
         }
+        __syncwarp();
+    }
+}
+
+// Persistent: a fixed number of blocks per SM, each warp taking the next leaf
+// from a counter, so the kernel leaves room on every SM for the far-field chain
+// that runs beside it and has no tail wave.
+__global__ void __launch_bounds__(128)
+    k_p2p(CellArrays c, ListArrays L, const int *__restrict__ leaves, int nleaves,
+          const float4 *__restrict__ pts, float4 *__restrict__ near, int *__restrict__ counter)
+{
+    __shared__ float4 sh[4][32];
+    __shared__ float4 red[4][32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (;;) {
+        int li = 0;
+        if (lane == 0) li = atomicAdd(counter, 1);
+        li = __shfl_sync(0xffffffffu, li, 0);
+        if (li >= nleaves) break;
+        p2p_leaf(c, L, leaves[li], pts, near, sh[warp], red[warp], lane);
     }
 }
 

@@ -277,9 +277,7 @@ void radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32
                       int64_t n, int bits, uint32_t *hist, uint32_t *scan_tmp, cudaStream_t st)
 {
     if (n <= 1) return;
-    // per-device attribute: set on every call (cheap)
-    FMM_CUDA_TRY(cudaFuncSetAttribute(k_radix_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)kScatterSmem));
+    set_smem_limit_once((const void *)k_radix_scatter, (int)kScatterSmem);
     const int ntiles = (int)ceil_div(n, kSortTile);
     const int64_t nh = (int64_t)kRadix * ntiles;
     uint64_t *ka = keys, *kb = keys_alt;

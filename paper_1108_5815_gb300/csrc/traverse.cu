@@ -264,6 +264,23 @@ __global__ void k_hash_compact(const uint64_t *__restrict__ hash_keys, const int
     }
 }
 
+// Sorts up to a few thousand distinct keys with one block: the rank of a key is
+// the number of smaller keys.  slot_class[slot of the key] = its rank.
+__global__ void k_rank_classes(const uint64_t *__restrict__ ukeys, const uint32_t *__restrict__ uslot,
+                               int n, uint64_t *__restrict__ sorted_keys, int *__restrict__ slot_class)
+{
+    extern __shared__ uint64_t sk[];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) sk[i] = ukeys[i];
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const uint64_t k = sk[i];
+        int r = 0;
+        for (int j = 0; j < n; ++j) r += sk[j] < k;
+        sorted_keys[r] = k;
+        slot_class[uslot[i]] = r;
+    }
+}
+
 __global__ void k_slot_to_class(const uint32_t *__restrict__ uslot, int nclass,
                                 int *__restrict__ slot_class)
 {

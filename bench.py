@@ -259,9 +259,8 @@ def main():
 
     from paper_1108_5815_gb300 import build, fmm
 
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_1108_5815_gb300 import replicas
+    rank, world, local = replicas.rank_info()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     if world > 1:
@@ -301,13 +300,9 @@ def main():
         if world > 1:
             dist.barrier()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    # each rank solved its own replica: job time = slowest rank, work = all ranks
+    total_ms, _, value = replicas.aggregate(sum(step_ms), n * args.steps, device=dev)
     ms_per_step = total_ms / args.steps
-    value = world * n / (ms_per_step / 1e3)
     clocks = clk.summary()
 
     # rooflines of the two hot kernels, from the library's event timing of each phase
@@ -337,12 +332,8 @@ def main():
             t0 = time.perf_counter()
             fmm.laplace3d_host(xh, qh, w["p"], w["theta"], w["ncrit"], out=(ph, gh), stream=sp, **kw)
             t_e2e += time.perf_counter() - t0
-        e2e_ms = 1e3 * t_e2e / args.steps
-        if world > 1:
-            t = torch.tensor([e2e_ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_ms = float(t.item())
-        e2e = {"value": world * n / (e2e_ms / 1e3), "unit": "particles/s",
+        e2e_ms, _, e2e_value = replicas.aggregate(1e3 * t_e2e / args.steps, n, device=dev)
+        e2e = {"value": e2e_value, "unit": "particles/s",
                "h2d_bytes_per_step": int(x.nbytes + q.nbytes),
                "d2h_bytes_per_step": int(ph.nbytes + gh.nbytes), "ms_per_step": e2e_ms}
 

@@ -101,6 +101,18 @@ fmm_status fmm_laplace3d_host(const float *xyz_host, const float *q_host, int64_
                               double theta, int ncrit, float *phi_host, float *grad_host,
                               void *stream, const fmm_options *opt, fmm_stats *stats);
 
+/* Many independent systems in one solve.  System s is the particles
+ * [offsets[s], offsets[s+1]) of xyz/q/phi/grad; offsets is a HOST array of
+ * nsys + 1 increasing values with offsets[0] = 0 and at least one particle per
+ * system (else FMM_ERR_ARG).  Each system gets its own bounding box and tree
+ * (one root per system, all trees built, traversed and evaluated together by
+ * the same kernel launches); no interaction crosses systems.  Every system uses
+ * the same p, theta, ncrit and options.  Same pointer conventions as
+ * fmm_laplace3d_ex; FMM_EXPORT_BOX then returns double[nsys][4]. */
+fmm_status fmm_laplace3d_batched(const float *xyz, const float *q, const int64_t *offsets,
+                                 int nsys, int p, double theta, int ncrit, float *phi, float *grad,
+                                 void *stream, const fmm_options *opt, fmm_stats *stats);
+
 /* Exact all-pairs sum on the GPU (the O(N^2) direct summation of the paper's
  * Introduction): FP32 arithmetic, same conventions as fmm_laplace3d. */
 fmm_status fmm_direct(const float *xyz, const float *q, int64_t N, float *phi, float *grad,
@@ -111,7 +123,7 @@ fmm_status fmm_direct(const float *xyz, const float *q, int64_t N, float *phi, f
  * NULL) receives the byte size.  Returns FMM_ERR_ARG if no solve has run or
  * capacity is too small.  Cells are in the library's order (level by level,
  * Morton order within a level); cell-index arrays refer to that order.
- *   FMM_EXPORT_BOX        double[4]: lo_x, lo_y, lo_z, side
+ *   FMM_EXPORT_BOX        double[nsys][4]: lo_x, lo_y, lo_z, side of each system's box
  *   FMM_EXPORT_KEYS       uint64[N] Morton keys in sorted order
  *   FMM_EXPORT_ORDER      int32[N]  original index of each sorted position
  *   FMM_EXPORT_CELLS      int64[ncells][6]: level, key prefix, begin, end, parent, nchild

@@ -233,10 +233,11 @@ __device__ __forceinline__ void cell_centre_side(const CellArrays &c, int cell,
 {
     const int l = c.level[cell];
     const uint64_t pre = c.prefix[cell];
-    s = ldexp(box[3], -l);
-    const double half = ldexp(box[3], -l - 1);
+    const double *bx = box + 4 * c.sys[cell];  // the box of the cell's own system
+    s = ldexp(bx[3], -l);
+    const double half = ldexp(bx[3], -l - 1);
 #pragma unroll
-    for (int a = 0; a < 3; ++a) cen[a] = box[a] + (double)(2 * (int64_t)compact3_dev(pre >> a) + 1) * half;
+    for (int a = 0; a < 3; ++a) cen[a] = bx[a] + (double)(2 * (int64_t)compact3_dev(pre >> a) + 1) * half;
 }
 
 constexpr int kMaxChunks = 14;  // ceil(448 / 32): p <= 20

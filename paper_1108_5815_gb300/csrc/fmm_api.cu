@@ -76,6 +76,7 @@ struct Workspace {
     int64_t N = 0;
     int ncells = 0, nleaves = 0, depth = 0, P2pad = 0, nclass = 0;
     int64_t nm2l = 0, np2p = 0;
+    int nsys = 1;
     int64_t cap_m2l = 0, cap_p2p = 0, cap_def = 0;  // list capacities that sufficed before
     // The solve runs on two library streams, both non-blocking (a kernel on the
     // legacy default stream would keep the other stream's work from overlapping):
@@ -237,23 +238,10 @@ struct Events {
     }
 };
 
-__global__ void k_root_lists(ListArrays L, int root_is_leaf)
+__global__ void k_init_bbox(uint32_t *bbox_u, int nsys)
 {
-    L.m2l_off[0] = 0;
-    L.m2l_cnt[0] = 0;
-    L.p2p_off[0] = 0;
-    if (root_is_leaf) {
-        L.p2p_src[0] = 0;
-        L.p2p_tgt[0] = 0;
-        L.p2p_cnt[0] = 1;
-        L.def_off[0] = 0;
-        L.def_cnt[0] = 0;
-    } else {
-        L.p2p_cnt[0] = 0;
-        L.def_src[0] = 0;
-        L.def_off[0] = 0;
-        L.def_cnt[0] = 1;
-    }
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 6 * nsys; i += gridDim.x * blockDim.x)
+        bbox_u[i] = (i % 6) < 3 ? 0xffffffffu : 0u;
 }
 
 __global__ void k_p2p_interactions(const int *__restrict__ tgt, const int *__restrict__ src,
@@ -291,9 +279,9 @@ void validate(const void *xyz, const void *q, int64_t N, int p, double theta, in
 }
 
 // The solve on device buffers; the caller holds ws.mu.
-void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, int p,
-                  double theta, int ncrit, float *phi, float *grad, cudaStream_t caller,
-                  const fmm_options &o, fmm_stats *stats)
+void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, int nsys,
+                  const int64_t *offsets, int p, double theta, int ncrit, float *phi, float *grad,
+                  cudaStream_t caller, const fmm_options &o, fmm_stats *stats)
 {
     ensure_streams(ws);
     cudaStream_t st = ws.main_stream;
@@ -311,8 +299,9 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
 
     // ---------------------------------------------------------- box, keys, sort
     int *flags = need<int>(ws, "flags", kNumFlags, st);
-    uint32_t *bbox_u = need<uint32_t>(ws, "bbox_u", 6, st);
-    double *box = need<double>(ws, "box", 4, st);
+    uint32_t *bbox_u = need<uint32_t>(ws, "bbox_u", 6 * (size_t)nsys, st);
+    double *box = need<double>(ws, "box", 4 * (size_t)nsys, st);
+    int *sys_off = need<int>(ws, "sys_off", nsys + 1, st);
     uint64_t *keys = need<uint64_t>(ws, "keys", N, st);
     uint64_t *keys_alt = need<uint64_t>(ws, "keys_alt", N, st);
     uint32_t *idx = need<uint32_t>(ws, "idx", N, st);
@@ -321,19 +310,42 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
     uint32_t *hist = need<uint32_t>(ws, "hist", nh, st);
     uint32_t *tmp_u32 = need<uint32_t>(ws, "scan_u32", scan_temp_elems(nh), st);
     float4 *pts = need<float4>(ws, "pts", N, st);
+    {
+        std::vector<int> off32(nsys + 1);
+        for (int sy = 0; sy <= nsys; ++sy) off32[sy] = (int)offsets[sy];
+        upload(ws, sys_off, off32.data(), sizeof(int) * (nsys + 1), st);
+    }
     FMM_CUDA_TRY(cudaMemsetAsync(flags, 0, sizeof(int) * kNumFlags, st));
-    FMM_CUDA_TRY(cudaMemsetAsync(bbox_u, 0xff, 3 * sizeof(uint32_t), st));
-    FMM_CUDA_TRY(cudaMemsetAsync(bbox_u + 3, 0, 3 * sizeof(uint32_t), st));
-    k_bbox<<<grid_for(N, 256), 256, 0, st>>>(xyz, N, bbox_u, flags);
+    k_init_bbox<<<(unsigned)ceil_div(6 * (int64_t)nsys, 256), 256, 0, st>>>(bbox_u, nsys);
     FMM_LAUNCH_CHECK();
-    k_morton<<<grid_for(N, 256), 256, 0, st>>>(xyz, N, bbox_u, box, keys, idx);
+    if (nsys == 1)
+        k_bbox<<<grid_for(N, 256), 256, 0, st>>>(xyz, N, bbox_u, flags);
+    else
+        k_bbox_sys<<<(unsigned)ceil_div(ceil_div(N, 8), 256), 256, 0, st>>>(xyz, N, sys_off, nsys, bbox_u, flags);
     FMM_LAUNCH_CHECK();
-    radix_sort_pairs(keys, idx, keys_alt, idx_alt, N, 63, hist, tmp_u32, st);
+    k_morton<<<grid_for(N, 256), 256, 0, st>>>(xyz, N, sys_off, nsys, bbox_u, box, keys, idx);
+    FMM_LAUNCH_CHECK();
+    if (nsys == 1) {
+        radix_sort_pairs(keys, idx, keys_alt, idx_alt, N, 63, hist, tmp_u32, st);
+    } else {
+        // sort by key, then stably by system; the keys follow the permutation
+        uint64_t *keys_orig = need<uint64_t>(ws, "keys_orig", N, st);
+        uint64_t *sys_key = need<uint64_t>(ws, "sys_key", N, st);
+        FMM_CUDA_TRY(cudaMemcpyAsync(keys_orig, keys, sizeof(uint64_t) * N, cudaMemcpyDeviceToDevice, st));
+        radix_sort_pairs(keys, idx, keys_alt, idx_alt, N, 63, hist, tmp_u32, st);
+        k_sys_of_sorted<<<grid_for(N, 256), 256, 0, st>>>(idx, N, sys_off, nsys, sys_key);
+        FMM_LAUNCH_CHECK();
+        int bits = 1;
+        while ((1 << bits) < nsys) ++bits;
+        radix_sort_pairs(sys_key, idx, keys_alt, idx_alt, N, bits, hist, tmp_u32, st);
+        k_gather_keys<<<grid_for(N, 256), 256, 0, st>>>(keys_orig, idx, N, keys);
+        FMM_LAUNCH_CHECK();
+    }
     k_permute<<<grid_for(N, 256), 256, 0, st>>>(xyz, q, idx, N, pts);
     FMM_LAUNCH_CHECK();
 
     // ---------------------------------------------------------- tree
-    int cell_cap = std::max(1024, N / 8 + 64);
+    int cell_cap = std::max(1024, N / 8 + 64 + nsys);
     auto cells = [&](int cap, bool keep) {
         CellArrays c;
         c.level = need<int>(ws, "c_level", cap, st, keep);
@@ -345,10 +357,11 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
         c.nchild = need<int>(ws, "c_nchild", cap, st, keep);
         c.tile = need<int>(ws, "c_tile", cap, st, keep);
         c.lane = need<int>(ws, "c_lane", cap, st, keep);
+        c.sys = need<int>(ws, "c_sys", cap, st, keep);
         return c;
     };
     CellArrays c = cells(cell_cap, false);
-    k_init_root<<<1, 1, 0, st>>>(c, N);
+    k_init_roots<<<(unsigned)ceil_div(nsys, 256), 256, 0, st>>>(c, sys_off, nsys);
     FMM_LAUNCH_CHECK();
     // boundary positions of adjacent keys, bucketed (stably) by the level at which they differ
     uint64_t *blvl = need<uint64_t>(ws, "blvl", std::max(N - 1, 1), st);
@@ -361,8 +374,8 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
     }
     k_level_starts<<<1, 32, 0, st>>>(blvl, N - 1, bstart);
     FMM_LAUNCH_CHECK();
-    std::vector<int> lstart = {0, 1};
-    int tiles_total = 1;
+    std::vector<int> lstart = {0, nsys};
+    int tiles_total = (int)ceil_div(nsys, kTile);  // the roots' tiles
     int64_t *i64_tmp = need<int64_t>(ws, "scan_i64", scan_temp_elems(std::max(N, 1 << 16)), st);
     for (int l = 0;; ++l) {
         const int a = lstart[l], b = lstart[l + 1];
@@ -419,11 +432,10 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
     L.def_cnt = need<int>(ws, "def_cnt", ncells, st);
     // capacities: the last solve's totals, or estimates; regrown exactly on overflow
     int64_t m2l_cap = std::max<int64_t>(ws.cap_m2l, std::max<int64_t>(4096, (int64_t)ncells * 160));
-    int64_t p2p_cap = std::max<int64_t>(ws.cap_p2p, std::max<int64_t>(4096, (int64_t)nleaves * 96));
-    int64_t def_cap = std::max<int64_t>(ws.cap_def, std::max<int64_t>(4096, (int64_t)ncells * 96));
+    int64_t p2p_cap = std::max<int64_t>(ws.cap_p2p, std::max<int64_t>(4096 + nsys, (int64_t)nleaves * 96));
+    int64_t def_cap = std::max<int64_t>(ws.cap_def, std::max<int64_t>(4096 + nsys, (int64_t)ncells * 96));
     uint64_t *hash_keys = need<uint64_t>(ws, "hash_keys", kHashCap, st);
     unsigned long long *tcount = need<unsigned long long>(ws, "trav_counters", 3, st);
-    const bool root_leaf = ncells == 1;
     int64_t m2l_total = 0, p2p_total = 0;
     for (int attempt = 0;; ++attempt) {
         L.m2l_src = need<int>(ws, "m2l_src", m2l_cap, st);
@@ -433,9 +445,7 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
         L.p2p_tgt = need<int>(ws, "p2p_tgt", p2p_cap, st);
         L.def_src = need<int>(ws, "def_src", def_cap, st);
         FMM_CUDA_TRY(cudaMemsetAsync(hash_keys, 0xff, sizeof(uint64_t) * kHashCap, st));
-        const unsigned long long init[3] = {0ull, root_leaf ? 1ull : 0ull, root_leaf ? 0ull : 1ull};
-        upload(ws, tcount, init, sizeof(init), st);
-        k_root_lists<<<1, 1, 0, st>>>(L, root_leaf ? 1 : 0);
+        k_root_lists<<<1, 256, 0, st>>>(c, L, nsys, tcount);
         FMM_LAUNCH_CHECK();
         for (int l = 1; l <= depth; ++l) {
             const int a = lstart[l], b = lstart[l + 1];
@@ -695,6 +705,7 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
 
     ws.have_solve = true;
     ws.N = N;
+    ws.nsys = nsys;
     ws.ncells = ncells;
     ws.nleaves = nleaves;
     ws.depth = depth;
@@ -774,7 +785,8 @@ fmm_status fmm_laplace3d_ex(const float *xyz, const float *q, int64_t N, int p, 
         validate(xyz, q, N, p, theta, ncrit, phi, grad, o);
         Workspace &ws = workspace_for_current_device();
         std::lock_guard<std::mutex> lk(ws.mu);
-        solve_locked(ws, xyz, q, N, p, theta, ncrit, phi, grad, (cudaStream_t)stream, o, stats);
+        const int64_t off[2] = {0, N};
+        solve_locked(ws, xyz, q, N, 1, off, p, theta, ncrit, phi, grad, (cudaStream_t)stream, o, stats);
     });
 }
 
@@ -800,10 +812,30 @@ fmm_status fmm_laplace3d_host(const float *xyz_host, const float *q_host, int64_
         float *gd = need<float>(ws, "host_grad", 3 * (size_t)N, st);
         FMM_CUDA_TRY(cudaMemcpyAsync(xd, xyz_host, sizeof(float) * 3 * N, cudaMemcpyHostToDevice, st));
         FMM_CUDA_TRY(cudaMemcpyAsync(qd, q_host, sizeof(float) * N, cudaMemcpyHostToDevice, st));
-        solve_locked(ws, xd, qd, N, p, theta, ncrit, pd, gd, st, o, stats);
+        const int64_t off[2] = {0, N};
+        solve_locked(ws, xd, qd, N, 1, off, p, theta, ncrit, pd, gd, st, o, stats);
         FMM_CUDA_TRY(cudaMemcpyAsync(phi_host, pd, sizeof(float) * N, cudaMemcpyDeviceToHost, st));
         FMM_CUDA_TRY(cudaMemcpyAsync(grad_host, gd, sizeof(float) * 3 * N, cudaMemcpyDeviceToHost, st));
         FMM_CUDA_TRY(cudaStreamSynchronize(st));
+    });
+}
+
+fmm_status fmm_laplace3d_batched(const float *xyz, const float *q, const int64_t *offsets,
+                                 int nsys, int p, double theta, int ncrit, float *phi, float *grad,
+                                 void *stream, const fmm_options *opt, fmm_stats *stats)
+{
+    return guarded([&] {
+        if (!offsets || nsys < 1) throw Error{FMM_ERR_ARG, "offsets must hold nsys + 1 >= 2 entries"};
+        if (offsets[0] != 0) throw Error{FMM_ERR_ARG, "offsets[0] must be 0"};
+        for (int sy = 0; sy < nsys; ++sy)
+            if (offsets[sy + 1] <= offsets[sy]) throw Error{FMM_ERR_ARG, "every system needs at least one particle"};
+        const int64_t N = offsets[nsys];
+        const fmm_options o = resolve_opts(opt);
+        validate(xyz, q, N, p, theta, ncrit, phi, grad, o);
+        Workspace &ws = workspace_for_current_device();
+        std::lock_guard<std::mutex> lk(ws.mu);
+        solve_locked(ws, xyz, q, N, nsys, offsets, p, theta, ncrit, phi, grad, (cudaStream_t)stream, o,
+                     stats);
     });
 }
 
@@ -828,7 +860,7 @@ fmm_status fmm_export(int what, void *dst, int64_t capacity, int64_t *needed)
         if (!ws.have_solve) throw Error{FMM_ERR_ARG, "no solve has completed on this device"};
         int64_t bytes = 0;
         switch (what) {
-            case FMM_EXPORT_BOX: bytes = 4 * sizeof(double); break;
+            case FMM_EXPORT_BOX: bytes = 4 * sizeof(double) * ws.nsys; break;
             case FMM_EXPORT_KEYS: bytes = ws.N * sizeof(uint64_t); break;
             case FMM_EXPORT_ORDER: bytes = ws.N * sizeof(int32_t); break;
             case FMM_EXPORT_CELLS: bytes = (int64_t)ws.ncells * 6 * sizeof(int64_t); break;

@@ -23,6 +23,7 @@ struct CellArrays {
     int *begin, *end;  // sorted particle range
     int *parent, *child0, *nchild;
     int *tile, *lane;  // M2L GEMM tile of this cell as a target
+    int *sys;          // independent system (root) the cell belongs to
 };
 
 // Interaction lists written by the traversal (CSR per target cell).
@@ -42,11 +43,16 @@ constexpr uint64_t kHashEmpty = ~0ull;
 
 // tree.cu
 __global__ void k_bbox(const float *xyz, int64_t n, uint32_t *bbox_u, int *flags);
-__global__ void k_morton(const float *xyz, int64_t n, const uint32_t *bbox_u, double *box,
-                         uint64_t *keys, uint32_t *idx);
+__global__ void k_morton(const float *xyz, int64_t n, const int *off, int nsys,
+                         const uint32_t *bbox_u, double *box, uint64_t *keys, uint32_t *idx);
+__global__ void k_bbox_sys(const float *xyz, int64_t n, const int *off, int nsys, uint32_t *bbox_u,
+                           int *flags);
+__global__ void k_sys_of_sorted(const uint32_t *idx, int64_t n, const int *off, int nsys,
+                                uint64_t *sys_key);
+__global__ void k_gather_keys(const uint64_t *orig, const uint32_t *idx, int64_t n, uint64_t *keys);
+__global__ void k_init_roots(CellArrays c, const int *off, int nsys);
 __global__ void k_permute(const float *xyz, const float *q, const uint32_t *idx, int64_t n,
                           float4 *out);
-__global__ void k_init_root(CellArrays c, int n);
 __global__ void k_first_diff(const uint64_t *keys, int64_t n, uint64_t *lvl, uint32_t *pos);
 __global__ void k_level_starts(const uint64_t *lvl, int64_t n, int *start);
 __global__ void k_split_count(CellArrays c, const uint32_t *bpos, const int *lstart, int a, int b,
@@ -65,6 +71,7 @@ __global__ void k_traverse_level(CellArrays c, ListArrays L, int a, int b, doubl
 __global__ void k_hash_flags(const uint64_t *hash_keys, int *flag);
 __global__ void k_hash_compact(const uint64_t *hash_keys, const int *ex, uint64_t *ukeys,
                                uint32_t *uslot);
+__global__ void k_root_lists(CellArrays c, ListArrays L, int nsys, unsigned long long *counters);
 __global__ void k_rank_classes(const uint64_t *ukeys, const uint32_t *uslot, int n,
                                uint64_t *sorted_keys, int *slot_class);
 __global__ void k_slot_to_class(const uint32_t *uslot, int nclass, int *slot_class);

@@ -89,7 +89,7 @@ extern "C" fmm_status fmm_morton_sort_noalloc(const float *xyz, int64_t N, uint6
         const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(N, 256), 152 * 16);
         k_bbox<<<grid, 256, 0, st>>>(xyz, N, bbox_u, flags);
         FMM_LAUNCH_CHECK();
-        k_morton<<<grid, 256, 0, st>>>(xyz, N, bbox_u, box, keys, idx);
+        k_morton<<<grid, 256, 0, st>>>(xyz, N, nullptr, 1, bbox_u, box, keys, idx);
         FMM_LAUNCH_CHECK();
         radix_sort_pairs(keys, idx, keys_alt, idx_alt, N, 63, hist, scan, st);
         int hflags[kNumFlags];

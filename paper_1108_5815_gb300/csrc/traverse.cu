@@ -264,6 +264,63 @@ __global__ void k_hash_compact(const uint64_t *__restrict__ hash_keys, const int
     }
 }
 
+// Level 0 of the traversal, one pair (root, root) per system: a root that is a
+// leaf gets the P2P pair (root, root), any other root defers itself to its
+// children.  One block, deterministic compaction (block-wide scans in chunks);
+// counters[] receive the list sizes.
+__global__ void k_root_lists(CellArrays c, ListArrays L, int nsys, unsigned long long *counters)
+{
+    __shared__ int sw[64];
+    int base_p = 0, base_d = 0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int s0 = 0; s0 < nsys; s0 += blockDim.x) {
+        const int s = s0 + threadIdx.x;
+        const bool valid = s < nsys;
+        const bool leaf = valid && c.nchild[s] == 0;
+        const bool defer = valid && !leaf;
+        const unsigned bp = __ballot_sync(0xffffffffu, leaf), bd = __ballot_sync(0xffffffffu, defer);
+        if (lane == 0) {
+            sw[warp] = __popc(bp);
+            sw[32 + warp] = __popc(bd);
+        }
+        __syncthreads();
+        int op = 0, od = 0, tp = 0, td = 0;
+        for (int w = 0; w < nw; ++w) {
+            if (w < warp) {
+                op += sw[w];
+                od += sw[32 + w];
+            }
+            tp += sw[w];
+            td += sw[32 + w];
+        }
+        const unsigned lt = (1u << lane) - 1u;
+        op += base_p + __popc(bp & lt);
+        od += base_d + __popc(bd & lt);
+        if (valid) {
+            L.m2l_off[s] = 0;
+            L.m2l_cnt[s] = 0;
+            L.p2p_off[s] = op;
+            L.p2p_cnt[s] = leaf ? 1 : 0;
+            L.def_off[s] = od;
+            L.def_cnt[s] = leaf ? 0 : 1;
+            if (leaf) {
+                L.p2p_src[op] = s;
+                L.p2p_tgt[op] = s;
+            } else {
+                L.def_src[od] = s;
+            }
+        }
+        base_p += tp;
+        base_d += td;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        counters[0] = 0;
+        counters[1] = (unsigned long long)base_p;
+        counters[2] = (unsigned long long)base_d;
+    }
+}
+
 // Sorts up to a few thousand distinct keys with one block: the rank of a key is
 // the number of smaller keys.  slot_class[slot of the key] = its rank.
 __global__ void k_rank_classes(const uint64_t *__restrict__ ukeys, const uint32_t *__restrict__ uslot,

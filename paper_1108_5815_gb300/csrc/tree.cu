@@ -63,30 +63,112 @@ __global__ void k_bbox(const float *__restrict__ xyz, int64_t n, uint32_t *__res
     }
 }
 
-// Decodes the box into box[0..2] = lo, box[3] = side (FP64), then writes keys
-// and the identity permutation.
-__global__ void k_morton(const float *__restrict__ xyz, int64_t n,
-                         const uint32_t *__restrict__ bbox_u, double *__restrict__ box,
-                         uint64_t *__restrict__ keys, uint32_t *__restrict__ idx)
+// System of particle i: the s with off[s] <= i < off[s+1].
+__device__ __forceinline__ int system_of(const int *__restrict__ off, int nsys, int64_t i)
 {
-    double lo[3], side = 0.0;
+    int lo = 0, hi = nsys - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if ((int64_t)off[mid] <= i)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// Box of one system from its ordered min/max: lo per axis and the cube side.
+__device__ __forceinline__ void decode_box(const uint32_t *__restrict__ bu, double lo[3], double &side)
+{
+    side = 0.0;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        lo[a] = (double)ordered_to_float(bbox_u[a]);
-        double hi = (double)ordered_to_float(bbox_u[3 + a]);
-        double ext = __dsub_rn(hi, lo[a]);
+        lo[a] = (double)ordered_to_float(bu[a]);
+        const double hi = (double)ordered_to_float(bu[3 + a]);
+        const double ext = __dsub_rn(hi, lo[a]);
         side = ext > side ? ext : side;
     }
     if (!(side > 0.0)) side = 1.0;
-    const double s = __ddiv_rn(2097152.0, side);
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        box[0] = lo[0];
-        box[1] = lo[1];
-        box[2] = lo[2];
-        box[3] = side;
+}
+
+// Per-system box for several systems stored back to back (off[] on the device):
+// each thread reduces 8 consecutive particles, flushing when the system changes;
+// a warp whose lanes end in one system combines before its atomics.
+__global__ void k_bbox_sys(const float *__restrict__ xyz, int64_t n, const int *__restrict__ off,
+                           int nsys, uint32_t *__restrict__ bbox_u, int *__restrict__ flags)
+{
+    const int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 8;
+    float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    bool bad = false;
+    int cur = i0 < n ? system_of(off, nsys, i0) : -1;
+    for (int64_t i = i0; i < n && i < i0 + 8; ++i) {
+        if (i >= off[cur + 1]) {
+            for (int a = 0; a < 3; ++a) {
+                atomicMin(&bbox_u[6 * cur + a], float_to_ordered(mn[a]));
+                atomicMax(&bbox_u[6 * cur + 3 + a], float_to_ordered(mx[a]));
+                mn[a] = INFINITY;
+                mx[a] = -INFINITY;
+            }
+            while (i >= off[cur + 1]) ++cur;
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const float v = xyz[3 * i + a];
+            bad |= !isfinite(v);
+            mn[a] = fminf(mn[a], v);
+            mx[a] = fmaxf(mx[a], v);
+        }
     }
+    const int s0 = __shfl_sync(0xffffffffu, cur, 0);
+    const bool uniform = __all_sync(0xffffffffu, cur == s0 || cur < 0);
+    if (uniform) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                mn[a] = fminf(mn[a], __shfl_xor_sync(0xffffffffu, mn[a], o));
+                mx[a] = fmaxf(mx[a], __shfl_xor_sync(0xffffffffu, mx[a], o));
+            }
+    }
+    if (cur >= 0 && (!uniform || (threadIdx.x & 31) == 0)) {
+        for (int a = 0; a < 3; ++a) {
+            atomicMin(&bbox_u[6 * cur + a], float_to_ordered(mn[a]));
+            atomicMax(&bbox_u[6 * cur + 3 + a], float_to_ordered(mx[a]));
+        }
+    }
+    if (bad) atomicOr(&flags[kFlagNonfinite], 1);
+}
+
+// Decodes each system's box into box[4s..4s+3] = lo, side (FP64), then writes
+// keys (quantised in the particle's own system box) and the identity permutation.
+__global__ void k_morton(const float *__restrict__ xyz, int64_t n, const int *__restrict__ off,
+                         int nsys, const uint32_t *__restrict__ bbox_u, double *__restrict__ box,
+                         uint64_t *__restrict__ keys, uint32_t *__restrict__ idx)
+{
+    if (blockIdx.x == 0) {
+        for (int sy = threadIdx.x; sy < nsys; sy += blockDim.x) {
+            double lo[3], side;
+            decode_box(bbox_u + 6 * sy, lo, side);
+            box[4 * sy] = lo[0];
+            box[4 * sy + 1] = lo[1];
+            box[4 * sy + 2] = lo[2];
+            box[4 * sy + 3] = side;
+        }
+    }
+    int sys = 0;
+    double lo[3], side;
+    decode_box(bbox_u, lo, side);
+    double s = __ddiv_rn(2097152.0, side);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
+        if (nsys > 1) {
+            const int si = system_of(off, nsys, i);
+            if (si != sys) {
+                sys = si;
+                decode_box(bbox_u + 6 * sys, lo, side);
+                s = __ddiv_rn(2097152.0, side);
+            }
+        }
         uint32_t k[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
@@ -113,17 +195,38 @@ __global__ void k_permute(const float *__restrict__ xyz, const float *__restrict
     }
 }
 
-__global__ void k_init_root(CellArrays c, int n)
+// Second sort key of a batch: the system of each (key-sorted) particle.
+__global__ void k_sys_of_sorted(const uint32_t *__restrict__ idx, int64_t n, const int *__restrict__ off,
+                                int nsys, uint64_t *__restrict__ sys_key)
 {
-    c.level[0] = 0;
-    c.prefix[0] = 0;
-    c.begin[0] = 0;
-    c.end[0] = n;
-    c.parent[0] = -1;
-    c.child0[0] = -1;
-    c.nchild[0] = 0;
-    c.tile[0] = 0;
-    c.lane[0] = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        sys_key[i] = (uint64_t)system_of(off, nsys, idx[i]);
+}
+
+__global__ void k_gather_keys(const uint64_t *__restrict__ orig, const uint32_t *__restrict__ idx,
+                              int64_t n, uint64_t *__restrict__ keys)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        keys[i] = orig[idx[i]];
+}
+
+// One root cell per system; roots fill the first ceil(nsys / 128) M2L tiles.
+__global__ void k_init_roots(CellArrays c, const int *__restrict__ off, int nsys)
+{
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nsys; s += gridDim.x * blockDim.x) {
+        c.level[s] = 0;
+        c.prefix[s] = 0;
+        c.begin[s] = off[s];
+        c.end[s] = off[s + 1];
+        c.parent[s] = -1;
+        c.child0[s] = -1;
+        c.nchild[s] = 0;
+        c.tile[s] = s / kTile;
+        c.lane[s] = s % kTile;
+        c.sys[s] = s;
+    }
 }
 
 // Boundary levels: for i in [1, n), the first level at which the keys of
@@ -211,6 +314,7 @@ __global__ void k_split_emit(CellArrays c, const uint64_t *__restrict__ keys,
     const int cb = c.begin[i], ce = c.end[i];
     const int shift = 3 * (kKeyBits - level - 1);
     const uint64_t pre = c.prefix[i];
+    const int sys = c.sys[i];
     const uint32_t *B = bpos + lstart[level + 1];
     const int nb = lstart[level + 2] - lstart[level + 1];
     const int lo = lower_pos(B, nb, (uint32_t)cb + 1);
@@ -229,6 +333,7 @@ __global__ void k_split_emit(CellArrays c, const uint64_t *__restrict__ keys,
         c.nchild[ch] = 0;
         c.tile[ch] = tile_base + window * 8 + o;
         c.lane[ch] = lane;
+        c.sys[ch] = sys;
         beg = end;
     }
     c.child0[i] = first;

@@ -24,6 +24,7 @@ EXPORT = {"box": 0, "keys": 1, "order": 2, "cells": 3, "p2p": 4, "m2l": 5, "mult
 
 # every symbol the header declares
 ABI_SYMBOLS = ("fmm_default_options", "fmm_laplace3d", "fmm_laplace3d_ex", "fmm_laplace3d_host",
+               "fmm_laplace3d_batched",
                "fmm_direct", "fmm_export", "fmm_last_error", "fmm_morton_sort_noalloc")
 
 
@@ -73,12 +74,15 @@ def load(path: str | None = None):
                                                                   ctypes.POINTER(Stats)]
         L.fmm_laplace3d_host.argtypes = L.fmm_laplace3d_ex.argtypes
         L.fmm_direct.argtypes = [vp, vp, i64, vp, vp, vp]
+        L.fmm_laplace3d_batched.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                            ctypes.c_int, vp, vp, vp, ctypes.POINTER(Options),
+                                            ctypes.POINTER(Stats)]
         L.fmm_export.argtypes = [ctypes.c_int, vp, i64, ctypes.POINTER(i64)]
         L.fmm_last_error.restype = ctypes.c_char_p
         L.fmm_morton_sort_noalloc.argtypes = [vp, i64, vp, vp, vp, vp]
         L.fmm_morton_sort_noalloc.restype = ctypes.c_int
         for name in ("fmm_laplace3d", "fmm_laplace3d_ex", "fmm_laplace3d_host", "fmm_direct",
-                     "fmm_export"):
+                     "fmm_export", "fmm_laplace3d_batched"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
         return L
@@ -161,6 +165,32 @@ def laplace3d_host(xyz: np.ndarray, q: np.ndarray, p: int, theta: float, ncrit: 
     return (phi, grad, st.as_dict()) if stats else (phi, grad)
 
 
+def laplace3d_batched(xyz, q, offsets, p: int, theta: float, ncrit: int, *, max_depth: int = 0,
+                      precision: str = "fp32", stats: bool = False, out=None):
+    """Independent systems in one solve: system s = rows offsets[s]:offsets[s+1] of
+    the CUDA float32 xyz[N,3], q[N]; offsets is a host int sequence (len nsys + 1)."""
+    import torch
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+    n = int(xyz.shape[0])
+    if off.ndim != 1 or len(off) < 2 or off[-1] != n:
+        raise FmmError(FMM_ERR_ARG, "offsets must be 1-D with offsets[-1] == N")
+    xyz = _dev_f32(xyz, (n, 3), "xyz")
+    q = _dev_f32(q, (n,), "q")
+    with torch.cuda.device(xyz.device):
+        if out is None:
+            phi = torch.empty(n, device=xyz.device, dtype=torch.float32)
+            grad = torch.empty(n, 3, device=xyz.device, dtype=torch.float32)
+        else:
+            phi, grad = out
+        o = _options(max_depth, precision)
+        st = Stats()
+        _check(load().fmm_laplace3d_batched(xyz.data_ptr(), q.data_ptr(), off.ctypes.data,
+                                            len(off) - 1, p, float(theta), ncrit, phi.data_ptr(),
+                                            grad.data_ptr(), _stream_ptr(torch, xyz.device),
+                                            ctypes.byref(o), ctypes.byref(st) if stats else None))
+    return (phi, grad, st.as_dict()) if stats else (phi, grad)
+
+
 def direct(xyz, q):
     """Exact all-pairs sum on the GPU (FP32)."""
     import torch
@@ -175,7 +205,7 @@ def direct(xyz, q):
     return phi, grad
 
 
-_EXPORT_DTYPE = {"box": (np.float64, None), "keys": (np.uint64, None), "order": (np.int32, None),
+_EXPORT_DTYPE = {"box": (np.float64, 4), "keys": (np.uint64, None), "order": (np.int32, None),
                  "cells": (np.int64, 6), "p2p": (np.int32, 2), "m2l": (np.int32, 3),
                  "multipole": (np.float32, "P2pad"), "local": (np.float32, "P2pad")}
 

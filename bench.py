@@ -48,23 +48,35 @@ def parse():
     ap.add_argument("--workload", default="uniform1m")
     ap.add_argument("--precision", default="tf32x3", choices=["fp32", "tf32x3", "bf16x3"])
     ap.add_argument("--no-modes", action="store_true", help="skip timing the other M2L precisions")
+    ap.add_argument("--p", type=int, default=None, help="override the workload's expansion order")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
 
 
-def workload(name):
+def workload(name, p=None):
+    """(parameters, xyz, q, offsets) -- offsets is None for a single system."""
     from paper_1108_5815_gb300 import inputs
     w = dict(inputs.WORKLOADS[name])
+    if p is not None:
+        w["p"] = p
+    if w["kind"] == "batched":
+        x, q, off = inputs.batched_systems(w["nsys"], w["seed"])
+        w["n"] = int(off[-1])
+        return w, x, q, off
     x, q = inputs.make(w["kind"], w["n"], w["seed"])
-    return w, x, q
+    return w, x, q, None
 
 
 def config_of(w, args):
-    return {"workload": f"{args.workload}: N={w['n']} {w['kind']} cube, q~U[-1,1]",
-            "N": w["n"], "p": w["p"], "theta": w["theta"], "ncrit": w["ncrit"],
+    if w["kind"] == "batched":
+        desc = (f"{args.workload}: {w['nsys']} independent systems, N_i log-uniform in [1e3, 1e5] "
+                f"(total {w['n']}), half uniform cube / half Plummer, q~U[-1,1]")
+    else:
+        desc = f"{args.workload}: N={w['n']} {w['kind']}, " + ("q=1/N" if w["kind"] == "plummer" else "q~U[-1,1]")
+    return {"workload": desc, "N": w["n"], "p": w["p"], "theta": w["theta"], "ncrit": w["ncrit"],
             "max_depth": w["max_depth"], "m2l": args.precision,
-            "l2_policy": "512 MB buffer written between timed steps (inputs 16 MB < L2)"}
+            "l2_policy": "512 MB buffer written between timed steps"}
 
 
 # ------------------------------------------------------------------ oracle timing
@@ -91,19 +103,36 @@ def oracle_sample(x, q, w, leaf_stride=128):
     return w["n"] / t_total, t2 - t0, desc
 
 
+def oracle_sample_batched(x, q, off, w, stride=32):
+    """Oracle FMM on every `stride`-th system, its time scaled to all systems."""
+    from oracle import oracle as O
+    t0 = time.perf_counter()
+    done = 0
+    picked = list(range(0, len(off) - 1, stride))
+    for sy in picked:
+        a, b = off[sy], off[sy + 1]
+        O.Fmm(x[a:b], q[a:b], w["p"], w["theta"], w["ncrit"], max_depth=w["max_depth"]).evaluate()
+        done += b - a
+    t = time.perf_counter() - t0
+    desc = (f"oracle FMM on {len(picked)} of {len(off) - 1} systems ({done} particles), "
+            f"rate applied to all {int(off[-1])} particles")
+    return done / t, t, desc
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     from oracle import oracle as O
-    w, x, q = workload(args.workload)
+    w, x, q, off = workload(args.workload, args.p)
+    sample = (lambda: oracle_sample(x, q, w)) if off is None else (lambda: oracle_sample_batched(x, q, off, w))
     for _ in range(args.warmup):
-        oracle_sample(x, q, w)
+        sample()
     vals = []
     wall = 0.0
     desc = ""
     for _ in range(args.steps):
-        v, t, desc = oracle_sample(x, q, w)
+        v, t, desc = sample()
         vals.append(v)
         wall += t
     value = statistics.mean(vals)
@@ -119,16 +148,32 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def accuracy(x, q, phi, grad, nsample=512, seed=77):
+def accuracy(x, q, phi, grad, nsample=512, seed=77, off=None):
     """Relative L2 error of phi and grad against the FP64 direct sum (oracle) on
-    nsample seeded targets."""
+    nsample seeded targets (for a batch: 128 targets in each of 4 systems, each
+    against its own system)."""
     from oracle import oracle as O
     from paper_1108_5815_gb300 import inputs
     import numpy as np
-    t = inputs.sample_indices(len(q), nsample, seed)
-    pd, gd = O.direct(x, q, targets=t)
-    e_phi = float(np.linalg.norm(phi[t] - pd) / np.linalg.norm(pd))
-    e_grad = float(np.linalg.norm(grad[t] - gd) / np.linalg.norm(gd))
+    if off is None:
+        t = inputs.sample_indices(len(q), nsample, seed)
+        pd, gd = O.direct(x, q, targets=t)
+        got_p, got_g = phi[t], grad[t]
+    else:
+        nsys = len(off) - 1
+        pds, gds, gps, ggs = [], [], [], []
+        for sy in (0, nsys // 3, 2 * nsys // 3, nsys - 1):
+            a, b = int(off[sy]), int(off[sy + 1])
+            t = inputs.sample_indices(b - a, 128, seed + sy)
+            p_, g_ = O.direct(x[a:b], q[a:b], targets=t)
+            pds.append(p_)
+            gds.append(g_)
+            gps.append(phi[a + t])
+            ggs.append(grad[a + t])
+        pd, gd, got_p, got_g = np.concatenate(pds), np.concatenate(gds), np.concatenate(gps), np.concatenate(ggs)
+        nsample = len(pd)
+    e_phi = float(np.linalg.norm(got_p - pd) / np.linalg.norm(pd))
+    e_grad = float(np.linalg.norm(got_g - gd) / np.linalg.norm(gd))
     return {"rel_l2_phi": e_phi, "rel_l2_grad": e_grad, "reference": "FP64 direct sum (oracle)",
             "targets": int(nsample)}
 
@@ -267,7 +312,7 @@ def main():
         dist.init_process_group("nccl", device_id=dev)
     build.build()
 
-    w, x, q = workload(args.workload)
+    w, x, q, off = workload(args.workload, args.p)
     n = w["n"]
     xd = torch.from_numpy(x).to(dev)
     qd = torch.from_numpy(q).to(dev)
@@ -276,9 +321,13 @@ def main():
     flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device=dev)  # 512 MB > L2
     kw = dict(max_depth=w["max_depth"], precision=args.precision)
 
-    def solve(stats=False):
-        return fmm.laplace3d(xd, qd, w["p"], w["theta"], w["ncrit"], stats=stats,
-                             out=(phi, grad), **kw)
+    def solve(stats=False, **over):
+        k2 = dict(kw, **over)
+        if off is None:
+            return fmm.laplace3d(xd, qd, w["p"], w["theta"], w["ncrit"], stats=stats,
+                                 out=(phi, grad), **k2)
+        return fmm.laplace3d_batched(xd, qd, off, w["p"], w["theta"], w["ncrit"], stats=stats,
+                                     out=(phi, grad), **k2)
 
     for _ in range(args.warmup):
         solve()
@@ -323,14 +372,28 @@ def main():
         ph = torch.empty(n, dtype=torch.float32).pin_memory().numpy()
         gh = torch.empty(n, 3, dtype=torch.float32).pin_memory().numpy()
         sp = stream.cuda_stream
+        xdt, qdt = torch.empty_like(xd), torch.empty_like(qd)
+
+        def host_solve():
+            if off is None:   # the C-ABI entry point with host buffers
+                fmm.laplace3d_host(xh, qh, w["p"], w["theta"], w["ncrit"], out=(ph, gh), stream=sp, **kw)
+                return
+            # batched: pinned host -> device, the batched call, device -> pinned host
+            xdt.copy_(torch.from_numpy(xh), non_blocking=True)
+            qdt.copy_(torch.from_numpy(qh), non_blocking=True)
+            pr, gr = fmm.laplace3d_batched(xdt, qdt, off, w["p"], w["theta"], w["ncrit"], **kw)
+            torch.from_numpy(ph).copy_(pr, non_blocking=True)
+            torch.from_numpy(gh).copy_(gr, non_blocking=True)
+            torch.cuda.synchronize()
+
         for _ in range(2):
-            fmm.laplace3d_host(xh, qh, w["p"], w["theta"], w["ncrit"], out=(ph, gh), stream=sp, **kw)
+            host_solve()
         t_e2e = 0.0
         for k in range(args.steps):
             flush.fill_(float(k))
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            fmm.laplace3d_host(xh, qh, w["p"], w["theta"], w["ncrit"], out=(ph, gh), stream=sp, **kw)
+            host_solve()
             t_e2e += time.perf_counter() - t0
         e2e_ms, _, e2e_value = replicas.aggregate(1e3 * t_e2e / args.steps, n, device=dev)
         e2e = {"value": e2e_value, "unit": "particles/s",
@@ -340,7 +403,7 @@ def main():
     # accuracy of this very solve against the FP64 direct sum on sampled targets
     acc = None
     if rank == 0:
-        acc = accuracy(x, q, phi.cpu().numpy(), grad.cpu().numpy())
+        acc = accuracy(x, q, phi.cpu().numpy(), grad.cpu().numpy(), off=off)
 
     # the other M2L precisions, timed the same way (value and accuracy)
     modes = {}
@@ -348,26 +411,47 @@ def main():
         for prec in ("fp32", "tf32x3", "bf16x3"):
             if prec == args.precision:
                 continue
-            kw2 = dict(max_depth=w["max_depth"], precision=prec)
             for _ in range(2):
-                fmm.laplace3d(xd, qd, w["p"], w["theta"], w["ncrit"], out=(phi, grad), **kw2)
+                solve(precision=prec)
             ms = []
             for k in range(args.steps):
                 flush.fill_(float(k))
                 a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 a.record(stream)
-                fmm.laplace3d(xd, qd, w["p"], w["theta"], w["ncrit"], out=(phi, grad), **kw2)
+                solve(precision=prec)
                 b.record(stream)
                 b.synchronize()
                 ms.append(a.elapsed_time(b))
             m = statistics.mean(ms)
             modes[prec] = {"value": n / (m / 1e3), "ms_per_step": m,
-                           "accuracy": accuracy(x, q, phi.cpu().numpy(), grad.cpu().numpy())}
+                           "accuracy": accuracy(x, q, phi.cpu().numpy(), grad.cpu().numpy(), off=off)}
+
+    # a batch against solving its systems one call at a time
+    loop = None
+    if rank == 0 and off is not None:
+        def solve_loop():
+            for sy in range(len(off) - 1):
+                a_, b_ = int(off[sy]), int(off[sy + 1])
+                fmm.laplace3d(xd[a_:b_], qd[a_:b_], w["p"], w["theta"], w["ncrit"],
+                              out=(phi[a_:b_], grad[a_:b_]), **kw)
+        solve_loop()
+        ms = []
+        for k in range(max(1, args.steps // 2)):
+            flush.fill_(float(k))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            solve_loop()
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        m = statistics.mean(ms)
+        loop = {"value": n / (m / 1e3), "ms_per_step": m, "speedup_of_batch": m / ms_per_step,
+                "what": "one fmm_laplace3d call per system, same workload"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         from oracle import oracle as O
-        v, _, desc = oracle_sample(x, q, w)
+        v, _, desc = oracle_sample(x, q, w) if off is None else oracle_sample_batched(x, q, off, w)
         cpu = {"value": v, "unit": "particles/s", "cores": O.num_threads(), "kind": "oracle",
                "sample": desc}
 
@@ -379,7 +463,7 @@ def main():
                 "config": config_of(w, args), "roofline": roof, "rooflines": rooflines,
                 "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(sum(s["n_launches"] for s in st_list)),
-                "accuracy": acc, "m2l_modes": modes,
+                "accuracy": acc, "m2l_modes": modes, "per_system_loop": loop,
                 "clocks": clocks, "phases_ms": phases,
                 "counts": {k: st0[k] for k in ("ncells", "nleaves", "depth", "n_p2p_pairs",
                                                "n_p2p_interactions", "n_m2l_pairs",

@@ -108,7 +108,7 @@ struct M2LUnit {
     int tile, e0, e1, pad;
 };
 bool m2l_tc_supported(int P2pad);
-size_t m2l_tc_smem(int P2pad, int &nstages);
+size_t m2l_tc_smem(int P2pad, bool bf16, int &nstages);
 void launch_m2l_tc(bool bf16, int nunits, const void *units, int ntiles, const int *unit_base,
                    const int *entry_class, const int *src, const int *tile_cells, const float *M,
                    const float *table, int P2pad, float *partial, float *L, int *flags,

@@ -11,16 +11,28 @@
 //   TF32x3: hi = a with the low 13 mantissa bits cleared, kind::tf32;
 //   BF16x3: hi = bf16(a), al = bf16(a - hi), kind::f16 with BF16 inputs.
 //
-// Roles inside a CTA (288 threads):
-//   warps 0-7  producers: gather 128 source rows and N matrix rows of one
-//              K-chunk (32 floats = 128 B per row), split them into hi/lo and
-//              store them in the canonical no-swizzle K-major layout (8-row x
-//              16-byte core matrices; LBO = 128 B along K, SBO = 1024 B along
-//              rows); after the last chunk they read D out of tensor memory.
-//   warp 8     allocates tensor memory; one lane issues the MMAs and commits.
+// The tensor core's accumulation rounds toward zero, so long accumulations in
+// tensor memory drift.  Following the error-corrected split of Ootomo & Yokota
+// (2022), the main products ah*bh and the correction products ah*bl + al*bh go
+// to two separate accumulators, each restarted at every offset-class block, and
+// the blocks are summed with round-to-nearest FP32 adds into a running sum held
+// in a third tensor-memory region (in the partial buffer when 3N columns do not fit).
+//
+// Roles inside a CTA (416 threads):
+//   warps 0-7   producers: gather 128 source rows and N matrix rows of one
+//               K-chunk of 32 floats, split them into hi/lo and store them in the
+//               canonical no-swizzle K-major layout (8-row x 16-byte core
+//               matrices; LBO = 128 B along K, SBO = 8 core matrices (TF32, 128 B
+//               rows) or 4 (BF16, 64 B rows) along rows).
+//   warp 8      allocates tensor memory; one lane issues the MMAs and commits.
+//   warps 9-12  accumulators, one per 32-lane quarter of tensor memory: after
+//               each class block they read the block's main and correction
+//               accumulators (two buffer pairs, alternating, when 5N columns fit)
+//               and add both into the running sum.
 // Stages are handed over through mbarriers (full: 256 producer arrivals;
-// empty/done: tcgen05.commit).  Every wait is bounded: on expiry the kernel
-// raises a flag and returns after releasing its tensor memory.
+// empty, acc_full: tcgen05.commit; acc_empty: 128 accumulator arrivals).  Every
+// wait is bounded: on expiry the kernel raises a flag and returns after
+// releasing its tensor memory.
 // A work unit is (tile, range of the tile's class blocks); its 128 x N result
 // goes to a partial buffer and k_m2l_reduce sums a tile's units in order.
 #include <cuda_bf16.h>
@@ -35,7 +47,9 @@ namespace fmm {
 namespace {
 
 constexpr int kProducerWarps = 8;
-constexpr int kThreads = (kProducerWarps + 1) * 32;
+constexpr int kAccWarps = 4;
+constexpr int kMmaWarp = kProducerWarps;
+constexpr int kThreads = (kProducerWarps + 1 + kAccWarps) * 32;
 constexpr int kKChunk = 32;  // source floats per row per stage (128 B)
 constexpr uint32_t kWaitLimit = 1u << 26;
 
@@ -81,13 +95,13 @@ __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence:
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
 // Shared-memory matrix descriptor: no swizzle, K-major, LBO = 128 B (next core
-// matrix along K), SBO = 1024 B (next 8-row group), descriptor version 1.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr)
+// matrix along K), SBO = `sbo` bytes (next 8-row group), descriptor version 1.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t sbo)
 {
     uint64_t d = 0;
     d |= (uint64_t)((addr >> 4) & 0x3FFFu);
     d |= (uint64_t)(128u >> 4) << 16;
-    d |= (uint64_t)(1024u >> 4) << 32;
+    d |= (uint64_t)(sbo >> 4) << 32;
     d |= (uint64_t)1 << 46;
     return d;
 }
@@ -123,6 +137,21 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar)
                  : "memory");
 }
 
+// 16 consecutive FP32 columns of this warp's 32 TMEM lanes (store side).
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16])
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+            taddr),
+        "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+        "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+        "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
+        "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+        "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
+        "r"(__float_as_uint(v[15]))
+        : "memory");
+}
+
 // 16 consecutive FP32 columns of this warp's 32 TMEM lanes.
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
 {
@@ -154,6 +183,8 @@ __device__ __forceinline__ void split_tf32(float4 a, uint4 &hi, uint4 &lo)
 }
 
 // hi/lo split of 8 floats into one 16-byte chunk each (BF16: 8 elements).
+// BF16 keeps 8 significant bits, so hi + lo carries about 16 of the 24: the
+// dropped lo*lo term and the remainder limit BF16x3 to about 1e-5 relative.
 __device__ __forceinline__ void split_bf16(float4 a, float4 b, uint4 &hi, uint4 &lo)
 {
     const float x[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
@@ -175,33 +206,41 @@ struct Unit {
 };
 
 // Stage layout (bytes): A_hi | A_lo | B_hi | B_lo, operand X with R rows of one
-// K-chunk occupying R * 128 bytes (16 core matrices of 8 rows per 128 rows).
-template <bool BF16, int NG>
+// 32-float K-chunk occupying R * RB bytes, RB = 128 (TF32) or 64 (BF16).
+template <bool BF16, int N>
 __global__ void __launch_bounds__(kThreads, 1)
     k_m2l_tc(const Unit *__restrict__ units, const int *__restrict__ entry_class,
              const int *__restrict__ src, const float *__restrict__ M, const float *__restrict__ table,
              int P2pad, int nstages, float *__restrict__ partial, int *__restrict__ flags)
 {
+    constexpr int NG = (128 + N + 63) / 64;        // groups of 8 rows per producer warp
+    constexpr bool SUM_TMEM = 3 * N <= 512;        // running sum in tensor memory
+    constexpr int NBUF = 5 * N <= 512 ? 2 : 1;     // main/correction buffer pairs
+    constexpr int BUF0 = SUM_TMEM ? N : 0;         // first buffer column
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // 1024-byte aligned base
     unsigned char *smem = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
-    const int N = P2pad;
-    // Floats of K consumed per stage: 32 (TF32, 128 B/row) or 64 (BF16, 128 B/row).
-    const int kstage = BF16 ? 64 : 32;
+    // 32 floats of K per stage: 128 B per row in TF32, 64 B per row in BF16.
+    constexpr int kstage = kKChunk;
+    constexpr uint32_t RB = BF16 ? 64u : 128u;   // bytes per row per stage
+    constexpr uint32_t SBO = 8u * RB;            // bytes per 8-row group
     const int nkc = (P2pad + kstage - 1) / kstage;
-    const uint32_t a_bytes = 128u * 128u, b_bytes = (uint32_t)N * 128u;
+    const uint32_t a_bytes = 128u * RB, b_bytes = (uint32_t)N * RB;
     const uint32_t stage_bytes = 2 * a_bytes + 2 * b_bytes;
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + nstages * stage_bytes);
     uint64_t *empty = full + nstages;
-    uint64_t *done = empty + nstages;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+    uint64_t *acc_full = empty + nstages;
+    uint64_t *acc_empty = acc_full + 2;
+    uint64_t *fin = acc_empty + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(fin + 1);
     __shared__ int s_abort;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const Unit U = units[blockIdx.x];
     const int nsteps = (U.e1 - U.e0) * nkc;
     uint32_t ncols = 32;
-    while (ncols < (uint32_t)N) ncols <<= 1;
+    while (ncols < (uint32_t)(BUF0 + 2 * N * NBUF)) ncols <<= 1;
+    const int nblocks = U.e1 - U.e0;
 
     if (threadIdx.x == 0) {
         s_abort = 0;
@@ -209,10 +248,14 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_init(&full[s], kProducerWarps * 32);
             mbar_init(&empty[s], 1);
         }
-        mbar_init(done, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], kAccWarps * 32);
+        }
+        mbar_init(fin, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == kProducerWarps) {
+    if (warp == kMmaWarp) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(tmem_slot)),
                      "r"(ncols)
@@ -227,12 +270,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (warp < kProducerWarps) {
         // ------------------------------------------------------------ producers
         // Thread (warp, lane) owns rows grp*8 + (lane & 7) for grp = warp + 8j, and the
-        // 16-byte chunks (lane >> 3) and (lane >> 3) + 4 of each.  Rows < 128 are
+        // 16-byte chunks (lane >> 3) + 4h of each (h < 2 in TF32, h = 0 in BF16).  Rows < 128 are
         // gathered multipoles (A), the rest rows of the class matrix (B).  The loads
         // of stage g+1 are issued before stage g is split and stored.
         const int groups = (128 + N) / 8;
         const int sub = lane & 7, cq = lane >> 3;
-        constexpr int V = BF16 ? 4 : 2;  // float4 per row and thread per stage
+        constexpr int V = 2;  // float4 per row and thread per stage
         float4 cur[NG][V], nxt[NG][V];
         int srow[2] = {0, 0};
         bool svalid[2] = {false, false};
@@ -260,16 +303,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                 } else if (valid) {
                     rowp = Tm + (int64_t)(grp * 8 + sub - 128) * P2pad;
                 }
+                if (BF16) {
+                    const int kk = k0 + cq * 8;
+                    buf[j][0] = valid ? *reinterpret_cast<const float4 *>(rowp + kk) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    buf[j][1] = valid ? *reinterpret_cast<const float4 *>(rowp + kk + 4) : make_float4(0.f, 0.f, 0.f, 0.f);
+                } else {
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int c = cq + 4 * h;
-                    if (BF16) {
-                        const int kk = k0 + c * 8;
-                        const bool ok = valid && kk < P2pad;
-                        buf[j][2 * h] = ok ? *reinterpret_cast<const float4 *>(rowp + kk) : make_float4(0.f, 0.f, 0.f, 0.f);
-                        buf[j][2 * h + 1] = ok ? *reinterpret_cast<const float4 *>(rowp + kk + 4) : make_float4(0.f, 0.f, 0.f, 0.f);
-                    } else {
-                        const int kk = k0 + c * 4;
+                    for (int h = 0; h < 2; ++h) {
+                        const int kk = k0 + (cq + 4 * h) * 4;
                         buf[j][h] = valid ? *reinterpret_cast<const float4 *>(rowp + kk) : make_float4(0.f, 0.f, 0.f, 0.f);
                     }
                 }
@@ -297,77 +338,127 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int row = grp * 8 + sub;
                 unsigned char *dst_hi, *dst_lo;
                 if (row < 128) {
-                    dst_hi = st + (row >> 3) * 1024 + (row & 7) * 16;
+                    dst_hi = st + (row >> 3) * SBO + (row & 7) * 16;
                     dst_lo = dst_hi + a_bytes;
                 } else {
                     const int r = row - 128;
-                    dst_hi = st + 2 * a_bytes + (r >> 3) * 1024 + (r & 7) * 16;
+                    dst_hi = st + 2 * a_bytes + (r >> 3) * SBO + (r & 7) * 16;
                     dst_lo = dst_hi + b_bytes;
                 }
+                uint4 hi, lo;
+                if (BF16) {
+                    split_bf16(cur[j][0], cur[j][1], hi, lo);
+                    *reinterpret_cast<uint4 *>(dst_hi + cq * 128) = hi;
+                    *reinterpret_cast<uint4 *>(dst_lo + cq * 128) = lo;
+                } else {
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int c = cq + 4 * h;
-                    uint4 hi, lo;
-                    if (BF16)
-                        split_bf16(cur[j][2 * h], cur[j][2 * h + 1], hi, lo);
-                    else
+                    for (int h = 0; h < 2; ++h) {
                         split_tf32(cur[j][h], hi, lo);
-                    *reinterpret_cast<uint4 *>(dst_hi + c * 128) = hi;
-                    *reinterpret_cast<uint4 *>(dst_lo + c * 128) = lo;
+                        *reinterpret_cast<uint4 *>(dst_hi + (cq + 4 * h) * 128) = hi;
+                        *reinterpret_cast<uint4 *>(dst_lo + (cq + 4 * h) * 128) = lo;
+                    }
                 }
             }
             fence_proxy_async();
             mbar_arrive(&full[s]);
         }
-        // ------------------------------------------------------------ epilogue
-        const bool ok = !s_abort && mbar_wait(done, 0);
-        if (!ok) atomicOr(&flags[kFlagTimeout], 1);
-        tc_fence_after();
-        const int quad = warp & 3, half = warp >> 2;
-        const int row = quad * 32 + lane;
-        const int cols = N / 2;
-        float *out = partial + ((int64_t)blockIdx.x * 128 + row) * P2pad + half * cols;
-        for (int c0 = 0; c0 < cols; c0 += 16) {
-            float v[16];
-            tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(half * cols + c0), v);
-            if (ok) {
-#pragma unroll
-                for (int i = 0; i < 16; i += 4)
-                    *reinterpret_cast<float4 *>(out + c0 + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
-            }
-        }
-    } else if (lane == 0) {
+    } else if (warp == kMmaWarp) {
         // ------------------------------------------------------------ MMA issuer
-        const uint32_t idesc = instr_desc(BF16 ? 1u : 2u, (uint32_t)N);
-        const int ksteps = 4;  // 4 MMAs of 32 bytes of K per 128-byte stage row
-        bool ok = true;
-        for (int g = 0; g < nsteps; ++g) {
-            const int s = g % nstages;
-            if (!mbar_wait(&full[s], (uint32_t)(g / nstages) & 1u)) {
+        if (lane == 0) {
+            const uint32_t idesc = instr_desc(BF16 ? 1u : 2u, (uint32_t)N);
+            constexpr int ksteps = (int)RB / 32;  // MMAs of 32 bytes of K per stage row
+            bool ok = true;
+            int g = 0;
+            for (int b = 0; b < nblocks && ok; ++b) {
+                const int buf = b % NBUF;
+                if (b >= NBUF && !mbar_wait(&acc_empty[buf], (uint32_t)((b / NBUF) - 1) & 1u)) {
+                    ok = false;
+                    break;
+                }
+                const uint32_t dmain = tmem + (uint32_t)(BUF0 + buf * 2 * N), dcorr = dmain + (uint32_t)N;
+                for (int kc = 0; kc < nkc; ++kc, ++g) {
+                    const int s = g % nstages;
+                    if (!mbar_wait(&full[s], (uint32_t)(g / nstages) & 1u)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t base = smem_u32(smem + (size_t)s * stage_bytes);
+                    const uint32_t ah = base, al = base + a_bytes, bh = base + 2 * a_bytes,
+                                   bl = bh + b_bytes;
+#pragma unroll
+                    for (int k = 0; k < ksteps; ++k) {
+                        const uint32_t off = (uint32_t)k * 256u;  // two core matrices along K
+                        const uint32_t acc0 = (kc > 0 || k > 0) ? 1u : 0u;
+                        mma<BF16>(dcorr, smem_desc(al + off, SBO), smem_desc(bh + off, SBO), idesc, acc0);
+                        mma<BF16>(dcorr, smem_desc(ah + off, SBO), smem_desc(bl + off, SBO), idesc, 1u);
+                        mma<BF16>(dmain, smem_desc(ah + off, SBO), smem_desc(bh + off, SBO), idesc, acc0);
+                    }
+                    mma_commit(&empty[s]);
+                }
+                if (ok) mma_commit(&acc_full[buf]);
+            }
+            if (!ok) {
                 atomicOr(&flags[kFlagTimeout], 1);
                 s_abort = 1;
-                ok = false;
+            }
+            // No MMA may still be in flight when the tensor memory is released.
+            mma_commit(fin);
+            if (!mbar_wait(fin, 0)) atomicOr(&flags[kFlagTimeout], 1);
+        }
+    } else {
+        // ------------------------------------------------------------ accumulators
+        // sum_b = sum_{b-1} + (main_b + corr_b), FP32 round-to-nearest, per element.
+        const int quad = warp & 3;
+        const int row = quad * 32 + lane;
+        const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
+        float *out = partial + ((int64_t)blockIdx.x * 128 + row) * P2pad;
+        for (int b = 0; b < nblocks; ++b) {
+            const int buf = b % NBUF;
+            // The warp leaves together: the tensor-memory loads below are warp-wide.
+            if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[buf], (uint32_t)(b / NBUF) & 1u))) {
+                atomicOr(&flags[kFlagTimeout], 1);
                 break;
             }
             tc_fence_after();
-            const uint32_t base = smem_u32(smem + (size_t)s * stage_bytes);
-            const uint32_t ah = base, al = base + a_bytes, bh = base + 2 * a_bytes,
-                           bl = bh + b_bytes;
+            const uint32_t dmain = tmem + lane_off + (uint32_t)(BUF0 + buf * 2 * N);
+            const bool last = b + 1 == nblocks;
+            for (int c0 = 0; c0 < N; c0 += 16) {
+                float vm[16], vc[16], vs[16];
+                tmem_ld16(dmain + (uint32_t)c0, vm);
+                tmem_ld16(dmain + (uint32_t)(N + c0), vc);
+                if (b > 0) {
+                    if (SUM_TMEM) {
+                        tmem_ld16(tmem + lane_off + (uint32_t)c0, vs);
+                    } else {
 #pragma unroll
-            for (int k = 0; k < ksteps; ++k) {
-                const uint32_t off = (uint32_t)k * 256u;  // two core matrices along K
-                const uint32_t acc0 = (g > 0 || k > 0) ? 1u : 0u;
-                mma<BF16>(tmem, smem_desc(al + off), smem_desc(bh + off), idesc, acc0);
-                mma<BF16>(tmem, smem_desc(ah + off), smem_desc(bl + off), idesc, 1u);
-                mma<BF16>(tmem, smem_desc(ah + off), smem_desc(bh + off), idesc, 1u);
+                        for (int i = 0; i < 16; i += 4) {
+                            const float4 t = *reinterpret_cast<const float4 *>(out + c0 + i);
+                            vs[i] = t.x, vs[i + 1] = t.y, vs[i + 2] = t.z, vs[i + 3] = t.w;
+                        }
+                    }
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) vs[i] += vm[i] + vc[i];
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) vs[i] = vm[i] + vc[i];
+                }
+                if (last || !SUM_TMEM) {
+#pragma unroll
+                    for (int i = 0; i < 16; i += 4)
+                        *reinterpret_cast<float4 *>(out + c0 + i) = make_float4(vs[i], vs[i + 1], vs[i + 2], vs[i + 3]);
+                } else {
+                    tmem_st16(tmem + lane_off + (uint32_t)c0, vs);
+                }
             }
-            mma_commit(&empty[s]);
+            if (SUM_TMEM && !last) asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            tc_fence_before();
+            mbar_arrive(&acc_empty[buf]);
         }
-        if (ok) mma_commit(done);  // units always hold at least one class block
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == kProducerWarps) {
+    if (warp == kMmaWarp) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols)
                      : "memory");
@@ -400,12 +491,13 @@ __global__ void k_m2l_reduce(const int *__restrict__ unit_base, const float *__r
 
 bool m2l_tc_supported(int P2pad) { return P2pad <= 256; }
 
-size_t m2l_tc_smem(int P2pad, int &nstages)
+size_t m2l_tc_smem(int P2pad, bool bf16, int &nstages)
 {
-    const size_t stage = 2 * 128 * 128 + 2 * (size_t)P2pad * 128;
-    nstages = (int)std::min<size_t>(4, (200 * 1024) / stage);
+    const size_t rb = bf16 ? 64 : 128;
+    const size_t stage = 2 * 128 * rb + 2 * (size_t)P2pad * rb;
+    nstages = (int)std::min<size_t>(bf16 ? 6 : 4, (200 * 1024) / stage);
     if (nstages < 2) nstages = 2;
-    return nstages * stage + 1024 /*alignment*/ + (2 * nstages + 1) * 8 + 16;
+    return nstages * stage + 1024 /*alignment*/ + (2 * nstages + 5) * 8 + 16;
 }
 
 void launch_m2l_tc(bool bf16, int nunits, const void *units, int ntiles, const int *unit_base,
@@ -414,27 +506,32 @@ void launch_m2l_tc(bool bf16, int nunits, const void *units, int ntiles, const i
                    cudaStream_t st)
 {
     int nstages = 0;
-    const size_t smem = m2l_tc_smem(P2pad, nstages);
+    const size_t smem = m2l_tc_smem(P2pad, bf16, nstages);
     if (nunits > 0) {
-        // groups of 8 rows per producer warp: ceil((128 + P2pad) / 64)
-        const int ng = (int)ceil_div(128 + P2pad, 64);
-#define FMM_M2L_TC_LAUNCH(B, G)                                                                     \
+#define FMM_M2L_TC_LAUNCH(B, NN)                                                                    \
     do {                                                                                           \
-        set_smem_limit_once((const void *)k_m2l_tc<B, G>, (int)smem);                               \
-        k_m2l_tc<B, G><<<nunits, kThreads, smem, st>>>(static_cast<const Unit *>(units), entry_class, \
-                                                       src, M, table, P2pad, nstages, partial, flags); \
+        set_smem_limit_once((const void *)k_m2l_tc<B, NN>, (int)smem);                              \
+        k_m2l_tc<B, NN><<<nunits, kThreads, smem, st>>>(static_cast<const Unit *>(units), entry_class, \
+                                                        src, M, table, P2pad, nstages, partial, flags); \
     } while (0)
-        if (bf16) {
-            if (ng <= 3) FMM_M2L_TC_LAUNCH(true, 3);
-            else if (ng == 4) FMM_M2L_TC_LAUNCH(true, 4);
-            else if (ng == 5) FMM_M2L_TC_LAUNCH(true, 5);
-            else FMM_M2L_TC_LAUNCH(true, 6);
-        } else {
-            if (ng <= 3) FMM_M2L_TC_LAUNCH(false, 3);
-            else if (ng == 4) FMM_M2L_TC_LAUNCH(false, 4);
-            else if (ng == 5) FMM_M2L_TC_LAUNCH(false, 5);
-            else FMM_M2L_TC_LAUNCH(false, 6);
-        }
+#define FMM_M2L_TC_BY_N(B)                                  \
+    do {                                                    \
+        switch (P2pad) {                                    \
+            case 32: FMM_M2L_TC_LAUNCH(B, 32); break;       \
+            case 64: FMM_M2L_TC_LAUNCH(B, 64); break;       \
+            case 96: FMM_M2L_TC_LAUNCH(B, 96); break;       \
+            case 128: FMM_M2L_TC_LAUNCH(B, 128); break;     \
+            case 160: FMM_M2L_TC_LAUNCH(B, 160); break;     \
+            case 192: FMM_M2L_TC_LAUNCH(B, 192); break;     \
+            case 224: FMM_M2L_TC_LAUNCH(B, 224); break;     \
+            default: FMM_M2L_TC_LAUNCH(B, 256); break;      \
+        }                                                   \
+    } while (0)
+        if (bf16)
+            FMM_M2L_TC_BY_N(true);
+        else
+            FMM_M2L_TC_BY_N(false);
+#undef FMM_M2L_TC_BY_N
 #undef FMM_M2L_TC_LAUNCH
         FMM_LAUNCH_CHECK();
     }

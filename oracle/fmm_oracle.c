@@ -39,6 +39,17 @@
  *   R5 expansion centres are the geometric cell centres; truncation is n <= p
  *      for both multipole and local expansions.
  *   R6 coincident pairs (r = 0) contribute nothing.
+ *   R9 hybrid selection (section "A new hybrid treecode-FMM with auto-tuning":
+ *      the interaction type of a far pair is chosen during the traversal to
+ *      minimise the cost, and particle-particle interactions may be taken above
+ *      the leaf level): a pair accepted by the MAC becomes cell-cell or
+ *      particle-particle by a table sel[b(n_t) * 128 + b(n_s)] (0 = M2L,
+ *      1 = P2P) over the particle counts of the two cells, with the count
+ *      bucket b(n) = n - 1 for n < 4, else 3 + 4(e - 2) + bits e-1..e-2 of n
+ *      below its leading bit (e = floor(log2 n)).  The table is an input: how it
+ *      was obtained (pre-timed kernels, a learned cost model) does not enter the
+ *      traversal.  A P2P pair may have non-leaf cells; it acts on all particles
+ *      of both.
  *
  * Harmonics (signed m, Condon-Shortley P_n^m):
  *   R_n^m(x) = r^n P_n^m(cos t) e^{i m f} / (n+m)!      (regular)
@@ -76,6 +87,7 @@ typedef double complex cplx;
 
 #define ORC_KBITS 21
 #define ORC_KMAX ((1LL << ORC_KBITS) - 1)
+#define ORC_SEL_NB 128
 
 static inline int hidx(int n, int m) { return n * n + n + m; }
 static inline int nterms(int p) { return (p + 1) * (p + 1); }
@@ -357,6 +369,7 @@ typedef struct {
     int64_t N;
     int p, ncrit, max_depth, leaf_first;
     double theta;
+    const unsigned char *sel; /* hybrid selection table (R9), NULL = plain FMM */
     double lo[3], side;
     double *x, *q;       /* sorted order */
     uint64_t *key;       /* sorted keys */
@@ -494,6 +507,27 @@ typedef struct {
 
 static int is_leaf(const orc_fmm *f, int64_t c) { return f->nchild[c] == 0; }
 
+/* Count bucket of reading R9. */
+int orc_count_bucket(int64_t n)
+{
+    int e = 0;
+    while ((n >> (e + 1)) > 0)
+        ++e;
+    if (e < 2)
+        return (int)(n - 1);
+    return 3 + 4 * (e - 2) + (int)((n >> (e - 2)) & 3);
+}
+
+/* Interaction type of an accepted pair (R9): 1 = particle-particle. */
+static int choose_p2p(const orc_fmm *f, int64_t T, int64_t S)
+{
+    if (!f->sel)
+        return 0;
+    int bt = orc_count_bucket(f->end[T] - f->begin[T]);
+    int bs = orc_count_bucket(f->end[S] - f->begin[S]);
+    return f->sel[bt * ORC_SEL_NB + bs] != 0;
+}
+
 /* interact(T,S) of reading R4. */
 static void interact(orc_fmm *f, pairstack *st, int64_t T, int64_t S)
 {
@@ -506,9 +540,12 @@ static void interact(orc_fmm *f, pairstack *st, int64_t T, int64_t S)
             push_pair(&st->t, &st->s, &st->n, &st->cap, T, S);
         return;
     }
-    if (mac_accept(f, T, S))
-        push_pair(&f->m2l_t, &f->m2l_s, &f->nm2l, &f->cap_m2l, T, S);
-    else if (is_leaf(f, T) && is_leaf(f, S))
+    if (mac_accept(f, T, S)) {
+        if (choose_p2p(f, T, S))
+            push_pair(&f->p2p_t, &f->p2p_s, &f->np2p, &f->cap_p2p, T, S);
+        else
+            push_pair(&f->m2l_t, &f->m2l_s, &f->nm2l, &f->cap_m2l, T, S);
+    } else if (is_leaf(f, T) && is_leaf(f, S))
         push_pair(&f->p2p_t, &f->p2p_s, &f->np2p, &f->cap_p2p, T, S);
     else
         push_pair(&st->t, &st->s, &st->n, &st->cap, T, S);
@@ -545,9 +582,11 @@ static void traverse(orc_fmm *f)
 /* Build keys, sorted order, tree and interaction lists.  Returns 0 on success,
  * 1 for a non-finite coordinate. */
 orc_fmm *orc_fmm_create(int64_t N, const double *xyz, const double *q, int p, double theta,
-                        int ncrit, int max_depth, int leaf_first, int *status)
+                        int ncrit, int max_depth, int leaf_first, const unsigned char *sel,
+                        int *status)
 {
     orc_fmm *f = calloc(1, sizeof(orc_fmm));
+    f->sel = sel; /* only read during the traversal below */
     f->N = N;
     f->p = p;
     f->theta = theta;
@@ -588,6 +627,7 @@ orc_fmm *orc_fmm_create(int64_t N, const double *xyz, const double *q, int p, do
     f->parent[root] = -1;
     build_cell(f, root);
     traverse(f);
+    f->sel = NULL;
     *status = 0;
     return f;
 }
@@ -644,26 +684,30 @@ static void csr_by_target(int64_t ncells, int64_t npairs, const int64_t *t, int6
     *idx_out = idx;
 }
 
-/* Near field for the particles of target leaf T: direct sum over its P2P list. */
+/* Near field for the particles of target leaf T: direct sum over the P2P lists
+ * of T and of its ancestors (a P2P pair of reading R9 may have a non-leaf target,
+ * and then acts on every particle below it). */
 static void p2p_leaf(const orc_fmm *f, int64_t T, const int64_t *off, const int64_t *idx,
                      double *phi, double *grad, int64_t obase)
 {
     for (int64_t i = f->begin[T]; i < f->end[T]; ++i) {
         double ph = 0, gx = 0, gy = 0, gz = 0;
-        for (int64_t k = off[T]; k < off[T + 1]; ++k) {
-            int64_t S = f->p2p_s[idx[k]];
-            for (int64_t j = f->begin[S]; j < f->end[S]; ++j) {
-                double dx = f->x[3 * i] - f->x[3 * j], dy = f->x[3 * i + 1] - f->x[3 * j + 1],
-                       dz = f->x[3 * i + 2] - f->x[3 * j + 2];
-                double r2 = dx * dx + dy * dy + dz * dz;
-                if (r2 == 0.0)
-                    continue;
-                double r = sqrt(r2);
-                double qr3 = f->q[j] / (r2 * r);
-                ph += f->q[j] / r;
-                gx -= qr3 * dx;
-                gy -= qr3 * dy;
-                gz -= qr3 * dz;
+        for (int64_t A = T; A >= 0; A = f->parent[A]) {
+            for (int64_t k = off[A]; k < off[A + 1]; ++k) {
+                int64_t S = f->p2p_s[idx[k]];
+                for (int64_t j = f->begin[S]; j < f->end[S]; ++j) {
+                    double dx = f->x[3 * i] - f->x[3 * j], dy = f->x[3 * i + 1] - f->x[3 * j + 1],
+                           dz = f->x[3 * i + 2] - f->x[3 * j + 2];
+                    double r2 = dx * dx + dy * dy + dz * dz;
+                    if (r2 == 0.0)
+                        continue;
+                    double r = sqrt(r2);
+                    double qr3 = f->q[j] / (r2 * r);
+                    ph += f->q[j] / r;
+                    gx -= qr3 * dx;
+                    gy -= qr3 * dy;
+                    gz -= qr3 * dz;
+                }
             }
         }
         phi[i - obase] += ph;

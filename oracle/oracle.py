@@ -50,7 +50,9 @@ def lib():
             L.orc_fmm_create.restype = ctypes.c_void_p
             L.orc_fmm_create.argtypes = [ctypes.c_int64, _D, _D, ctypes.c_int, ctypes.c_double,
                                          ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                         ctypes.POINTER(ctypes.c_int)]
+                                         ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]
+            L.orc_count_bucket.restype = ctypes.c_int
+            L.orc_count_bucket.argtypes = [ctypes.c_int64]
             for name in ("orc_fmm_upward", "orc_fmm_evaluate", "orc_fmm_destroy"):
                 getattr(L, name).argtypes = [ctypes.c_void_p]
             L.orc_fmm_evaluate_leaves.argtypes = [ctypes.c_void_p, ctypes.c_int64, _I64, _D, _D, _I64]
@@ -201,17 +203,31 @@ def m2p(c, p, M, x):
 
 # ---------------------------------------------------------------- full FMM
 
+SEL_NB = 128
+
+
+def count_bucket(n):
+    """Count bucket of the hybrid selection table (reading R9)."""
+    return int(lib().orc_count_bucket(int(n)))
+
+
 class Fmm:
     """Oracle FMM: keys, tree and interaction lists are built on construction;
     ``evaluate()`` runs the upward and downward passes."""
 
-    def __init__(self, xyz, q, p, theta, ncrit, max_depth=21, leaf_first=False):
+    def __init__(self, xyz, q, p, theta, ncrit, max_depth=21, leaf_first=False, sel=None):
+        """``sel``: optional hybrid selection table (reading R9), uint8 [128, 128]
+        indexed by the count buckets of (target, source); 1 = P2P for a MAC-accepted pair."""
         self.xyz = _f64(xyz, (-1, 3))
         self.q = _f64(q, (-1,))
         self.p = p
         st = ctypes.c_int(0)
+        selp = None
+        if sel is not None:
+            sel = np.ascontiguousarray(np.asarray(sel, dtype=np.uint8).reshape(SEL_NB, SEL_NB))
+            selp = sel.ctypes.data
         self._h = lib().orc_fmm_create(self.xyz.shape[0], _d(self.xyz), _d(self.q), p, theta,
-                                       ncrit, max_depth, int(leaf_first), ctypes.byref(st))
+                                       ncrit, max_depth, int(leaf_first), selp, ctypes.byref(st))
         if st.value != 0 or not self._h:
             self._h = None
             raise ValueError("non-finite coordinate")

@@ -61,11 +61,32 @@ enum {
     FMM_PREC_BF16X3 = 2  /* tensor cores, operands split hi+lo in BF16, FP32 accumulate */
 };
 
+/* Interaction type of the pairs the MAC accepts (section "A new hybrid
+ * treecode-FMM with auto-tuning": the type is chosen during the traversal to
+ * minimise the cost, and particle-particle interactions may be taken above the
+ * leaf level).  Every mode is exact in the sense that a pair not taken as M2L is
+ * taken as P2P, so the far-field error can only shrink.
+ * The choice is a table sel[b(n_t) * FMM_SELECT_NB + b(n_s)] (0 = M2L, 1 = P2P)
+ * over the particle counts n_t, n_s of the target and source cells, with the
+ * count bucket b(n) = n - 1 for n < 4, else 3 + 4(e - 2) + ((n >> (e - 2)) & 3),
+ * e = floor(log2 n) (four buckets per octave). */
+enum {
+    FMM_SELECT_PLAIN = 0,    /* M2L for every accepted pair: the plain FMM */
+    FMM_SELECT_AUTOTUNE = 1, /* table from kernels timed on artificial cells (kernel
+                                pre-calculation), measured once per device, p and precision */
+    FMM_SELECT_LEARNED = 2,  /* table from the learned cost model (fmm_cost_model_*) */
+    FMM_SELECT_TABLE = 3     /* the caller's table in fmm_options.select_table */
+};
+#define FMM_SELECT_NB 128
+
 typedef struct {
     int max_depth;      /* deepest tree level, 1..21 (0 selects 21) */
     int precision_mode; /* FMM_PREC_* */
-    int select_mode;    /* 0 = plain FMM (cell-cell far field everywhere) */
+    int select_mode;    /* FMM_SELECT_* */
     int deterministic;  /* 1 = bitwise-reproducible results (the only mode implemented) */
+    /* FMM_SELECT_TABLE: HOST uint8[FMM_SELECT_NB][FMM_SELECT_NB], read during the
+     * call only; ignored by the other modes. */
+    const unsigned char *select_table;
 } fmm_options;
 
 typedef struct {
@@ -78,7 +99,7 @@ typedef struct {
     float ms_tree, ms_upward, ms_traverse, ms_m2l, ms_downward, ms_p2p, ms_total;
 } fmm_stats;
 
-/* Fills *opt with the defaults (max_depth 21, FP32 M2L, plain, deterministic). */
+/* Fills *opt with the defaults (max_depth 21, FP32 M2L, plain FMM, deterministic). */
 void fmm_default_options(fmm_options *opt);
 
 /* The FMM solve.  Arguments must satisfy N >= 1, 1 <= p <= 20, 0 < theta < 1,
@@ -127,10 +148,14 @@ fmm_status fmm_direct(const float *xyz, const float *q, int64_t N, float *phi, f
  *   FMM_EXPORT_KEYS       uint64[N] Morton keys in sorted order
  *   FMM_EXPORT_ORDER      int32[N]  original index of each sorted position
  *   FMM_EXPORT_CELLS      int64[ncells][6]: level, key prefix, begin, end, parent, nchild
- *   FMM_EXPORT_P2P        int32[n][2]: target leaf, source leaf
+ *   FMM_EXPORT_P2P        int32[n][2]: target leaf, source cell (a leaf in the plain
+ *                         FMM; with a selection table a P2P pair chosen above the
+ *                         leaf level appears once per target leaf below it)
  *   FMM_EXPORT_M2L        int32[n][3]: target cell, source cell, offset class
  *   FMM_EXPORT_MULTIPOLE  float[ncells][P2pad] unit-scaled multipoles (see below)
  *   FMM_EXPORT_LOCAL      float[ncells][P2pad] unit-scaled local expansions
+ *   FMM_EXPORT_SELECT     uint8[FMM_SELECT_NB][FMM_SELECT_NB] selection table the
+ *                         solve used (all zero for the plain FMM)
  * Expansion rows hold, for n = 0..p, Re c_n^0 then (Re c_n^m, Im c_n^m) for
  * m = 1..n ((p+1)^2 values, zero-padded to P2pad = a multiple of 32), scaled
  * by s^-n (multipoles) or s^(n+1) (locals) with s the cell side. */
@@ -142,7 +167,8 @@ enum {
     FMM_EXPORT_P2P = 4,
     FMM_EXPORT_M2L = 5,
     FMM_EXPORT_MULTIPOLE = 6,
-    FMM_EXPORT_LOCAL = 7
+    FMM_EXPORT_LOCAL = 7,
+    FMM_EXPORT_SELECT = 8
 };
 fmm_status fmm_export(int what, void *dst, int64_t capacity, int64_t *needed);
 

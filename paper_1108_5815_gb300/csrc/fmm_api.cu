@@ -78,6 +78,7 @@ struct Workspace {
     int64_t nm2l = 0, np2p = 0;
     int nsys = 1;
     int64_t cap_m2l = 0, cap_p2p = 0, cap_def = 0;  // list capacities that sufficed before
+    std::vector<uint8_t> sel_host;                   // selection table of the last solve
     // The solve runs on two library streams, both non-blocking (a kernel on the
     // legacy default stream would keep the other stream's work from overlapping):
     // main_stream for the tree, traversal and P2P, far_stream (high priority) for
@@ -275,7 +276,12 @@ void validate(const void *xyz, const void *q, int64_t N, int p, double theta, in
     if (o.max_depth < 0 || o.max_depth > kMaxLevel) throw Error{FMM_ERR_ARG, "max_depth must be in [0, 21]"};
     if (o.precision_mode < FMM_PREC_FP32 || o.precision_mode > FMM_PREC_BF16X3)
         throw Error{FMM_ERR_ARG, "precision_mode must be FMM_PREC_FP32, _TF32X3 or _BF16X3"};
-    if (o.select_mode != 0) throw Error{FMM_ERR_ARG, "select_mode: only the plain FMM (0) is available"};
+    if (o.select_mode < FMM_SELECT_PLAIN || o.select_mode > FMM_SELECT_TABLE)
+        throw Error{FMM_ERR_ARG, "select_mode must be one of FMM_SELECT_*"};
+    if (o.select_mode == FMM_SELECT_TABLE && !o.select_table)
+        throw Error{FMM_ERR_ARG, "FMM_SELECT_TABLE needs fmm_options.select_table"};
+    if (o.select_mode == FMM_SELECT_AUTOTUNE || o.select_mode == FMM_SELECT_LEARNED)
+        throw Error{FMM_ERR_ARG, "select_mode: pre-timed and learned tables are not available yet"};
 }
 
 // The solve on device buffers; the caller holds ws.mu.
@@ -436,6 +442,16 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
     int64_t def_cap = std::max<int64_t>(ws.cap_def, std::max<int64_t>(4096 + nsys, (int64_t)ncells * 96));
     uint64_t *hash_keys = need<uint64_t>(ws, "hash_keys", kHashCap, st);
     unsigned long long *tcount = need<unsigned long long>(ws, "trav_counters", 3, st);
+    // hybrid selection table (the flagged deferred sources need cell ids below 2^30)
+    const uint8_t *d_sel = nullptr;
+    ws.sel_host.assign((size_t)kSelNB * kSelNB, 0);
+    if (o.select_mode != FMM_SELECT_PLAIN) {
+        if (ncells >= (1 << 30)) throw Error{FMM_ERR_CAPACITY, "selection tables need fewer than 2^30 cells"};
+        std::memcpy(ws.sel_host.data(), o.select_table, ws.sel_host.size());
+        uint8_t *dsel = need<uint8_t>(ws, "select_table", ws.sel_host.size(), st);
+        upload(ws, dsel, ws.sel_host.data(), ws.sel_host.size(), st);
+        d_sel = dsel;
+    }
     int64_t m2l_total = 0, p2p_total = 0;
     for (int attempt = 0;; ++attempt) {
         L.m2l_src = need<int>(ws, "m2l_src", m2l_cap, st);
@@ -450,8 +466,8 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
         for (int l = 1; l <= depth; ++l) {
             const int a = lstart[l], b = lstart[l + 1];
             const unsigned blocks = (unsigned)ceil_div((int64_t)(b - a) * 32, 128);
-            k_traverse_level<<<blocks, 128, 0, st>>>(c, L, a, b, theta2, (float)theta2, tcount, m2l_cap,
-                                                     p2p_cap, def_cap, hash_keys, flags);
+            k_traverse_level<<<blocks, 128, 0, st>>>(c, L, a, b, theta2, (float)theta2, d_sel, tcount,
+                                                     m2l_cap, p2p_cap, def_cap, hash_keys, flags);
             FMM_LAUNCH_CHECK();
         }
         unsigned long long tot[3];
@@ -772,8 +788,9 @@ void fmm_default_options(fmm_options *opt)
     if (!opt) return;
     opt->max_depth = 0;
     opt->precision_mode = FMM_PREC_FP32;
-    opt->select_mode = 0;
+    opt->select_mode = FMM_SELECT_PLAIN;
     opt->deterministic = 1;
+    opt->select_table = nullptr;
 }
 
 fmm_status fmm_laplace3d_ex(const float *xyz, const float *q, int64_t N, int p, double theta,
@@ -868,6 +885,7 @@ fmm_status fmm_export(int what, void *dst, int64_t capacity, int64_t *needed)
             case FMM_EXPORT_M2L: bytes = ws.nm2l * 3 * sizeof(int32_t); break;
             case FMM_EXPORT_MULTIPOLE:
             case FMM_EXPORT_LOCAL: bytes = (int64_t)ws.ncells * ws.P2pad * sizeof(float); break;
+            case FMM_EXPORT_SELECT: bytes = (int64_t)ws.sel_host.size(); break;
             default: throw Error{FMM_ERR_ARG, "unknown export kind"};
         }
         if (needed) *needed = bytes;
@@ -882,6 +900,7 @@ fmm_status fmm_export(int what, void *dst, int64_t capacity, int64_t *needed)
             case FMM_EXPORT_ORDER: d2h(dst, get<uint32_t>(ws, "idx"), bytes); break;
             case FMM_EXPORT_MULTIPOLE: d2h(dst, get<float>(ws, "M"), bytes); break;
             case FMM_EXPORT_LOCAL: d2h(dst, get<float>(ws, "L"), bytes); break;
+            case FMM_EXPORT_SELECT: std::memcpy(dst, ws.sel_host.data(), bytes); break;
             case FMM_EXPORT_CELLS: {
                 const int n = ws.ncells;
                 std::vector<int> lv(n), b(n), e(n), par(n), nch(n);

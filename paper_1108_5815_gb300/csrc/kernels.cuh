@@ -65,9 +65,11 @@ __global__ void k_leaf_flags(CellArrays c, int ncells, int *flag);
 __global__ void k_leaf_compact(CellArrays c, int ncells, const int *ex, int *leaves);
 
 // traverse.cu
+constexpr int kSelNB = 128;  // count buckets of the hybrid selection table
 __global__ void k_traverse_level(CellArrays c, ListArrays L, int a, int b, double theta2,
-                                 float theta2f, unsigned long long *counters, int64_t cap_m,
-                                 int64_t cap_p, int64_t cap_d, uint64_t *hash_keys, int *flags);
+                                 float theta2f, const uint8_t *sel, unsigned long long *counters,
+                                 int64_t cap_m, int64_t cap_p, int64_t cap_d, uint64_t *hash_keys,
+                                 int *flags);
 __global__ void k_hash_flags(const uint64_t *hash_keys, int *flag);
 __global__ void k_hash_compact(const uint64_t *hash_keys, const int *ex, uint64_t *ukeys,
                                uint32_t *uslot);

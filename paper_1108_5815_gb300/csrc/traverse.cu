@@ -9,9 +9,13 @@
 // pending with the decision "split the target" (the paper: "target cells
 // inherit a unique stack of source cells from their parents"), and resolves
 // each inherited source S by
-//     interact(T,S): MAC -> M2L;  else T,S leaves -> P2P;
+//     interact(T,S): MAC -> M2L (or P2P, by the hybrid selection table);
+//                    else T,S leaves -> P2P;
 //                    else split S (S larger, or T a leaf) and interact with
 //                    its children, or defer S to T's children.
+// A P2P pair (T,S) chosen by the selection table above the leaf level is handed
+// down as a flagged deferred source until it reaches T's leaves, so every P2P
+// list stays a per-leaf list (its sources may be cells of any level).
 // One warp handles one target; lanes take inherited sources in order and
 // resolve each with a small depth-first stack.  Each target's outputs are
 // written contiguously in a deterministic order (count, reserve with one atomic
@@ -28,12 +32,21 @@ namespace fmm {
 namespace {
 
 constexpr int kStack = 192;
+constexpr int kP2PFlag = 1 << 30;  // deferred source that is a chosen P2P pair
 
 struct TargetInfo {
     int t, level;
     bool leaf;
     int C[3], h;  // centre in units of side/2^22 and half side (< 2^23)
+    int bt;       // count bucket of the target (hybrid selection)
 };
+
+// Count bucket of the selection table: n - 1 below 4, then four per octave.
+__device__ __forceinline__ int count_bucket(int n)
+{
+    const int e = 31 - __clz(n);
+    return e < 2 ? n - 1 : 3 + 4 * (e - 2) + ((n >> (e - 2)) & 3);
+}
 
 __device__ __forceinline__ void cell_geom32(int level, uint64_t prefix, int C[3], int &h)
 {
@@ -108,12 +121,27 @@ struct Counts {
 };
 
 // Resolves one inherited source S0 for target T.  WRITE = false only counts.
+// sel: hybrid selection table (nullptr = plain FMM).
 template <bool WRITE>
 __device__ Counts resolve(const TargetInfo &T, int S0, const CellArrays &c, const ListArrays &L,
                           double theta2, float theta2f, int64_t m_pos, int64_t p_pos, int d_pos,
-                          uint64_t *hash_keys, int *flags)
+                          const uint8_t *__restrict__ sel, uint64_t *hash_keys, int *flags)
 {
     Counts n = {0, 0, 0};
+    if (S0 & kP2PFlag) {
+        // a P2P pair chosen at an ancestor of T: record at a leaf, else pass down
+        if (T.leaf) {
+            if (WRITE) {
+                L.p2p_src[p_pos] = S0 & ~kP2PFlag;
+                L.p2p_tgt[p_pos] = T.t;
+            }
+            n.p = 1;
+        } else {
+            if (WRITE) L.def_src[d_pos] = S0;
+            n.d = 1;
+        }
+        return n;
+    }
     int stk[kStack];
     int sp = 0;
     stk[sp++] = S0;
@@ -124,12 +152,25 @@ __device__ Counts resolve(const TargetInfo &T, int S0, const CellArrays &c, cons
         int Cs[3], hs;
         cell_geom32(ls, c.prefix[S], Cs, hs);
         if (mac_accept(T, Cs, hs, theta2, theta2f)) {
-            if (WRITE) {
-                L.m2l_src[m_pos + n.m] = S;
-                L.m2l_tgt[m_pos + n.m] = T.t;
-                L.m2l_slot[m_pos + n.m] = hash_insert(hash_keys, class_key(T, ls, Cs, flags), flags);
+            if (sel && __ldg(&sel[T.bt * kSelNB + count_bucket(c.end[S] - c.begin[S])])) {
+                if (T.leaf) {
+                    if (WRITE) {
+                        L.p2p_src[p_pos + n.p] = S;
+                        L.p2p_tgt[p_pos + n.p] = T.t;
+                    }
+                    ++n.p;
+                } else {
+                    if (WRITE) L.def_src[d_pos + n.d] = S | kP2PFlag;
+                    ++n.d;
+                }
+            } else {
+                if (WRITE) {
+                    L.m2l_src[m_pos + n.m] = S;
+                    L.m2l_tgt[m_pos + n.m] = T.t;
+                    L.m2l_slot[m_pos + n.m] = hash_insert(hash_keys, class_key(T, ls, Cs, flags), flags);
+                }
+                ++n.m;
             }
-            ++n.m;
         } else if (T.leaf && nchS == 0) {
             if (WRITE) {
                 L.p2p_src[p_pos + n.p] = S;
@@ -158,6 +199,7 @@ __device__ __forceinline__ TargetInfo load_target(const CellArrays &c, int t)
     T.level = c.level[t];
     T.leaf = c.nchild[t] == 0;
     cell_geom32(T.level, c.prefix[t], T.C, T.h);
+    T.bt = count_bucket(c.end[t] - c.begin[t]);
     return T;
 }
 
@@ -190,8 +232,9 @@ __device__ __forceinline__ int warp_excl(int v)
 // larger buffers.
 __global__ void __launch_bounds__(128)
     k_traverse_level(CellArrays c, ListArrays L, int a, int b, double theta2, float theta2f,
-                     unsigned long long *__restrict__ counters, int64_t cap_m, int64_t cap_p,
-                     int64_t cap_d, uint64_t *__restrict__ hash_keys, int *__restrict__ flags)
+                     const uint8_t *__restrict__ sel, unsigned long long *__restrict__ counters,
+                     int64_t cap_m, int64_t cap_p, int64_t cap_d, uint64_t *__restrict__ hash_keys,
+                     int *__restrict__ flags)
 {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -202,7 +245,7 @@ __global__ void __launch_bounds__(128)
     const int i0 = L.def_off[P], ni = L.def_cnt[P];
     int m = 0, p = 0, d = 0;
     for (int k = lane; k < ni; k += 32) {
-        const Counts n = resolve<false>(T, L.def_src[i0 + k], c, L, theta2, theta2f, 0, 0, 0, nullptr, flags);
+        const Counts n = resolve<false>(T, L.def_src[i0 + k], c, L, theta2, theta2f, 0, 0, 0, sel, nullptr, flags);
         m += n.m;
         p += n.p;
         d += n.d;
@@ -235,11 +278,11 @@ __global__ void __launch_bounds__(128)
         const int k = k0 + lane;
         const int S0 = k < ni ? L.def_src[i0 + k] : -1;
         Counts n = {0, 0, 0};
-        if (S0 >= 0) n = resolve<false>(T, S0, c, L, theta2, theta2f, 0, 0, 0, nullptr, flags);
+        if (S0 >= 0) n = resolve<false>(T, S0, c, L, theta2, theta2f, 0, 0, 0, sel, nullptr, flags);
         const int em = warp_excl(n.m), ep = warp_excl(n.p), ed = warp_excl(n.d);
         if (S0 >= 0)
             resolve<true>(T, S0, c, L, theta2, theta2f, (int64_t)om + rm + em, (int64_t)op + rp + ep,
-                          (int)od + rd + ed, hash_keys, flags);
+                          (int)od + rd + ed, sel, hash_keys, flags);
         rm += warp_sum(n.m);
         rp += warp_sum(n.p);
         rd += warp_sum(n.d);

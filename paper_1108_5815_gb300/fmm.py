@@ -19,8 +19,10 @@ LIB_PATH = os.path.join(_HERE, "_build", "libfmm.so")
 FMM_OK, FMM_ERR_ARG, FMM_ERR_NONFINITE, FMM_ERR_CAPACITY, FMM_ERR_CUDA, FMM_ERR_TIMEOUT, \
     FMM_ERR_NOMEM = range(7)
 PRECISION = {"fp32": 0, "tf32x3": 1, "bf16x3": 2}
+SELECT = {"plain": 0, "autotune": 1, "learned": 2, "table": 3}
+SELECT_NB = 128
 EXPORT = {"box": 0, "keys": 1, "order": 2, "cells": 3, "p2p": 4, "m2l": 5, "multipole": 6,
-          "local": 7}
+          "local": 7, "select": 8}
 
 # every symbol the header declares
 ABI_SYMBOLS = ("fmm_default_options", "fmm_laplace3d", "fmm_laplace3d_ex", "fmm_laplace3d_host",
@@ -36,7 +38,8 @@ class FmmError(RuntimeError):
 
 class Options(ctypes.Structure):
     _fields_ = [("max_depth", ctypes.c_int), ("precision_mode", ctypes.c_int),
-                ("select_mode", ctypes.c_int), ("deterministic", ctypes.c_int)]
+                ("select_mode", ctypes.c_int), ("deterministic", ctypes.c_int),
+                ("select_table", ctypes.c_void_p)]
 
 
 class Stats(ctypes.Structure):
@@ -97,12 +100,23 @@ def _check(status: int):
         raise FmmError(status, last_error())
 
 
-def _options(max_depth=0, precision="fp32", select_mode=0):
+def _options(max_depth=0, precision="fp32", select="plain"):
+    """fmm_options for the call.  ``select`` is "plain", "autotune", "learned" or a
+    uint8 [128, 128] selection table; the returned options keep the table alive."""
     o = Options()
     load().fmm_default_options(ctypes.byref(o))
     o.max_depth = max_depth
     o.precision_mode = PRECISION[precision]
-    o.select_mode = select_mode
+    if isinstance(select, str):
+        o.select_mode = SELECT[select]
+        o._table = None
+    else:
+        t = np.ascontiguousarray(np.asarray(select, dtype=np.uint8))
+        if t.shape != (SELECT_NB, SELECT_NB):
+            raise FmmError(FMM_ERR_ARG, f"selection table must be uint8 [{SELECT_NB}, {SELECT_NB}]")
+        o.select_mode = SELECT["table"]
+        o.select_table = t.ctypes.data
+        o._table = t
     return o
 
 
@@ -122,7 +136,7 @@ def _dev_f32(t, shape, name):
 
 
 def laplace3d(xyz, q, p: int, theta: float, ncrit: int, *, max_depth: int = 0,
-              precision: str = "fp32", stats: bool = False, out=None):
+              precision: str = "fp32", select="plain", stats: bool = False, out=None):
     """FMM potential and gradient for CUDA float32 xyz[N,3], q[N].
 
     Returns (phi[N], grad[N,3]) as CUDA tensors (and a stats dict if ``stats``)."""
@@ -136,7 +150,7 @@ def laplace3d(xyz, q, p: int, theta: float, ncrit: int, *, max_depth: int = 0,
             grad = torch.empty(n, 3, device=xyz.device, dtype=torch.float32)
         else:
             phi, grad = out
-        o = _options(max_depth, precision)
+        o = _options(max_depth, precision, select)
         st = Stats()
         _check(load().fmm_laplace3d_ex(xyz.data_ptr(), q.data_ptr(), n, p, float(theta), ncrit,
                                        phi.data_ptr(), grad.data_ptr(), _stream_ptr(torch, xyz.device),
@@ -145,7 +159,8 @@ def laplace3d(xyz, q, p: int, theta: float, ncrit: int, *, max_depth: int = 0,
 
 
 def laplace3d_host(xyz: np.ndarray, q: np.ndarray, p: int, theta: float, ncrit: int, *,
-                   max_depth: int = 0, precision: str = "fp32", stats: bool = False, out=None,
+                   max_depth: int = 0, precision: str = "fp32", select="plain", stats: bool = False,
+                   out=None,
                    stream=None):
     """Same solve with host (numpy) arrays: the library copies in and out."""
     xyz = np.ascontiguousarray(xyz, dtype=np.float32)
@@ -156,7 +171,7 @@ def laplace3d_host(xyz: np.ndarray, q: np.ndarray, p: int, theta: float, ncrit: 
         grad = np.empty((n, 3), dtype=np.float32)
     else:
         phi, grad = out
-    o = _options(max_depth, precision)
+    o = _options(max_depth, precision, select)
     st = Stats()
     _check(load().fmm_laplace3d_host(xyz.ctypes.data, q.ctypes.data, n, p, float(theta), ncrit,
                                      phi.ctypes.data, grad.ctypes.data,
@@ -166,7 +181,7 @@ def laplace3d_host(xyz: np.ndarray, q: np.ndarray, p: int, theta: float, ncrit: 
 
 
 def laplace3d_batched(xyz, q, offsets, p: int, theta: float, ncrit: int, *, max_depth: int = 0,
-                      precision: str = "fp32", stats: bool = False, out=None):
+                      precision: str = "fp32", select="plain", stats: bool = False, out=None):
     """Independent systems in one solve: system s = rows offsets[s]:offsets[s+1] of
     the CUDA float32 xyz[N,3], q[N]; offsets is a host int sequence (len nsys + 1)."""
     import torch
@@ -182,7 +197,7 @@ def laplace3d_batched(xyz, q, offsets, p: int, theta: float, ncrit: int, *, max_
             grad = torch.empty(n, 3, device=xyz.device, dtype=torch.float32)
         else:
             phi, grad = out
-        o = _options(max_depth, precision)
+        o = _options(max_depth, precision, select)
         st = Stats()
         _check(load().fmm_laplace3d_batched(xyz.data_ptr(), q.data_ptr(), off.ctypes.data,
                                             len(off) - 1, p, float(theta), ncrit, phi.data_ptr(),
@@ -207,7 +222,8 @@ def direct(xyz, q):
 
 _EXPORT_DTYPE = {"box": (np.float64, 4), "keys": (np.uint64, None), "order": (np.int32, None),
                  "cells": (np.int64, 6), "p2p": (np.int32, 2), "m2l": (np.int32, 3),
-                 "multipole": (np.float32, "P2pad"), "local": (np.float32, "P2pad")}
+                 "multipole": (np.float32, "P2pad"), "local": (np.float32, "P2pad"),
+                 "select": (np.uint8, SELECT_NB)}
 
 
 def export(what: str, p: int | None = None) -> np.ndarray:

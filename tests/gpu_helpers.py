@@ -13,13 +13,13 @@ def torch_cuda():
     return torch
 
 
-def gpu_solve(xyz, q, p, theta, ncrit, max_depth=0, precision="fp32", stats=False):
+def gpu_solve(xyz, q, p, theta, ncrit, max_depth=0, precision="fp32", stats=False, select="plain"):
     torch = torch_cuda()
     from paper_1108_5815_gb300 import fmm
     x = torch.from_numpy(np.ascontiguousarray(xyz, dtype=np.float32)).cuda()
     qq = torch.from_numpy(np.ascontiguousarray(q, dtype=np.float32)).cuda()
     res = fmm.laplace3d(x, qq, p, theta, ncrit, max_depth=max_depth, precision=precision,
-                        stats=stats)
+                        stats=stats, select=select)
     torch.cuda.synchronize()
     out = [res[0].cpu().numpy().astype(np.float64), res[1].cpu().numpy().astype(np.float64)]
     if stats:
@@ -72,3 +72,23 @@ def oracle_to_gpu_layout(E, p, side, which, P2pad):
                 row[n * n + 2 * m - 1] = c.real
                 row[n * n + 2 * m] = c.imag
     return row
+
+
+def expand_p2p_to_leaves(cells, t, s):
+    """P2P pairs (T, S) with any target cell -> (leaf below T, S), the per-leaf
+    form the GPU lists use."""
+    b, e, nch = (np.asarray(cells[k], np.int64) for k in ("begin", "end", "nchild"))
+    leaves = np.flatnonzero(nch == 0)
+    lb = b[leaves]
+    order = np.argsort(lb)
+    leaves, lb = leaves[order], lb[order]
+    out_t, out_s = [], []
+    for tt, ss in zip(np.asarray(t, np.int64), np.asarray(s, np.int64)):
+        if nch[tt] == 0:
+            out_t.append(tt)
+            out_s.append(ss)
+            continue
+        i0, i1 = np.searchsorted(lb, b[tt]), np.searchsorted(lb, e[tt])
+        out_t.extend(leaves[i0:i1])
+        out_s.extend([ss] * (i1 - i0))
+    return np.asarray(out_t, np.int64), np.asarray(out_s, np.int64)

@@ -172,6 +172,71 @@ enum {
 };
 fmm_status fmm_export(int what, void *dst, int64_t capacity, int64_t *needed);
 
+/* ------------------------------------------------------------------------
+ * Hybrid selection: pre-timed kernels and the learned cost model
+ * ------------------------------------------------------------------------
+ * Section "Kernel pre-calculation": the interaction kernels are timed on
+ * artificial coordinates and charges, and the traversal selects the cheapest
+ * interaction type from those timings.  FMM_SELECT_AUTOTUNE does exactly that:
+ * the P2P kernel is timed on artificial leaves over a grid of target and source
+ * counts (1..512, launches sized like real solves), the M2L time per pair comes
+ * from plain solves of an artificial uniform cube (2^18 particles) at the
+ * solve's p, theta and precision, and a pair becomes P2P where the (log-log
+ * interpolated) P2P time is below the M2L time.  Measured once per device and
+ * cached.
+ * FMM_SELECT_LEARNED replaces the interpolation by a network (3 layers, hidden
+ * width 64, FP16 parameters) trained on the GPU on those timings:
+ *   x = (log2 n_t, log2 n_s, sep, p), sep = R / (r_t + r_s) (1/theta for the
+ *   table), y = (ln ns per P2P pair, ln ns per M2L pair);
+ *   u = (x - (5, 5, 3, 8)) / (4, 4, 1.5, 4), h1 = tanh(W1 u + b1),
+ *   h2 = tanh(W2 h1 + b2), y = W3 h2 + b3;
+ *   parameters in the order W1 (64x4 row-major), b1, W2 (64x64), b2, W3 (2x64), b3;
+ *   loss = sum m (y - t)^2 / sum m over the masked outputs; Adam (lr 3e-3,
+ *   betas 0.9/0.999, eps 1e-8) on FP32 master weights, FP16 copy for the forward.
+ * The table takes, for each bucket, the geometric mean of its count range.
+ * Until a model is trained or set, FMM_SELECT_LEARNED uses the pre-timed table. */
+#define FMM_COST_MODEL_PARAMS 4610
+
+typedef struct {
+    int64_t n_samples_p2p, n_samples_m2l; /* training samples of each kind */
+    int steps;                            /* Adam steps (full batch) */
+    float loss_initial, loss_final;       /* loss before the first and after the last step */
+    float agreement;                      /* worst fraction, over the training (p, theta) grid, of
+                                             table entries with counts <= 4096 where the learned
+                                             table equals the pre-timed one */
+    float ms_pretime, ms_train;           /* time to generate the samples / to train */
+} fmm_cost_model_info;
+
+/* The selection table FMM_SELECT_AUTOTUNE or FMM_SELECT_LEARNED would use for
+ * (p, theta, precision) on the current device (measuring it if needed):
+ * host uint8[FMM_SELECT_NB][FMM_SELECT_NB]. */
+fmm_status fmm_selection_table(int select_mode, int p, double theta, int precision_mode,
+                               unsigned char *table);
+/* Generates timing samples (P2P on artificial leaves; M2L from artificial solves
+ * at p = p_lo..p_hi and theta in {0.35, 0.45, 0.55, 0.65}, in the given M2L
+ * precision), initialises the network from `seed` and trains it for `steps`
+ * full-batch Adam steps on the GPU.  info may be NULL. */
+fmm_status fmm_cost_model_train(int precision_mode, int p_lo, int p_hi, int steps, uint64_t seed,
+                                fmm_cost_model_info *info);
+/* Parameters as FP32 values: master != 0 gives the FP32 master copy, else the
+ * FP16 copy the forward pass uses.  params holds n >= FMM_COST_MODEL_PARAMS floats. */
+fmm_status fmm_cost_model_get(float *params, int64_t n, int master);
+/* Sets the parameters (n == FMM_COST_MODEL_PARAMS, finite): master copy = params,
+ * forward copy = params rounded to FP16; the Adam state is reset. */
+fmm_status fmm_cost_model_set(const float *params, int64_t n);
+/* Loss and gradient (w.r.t. the FP16 parameters) over a host batch x[B][4],
+ * t[B][2], m[B][2], computed by the GPU kernels; no update. */
+fmm_status fmm_cost_model_grad(const float *x, const float *t, const float *m, int64_t B, float *loss,
+                               float *grad);
+/* One Adam step on a host batch; *loss = the loss before the step. */
+fmm_status fmm_cost_model_adam_step(const float *x, const float *t, const float *m, int64_t B, float lr,
+                                    float *loss);
+/* Predictions y[B][2] for host features x[B][4]. */
+fmm_status fmm_cost_model_predict(const float *x, int64_t B, float *y);
+/* The samples of the last fmm_cost_model_train: *n receives their number; with
+ * non-NULL buffers of capacity >= n samples, x[n][4], t[n][2], m[n][2] are copied. */
+fmm_status fmm_cost_model_samples(float *x, float *t, float *m, int64_t capacity, int64_t *n);
+
 /* Morton keys and sorted order of the particles, allocating nothing.
  * (The paper has no counterpart: it is a library convenience.)  For callers
  * that must not allocate device memory after start-up -- code running under

@@ -10,13 +10,16 @@
 // exactly from those counts, so no list can overflow.
 #include <algorithm>
 #include <cstring>
+#include <cmath>
 #include <map>
+#include <tuple>
 #include <memory>
 #include <mutex>
 #include <unordered_map>
 #include <vector>
 
 #include "common.cuh"
+#include "cost_model.cuh"
 #include "kernels.cuh"
 
 namespace fmm {
@@ -79,6 +82,11 @@ struct Workspace {
     int nsys = 1;
     int64_t cap_m2l = 0, cap_p2p = 0, cap_def = 0;  // list capacities that sufficed before
     std::vector<uint8_t> sel_host;                   // selection table of the last solve
+    // hybrid selection: pre-timed kernels and the learned model
+    std::vector<P2PTiming> p2p_grid;                      // P2P time per pair on artificial leaves
+    std::map<std::tuple<int, uint64_t, int>, double> m2l_ns;  // (p, theta bits, precision) -> ns per pair
+    std::map<std::tuple<int, uint64_t, int, int>, std::vector<uint8_t>> tables;  // (mode, theta, p, prec)
+    CostModel cm;
     // The solve runs on two library streams, both non-blocking (a kernel on the
     // legacy default stream would keep the other stream's work from overlapping):
     // main_stream for the tree, traversal and P2P, far_stream (high priority) for
@@ -280,14 +288,13 @@ void validate(const void *xyz, const void *q, int64_t N, int p, double theta, in
         throw Error{FMM_ERR_ARG, "select_mode must be one of FMM_SELECT_*"};
     if (o.select_mode == FMM_SELECT_TABLE && !o.select_table)
         throw Error{FMM_ERR_ARG, "FMM_SELECT_TABLE needs fmm_options.select_table"};
-    if (o.select_mode == FMM_SELECT_AUTOTUNE || o.select_mode == FMM_SELECT_LEARNED)
-        throw Error{FMM_ERR_ARG, "select_mode: pre-timed and learned tables are not available yet"};
+
 }
 
 // The solve on device buffers; the caller holds ws.mu.
 void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, int nsys,
                   const int64_t *offsets, int p, double theta, int ncrit, float *phi, float *grad,
-                  cudaStream_t caller, const fmm_options &o, fmm_stats *stats)
+                  cudaStream_t caller, const fmm_options &o, fmm_stats *stats, const uint8_t *sel)
 {
     ensure_streams(ws);
     cudaStream_t st = ws.main_stream;
@@ -445,9 +452,9 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
     // hybrid selection table (the flagged deferred sources need cell ids below 2^30)
     const uint8_t *d_sel = nullptr;
     ws.sel_host.assign((size_t)kSelNB * kSelNB, 0);
-    if (o.select_mode != FMM_SELECT_PLAIN) {
+    if (sel) {
         if (ncells >= (1 << 30)) throw Error{FMM_ERR_CAPACITY, "selection tables need fewer than 2^30 cells"};
-        std::memcpy(ws.sel_host.data(), o.select_table, ws.sel_host.size());
+        std::memcpy(ws.sel_host.data(), sel, ws.sel_host.size());
         uint8_t *dsel = need<uint8_t>(ws, "select_table", ws.sel_host.size(), st);
         upload(ws, dsel, ws.sel_host.data(), ws.sel_host.size(), st);
         d_sel = dsel;
@@ -749,12 +756,101 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
     }
 }
 
+// Time per M2L pair from plain solves of an artificial uniform cube (2^18
+// particles, ncrit 32): M2L kernel time over the number of M2L pairs.
+double m2l_ns_per_pair(Workspace &ws, int p, double theta, int prec)
+{
+    const auto key = std::make_tuple(p, (uint64_t)std::llround(theta * 1e9), prec);
+    auto it = ws.m2l_ns.find(key);
+    if (it != ws.m2l_ns.end()) return it->second;
+    ensure_streams(ws);
+    cudaStream_t st = ws.main_stream;
+    const int64_t n = 1 << 18;
+    float *xyz = need<float>(ws, "syn_xyz", 3 * n, st);
+    float *q = need<float>(ws, "syn_q", n, st);
+    float *phi = need<float>(ws, "syn_phi", n, st);
+    float *grad = need<float>(ws, "syn_grad", 3 * n, st);
+    synth_uniform(xyz, q, n, 0x5eed0001ull, st);
+    fmm_options o;
+    fmm_default_options(&o);
+    o.precision_mode = prec;
+    const int64_t off[2] = {0, n};
+    double best = 1e30;
+    for (int rep = 0; rep < 3; ++rep) {
+        fmm_stats s{};
+        solve_locked(ws, xyz, q, n, 1, off, p, theta, 32, phi, grad, st, o, &s, nullptr);
+        if (rep > 0 && s.n_m2l_pairs > 0) best = std::min(best, (double)s.ms_m2l * 1e6 / (double)s.n_m2l_pairs);
+    }
+    ws.have_solve = false;
+    ws.m2l_ns[key] = best;
+    return best;
+}
+
+const std::vector<P2PTiming> &p2p_timings(Workspace &ws)
+{
+    if (ws.p2p_grid.empty()) {
+        ensure_streams(ws);
+        const std::vector<int> counts = {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512};
+        ws.p2p_grid = pretime_p2p(counts, 0x5eed0002ull, ws.main_stream);
+    }
+    return ws.p2p_grid;
+}
+
+const std::vector<uint8_t> &pretimed_table(Workspace &ws, int p, double theta, int prec)
+{
+    const auto key = std::make_tuple(FMM_SELECT_AUTOTUNE, (uint64_t)std::llround(theta * 1e9), p, prec);
+    auto it = ws.tables.find(key);
+    if (it != ws.tables.end()) return it->second;
+    const double m2l = m2l_ns_per_pair(ws, p, theta, prec);
+    std::vector<uint8_t> t((size_t)kSelNB * kSelNB);
+    table_from_timings(p2p_timings(ws), m2l, t.data());
+    return ws.tables[key] = std::move(t);
+}
+
+const std::vector<uint8_t> &learned_table(Workspace &ws, int p, double theta)
+{
+    const auto key = std::make_tuple(FMM_SELECT_LEARNED, (uint64_t)std::llround(theta * 1e9), p, 0);
+    auto it = ws.tables.find(key);
+    if (it != ws.tables.end()) return it->second;
+    ensure_streams(ws);
+    std::vector<uint8_t> t((size_t)kSelNB * kSelNB);
+    model_table(ws.cm, p, theta, t.data(), ws.main_stream);
+    return ws.tables[key] = std::move(t);
+}
+
+// The selection table of a solve (nullptr = plain FMM).  Pre-timed tables are
+// measured once per (p, theta, precision) and device; the learned mode falls
+// back to them while no model has been trained or set.
+const uint8_t *selection_table(Workspace &ws, const fmm_options &o, int p, double theta)
+{
+    switch (o.select_mode) {
+        case FMM_SELECT_TABLE: return o.select_table;
+        case FMM_SELECT_AUTOTUNE: return pretimed_table(ws, p, theta, o.precision_mode).data();
+        case FMM_SELECT_LEARNED:
+            if (!ws.cm.trained) return pretimed_table(ws, p, theta, o.precision_mode).data();
+            return learned_table(ws, p, theta).data();
+        default: return nullptr;
+    }
+}
+
 fmm_options resolve_opts(const fmm_options *opt)
 {
     fmm_options o;
     fmm_default_options(&o);
     if (opt) o = *opt;
     return o;
+}
+
+Samples host_samples(const float *x, const float *t, const float *m, int64_t B)
+{
+    if (!x || B < 1) throw Error{FMM_ERR_ARG, "need x and B >= 1"};
+    Samples s;
+    s.x.assign(x, x + 4 * B);
+    s.t.assign(2 * B, 0.f);
+    s.m.assign(2 * B, 0.f);
+    if (t) s.t.assign(t, t + 2 * B);
+    if (m) s.m.assign(m, m + 2 * B);
+    return s;
 }
 
 template <typename F>
@@ -802,8 +898,9 @@ fmm_status fmm_laplace3d_ex(const float *xyz, const float *q, int64_t N, int p, 
         validate(xyz, q, N, p, theta, ncrit, phi, grad, o);
         Workspace &ws = workspace_for_current_device();
         std::lock_guard<std::mutex> lk(ws.mu);
+        const uint8_t *sel = selection_table(ws, o, p, theta);
         const int64_t off[2] = {0, N};
-        solve_locked(ws, xyz, q, N, 1, off, p, theta, ncrit, phi, grad, (cudaStream_t)stream, o, stats);
+        solve_locked(ws, xyz, q, N, 1, off, p, theta, ncrit, phi, grad, (cudaStream_t)stream, o, stats, sel);
     });
 }
 
@@ -822,6 +919,7 @@ fmm_status fmm_laplace3d_host(const float *xyz_host, const float *q_host, int64_
         validate(xyz_host, q_host, N, p, theta, ncrit, phi_host, grad_host, o);
         Workspace &ws = workspace_for_current_device();
         std::lock_guard<std::mutex> lk(ws.mu);
+        const uint8_t *sel = selection_table(ws, o, p, theta);
         cudaStream_t st = (cudaStream_t)stream;
         float *xd = need<float>(ws, "host_xyz", 3 * (size_t)N, st);
         float *qd = need<float>(ws, "host_q", (size_t)N, st);
@@ -830,7 +928,7 @@ fmm_status fmm_laplace3d_host(const float *xyz_host, const float *q_host, int64_
         FMM_CUDA_TRY(cudaMemcpyAsync(xd, xyz_host, sizeof(float) * 3 * N, cudaMemcpyHostToDevice, st));
         FMM_CUDA_TRY(cudaMemcpyAsync(qd, q_host, sizeof(float) * N, cudaMemcpyHostToDevice, st));
         const int64_t off[2] = {0, N};
-        solve_locked(ws, xd, qd, N, 1, off, p, theta, ncrit, pd, gd, st, o, stats);
+        solve_locked(ws, xd, qd, N, 1, off, p, theta, ncrit, pd, gd, st, o, stats, sel);
         FMM_CUDA_TRY(cudaMemcpyAsync(phi_host, pd, sizeof(float) * N, cudaMemcpyDeviceToHost, st));
         FMM_CUDA_TRY(cudaMemcpyAsync(grad_host, gd, sizeof(float) * 3 * N, cudaMemcpyDeviceToHost, st));
         FMM_CUDA_TRY(cudaStreamSynchronize(st));
@@ -851,8 +949,206 @@ fmm_status fmm_laplace3d_batched(const float *xyz, const float *q, const int64_t
         validate(xyz, q, N, p, theta, ncrit, phi, grad, o);
         Workspace &ws = workspace_for_current_device();
         std::lock_guard<std::mutex> lk(ws.mu);
+        const uint8_t *sel = selection_table(ws, o, p, theta);
         solve_locked(ws, xyz, q, N, nsys, offsets, p, theta, ncrit, phi, grad, (cudaStream_t)stream, o,
-                     stats);
+                     stats, sel);
+    });
+}
+
+// ---------------------------------------------------------------- hybrid selection
+
+fmm_status fmm_selection_table(int select_mode, int p, double theta, int precision_mode,
+                               unsigned char *table)
+{
+    return guarded([&] {
+        if (!table) throw Error{FMM_ERR_ARG, "null table"};
+        if (p < 1 || p > 20 || !(theta > 0.0 && theta < 1.0)) throw Error{FMM_ERR_ARG, "p or theta out of range"};
+        if (precision_mode < FMM_PREC_FP32 || precision_mode > FMM_PREC_BF16X3)
+            throw Error{FMM_ERR_ARG, "precision_mode must be FMM_PREC_*"};
+        if (select_mode != FMM_SELECT_AUTOTUNE && select_mode != FMM_SELECT_LEARNED)
+            throw Error{FMM_ERR_ARG, "select_mode must be FMM_SELECT_AUTOTUNE or FMM_SELECT_LEARNED"};
+        fmm_options o;
+        fmm_default_options(&o);
+        o.select_mode = select_mode;
+        o.precision_mode = precision_mode;
+        Workspace &ws = workspace_for_current_device();
+        std::lock_guard<std::mutex> lk(ws.mu);
+        std::memcpy(table, selection_table(ws, o, p, theta), (size_t)kSelNB * kSelNB);
+    });
+}
+
+fmm_status fmm_cost_model_train(int precision_mode, int p_lo, int p_hi, int steps, uint64_t seed,
+                                fmm_cost_model_info *info)
+{
+    return guarded([&] {
+        if (p_lo < 1 || p_hi > 20 || p_lo > p_hi) throw Error{FMM_ERR_ARG, "need 1 <= p_lo <= p_hi <= 20"};
+        if (steps < 1) throw Error{FMM_ERR_ARG, "steps must be >= 1"};
+        if (precision_mode < FMM_PREC_FP32 || precision_mode > FMM_PREC_BF16X3)
+            throw Error{FMM_ERR_ARG, "precision_mode must be FMM_PREC_*"};
+        Workspace &ws = workspace_for_current_device();
+        std::lock_guard<std::mutex> lk(ws.mu);
+        ensure_streams(ws);
+        cudaStream_t st = ws.main_stream;
+        cudaEvent_t e0, e1, e2;
+        FMM_CUDA_TRY(cudaEventCreate(&e0));
+        FMM_CUDA_TRY(cudaEventCreate(&e1));
+        FMM_CUDA_TRY(cudaEventCreate(&e2));
+        FMM_CUDA_TRY(cudaEventRecord(e0, st));
+        // samples: P2P times on artificial leaves (cost independent of sep and p, which
+        // are drawn at random), M2L times from artificial solves at each (p, theta)
+        SplitMix64 rng{seed};
+        Samples s;
+        auto add = [&](double lnt, double lns, double sep, double pp, double t0, double t1, float m0, float m1) {
+            s.x.insert(s.x.end(), {(float)lnt, (float)lns, (float)sep, (float)pp});
+            s.t.insert(s.t.end(), {(float)t0, (float)t1});
+            s.m.insert(s.m.end(), {m0, m1});
+        };
+        int64_t np2p = 0, nm2l = 0;
+        for (const P2PTiming &g : p2p_timings(ws)) {
+            for (int r = 0; r < 2; ++r) {
+                add(std::log2((double)g.nt), std::log2((double)g.ns), 1.4 + 2.4 * rng.uniform(),
+                    p_lo + (p_hi - p_lo) * rng.uniform(), std::log(g.ns_per_pair), 0.0, 1.f, 0.f);
+                ++np2p;
+            }
+        }
+        const double thetas[4] = {0.35, 0.45, 0.55, 0.65};
+        for (int pp = p_lo; pp <= p_hi; ++pp) {
+            for (double th : thetas) {
+                const double lt = std::log(m2l_ns_per_pair(ws, pp, th, precision_mode));
+                for (int r = 0; r < 8; ++r) {
+                    add(10.0 * rng.uniform(), 10.0 * rng.uniform(), 1.0 / th, pp, 0.0, lt, 0.f, 1.f);
+                    ++nm2l;
+                }
+            }
+        }
+        FMM_CUDA_TRY(cudaEventRecord(e1, st));
+        const std::vector<float> w0 = model_init(s, seed ^ 0xa5a5a5a5ull);
+        model_set(ws.cm, w0.data(), st);
+        float l0 = 0.f, l1 = 0.f;
+        model_train(ws.cm, s, steps, 3e-3f, l0, l1, st);
+        FMM_CUDA_TRY(cudaEventRecord(e2, st));
+        FMM_CUDA_TRY(cudaEventSynchronize(e2));
+        ws.cm.trained = true;
+        ws.cm.last = s;
+        for (auto it = ws.tables.begin(); it != ws.tables.end();)
+            it = std::get<0>(it->first) == FMM_SELECT_LEARNED ? ws.tables.erase(it) : std::next(it);
+        // the judge: agreement of the learned table with the pre-timed one over
+        // counts up to 4096 (buckets < 43), worst case over the training grid
+        float agree = 1.f;
+        for (int pp = p_lo; pp <= p_hi; ++pp) {
+            for (double th : thetas) {
+                const std::vector<uint8_t> &a = pretimed_table(ws, pp, th, precision_mode);
+                const std::vector<uint8_t> &b = learned_table(ws, pp, th);
+                int same = 0, tot = 0;
+                for (int i = 0; i < 43; ++i)
+                    for (int j = 0; j < 43; ++j, ++tot) same += a[i * kSelNB + j] == b[i * kSelNB + j];
+                agree = std::min(agree, (float)same / (float)tot);
+            }
+        }
+        if (info) {
+            info->n_samples_p2p = np2p;
+            info->n_samples_m2l = nm2l;
+            info->steps = steps;
+            info->loss_initial = l0;
+            info->loss_final = l1;
+            info->agreement = agree;
+            FMM_CUDA_TRY(cudaEventElapsedTime(&info->ms_pretime, e0, e1));
+            FMM_CUDA_TRY(cudaEventElapsedTime(&info->ms_train, e1, e2));
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        cudaEventDestroy(e2);
+    });
+}
+
+fmm_status fmm_cost_model_get(float *params, int64_t n, int master)
+{
+    return guarded([&] {
+        if (!params || n < FMM_COST_MODEL_PARAMS) throw Error{FMM_ERR_ARG, "params needs FMM_COST_MODEL_PARAMS floats"};
+        Workspace &ws = workspace_for_current_device();
+        std::lock_guard<std::mutex> lk(ws.mu);
+        if (!ws.cm.w16) throw Error{FMM_ERR_ARG, "no cost model has been trained or set"};
+        if (master) {
+            FMM_CUDA_TRY(cudaMemcpy(params, ws.cm.w32, sizeof(float) * kMlpParams, cudaMemcpyDeviceToHost));
+        } else {
+            std::vector<__half> h(kMlpParams);
+            FMM_CUDA_TRY(cudaMemcpy(h.data(), ws.cm.w16, sizeof(__half) * kMlpParams, cudaMemcpyDeviceToHost));
+            for (int i = 0; i < kMlpParams; ++i) params[i] = __half2float(h[i]);
+        }
+    });
+}
+
+fmm_status fmm_cost_model_set(const float *params, int64_t n)
+{
+    return guarded([&] {
+        if (!params || n != FMM_COST_MODEL_PARAMS) throw Error{FMM_ERR_ARG, "params must hold FMM_COST_MODEL_PARAMS floats"};
+        for (int64_t i = 0; i < n; ++i)
+            if (!std::isfinite(params[i])) throw Error{FMM_ERR_NONFINITE, "non-finite parameter"};
+        Workspace &ws = workspace_for_current_device();
+        std::lock_guard<std::mutex> lk(ws.mu);
+        ensure_streams(ws);
+        model_set(ws.cm, params, ws.main_stream);
+        ws.cm.trained = true;
+        for (auto it = ws.tables.begin(); it != ws.tables.end();)
+            it = std::get<0>(it->first) == FMM_SELECT_LEARNED ? ws.tables.erase(it) : std::next(it);
+    });
+}
+
+fmm_status fmm_cost_model_grad(const float *x, const float *t, const float *m, int64_t B, float *loss,
+                               float *grad)
+{
+    return guarded([&] {
+        if (!t || !m || !loss || !grad) throw Error{FMM_ERR_ARG, "null argument"};
+        const Samples s = host_samples(x, t, m, B);
+        Workspace &ws = workspace_for_current_device();
+        std::lock_guard<std::mutex> lk(ws.mu);
+        if (!ws.cm.w16) throw Error{FMM_ERR_ARG, "no cost model has been trained or set"};
+        ensure_streams(ws);
+        model_grad(ws.cm, s, loss, grad, ws.main_stream);
+    });
+}
+
+fmm_status fmm_cost_model_adam_step(const float *x, const float *t, const float *m, int64_t B, float lr,
+                                    float *loss)
+{
+    return guarded([&] {
+        if (!t || !m || !loss || !(lr > 0.f)) throw Error{FMM_ERR_ARG, "bad argument"};
+        const Samples s = host_samples(x, t, m, B);
+        Workspace &ws = workspace_for_current_device();
+        std::lock_guard<std::mutex> lk(ws.mu);
+        if (!ws.cm.w16) throw Error{FMM_ERR_ARG, "no cost model has been trained or set"};
+        ensure_streams(ws);
+        model_adam_step(ws.cm, s, lr, loss, ws.main_stream);
+        for (auto it = ws.tables.begin(); it != ws.tables.end();)
+            it = std::get<0>(it->first) == FMM_SELECT_LEARNED ? ws.tables.erase(it) : std::next(it);
+    });
+}
+
+fmm_status fmm_cost_model_predict(const float *x, int64_t B, float *y)
+{
+    return guarded([&] {
+        if (!y) throw Error{FMM_ERR_ARG, "null y"};
+        const Samples s = host_samples(x, nullptr, nullptr, B);
+        Workspace &ws = workspace_for_current_device();
+        std::lock_guard<std::mutex> lk(ws.mu);
+        if (!ws.cm.w16) throw Error{FMM_ERR_ARG, "no cost model has been trained or set"};
+        ensure_streams(ws);
+        model_predict(ws.cm, s.x.data(), B, y, ws.main_stream);
+    });
+}
+
+fmm_status fmm_cost_model_samples(float *x, float *t, float *m, int64_t capacity, int64_t *n)
+{
+    return guarded([&] {
+        Workspace &ws = workspace_for_current_device();
+        std::lock_guard<std::mutex> lk(ws.mu);
+        const int64_t k = ws.cm.last.size();
+        if (n) *n = k;
+        if (!x && !t && !m) return;
+        if (!x || !t || !m || capacity < k) throw Error{FMM_ERR_ARG, "buffers too small"};
+        std::memcpy(x, ws.cm.last.x.data(), sizeof(float) * 4 * k);
+        std::memcpy(t, ws.cm.last.t.data(), sizeof(float) * 2 * k);
+        std::memcpy(m, ws.cm.last.m.data(), sizeof(float) * 2 * k);
     });
 }
 

@@ -2,6 +2,10 @@
 // the translation units of the CUDA path.
 #pragma once
 
+#include <cuda_fp16.h>
+
+#include <vector>
+
 #include "common.cuh"
 
 namespace fmm {
@@ -122,5 +126,40 @@ __global__ void k_p2p(CellArrays c, ListArrays L, const int *leaves, int nleaves
 __global__ void k_direct(const float *xyz, const float *q, int64_t n, float *phi, float *grad);
 __global__ void k_combine(const float4 *far, const float4 *near, const uint32_t *idx, int64_t n,
                           float *phi, float *grad);
+
+// mlp.cu -- cost-model network (3 layers, hidden 64, FP16 parameters)
+constexpr int kMlpIn = 4, kMlpHidden = 64, kMlpOut = 2;
+constexpr int kOffW1 = 0, kOffB1 = kOffW1 + kMlpHidden * kMlpIn, kOffW2 = kOffB1 + kMlpHidden,
+              kOffB2 = kOffW2 + kMlpHidden * kMlpHidden, kOffW3 = kOffB2 + kMlpHidden,
+              kOffB3 = kOffW3 + kMlpOut * kMlpHidden, kMlpParams = kOffB3 + kMlpOut;
+size_t mlp_grad_smem();
+__global__ void k_mlp_forward(const __half *w16, const float *x, int B, float *y);
+__global__ void k_mlp_grad_partial(const __half *w16, const float *x, const float *t, const float *m, int B,
+                                   const float *inv_cnt, float *partial, float *loss_part);
+__global__ void k_mlp_mask_count(const float *m, int n, float *inv_cnt);
+__global__ void k_mlp_reduce(const float *partial, int nblk, const float *loss_part, float *grad,
+                             float *loss);
+__global__ void k_mlp_adam(float *w32, float *mom, float *vel, const float *g, __half *w16, int *step,
+                           float lr, float beta1, float beta2, float eps);
+__global__ void k_mlp_step_inc(int *step);
+__global__ void k_mlp_table(const __half *w16, float p, float sep, uint8_t *sel);
+
+// cost_model.cu -- kernel pre-calculation on artificial cells
+struct P2PTiming {
+    int nt, ns;          // particles per target leaf and per source cell
+    double ns_per_pair;  // device time per (target leaf, source cell) pair
+};
+// Times the P2P kernel on artificial leaves for every (nt, ns) in counts x counts.
+std::vector<P2PTiming> pretime_p2p(const std::vector<int> &counts, uint64_t seed, cudaStream_t st);
+// Selection table: P2P iff the interpolated P2P time per pair is below m2l_ns.
+void table_from_timings(const std::vector<P2PTiming> &grid, double m2l_ns, uint8_t *sel);
+// log2 of the representative count of a selection-table bucket (host and device agree).
+__host__ __device__ inline float bucket_mid_log2(int b)
+{
+    if (b < 3) return log2f((float)(b + 1));
+    const int e = (b - 3) / 4 + 2, k = (b - 3) % 4;
+    const float lo = ldexpf(1.f + 0.25f * k, e), hi = ldexpf(1.f + 0.25f * (k + 1), e) - 1.f;
+    return 0.5f * (log2f(lo) + log2f(hi > lo ? hi : lo));
+}
 
 }  // namespace fmm

@@ -27,7 +27,11 @@ EXPORT = {"box": 0, "keys": 1, "order": 2, "cells": 3, "p2p": 4, "m2l": 5, "mult
 # every symbol the header declares
 ABI_SYMBOLS = ("fmm_default_options", "fmm_laplace3d", "fmm_laplace3d_ex", "fmm_laplace3d_host",
                "fmm_laplace3d_batched",
-               "fmm_direct", "fmm_export", "fmm_last_error", "fmm_morton_sort_noalloc")
+               "fmm_direct", "fmm_export", "fmm_last_error", "fmm_morton_sort_noalloc",
+               "fmm_selection_table", "fmm_cost_model_train", "fmm_cost_model_get",
+               "fmm_cost_model_set", "fmm_cost_model_grad", "fmm_cost_model_adam_step",
+               "fmm_cost_model_predict", "fmm_cost_model_samples")
+COST_MODEL_PARAMS = 4610
 
 
 class FmmError(RuntimeError):
@@ -40,6 +44,16 @@ class Options(ctypes.Structure):
     _fields_ = [("max_depth", ctypes.c_int), ("precision_mode", ctypes.c_int),
                 ("select_mode", ctypes.c_int), ("deterministic", ctypes.c_int),
                 ("select_table", ctypes.c_void_p)]
+
+
+class CostModelInfo(ctypes.Structure):
+    _fields_ = [("n_samples_p2p", ctypes.c_int64), ("n_samples_m2l", ctypes.c_int64),
+                ("steps", ctypes.c_int), ("loss_initial", ctypes.c_float),
+                ("loss_final", ctypes.c_float), ("agreement", ctypes.c_float),
+                ("ms_pretime", ctypes.c_float), ("ms_train", ctypes.c_float)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class Stats(ctypes.Structure):
@@ -84,8 +98,20 @@ def load(path: str | None = None):
         L.fmm_last_error.restype = ctypes.c_char_p
         L.fmm_morton_sort_noalloc.argtypes = [vp, i64, vp, vp, vp, vp]
         L.fmm_morton_sort_noalloc.restype = ctypes.c_int
+        L.fmm_selection_table.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, vp]
+        L.fmm_cost_model_train.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                           ctypes.c_uint64, ctypes.POINTER(CostModelInfo)]
+        L.fmm_cost_model_get.argtypes = [vp, i64, ctypes.c_int]
+        L.fmm_cost_model_set.argtypes = [vp, i64]
+        L.fmm_cost_model_grad.argtypes = [vp, vp, vp, i64, vp, vp]
+        L.fmm_cost_model_adam_step.argtypes = [vp, vp, vp, i64, ctypes.c_float, vp]
+        L.fmm_cost_model_predict.argtypes = [vp, i64, vp]
+        L.fmm_cost_model_samples.argtypes = [vp, vp, vp, i64, ctypes.POINTER(i64)]
         for name in ("fmm_laplace3d", "fmm_laplace3d_ex", "fmm_laplace3d_host", "fmm_direct",
-                     "fmm_export", "fmm_laplace3d_batched"):
+                     "fmm_export", "fmm_laplace3d_batched", "fmm_selection_table",
+                     "fmm_cost_model_train", "fmm_cost_model_get", "fmm_cost_model_set",
+                     "fmm_cost_model_grad", "fmm_cost_model_adam_step", "fmm_cost_model_predict",
+                     "fmm_cost_model_samples"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
         return L
@@ -260,3 +286,80 @@ def morton_sort_noalloc(xyz, out=None):
         _check(load().fmm_morton_sort_noalloc(xyz.data_ptr(), n, keys.data_ptr(), order.data_ptr(),
                                               box.data_ptr(), _stream_ptr(torch, xyz.device)))
     return keys, order, box
+
+
+# ---------------------------------------------------------------- hybrid selection
+
+def _f32(a, shape):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+    if shape is not None and a.shape != shape:
+        raise FmmError(FMM_ERR_ARG, f"expected shape {shape}, got {a.shape}")
+    return a
+
+
+def selection_table(mode: str, p: int, theta: float, precision: str = "fp32") -> np.ndarray:
+    """uint8 [128, 128] table the "autotune" or "learned" mode uses (see fmm.h)."""
+    t = np.zeros((SELECT_NB, SELECT_NB), dtype=np.uint8)
+    _check(load().fmm_selection_table(SELECT[mode], p, float(theta), PRECISION[precision], t.ctypes.data))
+    return t
+
+
+def cost_model_train(precision: str = "fp32", p_lo: int = 3, p_hi: int = 12, steps: int = 2000,
+                     seed: int = 1) -> dict:
+    """Time the kernels on artificial data and train the cost-model network on the GPU."""
+    info = CostModelInfo()
+    _check(load().fmm_cost_model_train(PRECISION[precision], p_lo, p_hi, steps, seed, ctypes.byref(info)))
+    return info.as_dict()
+
+
+def cost_model_get(master: bool = False) -> np.ndarray:
+    w = np.zeros(COST_MODEL_PARAMS, dtype=np.float32)
+    _check(load().fmm_cost_model_get(w.ctypes.data, w.size, int(master)))
+    return w
+
+
+def cost_model_set(params) -> None:
+    w = _f32(params, (COST_MODEL_PARAMS,))
+    _check(load().fmm_cost_model_set(w.ctypes.data, w.size))
+
+
+def cost_model_grad(x, t, m):
+    """(loss, gradient[4610]) of the current network over a host batch, on the GPU."""
+    x = _f32(x, None).reshape(-1, 4)
+    b = x.shape[0]
+    t, m = _f32(t, (b, 2)), _f32(m, (b, 2))
+    loss = np.zeros(1, dtype=np.float32)
+    g = np.zeros(COST_MODEL_PARAMS, dtype=np.float32)
+    _check(load().fmm_cost_model_grad(x.ctypes.data, t.ctypes.data, m.ctypes.data, b, loss.ctypes.data,
+                                      g.ctypes.data))
+    return float(loss[0]), g
+
+
+def cost_model_adam_step(x, t, m, lr: float) -> float:
+    x = _f32(x, None).reshape(-1, 4)
+    b = x.shape[0]
+    t, m = _f32(t, (b, 2)), _f32(m, (b, 2))
+    loss = np.zeros(1, dtype=np.float32)
+    _check(load().fmm_cost_model_adam_step(x.ctypes.data, t.ctypes.data, m.ctypes.data, b, float(lr),
+                                           loss.ctypes.data))
+    return float(loss[0])
+
+
+def cost_model_predict(x) -> np.ndarray:
+    x = _f32(x, None).reshape(-1, 4)
+    y = np.zeros((x.shape[0], 2), dtype=np.float32)
+    _check(load().fmm_cost_model_predict(x.ctypes.data, x.shape[0], y.ctypes.data))
+    return y
+
+
+def cost_model_samples():
+    """(x [n,4], t [n,2], m [n,2]) of the last training."""
+    n = ctypes.c_int64(0)
+    _check(load().fmm_cost_model_samples(None, None, None, 0, ctypes.byref(n)))
+    k = n.value
+    x = np.zeros((k, 4), np.float32)
+    t = np.zeros((k, 2), np.float32)
+    m = np.zeros((k, 2), np.float32)
+    if k:
+        _check(load().fmm_cost_model_samples(x.ctypes.data, t.ctypes.data, m.ctypes.data, k, ctypes.byref(n)))
+    return x, t, m

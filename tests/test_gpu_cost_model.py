@@ -1,0 +1,172 @@
+"""The learned cost model on the GPU: its forward, backward and Adam kernels
+against the FP64 oracle (oracle/cost_model.py), training on timings the method
+generates, and the hybrid selection it drives.
+
+* gradients of the loss w.r.t. the FP16 parameters: GPU (FP32 sums) vs FP64
+  oracle with the same parameters, relative L2 <= 1e-4;
+* one Adam step moves the FP32 master weights as the oracle's step does;
+* the trained network reproduces its timing samples and agrees with the
+  pre-timed table;
+* solves with the pre-timed and the learned tables give exactly the oracle's
+  interaction lists for the same table (bit-exact) and its fields (1e-5);
+* the learned selection is faster than the plain FMM where the plain FMM is
+  out of balance (small ncrit) and no less accurate."""
+import time
+
+import numpy as np
+import pytest
+
+from oracle import cost_model as C
+from oracle import oracle as O
+from paper_1108_5815_gb300 import inputs
+from tests.gpu_helpers import (canonical_ids, expand_p2p_to_leaves, gpu_cells, gpu_solve, pair_codes,
+                               rel_l2, torch_cuda)
+
+pytestmark = pytest.mark.gpu
+
+
+def _batch(rng, b):
+    x = np.stack([rng.uniform(0, 10, b), rng.uniform(0, 10, b), rng.uniform(1.4, 3.8, b),
+                  rng.integers(3, 13, b)], axis=1).astype(np.float32)
+    t = rng.normal(0, 2, (b, 2)).astype(np.float32)
+    m = (rng.random((b, 2)) < 0.5).astype(np.float32)
+    return x, t, m
+
+
+def _set_random(seed):
+    from paper_1108_5815_gb300 import fmm
+    rng = np.random.default_rng(seed)
+    w = rng.normal(0, 0.3, C.NPARAM).astype(np.float32)
+    fmm.cost_model_set(w)
+    return w, fmm.cost_model_get(master=False).astype(np.float64)
+
+
+def test_parameters_round_trip_through_fp16():
+    from paper_1108_5815_gb300 import fmm
+    torch_cuda()
+    w, w16 = _set_random(0)
+    assert np.array_equal(w16, C.to_fp16(w))
+    assert np.array_equal(fmm.cost_model_get(master=True), w)
+
+
+def test_gradient_matches_cpu_oracle():
+    from paper_1108_5815_gb300 import fmm
+    torch_cuda()
+    _, w16 = _set_random(1)
+    rng = np.random.default_rng(2)
+    for b in (1, 63, 64, 300):  # one sample, a partial block, one block, several blocks
+        x, t, m = _batch(rng, b)
+        m[0] = 1.0
+        loss, g = fmm.cost_model_grad(x, t, m)
+        oloss, og = C.grad(w16, x.astype(np.float64), t.astype(np.float64), m.astype(np.float64))
+        assert abs(loss - oloss) <= 1e-5 * abs(oloss)
+        assert np.linalg.norm(g - og) <= 1e-4 * np.linalg.norm(og)
+        for name, shp in C.SHAPES:  # every parameter block, not only the largest
+            a, b_ = C.unpack(g.astype(np.float64))[name], C.unpack(og)[name]
+            assert np.linalg.norm(a - b_) <= 1e-4 * np.linalg.norm(b_) + 1e-9, name
+
+
+def test_predict_matches_cpu_oracle():
+    from paper_1108_5815_gb300 import fmm
+    torch_cuda()
+    _, w16 = _set_random(3)
+    x, _, _ = _batch(np.random.default_rng(4), 1000)
+    y = fmm.cost_model_predict(x)
+    oy, _ = C.forward(w16, x.astype(np.float64))
+    assert np.max(np.abs(y - oy)) <= 1e-5 * (1.0 + np.max(np.abs(oy)))
+
+
+def test_adam_step_matches_cpu_oracle():
+    from paper_1108_5815_gb300 import fmm
+    torch_cuda()
+    w, w16 = _set_random(5)
+    x, t, m = _batch(np.random.default_rng(6), 200)
+    lr = 1e-3
+    loss = fmm.cost_model_adam_step(x, t, m, lr)
+    oloss, og = C.grad(w16, x.astype(np.float64), t.astype(np.float64), m.astype(np.float64))
+    assert abs(loss - oloss) <= 1e-5 * abs(oloss)
+    ow, _, _ = C.adam_step(w.astype(np.float64), np.zeros(C.NPARAM), np.zeros(C.NPARAM), og, 1, lr)
+    gw = fmm.cost_model_get(master=True).astype(np.float64)
+    clear = np.abs(og) > 1e-4 * np.max(np.abs(og))  # gradients whose sign FP32 cannot flip
+    assert np.max(np.abs(gw - ow)[clear]) <= 1e-6
+    assert np.max(np.abs(gw - ow)) <= 2 * lr + 1e-6
+    assert np.array_equal(fmm.cost_model_get(master=False), C.to_fp16(gw).astype(np.float32))
+
+
+@pytest.fixture(scope="module")
+def trained():
+    from paper_1108_5815_gb300 import fmm
+    torch_cuda()
+    info = fmm.cost_model_train(precision="fp32", p_lo=3, p_hi=10, steps=3000, seed=7)
+    return info
+
+
+def test_training_fits_the_timings(trained):
+    from paper_1108_5815_gb300 import fmm
+    info = trained
+    assert info["n_samples_p2p"] > 300 and info["n_samples_m2l"] > 100
+    assert info["loss_final"] < 0.1 * info["loss_initial"]
+    assert info["loss_final"] < 0.05          # about 20 % in time
+    assert info["agreement"] >= 0.9
+    x, t, m = fmm.cost_model_samples()
+    y = fmm.cost_model_predict(x)
+    # the network's loss on its own samples is the reported final loss
+    assert abs(np.sum(m * (y - t) ** 2) / np.sum(m) - info["loss_final"]) <= 1e-3 * (1 + info["loss_final"])
+    # timings are physical: P2P time per pair grows with the counts, M2L with p
+    sel = (m[:, 0] > 0)
+    big = sel & (x[:, 0] >= 8) & (x[:, 1] >= 8)
+    small = sel & (x[:, 0] <= 1) & (x[:, 1] <= 1)
+    assert np.min(t[big, 0]) > np.max(t[small, 0])
+
+
+@pytest.mark.parametrize("mode", ["autotune", "learned"])
+def test_selected_solve_matches_oracle_with_the_same_table(trained, mode):
+    from paper_1108_5815_gb300 import fmm
+    x, q = inputs.make("plummer", 30000, 44)
+    p, theta, ncrit = 6, 0.45, 4
+    phi, grad = gpu_solve(x, q, p, theta, ncrit, select=mode)
+    sel = fmm.export("select")
+    assert np.array_equal(sel, fmm.selection_table(mode, p, theta))
+    assert sel.any()  # the tables choose P2P somewhere at this ncrit
+    f = O.Fmm(x, q, p, theta, ncrit, sel=sel)
+    oc, gc = f.cells(), gpu_cells()
+    oid, _ = canonical_ids(oc["level"], oc["prefix"])
+    gid, _ = canonical_ids(gc["level"], gc["prefix"])
+    ol = f.lists()
+    et, es = expand_p2p_to_leaves(oc, ol["p2p_t"], ol["p2p_s"])
+    gp, gm = fmm.export("p2p"), fmm.export("m2l")
+    assert np.array_equal(pair_codes(et, es, oid, f.ncells), pair_codes(gp[:, 0], gp[:, 1], gid, f.ncells))
+    assert np.array_equal(pair_codes(ol["m2l_t"], ol["m2l_s"], oid, f.ncells),
+                          pair_codes(gm[:, 0], gm[:, 1], gid, f.ncells))
+    ophi, ograd = f.evaluate()
+    assert rel_l2(phi, ophi) < 1e-5 and rel_l2(grad, ograd) < 1e-5
+
+
+def _timed(xt, qt, p, theta, ncrit, select, reps=5):
+    torch = torch_cuda()
+    from paper_1108_5815_gb300 import fmm
+    for _ in range(2):
+        fmm.laplace3d(xt, qt, p, theta, ncrit, select=select)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        out = fmm.laplace3d(xt, qt, p, theta, ncrit, select=select)
+        torch.cuda.synchronize()
+        ts.append(time.perf_counter() - t0)
+    return float(np.median(ts)), out
+
+
+def test_learned_selection_gains_where_the_fmm_is_out_of_balance(trained):
+    torch = torch_cuda()
+    n, p, theta, ncrit = 1 << 20, 8, 0.5, 4
+    x, q = inputs.uniform_cube(n, 2024)
+    xt, qt = torch.from_numpy(x).cuda(), torch.from_numpy(q).cuda()
+    t_plain, (phi0, g0) = _timed(xt, qt, p, theta, ncrit, "plain")
+    t_learn, (phi1, g1) = _timed(xt, qt, p, theta, ncrit, "learned")
+    assert t_learn < 0.9 * t_plain, (t_learn, t_plain)
+    idx = inputs.sample_indices(n, 256, 5)
+    dphi, dgrad = O.direct(x, q, targets=idx)
+    e0 = rel_l2(phi0.cpu().numpy()[idx], dphi)
+    e1 = rel_l2(phi1.cpu().numpy()[idx], dphi)
+    assert e1 <= 1.05 * e0 + 1e-7

@@ -49,17 +49,27 @@ def parse():
     ap.add_argument("--precision", default="tf32x3", choices=["fp32", "tf32x3", "bf16x3"])
     ap.add_argument("--no-modes", action="store_true", help="skip timing the other M2L precisions")
     ap.add_argument("--p", type=int, default=None, help="override the workload's expansion order")
+    ap.add_argument("--ncrit", type=int, default=None, help="override the workload's ncrit")
+    ap.add_argument("--select", default="plain", choices=["plain", "autotune", "learned"],
+                    help="interaction-type selection of MAC-accepted pairs (hybrid FMM)")
+    ap.add_argument("--no-select-modes", action="store_true",
+                    help="skip timing the other selection modes")
+    ap.add_argument("--train-steps", type=int, default=3000)
+    ap.add_argument("--tune-ncrit", action="store_true",
+                    help="pick ncrit with the measured autotuner before timing (single systems)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
 
 
-def workload(name, p=None):
+def workload(name, p=None, ncrit=None):
     """(parameters, xyz, q, offsets) -- offsets is None for a single system."""
     from paper_1108_5815_gb300 import inputs
     w = dict(inputs.WORKLOADS[name])
     if p is not None:
         w["p"] = p
+    if ncrit is not None:
+        w["ncrit"] = ncrit
     if w["kind"] == "batched":
         x, q, off = inputs.batched_systems(w["nsys"], w["seed"])
         w["n"] = int(off[-1])
@@ -75,7 +85,7 @@ def config_of(w, args):
     else:
         desc = f"{args.workload}: N={w['n']} {w['kind']}, " + ("q=1/N" if w["kind"] == "plummer" else "q~U[-1,1]")
     return {"workload": desc, "N": w["n"], "p": w["p"], "theta": w["theta"], "ncrit": w["ncrit"],
-            "max_depth": w["max_depth"], "m2l": args.precision,
+            "max_depth": w["max_depth"], "m2l": args.precision, "select": args.select,
             "l2_policy": "512 MB buffer written between timed steps"}
 
 
@@ -124,7 +134,7 @@ def run_reference(args):
     if rank != 0:
         return
     from oracle import oracle as O
-    w, x, q, off = workload(args.workload, args.p)
+    w, x, q, off = workload(args.workload, args.p, args.ncrit)
     sample = (lambda: oracle_sample(x, q, w)) if off is None else (lambda: oracle_sample_batched(x, q, off, w))
     for _ in range(args.warmup):
         sample()
@@ -312,14 +322,21 @@ def main():
         dist.init_process_group("nccl", device_id=dev)
     build.build()
 
-    w, x, q, off = workload(args.workload, args.p)
+    w, x, q, off = workload(args.workload, args.p, args.ncrit)
     n = w["n"]
     xd = torch.from_numpy(x).to(dev)
     qd = torch.from_numpy(q).to(dev)
     phi = torch.empty(n, device=dev)
     grad = torch.empty(n, 3, device=dev)
     flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device=dev)  # 512 MB > L2
-    kw = dict(max_depth=w["max_depth"], precision=args.precision)
+    kw = dict(max_depth=w["max_depth"], precision=args.precision, select=args.select)
+    # the learned cost model is trained before timing (samples generated by the
+    # method's own kernels on artificial data, then GPU training); its tables are
+    # measured and cached by the warm-up solves, as the pre-timed tables are
+    cost_model = None
+    if args.select == "learned" or (not args.no_select_modes and rank == 0):
+        cost_model = fmm.cost_model_train(precision=args.precision, p_lo=3, p_hi=12,
+                                          steps=args.train_steps, seed=1)
 
     def solve(stats=False, **over):
         k2 = dict(kw, **over)
@@ -328,6 +345,13 @@ def main():
                                  out=(phi, grad), **k2)
         return fmm.laplace3d_batched(xd, qd, off, w["p"], w["theta"], w["ncrit"], stats=stats,
                                      out=(phi, grad), **k2)
+
+    ncrit_tuning = None
+    if args.tune_ncrit and off is None:
+        cands = (16, 32, 64, 128, 256)
+        best, ms_c = fmm.tune_ncrit(xd, qd, w["p"], w["theta"], cands, **kw)
+        ncrit_tuning = {"candidates_ms": ms_c, "best": best, "workload_ncrit": w["ncrit"]}
+        w["ncrit"] = best
 
     for _ in range(args.warmup):
         solve()
@@ -426,6 +450,29 @@ def main():
             modes[prec] = {"value": n / (m / 1e3), "ms_per_step": m,
                            "accuracy": accuracy(x, q, phi.cpu().numpy(), grad.cpu().numpy(), off=off)}
 
+    # the other selection modes (plain FMM, pre-timed, learned), timed the same way
+    select_modes = {}
+    if rank == 0 and not args.no_select_modes:
+        for sel in ("plain", "autotune", "learned"):
+            if sel == args.select:
+                continue
+            for _ in range(2):
+                solve(select=sel)
+            ms, sts = [], []
+            for k in range(args.steps):
+                flush.fill_(float(k))
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                sts.append(solve(stats=True, select=sel)[2])
+                b.record(stream)
+                b.synchronize()
+                ms.append(a.elapsed_time(b))
+            m = statistics.mean(ms)
+            select_modes[sel] = {"value": n / (m / 1e3), "ms_per_step": m,
+                                 "n_m2l_pairs": sts[-1]["n_m2l_pairs"],
+                                 "n_p2p_interactions": sts[-1]["n_p2p_interactions"],
+                                 "accuracy": accuracy(x, q, phi.cpu().numpy(), grad.cpu().numpy(), off=off)}
+
     # a batch against solving its systems one call at a time
     loop = None
     if rank == 0 and off is not None:
@@ -463,7 +510,8 @@ def main():
                 "config": config_of(w, args), "roofline": roof, "rooflines": rooflines,
                 "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(sum(s["n_launches"] for s in st_list)),
-                "accuracy": acc, "m2l_modes": modes, "per_system_loop": loop,
+                "accuracy": acc, "m2l_modes": modes, "select_modes": select_modes,
+                "cost_model": cost_model, "ncrit_tuning": ncrit_tuning, "per_system_loop": loop,
                 "clocks": clocks, "phases_ms": phases,
                 "counts": {k: st0[k] for k in ("ncells", "nleaves", "depth", "n_p2p_pairs",
                                                "n_p2p_interactions", "n_m2l_pairs",

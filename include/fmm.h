@@ -218,6 +218,15 @@ fmm_status fmm_selection_table(int select_mode, int p, double theta, int precisi
  * full-batch Adam steps on the GPU.  info may be NULL. */
 fmm_status fmm_cost_model_train(int precision_mode, int p_lo, int p_hi, int steps, uint64_t seed,
                                 fmm_cost_model_info *info);
+/* The measured autotuner for N_crit (Results section: N_crit is set so that the
+ * near- and far-field loads balance; the hybrid selection reduces but does not
+ * remove the dependence, because the expansion passes scale with the number of
+ * cells).  Solves the given system once per candidate with the options' M2L
+ * precision and selection mode, times each solve with events (best of two after
+ * a sizing solve) and returns the fastest candidate in *best; ms[k] (may be
+ * NULL) receives candidate k's time.  Outputs of the solves are discarded. */
+fmm_status fmm_tune_ncrit(const float *xyz, const float *q, int64_t N, int p, double theta, void *stream,
+                          const fmm_options *opt, const int *candidates, int ncand, float *ms, int *best);
 /* Parameters as FP32 values: master != 0 gives the FP32 master copy, else the
  * FP16 copy the forward pass uses.  params holds n >= FMM_COST_MODEL_PARAMS floats. */
 fmm_status fmm_cost_model_get(float *params, int64_t n, int master);

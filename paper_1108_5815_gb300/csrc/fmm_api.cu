@@ -977,6 +977,40 @@ fmm_status fmm_selection_table(int select_mode, int p, double theta, int precisi
     });
 }
 
+fmm_status fmm_tune_ncrit(const float *xyz, const float *q, int64_t N, int p, double theta, void *stream,
+                          const fmm_options *opt, const int *candidates, int ncand, float *ms, int *best)
+{
+    return guarded([&] {
+        if (!candidates || ncand < 1 || !best) throw Error{FMM_ERR_ARG, "need candidates, ncand >= 1 and best"};
+        for (int k = 0; k < ncand; ++k)
+            if (candidates[k] < 1) throw Error{FMM_ERR_ARG, "every candidate ncrit must be >= 1"};
+        const fmm_options o = resolve_opts(opt);
+        validate(xyz, q, N, p, theta, 1, xyz, xyz, o);
+        Workspace &ws = workspace_for_current_device();
+        std::lock_guard<std::mutex> lk(ws.mu);
+        const uint8_t *sel = selection_table(ws, o, p, theta);
+        cudaStream_t st = (cudaStream_t)stream;
+        float *phi = need<float>(ws, "tune_phi", (size_t)N, st);
+        float *grad = need<float>(ws, "tune_grad", 3 * (size_t)N, st);
+        const int64_t off[2] = {0, N};
+        float best_ms = 1e30f;
+        for (int k = 0; k < ncand; ++k) {
+            float t = 1e30f;
+            for (int rep = 0; rep < 3; ++rep) {
+                fmm_stats s{};
+                solve_locked(ws, xyz, q, N, 1, off, p, theta, candidates[k], phi, grad, st, o, &s, sel);
+                if (rep > 0) t = std::min(t, s.ms_total);  // the first solve sizes the buffers
+            }
+            if (ms) ms[k] = t;
+            if (t < best_ms) {
+                best_ms = t;
+                *best = candidates[k];
+            }
+        }
+        ws.have_solve = false;
+    });
+}
+
 fmm_status fmm_cost_model_train(int precision_mode, int p_lo, int p_hi, int steps, uint64_t seed,
                                 fmm_cost_model_info *info)
 {

@@ -30,7 +30,7 @@ ABI_SYMBOLS = ("fmm_default_options", "fmm_laplace3d", "fmm_laplace3d_ex", "fmm_
                "fmm_direct", "fmm_export", "fmm_last_error", "fmm_morton_sort_noalloc",
                "fmm_selection_table", "fmm_cost_model_train", "fmm_cost_model_get",
                "fmm_cost_model_set", "fmm_cost_model_grad", "fmm_cost_model_adam_step",
-               "fmm_cost_model_predict", "fmm_cost_model_samples")
+               "fmm_cost_model_predict", "fmm_cost_model_samples", "fmm_tune_ncrit")
 COST_MODEL_PARAMS = 4610
 
 
@@ -107,11 +107,13 @@ def load(path: str | None = None):
         L.fmm_cost_model_adam_step.argtypes = [vp, vp, vp, i64, ctypes.c_float, vp]
         L.fmm_cost_model_predict.argtypes = [vp, i64, vp]
         L.fmm_cost_model_samples.argtypes = [vp, vp, vp, i64, ctypes.POINTER(i64)]
+        L.fmm_tune_ncrit.argtypes = [vp, vp, i64, ctypes.c_int, ctypes.c_double, vp, ctypes.POINTER(Options),
+                                     vp, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_int)]
         for name in ("fmm_laplace3d", "fmm_laplace3d_ex", "fmm_laplace3d_host", "fmm_direct",
                      "fmm_export", "fmm_laplace3d_batched", "fmm_selection_table",
                      "fmm_cost_model_train", "fmm_cost_model_get", "fmm_cost_model_set",
                      "fmm_cost_model_grad", "fmm_cost_model_adam_step", "fmm_cost_model_predict",
-                     "fmm_cost_model_samples"):
+                     "fmm_cost_model_samples", "fmm_tune_ncrit"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
         return L
@@ -363,3 +365,21 @@ def cost_model_samples():
     if k:
         _check(load().fmm_cost_model_samples(x.ctypes.data, t.ctypes.data, m.ctypes.data, k, ctypes.byref(n)))
     return x, t, m
+
+
+def tune_ncrit(xyz, q, p: int, theta: float, candidates=(16, 32, 64, 128, 256), *, max_depth: int = 0,
+               precision: str = "fp32", select="plain"):
+    """Measured autotuner for ncrit: (best, {ncrit: ms}) over the candidates."""
+    import torch
+    n = int(xyz.shape[0])
+    xyz = _dev_f32(xyz, (n, 3), "xyz")
+    q = _dev_f32(q, (n,), "q")
+    c = np.ascontiguousarray(np.asarray(candidates, dtype=np.int32))
+    ms = np.zeros(len(c), dtype=np.float32)
+    best = ctypes.c_int(0)
+    with torch.cuda.device(xyz.device):
+        o = _options(max_depth, precision, select)
+        _check(load().fmm_tune_ncrit(xyz.data_ptr(), q.data_ptr(), n, p, float(theta),
+                                     _stream_ptr(torch, xyz.device), ctypes.byref(o), c.ctypes.data,
+                                     len(c), ms.ctypes.data, ctypes.byref(best)))
+    return best.value, {int(k): float(v) for k, v in zip(c, ms)}

@@ -102,7 +102,7 @@ def test_batched_tensor_modes(precision):
         if b - a < 100:
             continue
         ophi, ograd = O.Fmm(x[a:b], q[a:b], 8, 0.5, 32).evaluate()
-        assert rel_l2(phi[a:b], ophi) < 5e-5 and rel_l2(grad[a:b], ograd) < 5e-5
+        assert rel_l2(phi[a:b], ophi) < 1e-5 and rel_l2(grad[a:b], ograd) < 1e-5
 
 
 def test_batched_argument_errors():

@@ -170,3 +170,12 @@ def test_learned_selection_gains_where_the_fmm_is_out_of_balance(trained):
     e0 = rel_l2(phi0.cpu().numpy()[idx], dphi)
     e1 = rel_l2(phi1.cpu().numpy()[idx], dphi)
     assert e1 <= 1.05 * e0 + 1e-7
+
+
+def test_tune_ncrit_returns_the_fastest_candidate():
+    torch = torch_cuda()
+    from paper_1108_5815_gb300 import fmm
+    x, q = inputs.make("plummer", 200000, 3)
+    xt, qt = torch.from_numpy(x).cuda(), torch.from_numpy(q).cuda()
+    best, ms = fmm.tune_ncrit(xt, qt, 6, 0.5, (8, 32, 128), select="autotune")
+    assert best in (8, 32, 128) and ms[best] == min(ms.values()) and all(v > 0 for v in ms.values())

@@ -67,8 +67,8 @@ def test_sampled_targets_vs_direct(solved):
 @pytest.mark.parametrize("precision", ["tf32x3", "bf16x3"])
 def test_tensor_core_modes_at_full_size(solved, precision):
     """The tensor-core M2L modes on the same workload: the metric's 1e-4 against the
-    FP64 direct sum, and 5e-5 against the oracle (their accumulation error is about
-    1e-5, see the tolerance reading in the design notes)."""
+    FP64 direct sum, and the FP32 path's 1e-5 against the oracle (main and
+    correction products accumulate separately and are summed with round-to-nearest)."""
     x, q, phi0, grad0, st, ex, f = solved
     phi, grad = gpu_solve(x, q, W["p"], W["theta"], W["ncrit"], max_depth=W["max_depth"],
                           precision=precision)
@@ -80,4 +80,4 @@ def test_tensor_core_modes_at_full_size(solved, precision):
     pick = leaves[inputs.sample_indices(len(leaves), 32, 79)]
     pos, ophi, ograd = f.evaluate_leaves(pick)
     orig = f.sorted()[1][pos]
-    assert rel_l2(phi[orig], ophi) < 5e-5 and rel_l2(grad[orig], ograd) < 5e-5
+    assert rel_l2(phi[orig], ophi) < 1e-5 and rel_l2(grad[orig], ograd) < 1e-5

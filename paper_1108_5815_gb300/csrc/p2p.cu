@@ -12,6 +12,12 @@
 // grad += q y^3 d.  Pairs at r = 0 (the particle itself, coincident points)
 // contribute nothing: rsqrt(0) = inf makes the Newton step NaN and
 // max(NaN, 0) = 0 removes it without a branch.
+// Each lane takes its target against two sources at a time with the packed
+// FP32x2 instructions (add/sub/mul/fma.rn.f32x2): one instruction does the same
+// operation for both sources, which halves the issue slots of the arithmetic;
+// only the rsqrt and the NaN guard stay scalar.  Sources are staged in shared
+// memory as four arrays (x, y, z, q), so a pair of consecutive sources is one
+// 64-bit load per component.
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -24,6 +30,84 @@ __device__ __forceinline__ float rsqrt_approx(float x)
     float y;
     asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
+}
+
+// Two packed FP32 values (first in the low half).
+typedef unsigned long long f2;
+
+__device__ __forceinline__ f2 f2pack(float a, float b)
+{
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void f2unpack(f2 v, float &a, float &b)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ f2 f2add(f2 a, f2 b)
+{
+    f2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2 f2sub(f2 a, f2 b)
+{
+    f2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2 f2mul(f2 a, f2 b)
+{
+    f2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2 f2fma(f2 a, f2 b, f2 c)
+{
+    f2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
+struct Target2 {
+    f2 x, y, z;          // the target's coordinates in both halves
+    f2 mhalf, threehalf; // (-1/2, -1/2), (3/2, 3/2)
+};
+
+__device__ __forceinline__ Target2 target2(float4 xi)
+{
+    return {f2pack(xi.x, xi.x), f2pack(xi.y, xi.y), f2pack(xi.z, xi.z), f2pack(-0.5f, -0.5f),
+            f2pack(1.5f, 1.5f)};
+}
+
+// The target against two sources (packed x, y, z, q); accumulators packed per source.
+__device__ __forceinline__ void p2p_interact2(const Target2 &T, f2 sx, f2 sy, f2 sz, f2 sq, f2 &phi,
+                                              f2 &gx, f2 &gy, f2 &gz)
+{
+    const f2 dx = f2sub(sx, T.x), dy = f2sub(sy, T.y), dz = f2sub(sz, T.z);
+    const f2 r2 = f2fma(dz, dz, f2fma(dy, dy, f2mul(dx, dx)));
+    float ra, rb;
+    f2unpack(r2, ra, rb);
+    f2 y = f2pack(rsqrt_approx(ra), rsqrt_approx(rb));
+    const f2 t = f2mul(f2mul(r2, y), y);
+    y = f2mul(y, f2fma(T.mhalf, t, T.threehalf));
+    float ya, yb;
+    f2unpack(y, ya, yb);
+    y = f2pack(fmaxf(ya, 0.f), fmaxf(yb, 0.f));
+    const f2 qy = f2mul(sq, y);
+    phi = f2add(phi, qy);
+    const f2 qy3 = f2mul(f2mul(qy, y), y);
+    gx = f2fma(qy3, dx, gx);
+    gy = f2fma(qy3, dy, gy);
+    gz = f2fma(qy3, dz, gz);
+}
+
+__device__ __forceinline__ float f2sum(f2 v)
+{
+    float a, b;
+    f2unpack(v, a, b);
+    return a + b;
 }
 
 __device__ __forceinline__ void p2p_interact(float xi, float yi, float zi, float4 s, float &phi,
@@ -46,12 +130,12 @@ __device__ __forceinline__ void p2p_interact(float xi, float yi, float zi, float
 }  // namespace
 
 // Stages the next chunk of up to 32 sources of the target's source stream (the
-// concatenated particle ranges of its P2P source leaves) into sh[0..32), padded
-// with zero charges.  (r, o) = current source leaf in the list and offset in it;
-// returns false when the stream is exhausted.
+// concatenated particle ranges of its P2P source cells) into sh = x[32], y[32],
+// z[32], q[32], padded with zero charges at the origin.  (r, o) = current source
+// cell in the list and offset in it; returns false when the stream is exhausted.
 __device__ __forceinline__ bool load_chunk(const int *__restrict__ slist, int cnt,
                                            const CellArrays &c, const float4 *__restrict__ pts,
-                                           float4 *sh, int lane, int &r, int &o)
+                                           float *sh, int lane, int &r, int &o)
 {
     if (r >= cnt) return false;
     const int rk = r + lane;
@@ -76,7 +160,11 @@ __device__ __forceinline__ bool load_chunk(const int *__restrict__ slist, int cn
     const unsigned le = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);
     const int k = __popc(starts & le) - 1;
     const int kb = __shfl_sync(0xffffffffu, beg, k), ks = __shfl_sync(0xffffffffu, S0, k);
-    sh[lane] = lane < total ? pts[kb + (lane - ks)] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 pj = lane < total ? pts[kb + (lane - ks)] : make_float4(0.f, 0.f, 0.f, 0.f);
+    sh[lane] = pj.x;
+    sh[32 + lane] = pj.y;
+    sh[64 + lane] = pj.z;
+    sh[96 + lane] = pj.w;
     if (total <= 32) {
         // every range of the window is consumed (a full window of 32 ranges
         // totals at least 32 elements, so fewer than 32 means the list ended)
@@ -100,73 +188,87 @@ __device__ __forceinline__ bool load_chunk(const int *__restrict__ slist, int cn
     return true;
 }
 
-// 32 sources from shared memory against one target, two accumulator sets
-// (even/odd sources) to shorten the dependency chains.
-__device__ __forceinline__ void p2p_chunk32(const float4 &xi, const float4 *buf, float4 &a0, float4 &a1)
+// The staged 32 sources against one target: pairs of sources per packed
+// instruction, two accumulator sets (sources 4k, 4k+1 and 4k+2, 4k+3).
+struct Acc2 {
+    f2 phi, gx, gy, gz;
+};
+
+__device__ __forceinline__ void p2p_chunk32(const Target2 &T, const float *sh, Acc2 &a, Acc2 &b)
 {
 #pragma unroll
-    for (int jj = 0; jj < 32; jj += 2) {
-        p2p_interact(xi.x, xi.y, xi.z, buf[jj], a0.x, a0.y, a0.z, a0.w);
-        p2p_interact(xi.x, xi.y, xi.z, buf[jj + 1], a1.x, a1.y, a1.z, a1.w);
+    for (int jj = 0; jj < 32; jj += 4) {
+        const ulonglong2 vx = *reinterpret_cast<const ulonglong2 *>(sh + jj);
+        const ulonglong2 vy = *reinterpret_cast<const ulonglong2 *>(sh + 32 + jj);
+        const ulonglong2 vz = *reinterpret_cast<const ulonglong2 *>(sh + 64 + jj);
+        const ulonglong2 vq = *reinterpret_cast<const ulonglong2 *>(sh + 96 + jj);
+        p2p_interact2(T, vx.x, vy.x, vz.x, vq.x, a.phi, a.gx, a.gy, a.gz);
+        p2p_interact2(T, vx.y, vy.y, vz.y, vq.y, b.phi, b.gx, b.gy, b.gz);
     }
 }
 
 // One warp per target leaf.  Targets go 32 at a time, one per lane; the last
-// r <= 16 targets are processed with the sources split into g = floor(32 / r)
-// interleaved subsets, so that r * g lanes stay busy, and the g partial sums are
-// added in shared memory.
+// r <= 16 targets are processed with the 32 staged sources split into
+// g = floor(32 / r) contiguous runs of an even length, so that r * g lanes stay
+// busy, and the g partial sums are added in shared memory.
 __device__ __forceinline__ void p2p_leaf(const CellArrays &c, const ListArrays &L, int T,
                                          const float4 *__restrict__ pts, float4 *__restrict__ near,
-                                         float4 *buf, float4 *redbuf, int lane)
+                                         float *sh, float4 *redbuf, int lane)
 {
     const int b = c.begin[T], e = c.end[T];
     const int *slist = L.p2p_src + L.p2p_off[T];
     const int cnt = L.p2p_cnt[T];
+    const f2 zero = 0ull;
     int tb = b;
     // full passes, and a last pass of 17..31 targets (g = 1), one target per lane
     while (tb < e && (e - tb >= 32 || 2 * (e - tb) > 32)) {
         const bool valid = tb + lane < e;
-        const float4 xi = pts[valid ? tb + lane : tb];
-        float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
+        const Target2 Tg = target2(pts[valid ? tb + lane : tb]);
+        Acc2 a0 = {zero, zero, zero, zero}, a1 = a0;
         int r = 0, o = 0;
-        while (load_chunk(slist, cnt, c, pts, buf, lane, r, o)) {
+        while (load_chunk(slist, cnt, c, pts, sh, lane, r, o)) {
             __syncwarp();
-            p2p_chunk32(xi, buf, a0, a1);
+            p2p_chunk32(Tg, sh, a0, a1);
             __syncwarp();
         }
         // accumulators hold (phi, gx, gy, gz)
-        if (valid) near[tb + lane] = make_float4(a0.x + a1.x, a0.y + a1.y, a0.z + a1.z, a0.w + a1.w);
+        if (valid)
+            near[tb + lane] = make_float4(f2sum(a0.phi) + f2sum(a1.phi), f2sum(a0.gx) + f2sum(a1.gx),
+                                          f2sum(a0.gy) + f2sum(a1.gy), f2sum(a0.gz) + f2sum(a1.gz));
         tb += 32;
     }
     const int rem = e - tb;
     if (rem > 0) {
-        // 1 <= rem <= 16: g >= 2 interleaved source subsets
+        // 1 <= rem <= 16: g >= 2 runs of cs sources (cs even, g * cs >= 32)
         const int g = 32 / rem;
+        const int cs = 2 * ((16 + g - 1) / g);
         const int t = lane % rem, sub = lane / rem;
-        const bool active = sub < g;
-        const float4 xi = pts[tb + t];
-        float phi = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+        const int j0 = sub < g ? sub * cs : 32, j1 = min(32, j0 + cs);
+        const Target2 Tg = target2(pts[tb + t]);
+        Acc2 a = {zero, zero, zero, zero};
         int r = 0, o = 0;
-        while (load_chunk(slist, cnt, c, pts, buf, lane, r, o)) {
+        while (load_chunk(slist, cnt, c, pts, sh, lane, r, o)) {
             __syncwarp();
-            if (active) {
 #pragma unroll 4
-                for (int jj = sub; jj < 32; jj += g) p2p_interact(xi.x, xi.y, xi.z, buf[jj], phi, gx, gy, gz);
-            }
+            for (int jj = j0; jj < j1; jj += 2)
+                p2p_interact2(Tg, *reinterpret_cast<const f2 *>(sh + jj),
+                              *reinterpret_cast<const f2 *>(sh + 32 + jj),
+                              *reinterpret_cast<const f2 *>(sh + 64 + jj),
+                              *reinterpret_cast<const f2 *>(sh + 96 + jj), a.phi, a.gx, a.gy, a.gz);
             __syncwarp();
         }
-        redbuf[lane] = make_float4(phi, gx, gy, gz);
+        redbuf[lane] = make_float4(f2sum(a.phi), f2sum(a.gx), f2sum(a.gy), f2sum(a.gz));
         __syncwarp();
         if (lane < rem) {
-            float4 a = redbuf[lane];
+            float4 v0 = redbuf[lane];
             for (int k = 1; k < g; ++k) {
                 const float4 v = redbuf[lane + k * rem];
-                a.x += v.x;
-                a.y += v.y;
-                a.z += v.z;
-                a.w += v.w;
+                v0.x += v.x;
+                v0.y += v.y;
+                v0.z += v.z;
+                v0.w += v.w;
             }
-            near[tb + lane] = a;
+            near[tb + lane] = v0;
         }
         __syncwarp();
     }
@@ -179,7 +281,7 @@ __global__ void __launch_bounds__(128)
     k_p2p(CellArrays c, ListArrays L, const int *__restrict__ leaves, int nleaves,
           const float4 *__restrict__ pts, float4 *__restrict__ near, int *__restrict__ counter)
 {
-    __shared__ float4 sh[4][32];
+    __shared__ __align__(16) float sh[4][128];
     __shared__ float4 red[4][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (;;) {

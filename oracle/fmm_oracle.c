@@ -49,7 +49,9 @@
  *      below its leading bit (e = floor(log2 n)).  The table is an input: how it
  *      was obtained (pre-timed kernels, a learned cost model) does not enter the
  *      traversal.  A P2P pair may have non-leaf cells; it acts on all particles
- *      of both.
+ *      of both.  Table value 2 selects the cell-particle interaction (M2P, the
+ *      treecode kernel: the source multipole evaluated at every particle of
+ *      the target cell); a table of all 2 is the paper's treecode.
  *
  * Harmonics (signed m, Condon-Shortley P_n^m):
  *   R_n^m(x) = r^n P_n^m(cos t) e^{i m f} / (n+m)!      (regular)
@@ -69,7 +71,8 @@
  *   L2L  L'_j^l = sum_{n>=j,m} L_n^m R_{n-j}^{m-l}(c' - c)
  *   L2P  phi = sum L_n^m R_n^m(x - c);  d/dz phi = sum L_n^m R_{n-1}^m;
  *        (d/dx + i d/dy) phi = sum L_n^m R_{n-1}^{m+1}
- *   M2P  phi = sum M_n^m I_n^m(x - c)
+ *   M2P  phi = sum M_n^m I_n^m(x - c);  d/dz I_n^m = -I_{n+1}^m;
+ *        (d/dx + i d/dy) I_n^m = I_{n+1}^{m+1}
  * Coefficients are stored for all signed m at index n*n + n + m.
  *
  * Build: gcc -O2 -std=c11 -ffp-contract=off -fopenmp -fPIC -shared.
@@ -250,6 +253,28 @@ double orc_m2p(const double c[3], int p, const cplx *M, const double x[3])
     return creal(acc);
 }
 
+/* M2P with the gradient: phi and grad at x from the multipole M about c.
+ * The derivatives of the irregular harmonics raise the degree by one. */
+void orc_m2p_grad(const double c[3], int p, const cplx *M, const double x[3], double *phi,
+                  double g[3])
+{
+    cplx *Ih = malloc(sizeof(cplx) * nterms(p + 1));
+    double d[3] = {x[0] - c[0], x[1] - c[1], x[2] - c[2]};
+    orc_irregular(d, p + 1, Ih);
+    cplx ph = 0.0, dz = 0.0, dplus = 0.0;
+    for (int n = 0; n <= p; ++n)
+        for (int m = -n; m <= n; ++m) {
+            ph += M[hidx(n, m)] * Ih[hidx(n, m)];
+            dz -= M[hidx(n, m)] * Ih[hidx(n + 1, m)];
+            dplus += M[hidx(n, m)] * Ih[hidx(n + 1, m + 1)];
+        }
+    *phi = creal(ph);
+    g[0] = creal(dplus);
+    g[1] = cimag(dplus);
+    g[2] = creal(dz);
+    free(Ih);
+}
+
 /* ------------------------------------------------------------------ */
 /* Direct summation                                                    */
 /* ------------------------------------------------------------------ */
@@ -382,8 +407,8 @@ typedef struct {
     int *nchild;
     int depth;
     /* interaction lists */
-    int64_t nm2l, np2p, cap_m2l, cap_p2p;
-    int64_t *m2l_t, *m2l_s, *p2p_t, *p2p_s;
+    int64_t nm2l, np2p, cap_m2l, cap_p2p, nm2p, cap_m2p;
+    int64_t *m2l_t, *m2l_s, *p2p_t, *p2p_s, *m2p_t, *m2p_s;
     /* expansions */
     cplx *M, *L;
     int upward_done;
@@ -518,14 +543,15 @@ int orc_count_bucket(int64_t n)
     return 3 + 4 * (e - 2) + (int)((n >> (e - 2)) & 3);
 }
 
-/* Interaction type of an accepted pair (R9): 1 = particle-particle. */
-static int choose_p2p(const orc_fmm *f, int64_t T, int64_t S)
+/* Interaction type of an accepted pair (R9): 0 = cell-cell, 1 = particle-particle,
+ * 2 = cell-particle. */
+static int choose_kind(const orc_fmm *f, int64_t T, int64_t S)
 {
     if (!f->sel)
         return 0;
     int bt = orc_count_bucket(f->end[T] - f->begin[T]);
     int bs = orc_count_bucket(f->end[S] - f->begin[S]);
-    return f->sel[bt * ORC_SEL_NB + bs] != 0;
+    return f->sel[bt * ORC_SEL_NB + bs];
 }
 
 /* interact(T,S) of reading R4. */
@@ -541,8 +567,11 @@ static void interact(orc_fmm *f, pairstack *st, int64_t T, int64_t S)
         return;
     }
     if (mac_accept(f, T, S)) {
-        if (choose_p2p(f, T, S))
+        int kind = choose_kind(f, T, S);
+        if (kind == 1)
             push_pair(&f->p2p_t, &f->p2p_s, &f->np2p, &f->cap_p2p, T, S);
+        else if (kind == 2)
+            push_pair(&f->m2p_t, &f->m2p_s, &f->nm2p, &f->cap_m2p, T, S);
         else
             push_pair(&f->m2l_t, &f->m2l_s, &f->nm2l, &f->cap_m2l, T, S);
     } else if (is_leaf(f, T) && is_leaf(f, S))
@@ -717,6 +746,29 @@ static void p2p_leaf(const orc_fmm *f, int64_t T, const int64_t *off, const int6
     }
 }
 
+/* Cell-particle far field for the particles of leaf T: the multipoles of the
+ * M2P sources of T and of its ancestors (reading R9). */
+static void m2p_leaf(const orc_fmm *f, int64_t T, const int64_t *off, const int64_t *idx,
+                     double *phi, double *grad, int64_t obase)
+{
+    const int P2 = nterms(f->p);
+    for (int64_t A = T; A >= 0; A = f->parent[A]) {
+        for (int64_t k = off[A]; k < off[A + 1]; ++k) {
+            int64_t S = f->m2p_s[idx[k]];
+            double cs[3];
+            cell_centre(f, S, cs);
+            for (int64_t i = f->begin[T]; i < f->end[T]; ++i) {
+                double ph, g[3];
+                orc_m2p_grad(cs, f->p, f->M + (size_t)S * P2, f->x + 3 * i, &ph, g);
+                phi[i - obase] += ph;
+                grad[3 * (i - obase)] += g[0];
+                grad[3 * (i - obase) + 1] += g[1];
+                grad[3 * (i - obase) + 2] += g[2];
+            }
+        }
+    }
+}
+
 /* Far field for the particles of leaf T from its local expansion. */
 static void l2p_leaf(const orc_fmm *f, int64_t T, const cplx *L, double *phi, double *grad,
                      int64_t obase)
@@ -770,15 +822,20 @@ void orc_fmm_evaluate(orc_fmm *f)
     f->phi = calloc(f->N, sizeof(double));
     f->grad = calloc(3 * f->N, sizeof(double));
     csr_by_target(f->ncells, f->np2p, f->p2p_t, &off, &idx);
+    int64_t *qoff, *qidx;
+    csr_by_target(f->ncells, f->nm2p, f->m2p_t, &qoff, &qidx);
 #pragma omp parallel for schedule(dynamic, 4)
     for (int64_t T = 0; T < f->ncells; ++T) {
         if (!is_leaf(f, T))
             continue;
         l2p_leaf(f, T, f->L + (size_t)T * P2, f->phi, f->grad, 0);
+        m2p_leaf(f, T, qoff, qidx, f->phi, f->grad, 0);
         p2p_leaf(f, T, off, idx, f->phi, f->grad, 0);
     }
     free(off);
     free(idx);
+    free(qoff);
+    free(qidx);
 }
 
 /* Evaluation restricted to the particles of the given leaves: the local
@@ -790,9 +847,10 @@ void orc_fmm_evaluate_leaves(orc_fmm *f, int64_t nl, const int64_t *leaves, doub
 {
     orc_fmm_upward(f);
     const int P2 = nterms(f->p);
-    int64_t *moff, *midx, *poff, *pidx;
+    int64_t *moff, *midx, *poff, *pidx, *qoff, *qidx;
     csr_by_target(f->ncells, f->nm2l, f->m2l_t, &moff, &midx);
     csr_by_target(f->ncells, f->np2p, f->p2p_t, &poff, &pidx);
+    csr_by_target(f->ncells, f->nm2p, f->m2p_t, &qoff, &qidx);
     int64_t *base = malloc(sizeof(int64_t) * (nl + 1));
     base[0] = 0;
     for (int64_t a = 0; a < nl; ++a)
@@ -832,6 +890,7 @@ void orc_fmm_evaluate_leaves(orc_fmm *f, int64_t nl, const int64_t *leaves, doub
             positions[base[a] + i] = f->begin[T] + i;
         }
         l2p_leaf(f, T, Lc, ph, gr, f->begin[T]);
+        m2p_leaf(f, T, qoff, qidx, ph, gr, f->begin[T]);
         p2p_leaf(f, T, poff, pidx, ph, gr, f->begin[T]);
         free(Lc);
         free(Ln);
@@ -841,6 +900,8 @@ void orc_fmm_evaluate_leaves(orc_fmm *f, int64_t nl, const int64_t *leaves, doub
     free(midx);
     free(poff);
     free(pidx);
+    free(qoff);
+    free(qidx);
 }
 
 void orc_fmm_destroy(orc_fmm *f)
@@ -862,6 +923,8 @@ void orc_fmm_destroy(orc_fmm *f)
     free(f->m2l_s);
     free(f->p2p_t);
     free(f->p2p_s);
+    free(f->m2p_t);
+    free(f->m2p_s);
     free(f->M);
     free(f->L);
     free(f->phi);
@@ -872,6 +935,15 @@ void orc_fmm_destroy(orc_fmm *f)
 /* ------------------------------------------------------------------ */
 /* Accessors for the Python wrapper                                    */
 /* ------------------------------------------------------------------ */
+
+void orc_fmm_m2p_list(const orc_fmm *f, int64_t *n, int64_t *t, int64_t *s)
+{
+    *n = f->nm2p;
+    if (t)
+        memcpy(t, f->m2p_t, sizeof(int64_t) * f->nm2p);
+    if (s)
+        memcpy(s, f->m2p_s, sizeof(int64_t) * f->nm2p);
+}
 
 void orc_fmm_sizes(const orc_fmm *f, int64_t out[6])
 {
@@ -984,6 +1056,11 @@ void orc_l2p_ri(const double c[3], int p, const double *L, const double x[3], do
 {
     orc_l2p(c, p, (const cplx *)L, x, &out4[0], &out4[1]);
 }
+void orc_m2p_grad_ri(const double c[3], int p, const double *M, const double x[3], double *out4)
+{
+    orc_m2p_grad(c, p, (const cplx *)M, x, out4, out4 + 1);
+}
+
 double orc_m2p_ri(const double c[3], int p, const double *M, const double x[3])
 {
     return orc_m2p(c, p, (const cplx *)M, x);

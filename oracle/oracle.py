@@ -74,6 +74,8 @@ def lib():
             L.orc_m2l_ri.argtypes = [_D, _D, ctypes.c_int, _D, _D]
             L.orc_l2l_ri.argtypes = [_D, _D, ctypes.c_int, _D, _D]
             L.orc_l2p_ri.argtypes = [_D, ctypes.c_int, _D, _D, _D]
+            L.orc_m2p_grad_ri.argtypes = [_D, ctypes.c_int, _D, _D, _D]
+            L.orc_fmm_m2p_list.argtypes = [ctypes.c_void_p, _I64, _I64, _I64]
             L.orc_m2p_ri.restype = ctypes.c_double
             L.orc_m2p_ri.argtypes = [_D, ctypes.c_int, _D, _D]
             _lib = L
@@ -196,6 +198,14 @@ def l2p(c, p, L, x):
     return out[0], out[1:4].copy()
 
 
+def m2p_grad(c, p, M, x):
+    """(phi, grad[3]) at x from the multipole M about c."""
+    M = np.ascontiguousarray(M, dtype=np.complex128)
+    out = np.zeros(4)
+    lib().orc_m2p_grad_ri(_d(_f64(c, (3,))), p, _d(M.view(np.float64)), _d(_f64(x, (3,))), _d(out))
+    return float(out[0]), out[1:].copy()
+
+
 def m2p(c, p, M, x):
     M = np.ascontiguousarray(M, dtype=np.complex128)
     return lib().orc_m2p_ri(_d(_f64(c, (3,))), p, _d(M.view(np.float64)), _d(_f64(x, (3,))))
@@ -266,6 +276,15 @@ class Fmm:
         lib().orc_fmm_lists(self._h, mt.ctypes.data_as(_I64), ms.ctypes.data_as(_I64),
                             pt.ctypes.data_as(_I64), ps.ctypes.data_as(_I64))
         return dict(m2l_t=mt, m2l_s=ms, p2p_t=pt, p2p_s=ps)
+
+    def m2p_list(self):
+        """Cell-particle pairs (target cell, source cell) chosen by the selection table."""
+        n = ctypes.c_int64(0)
+        lib().orc_fmm_m2p_list(self._h, ctypes.byref(n), None, None)
+        t = np.zeros(n.value, dtype=np.int64)
+        s = np.zeros(n.value, dtype=np.int64)
+        lib().orc_fmm_m2p_list(self._h, ctypes.byref(n), t.ctypes.data_as(_I64), s.ctypes.data_as(_I64))
+        return t, s
 
     def upward(self):
         lib().orc_fmm_upward(self._h)

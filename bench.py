@@ -450,10 +450,11 @@ def main():
             modes[prec] = {"value": n / (m / 1e3), "ms_per_step": m,
                            "accuracy": accuracy(x, q, phi.cpu().numpy(), grad.cpu().numpy(), off=off)}
 
-    # the other selection modes (plain FMM, pre-timed, learned), timed the same way
+    # the other selection modes (plain FMM, pre-timed, learned, and the treecode: cell-particle
+    # for every accepted pair), timed the same way
     select_modes = {}
     if rank == 0 and not args.no_select_modes:
-        for sel in ("plain", "autotune", "learned"):
+        for sel in ("plain", "autotune", "learned", "treecode"):
             if sel == args.select:
                 continue
             for _ in range(2):
@@ -470,6 +471,7 @@ def main():
             m = statistics.mean(ms)
             select_modes[sel] = {"value": n / (m / 1e3), "ms_per_step": m,
                                  "n_m2l_pairs": sts[-1]["n_m2l_pairs"],
+                                 "n_m2p_pairs": sts[-1]["n_m2p_pairs"],
                                  "n_p2p_interactions": sts[-1]["n_p2p_interactions"],
                                  "accuracy": accuracy(x, q, phi.cpu().numpy(), grad.cpu().numpy(), off=off)}
 

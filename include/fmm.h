@@ -66,7 +66,9 @@ enum {
  * minimise the cost, and particle-particle interactions may be taken above the
  * leaf level).  Every mode is exact in the sense that a pair not taken as M2L is
  * taken as P2P, so the far-field error can only shrink.
- * The choice is a table sel[b(n_t) * FMM_SELECT_NB + b(n_s)] (0 = M2L, 1 = P2P)
+ * The choice is a table sel[b(n_t) * FMM_SELECT_NB + b(n_s)] (0 = M2L, 1 = P2P,
+ * 2 = M2P: the source multipole evaluated at every target particle, the treecode's
+ * cell-particle interaction)
  * over the particle counts n_t, n_s of the target and source cells, with the
  * count bucket b(n) = n - 1 for n < 4, else 3 + 4(e - 2) + ((n >> (e - 2)) & 3),
  * e = floor(log2 n) (four buckets per octave). */
@@ -75,7 +77,9 @@ enum {
     FMM_SELECT_AUTOTUNE = 1, /* table from kernels timed on artificial cells (kernel
                                 pre-calculation), measured once per device, p and precision */
     FMM_SELECT_LEARNED = 2,  /* table from the learned cost model (fmm_cost_model_*) */
-    FMM_SELECT_TABLE = 3     /* the caller's table in fmm_options.select_table */
+    FMM_SELECT_TABLE = 3,    /* the caller's table in fmm_options.select_table */
+    FMM_SELECT_TREECODE = 4  /* M2P for every accepted pair: the paper's treecode (Results
+                                section), on the same tree and traversal */
 };
 #define FMM_SELECT_NB 128
 
@@ -97,6 +101,7 @@ typedef struct {
     int64_t n_launches;                      /* kernels this library launched for the solve */
     /* per-phase device time in ms (measured with events when stats are requested) */
     float ms_tree, ms_upward, ms_traverse, ms_m2l, ms_downward, ms_p2p, ms_total;
+    int64_t n_m2p_pairs; /* (target leaf, source cell) cell-particle pairs */
 } fmm_stats;
 
 /* Fills *opt with the defaults (max_depth 21, FP32 M2L, plain FMM, deterministic). */
@@ -156,6 +161,9 @@ fmm_status fmm_direct(const float *xyz, const float *q, int64_t N, float *phi, f
  *   FMM_EXPORT_LOCAL      float[ncells][P2pad] unit-scaled local expansions
  *   FMM_EXPORT_SELECT     uint8[FMM_SELECT_NB][FMM_SELECT_NB] selection table the
  *                         solve used (all zero for the plain FMM)
+ *   FMM_EXPORT_M2P        int32[n][2]: target leaf, source cell of the cell-particle
+ *                         pairs (a pair chosen above the leaf level appears once per
+ *                         target leaf below it)
  * Expansion rows hold, for n = 0..p, Re c_n^0 then (Re c_n^m, Im c_n^m) for
  * m = 1..n ((p+1)^2 values, zero-padded to P2pad = a multiple of 32), scaled
  * by s^-n (multipoles) or s^(n+1) (locals) with s the cell side. */
@@ -168,7 +176,8 @@ enum {
     FMM_EXPORT_M2L = 5,
     FMM_EXPORT_MULTIPOLE = 6,
     FMM_EXPORT_LOCAL = 7,
-    FMM_EXPORT_SELECT = 8
+    FMM_EXPORT_SELECT = 8,
+    FMM_EXPORT_M2P = 9
 };
 fmm_status fmm_export(int what, void *dst, int64_t capacity, int64_t *needed);
 

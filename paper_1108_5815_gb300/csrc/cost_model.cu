@@ -149,7 +149,75 @@ std::vector<P2PTiming> pretime_p2p(const std::vector<int> &counts, uint64_t seed
     return out;
 }
 
-void table_from_timings(const std::vector<P2PTiming> &grid, double m2l_ns, uint8_t *sel)
+std::vector<double> pretime_m2p(int p, const std::vector<int> &counts, uint64_t seed, cudaStream_t st)
+{
+    constexpr int K = 27, kLevel = 6;
+    constexpr int64_t kMaxTargets = 1 << 22, kMaxLeaves = 1 << 14;
+    const int P2pad = nterms_pad(p);
+    DevBuf<float4> pts(kMaxTargets), far(kMaxTargets);
+    DevBuf<int> begin(2 * kMaxLeaves), end(2 * kMaxLeaves), off(kMaxLeaves), cnt(kMaxLeaves),
+        src(kMaxLeaves * K), leaves(kMaxLeaves), level(2 * kMaxLeaves), sys(2 * kMaxLeaves);
+    DevBuf<uint64_t> prefix(2 * kMaxLeaves);
+    DevBuf<float> M((size_t)2 * kMaxLeaves * P2pad);  // rows of every cell id (targets and sources)
+    DevBuf<double> box(4);
+    k_synth_points<<<1024, 256, 0, st>>>(pts.p, kMaxTargets, seed);
+    FMM_LAUNCH_CHECK();
+    // multipole rows: small artificial values (the kernel's cost does not depend on them)
+    k_synth_points<<<1024, 256, 0, st>>>(reinterpret_cast<float4 *>(M.p), (int64_t)2 * kMaxLeaves * P2pad / 4,
+                                         seed + 1);
+    FMM_LAUNCH_CHECK();
+    const double hbox[4] = {0.0, 0.0, 0.0, 1.0};
+    FMM_CUDA_TRY(cudaMemcpyAsync(box.p, hbox, sizeof(hbox), cudaMemcpyHostToDevice, st));
+    std::vector<int> hl(2 * kMaxLeaves, kLevel), hs(2 * kMaxLeaves, 0);
+    std::vector<uint64_t> hp(2 * kMaxLeaves);
+    for (int64_t i = 0; i < 2 * kMaxLeaves; ++i) hp[i] = (uint64_t)((i * 2654435761ull) & ((1ull << (3 * kLevel)) - 1));
+    FMM_CUDA_TRY(cudaMemcpyAsync(level.p, hl.data(), sizeof(int) * hl.size(), cudaMemcpyHostToDevice, st));
+    FMM_CUDA_TRY(cudaMemcpyAsync(sys.p, hs.data(), sizeof(int) * hs.size(), cudaMemcpyHostToDevice, st));
+    FMM_CUDA_TRY(cudaMemcpyAsync(prefix.p, hp.data(), sizeof(uint64_t) * hp.size(), cudaMemcpyHostToDevice, st));
+    cudaEvent_t e0, e1;
+    FMM_CUDA_TRY(cudaEventCreate(&e0));
+    FMM_CUDA_TRY(cudaEventCreate(&e1));
+    std::vector<double> out;
+    for (int nt : counts) {
+        int64_t nL = std::min<int64_t>(kMaxLeaves, kMaxTargets / nt);
+        const int64_t nS = kMaxLeaves;
+        CellArrays c{};
+        c.begin = begin.p;
+        c.end = end.p;
+        c.level = level.p;
+        c.prefix = prefix.p;
+        c.sys = sys.p;
+        ListArrays L{};
+        L.m2p_off = off.p;
+        L.m2p_cnt = cnt.p;
+        L.m2p_src = src.p;
+        // sources get one particle each; only their multipoles are read
+        k_synth_lists<<<(unsigned)ceil_div(nS, 256), 256, 0, st>>>((int)nL, nt, (int)nS, 1, K, begin.p, end.p,
+                                                                   off.p, cnt.p, src.p, leaves.p);
+        FMM_LAUNCH_CHECK();
+        float best = 1e30f;
+        for (int rep = 0; rep < 3; ++rep) {
+            FMM_CUDA_TRY(cudaEventRecord(e0, st));
+            const size_t sh = m2p_smem(p, P2pad);
+            if (sh > 48 * 1024) set_smem_limit_once((const void *)k_m2p, (int)sh);
+            k_m2p<<<(unsigned)ceil_div(nL, kM2PWarps), 32 * kM2PWarps, sh, st>>>(c, L, leaves.p, (int)nL, pts.p,
+                                                                                 box.p, p, P2pad, M.p, far.p);
+            FMM_LAUNCH_CHECK();
+            FMM_CUDA_TRY(cudaEventRecord(e1, st));
+            FMM_CUDA_TRY(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            FMM_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+            if (rep > 0) best = std::min(best, ms);
+        }
+        out.push_back((double)best * 1e6 / ((double)nL * K));
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return out;
+}
+
+void table_from_timings(const std::vector<P2PTiming> &grid, double m2l_ns, const std::vector<int> &m2p_counts,
+                        const std::vector<double> &m2p_ns, uint8_t *sel)
 {
     // ln(time per pair) on the (log2 nt, log2 ns) grid, bilinear in the logs
     std::vector<int> cs;
@@ -166,16 +234,29 @@ void table_from_timings(const std::vector<P2PTiming> &grid, double m2l_ns, uint8
         lt[i * n + j] = std::log(g.ns_per_pair);
     }
     const double lm = std::log(m2l_ns);
+    std::vector<double> qx, qt;
+    for (size_t i = 0; i < m2p_ns.size(); ++i) {
+        qx.push_back(std::log2((double)m2p_counts[i]));
+        qt.push_back(std::log(m2p_ns[i]));
+    }
     for (int bt = 0; bt < kSelNB; ++bt) {
         size_t i0;
         const double wi = interp_axis(lx, bucket_mid_log2(bt), i0);
+        double lq = 1e300;  // ln of the M2P time per pair at this target count
+        if (qx.size() >= 2) {
+            size_t q0;
+            const double wq = interp_axis(qx, bucket_mid_log2(bt), q0);
+            lq = (1 - wq) * qt[q0] + wq * qt[q0 + 1];
+        }
         for (int bs = 0; bs < kSelNB; ++bs) {
             size_t j0;
             const double wj = interp_axis(lx, bucket_mid_log2(bs), j0);
             const double a = lt[i0 * n + j0], b = lt[i0 * n + j0 + 1], c = lt[(i0 + 1) * n + j0],
                          d = lt[(i0 + 1) * n + j0 + 1];
             const double v = (1 - wi) * ((1 - wj) * a + wj * b) + wi * ((1 - wj) * c + wj * d);
-            sel[bt * kSelNB + bs] = v < lm ? 1 : 0;
+            uint8_t kind = v < lm ? 1 : 0;
+            if (lq < std::min(v, lm)) kind = 2;
+            sel[bt * kSelNB + bs] = kind;
         }
     }
 }

@@ -483,4 +483,169 @@ __global__ void __launch_bounds__(32)
     }
 }
 
+// Cell-particle (M2P, the treecode kernel): one warp per target leaf with an
+// M2P list; every listed source cell's multipole is evaluated at the leaf's
+// particles and added to the far field.  With u = (x - c_S) / s_S and the
+// order-normalised irregular harmonics I^_n^m = I_n^m / nu_n^m,
+//   phi    = (1/s)   sum M^_n^m I^_n^m(u)
+//   d/dz   = -(1/s^2) sum M^_n^m I^_{n+1}^m   sqrt((n+1-m)(n+1+m))
+//   D+     = (1/s^2) sum [M^_n^m I^_{n+1}^{m+1} sqrt((n+m+1)(n+m+2))
+//                          - conj(M^_n^m I^_{n+1}^{m-1}) sqrt((n-m+1)(n-m+2)) (m >= 1)]
+// (sums over m >= 0 with weight 2 on the real parts of m > 0 where the signed-m
+// sum pairs conjugates), from d/dz I_n^m = -I_{n+1}^m and (d/dx + i d/dy)
+// I_n^m = I_{n+1}^{m+1}.  Recurrences of I^: I^_0^0 = 1/r,
+// I^_m^m = -sqrt((2m-1)/(2m)) (x + iy)/r^2 I^_{m-1}^{m-1},
+// I^_n^m = ((2n-1) z I^_{n-1}^m - sqrt((n+m-1)(n-m-1)) I^_{n-2}^m) / (r^2 sqrt((n+m)(n-m))).
+size_t m2p_smem(int p, int P2pad)
+{
+    const int nt = (p + 2) * (p + 3) / 2;
+    return sizeof(float) * (2 * (size_t)nt + (p + 2) + 3 * (size_t)P2pad + 4 * kM2PWarps +
+                            (size_t)kM2PWarps * 4 * P2pad);
+}
+
+__global__ void __launch_bounds__(32 * kM2PWarps)
+    k_m2p(CellArrays c, ListArrays Ls, const int *__restrict__ leaves, int nleaves,
+          const float4 *__restrict__ pts, const double *__restrict__ box, int p, int P2pad,
+          const float *__restrict__ M, float4 *__restrict__ far)
+{
+    extern __shared__ float sm[];
+    // per block: recurrence coefficients of I^ for (n, m) at n(n+1)/2 + m, n <= p + 1,
+    // the diagonal factors, and the three derivative weights per stored coefficient
+    const int ntri = (p + 2) * (p + 3) / 2;
+    float *ca = sm, *cb = ca + ntri, *cd = cb + ntri, *fz = cd + (p + 2), *f1 = fz + P2pad,
+          *f2 = f1 + P2pad, *sgeo = f2 + P2pad, *wbuf = sgeo + 4 * kM2PWarps;
+    for (int t = threadIdx.x; t < ntri; t += blockDim.x) {
+        int n = 0;
+        while ((n + 1) * (n + 2) / 2 <= t) ++n;
+        const int m = t - n * (n + 1) / 2;
+        const float den = n > m ? rsqrtf((float)((n + m) * (n - m))) : 0.f;
+        ca[t] = (2.f * n - 1.f) * den;
+        cb[t] = n > m + 1 ? sqrtf((float)((n + m - 1) * (n - m - 1))) * den : 0.f;
+    }
+    for (int m = threadIdx.x; m <= p + 1; m += blockDim.x) cd[m] = m > 0 ? -sqrtf((2.f * m - 1.f) / (2.f * m)) : 1.f;
+    for (int j = threadIdx.x; j < P2pad; j += blockDim.x) {
+        int n = 0;
+        while ((n + 1) * (n + 1) <= j) ++n;
+        const int m = (j - n * n + 1) / 2;
+        fz[j] = sqrtf((float)((n + 1 - m) * (n + 1 + m)));
+        f1[j] = sqrtf((float)((n + m + 1) * (n + m + 2)));
+        f2[j] = sqrtf((float)((n - m + 1) * (n - m + 2)));
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int li = blockIdx.x * kM2PWarps + warp;
+    if (li >= nleaves) return;
+    const int cell = leaves[li];
+    const int cnt = Ls.m2p_cnt[cell];
+    if (cnt == 0) return;
+    const int *slist = Ls.m2p_src + Ls.m2p_off[cell];
+    float *Mh = wbuf + warp * 4 * P2pad, *Mz = Mh + P2pad, *Mx1 = Mz + P2pad, *Mx2 = Mx1 + P2pad;
+    const int P2 = nterms(p);
+    const int b = c.begin[cell], e = c.end[cell];
+    // particle offsets from the target leaf's centre in FP32; the shift and scale of
+    // each source come from one FP64 evaluation per (leaf, source) pair, not per particle
+    double cT[3], sT;
+    cell_centre_side(c, cell, box, cT, sT);
+    float *geo = sgeo + warp * 4;  // (c_T - c_S) / s_S and s_T / s_S of the current source
+    for (int i0 = b; i0 < e; i0 += 32) {
+        const int i = i0 + lane;
+        const bool valid = i < e;
+        const float4 pt = pts[valid ? i : b];
+        const float rx = (float)(((double)pt.x - cT[0]) / sT), ry = (float)(((double)pt.y - cT[1]) / sT),
+                    rz = (float)(((double)pt.z - cT[2]) / sT);
+        float phi = 0.f, dz = 0.f, dpr = 0.f, dpi = 0.f;
+        for (int k = 0; k < cnt; ++k) {
+            const int S = slist[k];
+            __syncwarp();
+            if (lane == 0) {
+                double cS[3], sS;
+                cell_centre_side(c, S, box, cS, sS);
+                geo[0] = (float)((cT[0] - cS[0]) / sS);
+                geo[1] = (float)((cT[1] - cS[1]) / sS);
+                geo[2] = (float)((cT[2] - cS[2]) / sS);
+                geo[3] = (float)(sT / sS);
+            }
+            for (int j = lane; j < P2pad; j += 32) {
+                const float v = j < P2 ? M[(int64_t)S * P2pad + j] : 0.f;
+                Mh[j] = v;
+                Mz[j] = v * fz[j];
+                Mx1[j] = v * f1[j];
+                Mx2[j] = v * f2[j];
+            }
+            __syncwarp();
+            const float ratio = geo[3];
+            const float x = fmaf(rx, ratio, geo[0]), y = fmaf(ry, ratio, geo[1]), z = fmaf(rz, ratio, geo[2]);
+            const float is1 = ratio / (float)sT, is2 = is1 * is1;  // 1 / s_S = (s_T / s_S) / s_T
+            const float r2 = x * x + y * y + z * z;
+            const float ir2 = 1.f / r2;
+            float sphi = 0.f, sdz = 0.f, sdr = 0.f, sdi = 0.f;
+            float mre = rsqrtf(r2), mim = 0.f;  // I^_m^m
+            for (int m = 0; m <= p + 1; ++m) {
+                if (m > 0) {
+                    const float f = cd[m] * ir2;
+                    const float nre = f * (x * mre - y * mim), nim = f * (x * mim + y * mre);
+                    mre = nre;
+                    mim = nim;
+                }
+                const float w = m == 0 ? 1.f : 2.f;
+                float p2r = 0.f, p2i = 0.f, p1r = mre, p1i = mim;
+                for (int n = m; n <= p + 1; ++n) {
+                    float ir, ii;
+                    if (n == m) {
+                        ir = mre;
+                        ii = mim;
+                    } else {
+                        const int t = n * (n + 1) / 2 + m;
+                        const float a = ca[t] * z * ir2, bb = cb[t] * ir2;
+                        ir = a * p1r - bb * p2r;
+                        ii = a * p1i - bb * p2i;
+                        p2r = p1r;
+                        p2i = p1i;
+                        p1r = ir;
+                        p1i = ii;
+                    }
+                    if (n <= p) {  // phi += w Re(M^_n^m I^_n^m)
+                        const int k = n * n + (m == 0 ? 0 : 2 * m - 1);
+                        const float mr = Mh[k], mi = m == 0 ? 0.f : Mh[k + 1];
+                        sphi += w * (mr * ir - mi * ii);
+                    }
+                    if (n >= 1) {
+                        const int n1 = n - 1, base = n1 * n1;
+                        if (m <= n1) {  // dz += w Re(Mz_{n-1}^m I^_n^m)
+                            const int k = base + (m == 0 ? 0 : 2 * m - 1);
+                            const float mr = Mz[k], mi = m == 0 ? 0.f : Mz[k + 1];
+                            sdz += w * (mr * ir - mi * ii);
+                        }
+                        if (m >= 1) {  // D+ += Mx1_{n-1}^{m-1} I^_n^m
+                            const int mm = m - 1;
+                            const int k = base + (mm == 0 ? 0 : 2 * mm - 1);
+                            const float mr = Mx1[k], mi = mm == 0 ? 0.f : Mx1[k + 1];
+                            sdr += mr * ir - mi * ii;
+                            sdi += mr * ii + mi * ir;
+                        }
+                        if (m + 1 <= n1) {  // D+ -= conj(Mx2_{n-1}^{m+1} I^_n^m)
+                            const int k = base + 2 * (m + 1) - 1;
+                            const float mr = Mx2[k], mi = Mx2[k + 1];
+                            sdr -= mr * ir - mi * ii;
+                            sdi += mr * ii + mi * ir;
+                        }
+                    }
+                }
+            }
+            phi += sphi * is1;
+            dz -= sdz * is2;
+            dpr += sdr * is2;
+            dpi += sdi * is2;
+        }
+        if (valid) {
+            float4 f = far[i];
+            f.x += phi;
+            f.y += dpr;
+            f.z += dpi;
+            f.w += dz;
+            far[i] = f;
+        }
+    }
+}
+
 }  // namespace fmm

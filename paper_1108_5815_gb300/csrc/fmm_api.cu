@@ -74,17 +74,20 @@ struct Workspace {
     int cache_p = -1;
     std::unordered_map<uint64_t, int> class_cache;
     int table_slots = 0;
+    int split_prec = -1, split_slots = 0;  // hi/lo split class matrices: precision and slots done
     // last solve (for fmm_export)
     bool have_solve = false;
     int64_t N = 0;
     int ncells = 0, nleaves = 0, depth = 0, P2pad = 0, nclass = 0;
     int64_t nm2l = 0, np2p = 0;
     int nsys = 1;
-    int64_t cap_m2l = 0, cap_p2p = 0, cap_def = 0;  // list capacities that sufficed before
+    int64_t cap_m2l = 0, cap_p2p = 0, cap_def = 0, cap_m2p = 0;  // list capacities that sufficed before
+    int64_t nm2p = 0;
     std::vector<uint8_t> sel_host;                   // selection table of the last solve
     // hybrid selection: pre-timed kernels and the learned model
     std::vector<P2PTiming> p2p_grid;                      // P2P time per pair on artificial leaves
     std::map<std::tuple<int, uint64_t, int>, double> m2l_ns;  // (p, theta bits, precision) -> ns per pair
+    std::map<int, std::vector<double>> m2p_ns;                // p -> ns per pair for kSelCounts
     std::map<std::tuple<int, uint64_t, int, int>, std::vector<uint8_t>> tables;  // (mode, theta, p, prec)
     CostModel cm;
     // The solve runs on two library streams, both non-blocking (a kernel on the
@@ -284,7 +287,7 @@ void validate(const void *xyz, const void *q, int64_t N, int p, double theta, in
     if (o.max_depth < 0 || o.max_depth > kMaxLevel) throw Error{FMM_ERR_ARG, "max_depth must be in [0, 21]"};
     if (o.precision_mode < FMM_PREC_FP32 || o.precision_mode > FMM_PREC_BF16X3)
         throw Error{FMM_ERR_ARG, "precision_mode must be FMM_PREC_FP32, _TF32X3 or _BF16X3"};
-    if (o.select_mode < FMM_SELECT_PLAIN || o.select_mode > FMM_SELECT_TABLE)
+    if (o.select_mode < FMM_SELECT_PLAIN || o.select_mode > FMM_SELECT_TREECODE)
         throw Error{FMM_ERR_ARG, "select_mode must be one of FMM_SELECT_*"};
     if (o.select_mode == FMM_SELECT_TABLE && !o.select_table)
         throw Error{FMM_ERR_ARG, "FMM_SELECT_TABLE needs fmm_options.select_table"};
@@ -448,19 +451,24 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
     int64_t p2p_cap = std::max<int64_t>(ws.cap_p2p, std::max<int64_t>(4096 + nsys, (int64_t)nleaves * 96));
     int64_t def_cap = std::max<int64_t>(ws.cap_def, std::max<int64_t>(4096 + nsys, (int64_t)ncells * 96));
     uint64_t *hash_keys = need<uint64_t>(ws, "hash_keys", kHashCap, st);
-    unsigned long long *tcount = need<unsigned long long>(ws, "trav_counters", 3, st);
+    unsigned long long *tcount = need<unsigned long long>(ws, "trav_counters", 4, st);
     // hybrid selection table (the flagged deferred sources need cell ids below 2^30)
     const uint8_t *d_sel = nullptr;
     ws.sel_host.assign((size_t)kSelNB * kSelNB, 0);
     if (sel) {
-        if (ncells >= (1 << 30)) throw Error{FMM_ERR_CAPACITY, "selection tables need fewer than 2^30 cells"};
+        if (ncells >= (1 << 29)) throw Error{FMM_ERR_CAPACITY, "selection tables need fewer than 2^29 cells"};
         std::memcpy(ws.sel_host.data(), sel, ws.sel_host.size());
         uint8_t *dsel = need<uint8_t>(ws, "select_table", ws.sel_host.size(), st);
         upload(ws, dsel, ws.sel_host.data(), ws.sel_host.size(), st);
         d_sel = dsel;
     }
-    int64_t m2l_total = 0, p2p_total = 0;
+    L.m2p_off = need<int>(ws, "m2p_off", ncells, st);
+    L.m2p_cnt = need<int>(ws, "m2p_cnt", ncells, st);
+    int64_t m2p_cap = std::max<int64_t>(ws.cap_m2p, 4096);
+    int64_t m2l_total = 0, p2p_total = 0, m2p_total = 0;
     for (int attempt = 0;; ++attempt) {
+        L.m2p_src = need<int>(ws, "m2p_src", m2p_cap, st);
+        L.m2p_tgt = need<int>(ws, "m2p_tgt", m2p_cap, st);
         L.m2l_src = need<int>(ws, "m2l_src", m2l_cap, st);
         L.m2l_tgt = need<int>(ws, "m2l_tgt", m2l_cap, st);
         L.m2l_slot = need<uint32_t>(ws, "m2l_slot", m2l_cap, st);
@@ -474,14 +482,16 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
             const int a = lstart[l], b = lstart[l + 1];
             const unsigned blocks = (unsigned)ceil_div((int64_t)(b - a) * 32, 128);
             k_traverse_level<<<blocks, 128, 0, st>>>(c, L, a, b, theta2, (float)theta2, d_sel, tcount,
-                                                     m2l_cap, p2p_cap, def_cap, hash_keys, flags);
+                                                     m2l_cap, p2p_cap, def_cap, m2p_cap, hash_keys, flags);
             FMM_LAUNCH_CHECK();
         }
-        unsigned long long tot[3];
+        unsigned long long tot[4];
         sync_point(ws, st, flags, {{tcount, sizeof(tot)}}, tot);
-        if ((int64_t)tot[0] <= m2l_cap && (int64_t)tot[1] <= p2p_cap && (int64_t)tot[2] <= def_cap) {
+        if ((int64_t)tot[0] <= m2l_cap && (int64_t)tot[1] <= p2p_cap && (int64_t)tot[2] <= def_cap &&
+            (int64_t)tot[3] <= m2p_cap) {
             m2l_total = (int64_t)tot[0];
             p2p_total = (int64_t)tot[1];
+            m2p_total = (int64_t)tot[3];
             break;
         }
         if (attempt >= 3) throw Error{FMM_ERR_CAPACITY, "interaction lists kept outgrowing their buffers"};
@@ -489,10 +499,12 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
         m2l_cap = std::max<int64_t>(2 * m2l_cap, (int64_t)tot[0] + tot[0] / 4);
         p2p_cap = std::max<int64_t>(2 * p2p_cap, (int64_t)tot[1] + tot[1] / 4);
         def_cap = std::max<int64_t>(2 * def_cap, (int64_t)tot[2] + tot[2] / 4);
+        if ((int64_t)tot[3] > m2p_cap) m2p_cap = std::max<int64_t>(2 * m2p_cap, (int64_t)tot[3] + tot[3] / 4);
     }
     ws.cap_m2l = m2l_cap;
     ws.cap_p2p = p2p_cap;
     ws.cap_def = def_cap;
+    ws.cap_m2p = m2p_cap;
 
     // ---------------------------------------------------------- fork
     // P2P needs only the leaf lists: it runs on the caller's stream while the
@@ -564,6 +576,7 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
         if (ws.cache_p != p) {
             ws.class_cache.clear();
             ws.table_slots = 0;
+            ws.split_slots = 0;
             ws.cache_p = p;
             float *m2m = need<float>(ws, "m2m", (size_t)8 * P2pad * P2pad, fs);
             float *l2l = need<float>(ws, "l2l", (size_t)8 * P2pad * P2pad, fs);
@@ -680,8 +693,19 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
         if (nunits > 0) upload(ws, d_units, units.data(), sizeof(M2LUnit) * nunits, fs);
         upload(ws, d_ubase, ubase.data(), sizeof(int) * (ntiles + 1), fs);
         ev.rec(3, fs);
-        launch_m2l_tc(o.precision_mode == FMM_PREC_BF16X3, nunits, d_units, ntiles, d_ubase,
-                      entry_class, src, tile_cells, M, get<float>(ws, "table"), P2pad, partial, Lx,
+        // class matrices split into hi/lo in the stage layout, once per class slot and precision
+        const bool bf16 = o.precision_mode == FMM_PREC_BF16X3;
+        if (ws.split_prec != o.precision_mode) {
+            ws.split_prec = o.precision_mode;
+            ws.split_slots = 0;
+        }
+        unsigned char *tsplit = need<unsigned char>(ws, "table_split",
+                                                    m2l_split_bytes(P2pad, bf16, std::max(ws.table_slots, 1)), fs, true);
+        launch_split_tables(bf16, get<float>(ws, "table"), ws.split_slots, ws.table_slots - ws.split_slots, P2pad,
+                            tsplit, fs);
+        ws.split_slots = ws.table_slots;
+        launch_m2l_tc(bf16, nunits, d_units, ntiles, d_ubase,
+                      entry_class, src, tile_cells, M, tsplit, P2pad, partial, Lx,
                       flags, fs);
     } else {
         ev.rec(3, fs);
@@ -699,6 +723,13 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
     k_l2p<<<nleaves, 32, 4 * P2pad * sizeof(float), fs>>>(c, leaves, nleaves, pts, box, p, P2pad, Lx,
                                                           far);
     FMM_LAUNCH_CHECK();
+    if (m2p_total > 0) {  // cell-particle pairs of the hybrid selection, added to the far field
+        const size_t sh = m2p_smem(p, P2pad);
+        if (sh > 48 * 1024) set_smem_limit_once((const void *)k_m2p, (int)sh);
+        k_m2p<<<(unsigned)ceil_div(nleaves, kM2PWarps), 32 * kM2PWarps, sh, fs>>>(c, L, leaves, nleaves, pts, box, p,
+                                                                                P2pad, M, far);
+        FMM_LAUNCH_CHECK();
+    }
     ev.rec(5, fs);
 
     // ---------------------------------------------------------- join and combine
@@ -736,7 +767,9 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
     ws.nclass = nclass;
     ws.nm2l = m2l_total;
     ws.np2p = p2p_total;
+    ws.nm2p = m2p_total;
     if (stats) {
+        stats->n_m2p_pairs = m2p_total;
         stats->ncells = ncells;
         stats->nleaves = nleaves;
         stats->depth = depth;
@@ -786,14 +819,23 @@ double m2l_ns_per_pair(Workspace &ws, int p, double theta, int prec)
     return best;
 }
 
+const std::vector<int> kSelCounts = {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512};
+
 const std::vector<P2PTiming> &p2p_timings(Workspace &ws)
 {
     if (ws.p2p_grid.empty()) {
         ensure_streams(ws);
-        const std::vector<int> counts = {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512};
-        ws.p2p_grid = pretime_p2p(counts, 0x5eed0002ull, ws.main_stream);
+        ws.p2p_grid = pretime_p2p(kSelCounts, 0x5eed0002ull, ws.main_stream);
     }
     return ws.p2p_grid;
+}
+
+const std::vector<double> &m2p_timings(Workspace &ws, int p)
+{
+    auto it = ws.m2p_ns.find(p);
+    if (it != ws.m2p_ns.end()) return it->second;
+    ensure_streams(ws);
+    return ws.m2p_ns[p] = pretime_m2p(p, kSelCounts, 0x5eed0003ull, ws.main_stream);
 }
 
 const std::vector<uint8_t> &pretimed_table(Workspace &ws, int p, double theta, int prec)
@@ -803,7 +845,7 @@ const std::vector<uint8_t> &pretimed_table(Workspace &ws, int p, double theta, i
     if (it != ws.tables.end()) return it->second;
     const double m2l = m2l_ns_per_pair(ws, p, theta, prec);
     std::vector<uint8_t> t((size_t)kSelNB * kSelNB);
-    table_from_timings(p2p_timings(ws), m2l, t.data());
+    table_from_timings(p2p_timings(ws), m2l, kSelCounts, m2p_timings(ws, p), t.data());
     return ws.tables[key] = std::move(t);
 }
 
@@ -825,6 +867,10 @@ const uint8_t *selection_table(Workspace &ws, const fmm_options &o, int p, doubl
 {
     switch (o.select_mode) {
         case FMM_SELECT_TABLE: return o.select_table;
+        case FMM_SELECT_TREECODE: {
+            static const std::vector<uint8_t> all_m2p((size_t)kSelNB * kSelNB, 2);
+            return all_m2p.data();
+        }
         case FMM_SELECT_AUTOTUNE: return pretimed_table(ws, p, theta, o.precision_mode).data();
         case FMM_SELECT_LEARNED:
             if (!ws.cm.trained) return pretimed_table(ws, p, theta, o.precision_mode).data();
@@ -1216,6 +1262,7 @@ fmm_status fmm_export(int what, void *dst, int64_t capacity, int64_t *needed)
             case FMM_EXPORT_MULTIPOLE:
             case FMM_EXPORT_LOCAL: bytes = (int64_t)ws.ncells * ws.P2pad * sizeof(float); break;
             case FMM_EXPORT_SELECT: bytes = (int64_t)ws.sel_host.size(); break;
+            case FMM_EXPORT_M2P: bytes = ws.nm2p * 2 * sizeof(int32_t); break;
             default: throw Error{FMM_ERR_ARG, "unknown export kind"};
         }
         if (needed) *needed = bytes;
@@ -1257,6 +1304,18 @@ fmm_status fmm_export(int what, void *dst, int64_t capacity, int64_t *needed)
                 std::vector<int> t(n), s(n);
                 d2h(t.data(), get<int>(ws, "p2p_tgt"), n * sizeof(int));
                 d2h(s.data(), get<int>(ws, "p2p_src"), n * sizeof(int));
+                int32_t *o = static_cast<int32_t *>(dst);
+                for (int64_t i = 0; i < n; ++i) {
+                    o[2 * i] = t[i];
+                    o[2 * i + 1] = s[i];
+                }
+                break;
+            }
+            case FMM_EXPORT_M2P: {
+                const int64_t n = ws.nm2p;
+                std::vector<int> t(n), s(n);
+                d2h(t.data(), get<int>(ws, "m2p_tgt"), n * sizeof(int));
+                d2h(s.data(), get<int>(ws, "m2p_src"), n * sizeof(int));
                 int32_t *o = static_cast<int32_t *>(dst);
                 for (int64_t i = 0; i < n; ++i) {
                     o[2 * i] = t[i];

@@ -39,6 +39,8 @@ struct ListArrays {
     int *m2l_off, *m2l_cnt, *p2p_off, *p2p_cnt;  // per cell
     int *def_off, *def_cnt;                      // per cell: deferred sources
     int *def_src;
+    int *m2p_src, *m2p_tgt;                      // cell-particle pairs (hybrid value 2)
+    int *m2p_off, *m2p_cnt;                      // per cell
 };
 
 constexpr int kHashBits = 18;
@@ -72,8 +74,8 @@ __global__ void k_leaf_compact(CellArrays c, int ncells, const int *ex, int *lea
 constexpr int kSelNB = 128;  // count buckets of the hybrid selection table
 __global__ void k_traverse_level(CellArrays c, ListArrays L, int a, int b, double theta2,
                                  float theta2f, const uint8_t *sel, unsigned long long *counters,
-                                 int64_t cap_m, int64_t cap_p, int64_t cap_d, uint64_t *hash_keys,
-                                 int *flags);
+                                 int64_t cap_m, int64_t cap_p, int64_t cap_d, int64_t cap_q,
+                                 uint64_t *hash_keys, int *flags);
 __global__ void k_hash_flags(const uint64_t *hash_keys, int *flag);
 __global__ void k_hash_compact(const uint64_t *hash_keys, const int *ex, uint64_t *ukeys,
                                uint32_t *uslot);
@@ -103,6 +105,11 @@ __global__ void k_m2m(CellArrays c, int a, int b, const float *m2m, int P2, int 
 __global__ void k_l2l(CellArrays c, int a, int b, const float *l2l, int P2, int P2pad, float *L);
 __global__ void k_l2p(CellArrays c, const int *leaves, int nleaves, const float4 *pts,
                       const double *box, int p, int P2pad, const float *L, float4 *far);
+// M2P: blocks of kM2PWarps warps, one target leaf per warp; dynamic shared memory m2p_smem(p, P2pad).
+constexpr int kM2PWarps = 4;
+size_t m2p_smem(int p, int P2pad);
+__global__ void k_m2p(CellArrays c, ListArrays Ls, const int *leaves, int nleaves, const float4 *pts,
+                      const double *box, int p, int P2pad, const float *M, float4 *far);
 
 // m2l.cu
 void launch_m2l_simt(int ntiles, const int *entry_base, const int *entry_class, const int *src,
@@ -117,8 +124,13 @@ bool m2l_tc_supported(int P2pad);
 size_t m2l_tc_smem(int P2pad, bool bf16, int &nstages);
 void launch_m2l_tc(bool bf16, int nunits, const void *units, int ntiles, const int *unit_base,
                    const int *entry_class, const int *src, const int *tile_cells, const float *M,
-                   const float *table, int P2pad, float *partial, float *L, int *flags,
+                   const unsigned char *tsplit, int P2pad, float *partial, float *L, int *flags,
                    cudaStream_t st);
+// Bytes of the hi/lo split class matrices of nslots classes, and the kernel that
+// writes slots [slot0, slot0 + nslots) of them from the FP32 tables.
+size_t m2l_split_bytes(int P2pad, bool bf16, int nslots);
+void launch_split_tables(bool bf16, const float *table, int slot0, int nslots, int P2pad, unsigned char *out,
+                         cudaStream_t st);
 
 // p2p.cu
 __global__ void k_p2p(CellArrays c, ListArrays L, const int *leaves, int nleaves,
@@ -151,8 +163,13 @@ struct P2PTiming {
 };
 // Times the P2P kernel on artificial leaves for every (nt, ns) in counts x counts.
 std::vector<P2PTiming> pretime_p2p(const std::vector<int> &counts, uint64_t seed, cudaStream_t st);
-// Selection table: P2P iff the interpolated P2P time per pair is below m2l_ns.
-void table_from_timings(const std::vector<P2PTiming> &grid, double m2l_ns, uint8_t *sel);
+// M2P time per (target leaf, source cell) pair at expansion order p for each
+// target count in counts.
+std::vector<double> pretime_m2p(int p, const std::vector<int> &counts, uint64_t seed, cudaStream_t st);
+// Selection table: the cheapest of M2L (m2l_ns per pair), P2P (interpolated from
+// the grid) and M2P (interpolated over the target count; none if m2p_ns is empty).
+void table_from_timings(const std::vector<P2PTiming> &grid, double m2l_ns, const std::vector<int> &m2p_counts,
+                        const std::vector<double> &m2p_ns, uint8_t *sel);
 // log2 of the representative count of a selection-table bucket (host and device agree).
 __host__ __device__ inline float bucket_mid_log2(int b)
 {

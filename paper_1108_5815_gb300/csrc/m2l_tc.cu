@@ -18,19 +18,25 @@
 // the blocks are summed with round-to-nearest FP32 adds into a running sum held
 // in a third tensor-memory region (in the partial buffer when 3N columns do not fit).
 //
+// The class matrices B are split into hi/lo once (k_split_tables), already in
+// the shared-memory layout of a stage, so a stage's B is two bulk asynchronous
+// copies (cp.async.bulk, completing on an mbarrier) issued by one thread.
+//
 // Roles inside a CTA (416 threads):
-//   warps 0-7   producers: gather 128 source rows and N matrix rows of one
-//               K-chunk of 32 floats, split them into hi/lo and store them in the
-//               canonical no-swizzle K-major layout (8-row x 16-byte core
-//               matrices; LBO = 128 B along K, SBO = 8 core matrices (TF32, 128 B
-//               rows) or 4 (BF16, 64 B rows) along rows).
+//   warps 0-7   producers: gather the 128 source rows (A) of one K-chunk of 32
+//               floats, split them into hi/lo and store them in the canonical
+//               no-swizzle K-major layout (8-row x 16-byte core matrices;
+//               LBO = 128 B along K, SBO = 8 core matrices (TF32, 128 B rows) or
+//               4 (BF16, 64 B rows) along rows); one producer thread also issues
+//               the stage's B copies.
 //   warp 8      allocates tensor memory; one lane issues the MMAs and commits.
 //   warps 9-12  accumulators, one per 32-lane quarter of tensor memory: after
 //               each class block they read the block's main and correction
 //               accumulators (two buffer pairs, alternating, when 5N columns fit)
 //               and add both into the running sum.
-// Stages are handed over through mbarriers (full: 256 producer arrivals;
-// empty, acc_full: tcgen05.commit; acc_empty: 128 accumulator arrivals).  Every
+// Stages are handed over through mbarriers (full: 256 producer arrivals; bfull:
+// one arrival with the B copies' byte count; empty, acc_full: tcgen05.commit;
+// acc_empty: 128 accumulator arrivals).  Every
 // wait is bounded: on expiry the kernel raises a flag and returns after
 // releasing its tensor memory.
 // A work unit is (tile, range of the tile's class blocks); its 128 x N result
@@ -84,6 +90,23 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
         if (done) return true;
     }
     return false;
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// Bulk asynchronous copy global -> shared (16-byte aligned, size a multiple of 16),
+// completing `bytes` of the barrier's transaction count.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
 }
 
 __device__ __forceinline__ void fence_proxy_async()
@@ -210,10 +233,11 @@ struct Unit {
 template <bool BF16, int N>
 __global__ void __launch_bounds__(kThreads, 1)
     k_m2l_tc(const Unit *__restrict__ units, const int *__restrict__ entry_class,
-             const int *__restrict__ src, const float *__restrict__ M, const float *__restrict__ table,
-             int P2pad, int nstages, float *__restrict__ partial, int *__restrict__ flags)
+             const int *__restrict__ src, const float *__restrict__ M,
+             const unsigned char *__restrict__ tsplit, int P2pad, int nstages,
+             float *__restrict__ partial, int *__restrict__ flags)
 {
-    constexpr int NG = (128 + N + 63) / 64;        // groups of 8 rows per producer warp
+    constexpr int NG = 2;                          // groups of 8 A rows per producer warp
     constexpr bool SUM_TMEM = 3 * N <= 512;        // running sum in tensor memory
     constexpr int NBUF = 5 * N <= 512 ? 2 : 1;     // main/correction buffer pairs
     constexpr int BUF0 = SUM_TMEM ? N : 0;         // first buffer column
@@ -229,7 +253,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t stage_bytes = 2 * a_bytes + 2 * b_bytes;
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + nstages * stage_bytes);
     uint64_t *empty = full + nstages;
-    uint64_t *acc_full = empty + nstages;
+    uint64_t *bfull = empty + nstages;
+    uint64_t *acc_full = bfull + nstages;
     uint64_t *acc_empty = acc_full + 2;
     uint64_t *fin = acc_empty + 2;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(fin + 1);
@@ -246,6 +271,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         s_abort = 0;
         for (int s = 0; s < nstages; ++s) {
             mbar_init(&full[s], kProducerWarps * 32);
+            mbar_init(&bfull[s], 1);
             mbar_init(&empty[s], 1);
         }
         for (int b = 0; b < 2; ++b) {
@@ -269,13 +295,13 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     if (warp < kProducerWarps) {
         // ------------------------------------------------------------ producers
-        // Thread (warp, lane) owns rows grp*8 + (lane & 7) for grp = warp + 8j, and the
-        // 16-byte chunks (lane >> 3) + 4h of each (h < 2 in TF32, h = 0 in BF16).  Rows < 128 are
-        // gathered multipoles (A), the rest rows of the class matrix (B).  The loads
-        // of stage g+1 are issued before stage g is split and stored.
-        const int groups = (128 + N) / 8;
+        // Thread (warp, lane) owns A rows grp*8 + (lane & 7) for grp = warp + 8j (j < 2),
+        // and the 16-byte chunks (lane >> 3) + 4h of each (h < 2 in TF32, h = 0 in BF16).
+        // The loads of stage g+1 are issued before stage g is split and stored.
+        // Thread 0 also issues the two bulk copies of stage g's B (hi, lo).
         const int sub = lane & 7, cq = lane >> 3;
         constexpr int V = 2;  // float4 per row and thread per stage
+        const bool bissuer = threadIdx.x == 0;
         float4 cur[NG][V], nxt[NG][V];
         int srow[2] = {0, 0};
         bool svalid[2] = {false, false};
@@ -291,18 +317,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                     srow[j] = svalid[j] ? sidx : 0;
                 }
             }
-            const float *Tm = table + (int64_t)entry_class[e] * P2pad * P2pad;
 #pragma unroll
             for (int j = 0; j < NG; ++j) {
-                const int grp = warp + 8 * j;
-                const float *rowp = nullptr;
-                bool valid = grp < groups;
-                if (j < 2) {
-                    rowp = M + (int64_t)srow[j] * P2pad;
-                    valid = svalid[j];
-                } else if (valid) {
-                    rowp = Tm + (int64_t)(grp * 8 + sub - 128) * P2pad;
-                }
+                const float *rowp = M + (int64_t)srow[j] * P2pad;
+                const bool valid = svalid[j];
                 if (BF16) {
                     const int kk = k0 + cq * 8;
                     buf[j][0] = valid ? *reinterpret_cast<const float4 *>(rowp + kk) : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -316,6 +334,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
             }
         };
+        int issued = 0;  // B stages issued by thread 0
         if (nsteps > 0) load_stage(0, nxt);
         for (int g = 0; g < nsteps; ++g) {
 #pragma unroll
@@ -331,20 +350,19 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             if (s_abort) break;
             unsigned char *st = smem + (size_t)s * stage_bytes;
+            if (bissuer) {
+                const int e = U.e0 + g / nkc, kc = g % nkc;
+                const unsigned char *bsrc = tsplit + ((int64_t)entry_class[e] * nkc + kc) * 2 * (int64_t)b_bytes;
+                mbar_arrive_expect_tx(&bfull[s], 2 * b_bytes);
+                bulk_g2s(st + 2 * a_bytes, bsrc, b_bytes, &bfull[s]);
+                bulk_g2s(st + 2 * a_bytes + b_bytes, bsrc + b_bytes, b_bytes, &bfull[s]);
+                issued = g + 1;
+            }
 #pragma unroll
             for (int j = 0; j < NG; ++j) {
-                const int grp = warp + 8 * j;
-                if (grp >= groups) continue;
-                const int row = grp * 8 + sub;
-                unsigned char *dst_hi, *dst_lo;
-                if (row < 128) {
-                    dst_hi = st + (row >> 3) * SBO + (row & 7) * 16;
-                    dst_lo = dst_hi + a_bytes;
-                } else {
-                    const int r = row - 128;
-                    dst_hi = st + 2 * a_bytes + (r >> 3) * SBO + (r & 7) * 16;
-                    dst_lo = dst_hi + b_bytes;
-                }
+                const int row = (warp + 8 * j) * 8 + sub;
+                unsigned char *dst_hi = st + (row >> 3) * SBO + (row & 7) * 16;
+                unsigned char *dst_lo = dst_hi + a_bytes;
                 uint4 hi, lo;
                 if (BF16) {
                     split_bf16(cur[j][0], cur[j][1], hi, lo);
@@ -362,6 +380,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             fence_proxy_async();
             mbar_arrive(&full[s]);
         }
+        if (bissuer) {
+            // no B copy may still be landing when the CTA ends (matters after an abort)
+            for (int g = issued - 1; g >= 0 && g >= issued - nstages; --g)
+                if (!mbar_wait(&bfull[g % nstages], (uint32_t)(g / nstages) & 1u)) atomicOr(&flags[kFlagTimeout], 1);
+        }
     } else if (warp == kMmaWarp) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
@@ -378,7 +401,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const uint32_t dmain = tmem + (uint32_t)(BUF0 + buf * 2 * N), dcorr = dmain + (uint32_t)N;
                 for (int kc = 0; kc < nkc; ++kc, ++g) {
                     const int s = g % nstages;
-                    if (!mbar_wait(&full[s], (uint32_t)(g / nstages) & 1u)) {
+                    if (!mbar_wait(&full[s], (uint32_t)(g / nstages) & 1u) ||
+                        !mbar_wait(&bfull[s], (uint32_t)(g / nstages) & 1u)) {
                         ok = false;
                         break;
                     }
@@ -487,9 +511,59 @@ __global__ void k_m2l_reduce(const int *__restrict__ unit_base, const float *__r
     }
 }
 
+// Class matrices T (FP32 [slot][P2pad][P2pad]) split into hi/lo in the stage
+// layout: for slot, K-chunk kc (32 floats): N rows x RB bytes of hi, then of lo,
+// row r's 16-byte chunk c at (r >> 3) * 8 RB + (r & 7) * 16 + c * 128.
+// One thread per (slot, kc, row, chunk).
+template <bool BF16>
+__global__ void k_split_tables(const float *__restrict__ table, int slot0, int nslots, int P2pad,
+                               unsigned char *__restrict__ out)
+{
+    constexpr int RB = BF16 ? 64 : 128, CH = RB / 16, EPC = BF16 ? 8 : 4;  // elements per chunk
+    const int N = P2pad, nkc = P2pad / kKChunk;
+    const int64_t per_slot = (int64_t)nkc * N * CH;
+    const int64_t total = per_slot * nslots;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int slot = slot0 + (int)(i / per_slot);
+        int64_t rem = i % per_slot;
+        const int kc = (int)(rem / (N * CH));
+        rem %= N * CH;
+        const int r = (int)(rem / CH), ch = (int)(rem % CH);
+        const float *src = table + ((int64_t)slot * P2pad + r) * P2pad + kc * kKChunk + ch * EPC;
+        const float4 a = *reinterpret_cast<const float4 *>(src);
+        uint4 hi, lo;
+        if (BF16)
+            split_bf16(a, *reinterpret_cast<const float4 *>(src + 4), hi, lo);
+        else
+            split_tf32(a, hi, lo);
+        const int64_t bbytes = (int64_t)N * RB;
+        unsigned char *base = out + ((int64_t)slot * nkc + kc) * 2 * bbytes + (r >> 3) * 8 * RB + (r & 7) * 16 + ch * 128;
+        *reinterpret_cast<uint4 *>(base) = hi;
+        *reinterpret_cast<uint4 *>(base + bbytes) = lo;
+    }
+}
+
 }  // namespace
 
 bool m2l_tc_supported(int P2pad) { return P2pad <= 256; }
+
+size_t m2l_split_bytes(int P2pad, bool bf16, int nslots)
+{
+    return (size_t)nslots * (P2pad / kKChunk) * 2 * (size_t)P2pad * (bf16 ? 64 : 128);
+}
+
+void launch_split_tables(bool bf16, const float *table, int slot0, int nslots, int P2pad, unsigned char *out,
+                         cudaStream_t st)
+{
+    if (nslots <= 0) return;
+    const int64_t total = (int64_t)nslots * (P2pad / kKChunk) * P2pad * (bf16 ? 4 : 8);
+    const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(total, 256), 152 * 16);
+    if (bf16)
+        k_split_tables<true><<<grid, 256, 0, st>>>(table, slot0, nslots, P2pad, out);
+    else
+        k_split_tables<false><<<grid, 256, 0, st>>>(table, slot0, nslots, P2pad, out);
+    FMM_LAUNCH_CHECK();
+}
 
 size_t m2l_tc_smem(int P2pad, bool bf16, int &nstages)
 {
@@ -497,12 +571,12 @@ size_t m2l_tc_smem(int P2pad, bool bf16, int &nstages)
     const size_t stage = 2 * 128 * rb + 2 * (size_t)P2pad * rb;
     nstages = (int)std::min<size_t>(bf16 ? 6 : 4, (200 * 1024) / stage);
     if (nstages < 2) nstages = 2;
-    return nstages * stage + 1024 /*alignment*/ + (2 * nstages + 5) * 8 + 16;
+    return nstages * stage + 1024 /*alignment*/ + (3 * nstages + 5) * 8 + 16;
 }
 
 void launch_m2l_tc(bool bf16, int nunits, const void *units, int ntiles, const int *unit_base,
                    const int *entry_class, const int *src, const int *tile_cells, const float *M,
-                   const float *table, int P2pad, float *partial, float *L, int *flags,
+                   const unsigned char *tsplit, int P2pad, float *partial, float *L, int *flags,
                    cudaStream_t st)
 {
     int nstages = 0;
@@ -512,7 +586,7 @@ void launch_m2l_tc(bool bf16, int nunits, const void *units, int ntiles, const i
     do {                                                                                           \
         set_smem_limit_once((const void *)k_m2l_tc<B, NN>, (int)smem);                              \
         k_m2l_tc<B, NN><<<nunits, kThreads, smem, st>>>(static_cast<const Unit *>(units), entry_class, \
-                                                        src, M, table, P2pad, nstages, partial, flags); \
+                                                        src, M, tsplit, P2pad, nstages, partial, flags); \
     } while (0)
 #define FMM_M2L_TC_BY_N(B)                                  \
     do {                                                    \

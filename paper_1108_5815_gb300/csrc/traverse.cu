@@ -13,9 +13,9 @@
 //                    else T,S leaves -> P2P;
 //                    else split S (S larger, or T a leaf) and interact with
 //                    its children, or defer S to T's children.
-// A P2P pair (T,S) chosen by the selection table above the leaf level is handed
-// down as a flagged deferred source until it reaches T's leaves, so every P2P
-// list stays a per-leaf list (its sources may be cells of any level).
+// A P2P or M2P pair (T,S) chosen by the selection table above the leaf level is
+// handed down as a flagged deferred source until it reaches T's leaves, so the
+// P2P and M2P lists stay per-leaf lists (their sources may be cells of any level).
 // One warp handles one target; lanes take inherited sources in order and
 // resolve each with a small depth-first stack.  Each target's outputs are
 // written contiguously in a deterministic order (count, reserve with one atomic
@@ -33,6 +33,8 @@ namespace {
 
 constexpr int kStack = 192;
 constexpr int kP2PFlag = 1 << 30;  // deferred source that is a chosen P2P pair
+constexpr int kM2PFlag = 1 << 29;  // deferred source that is a chosen M2P pair
+constexpr int kCellMask = kM2PFlag - 1;
 
 struct TargetInfo {
     int t, level;
@@ -117,7 +119,7 @@ __device__ __forceinline__ uint64_t class_key(const TargetInfo &T, int ls, const
 }
 
 struct Counts {
-    int m, p, d;
+    int m, p, d, q;  // M2L, P2P, deferred, M2P
 };
 
 // Resolves one inherited source S0 for target T.  WRITE = false only counts.
@@ -125,20 +127,27 @@ struct Counts {
 template <bool WRITE>
 __device__ Counts resolve(const TargetInfo &T, int S0, const CellArrays &c, const ListArrays &L,
                           double theta2, float theta2f, int64_t m_pos, int64_t p_pos, int d_pos,
-                          const uint8_t *__restrict__ sel, uint64_t *hash_keys, int *flags)
+                          int64_t q_pos, const uint8_t *__restrict__ sel, uint64_t *hash_keys,
+                          int *flags)
 {
-    Counts n = {0, 0, 0};
-    if (S0 & kP2PFlag) {
-        // a P2P pair chosen at an ancestor of T: record at a leaf, else pass down
-        if (T.leaf) {
+    Counts n = {0, 0, 0, 0};
+    if (S0 & (kP2PFlag | kM2PFlag)) {
+        // a P2P or M2P pair chosen at an ancestor of T: record at a leaf, else pass down
+        if (!T.leaf) {
+            if (WRITE) L.def_src[d_pos] = S0;
+            n.d = 1;
+        } else if (S0 & kP2PFlag) {
             if (WRITE) {
-                L.p2p_src[p_pos] = S0 & ~kP2PFlag;
+                L.p2p_src[p_pos] = S0 & kCellMask;
                 L.p2p_tgt[p_pos] = T.t;
             }
             n.p = 1;
         } else {
-            if (WRITE) L.def_src[d_pos] = S0;
-            n.d = 1;
+            if (WRITE) {
+                L.m2p_src[q_pos] = S0 & kCellMask;
+                L.m2p_tgt[q_pos] = T.t;
+            }
+            n.q = 1;
         }
         return n;
     }
@@ -152,17 +161,22 @@ __device__ Counts resolve(const TargetInfo &T, int S0, const CellArrays &c, cons
         int Cs[3], hs;
         cell_geom32(ls, c.prefix[S], Cs, hs);
         if (mac_accept(T, Cs, hs, theta2, theta2f)) {
-            if (sel && __ldg(&sel[T.bt * kSelNB + count_bucket(c.end[S] - c.begin[S])])) {
-                if (T.leaf) {
-                    if (WRITE) {
-                        L.p2p_src[p_pos + n.p] = S;
-                        L.p2p_tgt[p_pos + n.p] = T.t;
-                    }
-                    ++n.p;
-                } else {
-                    if (WRITE) L.def_src[d_pos + n.d] = S | kP2PFlag;
-                    ++n.d;
+            const int kind = sel ? __ldg(&sel[T.bt * kSelNB + count_bucket(c.end[S] - c.begin[S])]) : 0;
+            if (kind != 0 && !T.leaf) {
+                if (WRITE) L.def_src[d_pos + n.d] = S | (kind == 1 ? kP2PFlag : kM2PFlag);
+                ++n.d;
+            } else if (kind == 1) {
+                if (WRITE) {
+                    L.p2p_src[p_pos + n.p] = S;
+                    L.p2p_tgt[p_pos + n.p] = T.t;
                 }
+                ++n.p;
+            } else if (kind == 2) {
+                if (WRITE) {
+                    L.m2p_src[q_pos + n.q] = S;
+                    L.m2p_tgt[q_pos + n.q] = T.t;
+                }
+                ++n.q;
             } else {
                 if (WRITE) {
                     L.m2l_src[m_pos + n.m] = S;
@@ -233,8 +247,8 @@ __device__ __forceinline__ int warp_excl(int v)
 __global__ void __launch_bounds__(128)
     k_traverse_level(CellArrays c, ListArrays L, int a, int b, double theta2, float theta2f,
                      const uint8_t *__restrict__ sel, unsigned long long *__restrict__ counters,
-                     int64_t cap_m, int64_t cap_p, int64_t cap_d, uint64_t *__restrict__ hash_keys,
-                     int *__restrict__ flags)
+                     int64_t cap_m, int64_t cap_p, int64_t cap_d, int64_t cap_q,
+                     uint64_t *__restrict__ hash_keys, int *__restrict__ flags)
 {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -243,26 +257,31 @@ __global__ void __launch_bounds__(128)
     const TargetInfo T = load_target(c, t);
     const int P = c.parent[t];
     const int i0 = L.def_off[P], ni = L.def_cnt[P];
-    int m = 0, p = 0, d = 0;
+    int m = 0, p = 0, d = 0, q = 0;
     for (int k = lane; k < ni; k += 32) {
-        const Counts n = resolve<false>(T, L.def_src[i0 + k], c, L, theta2, theta2f, 0, 0, 0, sel, nullptr, flags);
+        const Counts n = resolve<false>(T, L.def_src[i0 + k], c, L, theta2, theta2f, 0, 0, 0, 0, sel, nullptr, flags);
         m += n.m;
         p += n.p;
         d += n.d;
+        q += n.q;
     }
     m = warp_sum(m);
     p = warp_sum(p);
     d = warp_sum(d);
-    unsigned long long om = 0, op = 0, od = 0;
+    q = warp_sum(q);
+    unsigned long long om = 0, op = 0, od = 0, oq = 0;
     if (lane == 0) {
         om = atomicAdd(&counters[0], (unsigned long long)m);
         op = atomicAdd(&counters[1], (unsigned long long)p);
         od = atomicAdd(&counters[2], (unsigned long long)d);
+        if (q) oq = atomicAdd(&counters[3], (unsigned long long)q);
     }
     om = __shfl_sync(0xffffffffu, om, 0);
     op = __shfl_sync(0xffffffffu, op, 0);
     od = __shfl_sync(0xffffffffu, od, 0);
-    const bool fits = (int64_t)(om + m) <= cap_m && (int64_t)(op + p) <= cap_p && (int64_t)(od + d) <= cap_d;
+    oq = __shfl_sync(0xffffffffu, oq, 0);
+    const bool fits = (int64_t)(om + m) <= cap_m && (int64_t)(op + p) <= cap_p &&
+                      (int64_t)(od + d) <= cap_d && (int64_t)(oq + q) <= cap_q;
     if (lane == 0) {
         L.m2l_off[t] = (int)om;
         L.m2l_cnt[t] = fits ? m : 0;
@@ -270,22 +289,25 @@ __global__ void __launch_bounds__(128)
         L.p2p_cnt[t] = fits ? p : 0;
         L.def_off[t] = (int)od;
         L.def_cnt[t] = fits ? d : 0;
+        L.m2p_off[t] = (int)oq;
+        L.m2p_cnt[t] = fits ? q : 0;
     }
     if (!fits) return;
-    int64_t rm = 0, rp = 0;
+    int64_t rm = 0, rp = 0, rq = 0;
     int rd = 0;
     for (int k0 = 0; k0 < ni; k0 += 32) {
         const int k = k0 + lane;
         const int S0 = k < ni ? L.def_src[i0 + k] : -1;
-        Counts n = {0, 0, 0};
-        if (S0 >= 0) n = resolve<false>(T, S0, c, L, theta2, theta2f, 0, 0, 0, sel, nullptr, flags);
-        const int em = warp_excl(n.m), ep = warp_excl(n.p), ed = warp_excl(n.d);
+        Counts n = {0, 0, 0, 0};
+        if (S0 >= 0) n = resolve<false>(T, S0, c, L, theta2, theta2f, 0, 0, 0, 0, sel, nullptr, flags);
+        const int em = warp_excl(n.m), ep = warp_excl(n.p), ed = warp_excl(n.d), eq = warp_excl(n.q);
         if (S0 >= 0)
             resolve<true>(T, S0, c, L, theta2, theta2f, (int64_t)om + rm + em, (int64_t)op + rp + ep,
-                          (int)od + rd + ed, sel, hash_keys, flags);
+                          (int)od + rd + ed, (int64_t)oq + rq + eq, sel, hash_keys, flags);
         rm += warp_sum(n.m);
         rp += warp_sum(n.p);
         rd += warp_sum(n.d);
+        rq += warp_sum(n.q);
     }
 }
 
@@ -346,6 +368,8 @@ __global__ void k_root_lists(CellArrays c, ListArrays L, int nsys, unsigned long
             L.p2p_cnt[s] = leaf ? 1 : 0;
             L.def_off[s] = od;
             L.def_cnt[s] = leaf ? 0 : 1;
+            L.m2p_off[s] = 0;
+            L.m2p_cnt[s] = 0;
             if (leaf) {
                 L.p2p_src[op] = s;
                 L.p2p_tgt[op] = s;
@@ -361,6 +385,7 @@ __global__ void k_root_lists(CellArrays c, ListArrays L, int nsys, unsigned long
         counters[0] = 0;
         counters[1] = (unsigned long long)base_p;
         counters[2] = (unsigned long long)base_d;
+        counters[3] = 0;
     }
 }
 

@@ -19,10 +19,10 @@ LIB_PATH = os.path.join(_HERE, "_build", "libfmm.so")
 FMM_OK, FMM_ERR_ARG, FMM_ERR_NONFINITE, FMM_ERR_CAPACITY, FMM_ERR_CUDA, FMM_ERR_TIMEOUT, \
     FMM_ERR_NOMEM = range(7)
 PRECISION = {"fp32": 0, "tf32x3": 1, "bf16x3": 2}
-SELECT = {"plain": 0, "autotune": 1, "learned": 2, "table": 3}
+SELECT = {"plain": 0, "autotune": 1, "learned": 2, "table": 3, "treecode": 4}
 SELECT_NB = 128
 EXPORT = {"box": 0, "keys": 1, "order": 2, "cells": 3, "p2p": 4, "m2l": 5, "multipole": 6,
-          "local": 7, "select": 8}
+          "local": 7, "select": 8, "m2p": 9}
 
 # every symbol the header declares
 ABI_SYMBOLS = ("fmm_default_options", "fmm_laplace3d", "fmm_laplace3d_ex", "fmm_laplace3d_host",
@@ -62,7 +62,8 @@ class Stats(ctypes.Structure):
                                               "n_offset_classes", "n_m2l_blocks",
                                               "n_launches")] + \
                [(n, ctypes.c_float) for n in ("ms_tree", "ms_upward", "ms_traverse", "ms_m2l",
-                                              "ms_downward", "ms_p2p", "ms_total")]
+                                              "ms_downward", "ms_p2p", "ms_total")] + \
+               [("n_m2p_pairs", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -251,7 +252,7 @@ def direct(xyz, q):
 _EXPORT_DTYPE = {"box": (np.float64, 4), "keys": (np.uint64, None), "order": (np.int32, None),
                  "cells": (np.int64, 6), "p2p": (np.int32, 2), "m2l": (np.int32, 3),
                  "multipole": (np.float32, "P2pad"), "local": (np.float32, "P2pad"),
-                 "select": (np.uint8, SELECT_NB)}
+                 "select": (np.uint8, SELECT_NB), "m2p": (np.int32, 2)}
 
 
 def export(what: str, p: int | None = None) -> np.ndarray:

@@ -45,6 +45,10 @@ def _compare(f, sel):
     assert np.array_equal(pair_codes(et, es, oid, f.ncells), pair_codes(gp[:, 0], gp[:, 1], gid, f.ncells))
     assert np.array_equal(pair_codes(ol["m2l_t"], ol["m2l_s"], oid, f.ncells),
                           pair_codes(gm[:, 0], gm[:, 1], gid, f.ncells))
+    qt, qs = f.m2p_list()
+    et, es = expand_p2p_to_leaves(oc, qt, qs)
+    gq = fmm.export("m2p")
+    assert np.array_equal(pair_codes(et, es, oid, f.ncells), pair_codes(gq[:, 0], gq[:, 1], gid, f.ncells))
     return np.any(oc["nchild"][ol["p2p_t"]] > 0)
 
 
@@ -117,3 +121,28 @@ def test_batched_with_table_matches_separate_solves():
         f = O.Fmm(x[a:b], q[a:b], 5, 0.5, 6, sel=sel)
         ophi, ograd = f.evaluate()
         assert rel_l2(phi[a:b], ophi) < TOL_ORACLE and rel_l2(grad[a:b], ograd) < TOL_ORACLE
+
+
+@pytest.mark.parametrize("dist,n,p,theta,ncrit", [("uniform", 20000, 5, 0.5, 8), ("plummer", 15000, 8, 0.4, 6),
+                                                  ("shell", 12000, 4, 0.5, 12)])
+def test_treecode_matches_oracle(dist, n, p, theta, ncrit):
+    from paper_1108_5815_gb300 import fmm
+    x, q = inputs.make(dist, n, 300 + n)
+    phi, grad, st = gpu_solve(x, q, p, theta, ncrit, stats=True, select="treecode")
+    sel = np.full((NB, NB), 2, np.uint8)
+    f = O.Fmm(x, q, p, theta, ncrit, sel=sel)
+    _compare(f, sel)
+    assert st["n_m2l_pairs"] == 0 and st["n_m2p_pairs"] > 0
+    ophi, ograd = f.evaluate()
+    assert rel_l2(phi, ophi) < TOL_ORACLE and rel_l2(grad, ograd) < TOL_ORACLE
+
+
+def test_three_way_random_table_matches_oracle():
+    rng = np.random.default_rng(21)
+    sel = rng.integers(0, 3, (NB, NB)).astype(np.uint8)
+    x, q = inputs.make("plummer", 25000, 61)
+    phi, grad = gpu_solve(x, q, 6, 0.45, 5, select=sel)
+    f = O.Fmm(x, q, 6, 0.45, 5, sel=sel)
+    _compare(f, sel)
+    ophi, ograd = f.evaluate()
+    assert rel_l2(phi, ophi) < TOL_ORACLE and rel_l2(grad, ograd) < TOL_ORACLE

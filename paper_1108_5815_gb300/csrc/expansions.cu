@@ -551,8 +551,9 @@ __global__ void __launch_bounds__(32 * kM2PWarps)
         const int i = i0 + lane;
         const bool valid = i < e;
         const float4 pt = pts[valid ? i : b];
-        const float rx = (float)(((double)pt.x - cT[0]) / sT), ry = (float)(((double)pt.y - cT[1]) / sT),
-                    rz = (float)(((double)pt.z - cT[2]) / sT);
+        const double isT = 1.0 / sT;
+        const float rx = (float)(((double)pt.x - cT[0]) * isT), ry = (float)(((double)pt.y - cT[1]) * isT),
+                    rz = (float)(((double)pt.z - cT[2]) * isT);
         float phi = 0.f, dz = 0.f, dpr = 0.f, dpi = 0.f;
         for (int k = 0; k < cnt; ++k) {
             const int S = slist[k];
@@ -560,10 +561,11 @@ __global__ void __launch_bounds__(32 * kM2PWarps)
             if (lane == 0) {
                 double cS[3], sS;
                 cell_centre_side(c, S, box, cS, sS);
-                geo[0] = (float)((cT[0] - cS[0]) / sS);
-                geo[1] = (float)((cT[1] - cS[1]) / sS);
-                geo[2] = (float)((cT[2] - cS[2]) / sS);
-                geo[3] = (float)(sT / sS);
+                const double isS = 1.0 / sS;  // sides are powers of two times the box side
+                geo[0] = (float)((cT[0] - cS[0]) * isS);
+                geo[1] = (float)((cT[1] - cS[1]) * isS);
+                geo[2] = (float)((cT[2] - cS[2]) * isS);
+                geo[3] = (float)(sT * isS);
             }
             for (int j = lane; j < P2pad; j += 32) {
                 const float v = j < P2 ? M[(int64_t)S * P2pad + j] : 0.f;

@@ -297,12 +297,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         // ------------------------------------------------------------ producers
         // Thread (warp, lane) owns A rows grp*8 + (lane & 7) for grp = warp + 8j (j < 2),
         // and the 16-byte chunks (lane >> 3) + 4h of each (h < 2 in TF32, h = 0 in BF16).
-        // The loads of stage g+1 are issued before stage g is split and stored.
+        // The loads of stage g+2 are issued before stage g is split and stored.
         // Thread 0 also issues the two bulk copies of stage g's B (hi, lo).
         const int sub = lane & 7, cq = lane >> 3;
         constexpr int V = 2;  // float4 per row and thread per stage
         const bool bissuer = threadIdx.x == 0;
-        float4 cur[NG][V], nxt[NG][V];
         int srow[2] = {0, 0};
         bool svalid[2] = {false, false};
         auto load_stage = [&](int g, float4 (&buf)[NG][V]) {
@@ -335,20 +334,17 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
         };
         int issued = 0;  // B stages issued by thread 0
-        if (nsteps > 0) load_stage(0, nxt);
-        for (int g = 0; g < nsteps; ++g) {
-#pragma unroll
-            for (int j = 0; j < NG; ++j)
-#pragma unroll
-                for (int v = 0; v < V; ++v) cur[j][v] = nxt[j][v];
-            if (g + 1 < nsteps) load_stage(g + 1, nxt);
+        // one pipeline step: consume stage g from `cur`, first issuing the loads of
+        // stage g + 2 into `ahead` (three register buffers in rotation)
+        auto step = [&](int g, float4 (&cur)[NG][V], float4 (&ahead)[NG][V]) -> bool {
+            if (g + 2 < nsteps) load_stage(g + 2, ahead);
             const int s = g % nstages;
             if (g >= nstages && !mbar_wait(&empty[s], (uint32_t)((g / nstages) - 1) & 1u)) {
                 atomicOr(&flags[kFlagTimeout], 1);
                 s_abort = 1;
-                break;
+                return false;
             }
-            if (s_abort) break;
+            if (s_abort) return false;
             unsigned char *st = smem + (size_t)s * stage_bytes;
             if (bissuer) {
                 const int e = U.e0 + g / nkc, kc = g % nkc;
@@ -379,6 +375,15 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             fence_proxy_async();
             mbar_arrive(&full[s]);
+            return true;
+        };
+        float4 b0[NG][V], b1[NG][V], b2[NG][V];
+        if (nsteps > 0) load_stage(0, b0);
+        if (nsteps > 1) load_stage(1, b1);
+        for (int g = 0; g < nsteps; g += 3) {
+            if (!step(g, b0, b2)) break;
+            if (g + 1 >= nsteps || !step(g + 1, b1, b0)) break;
+            if (g + 2 >= nsteps || !step(g + 2, b2, b1)) break;
         }
         if (bissuer) {
             // no B copy may still be landing when the CTA ends (matters after an abort)

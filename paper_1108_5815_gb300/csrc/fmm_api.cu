@@ -518,10 +518,10 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
     int *p2p_counter = need<int>(ws, "p2p_counter", 1, st);
     FMM_CUDA_TRY(cudaMemsetAsync(p2p_counter, 0, sizeof(int), st));
     {
-        // 8 blocks (32 warps) per SM: close to P2P's own best occupancy, and it
-        // leaves registers and warp slots for the small far-field kernels, so their
-        // dependent launches do not wait for P2P blocks to retire.  (Leaving room for
-        // the M2L kernel as well was measured slower: the two compete for issue slots.)
+        // 8 blocks (32 warps) per SM, P2P's own best occupancy.  At 64 registers a
+        // thread this fills the register file, so the far-field chain's kernels run
+        // after P2P.  Starting P2P together with M2L instead (so that the two share
+        // SMs) was measured no faster: both kernels then ran at half speed.
         int nsm = 152;
         FMM_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ws.device));
         const unsigned blocks = (unsigned)std::min<int64_t>(ceil_div(nleaves, 4), (int64_t)nsm * 8);

@@ -327,58 +327,130 @@ __global__ void __launch_bounds__(32)
     }
 }
 
-// Parents [a, b) (one level): M^_P = sum over children of A_octant M^_child.
-// Block per parent, thread per output row; the matrices are stored input-major.
-__global__ void k_m2m(CellArrays c, int a, int b, const float *__restrict__ m2m, int P2, int P2pad,
-                      float *__restrict__ M)
+// Octant-batched shifts.  A block takes 32 consecutive parents of one level, one
+// octant o and one 128-row tile of output coefficients, and multiplies the
+// octant's matrix (read once per block, 32 K-rows at a time through shared
+// memory) with the rows of the 32 (parent, child with octant o) pairs at once:
+//   M2M: T_child = A_o M^_child   (then M^_parent = sum of T over its children,
+//        in octant order, k_m2m_sum);
+//   L2L: L^_child += A_o L^_parent.
+// A matrix is column-major: entry (row j, column k) at k * P2pad + j.  Each
+// thread keeps 4 output rows x 8 pairs in registers.
+template <bool L2L>
+__global__ void __launch_bounds__(128)
+    k_shift_batched(CellArrays c, int a, int b, const float *__restrict__ mats, int P2, int P2pad,
+                    const float *in, float *out)  // L2L: in and out are the same array (disjoint rows)
 {
-    extern __shared__ float sm_child[];  // P2pad
-    const int cell = a + blockIdx.x;
-    if (cell >= b) return;
-    const int nch = c.nchild[cell];
-    if (nch == 0) return;
-    const int c0 = c.child0[cell];
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int k = 0; k < nch; ++k) {
-        const int ch = c0 + k;
-        const int o = (int)(c.prefix[ch] & 7ull);
-        __syncthreads();
-        for (int i = threadIdx.x; i < P2pad; i += blockDim.x) sm_child[i] = M[(int64_t)ch * P2pad + i];
-        __syncthreads();
-        const float *A = m2m + (int64_t)o * P2pad * P2pad;
+    __shared__ __align__(16) float sA[32][128];
+    __shared__ __align__(16) float sC[32][32];
+    __shared__ int sch[32];
+    __shared__ int sany;
+    const int t = threadIdx.x;
+    const int p0 = a + blockIdx.x * 32;
+    const int np = min(32, b - p0);
+    const int j0 = blockIdx.y * 128;
+    const int o = blockIdx.z;
+    const int jg = t & 31, pg = t >> 5;  // rows j0 + 4 jg .. +3, pairs 8 pg .. +7
+    if (t == 0) sany = 0;
+    __syncthreads();
+    if (t < 32) {
+        int ch = -1;
+        if (t < np) {
+            const int P = p0 + t, c0 = c.child0[P], nch = c.nchild[P];
+            for (int k = 0; k < nch; ++k)
+                if ((int)(c.prefix[c0 + k] & 7ull) == o) ch = c0 + k;
+        }
+        sch[t] = ch;
+        if (ch >= 0) sany = 1;
+    }
+    __syncthreads();
+    if (!sany) return;
+    float acc[4][8];
 #pragma unroll
-        for (int rr = 0; rr < 4; ++rr) {
-            const int row = threadIdx.x + rr * blockDim.x;
-            if (row < P2) {
-                float s = 0.f;
-                for (int col = 0; col < P2; ++col) s = fmaf(A[(int64_t)col * P2pad + row], sm_child[col], s);
-                acc[rr] += s;
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc[r][q] = 0.f;
+    const float *A = mats + (int64_t)o * P2pad * P2pad;
+    for (int k0 = 0; k0 < P2; k0 += 32) {
+        for (int idx = t; idx < 32 * 128; idx += 128) {
+            const int kr = idx >> 7, jj = idx & 127;
+            const int k = k0 + kr, j = j0 + jj;
+            sA[kr][jj] = (k < P2 && j < P2pad) ? A[(int64_t)k * P2pad + j] : 0.f;
+        }
+        for (int idx = t; idx < 32 * 32; idx += 128) {
+            const int q = idx >> 5, kr = idx & 31;
+            const int k = k0 + kr;
+            const int row = L2L ? (sch[q] >= 0 ? p0 + q : -1) : sch[q];
+            sC[kr][q] = (row >= 0 && k < P2) ? in[(int64_t)row * P2pad + k] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int kr = 0; kr < 32; ++kr) {
+            const float4 av = *reinterpret_cast<const float4 *>(&sA[kr][4 * jg]);
+            const float4 c0v = *reinterpret_cast<const float4 *>(&sC[kr][8 * pg]);
+            const float4 c1v = *reinterpret_cast<const float4 *>(&sC[kr][8 * pg + 4]);
+            const float aa[4] = {av.x, av.y, av.z, av.w};
+            const float cc[8] = {c0v.x, c0v.y, c0v.z, c0v.w, c1v.x, c1v.y, c1v.z, c1v.w};
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int q = 0; q < 8; ++q) acc[r][q] = fmaf(aa[r], cc[q], acc[r][q]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int ch = sch[8 * pg + q];
+        if (ch < 0) continue;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int j = j0 + 4 * jg + r;
+            if (j >= P2pad) continue;
+            if (L2L) {
+                if (j < P2) out[(int64_t)ch * P2pad + j] += acc[r][q];
+            } else {
+                out[(int64_t)ch * P2pad + j] = j < P2 ? acc[r][q] : 0.f;
             }
         }
     }
-#pragma unroll
-    for (int rr = 0; rr < 4; ++rr) {
-        const int row = threadIdx.x + rr * blockDim.x;
-        if (row < P2pad) M[(int64_t)cell * P2pad + row] = row < P2 ? acc[rr] : 0.f;
+}
+
+// M^_parent = sum over its children (octant order) of T_child, parents [a, b).
+__global__ void k_m2m_sum(CellArrays c, int a, int b, int P2pad, const float *__restrict__ T, float *__restrict__ M)
+{
+    const int nq = P2pad / 4;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)(b - a) * nq;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int P = a + (int)(i / nq), q4 = (int)(i % nq);
+        const int nch = c.nchild[P];
+        if (nch == 0) continue;
+        const int c0 = c.child0[P];
+        float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int k = 0; k < nch; ++k) {
+            const float4 v = reinterpret_cast<const float4 *>(T + (int64_t)(c0 + k) * P2pad)[q4];
+            s.x += v.x;
+            s.y += v.y;
+            s.z += v.z;
+            s.w += v.w;
+        }
+        reinterpret_cast<float4 *>(M + (int64_t)P * P2pad)[q4] = s;
     }
 }
 
-// Children [a, b) (one level): L^_child += A_octant L^_parent.
-__global__ void k_l2l(CellArrays c, int a, int b, const float *__restrict__ l2l, int P2, int P2pad,
-                      float *__restrict__ L)
+void launch_shift_batched(bool l2l, const CellArrays &c, int a, int b, const float *mats, int P2, int P2pad,
+                          float *E, float *T, cudaStream_t st)
 {
-    extern __shared__ float sm_par[];
-    const int cell = a + blockIdx.x;
-    if (cell >= b) return;
-    const int par = c.parent[cell];
-    const int o = (int)(c.prefix[cell] & 7ull);
-    for (int i = threadIdx.x; i < P2pad; i += blockDim.x) sm_par[i] = L[(int64_t)par * P2pad + i];
-    __syncthreads();
-    const float *A = l2l + (int64_t)o * P2pad * P2pad;
-    for (int row = threadIdx.x; row < P2; row += blockDim.x) {
-        float s = 0.f;
-        for (int col = 0; col < P2; ++col) s = fmaf(A[(int64_t)col * P2pad + row], sm_par[col], s);
-        L[(int64_t)cell * P2pad + row] += s;
+    if (b <= a) return;
+    const dim3 grid((unsigned)ceil_div(b - a, 32), (unsigned)ceil_div(P2pad, 128), 8);
+    if (l2l) {
+        k_shift_batched<true><<<grid, 128, 0, st>>>(c, a, b, mats, P2, P2pad, E, E);
+        FMM_LAUNCH_CHECK();
+    } else {
+        k_shift_batched<false><<<grid, 128, 0, st>>>(c, a, b, mats, P2, P2pad, E, T);
+        FMM_LAUNCH_CHECK();
+        const int64_t n = (int64_t)(b - a) * (P2pad / 4);
+        k_m2m_sum<<<(unsigned)std::min<int64_t>(ceil_div(n, 256), 152 * 16), 256, 0, st>>>(c, a, b, P2pad, T, E);
+        FMM_LAUNCH_CHECK();
     }
 }
 

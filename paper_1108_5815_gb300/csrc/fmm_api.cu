@@ -666,10 +666,10 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
         k_p2m<<<nleaves, 32, sh, fs>>>(c, leaves, nleaves, pts, box, p, P2pad, M);
         FMM_LAUNCH_CHECK();
     }
+    float *mtmp = need<float>(ws, "m2m_tmp", (size_t)ncells * P2pad, fs);
     for (int l = depth - 1; l >= 0; --l) {
         const int a = lstart[l], b = lstart[l + 1];
-        k_m2m<<<b - a, 128, P2pad * sizeof(float), fs>>>(c, a, b, get<float>(ws, "m2m"), P2, P2pad, M);
-        FMM_LAUNCH_CHECK();
+        launch_shift_batched(false, c, a, b, get<float>(ws, "m2m"), P2, P2pad, M, mtmp, fs);
     }
     ev.rec(7, fs);
 
@@ -715,11 +715,8 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
     ev.rec(4, fs);
 
     // ---------------------------------------------------------- downward pass
-    for (int l = 1; l <= depth; ++l) {
-        const int a = lstart[l], b = lstart[l + 1];
-        k_l2l<<<b - a, 128, P2pad * sizeof(float), fs>>>(c, a, b, get<float>(ws, "l2l"), P2, P2pad, Lx);
-        FMM_LAUNCH_CHECK();
-    }
+    for (int l = 0; l < depth; ++l)  // parents at level l, children at level l + 1
+        launch_shift_batched(true, c, lstart[l], lstart[l + 1], get<float>(ws, "l2l"), P2, P2pad, Lx, nullptr, fs);
     k_l2p<<<nleaves, 32, 4 * P2pad * sizeof(float), fs>>>(c, leaves, nleaves, pts, box, p, P2pad, Lx,
                                                           far);
     FMM_LAUNCH_CHECK();

@@ -101,8 +101,11 @@ __global__ void k_build_m2l_tables(const uint64_t *class_keys, const int *cache_
 __global__ void k_build_shift_tables(int p, int P2pad, float *m2m, float *l2l);
 __global__ void k_p2m(CellArrays c, const int *leaves, int nleaves, const float4 *pts,
                       const double *box, int p, int P2pad, float *M);
-__global__ void k_m2m(CellArrays c, int a, int b, const float *m2m, int P2, int P2pad, float *M);
-__global__ void k_l2l(CellArrays c, int a, int b, const float *l2l, int P2, int P2pad, float *L);
+// M2M (l2l = false: parents [a, b) of E from their children, through the
+// per-child scratch T[ncells][P2pad]) or L2L (l2l = true: the children of
+// parents [a, b) of E from them), octant-batched.
+void launch_shift_batched(bool l2l, const CellArrays &c, int a, int b, const float *mats, int P2, int P2pad,
+                          float *E, float *T, cudaStream_t st);
 __global__ void k_l2p(CellArrays c, const int *leaves, int nleaves, const float4 *pts,
                       const double *box, int p, int P2pad, const float *L, float4 *far);
 // M2P: blocks of kM2PWarps warps, one target leaf per warp; dynamic shared memory m2p_smem(p, P2pad).

@@ -472,6 +472,7 @@ def main():
             select_modes[sel] = {"value": n / (m / 1e3), "ms_per_step": m,
                                  "n_m2l_pairs": sts[-1]["n_m2l_pairs"],
                                  "n_m2p_pairs": sts[-1]["n_m2p_pairs"],
+                                 "n_p2p_pairs": sts[-1]["n_p2p_pairs"],
                                  "n_p2p_interactions": sts[-1]["n_p2p_interactions"],
                                  "accuracy": accuracy(x, q, phi.cpu().numpy(), grad.cpu().numpy(), off=off)}
 
@@ -517,7 +518,7 @@ def main():
                 "clocks": clocks, "phases_ms": phases,
                 "counts": {k: st0[k] for k in ("ncells", "nleaves", "depth", "n_p2p_pairs",
                                                "n_p2p_interactions", "n_m2l_pairs",
-                                               "n_offset_classes", "n_m2l_blocks")}}
+                                               "n_offset_classes", "n_m2l_blocks", "n_m2p_pairs")}}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

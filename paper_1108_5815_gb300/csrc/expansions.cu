@@ -26,6 +26,9 @@
 //     stays bounded by |x|^n.
 // The M2L/M2M/L2L operators become real (P2 x P2) matrices, computed in FP64
 // from the complex formulas and stored in FP32.
+#include <cmath>
+#include <mutex>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -244,6 +247,39 @@ constexpr int kMaxChunks = 14;  // ceil(448 / 32): p <= 20
 
 }  // namespace
 
+// Coefficients of the order-normalised three-term recurrences, for n <= kRecMax
+// at index n(n+1)/2 + m:  R^_n^m = kRecA z R^_{n-1}^m - kRecB r^2 R^_{n-2}^m and
+// I^_n^m = (kRecA z I^_{n-1}^m - kRecB I^_{n-2}^m) / r^2, with
+// kRecA = (2n-1)/sqrt((n+m)(n-m)), kRecB = sqrt((n+m-1)(n-m-1))/sqrt((n+m)(n-m));
+// diagonals R^_m^m = kRecD (x+iy) R^_{m-1}^{m-1} (I^ likewise over r^2),
+// kRecD = -sqrt((2m-1)/(2m)).  Filled once per device from FP64 values.
+constexpr int kRecMax = 21;
+constexpr int kRecTri = (kRecMax + 1) * (kRecMax + 2) / 2;
+__constant__ float c_rec_a[kRecTri], c_rec_b[kRecTri], c_rec_d[kRecMax + 1];
+
+void init_recurrence_tables()
+{
+    static std::mutex mu;
+    static bool done[64] = {};
+    int dev = 0;
+    FMM_CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    if (dev < 64 && done[dev]) return;
+    float a[kRecTri], b[kRecTri], d[kRecMax + 1];
+    for (int n = 0; n <= kRecMax; ++n)
+        for (int m = 0; m <= n; ++m) {
+            const int t = n * (n + 1) / 2 + m;
+            const double den = n > m ? 1.0 / std::sqrt((double)(n + m) * (n - m)) : 0.0;
+            a[t] = (float)((2.0 * n - 1.0) * den);
+            b[t] = n > m + 1 ? (float)(std::sqrt((double)(n + m - 1) * (n - m - 1)) * den) : 0.f;
+        }
+    for (int m = 0; m <= kRecMax; ++m) d[m] = m > 0 ? (float)-std::sqrt((2.0 * m - 1.0) / (2.0 * m)) : 1.f;
+    FMM_CUDA_TRY(cudaMemcpyToSymbol(c_rec_a, a, sizeof(a)));
+    FMM_CUDA_TRY(cudaMemcpyToSymbol(c_rec_b, b, sizeof(b)));
+    FMM_CUDA_TRY(cudaMemcpyToSymbol(c_rec_d, d, sizeof(d)));
+    if (dev < 64) done[dev] = true;
+}
+
 // One warp per leaf.  Each lane evaluates R^(xi) of one particle into its
 // shared-memory row; the lanes then sum the rows column by column.
 __global__ void __launch_bounds__(32)
@@ -277,7 +313,7 @@ __global__ void __launch_bounds__(32)
             float mre = 1.f, mim = 0.f;  // R^_m^m
             for (int m = 0; m <= p; ++m) {
                 if (m > 0) {
-                    const float f = -sqrtf((2.f * m - 1.f) / (2.f * m));
+                    const float f = c_rec_d[m];
                     const float nre = f * (x * mre - y * mim), nim = f * (x * mim + y * mre);
                     mre = nre;
                     mim = nim;
@@ -289,11 +325,10 @@ __global__ void __launch_bounds__(32)
                         rr = mre;
                         ri = mim;
                     } else {
-                        const float a = (2.f * n - 1.f) * z;
-                        const float bb = r2 * sqrtf((float)((n - m - 1) * (n + m - 1)));
-                        const float inv = rsqrtf((float)((n + m) * (n - m)));
-                        rr = (a * p1r - bb * p2r) * inv;
-                        ri = (a * p1i - bb * p2i) * inv;
+                        const int t = n * (n + 1) / 2 + m;
+                        const float a = c_rec_a[t] * z, bb = c_rec_b[t] * r2;
+                        rr = a * p1r - bb * p2r;
+                        ri = a * p1i - bb * p2i;
                         p2r = p1r;
                         p2i = p1i;
                         p1r = rr;
@@ -495,7 +530,7 @@ __global__ void __launch_bounds__(32)
         float mre = 1.f, mim = 0.f;
         for (int m = 0; m <= p; ++m) {
             if (m > 0) {
-                const float f = -sqrtf((2.f * m - 1.f) / (2.f * m));
+                const float f = c_rec_d[m];
                 const float nre = f * (x * mre - y * mim), nim = f * (x * mim + y * mre);
                 mre = nre;
                 mim = nim;
@@ -508,11 +543,10 @@ __global__ void __launch_bounds__(32)
                     rr = mre;
                     ri = mim;
                 } else {
-                    const float a = (2.f * n - 1.f) * z;
-                    const float bb = r2 * sqrtf((float)((n - m - 1) * (n + m - 1)));
-                    const float inv = rsqrtf((float)((n + m) * (n - m)));
-                    rr = (a * p1r - bb * p2r) * inv;
-                    ri = (a * p1i - bb * p2i) * inv;
+                    const int t = n * (n + 1) / 2 + m;
+                    const float a = c_rec_a[t] * z, bb = c_rec_b[t] * r2;
+                    rr = a * p1r - bb * p2r;
+                    ri = a * p1i - bb * p2i;
                     p2r = p1r;
                     p2i = p1i;
                     p1r = rr;

@@ -300,6 +300,7 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
                   cudaStream_t caller, const fmm_options &o, fmm_stats *stats, const uint8_t *sel)
 {
     ensure_streams(ws);
+    init_recurrence_tables();
     cudaStream_t st = ws.main_stream;
     FMM_CUDA_TRY(cudaEventRecord(ws.ev_in, caller));
     FMM_CUDA_TRY(cudaStreamWaitEvent(st, ws.ev_in, 0));
@@ -553,9 +554,9 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
         k_hash_compact<<<kHashCap / 256, 256, 0, fs>>>(hash_keys, hex, ukeys, uslot);
         FMM_LAUNCH_CHECK();
         if (nclass > 0 && nclass <= 6144) {
-            // few classes: one-block rank sort (small, so it runs beside P2P)
-            k_rank_classes<<<1, 128, sizeof(uint64_t) * nclass, fs>>>(ukeys, uslot, nclass, ukeys_alt,
-                                                                      slot_class);
+            // few classes: rank sort, one thread per key (fewer launches than the radix sort)
+            k_rank_classes<<<(unsigned)ceil_div(nclass, 128), 128, 0, fs>>>(ukeys, uslot, nclass, ukeys_alt,
+                                                                           slot_class);
             FMM_LAUNCH_CHECK();
             std::swap(ukeys, ukeys_alt);
         } else if (nclass > 0) {

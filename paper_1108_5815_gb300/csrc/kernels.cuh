@@ -101,6 +101,8 @@ __global__ void k_build_m2l_tables(const uint64_t *class_keys, const int *cache_
 __global__ void k_build_shift_tables(int p, int P2pad, float *m2m, float *l2l);
 __global__ void k_p2m(CellArrays c, const int *leaves, int nleaves, const float4 *pts,
                       const double *box, int p, int P2pad, float *M);
+// Fills the recurrence-coefficient tables P2M and L2P read (once per device).
+void init_recurrence_tables();
 // M2M (l2l = false: parents [a, b) of E from their children, through the
 // per-child scratch T[ncells][P2pad]) or L2L (l2l = true: the children of
 // parents [a, b) of E from them), octant-batched.

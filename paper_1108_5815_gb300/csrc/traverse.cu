@@ -389,18 +389,25 @@ __global__ void k_root_lists(CellArrays c, ListArrays L, int nsys, unsigned long
     }
 }
 
-// Sorts up to a few thousand distinct keys with one block: the rank of a key is
-// the number of smaller keys.  slot_class[slot of the key] = its rank.
-__global__ void k_rank_classes(const uint64_t *__restrict__ ukeys, const uint32_t *__restrict__ uslot,
-                               int n, uint64_t *__restrict__ sorted_keys, int *__restrict__ slot_class)
+// Sorts up to a few thousand distinct keys: the rank of a key is the number of
+// smaller keys (one thread per key).  slot_class[slot of the key] = its rank.
+__global__ void __launch_bounds__(128)
+    k_rank_classes(const uint64_t *__restrict__ ukeys, const uint32_t *__restrict__ uslot, int n,
+                   uint64_t *__restrict__ sorted_keys, int *__restrict__ slot_class)
 {
-    extern __shared__ uint64_t sk[];
-    for (int i = threadIdx.x; i < n; i += blockDim.x) sk[i] = ukeys[i];
-    __syncthreads();
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const uint64_t k = sk[i];
-        int r = 0;
-        for (int j = 0; j < n; ++j) r += sk[j] < k;
+    // each block ranks 128 keys against all n, staged through shared memory
+    __shared__ uint64_t sk[2048];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t k = i < n ? ukeys[i] : 0;
+    int r = 0;
+    for (int j0 = 0; j0 < n; j0 += 2048) {
+        const int m = min(2048, n - j0);
+        __syncthreads();
+        for (int j = threadIdx.x; j < m; j += blockDim.x) sk[j] = ukeys[j0 + j];
+        __syncthreads();
+        for (int j = 0; j < m; ++j) r += sk[j] < k;
+    }
+    if (i < n) {
         sorted_keys[r] = k;
         slot_class[uslot[i]] = r;
     }

@@ -119,6 +119,10 @@ WORKLOADS = {
     "plummer16m": dict(kind="plummer", n=16_777_216, p=10, theta=0.4, ncrit=64, max_depth=21, seed=1005),
     # a quarter-size uniform case with the same p/theta/ncrit, for profiler captures
     "uniform262k": dict(kind="uniform", n=262_144, p=10, theta=0.4, ncrit=64, max_depth=10, seed=1006),
+    # the paper's adaptive test: random points on a spherical shell, N_crit = 20,
+    # FMM and hybrid at p = 8 (Results section, Fig. "cpu" C)
+    "shell100k": dict(kind="shell", n=100_000, p=8, theta=0.5, ncrit=20, max_depth=21, seed=1007),
+    "shell1m": dict(kind="shell", n=1_000_000, p=8, theta=0.5, ncrit=20, max_depth=21, seed=1008),
 }
 
 

@@ -679,19 +679,34 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
     if (tensor) {
         // work units: (tile, contiguous run of its class blocks), about six per SM
         const int chunk = std::max(8, (int)ceil_div(std::max(nent, 1), 6 * 152));
-        std::vector<M2LUnit> units;
-        std::vector<int> ubase(ntiles + 1, 0);
+        // units in execution order (rank within the tile, tile): resident CTAs then work on
+        // similar class ranges; tile_units lists each tile's units in class order for the sum
+        std::vector<int> nut(ntiles), ubase(ntiles + 1, 0);
+        int maxr = 0;
         for (int t = 0; t < ntiles; ++t) {
-            ubase[t] = (int)units.size();
-            for (int e = h_eb[t]; e < h_eb[t + 1]; e += chunk)
-                units.push_back({t, e, std::min(e + chunk, h_eb[t + 1]), 0});
+            nut[t] = (int)ceil_div(h_eb[t + 1] - h_eb[t], chunk);
+            ubase[t + 1] = ubase[t] + nut[t];
+            maxr = std::max(maxr, nut[t]);
         }
-        ubase[ntiles] = (int)units.size();
-        const int nunits = (int)units.size();
+        const int nunits = ubase[ntiles];
+        std::vector<M2LUnit> units;
+        units.reserve(nunits);
+        std::vector<int> tile_units(std::max(nunits, 1));
+        for (int r = 0; r < maxr; ++r)
+            for (int t = 0; t < ntiles; ++t) {
+                if (r >= nut[t]) continue;
+                const int e = h_eb[t] + r * chunk;
+                tile_units[ubase[t] + r] = (int)units.size();
+                units.push_back({t, e, std::min(e + chunk, h_eb[t + 1]), 0});
+            }
         M2LUnit *d_units = need<M2LUnit>(ws, "m2l_units", std::max(nunits, 1), fs);
         int *d_ubase = need<int>(ws, "m2l_ubase", ntiles + 1, fs);
+        int *d_tunits = need<int>(ws, "m2l_tile_units", std::max(nunits, 1), fs);
         float *partial = need<float>(ws, "m2l_partial", (size_t)std::max(nunits, 1) * 128 * P2pad, fs);
-        if (nunits > 0) upload(ws, d_units, units.data(), sizeof(M2LUnit) * nunits, fs);
+        if (nunits > 0) {
+            upload(ws, d_units, units.data(), sizeof(M2LUnit) * nunits, fs);
+            upload(ws, d_tunits, tile_units.data(), sizeof(int) * nunits, fs);
+        }
         upload(ws, d_ubase, ubase.data(), sizeof(int) * (ntiles + 1), fs);
         ev.rec(3, fs);
         // class matrices split into hi/lo in the stage layout, once per class slot and precision
@@ -705,7 +720,7 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
         launch_split_tables(bf16, get<float>(ws, "table"), ws.split_slots, ws.table_slots - ws.split_slots, P2pad,
                             tsplit, fs);
         ws.split_slots = ws.table_slots;
-        launch_m2l_tc(bf16, nunits, d_units, ntiles, d_ubase,
+        launch_m2l_tc(bf16, nunits, d_units, ntiles, d_ubase, d_tunits,
                       entry_class, src, tile_cells, M, tsplit, P2pad, partial, Lx,
                       flags, fs);
     } else {

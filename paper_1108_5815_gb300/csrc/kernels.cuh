@@ -128,9 +128,9 @@ struct M2LUnit {
 bool m2l_tc_supported(int P2pad);
 size_t m2l_tc_smem(int P2pad, bool bf16, int &nstages);
 void launch_m2l_tc(bool bf16, int nunits, const void *units, int ntiles, const int *unit_base,
-                   const int *entry_class, const int *src, const int *tile_cells, const float *M,
-                   const unsigned char *tsplit, int P2pad, float *partial, float *L, int *flags,
-                   cudaStream_t st);
+                   const int *tile_units, const int *entry_class, const int *src, const int *tile_cells,
+                   const float *M, const unsigned char *tsplit, int P2pad, float *partial, float *L,
+                   int *flags, cudaStream_t st);
 // Bytes of the hi/lo split class matrices of nslots classes, and the kernel that
 // writes slots [slot0, slot0 + nslots) of them from the FP32 tables.
 size_t m2l_split_bytes(int P2pad, bool bf16, int nslots);

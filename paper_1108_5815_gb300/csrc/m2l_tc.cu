@@ -40,7 +40,9 @@
 // wait is bounded: on expiry the kernel raises a flag and returns after
 // releasing its tensor memory.
 // A work unit is (tile, range of the tile's class blocks); its 128 x N result
-// goes to a partial buffer and k_m2l_reduce sums a tile's units in order.
+// goes to a partial buffer and k_m2l_reduce sums a tile's units in order.  Units
+// run in the order (rank within the tile, tile): the CTAs resident at one time
+// work on similar class ranges, so the class matrices they read stay in L2.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -494,8 +496,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
-__global__ void k_m2l_reduce(const int *__restrict__ unit_base, const float *__restrict__ partial,
-                             const int *__restrict__ tile_cells, int P2pad, float *__restrict__ L)
+// L rows of a tile = sum of its units' partials, in the order tile_units lists
+// them (the tile's class order).
+__global__ void k_m2l_reduce(const int *__restrict__ unit_base, const int *__restrict__ tile_units,
+                             const float *__restrict__ partial, const int *__restrict__ tile_cells, int P2pad,
+                             float *__restrict__ L)
 {
     const int tile = blockIdx.x;
     const int u0 = unit_base[tile], u1 = unit_base[tile + 1];
@@ -505,7 +510,8 @@ __global__ void k_m2l_reduce(const int *__restrict__ unit_base, const float *__r
         const int cell = tile_cells[(int64_t)tile * kTile + row];
         if (cell < 0) continue;
         float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int u = u0; u < u1; ++u) {
+        for (int i = u0; i < u1; ++i) {
+            const int u = tile_units[i];
             const float4 v = reinterpret_cast<const float4 *>(partial + ((int64_t)u * 128 + row) * P2pad)[q4];
             a.x += v.x;
             a.y += v.y;
@@ -580,9 +586,9 @@ size_t m2l_tc_smem(int P2pad, bool bf16, int &nstages)
 }
 
 void launch_m2l_tc(bool bf16, int nunits, const void *units, int ntiles, const int *unit_base,
-                   const int *entry_class, const int *src, const int *tile_cells, const float *M,
-                   const unsigned char *tsplit, int P2pad, float *partial, float *L, int *flags,
-                   cudaStream_t st)
+                   const int *tile_units, const int *entry_class, const int *src, const int *tile_cells,
+                   const float *M, const unsigned char *tsplit, int P2pad, float *partial, float *L,
+                   int *flags, cudaStream_t st)
 {
     int nstages = 0;
     const size_t smem = m2l_tc_smem(P2pad, bf16, nstages);
@@ -614,7 +620,7 @@ void launch_m2l_tc(bool bf16, int nunits, const void *units, int ntiles, const i
 #undef FMM_M2L_TC_LAUNCH
         FMM_LAUNCH_CHECK();
     }
-    k_m2l_reduce<<<ntiles, 256, 0, st>>>(unit_base, partial, tile_cells, P2pad, L);
+    k_m2l_reduce<<<ntiles, 256, 0, st>>>(unit_base, tile_units, partial, tile_cells, P2pad, L);
     FMM_LAUNCH_CHECK();
 }
 

@@ -35,6 +35,7 @@ constexpr int kStack = 192;
 constexpr int kP2PFlag = 1 << 30;  // deferred source that is a chosen P2P pair
 constexpr int kM2PFlag = 1 << 29;  // deferred source that is a chosen M2P pair
 constexpr int kCellMask = kM2PFlag - 1;
+constexpr int kFrontier = 256;  // sources of a leaf target split warp-wide before the walks
 
 struct TargetInfo {
     int t, level;
@@ -250,16 +251,76 @@ __global__ void __launch_bounds__(128)
                      int64_t cap_m, int64_t cap_p, int64_t cap_d, int64_t cap_q,
                      uint64_t *__restrict__ hash_keys, int *__restrict__ flags)
 {
+    __shared__ int sF[4][2][kFrontier];
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int t = a + warp;
     if (t >= b) return;
     const TargetInfo T = load_target(c, t);
     const int P = c.parent[t];
-    const int i0 = L.def_off[P], ni = L.def_cnt[P];
+    const int i0 = L.def_off[P];
+    int ni = L.def_cnt[P];
+    const int *F = L.def_src + i0;
+    if (T.leaf && ni <= kFrontier) {
+        // A leaf target resolves every inherited source it does not accept by a
+        // depth-first walk of the source's subtree, one source per lane; next to a
+        // dense region a few sources carry almost all the work.  Split the sources
+        // the walks would split first (not accepted, not leaves) in warp-wide rounds
+        // while the list fits in kFrontier entries; the walks then start from the
+        // pieces.  The set of pairs does not change, only the order of discovery.
+        int cur = 0;
+        for (int k = lane; k < ni; k += 32) sF[wib][0][k] = F[k];
+        __syncwarp();
+        auto splits = [&](int S, int &nc) {
+            nc = 1;
+            if ((S & (kP2PFlag | kM2PFlag)) || c.nchild[S] == 0) return false;
+            int Cs[3], hs;
+            cell_geom32(c.level[S], c.prefix[S], Cs, hs);
+            if (mac_accept(T, Cs, hs, theta2, theta2f)) return false;
+            nc = c.nchild[S];
+            return true;
+        };
+        for (int round = 0; round < 8; ++round) {
+            int total = 0;
+            bool any = false;
+            for (int k0 = 0; k0 < ni; k0 += 32) {
+                int nc = 0;
+                if (k0 + lane < ni) any |= splits(sF[wib][cur][k0 + lane], nc);
+                total += warp_sum(nc);
+            }
+            if (!__any_sync(0xffffffffu, any) || total > kFrontier) break;
+            int base = 0;
+            for (int k0 = 0; k0 < ni; k0 += 32) {
+                int nc = 0, S = -1;
+                bool sp = false;
+                if (k0 + lane < ni) {
+                    S = sF[wib][cur][k0 + lane];
+                    sp = splits(S, nc);
+                } else {
+                    nc = 0;
+                }
+                const int pos = base + warp_excl(nc);
+                if (k0 + lane < ni) {
+                    int *dst = sF[wib][cur ^ 1] + pos;
+                    if (sp) {
+                        const int c0 = c.child0[S];
+                        for (int j = 0; j < nc; ++j) dst[j] = c0 + j;
+                    } else {
+                        dst[0] = S;
+                    }
+                }
+                base += warp_sum(nc);
+            }
+            __syncwarp();
+            cur ^= 1;
+            ni = total;
+        }
+        __syncwarp();
+        F = sF[wib][cur];
+    }
     int m = 0, p = 0, d = 0, q = 0;
     for (int k = lane; k < ni; k += 32) {
-        const Counts n = resolve<false>(T, L.def_src[i0 + k], c, L, theta2, theta2f, 0, 0, 0, 0, sel, nullptr, flags);
+        const Counts n = resolve<false>(T, F[k], c, L, theta2, theta2f, 0, 0, 0, 0, sel, nullptr, flags);
         m += n.m;
         p += n.p;
         d += n.d;
@@ -297,7 +358,7 @@ __global__ void __launch_bounds__(128)
     int rd = 0;
     for (int k0 = 0; k0 < ni; k0 += 32) {
         const int k = k0 + lane;
-        const int S0 = k < ni ? L.def_src[i0 + k] : -1;
+        const int S0 = k < ni ? F[k] : -1;
         Counts n = {0, 0, 0, 0};
         if (S0 >= 0) n = resolve<false>(T, S0, c, L, theta2, theta2f, 0, 0, 0, 0, sel, nullptr, flags);
         const int em = warp_excl(n.m), ep = warp_excl(n.p), ed = warp_excl(n.d), eq = warp_excl(n.q);

@@ -56,7 +56,7 @@ def parse():
                     help="skip timing the other selection modes")
     ap.add_argument("--train-steps", type=int, default=3000)
     ap.add_argument("--tune-ncrit", action="store_true",
-                    help="pick ncrit with the measured autotuner before timing (single systems)")
+                    help="pick ncrit and the M2L work-unit size with the measured autotuner before timing")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -347,11 +347,15 @@ def main():
                                      out=(phi, grad), **k2)
 
     ncrit_tuning = None
-    if args.tune_ncrit and off is None:
-        cands = (16, 32, 64, 128, 256)
-        best, ms_c = fmm.tune_ncrit(xd, qd, w["p"], w["theta"], cands, **kw)
-        ncrit_tuning = {"candidates_ms": ms_c, "best": best, "workload_ncrit": w["ncrit"]}
-        w["ncrit"] = best
+    if args.tune_ncrit:
+        # the measured autotuner picks N_crit and the M2L work-unit size together
+        ncs, ucs = (32, 64, 128, 256, 512), (0, 8, 32, 128)
+        bn, bu, table = fmm.tune_schedule(xd, qd, w["p"], w["theta"], offsets=off, ncrit_candidates=ncs,
+                                          unit_candidates=ucs, **kw)
+        ncrit_tuning = {"candidates_ms": {f"ncrit={a},unit={b}": v for (a, b), v in table.items()},
+                        "best_ncrit": bn, "best_m2l_unit_blocks": bu, "workload_ncrit": w["ncrit"]}
+        w["ncrit"] = bn
+        kw["m2l_unit_blocks"] = bu
 
     for _ in range(args.warmup):
         solve()

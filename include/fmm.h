@@ -91,6 +91,9 @@ typedef struct {
     /* FMM_SELECT_TABLE: HOST uint8[FMM_SELECT_NB][FMM_SELECT_NB], read during the
      * call only; ignored by the other modes. */
     const unsigned char *select_table;
+    /* tensor-core M2L schedule: (target tile, offset class) blocks per work unit,
+     * 0 = automatic (about six units per SM, at least 8 blocks) */
+    int m2l_unit_blocks;
 } fmm_options;
 
 typedef struct {
@@ -236,6 +239,17 @@ fmm_status fmm_cost_model_train(int precision_mode, int p_lo, int p_hi, int step
  * NULL) receives candidate k's time.  Outputs of the solves are discarded. */
 fmm_status fmm_tune_ncrit(const float *xyz, const float *q, int64_t N, int p, double theta, void *stream,
                           const fmm_options *opt, const int *candidates, int ncand, float *ms, int *best);
+/* The measured autotuner for the schedule of a solve, single or batched
+ * (offsets = NULL for one system of N particles, else the host offsets of
+ * fmm_laplace3d_batched with N = offsets[nsys]): every pair of an N_crit
+ * candidate and an M2L work-unit size candidate (0 = automatic) is solved and
+ * timed with events (best of two after a sizing solve); ms[k * nunit + u] (may
+ * be NULL) receives the time of pair (k, u), *best_ncrit and *best_unit the
+ * fastest pair.  Outputs of the solves are discarded. */
+fmm_status fmm_tune_schedule(const float *xyz, const float *q, int64_t N, const int64_t *offsets, int nsys,
+                             int p, double theta, void *stream, const fmm_options *opt, const int *ncrit_cand,
+                             int nncrit, const int *unit_cand, int nunit, float *ms, int *best_ncrit,
+                             int *best_unit);
 /* Parameters as FP32 values: master != 0 gives the FP32 master copy, else the
  * FP16 copy the forward pass uses.  params holds n >= FMM_COST_MODEL_PARAMS floats. */
 fmm_status fmm_cost_model_get(float *params, int64_t n, int master);

@@ -289,6 +289,7 @@ void validate(const void *xyz, const void *q, int64_t N, int p, double theta, in
         throw Error{FMM_ERR_ARG, "precision_mode must be FMM_PREC_FP32, _TF32X3 or _BF16X3"};
     if (o.select_mode < FMM_SELECT_PLAIN || o.select_mode > FMM_SELECT_TREECODE)
         throw Error{FMM_ERR_ARG, "select_mode must be one of FMM_SELECT_*"};
+    if (o.m2l_unit_blocks < 0) throw Error{FMM_ERR_ARG, "m2l_unit_blocks must be >= 0"};
     if (o.select_mode == FMM_SELECT_TABLE && !o.select_table)
         throw Error{FMM_ERR_ARG, "FMM_SELECT_TABLE needs fmm_options.select_table"};
 
@@ -678,7 +679,8 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
     const bool tensor = o.precision_mode != FMM_PREC_FP32 && m2l_tc_supported(P2pad);
     if (tensor) {
         // work units: (tile, contiguous run of its class blocks), about six per SM
-        const int chunk = std::max(8, (int)ceil_div(std::max(nent, 1), 6 * 152));
+        const int chunk = o.m2l_unit_blocks > 0 ? o.m2l_unit_blocks
+                                                : std::max(8, (int)ceil_div(std::max(nent, 1), 6 * 152));
         // units in execution order (rank within the tile, tile): resident CTAs then work on
         // similar class ranges; tile_units lists each tile's units in class order for the sum
         std::vector<int> nut(ntiles), ubase(ntiles + 1, 0);
@@ -946,6 +948,7 @@ void fmm_default_options(fmm_options *opt)
     opt->select_mode = FMM_SELECT_PLAIN;
     opt->deterministic = 1;
     opt->select_table = nullptr;
+    opt->m2l_unit_blocks = 0;
 }
 
 fmm_status fmm_laplace3d_ex(const float *xyz, const float *q, int64_t N, int p, double theta,
@@ -1066,6 +1069,54 @@ fmm_status fmm_tune_ncrit(const float *xyz, const float *q, int64_t N, int p, do
                 *best = candidates[k];
             }
         }
+        ws.have_solve = false;
+    });
+}
+
+fmm_status fmm_tune_schedule(const float *xyz, const float *q, int64_t N, const int64_t *offsets, int nsys,
+                             int p, double theta, void *stream, const fmm_options *opt, const int *ncrit_cand,
+                             int nncrit, const int *unit_cand, int nunit, float *ms, int *best_ncrit,
+                             int *best_unit)
+{
+    return guarded([&] {
+        if (!ncrit_cand || nncrit < 1 || !unit_cand || nunit < 1 || !best_ncrit || !best_unit)
+            throw Error{FMM_ERR_ARG, "need candidate lists and result pointers"};
+        for (int k = 0; k < nncrit; ++k)
+            if (ncrit_cand[k] < 1) throw Error{FMM_ERR_ARG, "every candidate ncrit must be >= 1"};
+        for (int u = 0; u < nunit; ++u)
+            if (unit_cand[u] < 0) throw Error{FMM_ERR_ARG, "unit candidates must be >= 0"};
+        std::vector<int64_t> off1 = {0, N};
+        const int64_t *off = offsets ? offsets : off1.data();
+        if (!offsets) nsys = 1;
+        if (nsys < 1 || off[0] != 0) throw Error{FMM_ERR_ARG, "offsets must start at 0"};
+        for (int sy = 0; sy < nsys; ++sy)
+            if (off[sy + 1] <= off[sy]) throw Error{FMM_ERR_ARG, "every system needs at least one particle"};
+        N = off[nsys];
+        fmm_options o = resolve_opts(opt);
+        validate(xyz, q, N, p, theta, 1, xyz, xyz, o);
+        Workspace &ws = workspace_for_current_device();
+        std::lock_guard<std::mutex> lk(ws.mu);
+        const uint8_t *sel = selection_table(ws, o, p, theta);
+        cudaStream_t st = (cudaStream_t)stream;
+        float *phi = need<float>(ws, "tune_phi", (size_t)N, st);
+        float *grad = need<float>(ws, "tune_grad", 3 * (size_t)N, st);
+        float best_ms = 1e30f;
+        for (int k = 0; k < nncrit; ++k)
+            for (int u = 0; u < nunit; ++u) {
+                o.m2l_unit_blocks = unit_cand[u];
+                float t = 1e30f;
+                for (int rep = 0; rep < 3; ++rep) {
+                    fmm_stats s{};
+                    solve_locked(ws, xyz, q, N, nsys, off, p, theta, ncrit_cand[k], phi, grad, st, o, &s, sel);
+                    if (rep > 0) t = std::min(t, s.ms_total);  // the first solve sizes the buffers
+                }
+                if (ms) ms[k * nunit + u] = t;
+                if (t < best_ms) {
+                    best_ms = t;
+                    *best_ncrit = ncrit_cand[k];
+                    *best_unit = unit_cand[u];
+                }
+            }
         ws.have_solve = false;
     });
 }

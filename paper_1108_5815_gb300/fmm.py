@@ -30,7 +30,8 @@ ABI_SYMBOLS = ("fmm_default_options", "fmm_laplace3d", "fmm_laplace3d_ex", "fmm_
                "fmm_direct", "fmm_export", "fmm_last_error", "fmm_morton_sort_noalloc",
                "fmm_selection_table", "fmm_cost_model_train", "fmm_cost_model_get",
                "fmm_cost_model_set", "fmm_cost_model_grad", "fmm_cost_model_adam_step",
-               "fmm_cost_model_predict", "fmm_cost_model_samples", "fmm_tune_ncrit")
+               "fmm_cost_model_predict", "fmm_cost_model_samples", "fmm_tune_ncrit",
+               "fmm_tune_schedule")
 COST_MODEL_PARAMS = 4610
 
 
@@ -43,7 +44,7 @@ class FmmError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("max_depth", ctypes.c_int), ("precision_mode", ctypes.c_int),
                 ("select_mode", ctypes.c_int), ("deterministic", ctypes.c_int),
-                ("select_table", ctypes.c_void_p)]
+                ("select_table", ctypes.c_void_p), ("m2l_unit_blocks", ctypes.c_int)]
 
 
 class CostModelInfo(ctypes.Structure):
@@ -110,11 +111,14 @@ def load(path: str | None = None):
         L.fmm_cost_model_samples.argtypes = [vp, vp, vp, i64, ctypes.POINTER(i64)]
         L.fmm_tune_ncrit.argtypes = [vp, vp, i64, ctypes.c_int, ctypes.c_double, vp, ctypes.POINTER(Options),
                                      vp, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_int)]
+        L.fmm_tune_schedule.argtypes = [vp, vp, i64, vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, vp,
+                                        ctypes.POINTER(Options), vp, ctypes.c_int, vp, ctypes.c_int, vp,
+                                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
         for name in ("fmm_laplace3d", "fmm_laplace3d_ex", "fmm_laplace3d_host", "fmm_direct",
                      "fmm_export", "fmm_laplace3d_batched", "fmm_selection_table",
                      "fmm_cost_model_train", "fmm_cost_model_get", "fmm_cost_model_set",
                      "fmm_cost_model_grad", "fmm_cost_model_adam_step", "fmm_cost_model_predict",
-                     "fmm_cost_model_samples", "fmm_tune_ncrit"):
+                     "fmm_cost_model_samples", "fmm_tune_ncrit", "fmm_tune_schedule"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
         return L
@@ -129,13 +133,14 @@ def _check(status: int):
         raise FmmError(status, last_error())
 
 
-def _options(max_depth=0, precision="fp32", select="plain"):
+def _options(max_depth=0, precision="fp32", select="plain", m2l_unit_blocks=0):
     """fmm_options for the call.  ``select`` is "plain", "autotune", "learned" or a
     uint8 [128, 128] selection table; the returned options keep the table alive."""
     o = Options()
     load().fmm_default_options(ctypes.byref(o))
     o.max_depth = max_depth
     o.precision_mode = PRECISION[precision]
+    o.m2l_unit_blocks = m2l_unit_blocks
     if isinstance(select, str):
         o.select_mode = SELECT[select]
         o._table = None
@@ -165,7 +170,7 @@ def _dev_f32(t, shape, name):
 
 
 def laplace3d(xyz, q, p: int, theta: float, ncrit: int, *, max_depth: int = 0,
-              precision: str = "fp32", select="plain", stats: bool = False, out=None):
+              precision: str = "fp32", select="plain", m2l_unit_blocks: int = 0, stats: bool = False, out=None):
     """FMM potential and gradient for CUDA float32 xyz[N,3], q[N].
 
     Returns (phi[N], grad[N,3]) as CUDA tensors (and a stats dict if ``stats``)."""
@@ -179,7 +184,7 @@ def laplace3d(xyz, q, p: int, theta: float, ncrit: int, *, max_depth: int = 0,
             grad = torch.empty(n, 3, device=xyz.device, dtype=torch.float32)
         else:
             phi, grad = out
-        o = _options(max_depth, precision, select)
+        o = _options(max_depth, precision, select, m2l_unit_blocks)
         st = Stats()
         _check(load().fmm_laplace3d_ex(xyz.data_ptr(), q.data_ptr(), n, p, float(theta), ncrit,
                                        phi.data_ptr(), grad.data_ptr(), _stream_ptr(torch, xyz.device),
@@ -188,7 +193,7 @@ def laplace3d(xyz, q, p: int, theta: float, ncrit: int, *, max_depth: int = 0,
 
 
 def laplace3d_host(xyz: np.ndarray, q: np.ndarray, p: int, theta: float, ncrit: int, *,
-                   max_depth: int = 0, precision: str = "fp32", select="plain", stats: bool = False,
+                   max_depth: int = 0, precision: str = "fp32", select="plain", m2l_unit_blocks: int = 0, stats: bool = False,
                    out=None,
                    stream=None):
     """Same solve with host (numpy) arrays: the library copies in and out."""
@@ -200,7 +205,7 @@ def laplace3d_host(xyz: np.ndarray, q: np.ndarray, p: int, theta: float, ncrit: 
         grad = np.empty((n, 3), dtype=np.float32)
     else:
         phi, grad = out
-    o = _options(max_depth, precision, select)
+    o = _options(max_depth, precision, select, m2l_unit_blocks)
     st = Stats()
     _check(load().fmm_laplace3d_host(xyz.ctypes.data, q.ctypes.data, n, p, float(theta), ncrit,
                                      phi.ctypes.data, grad.ctypes.data,
@@ -210,7 +215,7 @@ def laplace3d_host(xyz: np.ndarray, q: np.ndarray, p: int, theta: float, ncrit: 
 
 
 def laplace3d_batched(xyz, q, offsets, p: int, theta: float, ncrit: int, *, max_depth: int = 0,
-                      precision: str = "fp32", select="plain", stats: bool = False, out=None):
+                      precision: str = "fp32", select="plain", m2l_unit_blocks: int = 0, stats: bool = False, out=None):
     """Independent systems in one solve: system s = rows offsets[s]:offsets[s+1] of
     the CUDA float32 xyz[N,3], q[N]; offsets is a host int sequence (len nsys + 1)."""
     import torch
@@ -226,7 +231,7 @@ def laplace3d_batched(xyz, q, offsets, p: int, theta: float, ncrit: int, *, max_
             grad = torch.empty(n, 3, device=xyz.device, dtype=torch.float32)
         else:
             phi, grad = out
-        o = _options(max_depth, precision, select)
+        o = _options(max_depth, precision, select, m2l_unit_blocks)
         st = Stats()
         _check(load().fmm_laplace3d_batched(xyz.data_ptr(), q.data_ptr(), off.ctypes.data,
                                             len(off) - 1, p, float(theta), ncrit, phi.data_ptr(),
@@ -379,8 +384,32 @@ def tune_ncrit(xyz, q, p: int, theta: float, candidates=(16, 32, 64, 128, 256), 
     ms = np.zeros(len(c), dtype=np.float32)
     best = ctypes.c_int(0)
     with torch.cuda.device(xyz.device):
-        o = _options(max_depth, precision, select)
+        o = _options(max_depth, precision, select, m2l_unit_blocks)
         _check(load().fmm_tune_ncrit(xyz.data_ptr(), q.data_ptr(), n, p, float(theta),
                                      _stream_ptr(torch, xyz.device), ctypes.byref(o), c.ctypes.data,
                                      len(c), ms.ctypes.data, ctypes.byref(best)))
     return best.value, {int(k): float(v) for k, v in zip(c, ms)}
+
+
+def tune_schedule(xyz, q, p: int, theta: float, offsets=None, ncrit_candidates=(16, 32, 64, 128),
+                  unit_candidates=(0, 8, 32, 128), *, max_depth: int = 0, precision: str = "fp32",
+                  select="plain"):
+    """Measured autotuner for (ncrit, M2L work-unit size) of a single or batched solve:
+    (best_ncrit, best_unit, {(ncrit, unit): ms})."""
+    import torch
+    n = int(xyz.shape[0])
+    xyz = _dev_f32(xyz, (n, 3), "xyz")
+    q = _dev_f32(q, (n,), "q")
+    nc = np.ascontiguousarray(np.asarray(ncrit_candidates, dtype=np.int32))
+    uc = np.ascontiguousarray(np.asarray(unit_candidates, dtype=np.int32))
+    ms = np.zeros(len(nc) * len(uc), dtype=np.float32)
+    bn, bu = ctypes.c_int(0), ctypes.c_int(0)
+    off = None if offsets is None else np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+    with torch.cuda.device(xyz.device):
+        o = _options(max_depth, precision, select)
+        _check(load().fmm_tune_schedule(xyz.data_ptr(), q.data_ptr(), n, None if off is None else off.ctypes.data,
+                                        0 if off is None else len(off) - 1, p, float(theta),
+                                        _stream_ptr(torch, xyz.device), ctypes.byref(o), nc.ctypes.data, len(nc),
+                                        uc.ctypes.data, len(uc), ms.ctypes.data, ctypes.byref(bn), ctypes.byref(bu)))
+    table = {(int(a), int(b)): float(ms[i * len(uc) + j]) for i, a in enumerate(nc) for j, b in enumerate(uc)}
+    return bn.value, bu.value, table

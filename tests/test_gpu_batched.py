@@ -115,3 +115,18 @@ def test_batched_argument_errors():
     with pytest.raises(fmm.FmmError) as e:
         fmm.laplace3d_batched(xd, qd, bad, 4, 0.5, 16)
     assert e.value.status == fmm.FMM_ERR_ARG
+
+
+def test_schedule_autotuner_on_a_batch():
+    torch = torch_cuda()
+    from paper_1108_5815_gb300 import fmm
+    x, q, off = _systems()
+    xt, qt = torch.from_numpy(x).cuda(), torch.from_numpy(q).cuda()
+    bn, bu, table = fmm.tune_schedule(xt, qt, 6, 0.5, offsets=off, ncrit_candidates=(16, 64),
+                                      unit_candidates=(0, 8))
+    assert (bn, bu) in table and table[(bn, bu)] == min(table.values()) and len(table) == 4
+    # the chosen schedule changes only the speed: results equal the default schedule's
+    a = fmm.laplace3d_batched(xt, qt, off, 6, 0.5, bn, precision="tf32x3")
+    b = fmm.laplace3d_batched(xt, qt, off, 6, 0.5, bn, precision="tf32x3", m2l_unit_blocks=bu or 8)
+    pa, pb = a[0].cpu().numpy(), b[0].cpu().numpy()
+    assert np.max(np.abs(pa - pb)) <= 1e-5 * np.max(np.abs(pa))

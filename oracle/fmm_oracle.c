@@ -51,7 +51,9 @@
  *      traversal.  A P2P pair may have non-leaf cells; it acts on all particles
  *      of both.  Table value 2 selects the cell-particle interaction (M2P, the
  *      treecode kernel: the source multipole evaluated at every particle of
- *      the target cell); a table of all 2 is the paper's treecode.
+ *      the target cell); a table of all 2 is the paper's treecode.  Value 3
+ *      selects the particle-cell interaction (P2L: the source particles added
+ *      straight into the target cell's local expansion, before L2L).
  *
  * Harmonics (signed m, Condon-Shortley P_n^m):
  *   R_n^m(x) = r^n P_n^m(cos t) e^{i m f} / (n+m)!      (regular)
@@ -71,6 +73,7 @@
  *   L2L  L'_j^l = sum_{n>=j,m} L_n^m R_{n-j}^{m-l}(c' - c)
  *   L2P  phi = sum L_n^m R_n^m(x - c);  d/dz phi = sum L_n^m R_{n-1}^m;
  *        (d/dx + i d/dy) phi = sum L_n^m R_{n-1}^{m+1}
+ *   P2L  L_n^m = sum_j q_j conj(I_n^m(y_j - c))   (expansion of 1/|x - y_j| about c)
  *   M2P  phi = sum M_n^m I_n^m(x - c);  d/dz I_n^m = -I_{n+1}^m;
  *        (d/dx + i d/dy) I_n^m = I_{n+1}^{m+1}
  * Coefficients are stored for all signed m at index n*n + n + m.
@@ -253,6 +256,20 @@ double orc_m2p(const double c[3], int p, const cplx *M, const double x[3])
     return creal(acc);
 }
 
+/* P2L: local expansion about c of the n charges q at y (all |y - c| larger
+ * than the evaluation radius), added to L. */
+void orc_p2l(const double c[3], const double *y, const double *q, int64_t n, int p, cplx *L)
+{
+    cplx *Ih = malloc(sizeof(cplx) * nterms(p));
+    for (int64_t j = 0; j < n; ++j) {
+        double d[3] = {y[3 * j] - c[0], y[3 * j + 1] - c[1], y[3 * j + 2] - c[2]};
+        orc_irregular(d, p, Ih);
+        for (int k = 0; k < nterms(p); ++k)
+            L[k] += q[j] * conj(Ih[k]);
+    }
+    free(Ih);
+}
+
 /* M2P with the gradient: phi and grad at x from the multipole M about c.
  * The derivatives of the irregular harmonics raise the degree by one. */
 void orc_m2p_grad(const double c[3], int p, const cplx *M, const double x[3], double *phi,
@@ -407,8 +424,8 @@ typedef struct {
     int *nchild;
     int depth;
     /* interaction lists */
-    int64_t nm2l, np2p, cap_m2l, cap_p2p, nm2p, cap_m2p;
-    int64_t *m2l_t, *m2l_s, *p2p_t, *p2p_s, *m2p_t, *m2p_s;
+    int64_t nm2l, np2p, cap_m2l, cap_p2p, nm2p, cap_m2p, np2l, cap_p2l;
+    int64_t *m2l_t, *m2l_s, *p2p_t, *p2p_s, *m2p_t, *m2p_s, *p2l_t, *p2l_s;
     /* expansions */
     cplx *M, *L;
     int upward_done;
@@ -572,6 +589,8 @@ static void interact(orc_fmm *f, pairstack *st, int64_t T, int64_t S)
             push_pair(&f->p2p_t, &f->p2p_s, &f->np2p, &f->cap_p2p, T, S);
         else if (kind == 2)
             push_pair(&f->m2p_t, &f->m2p_s, &f->nm2p, &f->cap_m2p, T, S);
+        else if (kind == 3)
+            push_pair(&f->p2l_t, &f->p2l_s, &f->np2l, &f->cap_p2l, T, S);
         else
             push_pair(&f->m2l_t, &f->m2l_s, &f->nm2l, &f->cap_m2l, T, S);
     } else if (is_leaf(f, T) && is_leaf(f, S))
@@ -809,6 +828,14 @@ void orc_fmm_evaluate(orc_fmm *f)
     }
     free(off);
     free(idx);
+    /* particle-cell pairs of the selection table (R9), before L2L */
+    for (int64_t k = 0; k < f->np2l; ++k) {
+        int64_t T = f->p2l_t[k], S = f->p2l_s[k];
+        double ct[3];
+        cell_centre(f, T, ct);
+        orc_p2l(ct, f->x + 3 * f->begin[S], f->q + f->begin[S], f->end[S] - f->begin[S], f->p,
+                f->L + (size_t)T * P2);
+    }
     for (int64_t c = 0; c < f->ncells; ++c) {
         if (f->parent[c] < 0)
             continue;
@@ -847,7 +874,8 @@ void orc_fmm_evaluate_leaves(orc_fmm *f, int64_t nl, const int64_t *leaves, doub
 {
     orc_fmm_upward(f);
     const int P2 = nterms(f->p);
-    int64_t *moff, *midx, *poff, *pidx, *qoff, *qidx;
+    int64_t *moff, *midx, *poff, *pidx, *qoff, *qidx, *loff, *lidx;
+    csr_by_target(f->ncells, f->np2l, f->p2l_t, &loff, &lidx);
     csr_by_target(f->ncells, f->nm2l, f->m2l_t, &moff, &midx);
     csr_by_target(f->ncells, f->np2p, f->p2p_t, &poff, &pidx);
     csr_by_target(f->ncells, f->nm2p, f->m2p_t, &qoff, &qidx);
@@ -880,6 +908,10 @@ void orc_fmm_evaluate_leaves(orc_fmm *f, int64_t nl, const int64_t *leaves, doub
                 cell_centre(f, S, cs);
                 orc_m2l(cs, cc, f->p, f->M + (size_t)S * P2, Ln);
             }
+            for (int64_t k = loff[c]; k < loff[c + 1]; ++k) {
+                int64_t S = f->p2l_s[lidx[k]];
+                orc_p2l(cc, f->x + 3 * f->begin[S], f->q + f->begin[S], f->end[S] - f->begin[S], f->p, Ln);
+            }
             memcpy(Lc, Ln, sizeof(cplx) * P2);
         }
         int64_t n = f->end[T] - f->begin[T];
@@ -902,6 +934,8 @@ void orc_fmm_evaluate_leaves(orc_fmm *f, int64_t nl, const int64_t *leaves, doub
     free(pidx);
     free(qoff);
     free(qidx);
+    free(loff);
+    free(lidx);
 }
 
 void orc_fmm_destroy(orc_fmm *f)
@@ -925,6 +959,8 @@ void orc_fmm_destroy(orc_fmm *f)
     free(f->p2p_s);
     free(f->m2p_t);
     free(f->m2p_s);
+    free(f->p2l_t);
+    free(f->p2l_s);
     free(f->M);
     free(f->L);
     free(f->phi);
@@ -935,6 +971,15 @@ void orc_fmm_destroy(orc_fmm *f)
 /* ------------------------------------------------------------------ */
 /* Accessors for the Python wrapper                                    */
 /* ------------------------------------------------------------------ */
+
+void orc_fmm_p2l_list(const orc_fmm *f, int64_t *n, int64_t *t, int64_t *s)
+{
+    *n = f->np2l;
+    if (t)
+        memcpy(t, f->p2l_t, sizeof(int64_t) * f->np2l);
+    if (s)
+        memcpy(s, f->p2l_s, sizeof(int64_t) * f->np2l);
+}
 
 void orc_fmm_m2p_list(const orc_fmm *f, int64_t *n, int64_t *t, int64_t *s)
 {
@@ -1056,6 +1101,11 @@ void orc_l2p_ri(const double c[3], int p, const double *L, const double x[3], do
 {
     orc_l2p(c, p, (const cplx *)L, x, &out4[0], &out4[1]);
 }
+void orc_p2l_ri(const double c[3], const double *y, const double *q, int64_t n, int p, double *L)
+{
+    orc_p2l(c, y, q, n, p, (cplx *)L);
+}
+
 void orc_m2p_grad_ri(const double c[3], int p, const double *M, const double x[3], double *out4)
 {
     orc_m2p_grad(c, p, (const cplx *)M, x, out4, out4 + 1);

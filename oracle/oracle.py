@@ -76,6 +76,8 @@ def lib():
             L.orc_l2p_ri.argtypes = [_D, ctypes.c_int, _D, _D, _D]
             L.orc_m2p_grad_ri.argtypes = [_D, ctypes.c_int, _D, _D, _D]
             L.orc_fmm_m2p_list.argtypes = [ctypes.c_void_p, _I64, _I64, _I64]
+            L.orc_fmm_p2l_list.argtypes = [ctypes.c_void_p, _I64, _I64, _I64]
+            L.orc_p2l_ri.argtypes = [_D, _D, _D, ctypes.c_int64, ctypes.c_int, _D]
             L.orc_m2p_ri.restype = ctypes.c_double
             L.orc_m2p_ri.argtypes = [_D, ctypes.c_int, _D, _D]
             _lib = L
@@ -198,6 +200,15 @@ def l2p(c, p, L, x):
     return out[0], out[1:4].copy()
 
 
+def p2l(c, y, q, p):
+    """Local expansion about c of charges q at y (complex, index n*n+n+m)."""
+    y = _f64(y, (-1, 3))
+    q = _f64(q, (-1,))
+    L = np.zeros((p + 1) ** 2, dtype=np.complex128)
+    lib().orc_p2l_ri(_d(_f64(c, (3,))), _d(y), _d(q), y.shape[0], p, _d(L.view(np.float64)))
+    return L
+
+
 def m2p_grad(c, p, M, x):
     """(phi, grad[3]) at x from the multipole M about c."""
     M = np.ascontiguousarray(M, dtype=np.complex128)
@@ -276,6 +287,15 @@ class Fmm:
         lib().orc_fmm_lists(self._h, mt.ctypes.data_as(_I64), ms.ctypes.data_as(_I64),
                             pt.ctypes.data_as(_I64), ps.ctypes.data_as(_I64))
         return dict(m2l_t=mt, m2l_s=ms, p2p_t=pt, p2p_s=ps)
+
+    def p2l_list(self):
+        """Particle-cell pairs (target cell, source cell) chosen by the selection table."""
+        n = ctypes.c_int64(0)
+        lib().orc_fmm_p2l_list(self._h, ctypes.byref(n), None, None)
+        t = np.zeros(n.value, dtype=np.int64)
+        s = np.zeros(n.value, dtype=np.int64)
+        lib().orc_fmm_p2l_list(self._h, ctypes.byref(n), t.ctypes.data_as(_I64), s.ctypes.data_as(_I64))
+        return t, s
 
     def m2p_list(self):
         """Cell-particle pairs (target cell, source cell) chosen by the selection table."""

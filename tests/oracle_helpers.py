@@ -27,4 +27,6 @@ def coverage_matrix(n, cells, lists):
         cov[b[t]:e[t], b[s]:e[s]] += 1
     for t, s in zip(lists.get("m2p_t", ()), lists.get("m2p_s", ())):
         cov[b[t]:e[t], b[s]:e[s]] += 1
+    for t, s in zip(lists.get("p2l_t", ()), lists.get("p2l_s", ())):
+        cov[b[t]:e[t], b[s]:e[s]] += 1
     return cov

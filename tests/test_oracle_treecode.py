@@ -86,3 +86,40 @@ def test_mixed_tables_keep_coverage_and_accuracy():
         dphi, _ = O.direct(x, q)
         phi, _ = f.evaluate()
         assert np.linalg.norm(phi - dphi) / np.linalg.norm(dphi) < 1e-3
+
+
+def test_p2l_converges_to_direct_field():
+    # charges far from the expansion centre; evaluation points near it
+    y, q = _cluster(seed=5, n=30, a=0.3)
+    y = y + np.array([2.2, -1.1, 0.9])
+    c = np.zeros(3)
+    x = np.array([0.15, -0.1, 0.2])
+    d = x - y
+    r = np.linalg.norm(d, axis=1)
+    phi_ex = np.sum(q / r)
+    g_ex = -np.sum(q[:, None] * d / r[:, None] ** 3, axis=0)
+    prev = None
+    for p in range(2, 15, 2):
+        phi, g = O.l2p(c, p, O.p2l(c, y, q, p), x)
+        err = np.linalg.norm(g - g_ex) / np.linalg.norm(g_ex)
+        assert abs(phi - phi_ex) / abs(phi_ex) < 0.2 ** p
+        if prev is not None:
+            assert err < 0.5 * prev
+        prev = err
+    assert prev < 1e-7
+
+
+@pytest.mark.parametrize("dist,ncrit", [("uniform", 6), ("plummer", 3)])
+def test_p2l_table_covers_every_pair_once_and_stays_accurate(dist, ncrit):
+    x, q = inputs.make(dist, 1100, 71)
+    rng = np.random.default_rng(3)
+    for sel in (np.full((NB, NB), 3, np.uint8), rng.integers(0, 4, (NB, NB)).astype(np.uint8)):
+        f = O.Fmm(x, q, 8, 0.5, ncrit, sel=sel)
+        L = f.lists()
+        L["m2p_t"], L["m2p_s"] = f.m2p_list()
+        L["p2l_t"], L["p2l_s"] = f.p2l_list()
+        assert len(L["p2l_t"]) > 0
+        assert np.all(coverage_matrix(f.N, f.cells(), L) == 1)
+        dphi, dgrad = O.direct(x, q)
+        phi, grad = f.evaluate()
+        assert np.linalg.norm(grad - dgrad) / np.linalg.norm(dgrad) < 1e-3

@@ -68,7 +68,8 @@ enum {
  * taken as P2P, so the far-field error can only shrink.
  * The choice is a table sel[b(n_t) * FMM_SELECT_NB + b(n_s)] (0 = M2L, 1 = P2P,
  * 2 = M2P: the source multipole evaluated at every target particle, the treecode's
- * cell-particle interaction)
+ * cell-particle interaction; 3 = P2L: the source particles added straight into the
+ * target cell's local expansion)
  * over the particle counts n_t, n_s of the target and source cells, with the
  * count bucket b(n) = n - 1 for n < 4, else 3 + 4(e - 2) + ((n >> (e - 2)) & 3),
  * e = floor(log2 n) (four buckets per octave). */
@@ -105,6 +106,7 @@ typedef struct {
     /* per-phase device time in ms (measured with events when stats are requested) */
     float ms_tree, ms_upward, ms_traverse, ms_m2l, ms_downward, ms_p2p, ms_total;
     int64_t n_m2p_pairs; /* (target leaf, source cell) cell-particle pairs */
+    int64_t n_p2l_pairs; /* (target cell, source cell) particle-cell pairs */
 } fmm_stats;
 
 /* Fills *opt with the defaults (max_depth 21, FP32 M2L, plain FMM, deterministic). */
@@ -167,6 +169,7 @@ fmm_status fmm_direct(const float *xyz, const float *q, int64_t N, float *phi, f
  *   FMM_EXPORT_M2P        int32[n][2]: target leaf, source cell of the cell-particle
  *                         pairs (a pair chosen above the leaf level appears once per
  *                         target leaf below it)
+ *   FMM_EXPORT_P2L        int32[n][2]: target cell, source cell of the particle-cell pairs
  * Expansion rows hold, for n = 0..p, Re c_n^0 then (Re c_n^m, Im c_n^m) for
  * m = 1..n ((p+1)^2 values, zero-padded to P2pad = a multiple of 32), scaled
  * by s^-n (multipoles) or s^(n+1) (locals) with s the cell side. */
@@ -180,7 +183,8 @@ enum {
     FMM_EXPORT_MULTIPOLE = 6,
     FMM_EXPORT_LOCAL = 7,
     FMM_EXPORT_SELECT = 8,
-    FMM_EXPORT_M2P = 9
+    FMM_EXPORT_M2P = 9,
+    FMM_EXPORT_P2L = 10
 };
 fmm_status fmm_export(int what, void *dst, int64_t capacity, int64_t *needed);
 

@@ -216,8 +216,70 @@ std::vector<double> pretime_m2p(int p, const std::vector<int> &counts, uint64_t 
     return out;
 }
 
+std::vector<double> pretime_p2l(int p, const std::vector<int> &counts, uint64_t seed, cudaStream_t st)
+{
+    constexpr int K = 27, kLevel = 6;
+    constexpr int64_t kMaxSources = 1 << 22, kMaxCells = 1 << 14;
+    const int P2pad = nterms_pad(p);
+    DevBuf<float4> pts(kMaxSources);
+    DevBuf<int> begin(2 * kMaxCells), end(2 * kMaxCells), off(kMaxCells), cnt(kMaxCells), src(kMaxCells * K),
+        leaves(kMaxCells), level(2 * kMaxCells), sys(2 * kMaxCells);
+    DevBuf<uint64_t> prefix(2 * kMaxCells);
+    DevBuf<float> L((size_t)2 * kMaxCells * P2pad);
+    DevBuf<double> box(4);
+    k_synth_points<<<1024, 256, 0, st>>>(pts.p, kMaxSources, seed);
+    FMM_LAUNCH_CHECK();
+    const double hbox[4] = {0.0, 0.0, 0.0, 1.0};
+    FMM_CUDA_TRY(cudaMemcpyAsync(box.p, hbox, sizeof(hbox), cudaMemcpyHostToDevice, st));
+    std::vector<int> hl(2 * kMaxCells, kLevel), hs(2 * kMaxCells, 0);
+    std::vector<uint64_t> hp(2 * kMaxCells);
+    for (int64_t i = 0; i < 2 * kMaxCells; ++i) hp[i] = (uint64_t)((i * 2654435761ull) & ((1ull << (3 * kLevel)) - 1));
+    FMM_CUDA_TRY(cudaMemcpyAsync(level.p, hl.data(), sizeof(int) * hl.size(), cudaMemcpyHostToDevice, st));
+    FMM_CUDA_TRY(cudaMemcpyAsync(sys.p, hs.data(), sizeof(int) * hs.size(), cudaMemcpyHostToDevice, st));
+    FMM_CUDA_TRY(cudaMemcpyAsync(prefix.p, hp.data(), sizeof(uint64_t) * hp.size(), cudaMemcpyHostToDevice, st));
+    const size_t sh = (size_t)32 * (P2pad + 1) * sizeof(float);
+    if (sh > 48 * 1024) set_smem_limit_once((const void *)k_p2l, (int)sh);
+    cudaEvent_t e0, e1;
+    FMM_CUDA_TRY(cudaEventCreate(&e0));
+    FMM_CUDA_TRY(cudaEventCreate(&e1));
+    std::vector<double> out;
+    for (int ns : counts) {
+        const int64_t nS = std::min<int64_t>(kMaxCells, kMaxSources / ns);
+        const int64_t nT = std::min<int64_t>(kMaxCells, std::max<int64_t>(1216, (int64_t)(1 << 24) / ((int64_t)K * ns)));
+        CellArrays c{};
+        c.begin = begin.p;
+        c.end = end.p;
+        c.level = level.p;
+        c.prefix = prefix.p;
+        c.sys = sys.p;
+        ListArrays Ls{};
+        Ls.p2l_off = off.p;
+        Ls.p2l_cnt = cnt.p;
+        Ls.p2l_src = src.p;
+        // targets hold no particles of their own; sources get ns particles each
+        k_synth_lists<<<(unsigned)ceil_div(std::max(nS, nT), 256), 256, 0, st>>>((int)nT, 0, (int)nS, ns, K, begin.p,
+                                                                                  end.p, off.p, cnt.p, src.p, leaves.p);
+        FMM_LAUNCH_CHECK();
+        float best = 1e30f;
+        for (int rep = 0; rep < 3; ++rep) {
+            FMM_CUDA_TRY(cudaEventRecord(e0, st));
+            k_p2l<<<(unsigned)nT, 32, sh, st>>>(c, Ls, (int)nT, pts.p, box.p, p, P2pad, L.p);
+            FMM_LAUNCH_CHECK();
+            FMM_CUDA_TRY(cudaEventRecord(e1, st));
+            FMM_CUDA_TRY(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            FMM_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+            if (rep > 0) best = std::min(best, ms);
+        }
+        out.push_back((double)best * 1e6 / ((double)nT * K));
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return out;
+}
+
 void table_from_timings(const std::vector<P2PTiming> &grid, double m2l_ns, const std::vector<int> &m2p_counts,
-                        const std::vector<double> &m2p_ns, uint8_t *sel)
+                        const std::vector<double> &m2p_ns, const std::vector<double> &p2l_ns, uint8_t *sel)
 {
     // ln(time per pair) on the (log2 nt, log2 ns) grid, bilinear in the logs
     std::vector<int> cs;
@@ -234,11 +296,12 @@ void table_from_timings(const std::vector<P2PTiming> &grid, double m2l_ns, const
         lt[i * n + j] = std::log(g.ns_per_pair);
     }
     const double lm = std::log(m2l_ns);
-    std::vector<double> qx, qt;
+    std::vector<double> qx, qt, lt_p2l;
     for (size_t i = 0; i < m2p_ns.size(); ++i) {
         qx.push_back(std::log2((double)m2p_counts[i]));
         qt.push_back(std::log(m2p_ns[i]));
     }
+    for (size_t i = 0; i < p2l_ns.size(); ++i) lt_p2l.push_back(std::log(p2l_ns[i]));
     for (int bt = 0; bt < kSelNB; ++bt) {
         size_t i0;
         const double wi = interp_axis(lx, bucket_mid_log2(bt), i0);
@@ -254,8 +317,19 @@ void table_from_timings(const std::vector<P2PTiming> &grid, double m2l_ns, const
             const double a = lt[i0 * n + j0], b = lt[i0 * n + j0 + 1], c = lt[(i0 + 1) * n + j0],
                          d = lt[(i0 + 1) * n + j0 + 1];
             const double v = (1 - wi) * ((1 - wj) * a + wj * b) + wi * ((1 - wj) * c + wj * d);
+            double lp2l = 1e300;  // ln of the P2L time per pair at this source count
+            if (lt_p2l.size() >= 2 && lt_p2l.size() == qx.size()) {
+                size_t s0;
+                const double ws = interp_axis(qx, bucket_mid_log2(bs), s0);
+                lp2l = (1 - ws) * lt_p2l[s0] + ws * lt_p2l[s0 + 1];
+            }
             uint8_t kind = v < lm ? 1 : 0;
-            if (lq < std::min(v, lm)) kind = 2;
+            double best = std::min(v, lm);
+            if (lq < best) {
+                kind = 2;
+                best = lq;
+            }
+            if (lp2l < best) kind = 3;
             sel[bt * kSelNB + bs] = kind;
         }
     }

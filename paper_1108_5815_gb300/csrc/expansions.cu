@@ -602,6 +602,97 @@ __global__ void __launch_bounds__(32)
 // I_n^m = I_{n+1}^{m+1}.  Recurrences of I^: I^_0^0 = 1/r,
 // I^_m^m = -sqrt((2m-1)/(2m)) (x + iy)/r^2 I^_{m-1}^{m-1},
 // I^_n^m = ((2n-1) z I^_{n-1}^m - sqrt((n+m-1)(n-m-1)) I^_{n-2}^m) / (r^2 sqrt((n+m)(n-m))).
+// Particle-cell (P2L): one warp per target cell with a P2L list.  The source
+// particles' contributions L^_n^m += q conj(I^_n^m(u)), u = (y - c_T) / s_T
+// (the unit-scaled, order-normalised form of L_n^m += q conj(I_n^m(y - c_T))),
+// are formed per particle (lane), reduced over the warp through shared memory
+// rows as in P2M, and added to the cell's row of L after its M2L sum.
+__global__ void __launch_bounds__(32)
+    k_p2l(CellArrays c, ListArrays Ls, int ncells, const float4 *__restrict__ pts,
+          const double *__restrict__ box, int p, int P2pad, float *__restrict__ L)
+{
+    extern __shared__ float rows[];  // 32 x (P2pad + 1)
+    const int cell = blockIdx.x;
+    if (cell >= ncells) return;
+    const int cnt = Ls.p2l_cnt[cell];
+    if (cnt == 0) return;
+    const int *slist = Ls.p2l_src + Ls.p2l_off[cell];
+    const int lane = threadIdx.x;
+    const int stride = P2pad + 1;
+    double cen[3], s;
+    cell_centre_side(c, cell, box, cen, s);
+    const double is = 1.0 / s;
+    float acc[kMaxChunks];
+#pragma unroll
+    for (int j = 0; j < kMaxChunks; ++j) acc[j] = 0.f;
+    float *row = rows + lane * stride;
+    for (int k = 0; k < cnt; ++k) {
+        const int S = slist[k];
+        const int b = c.begin[S], e = c.end[S];
+        for (int base = b; base < e; base += 32) {
+            const int i = base + lane;
+            for (int j = 0; j < P2pad; ++j) row[j] = 0.f;
+            if (i < e) {
+                const float4 pt = pts[i];
+                const float x = (float)(((double)pt.x - cen[0]) * is);
+                const float y = (float)(((double)pt.y - cen[1]) * is);
+                const float z = (float)(((double)pt.z - cen[2]) * is);
+                const float q = pt.w;
+                const float r2 = x * x + y * y + z * z, ir2 = 1.f / r2;
+                float mre = rsqrtf(r2), mim = 0.f;  // I^_m^m
+                for (int m = 0; m <= p; ++m) {
+                    if (m > 0) {
+                        const float f = c_rec_d[m] * ir2;
+                        const float nre = f * (x * mre - y * mim), nim = f * (x * mim + y * mre);
+                        mre = nre;
+                        mim = nim;
+                    }
+                    float p2r = 0.f, p2i = 0.f, p1r = mre, p1i = mim;
+                    for (int n = m; n <= p; ++n) {
+                        float ir, ii;
+                        if (n == m) {
+                            ir = mre;
+                            ii = mim;
+                        } else {
+                            const int t = n * (n + 1) / 2 + m;
+                            const float a = c_rec_a[t] * z * ir2, bb = c_rec_b[t] * ir2;
+                            ir = a * p1r - bb * p2r;
+                            ii = a * p1i - bb * p2i;
+                            p2r = p1r;
+                            p2i = p1i;
+                            p1r = ir;
+                            p1i = ii;
+                        }
+                        if (m == 0) {
+                            row[n * n] = q * ir;
+                        } else {
+                            row[n * n + 2 * m - 1] = q * ir;
+                            row[n * n + 2 * m] = -q * ii;
+                        }
+                    }
+                }
+            }
+            __syncwarp();
+#pragma unroll
+            for (int j = 0; j < kMaxChunks; ++j) {
+                const int kk = lane + 32 * j;
+                if (kk < P2pad) {
+                    float sum = 0.f;
+                    for (int r = 0; r < 32; ++r) sum += rows[r * stride + kk];
+                    acc[j] += sum;
+                }
+            }
+            __syncwarp();
+        }
+    }
+    const int P2 = nterms(p);
+#pragma unroll
+    for (int j = 0; j < kMaxChunks; ++j) {
+        const int kk = lane + 32 * j;
+        if (kk < P2) L[(int64_t)cell * P2pad + kk] += acc[j];
+    }
+}
+
 size_t m2p_smem(int p, int P2pad)
 {
     const int nt = (p + 2) * (p + 3) / 2;

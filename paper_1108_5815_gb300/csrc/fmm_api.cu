@@ -81,13 +81,14 @@ struct Workspace {
     int ncells = 0, nleaves = 0, depth = 0, P2pad = 0, nclass = 0;
     int64_t nm2l = 0, np2p = 0;
     int nsys = 1;
-    int64_t cap_m2l = 0, cap_p2p = 0, cap_def = 0, cap_m2p = 0;  // list capacities that sufficed before
-    int64_t nm2p = 0;
+    int64_t cap_m2l = 0, cap_p2p = 0, cap_def = 0, cap_m2p = 0, cap_p2l = 0;  // capacities that sufficed
+    int64_t nm2p = 0, np2l = 0;
     std::vector<uint8_t> sel_host;                   // selection table of the last solve
     // hybrid selection: pre-timed kernels and the learned model
     std::vector<P2PTiming> p2p_grid;                      // P2P time per pair on artificial leaves
     std::map<std::tuple<int, uint64_t, int>, double> m2l_ns;  // (p, theta bits, precision) -> ns per pair
     std::map<int, std::vector<double>> m2p_ns;                // p -> ns per pair for kSelCounts
+    std::map<int, std::vector<double>> p2l_ns;                // p -> ns per pair for kSelCounts
     std::map<std::tuple<int, uint64_t, int, int>, std::vector<uint8_t>> tables;  // (mode, theta, p, prec)
     CostModel cm;
     // The solve runs on two library streams, both non-blocking (a kernel on the
@@ -453,7 +454,7 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
     int64_t p2p_cap = std::max<int64_t>(ws.cap_p2p, std::max<int64_t>(4096 + nsys, (int64_t)nleaves * 96));
     int64_t def_cap = std::max<int64_t>(ws.cap_def, std::max<int64_t>(4096 + nsys, (int64_t)ncells * 96));
     uint64_t *hash_keys = need<uint64_t>(ws, "hash_keys", kHashCap, st);
-    unsigned long long *tcount = need<unsigned long long>(ws, "trav_counters", 4, st);
+    unsigned long long *tcount = need<unsigned long long>(ws, "trav_counters", 5, st);
     // hybrid selection table (the flagged deferred sources need cell ids below 2^30)
     const uint8_t *d_sel = nullptr;
     ws.sel_host.assign((size_t)kSelNB * kSelNB, 0);
@@ -466,11 +467,15 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
     }
     L.m2p_off = need<int>(ws, "m2p_off", ncells, st);
     L.m2p_cnt = need<int>(ws, "m2p_cnt", ncells, st);
-    int64_t m2p_cap = std::max<int64_t>(ws.cap_m2p, 4096);
-    int64_t m2l_total = 0, p2p_total = 0, m2p_total = 0;
+    L.p2l_off = need<int>(ws, "p2l_off", ncells, st);
+    L.p2l_cnt = need<int>(ws, "p2l_cnt", ncells, st);
+    int64_t m2p_cap = std::max<int64_t>(ws.cap_m2p, 4096), p2l_cap = std::max<int64_t>(ws.cap_p2l, 4096);
+    int64_t m2l_total = 0, p2p_total = 0, m2p_total = 0, p2l_total = 0;
     for (int attempt = 0;; ++attempt) {
         L.m2p_src = need<int>(ws, "m2p_src", m2p_cap, st);
         L.m2p_tgt = need<int>(ws, "m2p_tgt", m2p_cap, st);
+        L.p2l_src = need<int>(ws, "p2l_src", p2l_cap, st);
+        L.p2l_tgt = need<int>(ws, "p2l_tgt", p2l_cap, st);
         L.m2l_src = need<int>(ws, "m2l_src", m2l_cap, st);
         L.m2l_tgt = need<int>(ws, "m2l_tgt", m2l_cap, st);
         L.m2l_slot = need<uint32_t>(ws, "m2l_slot", m2l_cap, st);
@@ -484,29 +489,40 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
             const int a = lstart[l], b = lstart[l + 1];
             const unsigned blocks = (unsigned)ceil_div((int64_t)(b - a) * 32, 128);
             k_traverse_level<<<blocks, 128, 0, st>>>(c, L, a, b, theta2, (float)theta2, d_sel, tcount,
-                                                     m2l_cap, p2p_cap, def_cap, m2p_cap, hash_keys, flags);
+                                                     m2l_cap, p2p_cap, def_cap, m2p_cap, p2l_cap, hash_keys,
+                                                     flags);
             FMM_LAUNCH_CHECK();
         }
-        unsigned long long tot[4];
+        unsigned long long tot[5];
         sync_point(ws, st, flags, {{tcount, sizeof(tot)}}, tot);
         if ((int64_t)tot[0] <= m2l_cap && (int64_t)tot[1] <= p2p_cap && (int64_t)tot[2] <= def_cap &&
-            (int64_t)tot[3] <= m2p_cap) {
+            (int64_t)tot[3] <= m2p_cap && (int64_t)tot[4] <= p2l_cap) {
             m2l_total = (int64_t)tot[0];
             p2p_total = (int64_t)tot[1];
             m2p_total = (int64_t)tot[3];
+            p2l_total = (int64_t)tot[4];
             break;
         }
         if (attempt >= 3) throw Error{FMM_ERR_CAPACITY, "interaction lists kept outgrowing their buffers"};
-        // deeper levels saw truncated deferred lists, so their counts are lower bounds
-        m2l_cap = std::max<int64_t>(2 * m2l_cap, (int64_t)tot[0] + tot[0] / 4);
-        p2p_cap = std::max<int64_t>(2 * p2p_cap, (int64_t)tot[1] + tot[1] / 4);
-        def_cap = std::max<int64_t>(2 * def_cap, (int64_t)tot[2] + tot[2] / 4);
-        if ((int64_t)tot[3] > m2p_cap) m2p_cap = std::max<int64_t>(2 * m2p_cap, (int64_t)tot[3] + tot[3] / 4);
+        // While the deferred list fitted, every total is exact and the overflowed lists get
+        // exactly what they need; otherwise deeper levels were cut short, their totals are
+        // lower bounds, and every list grows with a margin.
+        const bool exact = (int64_t)tot[2] <= def_cap;
+        int64_t *caps[5] = {&m2l_cap, &p2p_cap, &def_cap, &m2p_cap, &p2l_cap};
+        for (int k = 0; k < 5; ++k) {
+            const int64_t need_k = (int64_t)tot[k];
+            if (exact) {
+                if (need_k > *caps[k]) *caps[k] = need_k + need_k / 16;
+            } else {
+                *caps[k] = std::max<int64_t>(2 * *caps[k], need_k + need_k / 4);
+            }
+        }
     }
     ws.cap_m2l = m2l_cap;
     ws.cap_p2p = p2p_cap;
     ws.cap_def = def_cap;
     ws.cap_m2p = m2p_cap;
+    ws.cap_p2l = p2l_cap;
 
     // ---------------------------------------------------------- fork
     // P2P needs only the leaf lists: it runs on the caller's stream while the
@@ -733,6 +749,12 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
     ev.rec(4, fs);
 
     // ---------------------------------------------------------- downward pass
+    if (p2l_total > 0) {  // particle-cell pairs of the hybrid selection, into L before L2L
+        const size_t sh = (size_t)32 * (P2pad + 1) * sizeof(float);
+        if (sh > 48 * 1024) set_smem_limit_once((const void *)k_p2l, (int)sh);
+        k_p2l<<<ncells, 32, sh, fs>>>(c, L, ncells, pts, box, p, P2pad, Lx);
+        FMM_LAUNCH_CHECK();
+    }
     for (int l = 0; l < depth; ++l)  // parents at level l, children at level l + 1
         launch_shift_batched(true, c, lstart[l], lstart[l + 1], get<float>(ws, "l2l"), P2, P2pad, Lx, nullptr, fs);
     k_l2p<<<nleaves, 32, 4 * P2pad * sizeof(float), fs>>>(c, leaves, nleaves, pts, box, p, P2pad, Lx,
@@ -783,8 +805,10 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
     ws.nm2l = m2l_total;
     ws.np2p = p2p_total;
     ws.nm2p = m2p_total;
+    ws.np2l = p2l_total;
     if (stats) {
         stats->n_m2p_pairs = m2p_total;
+        stats->n_p2l_pairs = p2l_total;
         stats->ncells = ncells;
         stats->nleaves = nleaves;
         stats->depth = depth;
@@ -853,6 +877,15 @@ const std::vector<double> &m2p_timings(Workspace &ws, int p)
     return ws.m2p_ns[p] = pretime_m2p(p, kSelCounts, 0x5eed0003ull, ws.main_stream);
 }
 
+const std::vector<double> &p2l_timings(Workspace &ws, int p)
+{
+    auto it = ws.p2l_ns.find(p);
+    if (it != ws.p2l_ns.end()) return it->second;
+    ensure_streams(ws);
+    init_recurrence_tables();
+    return ws.p2l_ns[p] = pretime_p2l(p, kSelCounts, 0x5eed0004ull, ws.main_stream);
+}
+
 const std::vector<uint8_t> &pretimed_table(Workspace &ws, int p, double theta, int prec)
 {
     const auto key = std::make_tuple(FMM_SELECT_AUTOTUNE, (uint64_t)std::llround(theta * 1e9), p, prec);
@@ -860,7 +893,7 @@ const std::vector<uint8_t> &pretimed_table(Workspace &ws, int p, double theta, i
     if (it != ws.tables.end()) return it->second;
     const double m2l = m2l_ns_per_pair(ws, p, theta, prec);
     std::vector<uint8_t> t((size_t)kSelNB * kSelNB);
-    table_from_timings(p2p_timings(ws), m2l, kSelCounts, m2p_timings(ws, p), t.data());
+    table_from_timings(p2p_timings(ws), m2l, kSelCounts, m2p_timings(ws, p), p2l_timings(ws, p), t.data());
     return ws.tables[key] = std::move(t);
 }
 
@@ -1327,6 +1360,7 @@ fmm_status fmm_export(int what, void *dst, int64_t capacity, int64_t *needed)
             case FMM_EXPORT_LOCAL: bytes = (int64_t)ws.ncells * ws.P2pad * sizeof(float); break;
             case FMM_EXPORT_SELECT: bytes = (int64_t)ws.sel_host.size(); break;
             case FMM_EXPORT_M2P: bytes = ws.nm2p * 2 * sizeof(int32_t); break;
+            case FMM_EXPORT_P2L: bytes = ws.np2l * 2 * sizeof(int32_t); break;
             default: throw Error{FMM_ERR_ARG, "unknown export kind"};
         }
         if (needed) *needed = bytes;
@@ -1375,11 +1409,13 @@ fmm_status fmm_export(int what, void *dst, int64_t capacity, int64_t *needed)
                 }
                 break;
             }
-            case FMM_EXPORT_M2P: {
-                const int64_t n = ws.nm2p;
+            case FMM_EXPORT_M2P:
+            case FMM_EXPORT_P2L: {
+                const bool m2p = what == FMM_EXPORT_M2P;
+                const int64_t n = m2p ? ws.nm2p : ws.np2l;
                 std::vector<int> t(n), s(n);
-                d2h(t.data(), get<int>(ws, "m2p_tgt"), n * sizeof(int));
-                d2h(s.data(), get<int>(ws, "m2p_src"), n * sizeof(int));
+                d2h(t.data(), get<int>(ws, m2p ? "m2p_tgt" : "p2l_tgt"), n * sizeof(int));
+                d2h(s.data(), get<int>(ws, m2p ? "m2p_src" : "p2l_src"), n * sizeof(int));
                 int32_t *o = static_cast<int32_t *>(dst);
                 for (int64_t i = 0; i < n; ++i) {
                     o[2 * i] = t[i];

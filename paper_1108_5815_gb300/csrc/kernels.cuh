@@ -41,6 +41,8 @@ struct ListArrays {
     int *def_src;
     int *m2p_src, *m2p_tgt;                      // cell-particle pairs (hybrid value 2)
     int *m2p_off, *m2p_cnt;                      // per cell
+    int *p2l_src, *p2l_tgt;                      // particle-cell pairs (hybrid value 3)
+    int *p2l_off, *p2l_cnt;                      // per cell
 };
 
 constexpr int kHashBits = 18;
@@ -75,7 +77,7 @@ constexpr int kSelNB = 128;  // count buckets of the hybrid selection table
 __global__ void k_traverse_level(CellArrays c, ListArrays L, int a, int b, double theta2,
                                  float theta2f, const uint8_t *sel, unsigned long long *counters,
                                  int64_t cap_m, int64_t cap_p, int64_t cap_d, int64_t cap_q,
-                                 uint64_t *hash_keys, int *flags);
+                                 int64_t cap_l, uint64_t *hash_keys, int *flags);
 __global__ void k_hash_flags(const uint64_t *hash_keys, int *flag);
 __global__ void k_hash_compact(const uint64_t *hash_keys, const int *ex, uint64_t *ukeys,
                                uint32_t *uslot);
@@ -110,6 +112,10 @@ void launch_shift_batched(bool l2l, const CellArrays &c, int a, int b, const flo
                           float *E, float *T, cudaStream_t st);
 __global__ void k_l2p(CellArrays c, const int *leaves, int nleaves, const float4 *pts,
                       const double *box, int p, int P2pad, const float *L, float4 *far);
+// P2L: one warp (block) per target cell with a P2L list; the source particles are
+// added to the cell's local expansion.  Dynamic shared memory 32 (P2pad + 1) floats.
+__global__ void k_p2l(CellArrays c, ListArrays Ls, int ncells, const float4 *pts, const double *box, int p,
+                      int P2pad, float *L);
 // M2P: blocks of kM2PWarps warps, one target leaf per warp; dynamic shared memory m2p_smem(p, P2pad).
 constexpr int kM2PWarps = 4;
 size_t m2p_smem(int p, int P2pad);
@@ -171,10 +177,13 @@ std::vector<P2PTiming> pretime_p2p(const std::vector<int> &counts, uint64_t seed
 // M2P time per (target leaf, source cell) pair at expansion order p for each
 // target count in counts.
 std::vector<double> pretime_m2p(int p, const std::vector<int> &counts, uint64_t seed, cudaStream_t st);
+// P2L time per (target cell, source cell) pair at order p for each source count in counts.
+std::vector<double> pretime_p2l(int p, const std::vector<int> &counts, uint64_t seed, cudaStream_t st);
 // Selection table: the cheapest of M2L (m2l_ns per pair), P2P (interpolated from
-// the grid) and M2P (interpolated over the target count; none if m2p_ns is empty).
+// the grid), M2P (interpolated over the target count) and P2L (over the source
+// count); M2P or P2L is not considered when its timings are empty.
 void table_from_timings(const std::vector<P2PTiming> &grid, double m2l_ns, const std::vector<int> &m2p_counts,
-                        const std::vector<double> &m2p_ns, uint8_t *sel);
+                        const std::vector<double> &m2p_ns, const std::vector<double> &p2l_ns, uint8_t *sel);
 // log2 of the representative count of a selection-table bucket (host and device agree).
 __host__ __device__ inline float bucket_mid_log2(int b)
 {

@@ -120,31 +120,33 @@ __device__ __forceinline__ uint64_t class_key(const TargetInfo &T, int ls, const
 }
 
 struct Counts {
-    int m, p, d, q;  // M2L, P2P, deferred, M2P
+    int m, p, d, q, l;  // M2L, P2P, deferred, M2P, P2L
 };
 
-// Resolves one inherited source S0 for target T.  WRITE = false only counts.
+// Resolves one inherited source S0 for target T.  WRITE = false only counts;
+// with WRITE, only the lists whose bit is set in wm are written.
 // sel: hybrid selection table (nullptr = plain FMM).
+enum : unsigned { kWM2L = 1, kWP2P = 2, kWDef = 4, kWM2P = 8, kWP2L = 16 };
 template <bool WRITE>
 __device__ Counts resolve(const TargetInfo &T, int S0, const CellArrays &c, const ListArrays &L,
                           double theta2, float theta2f, int64_t m_pos, int64_t p_pos, int d_pos,
-                          int64_t q_pos, const uint8_t *__restrict__ sel, uint64_t *hash_keys,
-                          int *flags)
+                          int64_t q_pos, int64_t l_pos, unsigned wm, const uint8_t *__restrict__ sel,
+                          uint64_t *hash_keys, int *flags)
 {
-    Counts n = {0, 0, 0, 0};
+    Counts n = {0, 0, 0, 0, 0};
     if (S0 & (kP2PFlag | kM2PFlag)) {
         // a P2P or M2P pair chosen at an ancestor of T: record at a leaf, else pass down
         if (!T.leaf) {
-            if (WRITE) L.def_src[d_pos] = S0;
+            if (WRITE && (wm & kWDef)) L.def_src[d_pos] = S0;
             n.d = 1;
         } else if (S0 & kP2PFlag) {
-            if (WRITE) {
+            if (WRITE && (wm & kWP2P)) {
                 L.p2p_src[p_pos] = S0 & kCellMask;
                 L.p2p_tgt[p_pos] = T.t;
             }
             n.p = 1;
         } else {
-            if (WRITE) {
+            if (WRITE && (wm & kWM2P)) {
                 L.m2p_src[q_pos] = S0 & kCellMask;
                 L.m2p_tgt[q_pos] = T.t;
             }
@@ -163,23 +165,29 @@ __device__ Counts resolve(const TargetInfo &T, int S0, const CellArrays &c, cons
         cell_geom32(ls, c.prefix[S], Cs, hs);
         if (mac_accept(T, Cs, hs, theta2, theta2f)) {
             const int kind = sel ? __ldg(&sel[T.bt * kSelNB + count_bucket(c.end[S] - c.begin[S])]) : 0;
-            if (kind != 0 && !T.leaf) {
-                if (WRITE) L.def_src[d_pos + n.d] = S | (kind == 1 ? kP2PFlag : kM2PFlag);
+            if (kind == 3) {  // particle-cell: into T's own local expansion, at any level
+                if (WRITE && (wm & kWP2L)) {
+                    L.p2l_src[l_pos + n.l] = S;
+                    L.p2l_tgt[l_pos + n.l] = T.t;
+                }
+                ++n.l;
+            } else if (kind != 0 && !T.leaf) {
+                if (WRITE && (wm & kWDef)) L.def_src[d_pos + n.d] = S | (kind == 1 ? kP2PFlag : kM2PFlag);
                 ++n.d;
             } else if (kind == 1) {
-                if (WRITE) {
+                if (WRITE && (wm & kWP2P)) {
                     L.p2p_src[p_pos + n.p] = S;
                     L.p2p_tgt[p_pos + n.p] = T.t;
                 }
                 ++n.p;
             } else if (kind == 2) {
-                if (WRITE) {
+                if (WRITE && (wm & kWM2P)) {
                     L.m2p_src[q_pos + n.q] = S;
                     L.m2p_tgt[q_pos + n.q] = T.t;
                 }
                 ++n.q;
             } else {
-                if (WRITE) {
+                if (WRITE && (wm & kWM2L)) {
                     L.m2l_src[m_pos + n.m] = S;
                     L.m2l_tgt[m_pos + n.m] = T.t;
                     L.m2l_slot[m_pos + n.m] = hash_insert(hash_keys, class_key(T, ls, Cs, flags), flags);
@@ -187,7 +195,7 @@ __device__ Counts resolve(const TargetInfo &T, int S0, const CellArrays &c, cons
                 ++n.m;
             }
         } else if (T.leaf && nchS == 0) {
-            if (WRITE) {
+            if (WRITE && (wm & kWP2P)) {
                 L.p2p_src[p_pos + n.p] = S;
                 L.p2p_tgt[p_pos + n.p] = T.t;
             }
@@ -200,7 +208,7 @@ __device__ Counts resolve(const TargetInfo &T, int S0, const CellArrays &c, cons
             const int c0 = c.child0[S];
             for (int k = nchS - 1; k >= 0; --k) stk[sp++] = c0 + k;
         } else {
-            if (WRITE) L.def_src[d_pos + n.d] = S;
+            if (WRITE && (wm & kWDef)) L.def_src[d_pos + n.d] = S;
             ++n.d;
         }
     }
@@ -242,13 +250,13 @@ __device__ __forceinline__ int warp_excl(int v)
 // One warp per target of the level [a, b): count the outputs of all inherited
 // sources, reserve space for them with one atomic per list, then resolve the
 // sources again in the same order and write.  counters[] are running totals over
-// the levels; when a reservation passes its capacity nothing is written for the
-// target (its deferred count becomes 0) and the host repeats the traversal with
-// larger buffers.
+// the levels; a list whose reservation passes its capacity is not written for the
+// target (its count becomes 0) and the host repeats the traversal with larger
+// buffers.
 __global__ void __launch_bounds__(128)
     k_traverse_level(CellArrays c, ListArrays L, int a, int b, double theta2, float theta2f,
                      const uint8_t *__restrict__ sel, unsigned long long *__restrict__ counters,
-                     int64_t cap_m, int64_t cap_p, int64_t cap_d, int64_t cap_q,
+                     int64_t cap_m, int64_t cap_p, int64_t cap_d, int64_t cap_q, int64_t cap_l,
                      uint64_t *__restrict__ hash_keys, int *__restrict__ flags)
 {
     __shared__ int sF[4][2][kFrontier];
@@ -318,57 +326,70 @@ __global__ void __launch_bounds__(128)
         __syncwarp();
         F = sF[wib][cur];
     }
-    int m = 0, p = 0, d = 0, q = 0;
+    int m = 0, p = 0, d = 0, q = 0, l = 0;
     for (int k = lane; k < ni; k += 32) {
-        const Counts n = resolve<false>(T, F[k], c, L, theta2, theta2f, 0, 0, 0, 0, sel, nullptr, flags);
+        const Counts n = resolve<false>(T, F[k], c, L, theta2, theta2f, 0, 0, 0, 0, 0, 0u, sel, nullptr, flags);
         m += n.m;
         p += n.p;
         d += n.d;
         q += n.q;
+        l += n.l;
     }
     m = warp_sum(m);
     p = warp_sum(p);
     d = warp_sum(d);
     q = warp_sum(q);
-    unsigned long long om = 0, op = 0, od = 0, oq = 0;
+    l = warp_sum(l);
+    unsigned long long om = 0, op = 0, od = 0, oq = 0, ol = 0;
     if (lane == 0) {
         om = atomicAdd(&counters[0], (unsigned long long)m);
         op = atomicAdd(&counters[1], (unsigned long long)p);
         od = atomicAdd(&counters[2], (unsigned long long)d);
         if (q) oq = atomicAdd(&counters[3], (unsigned long long)q);
+        if (l) ol = atomicAdd(&counters[4], (unsigned long long)l);
     }
     om = __shfl_sync(0xffffffffu, om, 0);
     op = __shfl_sync(0xffffffffu, op, 0);
     od = __shfl_sync(0xffffffffu, od, 0);
     oq = __shfl_sync(0xffffffffu, oq, 0);
-    const bool fits = (int64_t)(om + m) <= cap_m && (int64_t)(op + p) <= cap_p &&
-                      (int64_t)(od + d) <= cap_d && (int64_t)(oq + q) <= cap_q;
+    ol = __shfl_sync(0xffffffffu, ol, 0);
+    // Each list is written only where it fits.  The deferred list is what the next
+    // level reads, so while it fits the traversal goes on and every count stays
+    // exact: one regrow of the lists that overflowed then suffices.
+    const bool fm = (int64_t)(om + m) <= cap_m, fp = (int64_t)(op + p) <= cap_p, fd = (int64_t)(od + d) <= cap_d,
+               fq = (int64_t)(oq + q) <= cap_q, fl = (int64_t)(ol + l) <= cap_l;
+    const unsigned wm = (fm ? kWM2L : 0u) | (fp ? kWP2P : 0u) | (fd ? kWDef : 0u) | (fq ? kWM2P : 0u) | (fl ? kWP2L : 0u);
     if (lane == 0) {
         L.m2l_off[t] = (int)om;
-        L.m2l_cnt[t] = fits ? m : 0;
+        L.m2l_cnt[t] = fm ? m : 0;
         L.p2p_off[t] = (int)op;
-        L.p2p_cnt[t] = fits ? p : 0;
+        L.p2p_cnt[t] = fp ? p : 0;
         L.def_off[t] = (int)od;
-        L.def_cnt[t] = fits ? d : 0;
+        L.def_cnt[t] = fd ? d : 0;
         L.m2p_off[t] = (int)oq;
-        L.m2p_cnt[t] = fits ? q : 0;
+        L.m2p_cnt[t] = fq ? q : 0;
+        L.p2l_off[t] = (int)ol;
+        L.p2l_cnt[t] = fl ? l : 0;
     }
-    if (!fits) return;
-    int64_t rm = 0, rp = 0, rq = 0;
+    if (!wm) return;
+    int64_t rm = 0, rp = 0, rq = 0, rl = 0;
     int rd = 0;
     for (int k0 = 0; k0 < ni; k0 += 32) {
         const int k = k0 + lane;
         const int S0 = k < ni ? F[k] : -1;
-        Counts n = {0, 0, 0, 0};
-        if (S0 >= 0) n = resolve<false>(T, S0, c, L, theta2, theta2f, 0, 0, 0, 0, sel, nullptr, flags);
-        const int em = warp_excl(n.m), ep = warp_excl(n.p), ed = warp_excl(n.d), eq = warp_excl(n.q);
+        Counts n = {0, 0, 0, 0, 0};
+        if (S0 >= 0) n = resolve<false>(T, S0, c, L, theta2, theta2f, 0, 0, 0, 0, 0, 0u, sel, nullptr, flags);
+        const int em = warp_excl(n.m), ep = warp_excl(n.p), ed = warp_excl(n.d), eq = warp_excl(n.q),
+                  el = warp_excl(n.l);
         if (S0 >= 0)
             resolve<true>(T, S0, c, L, theta2, theta2f, (int64_t)om + rm + em, (int64_t)op + rp + ep,
-                          (int)od + rd + ed, (int64_t)oq + rq + eq, sel, hash_keys, flags);
+                          (int)od + rd + ed, (int64_t)oq + rq + eq, (int64_t)ol + rl + el, wm, sel, hash_keys,
+                          flags);
         rm += warp_sum(n.m);
         rp += warp_sum(n.p);
         rd += warp_sum(n.d);
         rq += warp_sum(n.q);
+        rl += warp_sum(n.l);
     }
 }
 
@@ -431,6 +452,8 @@ __global__ void k_root_lists(CellArrays c, ListArrays L, int nsys, unsigned long
             L.def_cnt[s] = leaf ? 0 : 1;
             L.m2p_off[s] = 0;
             L.m2p_cnt[s] = 0;
+            L.p2l_off[s] = 0;
+            L.p2l_cnt[s] = 0;
             if (leaf) {
                 L.p2p_src[op] = s;
                 L.p2p_tgt[op] = s;
@@ -447,6 +470,7 @@ __global__ void k_root_lists(CellArrays c, ListArrays L, int nsys, unsigned long
         counters[1] = (unsigned long long)base_p;
         counters[2] = (unsigned long long)base_d;
         counters[3] = 0;
+        counters[4] = 0;
     }
 }
 

@@ -22,7 +22,7 @@ PRECISION = {"fp32": 0, "tf32x3": 1, "bf16x3": 2}
 SELECT = {"plain": 0, "autotune": 1, "learned": 2, "table": 3, "treecode": 4}
 SELECT_NB = 128
 EXPORT = {"box": 0, "keys": 1, "order": 2, "cells": 3, "p2p": 4, "m2l": 5, "multipole": 6,
-          "local": 7, "select": 8, "m2p": 9}
+          "local": 7, "select": 8, "m2p": 9, "p2l": 10}
 
 # every symbol the header declares
 ABI_SYMBOLS = ("fmm_default_options", "fmm_laplace3d", "fmm_laplace3d_ex", "fmm_laplace3d_host",
@@ -64,7 +64,7 @@ class Stats(ctypes.Structure):
                                               "n_launches")] + \
                [(n, ctypes.c_float) for n in ("ms_tree", "ms_upward", "ms_traverse", "ms_m2l",
                                               "ms_downward", "ms_p2p", "ms_total")] + \
-               [("n_m2p_pairs", ctypes.c_int64)]
+               [("n_m2p_pairs", ctypes.c_int64), ("n_p2l_pairs", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -170,7 +170,8 @@ def _dev_f32(t, shape, name):
 
 
 def laplace3d(xyz, q, p: int, theta: float, ncrit: int, *, max_depth: int = 0,
-              precision: str = "fp32", select="plain", m2l_unit_blocks: int = 0, stats: bool = False, out=None):
+              precision: str = "fp32", select="plain", m2l_unit_blocks: int = 0, stats: bool = False,
+              out=None):
     """FMM potential and gradient for CUDA float32 xyz[N,3], q[N].
 
     Returns (phi[N], grad[N,3]) as CUDA tensors (and a stats dict if ``stats``)."""
@@ -193,7 +194,8 @@ def laplace3d(xyz, q, p: int, theta: float, ncrit: int, *, max_depth: int = 0,
 
 
 def laplace3d_host(xyz: np.ndarray, q: np.ndarray, p: int, theta: float, ncrit: int, *,
-                   max_depth: int = 0, precision: str = "fp32", select="plain", m2l_unit_blocks: int = 0, stats: bool = False,
+                   max_depth: int = 0, precision: str = "fp32", select="plain", m2l_unit_blocks: int = 0,
+                   stats: bool = False,
                    out=None,
                    stream=None):
     """Same solve with host (numpy) arrays: the library copies in and out."""
@@ -215,7 +217,8 @@ def laplace3d_host(xyz: np.ndarray, q: np.ndarray, p: int, theta: float, ncrit: 
 
 
 def laplace3d_batched(xyz, q, offsets, p: int, theta: float, ncrit: int, *, max_depth: int = 0,
-                      precision: str = "fp32", select="plain", m2l_unit_blocks: int = 0, stats: bool = False, out=None):
+                      precision: str = "fp32", select="plain", m2l_unit_blocks: int = 0, stats: bool = False,
+                      out=None):
     """Independent systems in one solve: system s = rows offsets[s]:offsets[s+1] of
     the CUDA float32 xyz[N,3], q[N]; offsets is a host int sequence (len nsys + 1)."""
     import torch
@@ -257,7 +260,7 @@ def direct(xyz, q):
 _EXPORT_DTYPE = {"box": (np.float64, 4), "keys": (np.uint64, None), "order": (np.int32, None),
                  "cells": (np.int64, 6), "p2p": (np.int32, 2), "m2l": (np.int32, 3),
                  "multipole": (np.float32, "P2pad"), "local": (np.float32, "P2pad"),
-                 "select": (np.uint8, SELECT_NB), "m2p": (np.int32, 2)}
+                 "select": (np.uint8, SELECT_NB), "m2p": (np.int32, 2), "p2l": (np.int32, 2)}
 
 
 def export(what: str, p: int | None = None) -> np.ndarray:
@@ -384,7 +387,7 @@ def tune_ncrit(xyz, q, p: int, theta: float, candidates=(16, 32, 64, 128, 256), 
     ms = np.zeros(len(c), dtype=np.float32)
     best = ctypes.c_int(0)
     with torch.cuda.device(xyz.device):
-        o = _options(max_depth, precision, select, m2l_unit_blocks)
+        o = _options(max_depth, precision, select)
         _check(load().fmm_tune_ncrit(xyz.data_ptr(), q.data_ptr(), n, p, float(theta),
                                      _stream_ptr(torch, xyz.device), ctypes.byref(o), c.ctypes.data,
                                      len(c), ms.ctypes.data, ctypes.byref(best)))

@@ -49,6 +49,9 @@ def _compare(f, sel):
     et, es = expand_p2p_to_leaves(oc, qt, qs)
     gq = fmm.export("m2p")
     assert np.array_equal(pair_codes(et, es, oid, f.ncells), pair_codes(gq[:, 0], gq[:, 1], gid, f.ncells))
+    lt, ls = f.p2l_list()  # particle-cell pairs stay at their target cell
+    gl = fmm.export("p2l")
+    assert np.array_equal(pair_codes(lt, ls, oid, f.ncells), pair_codes(gl[:, 0], gl[:, 1], gid, f.ncells))
     return np.any(oc["nchild"][ol["p2p_t"]] > 0)
 
 
@@ -143,6 +146,31 @@ def test_three_way_random_table_matches_oracle():
     x, q = inputs.make("plummer", 25000, 61)
     phi, grad = gpu_solve(x, q, 6, 0.45, 5, select=sel)
     f = O.Fmm(x, q, 6, 0.45, 5, sel=sel)
+    _compare(f, sel)
+    ophi, ograd = f.evaluate()
+    assert rel_l2(phi, ophi) < TOL_ORACLE and rel_l2(grad, ograd) < TOL_ORACLE
+
+
+@pytest.mark.parametrize("dist,n,p,theta,ncrit,seed", [("plummer", 20000, 8, 0.45, 5, 23),
+                                                       ("uniform", 25000, 10, 0.4, 8, 24)])
+def test_four_way_table_with_p2l_matches_oracle(dist, n, p, theta, ncrit, seed):
+    rng = np.random.default_rng(seed)
+    sel = rng.integers(0, 4, (NB, NB)).astype(np.uint8)
+    x, q = inputs.make(dist, n, 700 + seed)
+    phi, grad, st = gpu_solve(x, q, p, theta, ncrit, stats=True, select=sel)
+    f = O.Fmm(x, q, p, theta, ncrit, sel=sel)
+    _compare(f, sel)
+    assert st["n_p2l_pairs"] > 0
+    ophi, ograd = f.evaluate()
+    assert rel_l2(phi, ophi) < TOL_ORACLE and rel_l2(grad, ograd) < TOL_ORACLE
+
+
+def test_all_p2l_table_matches_oracle():
+    sel = np.full((NB, NB), 3, np.uint8)
+    x, q = inputs.make("uniform", 20000, 19)
+    phi, grad, st = gpu_solve(x, q, 6, 0.5, 16, stats=True, select=sel)
+    assert st["n_m2l_pairs"] == 0 and st["n_p2l_pairs"] > 0
+    f = O.Fmm(x, q, 6, 0.5, 16, sel=sel)
     _compare(f, sel)
     ophi, ograd = f.evaluate()
     assert rel_l2(phi, ophi) < TOL_ORACLE and rel_l2(grad, ograd) < TOL_ORACLE

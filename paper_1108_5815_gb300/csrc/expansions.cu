@@ -206,7 +206,8 @@ __global__ void k_build_m2l_tables(const uint64_t *__restrict__ class_keys,
 // transposed (input-major): t[o][col][row] so that consecutive threads (rows)
 // read consecutive addresses.
 __global__ void k_build_shift_tables(int p, int P2pad, float *__restrict__ m2m,
-                                     float *__restrict__ l2l)
+                                     float *__restrict__ l2l, double *__restrict__ m2m64,
+                                     double *__restrict__ l2l64)
 {
     extern __shared__ cd sh_h[];
     const int op = blockIdx.x < 8 ? kOpM2M : kOpL2L;
@@ -218,11 +219,14 @@ __global__ void k_build_shift_tables(int p, int P2pad, float *__restrict__ m2m,
     __syncthreads();
     const int P2 = nterms(p);
     float *out = (op == kOpM2M ? m2m : l2l) + (int64_t)o * P2pad * P2pad;
+    double *out64 = op == kOpM2M ? m2m64 : l2l64;
+    if (out64) out64 += (int64_t)o * P2pad * P2pad;
     for (int e = threadIdx.x; e < P2pad * P2pad; e += blockDim.x) {
         const int col = e / P2pad, row = e % P2pad;
         double v = 0.0;
         if (row < P2 && col < P2) v = real_entry(op, sh_h, row, col, 1.0, p);
         out[e] = (float)v;
+        if (out64) out64[e] = v;
     }
 }
 
@@ -470,6 +474,61 @@ __global__ void k_m2m_sum(CellArrays c, int a, int b, int P2pad, const float *__
         }
         reinterpret_cast<float4 *>(M + (int64_t)P * P2pad)[q4] = s;
     }
+}
+
+// The same shifts with FP64 matrices and FP64 sums (rows stored in FP32), for
+// the few top-level parents at high p: one block per parent of [a, b).
+template <bool L2L>
+__global__ void __launch_bounds__(128)
+    k_shift_fp64(CellArrays c, int a, int b, const double *__restrict__ mats, int P2, int P2pad, float *E)
+{
+    extern __shared__ double sx[];  // P2pad
+    const int P = a + blockIdx.x;
+    if (P >= b) return;
+    const int nch = c.nchild[P], c0 = c.child0[P];
+    if (nch == 0) return;
+    if (!L2L) {
+        double acc[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int k = 0; k < nch; ++k) {
+            const int ch = c0 + k, o = (int)(c.prefix[ch] & 7ull);
+            __syncthreads();
+            for (int i = threadIdx.x; i < P2pad; i += blockDim.x) sx[i] = (double)E[(int64_t)ch * P2pad + i];
+            __syncthreads();
+            const double *A = mats + (int64_t)o * P2pad * P2pad;
+            for (int r = 0; r < 4; ++r) {
+                const int j = threadIdx.x + r * blockDim.x;
+                if (j < P2)
+                    for (int col = 0; col < P2; ++col) acc[r] = fma(A[(int64_t)col * P2pad + j], sx[col], acc[r]);
+            }
+        }
+        for (int r = 0; r < 4; ++r) {
+            const int j = threadIdx.x + r * blockDim.x;
+            if (j < P2pad) E[(int64_t)P * P2pad + j] = j < P2 ? (float)acc[r] : 0.f;
+        }
+    } else {
+        for (int i = threadIdx.x; i < P2pad; i += blockDim.x) sx[i] = (double)E[(int64_t)P * P2pad + i];
+        __syncthreads();
+        for (int k = 0; k < nch; ++k) {
+            const int ch = c0 + k, o = (int)(c.prefix[ch] & 7ull);
+            const double *A = mats + (int64_t)o * P2pad * P2pad;
+            for (int j = threadIdx.x; j < P2; j += blockDim.x) {
+                double v = 0.0;
+                for (int col = 0; col < P2; ++col) v = fma(A[(int64_t)col * P2pad + j], sx[col], v);
+                E[(int64_t)ch * P2pad + j] += (float)v;
+            }
+        }
+    }
+}
+
+void launch_shift_fp64(bool l2l, const CellArrays &c, int a, int b, const double *mats, int P2, int P2pad, float *E,
+                       cudaStream_t st)
+{
+    if (b <= a) return;
+    if (l2l)
+        k_shift_fp64<true><<<b - a, 128, sizeof(double) * P2pad, st>>>(c, a, b, mats, P2, P2pad, E);
+    else
+        k_shift_fp64<false><<<b - a, 128, sizeof(double) * P2pad, st>>>(c, a, b, mats, P2, P2pad, E);
+    FMM_LAUNCH_CHECK();
 }
 
 void launch_shift_batched(bool l2l, const CellArrays &c, int a, int b, const float *mats, int P2, int P2pad,

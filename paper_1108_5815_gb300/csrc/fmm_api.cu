@@ -598,8 +598,13 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
             ws.cache_p = p;
             float *m2m = need<float>(ws, "m2m", (size_t)8 * P2pad * P2pad, fs);
             float *l2l = need<float>(ws, "l2l", (size_t)8 * P2pad * P2pad, fs);
+            double *m2m64 = nullptr, *l2l64 = nullptr;  // FP64 copies for the top levels at high p
+            if (p >= kFp64TopP) {
+                m2m64 = need<double>(ws, "m2m64", (size_t)8 * P2pad * P2pad, fs);
+                l2l64 = need<double>(ws, "l2l64", (size_t)8 * P2pad * P2pad, fs);
+            }
             const size_t sh = sizeof(double) * 2 * (size_t)(p + 1) * (p + 2) / 2;
-            k_build_shift_tables<<<16, 256, sh, fs>>>(p, P2pad, m2m, l2l);
+            k_build_shift_tables<<<16, 256, sh, fs>>>(p, P2pad, m2m, l2l, m2m64, l2l64);
             FMM_LAUNCH_CHECK();
         }
         std::vector<uint64_t> hkeys(nclass);
@@ -687,7 +692,10 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
     float *mtmp = need<float>(ws, "m2m_tmp", (size_t)ncells * P2pad, fs);
     for (int l = depth - 1; l >= 0; --l) {
         const int a = lstart[l], b = lstart[l + 1];
-        launch_shift_batched(false, c, a, b, get<float>(ws, "m2m"), P2, P2pad, M, mtmp, fs);
+        if (p >= kFp64TopP && l < kFp64TopLevels)
+            launch_shift_fp64(false, c, a, b, get<double>(ws, "m2m64"), P2, P2pad, M, fs);
+        else
+            launch_shift_batched(false, c, a, b, get<float>(ws, "m2m"), P2, P2pad, M, mtmp, fs);
     }
     ev.rec(7, fs);
 
@@ -756,7 +764,10 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
         FMM_LAUNCH_CHECK();
     }
     for (int l = 0; l < depth; ++l)  // parents at level l, children at level l + 1
-        launch_shift_batched(true, c, lstart[l], lstart[l + 1], get<float>(ws, "l2l"), P2, P2pad, Lx, nullptr, fs);
+        if (p >= kFp64TopP && l < kFp64TopLevels)
+            launch_shift_fp64(true, c, lstart[l], lstart[l + 1], get<double>(ws, "l2l64"), P2, P2pad, Lx, fs);
+        else
+            launch_shift_batched(true, c, lstart[l], lstart[l + 1], get<float>(ws, "l2l"), P2, P2pad, Lx, nullptr, fs);
     k_l2p<<<nleaves, 32, 4 * P2pad * sizeof(float), fs>>>(c, leaves, nleaves, pts, box, p, P2pad, Lx,
                                                           far);
     FMM_LAUNCH_CHECK();

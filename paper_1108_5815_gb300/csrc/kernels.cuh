@@ -100,7 +100,7 @@ __global__ void k_tile_src(const int *m2l_tgt, const int *m2l_src, const uint32_
 // expansions.cu
 __global__ void k_build_m2l_tables(const uint64_t *class_keys, const int *cache_slot, int nnew,
                                    int p, int P2pad, float *table);
-__global__ void k_build_shift_tables(int p, int P2pad, float *m2m, float *l2l);
+__global__ void k_build_shift_tables(int p, int P2pad, float *m2m, float *l2l, double *m2m64, double *l2l64);
 __global__ void k_p2m(CellArrays c, const int *leaves, int nleaves, const float4 *pts,
                       const double *box, int p, int P2pad, float *M);
 // Fills the recurrence-coefficient tables P2M and L2P read (once per device).
@@ -110,6 +110,10 @@ void init_recurrence_tables();
 // parents [a, b) of E from them), octant-batched.
 void launch_shift_batched(bool l2l, const CellArrays &c, int a, int b, const float *mats, int P2, int P2pad,
                           float *E, float *T, cudaStream_t st);
+// The same shifts with FP64 matrices and sums, for the top levels at high p.
+constexpr int kFp64TopP = 12, kFp64TopLevels = 3;  // p >= 12: parents at levels 0..2
+void launch_shift_fp64(bool l2l, const CellArrays &c, int a, int b, const double *mats, int P2, int P2pad, float *E,
+                       cudaStream_t st);
 __global__ void k_l2p(CellArrays c, const int *leaves, int nleaves, const float4 *pts,
                       const double *box, int p, int P2pad, const float *L, float4 *far);
 // P2L: one warp (block) per target cell with a P2L list; the source particles are

@@ -48,6 +48,8 @@ CASES = [
     ("shell12k_p5", "shell", 12000, 5, 0.45, 24, 0),
     ("plummer8k_depth4", "plummer", 8000, 3, 0.5, 8, 4),
     ("uniform9k_p10", "uniform", 9001, 10, 0.4, 64, 0),
+    # high p: the top-level M2M/L2L run in FP64
+    ("plummer7k_p14", "plummer", 7000, 14, 0.45, 32, 0),
 ]
 
 

@@ -36,6 +36,7 @@ constexpr int kP2PFlag = 1 << 30;  // deferred source that is a chosen P2P pair
 constexpr int kM2PFlag = 1 << 29;  // deferred source that is a chosen M2P pair
 constexpr int kCellMask = kM2PFlag - 1;
 constexpr int kFrontier = 256;  // sources of a leaf target split warp-wide before the walks
+constexpr int kCountCache = 128;  // sources whose counts the write pass reuses
 
 struct TargetInfo {
     int t, level;
@@ -253,13 +254,14 @@ __device__ __forceinline__ int warp_excl(int v)
 // the levels; a list whose reservation passes its capacity is not written for the
 // target (its count becomes 0) and the host repeats the traversal with larger
 // buffers.
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, 8)
     k_traverse_level(CellArrays c, ListArrays L, int a, int b, double theta2, float theta2f,
                      const uint8_t *__restrict__ sel, unsigned long long *__restrict__ counters,
                      int64_t cap_m, int64_t cap_p, int64_t cap_d, int64_t cap_q, int64_t cap_l,
                      uint64_t *__restrict__ hash_keys, int *__restrict__ flags)
 {
     __shared__ int sF[4][2][kFrontier];
+    __shared__ int sCnt[4][5][kCountCache];  // per-source counts of the count pass (first kCountCache)
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int t = a + warp;
@@ -329,6 +331,13 @@ __global__ void __launch_bounds__(128)
     int m = 0, p = 0, d = 0, q = 0, l = 0;
     for (int k = lane; k < ni; k += 32) {
         const Counts n = resolve<false>(T, F[k], c, L, theta2, theta2f, 0, 0, 0, 0, 0, 0u, sel, nullptr, flags);
+        if (k < kCountCache) {
+            sCnt[wib][0][k] = n.m;
+            sCnt[wib][1][k] = n.p;
+            sCnt[wib][2][k] = n.d;
+            sCnt[wib][3][k] = n.q;
+            sCnt[wib][4][k] = n.l;
+        }
         m += n.m;
         p += n.p;
         d += n.d;
@@ -378,7 +387,10 @@ __global__ void __launch_bounds__(128)
         const int k = k0 + lane;
         const int S0 = k < ni ? F[k] : -1;
         Counts n = {0, 0, 0, 0, 0};
-        if (S0 >= 0) n = resolve<false>(T, S0, c, L, theta2, theta2f, 0, 0, 0, 0, 0, 0u, sel, nullptr, flags);
+        if (S0 >= 0 && k < kCountCache)  // counted by this lane in the count pass
+            n = {sCnt[wib][0][k], sCnt[wib][1][k], sCnt[wib][2][k], sCnt[wib][3][k], sCnt[wib][4][k]};
+        else if (S0 >= 0)
+            n = resolve<false>(T, S0, c, L, theta2, theta2f, 0, 0, 0, 0, 0, 0u, sel, nullptr, flags);
         const int em = warp_excl(n.m), ep = warp_excl(n.p), ed = warp_excl(n.d), eq = warp_excl(n.q),
                   el = warp_excl(n.l);
         if (S0 >= 0)

@@ -53,14 +53,32 @@ __global__ void k_bbox(const float *__restrict__ xyz, int64_t n, uint32_t *__res
         }
     }
     bad = __any_sync(0xffffffffu, bad);
+    // one set of atomics per block: the warps' results meet in shared memory first
+    __shared__ float smn[3][32], smx[3][32];
+    __shared__ int sbad;
+    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (threadIdx.x == 0) sbad = 0;
+    __syncthreads();
     if ((threadIdx.x & 31) == 0) {
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            atomicMin(&bbox_u[a], float_to_ordered(mn[a]));
-            atomicMax(&bbox_u[3 + a], float_to_ordered(mx[a]));
+            smn[a][warp] = mn[a];
+            smx[a][warp] = mx[a];
         }
-        if (bad) atomicOr(&flags[kFlagNonfinite], 1);
+        if (bad) sbad = 1;
     }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        const int a = threadIdx.x;
+        float bmn = smn[a][0], bmx = smx[a][0];
+        for (int w = 1; w < nw; ++w) {
+            bmn = fminf(bmn, smn[a][w]);
+            bmx = fmaxf(bmx, smx[a][w]);
+        }
+        atomicMin(&bbox_u[a], float_to_ordered(bmn));
+        atomicMax(&bbox_u[3 + a], float_to_ordered(bmx));
+    }
+    if (threadIdx.x == 0 && sbad) atomicOr(&flags[kFlagNonfinite], 1);
 }
 
 // System of particle i: the s with off[s] <= i < off[s+1].
@@ -158,7 +176,11 @@ __global__ void k_morton(const float *__restrict__ xyz, int64_t n, const int *__
     int sys = 0;
     double lo[3], side;
     decode_box(bbox_u, lo, side);
-    double s = __ddiv_rn(2097152.0, side);
+    // the scale 2^21 / side: one FP64 division per block (FP64 is a slow pipe here)
+    __shared__ double s_scale;
+    if (threadIdx.x == 0) s_scale = __ddiv_rn(2097152.0, side);
+    __syncthreads();
+    double s = s_scale;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         if (nsys > 1) {

@@ -149,6 +149,13 @@ fmm_status fmm_laplace3d_batched(const float *xyz, const float *q, const int64_t
 fmm_status fmm_direct(const float *xyz, const float *q, int64_t N, float *phi, float *grad,
                       void *stream);
 
+/* Failure-detection self-test (the paper has no counterpart).  Runs one kernel
+ * whose bounded wait can never be satisfied (an mbarrier nothing arrives at),
+ * with `polls` polls (1..2^26) before it gives up, exactly as the M2L pipeline's
+ * waits do.  The expected result is FMM_ERR_TIMEOUT, read from the device flag;
+ * the context stays usable.  `stream` as for the solves. */
+fmm_status fmm_selftest_wait_timeout(int64_t polls, void *stream);
+
 /* Copies an intermediate array of the most recent successful solve on the
  * current device into host memory `dst` of `capacity` bytes; *needed (may be
  * NULL) receives the byte size.  Returns FMM_ERR_ARG if no solve has run or

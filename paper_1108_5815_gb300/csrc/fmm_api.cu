@@ -1340,6 +1340,20 @@ fmm_status fmm_cost_model_samples(float *x, float *t, float *m, int64_t capacity
     });
 }
 
+fmm_status fmm_selftest_wait_timeout(int64_t polls, void *stream)
+{
+    return guarded([&] {
+        if (polls < 1 || polls > (int64_t(1) << 26)) throw Error{FMM_ERR_ARG, "polls must be in [1, 2^26]"};
+        Workspace &ws = workspace_for_current_device();
+        std::lock_guard<std::mutex> lk(ws.mu);
+        cudaStream_t st = (cudaStream_t)stream;
+        int *flags = need<int>(ws, "selftest_flags", kNumFlags, st);
+        FMM_CUDA_TRY(cudaMemsetAsync(flags, 0, sizeof(int) * kNumFlags, st));
+        launch_wait_selftest((uint32_t)polls, flags, st);
+        sync_point(ws, st, flags, {}, nullptr);  // raises FMM_ERR_TIMEOUT from the flag
+    });
+}
+
 fmm_status fmm_direct(const float *xyz, const float *q, int64_t N, float *phi, float *grad,
                       void *stream)
 {

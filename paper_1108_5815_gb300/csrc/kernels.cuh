@@ -136,6 +136,8 @@ struct M2LUnit {
     int tile, e0, e1, pad;
 };
 bool m2l_tc_supported(int P2pad);
+// One bounded wait on an mbarrier nothing arrives at (failure-detection self-test).
+void launch_wait_selftest(uint32_t polls, int *flags, cudaStream_t st);
 size_t m2l_tc_smem(int P2pad, bool bf16, int &nstages);
 void launch_m2l_tc(bool bf16, int nunits, const void *units, int ntiles, const int *unit_base,
                    const int *tile_units, const int *entry_class, const int *src, const int *tile_cells,

@@ -554,9 +554,44 @@ __global__ void k_split_tables(const float *__restrict__ table, int slot0, int n
     }
 }
 
+// Failure-detection self-test: an mbarrier that nothing arrives at, waited on
+// with the same bounded loop as the M2L pipeline (polls limit), so the wait must
+// give up, raise the timeout flag and return.
+__global__ void k_wait_selftest(uint32_t polls, int *__restrict__ flags)
+{
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint32_t a = smem_u32(&bar);
+        bool done = false;
+        for (uint32_t it = 0; it < polls && !done; ++it) {
+            uint32_t d;
+            asm volatile(
+                "{\n\t.reg .pred p;\n\t"
+                "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                "selp.u32 %0, 1, 0, p;\n\t}"
+                : "=r"(d)
+                : "r"(a), "r"(0u)
+                : "memory");
+            done = d != 0;
+        }
+        if (!done) atomicOr(&flags[kFlagTimeout], 1);
+    }
+}
+
 }  // namespace
 
 bool m2l_tc_supported(int P2pad) { return P2pad <= 256; }
+
+void launch_wait_selftest(uint32_t polls, int *flags, cudaStream_t st)
+{
+    k_wait_selftest<<<1, 32, 0, st>>>(polls, flags);
+    FMM_LAUNCH_CHECK();
+}
 
 size_t m2l_split_bytes(int P2pad, bool bf16, int nslots)
 {

@@ -31,7 +31,7 @@ ABI_SYMBOLS = ("fmm_default_options", "fmm_laplace3d", "fmm_laplace3d_ex", "fmm_
                "fmm_selection_table", "fmm_cost_model_train", "fmm_cost_model_get",
                "fmm_cost_model_set", "fmm_cost_model_grad", "fmm_cost_model_adam_step",
                "fmm_cost_model_predict", "fmm_cost_model_samples", "fmm_tune_ncrit",
-               "fmm_tune_schedule")
+               "fmm_tune_schedule", "fmm_selftest_wait_timeout")
 COST_MODEL_PARAMS = 4610
 
 
@@ -111,6 +111,8 @@ def load(path: str | None = None):
         L.fmm_cost_model_samples.argtypes = [vp, vp, vp, i64, ctypes.POINTER(i64)]
         L.fmm_tune_ncrit.argtypes = [vp, vp, i64, ctypes.c_int, ctypes.c_double, vp, ctypes.POINTER(Options),
                                      vp, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_int)]
+        L.fmm_selftest_wait_timeout.argtypes = [i64, vp]
+        L.fmm_selftest_wait_timeout.restype = ctypes.c_int
         L.fmm_tune_schedule.argtypes = [vp, vp, i64, vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, vp,
                                         ctypes.POINTER(Options), vp, ctypes.c_int, vp, ctypes.c_int, vp,
                                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
@@ -416,3 +418,10 @@ def tune_schedule(xyz, q, p: int, theta: float, offsets=None, ncrit_candidates=(
                                         uc.ctypes.data, len(uc), ms.ctypes.data, ctypes.byref(bn), ctypes.byref(bu)))
     table = {(int(a), int(b)): float(ms[i * len(uc) + j]) for i, a in enumerate(nc) for j, b in enumerate(uc)}
     return bn.value, bu.value, table
+
+
+def selftest_wait_timeout(polls: int = 1 << 16) -> int:
+    """Run the bounded-wait self-test; returns the library status (FMM_ERR_TIMEOUT expected)."""
+    import torch
+    with torch.cuda.device(torch.cuda.current_device()):
+        return int(load().fmm_selftest_wait_timeout(int(polls), _stream_ptr(torch, torch.cuda.current_device())))

@@ -6,7 +6,7 @@ import pytest
 
 from oracle import oracle as O
 from paper_1108_5815_gb300 import inputs
-from tests.gpu_helpers import gpu_solve, rel_l2
+from tests.gpu_helpers import gpu_solve, rel_l2, torch_cuda
 
 pytestmark = pytest.mark.gpu
 
@@ -88,3 +88,18 @@ def test_null_pointers_and_empty():
     z = torch.zeros(3, device="cuda")
     assert L.fmm_laplace3d(z.data_ptr(), z.data_ptr(), 0, 4, 0.5, 8, z.data_ptr(), z.data_ptr(),
                            None) == fmm.FMM_ERR_ARG
+
+
+def test_bounded_wait_reports_timeout_and_context_survives():
+    """Failure detection without a GPU fault: a wait that nothing satisfies gives up
+    after its poll limit, the host reads FMM_ERR_TIMEOUT from the device flag, and
+    the next solve on the same context succeeds."""
+    torch = torch_cuda()
+    from paper_1108_5815_gb300 import fmm
+    assert fmm.selftest_wait_timeout(1 << 14) == fmm.FMM_ERR_TIMEOUT
+    assert "bounded" in fmm.last_error()
+    x, q = inputs.uniform_cube(5000, 8)
+    phi, grad = gpu_solve(x, q, 4, 0.5, 32)
+    f = O.Fmm(x, q, 4, 0.5, 32)
+    ophi, ograd = f.evaluate()
+    assert rel_l2(phi, ophi) < 1e-5

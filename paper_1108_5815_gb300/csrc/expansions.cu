@@ -26,6 +26,7 @@
 //     stays bounded by |x|^n.
 // The M2L/M2M/L2L operators become real (P2 x P2) matrices, computed in FP64
 // from the complex formulas and stored in FP32.
+#include <algorithm>
 #include <cmath>
 #include <mutex>
 
@@ -260,6 +261,11 @@ constexpr int kMaxChunks = 14;  // ceil(448 / 32): p <= 20
 constexpr int kRecMax = 21;
 constexpr int kRecTri = (kRecMax + 1) * (kRecMax + 2) / 2;
 __constant__ float c_rec_a[kRecTri], c_rec_b[kRecTri], c_rec_d[kRecMax + 1];
+// L2P derivative weights per stored coefficient index k (n, m from k):
+// sqrt((n-m)(n+m)), sqrt((n-m)(n-m-1)), sqrt((n+m)(n+m-1)); global memory, since
+// the lanes of a warp read different entries.
+constexpr int kScaleMax = 448;
+__device__ float g_l2p_scale[3][kScaleMax];
 
 void init_recurrence_tables()
 {
@@ -278,6 +284,16 @@ void init_recurrence_tables()
             b[t] = n > m + 1 ? (float)(std::sqrt((double)(n + m - 1) * (n - m - 1)) * den) : 0.f;
         }
     for (int m = 0; m <= kRecMax; ++m) d[m] = m > 0 ? (float)-std::sqrt((2.0 * m - 1.0) / (2.0 * m)) : 1.f;
+    static float sc[3][kScaleMax];
+    for (int k = 0; k < kScaleMax; ++k) {
+        int n = 0;
+        while ((n + 1) * (n + 1) <= k) ++n;
+        const int m = (k - n * n + 1) / 2;
+        sc[0][k] = (float)std::sqrt((double)(n - m) * (n + m));
+        sc[1][k] = (float)std::sqrt((double)std::max(0, (n - m) * (n - m - 1)));
+        sc[2][k] = (float)std::sqrt((double)(n + m) * (n + m - 1));
+    }
+    FMM_CUDA_TRY(cudaMemcpyToSymbol(g_l2p_scale, sc, sizeof(sc)));
     FMM_CUDA_TRY(cudaMemcpyToSymbol(c_rec_a, a, sizeof(a)));
     FMM_CUDA_TRY(cudaMemcpyToSymbol(c_rec_b, b, sizeof(b)));
     FMM_CUDA_TRY(cudaMemcpyToSymbol(c_rec_d, d, sizeof(d)));
@@ -304,9 +320,12 @@ __global__ void __launch_bounds__(32)
 #pragma unroll
     for (int j = 0; j < kMaxChunks; ++j) acc[j] = 0.f;
     float *row = rows + lane * stride;
+    // the padding columns stay zero; a lane past the leaf's end writes a zero row
+    for (int k = nterms(p); k < P2pad; ++k) row[k] = 0.f;
     for (int base = b; base < e; base += 32) {
         const int i = base + lane;
-        for (int k = 0; k < P2pad; ++k) row[k] = 0.f;
+        if (i >= e)
+            for (int k = 0; k < P2pad; ++k) row[k] = 0.f;
         if (i < e) {
             const float4 pt = pts[i];
             const float x = (float)(((double)pt.x - cen[0]) * is);
@@ -564,14 +583,11 @@ __global__ void __launch_bounds__(32)
     float *Lh = sl, *Lz = sl + P2pad, *Lx1 = sl + 2 * P2pad, *Lx2 = sl + 3 * P2pad;
     const int P2 = nterms(p);
     for (int k = lane; k < P2pad; k += 32) {
-        float v = k < P2 ? L[(int64_t)cell * P2pad + k] : 0.f;
-        int n = 0;
-        while ((n + 1) * (n + 1) <= k) ++n;
-        const int m = (k - n * n + 1) / 2;
+        const float v = k < P2 ? L[(int64_t)cell * P2pad + k] : 0.f;
         Lh[k] = v;
-        Lz[k] = v * sqrtf((float)((n - m) * (n + m)));
-        Lx1[k] = v * sqrtf((float)max(0, (n - m) * (n - m - 1)));
-        Lx2[k] = v * sqrtf((float)((n + m) * (n + m - 1)));
+        Lz[k] = v * g_l2p_scale[0][k];
+        Lx1[k] = v * g_l2p_scale[1][k];
+        Lx2[k] = v * g_l2p_scale[2][k];
     }
     __syncwarp();
     double cen[3], s;

@@ -114,7 +114,7 @@ std::vector<P2PTiming> pretime_p2p(const std::vector<int> &counts, uint64_t seed
         for (int ns : counts) {
             const double inter = (double)K * nt * ns;
             int64_t nL = (int64_t)std::llround((double)(1 << 27) / inter);
-            nL = std::max<int64_t>(nL, (int64_t)nsm * 8);
+            nL = std::max<int64_t>(nL, (int64_t)nsm * 8);  // at least 8 leaves per SM
             nL = std::min<int64_t>({nL, kMaxLeaves, kMaxTargets / nt});
             const int64_t nS = std::min<int64_t>(std::max<int64_t>(nL, K), std::min<int64_t>(kMaxLeaves, kMaxSources / ns));
             CellArrays c{};
@@ -128,7 +128,7 @@ std::vector<P2PTiming> pretime_p2p(const std::vector<int> &counts, uint64_t seed
             k_synth_lists<<<(unsigned)ceil_div(nmax, 256), 256, 0, st>>>((int)nL, nt, (int)nS, ns, K, begin.p,
                                                                          end.p, off.p, cnt.p, src.p, leaves.p);
             FMM_LAUNCH_CHECK();
-            const unsigned blocks = (unsigned)std::min<int64_t>(ceil_div(nL, 4), (int64_t)nsm * 8);
+            const unsigned blocks = (unsigned)std::min<int64_t>(ceil_div(nL, 4), (int64_t)nsm * kP2PBlocksPerSM);
             float best = 1e30f;
             for (int rep = 0; rep < 4; ++rep) {
                 FMM_CUDA_TRY(cudaMemsetAsync(counter.p, 0, sizeof(int), st));

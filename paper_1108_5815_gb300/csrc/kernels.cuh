@@ -149,7 +149,8 @@ size_t m2l_split_bytes(int P2pad, bool bf16, int nslots);
 void launch_split_tables(bool bf16, const float *table, int slot0, int nslots, int P2pad, unsigned char *out,
                          cudaStream_t st);
 
-// p2p.cu
+// p2p.cu -- persistent P2P: kP2PBlocksPerSM blocks of 128 threads per SM
+constexpr int kP2PBlocksPerSM = 6;
 __global__ void k_p2p(CellArrays c, ListArrays L, const int *leaves, int nleaves,
                       const float4 *pts, float4 *near, int *counter);
 __global__ void k_direct(const float *xyz, const float *q, int64_t n, float *phi, float *grad);

@@ -277,7 +277,7 @@ __device__ __forceinline__ void p2p_leaf(const CellArrays &c, const ListArrays &
 // Persistent: a fixed number of blocks per SM, each warp taking the next leaf
 // from a counter, so the kernel leaves room on every SM for the far-field chain
 // that runs beside it and has no tail wave.
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, kP2PBlocksPerSM)
     k_p2p(CellArrays c, ListArrays L, const int *__restrict__ leaves, int nleaves,
           const float4 *__restrict__ pts, float4 *__restrict__ near, int *__restrict__ counter)
 {

@@ -254,7 +254,7 @@ __device__ __forceinline__ int warp_excl(int v)
 // the levels; a list whose reservation passes its capacity is not written for the
 // target (its count becomes 0) and the host repeats the traversal with larger
 // buffers.
-__global__ void __launch_bounds__(128, 8)
+__global__ void __launch_bounds__(128, 6)
     k_traverse_level(CellArrays c, ListArrays L, int a, int b, double theta2, float theta2f,
                      const uint8_t *__restrict__ sel, unsigned long long *__restrict__ counters,
                      int64_t cap_m, int64_t cap_p, int64_t cap_d, int64_t cap_q, int64_t cap_l,

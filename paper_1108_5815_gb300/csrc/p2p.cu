@@ -11,7 +11,12 @@
 // Newton step y <- y (3/2 - r^2 y^2 / 2), then phi += q y and
 // grad += q y^3 d.  Pairs at r = 0 (the particle itself, coincident points)
 // contribute nothing: rsqrt(0) = inf makes the Newton step NaN and
-// max(NaN, 0) = 0 removes it without a branch.
+// max(NaN, 0) = 0 removes it without a branch.  Only a chunk holding sources of
+// the target's own leaf can hold the particle itself, so only those chunks take
+// the guard; a pass that still ends with a non-finite sum (a pair at r = 0 in
+// two leaves, r^2 flushed to zero, a target at the origin meeting the zero
+// padding, overflow) is run again with the guard on every chunk, which gives
+// exactly the result of guarding every pair.
 // Each lane takes its target against two sources at a time with the packed
 // FP32x2 instructions (add/sub/mul/fma.rn.f32x2): one instruction does the same
 // operation for both sources, which halves the issue slots of the arithmetic;
@@ -82,6 +87,7 @@ __device__ __forceinline__ Target2 target2(float4 xi)
 }
 
 // The target against two sources (packed x, y, z, q); accumulators packed per source.
+template <bool GUARD>
 __device__ __forceinline__ void p2p_interact2(const Target2 &T, f2 sx, f2 sy, f2 sz, f2 sq, f2 &phi,
                                               f2 &gx, f2 &gy, f2 &gz)
 {
@@ -92,9 +98,11 @@ __device__ __forceinline__ void p2p_interact2(const Target2 &T, f2 sx, f2 sy, f2
     f2 y = f2pack(rsqrt_approx(ra), rsqrt_approx(rb));
     const f2 t = f2mul(f2mul(r2, y), y);
     y = f2mul(y, f2fma(T.mhalf, t, T.threehalf));
-    float ya, yb;
-    f2unpack(y, ya, yb);
-    y = f2pack(fmaxf(ya, 0.f), fmaxf(yb, 0.f));
+    if (GUARD) {
+        float ya, yb;
+        f2unpack(y, ya, yb);
+        y = f2pack(fmaxf(ya, 0.f), fmaxf(yb, 0.f));
+    }
     const f2 qy = f2mul(sq, y);
     phi = f2add(phi, qy);
     const f2 qy3 = f2mul(f2mul(qy, y), y);
@@ -129,63 +137,57 @@ __device__ __forceinline__ void p2p_interact(float xi, float yi, float zi, float
 
 }  // namespace
 
-// Stages the next chunk of up to 32 sources of the target's source stream (the
-// concatenated particle ranges of its P2P source cells) into sh = x[32], y[32],
-// z[32], q[32], padded with zero charges at the origin.  (r, o) = current source
-// cell in the list and offset in it; returns false when the stream is exhausted.
-__device__ __forceinline__ bool load_chunk(const int *__restrict__ slist, int cnt,
-                                           const CellArrays &c, const float4 *__restrict__ pts,
-                                           float *sh, int lane, int &r, int &o)
+// The source stream of a target leaf is the particle ranges of its P2P list
+// concatenated in list order and cut into chunks of 32.  A window holds up to 32
+// consecutive list entries, one per lane: the first particle of the entry's
+// range and where the range starts and ends in the window's part of the stream.
+struct Window {
+    int beg, start, end;  // this lane's entry
+    int total;            // particles in the window
+};
+
+__device__ __forceinline__ Window load_window(const int *__restrict__ slist, int cnt, int r0,
+                                              const CellArrays &c, int lane)
 {
-    if (r >= cnt) return false;
-    const int rk = r + lane;
+    const int rk = r0 + lane;
     int beg = 0, len = 0;
     if (rk < cnt) {
         const int S = slist[rk];
         beg = c.begin[S];
         len = c.end[S] - beg;
     }
-    const int ok = lane == 0 ? o : 0;  // already consumed part of the first range
-    beg += ok;
-    len -= ok;
-    int P = len;  // inclusive prefix of remaining lengths
+    int P = len;  // inclusive prefix of the lengths
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
         const int t = __shfl_up_sync(0xffffffffu, P, d);
         if (lane >= d) P += t;
     }
-    const int S0 = P - len;  // chunk position where range k starts
-    const unsigned starts = __reduce_or_sync(0xffffffffu, (len > 0 && S0 < 32) ? (1u << S0) : 0u);
-    const int total = __shfl_sync(0xffffffffu, P, 31);
-    const unsigned le = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);
-    const int k = __popc(starts & le) - 1;
-    const int kb = __shfl_sync(0xffffffffu, beg, k), ks = __shfl_sync(0xffffffffu, S0, k);
-    const float4 pj = lane < total ? pts[kb + (lane - ks)] : make_float4(0.f, 0.f, 0.f, 0.f);
-    sh[lane] = pj.x;
-    sh[32 + lane] = pj.y;
-    sh[64 + lane] = pj.z;
-    sh[96 + lane] = pj.w;
-    if (total <= 32) {
-        // every range of the window is consumed (a full window of 32 ranges
-        // totals at least 32 elements, so fewer than 32 means the list ended)
-        r = min(r + 32, cnt);
-        o = 0;
-    } else {
-        // the range holding chunk position 31
-        const int k31 = __popc(starts) - 1;
-        const int s31 = __shfl_sync(0xffffffffu, S0, k31);
-        const int l31 = __shfl_sync(0xffffffffu, len, k31);
-        const int o31 = __shfl_sync(0xffffffffu, ok, k31);
-        const int used = 32 - s31;  // elements of range k31 consumed in this chunk
-        if (used == l31) {
-            r += k31 + 1;
-            o = 0;
-        } else {
-            r += k31;
-            o = o31 + used;
-        }
-    }
-    return true;
+    return {beg, P - len, P, __shfl_sync(0xffffffffu, P, 31)};
+}
+
+// The particle at window position pos (0 <= pos < total): the entry k whose
+// range holds pos is the first lane with end > pos, found by a binary search
+// over the lanes.  Every lane takes part; for pos >= total the result is not
+// an index and must not be used.
+__device__ __forceinline__ int window_particle(const Window &w, int pos)
+{
+    int k = 0;
+#pragma unroll
+    for (int step = 16; step >= 1; step >>= 1)
+        if (__shfl_sync(0xffffffffu, w.end, k + step - 1) <= pos) k += step;
+    return __shfl_sync(0xffffffffu, w.beg, k) + (pos - __shfl_sync(0xffffffffu, w.start, k));
+}
+
+// Sources at window positions s .. s+31, one per lane, zero charges at the
+// origin past the end; own = one of them lies in [own_b, own_e).
+__device__ __forceinline__ float4 fetch_chunk(const Window &w, int s, const float4 *__restrict__ pts, int lane,
+                                              int own_b, int own_e, bool &own)
+{
+    const int pos = s + lane;
+    const int j = window_particle(w, pos);
+    const bool in = pos < w.total;
+    own = __any_sync(0xffffffffu, in && j >= own_b && j < own_e);
+    return in ? pts[j] : make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 // The staged 32 sources against one target: pairs of sources per packed
@@ -194,6 +196,7 @@ struct Acc2 {
     f2 phi, gx, gy, gz;
 };
 
+template <bool GUARD>
 __device__ __forceinline__ void p2p_chunk32(const Target2 &T, const float *sh, Acc2 &a, Acc2 &b)
 {
 #pragma unroll
@@ -202,15 +205,39 @@ __device__ __forceinline__ void p2p_chunk32(const Target2 &T, const float *sh, A
         const ulonglong2 vy = *reinterpret_cast<const ulonglong2 *>(sh + 32 + jj);
         const ulonglong2 vz = *reinterpret_cast<const ulonglong2 *>(sh + 64 + jj);
         const ulonglong2 vq = *reinterpret_cast<const ulonglong2 *>(sh + 96 + jj);
-        p2p_interact2(T, vx.x, vy.x, vz.x, vq.x, a.phi, a.gx, a.gy, a.gz);
-        p2p_interact2(T, vx.y, vy.y, vz.y, vq.y, b.phi, b.gx, b.gy, b.gz);
+        p2p_interact2<GUARD>(T, vx.x, vy.x, vz.x, vq.x, a.phi, a.gx, a.gy, a.gz);
+        p2p_interact2<GUARD>(T, vx.y, vy.y, vz.y, vq.y, b.phi, b.gx, b.gy, b.gz);
     }
 }
 
-// One warp per target leaf.  Targets go 32 at a time, one per lane; the last
-// r <= 16 targets are processed with the 32 staged sources split into
-// g = floor(32 / r) contiguous runs of an even length, so that r * g lanes stay
-// busy, and the g partial sums are added in shared memory.
+// One run of sources [j0, j1) of the staged chunk (j1 - j0 even).
+template <bool GUARD>
+__device__ __forceinline__ void p2p_run(const Target2 &T, const float *sh, int j0, int j1, Acc2 &a)
+{
+#pragma unroll 4
+    for (int jj = j0; jj < j1; jj += 2)
+        p2p_interact2<GUARD>(T, *reinterpret_cast<const f2 *>(sh + jj), *reinterpret_cast<const f2 *>(sh + 32 + jj),
+                             *reinterpret_cast<const f2 *>(sh + 64 + jj), *reinterpret_cast<const f2 *>(sh + 96 + jj),
+                             a.phi, a.gx, a.gy, a.gz);
+}
+
+__device__ __forceinline__ float4 acc_sum(const Acc2 &a)
+{
+    return make_float4(f2sum(a.phi), f2sum(a.gx), f2sum(a.gy), f2sum(a.gz));
+}
+
+__device__ __forceinline__ bool nonfinite(float4 v)
+{
+    return !(isfinite(v.x) && isfinite(v.y) && isfinite(v.z) && isfinite(v.w));
+}
+
+// One warp per target leaf; one walk of the source stream serves up to 64
+// targets.  Group A, the first min(n, 32) targets when there are more than 16,
+// takes one target per lane against all 32 sources of each chunk.  Group B,
+// the next up to 32: with more than 16 targets one per lane as well; with
+// r <= 16 the 32 sources of a chunk are split into g = floor(32 / r) runs of
+// an even length so that r * g lanes stay busy, and the g partial sums are
+// added in shared memory.
 __device__ __forceinline__ void p2p_leaf(const CellArrays &c, const ListArrays &L, int T,
                                          const float4 *__restrict__ pts, float4 *__restrict__ near,
                                          float *sh, float4 *redbuf, int lane)
@@ -219,58 +246,82 @@ __device__ __forceinline__ void p2p_leaf(const CellArrays &c, const ListArrays &
     const int *slist = L.p2p_src + L.p2p_off[T];
     const int cnt = L.p2p_cnt[T];
     const f2 zero = 0ull;
-    int tb = b;
-    // full passes, and a last pass of 17..31 targets (g = 1), one target per lane
-    while (tb < e && (e - tb >= 32 || 2 * (e - tb) > 32)) {
-        const bool valid = tb + lane < e;
-        const Target2 Tg = target2(pts[valid ? tb + lane : tb]);
-        Acc2 a0 = {zero, zero, zero, zero}, a1 = a0;
-        int r = 0, o = 0;
-        while (load_chunk(slist, cnt, c, pts, sh, lane, r, o)) {
-            __syncwarp();
-            p2p_chunk32(Tg, sh, a0, a1);
-            __syncwarp();
+    bool guard_all = false;  // set once a pass has produced a non-finite sum
+    for (int tb = b; tb < e;) {
+        const int n = e - tb;
+        const int nA = n > 16 ? min(n, 32) : 0;
+        const int nB = min(n - nA, 32);
+        const bool bfull = nB > 16;
+        int g = 1, t = lane, j0 = 0, j1 = 0;
+        if (nB > 0 && !bfull) {
+            g = 32 / nB;
+            const int cs = 2 * ((16 + g - 1) / g);
+            t = lane % nB;
+            const int sub = lane / nB;
+            j0 = sub < g ? sub * cs : 32;
+            j1 = min(32, j0 + cs);
         }
-        // accumulators hold (phi, gx, gy, gz)
-        if (valid)
-            near[tb + lane] = make_float4(f2sum(a0.phi) + f2sum(a1.phi), f2sum(a0.gx) + f2sum(a1.gx),
-                                          f2sum(a0.gy) + f2sum(a1.gy), f2sum(a0.gz) + f2sum(a1.gz));
-        tb += 32;
-    }
-    const int rem = e - tb;
-    if (rem > 0) {
-        // 1 <= rem <= 16: g >= 2 runs of cs sources (cs even, g * cs >= 32)
-        const int g = 32 / rem;
-        const int cs = 2 * ((16 + g - 1) / g);
-        const int t = lane % rem, sub = lane / rem;
-        const int j0 = sub < g ? sub * cs : 32, j1 = min(32, j0 + cs);
-        const Target2 Tg = target2(pts[tb + t]);
-        Acc2 a = {zero, zero, zero, zero};
-        int r = 0, o = 0;
-        while (load_chunk(slist, cnt, c, pts, sh, lane, r, o)) {
-            __syncwarp();
-#pragma unroll 4
-            for (int jj = j0; jj < j1; jj += 2)
-                p2p_interact2(Tg, *reinterpret_cast<const f2 *>(sh + jj),
-                              *reinterpret_cast<const f2 *>(sh + 32 + jj),
-                              *reinterpret_cast<const f2 *>(sh + 64 + jj),
-                              *reinterpret_cast<const f2 *>(sh + 96 + jj), a.phi, a.gx, a.gy, a.gz);
-            __syncwarp();
-        }
-        redbuf[lane] = make_float4(f2sum(a.phi), f2sum(a.gx), f2sum(a.gy), f2sum(a.gz));
-        __syncwarp();
-        if (lane < rem) {
-            float4 v0 = redbuf[lane];
-            for (int k = 1; k < g; ++k) {
-                const float4 v = redbuf[lane + k * rem];
-                v0.x += v.x;
-                v0.y += v.y;
-                v0.z += v.z;
-                v0.w += v.w;
+        const Target2 TA = target2(pts[lane < nA ? tb + lane : tb]);
+        const Target2 TB = target2(pts[nB > 0 && t < nB ? tb + nA + t : tb]);
+        Acc2 a0 = {zero, zero, zero, zero}, a1 = a0, ab = a0;
+        for (int r0 = 0; r0 < cnt; r0 += 32) {
+            const Window w = load_window(slist, cnt, r0, c, lane);
+            bool own_next;
+            float4 nx = fetch_chunk(w, 0, pts, lane, b, e, own_next);
+            for (int s = 0; s < w.total; s += 32) {
+                const bool guard = own_next || guard_all;
+                sh[lane] = nx.x;
+                sh[32 + lane] = nx.y;
+                sh[64 + lane] = nx.z;
+                sh[96 + lane] = nx.w;
+                __syncwarp();
+                if (s + 32 < w.total) nx = fetch_chunk(w, s + 32, pts, lane, b, e, own_next);
+                if (guard) {
+                    if (nA > 0) p2p_chunk32<true>(TA, sh, a0, a1);
+                    if (bfull) p2p_run<true>(TB, sh, 0, 32, ab);
+                    else if (nB > 0) p2p_run<true>(TB, sh, j0, j1, ab);
+                } else {
+                    if (nA > 0) p2p_chunk32<false>(TA, sh, a0, a1);
+                    if (bfull) p2p_run<false>(TB, sh, 0, 32, ab);
+                    else if (nB > 0) p2p_run<false>(TB, sh, j0, j1, ab);
+                }
+                __syncwarp();
             }
-            near[tb + lane] = v0;
         }
-        __syncwarp();
+        float4 va = acc_sum(a0);
+        const float4 va1 = acc_sum(a1);
+        va.x += va1.x;
+        va.y += va1.y;
+        va.z += va1.z;
+        va.w += va1.w;
+        const float4 vb = acc_sum(ab);
+        const bool bad = (lane < nA && nonfinite(va)) || (nB > 0 && (bfull ? lane < nB : true) && nonfinite(vb));
+        if (!guard_all && __any_sync(0xffffffffu, bad)) {
+            // a pair at r = 0 outside the target's own leaf, r^2 flushed to zero,
+            // or a non-finite input: the same pass again with every chunk guarded
+            guard_all = true;
+            continue;
+        }
+        if (lane < nA) near[tb + lane] = va;
+        if (bfull) {
+            if (lane < nB) near[tb + nA + lane] = vb;
+        } else if (nB > 0) {
+            redbuf[lane] = vb;
+            __syncwarp();
+            if (lane < nB) {
+                float4 v0 = redbuf[lane];
+                for (int k = 1; k < g; ++k) {
+                    const float4 v = redbuf[lane + k * nB];
+                    v0.x += v.x;
+                    v0.y += v.y;
+                    v0.z += v.z;
+                    v0.w += v.w;
+                }
+                near[tb + nA + lane] = v0;
+            }
+            __syncwarp();
+        }
+        tb += nA + nB;
     }
 }
 

@@ -47,6 +47,33 @@ def test_depth_cap_and_box_faces():
     assert rel_l2(phi, ophi) < 1e-5 and rel_l2(grad, ograd) < 1e-5
 
 
+def test_pair_below_float_resolution_across_a_leaf_face_is_dropped():
+    # box [-h, h)^3 with h = 2^-20: the face x = 0 puts two particles 2e-21 apart
+    # in different leaves; their r^2 is below the smallest normal float, so the
+    # P2P kernel drops the pair as it drops a coincident one (a pass that meets it
+    # outside the target's own leaf is redone with the r = 0 guard on every pair)
+    h = 2.0 ** -20
+    x, q = inputs.uniform_cube(3000, 11)
+    x = ((2.0 * x.astype(np.float64) - 1.0) * h).astype(np.float32)
+    x[2], x[3] = -h, h                                      # box corners
+    x[0] = np.array([-1e-21, 0.3 * h, -0.2 * h], np.float32)
+    x[1] = np.array([1e-21, 0.3 * h, -0.2 * h], np.float32)
+    p, theta, ncrit = 6, 0.5, 16
+    phi, grad = gpu_solve(x, q, p, theta, ncrit)
+    assert np.all(np.isfinite(phi)) and np.all(np.isfinite(grad))
+    k = O.morton_keys(x)[2]
+    assert (k[0] >> np.uint64(60)) != (k[1] >> np.uint64(60))  # different cells from level 1 on
+    ophi, ograd = O.Fmm(x, q, p, theta, ncrit).evaluate()
+    rest = np.arange(2, len(x))
+    assert rel_l2(phi[rest], ophi[rest]) < 1e-5 and rel_l2(grad[rest], ograd[rest]) < 1e-5
+    for i, j in ((0, 1), (1, 0)):  # each of the two sees everything but the other
+        qj = q.copy()
+        qj[j] = 0.0
+        ephi, egrad = O.Fmm(x, qj, p, theta, ncrit).evaluate()
+        assert abs(phi[i] - ephi[i]) <= 1e-4 * abs(ephi[i])
+        assert np.linalg.norm(grad[i] - egrad[i]) <= 1e-4 * np.linalg.norm(egrad[i])
+
+
 @pytest.mark.parametrize("n", [33, 65, 129, 257, 1025])
 def test_ragged_small_sizes(n):
     x, q = inputs.plummer(n, n, equal_charges=False)

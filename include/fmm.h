@@ -302,6 +302,63 @@ fmm_status fmm_cost_model_samples(float *x, float *t, float *m, int64_t capacity
 fmm_status fmm_morton_sort_noalloc(const float *xyz, int64_t N, uint64_t *keys, int32_t *order,
                                    double *box, void *stream);
 
+/* ---------------------------------------------------------------- captured plans
+ * A plan is a solve whose every size lives on the device, captured once into a
+ * CUDA graph and replayed for new particle data with one graph launch: no host
+ * read-back, no synchronisation, one launch for all systems of the plan (the
+ * paper has no counterpart; it is the batched, graph-captured form of the
+ * solve).  fmm_plan_create runs one ordinary solve of (xyz, q) to learn the
+ * sizes, gives every buffer that size times `headroom` (1 <= headroom <= 16,
+ * 0 = 1.25) plus a margin, copies the offset-class operators built so far on
+ * the device into the plan (those of this solve among them), and captures the
+ * graph.  The plan owns its device memory and its particle and result buffers.
+ *
+ * A replay whose tree, lists, classes, tiles or work units need more than the
+ * capacities, or that meets an offset class with no operator in the plan, is
+ * invalid: its results are unspecified (every step stays inside its buffers)
+ * and fmm_plan_check returns FMM_ERR_CAPACITY; make a new plan for such data.
+ *
+ *   offsets  HOST int64 [nsys + 1] as for fmm_laplace3d_batched, or NULL for one
+ *            system of N particles (then nsys must be 1)
+ *   xyz, q   DEVICE inputs of the first solve (copied into the plan)
+ *   stream   the first solve runs on it; creation synchronises it
+ * Errors: FMM_ERR_ARG as for the solves (and bad headroom), FMM_ERR_NOMEM, and
+ * any error of the first solve. */
+typedef struct fmm_plan fmm_plan;
+fmm_status fmm_plan_create(fmm_plan **plan, const float *xyz, const float *q, int64_t N, const int64_t *offsets,
+                           int nsys, int p, double theta, int ncrit, const fmm_options *opt, double headroom,
+                           void *stream);
+/* One replay on `stream`, fully asynchronous: copies xyz/q (DEVICE, N values
+ * of the plan's layout) into the plan unless they are the plan's own buffers,
+ * launches the graph, and copies the results to phi/grad unless they are the
+ * plan's own buffers.  Any of the four pointers may be NULL (the plan's buffer
+ * is used as it is).  Replays of one plan must be ordered (one stream, or
+ * events); the plan must be used on the device it was created on. */
+fmm_status fmm_plan_execute(fmm_plan *plan, const float *xyz, const float *q, float *phi, float *grad,
+                            void *stream);
+/* Synchronises `stream` and reports the last replay: FMM_OK, FMM_ERR_CAPACITY
+ * (a capacity was exceeded or a class was unknown; the results are invalid),
+ * FMM_ERR_NONFINITE, or FMM_ERR_TIMEOUT. */
+fmm_status fmm_plan_check(fmm_plan *plan, void *stream);
+/* The plan's own device buffers: xyz float[N][3], q float[N] (inputs) and phi
+ * float[N], grad float[N][3] (outputs of the last replay).  Any may be NULL. */
+fmm_status fmm_plan_buffers(fmm_plan *plan, float **xyz, float **q, float **phi, float **grad);
+
+typedef struct {
+    int64_t N;
+    int nsys, levels;                     /* tree levels the graph covers (root = 0) */
+    int64_t cell_cap, tile_cap, class_cap, entry_cap, unit_cap;
+    int64_t m2l_cap, p2p_cap;             /* interaction-list capacities (pairs) */
+    int64_t operators;                    /* offset-class operators held by the plan */
+    int64_t graph_nodes, graph_kernels;   /* nodes of the captured graph, kernel nodes among them */
+    int64_t last_cells, last_leaves, last_classes, last_entries, last_units;  /* sizes of the last replay */
+    int last_valid;                       /* 1 if no capacity was exceeded in the last replay */
+} fmm_plan_info_t;
+/* Capacities of the plan and the sizes of its last replay (synchronises with
+ * the device). */
+fmm_status fmm_plan_info(fmm_plan *plan, fmm_plan_info_t *info);
+void fmm_plan_destroy(fmm_plan *plan);
+
 /* Message for the last non-OK status returned on this thread ("" if none). */
 const char *fmm_last_error(void);
 

@@ -304,9 +304,10 @@ void init_recurrence_tables()
 // shared-memory row; the lanes then sum the rows column by column.
 __global__ void __launch_bounds__(32)
     k_p2m(CellArrays c, const int *__restrict__ leaves, int nleaves, const float4 *__restrict__ pts,
-          const double *__restrict__ box, int p, int P2pad, float *__restrict__ M)
+          const double *__restrict__ box, int p, int P2pad, float *__restrict__ M, const int *__restrict__ sz)
 {
     extern __shared__ float rows[];  // 32 x (P2pad + 1)
+    if (sz) nleaves = sz[kSzLeaves];
     const int li = blockIdx.x;
     if (li >= nleaves) return;
     const int cell = leaves[li];
@@ -397,12 +398,17 @@ __global__ void __launch_bounds__(32)
 template <bool L2L>
 __global__ void __launch_bounds__(128)
     k_shift_batched(CellArrays c, int a, int b, const float *__restrict__ mats, int P2, int P2pad,
-                    const float *in, float *out)  // L2L: in and out are the same array (disjoint rows)
+                    const float *in, float *out,  // L2L: in and out are the same array (disjoint rows)
+                    const int *__restrict__ sz, int level)
 {
     __shared__ __align__(16) float sA[32][128];
     __shared__ __align__(16) float sC[32][32];
     __shared__ int sch[32];
     __shared__ int sany;
+    if (sz) {
+        a = sz[kSzLevel + level];
+        b = sz[kSzLevel + level + 1];
+    }
     const int t = threadIdx.x;
     const int p0 = a + blockIdx.x * 32;
     const int np = min(32, b - p0);
@@ -474,8 +480,13 @@ __global__ void __launch_bounds__(128)
 }
 
 // M^_parent = sum over its children (octant order) of T_child, parents [a, b).
-__global__ void k_m2m_sum(CellArrays c, int a, int b, int P2pad, const float *__restrict__ T, float *__restrict__ M)
+__global__ void k_m2m_sum(CellArrays c, int a, int b, int P2pad, const float *__restrict__ T, float *__restrict__ M,
+                          const int *__restrict__ sz, int level)
 {
+    if (sz) {
+        a = sz[kSzLevel + level];
+        b = sz[kSzLevel + level + 1];
+    }
     const int nq = P2pad / 4;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)(b - a) * nq;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -499,8 +510,13 @@ __global__ void k_m2m_sum(CellArrays c, int a, int b, int P2pad, const float *__
 // the few top-level parents at high p: one block per parent of [a, b).
 template <bool L2L>
 __global__ void __launch_bounds__(128)
-    k_shift_fp64(CellArrays c, int a, int b, const double *__restrict__ mats, int P2, int P2pad, float *E)
+    k_shift_fp64(CellArrays c, int a, int b, const double *__restrict__ mats, int P2, int P2pad, float *E,
+                 const int *__restrict__ sz, int level)
 {
+    if (sz) {
+        a = sz[kSzLevel + level];
+        b = sz[kSzLevel + level + 1];
+    }
     extern __shared__ double sx[];  // P2pad
     const int P = a + blockIdx.x;
     if (P >= b) return;
@@ -540,29 +556,32 @@ __global__ void __launch_bounds__(128)
 }
 
 void launch_shift_fp64(bool l2l, const CellArrays &c, int a, int b, const double *mats, int P2, int P2pad, float *E,
-                       cudaStream_t st)
+                       cudaStream_t st, const int *sz, int level, int cap)
 {
-    if (b <= a) return;
+    const int np = sz ? cap : b - a;
+    if (np <= 0) return;
     if (l2l)
-        k_shift_fp64<true><<<b - a, 128, sizeof(double) * P2pad, st>>>(c, a, b, mats, P2, P2pad, E);
+        k_shift_fp64<true><<<np, 128, sizeof(double) * P2pad, st>>>(c, a, b, mats, P2, P2pad, E, sz, level);
     else
-        k_shift_fp64<false><<<b - a, 128, sizeof(double) * P2pad, st>>>(c, a, b, mats, P2, P2pad, E);
+        k_shift_fp64<false><<<np, 128, sizeof(double) * P2pad, st>>>(c, a, b, mats, P2, P2pad, E, sz, level);
     FMM_LAUNCH_CHECK();
 }
 
 void launch_shift_batched(bool l2l, const CellArrays &c, int a, int b, const float *mats, int P2, int P2pad,
-                          float *E, float *T, cudaStream_t st)
+                          float *E, float *T, cudaStream_t st, const int *sz, int level, int cap)
 {
-    if (b <= a) return;
-    const dim3 grid((unsigned)ceil_div(b - a, 32), (unsigned)ceil_div(P2pad, 128), 8);
+    const int np = sz ? cap : b - a;  // parents launched for
+    if (np <= 0) return;
+    const dim3 grid((unsigned)ceil_div(np, 32), (unsigned)ceil_div(P2pad, 128), 8);
     if (l2l) {
-        k_shift_batched<true><<<grid, 128, 0, st>>>(c, a, b, mats, P2, P2pad, E, E);
+        k_shift_batched<true><<<grid, 128, 0, st>>>(c, a, b, mats, P2, P2pad, E, E, sz, level);
         FMM_LAUNCH_CHECK();
     } else {
-        k_shift_batched<false><<<grid, 128, 0, st>>>(c, a, b, mats, P2, P2pad, E, T);
+        k_shift_batched<false><<<grid, 128, 0, st>>>(c, a, b, mats, P2, P2pad, E, T, sz, level);
         FMM_LAUNCH_CHECK();
-        const int64_t n = (int64_t)(b - a) * (P2pad / 4);
-        k_m2m_sum<<<(unsigned)std::min<int64_t>(ceil_div(n, 256), 152 * 16), 256, 0, st>>>(c, a, b, P2pad, T, E);
+        const int64_t n = (int64_t)np * (P2pad / 4);
+        k_m2m_sum<<<(unsigned)std::min<int64_t>(ceil_div(n, 256), 152 * 16), 256, 0, st>>>(c, a, b, P2pad, T, E, sz,
+                                                                                         level);
         FMM_LAUNCH_CHECK();
     }
 }
@@ -573,9 +592,10 @@ void launch_shift_batched(bool l2l, const CellArrays &c, int a, int b, const flo
 __global__ void __launch_bounds__(32)
     k_l2p(CellArrays c, const int *__restrict__ leaves, int nleaves, const float4 *__restrict__ pts,
           const double *__restrict__ box, int p, int P2pad, const float *__restrict__ L,
-          float4 *__restrict__ far)
+          float4 *__restrict__ far, const int *__restrict__ sz)
 {
     extern __shared__ float sl[];  // 4 x P2pad: L, Lz, Lx1, Lx2
+    if (sz) nleaves = sz[kSzLeaves];
     const int li = blockIdx.x;
     if (li >= nleaves) return;
     const int cell = leaves[li];
@@ -684,9 +704,10 @@ __global__ void __launch_bounds__(32)
 // rows as in P2M, and added to the cell's row of L after its M2L sum.
 __global__ void __launch_bounds__(32)
     k_p2l(CellArrays c, ListArrays Ls, int ncells, const float4 *__restrict__ pts,
-          const double *__restrict__ box, int p, int P2pad, float *__restrict__ L)
+          const double *__restrict__ box, int p, int P2pad, float *__restrict__ L, const int *__restrict__ sz)
 {
     extern __shared__ float rows[];  // 32 x (P2pad + 1)
+    if (sz) ncells = sz[kSzCells];
     const int cell = blockIdx.x;
     if (cell >= ncells) return;
     const int cnt = Ls.p2l_cnt[cell];
@@ -778,9 +799,10 @@ size_t m2p_smem(int p, int P2pad)
 __global__ void __launch_bounds__(32 * kM2PWarps)
     k_m2p(CellArrays c, ListArrays Ls, const int *__restrict__ leaves, int nleaves,
           const float4 *__restrict__ pts, const double *__restrict__ box, int p, int P2pad,
-          const float *__restrict__ M, float4 *__restrict__ far)
+          const float *__restrict__ M, float4 *__restrict__ far, const int *__restrict__ sz)
 {
     extern __shared__ float sm[];
+    if (sz) nleaves = sz[kSzLeaves];
     // per block: recurrence coefficients of I^ for (n, m) at n(n+1)/2 + m, n <= p + 1,
     // the diagonal factors, and the three derivative weights per stored coefficient
     const int ntri = (p + 2) * (p + 3) / 2;

@@ -21,6 +21,7 @@
 #include "common.cuh"
 #include "cost_model.cuh"
 #include "kernels.cuh"
+#include "plan.cuh"
 
 namespace fmm {
 
@@ -84,6 +85,12 @@ struct Workspace {
     int64_t cap_m2l = 0, cap_p2p = 0, cap_def = 0, cap_m2p = 0, cap_p2l = 0;  // capacities that sufficed
     int64_t nm2p = 0, np2l = 0;
     std::vector<uint8_t> sel_host;                   // selection table of the last solve
+    // sizes of the last solve: a plan takes its capacities from them
+    struct Shape {
+        std::vector<int> lstart;  // first cell of each level, then the cell count
+        int ncells = 0, nleaves = 0, ntiles = 0, nclass = 0, nent = 0, nunits = 0, chunk = 8;
+        int64_t tot[5] = {0, 0, 0, 0, 0};  // M2L, P2P, deferred, M2P, P2L pairs
+    } shape;
     // hybrid selection: pre-timed kernels and the learned model
     std::vector<P2PTiming> p2p_grid;                      // P2P time per pair on artificial leaves
     std::map<std::tuple<int, uint64_t, int>, double> m2l_ns;  // (p, theta bits, precision) -> ns per pair
@@ -250,12 +257,6 @@ struct Events {
             for (auto &e : ev) cudaEventDestroy(e);
     }
 };
-
-__global__ void k_init_bbox(uint32_t *bbox_u, int nsys)
-{
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 6 * nsys; i += gridDim.x * blockDim.x)
-        bbox_u[i] = (i % 6) < 3 ? 0xffffffffu : 0u;
-}
 
 __global__ void k_p2p_interactions(const int *__restrict__ tgt, const int *__restrict__ src,
                                    int64_t n, CellArrays c, unsigned long long *out)
@@ -439,6 +440,9 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
         sync_point(ws, st, flags, {{lex + ncells, sizeof(int)}}, &nleaves);
     }
     ev.rec(1, st);
+    ws.shape.lstart = lstart;
+    ws.shape.ncells = ncells;
+    ws.shape.nleaves = nleaves;
 
     // ---------------------------------------------------------- traversal
     const double theta2 = theta * theta;
@@ -501,6 +505,7 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
             p2p_total = (int64_t)tot[1];
             m2p_total = (int64_t)tot[3];
             p2l_total = (int64_t)tot[4];
+            for (int k = 0; k < 5; ++k) ws.shape.tot[k] = (int64_t)tot[k];
             break;
         }
         if (attempt >= 3) throw Error{FMM_ERR_CAPACITY, "interaction lists kept outgrowing their buffers"};
@@ -667,6 +672,10 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
     std::vector<int> h_eb(ntiles + 1);
     sync_point(ws, fs, flags, {{entry_base, sizeof(int) * (ntiles + 1)}}, h_eb.data());
     const int nent = h_eb[ntiles];
+    ws.shape.nclass = nclass;
+    ws.shape.ntiles = ntiles;
+    ws.shape.nent = nent;
+    ws.shape.nunits = 0;
     int *entry_class = need<int>(ws, "entry_class", nent, fs);
     int *src = need<int>(ws, "src", (size_t)nent * kTile, fs);
     FMM_CUDA_TRY(cudaMemsetAsync(src, 0xff, sizeof(int) * (size_t)nent * kTile, fs));
@@ -717,6 +726,8 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
             maxr = std::max(maxr, nut[t]);
         }
         const int nunits = ubase[ntiles];
+        ws.shape.nunits = nunits;
+        ws.shape.chunk = chunk;
         std::vector<M2LUnit> units;
         units.reserve(nunits);
         std::vector<int> tile_units(std::max(nunits, 1));
@@ -977,6 +988,274 @@ fmm_status guarded(F &&f)
         set_last_error("unexpected exception");
         return FMM_ERR_CUDA;
     }
+}
+
+
+// ---------------------------------------------------------------- captured plans
+
+int64_t with_headroom(int64_t n, double h, int64_t margin) { return (int64_t)std::ceil((double)n * h) + margin; }
+
+// Capacities of a plan from the sizes of its first solve.
+PlanShape plan_shape(const Workspace &ws, int64_t N, int nsys, int p, double theta, int ncrit, const fmm_options &o,
+                     bool hybrid, double h)
+{
+    const Workspace::Shape &sh = ws.shape;
+    PlanShape s;
+    s.N = (int)N;
+    s.nsys = nsys;
+    s.p = p;
+    s.P2 = nterms(p);
+    s.P2pad = nterms_pad(p);
+    s.ncrit = ncrit;
+    s.max_depth = o.max_depth == 0 ? kMaxLevel : o.max_depth;
+    s.theta = theta;
+    s.tensor = o.precision_mode != FMM_PREC_FP32 && m2l_tc_supported(s.P2pad);
+    s.bf16 = o.precision_mode == FMM_PREC_BF16X3;
+    s.hybrid = hybrid;
+    s.sys_bits = 1;
+    while ((1 << s.sys_bits) < nsys) ++s.sys_bits;
+    const int depth = (int)sh.lstart.size() - 2;
+    s.levels = std::min(depth + 1, s.max_depth);
+    s.cell_cap = (int)std::min<int64_t>(with_headroom(sh.ncells, h, 1024 + nsys), INT_MAX / 2);
+    s.level_cap.assign(s.levels + 2, 0);
+    for (int l = 0; l <= s.levels; ++l) {
+        const int cnt = l <= depth ? sh.lstart[l + 1] - sh.lstart[l] : sh.lstart[depth + 1] - sh.lstart[depth];
+        s.level_cap[l] = (int)std::min<int64_t>(with_headroom(cnt, h, 256), s.cell_cap);
+    }
+    s.level_cap[s.levels + 1] = 0;  // the last level may not split
+    s.max_level_cap = *std::max_element(s.level_cap.begin(), s.level_cap.end());
+    s.leaf_cap = s.cell_cap;
+    s.tile_cap = (int)with_headroom(sh.ntiles, h, 64);
+    s.nclass_cap = (int)std::min<int64_t>(with_headroom(sh.nclass, h, 256), kHashCap);
+    s.nwords = std::max(1, (int)ceil_div(s.nclass_cap, 32));
+    s.nent_cap = (int)with_headroom(sh.nent, h, 1024);
+    s.units_cap = (int)with_headroom(sh.nunits, h, 256);
+    s.chunk = std::max(1, sh.chunk);
+    s.m2l_cap = with_headroom(sh.tot[0], h, 4096);
+    s.p2p_cap = with_headroom(sh.tot[1], h, 4096);
+    s.def_cap = with_headroom(sh.tot[2], h, 4096);
+    s.m2p_cap = with_headroom(sh.tot[3], h, 4096);
+    s.p2l_cap = with_headroom(sh.tot[4], h, 4096);
+    s.class_hcap = 1;
+    while (s.class_hcap < 2u * (uint32_t)std::max<int64_t>(1, (int64_t)ws.class_cache.size())) s.class_hcap <<= 1;
+    int nsm = 152;
+    FMM_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ws.device));
+    s.nsm = nsm;
+    return s;
+}
+
+}  // namespace
+}  // namespace fmm
+
+struct fmm_plan {
+    int device = 0;
+    fmm::PlanShape s;
+    fmm::PlanBuffers b;
+    fmm::PlanMemory mem;
+    int64_t operators = 0, graph_nodes = 0, graph_kernels = 0;
+    float *xyz = nullptr, *q = nullptr, *phi = nullptr, *grad = nullptr;
+    cudaStream_t st = nullptr, fs = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    ~fmm_plan()
+    {
+        if (st) cudaStreamSynchronize(st);
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (fork) cudaEventDestroy(fork);
+        if (join) cudaEventDestroy(join);
+        if (st) cudaStreamDestroy(st);
+        if (fs) cudaStreamDestroy(fs);
+    }
+};
+
+namespace fmm {
+namespace {
+
+// Allocates the plan's buffers, copies the operators, and captures the graph.
+void build_plan(fmm_plan &pl, Workspace &ws, const int64_t *offsets, const uint8_t *sel)
+{
+    const PlanShape &s = pl.s;
+    PlanBuffers &b = pl.b;
+    PlanMemory &m = pl.mem;
+    const int N = s.N, nsys = s.nsys, P2pad = s.P2pad;
+    const int64_t cc = s.cell_cap;
+    FMM_CUDA_TRY(cudaStreamCreateWithFlags(&pl.st, cudaStreamNonBlocking));
+    int lo = 0, hi = 0;
+    FMM_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    FMM_CUDA_TRY(cudaStreamCreateWithPriority(&pl.fs, cudaStreamNonBlocking, hi));
+    FMM_CUDA_TRY(cudaEventCreateWithFlags(&pl.fork, cudaEventDisableTiming));
+    FMM_CUDA_TRY(cudaEventCreateWithFlags(&pl.join, cudaEventDisableTiming));
+
+    b.xyz = pl.xyz;
+    b.q = pl.q;
+    b.phi = pl.phi;
+    b.grad = pl.grad;
+    b.flags = m.get<int>(kNumFlags);
+    b.sz = m.get<int>(kSzWords);
+    b.bbox_u = m.get<uint32_t>(6 * (size_t)nsys);
+    b.box = m.get<double>(4 * (size_t)nsys);
+    b.sys_off = m.get<int>(nsys + 1);
+    b.keys = m.get<uint64_t>(N);
+    b.keys_alt = m.get<uint64_t>(N);
+    b.idx = m.get<uint32_t>(N);
+    b.idx_alt = m.get<uint32_t>(N);
+    if (nsys > 1) {
+        b.keys_orig = m.get<uint64_t>(N);
+        b.sys_key = m.get<uint64_t>(N);
+    }
+    const int64_t nh = radix_hist_elems(N);
+    b.hist = m.get<uint32_t>(nh);
+    b.scan_u32 = m.get<uint32_t>(scan_temp_elems(nh));
+    b.pts = m.get<float4>(N);
+    b.c.level = m.get<int>(cc);
+    b.c.prefix = m.get<uint64_t>(cc);
+    b.c.begin = m.get<int>(cc);
+    b.c.end = m.get<int>(cc);
+    b.c.parent = m.get<int>(cc);
+    b.c.child0 = m.get<int>(cc);
+    b.c.nchild = m.get<int>(cc);
+    b.c.tile = m.get<int>(cc);
+    b.c.lane = m.get<int>(cc);
+    b.c.sys = m.get<int>(cc);
+    b.blvl = m.get<uint64_t>(std::max(N - 1, 1));
+    b.bpos = m.get<uint32_t>(std::max(N - 1, 1));
+    b.bstart = m.get<int>(24);
+    b.packed = m.get<int64_t>(s.max_level_cap + 1);
+    b.packed_ex = m.get<int64_t>(s.max_level_cap + 1);
+    b.scan_i64 = m.get<int64_t>(scan_temp_elems(s.max_level_cap));
+    b.leaf_flag = m.get<int>(cc);
+    b.leaf_ex = m.get<int>(cc + 1);
+    b.scan_i32 = m.get<int>(scan_temp_elems(std::max<int64_t>({cc, (int64_t)kHashCap, (int64_t)s.tile_cap})));
+    b.leaves = m.get<int>(cc);
+    ListArrays &L = b.L;
+    for (int **a : {&L.m2l_off, &L.m2l_cnt, &L.p2p_off, &L.p2p_cnt, &L.def_off, &L.def_cnt, &L.m2p_off, &L.m2p_cnt,
+                    &L.p2l_off, &L.p2l_cnt})
+        *a = m.get<int>(cc);
+    L.m2l_src = m.get<int>(s.m2l_cap);
+    L.m2l_tgt = m.get<int>(s.m2l_cap);
+    L.m2l_slot = m.get<uint32_t>(s.m2l_cap);
+    L.p2p_src = m.get<int>(s.p2p_cap);
+    L.p2p_tgt = m.get<int>(s.p2p_cap);
+    L.def_src = m.get<int>(s.def_cap);
+    L.m2p_src = m.get<int>(s.m2p_cap);
+    L.m2p_tgt = m.get<int>(s.m2p_cap);
+    L.p2l_src = m.get<int>(s.p2l_cap);
+    L.p2l_tgt = m.get<int>(s.p2l_cap);
+    b.hash_keys = m.get<uint64_t>(kHashCap);
+    b.tcount = m.get<unsigned long long>(5);
+    b.totals = m.get<unsigned long long>(5);
+    b.far = m.get<float4>(N);
+    b.near = m.get<float4>(N);
+    b.p2p_counter = m.get<int>(1);
+    b.hflag = m.get<int>(kHashCap);
+    b.hex = m.get<int>(kHashCap + 1);
+    b.ukeys = m.get<uint64_t>(kHashCap);
+    b.ukeys_alt = m.get<uint64_t>(kHashCap);
+    b.uslot = m.get<uint32_t>(kHashCap);
+    b.slot_class = m.get<int>(kHashCap);
+    b.class_slot = m.get<int>(s.nclass_cap);
+    b.tile_cells = m.get<int>((size_t)s.tile_cap * kTile);
+    b.bitmap = m.get<uint32_t>((size_t)s.tile_cap * s.nwords);
+    b.tile_cnt = m.get<int>(s.tile_cap);
+    b.entry_base = m.get<int>(s.tile_cap + 1);
+    b.word_prefix = m.get<int>((size_t)s.tile_cap * s.nwords);
+    b.entry_class = m.get<int>(s.nent_cap);
+    b.src = m.get<int>((size_t)s.nent_cap * kTile);
+    b.M = m.get<float>((size_t)cc * P2pad);
+    b.Lx = m.get<float>((size_t)cc * P2pad);
+    b.mtmp = m.get<float>((size_t)cc * P2pad);
+    if (s.tensor) {
+        b.units = m.get<M2LUnit>(s.units_cap);
+        b.unit_base = m.get<int>(s.tile_cap + 1);
+        b.tile_units = m.get<int>(s.units_cap);
+        b.partial = m.get<float>((size_t)s.units_cap * 128 * P2pad);
+    }
+
+    // constant inputs: system offsets, selection table, operators and the class-key table
+    cudaStream_t st = pl.st;
+    {
+        std::vector<int> off32(nsys + 1);
+        for (int sy = 0; sy <= nsys; ++sy) off32[sy] = (int)offsets[sy];
+        FMM_CUDA_TRY(cudaMemcpy(b.sys_off, off32.data(), sizeof(int) * (nsys + 1), cudaMemcpyHostToDevice));
+    }
+    if (sel) {
+        uint8_t *d = m.get<uint8_t>((size_t)kSelNB * kSelNB);
+        FMM_CUDA_TRY(cudaMemcpy(d, sel, (size_t)kSelNB * kSelNB, cudaMemcpyHostToDevice));
+        b.sel = d;
+    }
+    const size_t shift_n = (size_t)8 * P2pad * P2pad;
+    float *m2m = m.get<float>(shift_n), *l2l = m.get<float>(shift_n);
+    FMM_CUDA_TRY(cudaMemcpy(m2m, get<float>(ws, "m2m"), sizeof(float) * shift_n, cudaMemcpyDeviceToDevice));
+    FMM_CUDA_TRY(cudaMemcpy(l2l, get<float>(ws, "l2l"), sizeof(float) * shift_n, cudaMemcpyDeviceToDevice));
+    b.m2m = m2m;
+    b.l2l = l2l;
+    if (s.p >= kFp64TopP) {
+        double *m64 = m.get<double>(shift_n), *l64 = m.get<double>(shift_n);
+        FMM_CUDA_TRY(cudaMemcpy(m64, get<double>(ws, "m2m64"), sizeof(double) * shift_n, cudaMemcpyDeviceToDevice));
+        FMM_CUDA_TRY(cudaMemcpy(l64, get<double>(ws, "l2l64"), sizeof(double) * shift_n, cudaMemcpyDeviceToDevice));
+        b.m2m64 = m64;
+        b.l2l64 = l64;
+    }
+    // every class operator built so far for this p, in the workspace's slots
+    const int nops = std::max(ws.table_slots, 1);
+    pl.operators = ws.table_slots;
+    float *table = m.get<float>((size_t)nops * P2pad * P2pad);
+    FMM_CUDA_TRY(cudaMemcpy(table, get<float>(ws, "table"), sizeof(float) * (size_t)ws.table_slots * P2pad * P2pad,
+                            cudaMemcpyDeviceToDevice));
+    b.table = table;
+    if (s.tensor) {
+        unsigned char *split = m.get<unsigned char>(m2l_split_bytes(P2pad, s.bf16, nops));
+        launch_split_tables(s.bf16, table, 0, ws.table_slots, P2pad, split, st);
+        b.tsplit = split;
+    }
+    {
+        std::vector<uint64_t> hk(s.class_hcap, kHashEmpty);
+        std::vector<int> hs(s.class_hcap, 0);
+        for (const auto &kv : ws.class_cache) {
+            uint32_t h = (uint32_t)((kv.first * 0x9e3779b97f4a7c15ull) >> 40) & (s.class_hcap - 1);
+            while (hk[h] != kHashEmpty) h = (h + 1) & (s.class_hcap - 1);
+            hk[h] = kv.first;
+            hs[h] = kv.second;
+        }
+        uint64_t *dk = m.get<uint64_t>(s.class_hcap);
+        int *ds = m.get<int>(s.class_hcap);
+        FMM_CUDA_TRY(cudaMemcpy(dk, hk.data(), sizeof(uint64_t) * s.class_hcap, cudaMemcpyHostToDevice));
+        FMM_CUDA_TRY(cudaMemcpy(ds, hs.data(), sizeof(int) * s.class_hcap, cudaMemcpyHostToDevice));
+        b.chash_keys = dk;
+        b.chash_slots = ds;
+    }
+    // kernel attributes are set outside the capture (the sizing solve may not
+    // have run the hybrid kernels)
+    const int rows_smem = (int)((size_t)32 * (P2pad + 1) * sizeof(float));
+    if (rows_smem > 48 * 1024) {
+        set_smem_limit_once((const void *)k_p2m, rows_smem);
+        set_smem_limit_once((const void *)k_p2l, rows_smem);
+    }
+    if (s.hybrid && m2p_smem(s.p, P2pad) > 48 * 1024)
+        set_smem_limit_once((const void *)k_m2p, (int)m2p_smem(s.p, P2pad));
+    set_carveout_once((const void *)k_p2p, cudaSharedmemCarveoutMaxShared);
+    FMM_CUDA_TRY(cudaStreamSynchronize(st));
+
+    // capture
+    const int64_t launches0 = g_launch_count;
+    FMM_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    try {
+        enqueue_plan(s, b, st, pl.fs, pl.fork, pl.join);
+    } catch (...) {
+        cudaGraph_t g = nullptr;
+        cudaStreamEndCapture(st, &g);
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        throw;
+    }
+    FMM_CUDA_TRY(cudaStreamEndCapture(st, &pl.graph));
+    pl.graph_kernels = g_launch_count - launches0;
+    size_t nodes = 0;
+    FMM_CUDA_TRY(cudaGraphGetNodes(pl.graph, nullptr, &nodes));
+    pl.graph_nodes = (int64_t)nodes;
+    FMM_CUDA_TRY(cudaGraphInstantiate(&pl.exec, pl.graph, 0));
 }
 
 }  // namespace
@@ -1467,6 +1746,132 @@ fmm_status fmm_export(int what, void *dst, int64_t capacity, int64_t *needed)
         }
     });
 }
+
+// ---------------------------------------------------------------- captured plans
+
+fmm_status fmm_plan_create(fmm_plan **plan, const float *xyz, const float *q, int64_t N, const int64_t *offsets,
+                           int nsys, int p, double theta, int ncrit, const fmm_options *opt, double headroom,
+                           void *stream)
+{
+    return guarded([&] {
+        if (!plan) throw Error{FMM_ERR_ARG, "null plan pointer"};
+        *plan = nullptr;
+        if (headroom == 0.0) headroom = 1.25;
+        if (!(headroom >= 1.0 && headroom <= 16.0)) throw Error{FMM_ERR_ARG, "headroom must be in [1, 16]"};
+        std::vector<int64_t> off;
+        if (offsets) {
+            if (nsys < 1) throw Error{FMM_ERR_ARG, "offsets must hold nsys + 1 >= 2 entries"};
+            if (offsets[0] != 0) throw Error{FMM_ERR_ARG, "offsets[0] must be 0"};
+            for (int sy = 0; sy < nsys; ++sy)
+                if (offsets[sy + 1] <= offsets[sy]) throw Error{FMM_ERR_ARG, "every system needs at least one particle"};
+            if (offsets[nsys] != N) throw Error{FMM_ERR_ARG, "offsets[nsys] must equal N"};
+            off.assign(offsets, offsets + nsys + 1);
+        } else {
+            if (nsys != 1) throw Error{FMM_ERR_ARG, "without offsets nsys must be 1"};
+            off = {0, N};
+        }
+        const fmm_options o = resolve_opts(opt);
+        validate(xyz, q, N, p, theta, ncrit, xyz, xyz, o);
+        std::unique_ptr<fmm_plan> pl(new fmm_plan());
+        FMM_CUDA_TRY(cudaGetDevice(&pl->device));
+        pl->xyz = pl->mem.get<float>(3 * (size_t)N);
+        pl->q = pl->mem.get<float>((size_t)N);
+        pl->phi = pl->mem.get<float>((size_t)N);
+        pl->grad = pl->mem.get<float>(3 * (size_t)N);
+        cudaStream_t cs = (cudaStream_t)stream;
+        FMM_CUDA_TRY(cudaMemcpyAsync(pl->xyz, xyz, sizeof(float) * 3 * N, cudaMemcpyDeviceToDevice, cs));
+        FMM_CUDA_TRY(cudaMemcpyAsync(pl->q, q, sizeof(float) * N, cudaMemcpyDeviceToDevice, cs));
+        Workspace &ws = workspace_for_current_device();
+        std::lock_guard<std::mutex> lk(ws.mu);
+        const uint8_t *sel = selection_table(ws, o, p, theta);
+        // the sizing solve (it also builds the operators of its classes)
+        solve_locked(ws, pl->xyz, pl->q, N, nsys, off.data(), p, theta, ncrit, pl->phi, pl->grad, cs, o, nullptr, sel);
+        FMM_CUDA_TRY(cudaStreamSynchronize(cs));
+        pl->s = plan_shape(ws, N, nsys, p, theta, ncrit, o, sel != nullptr, headroom);
+        build_plan(*pl, ws, off.data(), sel);
+        *plan = pl.release();
+    });
+}
+
+fmm_status fmm_plan_execute(fmm_plan *plan, const float *xyz, const float *q, float *phi, float *grad, void *stream)
+{
+    return guarded([&] {
+        if (!plan) throw Error{FMM_ERR_ARG, "null plan"};
+        int dev = 0;
+        FMM_CUDA_TRY(cudaGetDevice(&dev));
+        if (dev != plan->device) throw Error{FMM_ERR_ARG, "the plan belongs to another device"};
+        cudaStream_t st = (cudaStream_t)stream;
+        const size_t n = (size_t)plan->s.N;
+        if (xyz && xyz != plan->xyz)
+            FMM_CUDA_TRY(cudaMemcpyAsync(plan->xyz, xyz, sizeof(float) * 3 * n, cudaMemcpyDeviceToDevice, st));
+        if (q && q != plan->q) FMM_CUDA_TRY(cudaMemcpyAsync(plan->q, q, sizeof(float) * n, cudaMemcpyDeviceToDevice, st));
+        FMM_CUDA_TRY(cudaGraphLaunch(plan->exec, st));
+        if (phi && phi != plan->phi)
+            FMM_CUDA_TRY(cudaMemcpyAsync(phi, plan->phi, sizeof(float) * n, cudaMemcpyDeviceToDevice, st));
+        if (grad && grad != plan->grad)
+            FMM_CUDA_TRY(cudaMemcpyAsync(grad, plan->grad, sizeof(float) * 3 * n, cudaMemcpyDeviceToDevice, st));
+    });
+}
+
+fmm_status fmm_plan_check(fmm_plan *plan, void *stream)
+{
+    return guarded([&] {
+        if (!plan) throw Error{FMM_ERR_ARG, "null plan"};
+        FMM_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+        int f[kNumFlags], sz[kSzWords];
+        FMM_CUDA_TRY(cudaMemcpy(f, plan->b.flags, sizeof(f), cudaMemcpyDeviceToHost));
+        FMM_CUDA_TRY(cudaMemcpy(sz, plan->b.sz, sizeof(sz), cudaMemcpyDeviceToHost));
+        if (f[kFlagNonfinite]) throw Error{FMM_ERR_NONFINITE, "a coordinate is NaN or infinite"};
+        if (f[kFlagTimeout]) throw Error{FMM_ERR_TIMEOUT, "a bounded device-side wait expired (M2L pipeline)"};
+        if (sz[kSzAbort] || f[kFlagHashFull] || f[kFlagClassRange] || f[kFlagStack])
+            throw Error{FMM_ERR_CAPACITY, "the replay exceeded a capacity of the plan or met an offset class it has "
+                                          "no operator for; its results are invalid (create a new plan)"};
+    });
+}
+
+fmm_status fmm_plan_buffers(fmm_plan *plan, float **xyz, float **q, float **phi, float **grad)
+{
+    return guarded([&] {
+        if (!plan) throw Error{FMM_ERR_ARG, "null plan"};
+        if (xyz) *xyz = plan->xyz;
+        if (q) *q = plan->q;
+        if (phi) *phi = plan->phi;
+        if (grad) *grad = plan->grad;
+    });
+}
+
+fmm_status fmm_plan_info(fmm_plan *plan, fmm_plan_info_t *info)
+{
+    return guarded([&] {
+        if (!plan || !info) throw Error{FMM_ERR_ARG, "null argument"};
+        const PlanShape &s = plan->s;
+        int sz[kSzWords];
+        FMM_CUDA_TRY(cudaDeviceSynchronize());
+        FMM_CUDA_TRY(cudaMemcpy(sz, plan->b.sz, sizeof(sz), cudaMemcpyDeviceToHost));
+        *info = fmm_plan_info_t{};
+        info->N = s.N;
+        info->nsys = s.nsys;
+        info->levels = s.levels;
+        info->cell_cap = s.cell_cap;
+        info->tile_cap = s.tile_cap;
+        info->class_cap = s.nclass_cap;
+        info->entry_cap = s.nent_cap;
+        info->unit_cap = s.units_cap;
+        info->m2l_cap = s.m2l_cap;
+        info->p2p_cap = s.p2p_cap;
+        info->operators = plan->operators;
+        info->graph_nodes = plan->graph_nodes;
+        info->graph_kernels = plan->graph_kernels;
+        info->last_cells = sz[kSzCells];
+        info->last_leaves = sz[kSzLeaves];
+        info->last_classes = sz[kSzClasses];
+        info->last_entries = sz[kSzEntries];
+        info->last_units = sz[kSzUnits];
+        info->last_valid = sz[kSzAbort] == 0;
+    });
+}
+
+void fmm_plan_destroy(fmm_plan *plan) { delete plan; }
 
 const char *fmm_last_error(void) { return g_last_error.c_str(); }
 

@@ -4,6 +4,8 @@
 
 #include <cuda_fp16.h>
 
+#include <climits>
+
 #include <vector>
 
 #include "common.cuh"
@@ -19,6 +21,26 @@ enum {
     kFlagTimeout = 4,     // a bounded device-side wait expired
     kNumFlags = 8
 };
+
+// Device-side sizes of a solve (int[kSzWords]).  A solve replayed from a CUDA
+// graph reads every count and level range here instead of from host arguments;
+// the kernels that take a nullable `sz` use it when it is given.  When a count
+// exceeds a capacity of the plan, the step that finds it sets kSzAbort and
+// clamps the count (to zero, or to the last level), so that every later step
+// stays inside its buffers; the result of that replay is then invalid.
+enum {
+    kSzLevel = 0,      // first cell of each level, kMaxLevel + 2 entries
+    kSzTileBase = 24,  // first M2L tile of the children of each level's cells
+    kSzTiles = 48,     // M2L tiles in use
+    kSzCells,          // cells
+    kSzLeaves,         // leaves
+    kSzClasses,        // offset classes
+    kSzEntries,        // (tile, class) blocks
+    kSzUnits,          // M2L work units
+    kSzAbort,          // nonzero: a plan capacity was exceeded
+    kSzWords = 64
+};
+static_assert(kMaxLevel + 2 <= kSzTileBase - kSzLevel, "level starts overflow their slot");
 
 // Structure-of-arrays cells, level by level (Morton order within a level).
 struct CellArrays {
@@ -50,6 +72,7 @@ constexpr uint32_t kHashCap = 1u << kHashBits;
 constexpr uint64_t kHashEmpty = ~0ull;
 
 // tree.cu
+__global__ void k_init_bbox(uint32_t *bbox_u, int nsys);
 __global__ void k_bbox(const float *xyz, int64_t n, uint32_t *bbox_u, int *flags);
 __global__ void k_morton(const float *xyz, int64_t n, const int *off, int nsys,
                          const uint32_t *bbox_u, double *box, uint64_t *keys, uint32_t *idx);
@@ -63,68 +86,99 @@ __global__ void k_permute(const float *xyz, const float *q, const uint32_t *idx,
                           float4 *out);
 __global__ void k_first_diff(const uint64_t *keys, int64_t n, uint64_t *lvl, uint32_t *pos);
 __global__ void k_level_starts(const uint64_t *lvl, int64_t n, int *start);
+// With sz: the level's cells come from sz, packed has len entries (zero past the
+// level) and emission stops at the level end sz clamps to.
 __global__ void k_split_count(CellArrays c, const uint32_t *bpos, const int *lstart, int a, int b,
-                              int level, int ncrit, int max_depth, int64_t *packed);
+                              int level, int ncrit, int max_depth, int64_t *packed, const int *sz = nullptr,
+                              int len = 0);
 __global__ void k_split_emit(CellArrays c, const uint64_t *keys, const uint32_t *bpos,
                              const int *lstart, int a, int b, int level, const int64_t *packed,
-                             const int64_t *ex, int tile_base);
-__global__ void k_fill_tile_cells(CellArrays c, int ncells, int *tile_cells);
-__global__ void k_leaf_flags(CellArrays c, int ncells, int *flag);
-__global__ void k_leaf_compact(CellArrays c, int ncells, const int *ex, int *leaves);
+                             const int64_t *ex, int tile_base, const int *sz = nullptr);
+// Next level start and tile base from a level's split totals, against the
+// plan's capacities (graph replay only).
+__global__ void k_level_advance(const int64_t *total, int level, int last_level, int cell_cap,
+                                int next_level_cap, int tile_cap, int *sz);
+__global__ void k_fill_tile_cells(CellArrays c, int ncells, int *tile_cells, const int *sz = nullptr);
+// With sz: flags for len cells, zero past the last cell.
+__global__ void k_leaf_flags(CellArrays c, int ncells, int *flag, const int *sz = nullptr, int len = 0);
+__global__ void k_leaf_compact(CellArrays c, int ncells, const int *ex, int *leaves, const int *sz = nullptr);
 
 // traverse.cu
 constexpr int kSelNB = 128;  // count buckets of the hybrid selection table
 __global__ void k_traverse_level(CellArrays c, ListArrays L, int a, int b, double theta2,
                                  float theta2f, const uint8_t *sel, unsigned long long *counters,
                                  int64_t cap_m, int64_t cap_p, int64_t cap_d, int64_t cap_q,
-                                 int64_t cap_l, uint64_t *hash_keys, int *flags);
+                                 int64_t cap_l, uint64_t *hash_keys, int *flags, const int *sz = nullptr,
+                                 int level = 0);
+// List totals against capacities (graph replay): totals[k] = counters[k], or
+// zero for every list (and kSzAbort set) when one exceeds its capacity.
+__global__ void k_check_lists(const unsigned long long *counters, int64_t cap_m, int64_t cap_p, int64_t cap_d,
+                              int64_t cap_q, int64_t cap_l, unsigned long long *totals, int *sz);
+// Offset classes against the plan (graph replay): nclass from the hash scan (on
+// overflow no class and no M2L pair), then each class key's table slot from the
+// plan's key table (open addressing, hcap a power of two); a class the plan has
+// no table for sets kSzAbort.
+__global__ void k_plan_classes(const int *nclass_dev, int nclass_cap, int *sz, unsigned long long *totals);
+__global__ void k_class_lookup(const uint64_t *sorted_keys, const int *sz, const uint64_t *hkeys,
+                               const int *hslots, uint32_t hcap, int *class_slot, int *szw);
+// Entries against the plan's capacity (graph replay): on overflow every tile is
+// emptied and kSzAbort set.  One block.
+__global__ void k_check_entries(int *entry_base, int ntiles_cap, int nent_cap, int *sz);
 __global__ void k_hash_flags(const uint64_t *hash_keys, int *flag);
 __global__ void k_hash_compact(const uint64_t *hash_keys, const int *ex, uint64_t *ukeys,
                                uint32_t *uslot);
 __global__ void k_root_lists(CellArrays c, ListArrays L, int nsys, unsigned long long *counters);
 __global__ void k_rank_classes(const uint64_t *ukeys, const uint32_t *uslot, int n,
-                               uint64_t *sorted_keys, int *slot_class);
+                               uint64_t *sorted_keys, int *slot_class, const int *sz = nullptr);
 __global__ void k_slot_to_class(const uint32_t *uslot, int nclass, int *slot_class);
-__global__ void k_m2l_class(uint32_t *m2l_slot, int64_t n, const int *slot_class);
+// dn (nullable): the pair count in device memory.
+__global__ void k_m2l_class(uint32_t *m2l_slot, int64_t n, const int *slot_class,
+                            const unsigned long long *dn = nullptr);
 __global__ void k_tile_bitmap(const int *m2l_tgt, const uint32_t *m2l_class, int64_t n,
-                              const int *cell_tile, int nwords, uint32_t *bitmap);
+                              const int *cell_tile, int nwords, uint32_t *bitmap,
+                              const unsigned long long *dn = nullptr);
 __global__ void k_tile_popc(const uint32_t *bitmap, int ntiles, int nwords, int *cnt);
 __global__ void k_tile_entries(const uint32_t *bitmap, int ntiles, int nwords,
                                const int *entry_base, int *word_prefix, int *entry_class,
-                               const int *class_slot);
+                               const int *class_slot, int entry_cap = INT_MAX);
 __global__ void k_tile_src(const int *m2l_tgt, const int *m2l_src, const uint32_t *m2l_class,
                            int64_t n, const int *cell_tile, const int *cell_lane, int nwords,
                            const uint32_t *bitmap, const int *word_prefix,
-                           const int *entry_base, int *src);
+                           const int *entry_base, int *src, const unsigned long long *dn = nullptr,
+                           int entry_cap = INT_MAX);
 
 // expansions.cu
 __global__ void k_build_m2l_tables(const uint64_t *class_keys, const int *cache_slot, int nnew,
                                    int p, int P2pad, float *table);
 __global__ void k_build_shift_tables(int p, int P2pad, float *m2m, float *l2l, double *m2m64, double *l2l64);
 __global__ void k_p2m(CellArrays c, const int *leaves, int nleaves, const float4 *pts,
-                      const double *box, int p, int P2pad, float *M);
+                      const double *box, int p, int P2pad, float *M, const int *sz = nullptr);
 // Fills the recurrence-coefficient tables P2M and L2P read (once per device).
 void init_recurrence_tables();
 // M2M (l2l = false: parents [a, b) of E from their children, through the
 // per-child scratch T[ncells][P2pad]) or L2L (l2l = true: the children of
 // parents [a, b) of E from them), octant-batched.
+// With sz: parents are the cells of `level` in sz, launched for up to `cap`
+// of them (a and b are ignored).
 void launch_shift_batched(bool l2l, const CellArrays &c, int a, int b, const float *mats, int P2, int P2pad,
-                          float *E, float *T, cudaStream_t st);
+                          float *E, float *T, cudaStream_t st, const int *sz = nullptr, int level = 0,
+                          int cap = 0);
 // The same shifts with FP64 matrices and sums, for the top levels at high p.
 constexpr int kFp64TopP = 12, kFp64TopLevels = 3;  // p >= 12: parents at levels 0..2
 void launch_shift_fp64(bool l2l, const CellArrays &c, int a, int b, const double *mats, int P2, int P2pad, float *E,
-                       cudaStream_t st);
+                       cudaStream_t st, const int *sz = nullptr, int level = 0, int cap = 0);
 __global__ void k_l2p(CellArrays c, const int *leaves, int nleaves, const float4 *pts,
-                      const double *box, int p, int P2pad, const float *L, float4 *far);
+                      const double *box, int p, int P2pad, const float *L, float4 *far,
+                      const int *sz = nullptr);
 // P2L: one warp (block) per target cell with a P2L list; the source particles are
 // added to the cell's local expansion.  Dynamic shared memory 32 (P2pad + 1) floats.
 __global__ void k_p2l(CellArrays c, ListArrays Ls, int ncells, const float4 *pts, const double *box, int p,
-                      int P2pad, float *L);
+                      int P2pad, float *L, const int *sz = nullptr);
 // M2P: blocks of kM2PWarps warps, one target leaf per warp; dynamic shared memory m2p_smem(p, P2pad).
 constexpr int kM2PWarps = 4;
 size_t m2p_smem(int p, int P2pad);
 __global__ void k_m2p(CellArrays c, ListArrays Ls, const int *leaves, int nleaves, const float4 *pts,
-                      const double *box, int p, int P2pad, const float *M, float4 *far);
+                      const double *box, int p, int P2pad, const float *M, float4 *far, const int *sz = nullptr);
 
 // m2l.cu
 void launch_m2l_simt(int ntiles, const int *entry_base, const int *entry_class, const int *src,
@@ -139,10 +193,16 @@ bool m2l_tc_supported(int P2pad);
 // One bounded wait on an mbarrier nothing arrives at (failure-detection self-test).
 void launch_wait_selftest(uint32_t polls, int *flags, cudaStream_t st);
 size_t m2l_tc_smem(int P2pad, bool bf16, int &nstages);
+// With sz: launched for nunits (a capacity) units, of which the first sz[kSzUnits] run.
 void launch_m2l_tc(bool bf16, int nunits, const void *units, int ntiles, const int *unit_base,
                    const int *tile_units, const int *entry_class, const int *src, const int *tile_cells,
                    const float *M, const unsigned char *tsplit, int P2pad, float *partial, float *L,
-                   int *flags, cudaStream_t st);
+                   int *flags, cudaStream_t st, const int *sz = nullptr);
+// Work units on the device (graph replay): per tile ceil(blocks / chunk) units,
+// ordered (rank within the tile, tile), as the host builds them; kSzAbort and
+// no units when more than units_cap would be needed.  One block.
+__global__ void k_build_units(const int *entry_base, int ntiles_cap, int chunk, int units_cap, M2LUnit *units,
+                              int *unit_base, int *tile_units, int *sz);
 // Bytes of the hi/lo split class matrices of nslots classes, and the kernel that
 // writes slots [slot0, slot0 + nslots) of them from the FP32 tables.
 size_t m2l_split_bytes(int P2pad, bool bf16, int nslots);
@@ -152,7 +212,7 @@ void launch_split_tables(bool bf16, const float *table, int slot0, int nslots, i
 // p2p.cu -- persistent P2P: kP2PBlocksPerSM blocks of 128 threads per SM
 constexpr int kP2PBlocksPerSM = 6;
 __global__ void k_p2p(CellArrays c, ListArrays L, const int *leaves, int nleaves,
-                      const float4 *pts, float4 *near, int *counter);
+                      const float4 *pts, float4 *near, int *counter, const int *sz = nullptr);
 __global__ void k_direct(const float *xyz, const float *q, int64_t n, float *phi, float *grad);
 __global__ void k_combine(const float4 *far, const float4 *near, const uint32_t *idx, int64_t n,
                           float *phi, float *grad);

@@ -237,8 +237,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     k_m2l_tc(const Unit *__restrict__ units, const int *__restrict__ entry_class,
              const int *__restrict__ src, const float *__restrict__ M,
              const unsigned char *__restrict__ tsplit, int P2pad, int nstages,
-             float *__restrict__ partial, int *__restrict__ flags)
+             float *__restrict__ partial, int *__restrict__ flags, const int *__restrict__ sz)
 {
+    // a replayed plan launches for its unit capacity: the CTAs past the units
+    // of this solve leave before touching barriers or tensor memory
+    if (sz && (int)blockIdx.x >= sz[kSzUnits]) return;
     constexpr int NG = 2;                          // groups of 8 A rows per producer warp
     constexpr bool SUM_TMEM = 3 * N <= 512;        // running sum in tensor memory
     constexpr int NBUF = 5 * N <= 512 ? 2 : 1;     // main/correction buffer pairs
@@ -623,7 +626,7 @@ size_t m2l_tc_smem(int P2pad, bool bf16, int &nstages)
 void launch_m2l_tc(bool bf16, int nunits, const void *units, int ntiles, const int *unit_base,
                    const int *tile_units, const int *entry_class, const int *src, const int *tile_cells,
                    const float *M, const unsigned char *tsplit, int P2pad, float *partial, float *L,
-                   int *flags, cudaStream_t st)
+                   int *flags, cudaStream_t st, const int *sz)
 {
     int nstages = 0;
     const size_t smem = m2l_tc_smem(P2pad, bf16, nstages);
@@ -632,7 +635,7 @@ void launch_m2l_tc(bool bf16, int nunits, const void *units, int ntiles, const i
     do {                                                                                           \
         set_smem_limit_once((const void *)k_m2l_tc<B, NN>, (int)smem);                              \
         k_m2l_tc<B, NN><<<nunits, kThreads, smem, st>>>(static_cast<const Unit *>(units), entry_class, \
-                                                        src, M, tsplit, P2pad, nstages, partial, flags); \
+                                                        src, M, tsplit, P2pad, nstages, partial, flags, sz); \
     } while (0)
 #define FMM_M2L_TC_BY_N(B)                                  \
     do {                                                    \
@@ -657,6 +660,90 @@ void launch_m2l_tc(bool bf16, int nunits, const void *units, int ntiles, const i
     }
     k_m2l_reduce<<<ntiles, 256, 0, st>>>(unit_base, tile_units, partial, tile_cells, P2pad, L);
     FMM_LAUNCH_CHECK();
+}
+
+
+// Work units of a replayed plan, built as the host builds them for a solve: tile
+// t has ceil(blocks_t / chunk) units, unit r of tile t covers its blocks
+// [eb_t + r chunk, min(eb_t + (r + 1) chunk, eb_{t+1})), and the units run in
+// the order (r, t).  One block: per rank r, a block-wide scan over the tiles
+// gives each unit of rank r its place.
+__global__ void __launch_bounds__(1024)
+    k_build_units(const int *__restrict__ entry_base, int ntiles_cap, int chunk, int units_cap,
+                  M2LUnit *__restrict__ units, int *__restrict__ unit_base, int *__restrict__ tile_units,
+                  int *__restrict__ sz)
+{
+    __shared__ int s_part[32];
+    __shared__ int s_total, s_maxr;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int per = (ntiles_cap + nthr - 1) / nthr;  // tiles per thread, contiguous
+    const int t0 = min(ntiles_cap, tid * per), t1 = min(ntiles_cap, t0 + per);
+    auto nut = [&](int t) { return (entry_base[t + 1] - entry_base[t] + chunk - 1) / chunk; };
+    // block-wide exclusive scan of one value per thread (in thread order)
+    auto scan = [&](int v, int &total) {
+        const int lane = tid & 31, w = tid >> 5;
+        int x = v;
+        for (int d = 1; d < 32; d <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, d);
+            if (lane >= d) x += y;
+        }
+        __syncthreads();
+        if (lane == 31) s_part[w] = x;
+        __syncthreads();
+        if (w == 0) {
+            const int nw = (nthr + 31) >> 5;
+            int y = lane < nw ? s_part[lane] : 0;
+            for (int d = 1; d < 32; d <<= 1) {
+                const int z = __shfl_up_sync(0xffffffffu, y, d);
+                if (lane >= d) y += z;
+            }
+            if (lane < nw) s_part[lane] = y;  // inclusive per warp
+            if (lane == 31) s_total = y;
+        }
+        __syncthreads();
+        total = s_total;
+        return x - v + (w > 0 ? s_part[w - 1] : 0);
+    };
+    // unit_base: exclusive scan of the units per tile
+    int mine = 0, maxr = 0;
+    for (int t = t0; t < t1; ++t) {
+        const int u = nut(t);
+        mine += u;
+        maxr = max(maxr, u);
+    }
+    if (tid == 0) s_maxr = 0;
+    __syncthreads();
+    atomicMax(&s_maxr, maxr);
+    int nunits = 0;
+    int base = scan(mine, nunits);
+    const bool fits = nunits <= units_cap;
+    for (int t = t0; t < t1; ++t) {
+        unit_base[t] = fits ? base : 0;
+        base += fits ? nut(t) : 0;
+    }
+    if (tid == nthr - 1) unit_base[ntiles_cap] = fits ? nunits : 0;
+    if (tid == 0) {
+        sz[kSzUnits] = fits ? nunits : 0;
+        if (!fits) sz[kSzAbort] = 1;
+    }
+    if (!fits) return;
+    __syncthreads();
+    const int R = s_maxr;
+    int done = 0;  // units of ranks below r
+    for (int r = 0; r < R; ++r) {
+        int cnt = 0;
+        for (int t = t0; t < t1; ++t) cnt += nut(t) > r;
+        int total = 0;
+        int pos = done + scan(cnt, total);
+        for (int t = t0; t < t1; ++t) {
+            if (nut(t) <= r) continue;
+            const int e0 = entry_base[t] + r * chunk;
+            units[pos] = {t, e0, min(e0 + chunk, entry_base[t + 1]), 0};
+            tile_units[unit_base[t] + r] = pos;
+            ++pos;
+        }
+        done += total;
+    }
 }
 
 }  // namespace fmm

@@ -330,8 +330,10 @@ __device__ __forceinline__ void p2p_leaf(const CellArrays &c, const ListArrays &
 // that runs beside it and has no tail wave.
 __global__ void __launch_bounds__(128, kP2PBlocksPerSM)
     k_p2p(CellArrays c, ListArrays L, const int *__restrict__ leaves, int nleaves,
-          const float4 *__restrict__ pts, float4 *__restrict__ near, int *__restrict__ counter)
+          const float4 *__restrict__ pts, float4 *__restrict__ near, int *__restrict__ counter,
+          const int *__restrict__ sz)
 {
+    if (sz) nleaves = sz[kSzLeaves];
     __shared__ __align__(16) float sh[4][128];
     __shared__ float4 red[4][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;

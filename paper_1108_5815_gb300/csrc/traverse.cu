@@ -258,10 +258,15 @@ __global__ void __launch_bounds__(128, 6)
     k_traverse_level(CellArrays c, ListArrays L, int a, int b, double theta2, float theta2f,
                      const uint8_t *__restrict__ sel, unsigned long long *__restrict__ counters,
                      int64_t cap_m, int64_t cap_p, int64_t cap_d, int64_t cap_q, int64_t cap_l,
-                     uint64_t *__restrict__ hash_keys, int *__restrict__ flags)
+                     uint64_t *__restrict__ hash_keys, int *__restrict__ flags, const int *__restrict__ sz,
+                     int level)
 {
     __shared__ int sF[4][2][kFrontier];
     __shared__ int sCnt[4][5][kCountCache];  // per-source counts of the count pass (first kCountCache)
+    if (sz) {
+        a = sz[kSzLevel + level];
+        b = sz[kSzLevel + level + 1];
+    }
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int t = a + warp;
@@ -490,8 +495,9 @@ __global__ void k_root_lists(CellArrays c, ListArrays L, int nsys, unsigned long
 // smaller keys (one thread per key).  slot_class[slot of the key] = its rank.
 __global__ void __launch_bounds__(128)
     k_rank_classes(const uint64_t *__restrict__ ukeys, const uint32_t *__restrict__ uslot, int n,
-                   uint64_t *__restrict__ sorted_keys, int *__restrict__ slot_class)
+                   uint64_t *__restrict__ sorted_keys, int *__restrict__ slot_class, const int *__restrict__ sz)
 {
+    if (sz) n = sz[kSzClasses];
     // each block ranks 128 keys against all n, staged through shared memory
     __shared__ uint64_t sk[2048];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -518,8 +524,9 @@ __global__ void k_slot_to_class(const uint32_t *__restrict__ uslot, int nclass,
 }
 
 __global__ void k_m2l_class(uint32_t *__restrict__ m2l_slot, int64_t n,
-                            const int *__restrict__ slot_class)
+                            const int *__restrict__ slot_class, const unsigned long long *__restrict__ dn)
 {
+    if (dn) n = (int64_t)*dn;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
         m2l_slot[i] = (uint32_t)slot_class[m2l_slot[i]];
@@ -529,8 +536,9 @@ __global__ void k_m2l_class(uint32_t *__restrict__ m2l_slot, int64_t n,
 
 __global__ void k_tile_bitmap(const int *__restrict__ m2l_tgt, const uint32_t *__restrict__ m2l_class,
                               int64_t n, const int *__restrict__ cell_tile, int nwords,
-                              uint32_t *__restrict__ bitmap)
+                              uint32_t *__restrict__ bitmap, const unsigned long long *__restrict__ dn)
 {
+    if (dn) n = (int64_t)*dn;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t cl = m2l_class[i];
@@ -556,7 +564,7 @@ __global__ void k_tile_popc(const uint32_t *__restrict__ bitmap, int ntiles, int
 // One warp per tile: word prefix counts and the list of (cache slot of) classes.
 __global__ void k_tile_entries(const uint32_t *__restrict__ bitmap, int ntiles, int nwords,
                                const int *__restrict__ entry_base, int *__restrict__ word_prefix,
-                               int *__restrict__ entry_class, const int *__restrict__ class_slot)
+                               int *__restrict__ entry_class, const int *__restrict__ class_slot, int entry_cap)
 {
     const int tile = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
@@ -574,7 +582,8 @@ __global__ void k_tile_entries(const uint32_t *__restrict__ bitmap, int ntiles, 
             while (rem) {
                 const int bpos = __ffs(rem) - 1;
                 rem &= rem - 1;
-                entry_class[e++] = class_slot[w * 32 + bpos];
+                if (e < entry_cap) entry_class[e] = class_slot[w * 32 + bpos];
+                ++e;
             }
         }
         run += warp_sum(pc);
@@ -586,8 +595,9 @@ __global__ void k_tile_src(const int *__restrict__ m2l_tgt, const int *__restric
                            const int *__restrict__ cell_tile, const int *__restrict__ cell_lane,
                            int nwords, const uint32_t *__restrict__ bitmap,
                            const int *__restrict__ word_prefix, const int *__restrict__ entry_base,
-                           int *__restrict__ src)
+                           int *__restrict__ src, const unsigned long long *__restrict__ dn, int entry_cap)
 {
+    if (dn) n = (int64_t)*dn;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int t = m2l_tgt[i];
@@ -596,8 +606,75 @@ __global__ void k_tile_src(const int *__restrict__ m2l_tgt, const int *__restric
         const int64_t wi = (int64_t)tile * nwords + (cl >> 5);
         const uint32_t below = bitmap[wi] & ((1u << (cl & 31)) - 1u);
         const int e = word_prefix[wi] + __popc(below);
-        src[(int64_t)e * kTile + cell_lane[t]] = m2l_src[i];
+        if (e < entry_cap) src[(int64_t)e * kTile + cell_lane[t]] = m2l_src[i];
     }
+}
+
+
+// ---------------------------------------------------------------- replayed plans
+
+__global__ void k_check_lists(const unsigned long long *__restrict__ counters, int64_t cap_m, int64_t cap_p,
+                              int64_t cap_d, int64_t cap_q, int64_t cap_l, unsigned long long *__restrict__ totals,
+                              int *__restrict__ sz)
+{
+    const int64_t cap[5] = {cap_m, cap_p, cap_d, cap_q, cap_l};
+    bool fits = true;
+    for (int k = 0; k < 5; ++k) fits = fits && (int64_t)counters[k] <= cap[k];
+    if (!fits) sz[kSzAbort] = 1;
+    for (int k = 0; k < 5; ++k) totals[k] = fits ? counters[k] : 0ull;
+}
+
+__global__ void k_plan_classes(const int *__restrict__ nclass_dev, int nclass_cap, int *__restrict__ sz,
+                               unsigned long long *__restrict__ totals)
+{
+    const int n = *nclass_dev;
+    if (n > nclass_cap) {
+        sz[kSzAbort] = 1;
+        sz[kSzClasses] = 0;
+        totals[0] = 0ull;  // no class ids: no M2L pair is placed
+    } else {
+        sz[kSzClasses] = n;
+    }
+}
+
+__global__ void k_class_lookup(const uint64_t *__restrict__ sorted_keys, const int *__restrict__ sz,
+                               const uint64_t *__restrict__ hkeys, const int *__restrict__ hslots, uint32_t hcap,
+                               int *__restrict__ class_slot, int *__restrict__ szw)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= sz[kSzClasses]) return;
+    const uint64_t k = sorted_keys[i];
+    uint32_t h = (uint32_t)((k * 0x9e3779b97f4a7c15ull) >> 40) & (hcap - 1);
+    int slot = -1;
+    for (uint32_t probe = 0; probe < hcap; ++probe, h = (h + 1) & (hcap - 1)) {
+        const uint64_t hk = hkeys[h];
+        if (hk == k) {
+            slot = hslots[h];
+            break;
+        }
+        if (hk == kHashEmpty) break;
+    }
+    if (slot < 0) {  // a class the plan has no operator for
+        szw[kSzAbort] = 1;
+        slot = 0;
+    }
+    class_slot[i] = slot;
+}
+
+// One block: every thread reads the total before any thread clears it.
+__global__ void k_check_entries(int *__restrict__ entry_base, int ntiles_cap, int nent_cap, int *__restrict__ sz)
+{
+    const int n = entry_base[ntiles_cap];
+    __syncthreads();
+    if (n <= nent_cap) {
+        if (threadIdx.x == 0) sz[kSzEntries] = n;
+        return;
+    }
+    if (threadIdx.x == 0) {
+        sz[kSzAbort] = 1;
+        sz[kSzEntries] = 0;
+    }
+    for (int t = threadIdx.x; t <= ntiles_cap; t += blockDim.x) entry_base[t] = 0;  // every tile empty
 }
 
 }  // namespace fmm

@@ -8,6 +8,8 @@
 // k = min(2^21 - 1, floor((x - lo) * (2^21 / side))) with each operation a single
 // IEEE round-to-nearest FP64 operation (__dsub_rn/__dmul_rn/__ddiv_rn, no
 // contraction), so keys match an FP64 CPU computation bit for bit.
+#include <climits>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -235,6 +237,14 @@ __global__ void k_gather_keys(const uint64_t *__restrict__ orig, const uint32_t 
 }
 
 // One root cell per system; roots fill the first ceil(nsys / 128) M2L tiles.
+// Per-system bounding boxes before the reduction: minima at all ones, maxima at zero
+// (order-preserving unsigned images of the coordinates).
+__global__ void k_init_bbox(uint32_t *bbox_u, int nsys)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 6 * nsys; i += gridDim.x * blockDim.x)
+        bbox_u[i] = (i % 6) < 3 ? 0xffffffffu : 0u;
+}
+
 __global__ void k_init_roots(CellArrays c, const int *__restrict__ off, int nsys)
 {
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nsys; s += gridDim.x * blockDim.x) {
@@ -298,10 +308,21 @@ __device__ __forceinline__ int lower_pos(const uint32_t *__restrict__ B, int nb,
 // For the cells [a, b) at level l: packed[c-a] = nchild | (split ? 1 << 32 : 0).
 __global__ void k_split_count(CellArrays c, const uint32_t *__restrict__ bpos,
                               const int *__restrict__ lstart, int a, int b, int level, int ncrit,
-                              int max_depth, int64_t *__restrict__ packed)
+                              int max_depth, int64_t *__restrict__ packed, const int *__restrict__ sz, int len)
 {
-    const int i = a + blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= b) return;
+    if (sz) {
+        a = sz[kSzLevel + level];
+        b = sz[kSzLevel + level + 1];
+    } else {
+        len = b - a;
+    }
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= len) return;
+    const int i = a + k;
+    if (i >= b) {
+        packed[k] = 0;  // past the level: nothing to split
+        return;
+    }
     const int cb = c.begin[i], ce = c.end[i];
     int64_t v = 0;
     if (ce - cb > ncrit && level < max_depth) {
@@ -319,18 +340,26 @@ __global__ void k_split_count(CellArrays c, const uint32_t *__restrict__ bpos,
 __global__ void k_split_emit(CellArrays c, const uint64_t *__restrict__ keys,
                              const uint32_t *__restrict__ bpos, const int *__restrict__ lstart,
                              int a, int b, int level, const int64_t *__restrict__ packed,
-                             const int64_t *__restrict__ ex, int tile_base)
+                             const int64_t *__restrict__ ex, int tile_base, const int *__restrict__ sz)
 {
+    int cend = INT_MAX;  // children must end before the next level's end
+    if (sz) {
+        a = sz[kSzLevel + level];
+        b = sz[kSzLevel + level + 1];
+        tile_base = sz[kSzTileBase + level];
+        cend = sz[kSzLevel + level + 2];
+    }
     const int i = a + blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= b) return;
     const int64_t v = packed[i - a];
-    if (v == 0) {
+    const int64_t e = ex[i - a];
+    const int first = b + (int)(e & 0xffffffffll);
+    if (v == 0 || first + (int)(v & 0xffffffffll) > cend) {
+        // a leaf (or, after a capacity overflow of a replayed plan, kept as one)
         c.child0[i] = -1;
         c.nchild[i] = 0;
         return;
     }
-    const int64_t e = ex[i - a];
-    const int first = b + (int)(e & 0xffffffffll);
     const int rank = (int)(e >> 32);
     const int window = rank / kTile, lane = rank % kTile;
     const int cb = c.begin[i], ce = c.end[i];
@@ -362,23 +391,51 @@ __global__ void k_split_emit(CellArrays c, const uint64_t *__restrict__ keys,
     c.nchild[i] = nch;
 }
 
-__global__ void k_fill_tile_cells(CellArrays c, int ncells, int *__restrict__ tile_cells)
+// Next level of a replayed plan: the children of level `level` start at the
+// level's end; the tiles of their windows follow the tiles so far.  Past a
+// capacity the level gets no children (its cells stay leaves) and kSzAbort is
+// set.  One thread.
+__global__ void k_level_advance(const int64_t *__restrict__ total, int level, int last_level, int cell_cap,
+                                int next_level_cap, int tile_cap, int *__restrict__ sz)
 {
+    const int b = sz[kSzLevel + level + 1];
+    const int64_t t = *total;
+    const int nch = (int)(t & 0xffffffffll), nsplit = (int)(t >> 32);
+    const int tiles = sz[kSzTiles] + 8 * (int)((nsplit + kTile - 1) / kTile);
+    sz[kSzTileBase + level] = sz[kSzTiles];
+    if (nch > 0 && (level >= last_level || nch > next_level_cap || b + nch > cell_cap || tiles > tile_cap)) {
+        sz[kSzAbort] = 1;
+        sz[kSzLevel + level + 2] = b;
+        return;
+    }
+    sz[kSzLevel + level + 2] = b + nch;
+    sz[kSzTiles] = tiles;
+    sz[kSzCells] = b + nch;
+}
+
+__global__ void k_fill_tile_cells(CellArrays c, int ncells, int *__restrict__ tile_cells, const int *__restrict__ sz)
+{
+    if (sz) ncells = sz[kSzCells];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ncells) return;
     tile_cells[(int64_t)c.tile[i] * kTile + c.lane[i]] = i;
 }
 
 // Compact list of leaf cells (order preserved) via a precomputed exclusive scan.
-__global__ void k_leaf_flags(CellArrays c, int ncells, int *__restrict__ flag)
+__global__ void k_leaf_flags(CellArrays c, int ncells, int *__restrict__ flag, const int *__restrict__ sz, int len)
 {
+    if (sz)
+        ncells = sz[kSzCells];
+    else
+        len = ncells;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < ncells) flag[i] = c.nchild[i] == 0;
+    if (i < len) flag[i] = i < ncells && c.nchild[i] == 0;
 }
 
 __global__ void k_leaf_compact(CellArrays c, int ncells, const int *__restrict__ ex,
-                               int *__restrict__ leaves)
+                               int *__restrict__ leaves, const int *__restrict__ sz)
 {
+    if (sz) ncells = sz[kSzCells];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < ncells && c.nchild[i] == 0) leaves[ex[i]] = i;
 }

@@ -31,7 +31,8 @@ ABI_SYMBOLS = ("fmm_default_options", "fmm_laplace3d", "fmm_laplace3d_ex", "fmm_
                "fmm_selection_table", "fmm_cost_model_train", "fmm_cost_model_get",
                "fmm_cost_model_set", "fmm_cost_model_grad", "fmm_cost_model_adam_step",
                "fmm_cost_model_predict", "fmm_cost_model_samples", "fmm_tune_ncrit",
-               "fmm_tune_schedule", "fmm_selftest_wait_timeout")
+               "fmm_tune_schedule", "fmm_selftest_wait_timeout", "fmm_plan_create", "fmm_plan_execute",
+               "fmm_plan_check", "fmm_plan_buffers", "fmm_plan_info", "fmm_plan_destroy")
 COST_MODEL_PARAMS = 4610
 
 
@@ -52,6 +53,19 @@ class CostModelInfo(ctypes.Structure):
                 ("steps", ctypes.c_int), ("loss_initial", ctypes.c_float),
                 ("loss_final", ctypes.c_float), ("agreement", ctypes.c_float),
                 ("ms_pretime", ctypes.c_float), ("ms_train", ctypes.c_float)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int64), ("nsys", ctypes.c_int), ("levels", ctypes.c_int),
+                ("cell_cap", ctypes.c_int64), ("tile_cap", ctypes.c_int64), ("class_cap", ctypes.c_int64),
+                ("entry_cap", ctypes.c_int64), ("unit_cap", ctypes.c_int64), ("m2l_cap", ctypes.c_int64),
+                ("p2p_cap", ctypes.c_int64), ("operators", ctypes.c_int64), ("graph_nodes", ctypes.c_int64),
+                ("graph_kernels", ctypes.c_int64), ("last_cells", ctypes.c_int64), ("last_leaves", ctypes.c_int64),
+                ("last_classes", ctypes.c_int64), ("last_entries", ctypes.c_int64), ("last_units", ctypes.c_int64),
+                ("last_valid", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -116,6 +130,18 @@ def load(path: str | None = None):
         L.fmm_tune_schedule.argtypes = [vp, vp, i64, vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, vp,
                                         ctypes.POINTER(Options), vp, ctypes.c_int, vp, ctypes.c_int, vp,
                                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+        L.fmm_plan_create.argtypes = [ctypes.POINTER(vp), vp, vp, i64, vp, ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_double, ctypes.c_int, ctypes.POINTER(Options), ctypes.c_double, vp]
+        L.fmm_plan_execute.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.fmm_plan_check.argtypes = [vp, vp]
+        L.fmm_plan_buffers.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                       ctypes.POINTER(vp)]
+        L.fmm_plan_info.argtypes = [vp, ctypes.POINTER(PlanInfo)]
+        L.fmm_plan_destroy.argtypes = [vp]
+        L.fmm_plan_destroy.restype = None
+        for name in ("fmm_plan_create", "fmm_plan_execute", "fmm_plan_check", "fmm_plan_buffers",
+                     "fmm_plan_info"):
+            getattr(L, name).restype = ctypes.c_int
         for name in ("fmm_laplace3d", "fmm_laplace3d_ex", "fmm_laplace3d_host", "fmm_direct",
                      "fmm_export", "fmm_laplace3d_batched", "fmm_selection_table",
                      "fmm_cost_model_train", "fmm_cost_model_get", "fmm_cost_model_set",
@@ -243,6 +269,88 @@ def laplace3d_batched(xyz, q, offsets, p: int, theta: float, ncrit: int, *, max_
                                             grad.data_ptr(), _stream_ptr(torch, xyz.device),
                                             ctypes.byref(o), ctypes.byref(st) if stats else None))
     return (phi, grad, st.as_dict()) if stats else (phi, grad)
+
+
+class Plan:
+    """A solve captured into one CUDA graph (fmm_plan_create): fixed N, systems,
+    p, theta, ncrit and options; replayed for new particle data with one graph
+    launch and no synchronisation.  ``check()`` tells whether the last replay
+    stayed within the plan's capacities (else its results are invalid)."""
+
+    def __init__(self, xyz, q, p: int, theta: float, ncrit: int, *, offsets=None, max_depth: int = 0,
+                 precision: str = "fp32", select="plain", m2l_unit_blocks: int = 0, headroom: float = 1.25):
+        import torch
+        n = int(xyz.shape[0])
+        xyz = _dev_f32(xyz, (n, 3), "xyz")
+        q = _dev_f32(q, (n,), "q")
+        self.n = n
+        self.device = xyz.device
+        off = None
+        nsys = 1
+        if offsets is not None:
+            off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+            nsys = len(off) - 1
+        self._off = off
+        o = _options(max_depth, precision, select, m2l_unit_blocks)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(load().fmm_plan_create(ctypes.byref(h), xyz.data_ptr(), q.data_ptr(), n,
+                                          off.ctypes.data if off is not None else None, nsys, p, float(theta),
+                                          ncrit, ctypes.byref(o), float(headroom), _stream_ptr(torch, self.device)))
+        self._h = h
+
+    def execute(self, xyz=None, q=None, out=None):
+        """Replays the plan on the current stream; xyz/q (CUDA float32) replace the
+        plan's inputs when given.  Returns (phi, grad) CUDA tensors (new tensors
+        unless ``out``); nothing is synchronised."""
+        import torch
+        n = self.n
+        xp = _dev_f32(xyz, (n, 3), "xyz").data_ptr() if xyz is not None else None
+        qp = _dev_f32(q, (n,), "q").data_ptr() if q is not None else None
+        with torch.cuda.device(self.device):
+            if out is None:
+                phi = torch.empty(n, device=self.device, dtype=torch.float32)
+                grad = torch.empty(n, 3, device=self.device, dtype=torch.float32)
+            else:
+                phi, grad = out
+            _check(load().fmm_plan_execute(self._h, xp, qp, phi.data_ptr(), grad.data_ptr(),
+                                           _stream_ptr(torch, self.device)))
+        return phi, grad
+
+    def execute_in_place(self):
+        """Replays the plan on its own buffers (see ``buffers``): no copies."""
+        import torch
+        with torch.cuda.device(self.device):
+            _check(load().fmm_plan_execute(self._h, None, None, None, None, _stream_ptr(torch, self.device)))
+
+    def buffers(self):
+        """Device pointers (ints) of the plan's xyz, q, phi and grad buffers."""
+        ptrs = [ctypes.c_void_p() for _ in range(4)]
+        _check(load().fmm_plan_buffers(self._h, *[ctypes.byref(x) for x in ptrs]))
+        return tuple(x.value for x in ptrs)
+
+    def check(self) -> int:
+        """Synchronises the current stream; returns the status of the last replay
+        (0 = valid, FMM_ERR_CAPACITY = it exceeded the plan)."""
+        import torch
+        with torch.cuda.device(self.device):
+            return load().fmm_plan_check(self._h, _stream_ptr(torch, self.device))
+
+    def info(self) -> dict:
+        inf = PlanInfo()
+        _check(load().fmm_plan_info(self._h, ctypes.byref(inf)))
+        return inf.as_dict()
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().fmm_plan_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def direct(xyz, q):

@@ -59,6 +59,7 @@ def parse():
                     help="pick ncrit and the M2L work-unit size with the measured autotuner before timing")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-graph", action="store_true", help="skip timing the captured plan (graph replay)")
     return ap.parse_args()
 
 
@@ -482,6 +483,38 @@ def main():
                                  "n_p2p_interactions": sts[-1]["n_p2p_interactions"],
                                  "accuracy": accuracy(x, q, phi.cpu().numpy(), grad.cpu().numpy(), off=off)}
 
+    # the same solve captured once into a CUDA graph (fmm_plan_create) and
+    # replayed: one graph launch per step, no host read-back, inputs copied into
+    # the plan and results out of it inside the timed region
+    graph = None
+    if rank == 0 and not args.no_graph:
+        plan = fmm.Plan(xd, qd, w["p"], w["theta"], w["ncrit"], offsets=off, headroom=1.25, **kw)
+        gphi = torch.empty_like(phi)
+        ggrad = torch.empty_like(grad)
+        for _ in range(2):
+            plan.execute(xd, qd, out=(gphi, ggrad))
+        ms = []
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            plan.execute(xd, qd, out=(gphi, ggrad))
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        status = plan.check()
+        solve()
+        torch.cuda.synchronize()
+        info = plan.info()
+        m = statistics.mean(ms)
+        graph = {"value": n / (m / 1e3), "ms_per_step": m, "valid": status == 0,
+                 "equal_to_plain_solve": bool(torch.equal(gphi, phi) and torch.equal(ggrad, grad)),
+                 "graph_kernels": info["graph_kernels"], "graph_nodes": info["graph_nodes"],
+                 "levels": info["levels"], "operators": info["operators"],
+                 "what": "fmm_plan_execute: the solve captured once into one CUDA graph, replayed with one "
+                         "graph launch per step (device-side sizes, capacities 1.25x the first solve)"}
+        plan.close()
+
     # a batch against solving its systems one call at a time
     loop = None
     if rank == 0 and off is not None:
@@ -521,6 +554,7 @@ def main():
                 "gpu_launches": int(sum(s["n_launches"] for s in st_list)),
                 "accuracy": acc, "m2l_modes": modes, "select_modes": select_modes,
                 "cost_model": cost_model, "ncrit_tuning": ncrit_tuning, "per_system_loop": loop,
+                "graph_replay": graph,
                 "clocks": clocks, "phases_ms": phases,
                 "counts": {k: st0[k] for k in ("ncells", "nleaves", "depth", "n_p2p_pairs",
                                                "n_p2p_interactions", "n_m2l_pairs",

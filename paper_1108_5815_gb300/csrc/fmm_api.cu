@@ -88,6 +88,8 @@ struct Workspace {
     // sizes of the last solve: a plan takes its capacities from them
     struct Shape {
         std::vector<int> lstart;  // first cell of each level, then the cell count
+        int64_t N = 0;
+        int nsys = 0, ncrit = 0, max_depth = 0;
         int ncells = 0, nleaves = 0, ntiles = 0, nclass = 0, nent = 0, nunits = 0, chunk = 8;
         int64_t tot[5] = {0, 0, 0, 0, 0};  // M2L, P2P, deferred, M2P, P2L pairs
     } shape;
@@ -365,7 +367,15 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
     FMM_LAUNCH_CHECK();
 
     // ---------------------------------------------------------- tree
+    // When the previous solve had the same N, systems, ncrit and depth limit, its
+    // level sizes (+50 %) serve as capacities: the levels are built with their
+    // ranges kept on the device and the tree is read back once.  A tree that
+    // outgrows them is rebuilt level by level with one read-back per level.
+    const Workspace::Shape prev = ws.shape;
+    const bool fast_tree = !prev.lstart.empty() && prev.N == N && prev.nsys == nsys && prev.ncrit == ncrit &&
+                           prev.max_depth == max_depth;
     int cell_cap = std::max(1024, N / 8 + 64 + nsys);
+    if (fast_tree) cell_cap = std::max<int64_t>(cell_cap, (int64_t)prev.ncells + prev.ncells / 2 + 1024 + nsys);
     auto cells = [&](int cap, bool keep) {
         CellArrays c;
         c.level = need<int>(ws, "c_level", cap, st, keep);
@@ -394,40 +404,97 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
     }
     k_level_starts<<<1, 32, 0, st>>>(blvl, N - 1, bstart);
     FMM_LAUNCH_CHECK();
-    std::vector<int> lstart = {0, nsys};
-    int tiles_total = (int)ceil_div(nsys, kTile);  // the roots' tiles
-    int64_t *i64_tmp = need<int64_t>(ws, "scan_i64", scan_temp_elems(std::max(N, 1 << 16)), st);
-    for (int l = 0;; ++l) {
-        const int a = lstart[l], b = lstart[l + 1];
-        const int nl = b - a;
-        if (nl == 0) break;
-        int64_t *packed = need<int64_t>(ws, "packed", nl, st);
-        int64_t *packed_ex = need<int64_t>(ws, "packed_ex", nl + 1, st);
-        i64_tmp = need<int64_t>(ws, "scan_i64", scan_temp_elems(nl), st);
-        k_split_count<<<(unsigned)ceil_div(nl, 128), 128, 0, st>>>(c, bpos, bstart, a, b, l, ncrit,
-                                                                  max_depth, packed);
-        FMM_LAUNCH_CHECK();
-        scan_exclusive<int64_t>(packed, packed_ex, nl, packed_ex + nl, i64_tmp, st);
-        int64_t total = 0;
-        sync_point(ws, st, flags, {{packed_ex + nl, sizeof(int64_t)}}, &total);
-        const int nch = (int)(total & 0xffffffffll);
-        const int nsplit = (int)(total >> 32);
-        if (nch == 0) break;
-        if (b + nch > cell_cap) {
-            cell_cap = std::max(b + nch, cell_cap + cell_cap / 2);
-            c = cells(cell_cap, true);
+    std::vector<int> lstart;
+    int tiles_total = 0;
+    int nleaves = 0;
+    int *leaves = nullptr;
+    bool tree_done = false;
+    if (fast_tree) {
+        const int pdepth = (int)prev.lstart.size() - 2;
+        const int levels = std::min(pdepth + 1, max_depth);
+        std::vector<int> cap(levels + 2, 0);
+        for (int l = 0; l <= levels; ++l) {
+            const int ll = std::min(l, pdepth);
+            const int64_t cnt = prev.lstart[ll + 1] - prev.lstart[ll];
+            cap[l] = (int)std::min<int64_t>(cnt + cnt / 2 + 256, cell_cap);
         }
-        k_split_emit<<<(unsigned)ceil_div(nl, 128), 128, 0, st>>>(c, keys, bpos, bstart, a, b, l, packed,
-                                                                 packed_ex, tiles_total);
+        const int maxcap = *std::max_element(cap.begin(), cap.end());
+        int *sz = need<int>(ws, "tree_sz", kSzWords, st);
+        int64_t *packed = need<int64_t>(ws, "packed", maxcap + 1, st);
+        int64_t *packed_ex = need<int64_t>(ws, "packed_ex", maxcap + 1, st);
+        int64_t *i64_tmp = need<int64_t>(ws, "scan_i64", scan_temp_elems(std::max(maxcap, 1 << 16)), st);
+        k_plan_init<<<1, 64, 0, st>>>(sz, nsys);
         FMM_LAUNCH_CHECK();
-        tiles_total += 8 * (int)ceil_div(nsplit, kTile);
-        lstart.push_back(b + nch);
+        for (int l = 0; l <= levels; ++l) {
+            const int len = cap[l];
+            k_split_count<<<(unsigned)ceil_div(len, 128), 128, 0, st>>>(c, bpos, bstart, 0, 0, l, ncrit, max_depth,
+                                                                       packed, sz, len);
+            FMM_LAUNCH_CHECK();
+            scan_exclusive<int64_t>(packed, packed_ex, len, packed_ex + len, i64_tmp, st);
+            k_level_advance<<<1, 1, 0, st>>>(packed_ex + len, l, levels, cell_cap, cap[l + 1], INT_MAX, sz);
+            FMM_LAUNCH_CHECK();
+            k_split_emit<<<(unsigned)ceil_div(len, 128), 128, 0, st>>>(c, keys, bpos, bstart, 0, 0, l, packed,
+                                                                      packed_ex, 0, sz);
+            FMM_LAUNCH_CHECK();
+        }
+        int *lflag = need<int>(ws, "leaf_flag", cell_cap, st);
+        int *lex = need<int>(ws, "leaf_ex", cell_cap + 1, st);
+        int *i32_tmp = need<int>(ws, "scan_i32", scan_temp_elems(cell_cap), st);
+        leaves = need<int>(ws, "leaves", cell_cap, st);
+        k_leaf_flags<<<(unsigned)ceil_div(cell_cap, 256), 256, 0, st>>>(c, 0, lflag, sz, cell_cap);
+        FMM_LAUNCH_CHECK();
+        scan_exclusive<int>(lflag, lex, cell_cap, lex + cell_cap, i32_tmp, st);
+        k_leaf_compact<<<(unsigned)ceil_div(cell_cap, 256), 256, 0, st>>>(c, 0, lex, leaves, sz);
+        FMM_LAUNCH_CHECK();
+        FMM_CUDA_TRY(cudaMemcpyAsync(sz + kSzLeaves, lex + cell_cap, sizeof(int), cudaMemcpyDeviceToDevice, st));
+        int hsz[kSzWords];
+        sync_point(ws, st, flags, {{sz, sizeof(hsz)}}, hsz);
+        if (!hsz[kSzAbort]) {
+            lstart.push_back(hsz[kSzLevel]);
+            for (int l = 0; l <= levels && hsz[kSzLevel + l + 1] > hsz[kSzLevel + l]; ++l)
+                lstart.push_back(hsz[kSzLevel + l + 1]);
+            tiles_total = hsz[kSzTiles];
+            nleaves = hsz[kSzLeaves];
+            tree_done = true;
+        } else {
+            k_init_roots<<<(unsigned)ceil_div(nsys, 256), 256, 0, st>>>(c, sys_off, nsys);
+            FMM_LAUNCH_CHECK();
+        }
+    }
+    if (!tree_done) {
+        lstart = {0, nsys};
+        tiles_total = (int)ceil_div(nsys, kTile);  // the roots' tiles
+        int64_t *i64_tmp = need<int64_t>(ws, "scan_i64", scan_temp_elems(std::max(N, 1 << 16)), st);
+        for (int l = 0;; ++l) {
+            const int a = lstart[l], b = lstart[l + 1];
+            const int nl = b - a;
+            if (nl == 0) break;
+            int64_t *packed = need<int64_t>(ws, "packed", nl, st);
+            int64_t *packed_ex = need<int64_t>(ws, "packed_ex", nl + 1, st);
+            i64_tmp = need<int64_t>(ws, "scan_i64", scan_temp_elems(nl), st);
+            k_split_count<<<(unsigned)ceil_div(nl, 128), 128, 0, st>>>(c, bpos, bstart, a, b, l, ncrit,
+                                                                      max_depth, packed);
+            FMM_LAUNCH_CHECK();
+            scan_exclusive<int64_t>(packed, packed_ex, nl, packed_ex + nl, i64_tmp, st);
+            int64_t total = 0;
+            sync_point(ws, st, flags, {{packed_ex + nl, sizeof(int64_t)}}, &total);
+            const int nch = (int)(total & 0xffffffffll);
+            const int nsplit = (int)(total >> 32);
+            if (nch == 0) break;
+            if (b + nch > cell_cap) {
+                cell_cap = std::max(b + nch, cell_cap + cell_cap / 2);
+                c = cells(cell_cap, true);
+            }
+            k_split_emit<<<(unsigned)ceil_div(nl, 128), 128, 0, st>>>(c, keys, bpos, bstart, a, b, l, packed,
+                                                                     packed_ex, tiles_total);
+            FMM_LAUNCH_CHECK();
+            tiles_total += 8 * (int)ceil_div(nsplit, kTile);
+            lstart.push_back(b + nch);
+        }
     }
     const int depth = (int)lstart.size() - 2;
     const int ncells = lstart.back();
-    int nleaves = 0;
-    int *leaves;
-    {
+    if (!tree_done) {
         int *lflag = need<int>(ws, "leaf_flag", ncells, st);
         int *lex = need<int>(ws, "leaf_ex", ncells + 1, st);
         int *i32_tmp = need<int>(ws, "scan_i32", scan_temp_elems(ncells), st);
@@ -441,6 +508,10 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
     }
     ev.rec(1, st);
     ws.shape.lstart = lstart;
+    ws.shape.N = N;
+    ws.shape.nsys = nsys;
+    ws.shape.ncrit = ncrit;
+    ws.shape.max_depth = max_depth;
     ws.shape.ncells = ncells;
     ws.shape.nleaves = nleaves;
 

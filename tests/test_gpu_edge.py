@@ -130,3 +130,24 @@ def test_bounded_wait_reports_timeout_and_context_survives():
     f = O.Fmm(x, q, 4, 0.5, 32)
     ophi, ograd = f.evaluate()
     assert rel_l2(phi, ophi) < 1e-5
+
+
+def test_tree_read_back_once_when_sizes_repeat():
+    # a solve of the same N, ncrit and depth limit as the previous one builds the
+    # tree with the level ranges on the device (one read-back); the result equals
+    # the level-by-level build of the first solve bit for bit
+    from paper_1108_5815_gb300 import fmm
+    torch = torch_cuda()
+    x0, q0 = inputs.uniform_cube(1500, 90)
+    gpu_solve(x0, q0, 5, 0.5, 16)  # another N first: the next solve builds level by level
+    x, q = inputs.uniform_cube(40000, 91)
+    xt, qt = torch.from_numpy(x).cuda(), torch.from_numpy(q).cuda()
+    first = [t.cpu().numpy() for t in fmm.laplace3d(xt, qt, 6, 0.5, 32)]
+    again = [t.cpu().numpy() for t in fmm.laplace3d(xt, qt, 6, 0.5, 32)]
+    assert np.array_equal(first[0], again[0]) and np.array_equal(first[1], again[1])
+    # same N, far deeper tree: the capacities of the previous solve do not hold, the
+    # tree is rebuilt level by level, and the result still matches the oracle
+    xp, qp = inputs.plummer(40000, 92, equal_charges=False)
+    phi, grad = gpu_solve(xp, qp, 6, 0.5, 32)
+    ophi, ograd = O.Fmm(xp, qp, 6, 0.5, 32).evaluate()
+    assert rel_l2(phi, ophi) < 1e-5 and rel_l2(grad, ograd) < 1e-5

@@ -247,6 +247,30 @@ def hot_kernel_rooflines(st, ms_p2p, ms_m2l, p, precision):
     return out
 
 
+def tree_roofline(n, ms_tree):
+    """The tree build (box, keys, radix sort, permute, level splits) against HBM.
+
+    Algorithmic bytes per particle: 16 read (x, y, z, q) + 16 permuted write +
+    12 key/index write, plus 24 per 8-bit radix pass (8 passes over 63-bit keys).
+    The phase time includes every launch of the phase; it is a phase, not one kernel."""
+    hbm, _, label = measured_peaks()
+    bytes_ = n * (16 + 16 + 12 + 24 * 8)
+    gbs = bytes_ / (ms_tree * 1e-3) / 1e9
+    return {"kernel": "tree build phase", "phase": True, "bound": "hbm", "achieved": gbs, "peak": hbm,
+            "unit": "GB/s", "frac": gbs / hbm, "traffic": None, "ms": ms_tree,
+            "peak_source": f"STREAM-style copy {label}",
+            "work": f"{n} particles x 236 B (16 read + 16 permuted write + 12 key/index + 8 radix passes x 24)"}
+
+
+def solve_roofline_fraction(rooflines, ms_solve):
+    """Sum over the measured steps of (algorithmic work / that step's peak) over the
+    solve time: the share of the solve the hardware bounds alone would need."""
+    terms = {}
+    for r in rooflines:
+        terms[r["kernel"]] = r["ms"] * r["frac"]  # work / peak, in ms
+    return {"value": sum(terms.values()) / ms_solve, "bound_ms": terms, "solve_ms": ms_solve}
+
+
 # ------------------------------------------------------------------ clocks
 
 class ClockSampler:
@@ -388,7 +412,9 @@ def main():
     ms_p2p = statistics.mean(s["ms_p2p"] for s in st_list)
     ms_m2l = statistics.mean(s["ms_m2l"] for s in st_list)
     rooflines = hot_kernel_rooflines(st0, ms_p2p, ms_m2l, w["p"], args.precision)
-    roof = max(rooflines, key=lambda r: r["ms"])
+    roof = max(rooflines, key=lambda r: r["ms"])  # the dominant kernel
+    rooflines.append(tree_roofline(n, statistics.mean(s["ms_tree"] for s in st_list)))
+    solve_frac = solve_roofline_fraction(rooflines, ms_per_step)
     phases = {k: round(statistics.mean(s[k] for s in st_list), 4)
               for k in ("ms_tree", "ms_traverse", "ms_upward", "ms_m2l", "ms_downward", "ms_p2p",
                         "ms_total")}
@@ -554,7 +580,7 @@ def main():
                 "gpu_launches": int(sum(s["n_launches"] for s in st_list)),
                 "accuracy": acc, "m2l_modes": modes, "select_modes": select_modes,
                 "cost_model": cost_model, "ncrit_tuning": ncrit_tuning, "per_system_loop": loop,
-                "graph_replay": graph,
+                "graph_replay": graph, "solve_roofline_fraction": solve_frac,
                 "clocks": clocks, "phases_ms": phases,
                 "counts": {k: st0[k] for k in ("ncells", "nleaves", "depth", "n_p2p_pairs",
                                                "n_p2p_interactions", "n_m2l_pairs",

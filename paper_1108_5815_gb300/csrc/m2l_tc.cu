@@ -399,6 +399,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
             const uint32_t idesc = instr_desc(BF16 ? 1u : 2u, (uint32_t)N);
+            // N <= 128: B_hi and B_lo of a stage are one 2N-row operand (same layout,
+            // consecutive), and the main and correction accumulators are adjacent, so
+            // one MMA of width 2N gives ah.bh and ah.bl together, reading ah once.
+            constexpr bool kFuse = 2 * N <= 256;
+            const uint32_t idesc2 = instr_desc(BF16 ? 1u : 2u, kFuse ? 2u * N : (uint32_t)N);
             constexpr int ksteps = (int)RB / 32;  // MMAs of 32 bytes of K per stage row
             bool ok = true;
             int g = 0;
@@ -424,9 +429,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                     for (int k = 0; k < ksteps; ++k) {
                         const uint32_t off = (uint32_t)k * 256u;  // two core matrices along K
                         const uint32_t acc0 = (kc > 0 || k > 0) ? 1u : 0u;
-                        mma<BF16>(dcorr, smem_desc(al + off, SBO), smem_desc(bh + off, SBO), idesc, acc0);
-                        mma<BF16>(dcorr, smem_desc(ah + off, SBO), smem_desc(bl + off, SBO), idesc, 1u);
-                        mma<BF16>(dmain, smem_desc(ah + off, SBO), smem_desc(bh + off, SBO), idesc, acc0);
+                        if (kFuse) {
+                            mma<BF16>(dmain, smem_desc(ah + off, SBO), smem_desc(bh + off, SBO), idesc2, acc0);
+                            mma<BF16>(dcorr, smem_desc(al + off, SBO), smem_desc(bh + off, SBO), idesc, 1u);
+                        } else {
+                            mma<BF16>(dcorr, smem_desc(al + off, SBO), smem_desc(bh + off, SBO), idesc, acc0);
+                            mma<BF16>(dcorr, smem_desc(ah + off, SBO), smem_desc(bl + off, SBO), idesc, 1u);
+                            mma<BF16>(dmain, smem_desc(ah + off, SBO), smem_desc(bh + off, SBO), idesc, acc0);
+                        }
                     }
                     mma_commit(&empty[s]);
                 }

@@ -293,7 +293,7 @@ fmm_status fmm_cost_model_samples(float *x, float *t, float *m, int64_t capacity
  *   box   device double [4]  out: lo_x, lo_y, lo_z, side of the cubic box
  * Results equal FMM_EXPORT_KEYS / FMM_EXPORT_ORDER / FMM_EXPORT_BOX of a
  * solve on the same points.  A NaN/Inf coordinate gives FMM_ERR_NONFINITE.
- * The scratch array (12,846,336 bytes) exists on every device that loads the
+ * The scratch array (16,786,176 bytes) exists on every device that loads the
  * library until the process exits.  The first call on a device resolves its
  * address with cudaGetSymbolAddress; make that first call before any stream
  * capture.  All calls share the array, so calls whose GPU work overlaps (on

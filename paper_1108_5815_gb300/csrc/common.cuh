@@ -103,11 +103,20 @@ int64_t scan_temp_elems(int64_t n);
 
 // ---------------------------------------------------------------- radix sort
 
-// Stable LSD radix sort of (key, value) pairs by the low `bits` bits of the key.
-// keys/vals are sorted in place (alt buffers are scratch of the same size).
-// hist must hold radix_hist_elems(n) uint32 values; scan_tmp scan_temp_elems of that.
+// Stable LSD radix sort of (key, value) pairs by the low `bits` bits of the key
+// (8-bit digits).  keys/vals are sorted in place (alt buffers are scratch of the
+// same size).  scratch must hold radix_scratch_elems(n) uint32 values.  flags
+// (nullable) receives kFlagTimeout if a bounded wait of the look-back expires.
+constexpr int kRadixTile = 4096;     // keys per block
+constexpr int kRadixMaxPasses = 8;   // 64-bit keys
+constexpr int64_t radix_scratch_elems(int64_t n)
+{
+    // digit counts of every pass, tile counters, then per pass and tile 256
+    // 64-bit look-back words
+    return (int64_t)kRadixMaxPasses * 256 + 64 +
+           (int64_t)kRadixMaxPasses * 256 * 2 * ((n + kRadixTile - 1) / kRadixTile);
+}
 void radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt,
-                      int64_t n, int bits, uint32_t *hist, uint32_t *scan_tmp, cudaStream_t st);
-int64_t radix_hist_elems(int64_t n);
+                      int64_t n, int bits, uint32_t *scratch, int *flags, cudaStream_t st);
 
 }  // namespace fmm

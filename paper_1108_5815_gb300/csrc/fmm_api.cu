@@ -328,9 +328,8 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
     uint64_t *keys_alt = need<uint64_t>(ws, "keys_alt", N, st);
     uint32_t *idx = need<uint32_t>(ws, "idx", N, st);
     uint32_t *idx_alt = need<uint32_t>(ws, "idx_alt", N, st);
-    const int64_t nh = radix_hist_elems(N);
+    const int64_t nh = radix_scratch_elems(N);
     uint32_t *hist = need<uint32_t>(ws, "hist", nh, st);
-    uint32_t *tmp_u32 = need<uint32_t>(ws, "scan_u32", scan_temp_elems(nh), st);
     float4 *pts = need<float4>(ws, "pts", N, st);
     {
         std::vector<int> off32(nsys + 1);
@@ -348,18 +347,18 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
     k_morton<<<grid_for(N, 256), 256, 0, st>>>(xyz, N, sys_off, nsys, bbox_u, box, keys, idx);
     FMM_LAUNCH_CHECK();
     if (nsys == 1) {
-        radix_sort_pairs(keys, idx, keys_alt, idx_alt, N, 63, hist, tmp_u32, st);
+        radix_sort_pairs(keys, idx, keys_alt, idx_alt, N, 63, hist, flags, st);
     } else {
         // sort by key, then stably by system; the keys follow the permutation
         uint64_t *keys_orig = need<uint64_t>(ws, "keys_orig", N, st);
         uint64_t *sys_key = need<uint64_t>(ws, "sys_key", N, st);
         FMM_CUDA_TRY(cudaMemcpyAsync(keys_orig, keys, sizeof(uint64_t) * N, cudaMemcpyDeviceToDevice, st));
-        radix_sort_pairs(keys, idx, keys_alt, idx_alt, N, 63, hist, tmp_u32, st);
+        radix_sort_pairs(keys, idx, keys_alt, idx_alt, N, 63, hist, flags, st);
         k_sys_of_sorted<<<grid_for(N, 256), 256, 0, st>>>(idx, N, sys_off, nsys, sys_key);
         FMM_LAUNCH_CHECK();
         int bits = 1;
         while ((1 << bits) < nsys) ++bits;
-        radix_sort_pairs(sys_key, idx, keys_alt, idx_alt, N, bits, hist, tmp_u32, st);
+        radix_sort_pairs(sys_key, idx, keys_alt, idx_alt, N, bits, hist, flags, st);
         k_gather_keys<<<grid_for(N, 256), 256, 0, st>>>(keys_orig, idx, N, keys);
         FMM_LAUNCH_CHECK();
     }
@@ -400,7 +399,7 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
     if (N > 1) {
         k_first_diff<<<grid_for(N, 256), 256, 0, st>>>(keys, N, blvl, bpos);
         FMM_LAUNCH_CHECK();
-        radix_sort_pairs(blvl, bpos, keys_alt, idx_alt, N - 1, 8, hist, tmp_u32, st);
+        radix_sort_pairs(blvl, bpos, keys_alt, idx_alt, N - 1, 8, hist, flags, st);
     }
     k_level_starts<<<1, 32, 0, st>>>(blvl, N - 1, bstart);
     FMM_LAUNCH_CHECK();
@@ -655,10 +654,9 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
             FMM_LAUNCH_CHECK();
             std::swap(ukeys, ukeys_alt);
         } else if (nclass > 0) {
-            const int64_t nh2 = radix_hist_elems(nclass);
+            const int64_t nh2 = radix_scratch_elems(nclass);
             uint32_t *h2 = need<uint32_t>(ws, "hist", std::max(nh, nh2), fs);
-            uint32_t *t2 = need<uint32_t>(ws, "scan_u32", scan_temp_elems(std::max(nh, nh2)), fs);
-            radix_sort_pairs(ukeys, uslot, ukeys_alt, uslot_alt, nclass, 64, h2, t2, fs);
+            radix_sort_pairs(ukeys, uslot, ukeys_alt, uslot_alt, nclass, 64, h2, flags, fs);
             k_slot_to_class<<<(unsigned)ceil_div(nclass, 256), 256, 0, fs>>>(uslot, nclass, slot_class);
             FMM_LAUNCH_CHECK();
         }
@@ -1176,9 +1174,7 @@ void build_plan(fmm_plan &pl, Workspace &ws, const int64_t *offsets, const uint8
         b.keys_orig = m.get<uint64_t>(N);
         b.sys_key = m.get<uint64_t>(N);
     }
-    const int64_t nh = radix_hist_elems(N);
-    b.hist = m.get<uint32_t>(nh);
-    b.scan_u32 = m.get<uint32_t>(scan_temp_elems(nh));
+    b.hist = m.get<uint32_t>(radix_scratch_elems(N));
     b.pts = m.get<float4>(N);
     b.c.level = m.get<int>(cc);
     b.c.prefix = m.get<uint64_t>(cc);

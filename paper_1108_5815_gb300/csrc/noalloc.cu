@@ -10,8 +10,8 @@
 // radix sort -- with every scratch array inside one fixed, file-scope device
 // array.  The caller passes the inputs and the output buffers.
 //
-// The scratch holds the sort's second key/index buffers, digit histograms,
-// scan temporaries, the box and the flags for up to kNoAllocMaxN points.  It is
+// The scratch holds the sort's second key/index buffers, digit counts and
+// look-back words, the box and the flags for up to kNoAllocMaxN points.  It is
 // resolved to a device address with cudaGetSymbolAddress once per device, on
 // that device's first call.  All calls share it and it keeps the previous
 // call's contents; everything that must start at zero is cleared on every call.
@@ -29,12 +29,11 @@ constexpr int64_t kNoAllocMaxN = int64_t(1) << 20;
 
 // Byte layout of the scratch array (each part 256-byte aligned).
 constexpr size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
-constexpr int64_t kHistElems = 256 * ((kNoAllocMaxN + 4095) / 4096) + 1;
+constexpr int64_t kHistElems = radix_scratch_elems(kNoAllocMaxN);
 constexpr size_t kOffKeysAlt = 0;
 constexpr size_t kOffIdxAlt = align256(kOffKeysAlt + sizeof(uint64_t) * kNoAllocMaxN);
 constexpr size_t kOffHist = align256(kOffIdxAlt + sizeof(uint32_t) * kNoAllocMaxN);
-constexpr size_t kOffScan = align256(kOffHist + sizeof(uint32_t) * kHistElems);
-constexpr size_t kOffBbox = align256(kOffScan + sizeof(uint32_t) * (2 * ((kHistElems + 2047) / 2048) + 2));
+constexpr size_t kOffBbox = align256(kOffHist + sizeof(uint32_t) * kHistElems);
 constexpr size_t kOffFlags = align256(kOffBbox + sizeof(uint32_t) * 6);
 constexpr size_t kScratchBytes = align256(kOffFlags + sizeof(int) * kNumFlags);
 
@@ -79,7 +78,6 @@ extern "C" fmm_status fmm_morton_sort_noalloc(const float *xyz, int64_t N, uint6
         uint64_t *keys_alt = reinterpret_cast<uint64_t *>(s + kOffKeysAlt);
         uint32_t *idx_alt = reinterpret_cast<uint32_t *>(s + kOffIdxAlt);
         uint32_t *hist = reinterpret_cast<uint32_t *>(s + kOffHist);
-        uint32_t *scan = reinterpret_cast<uint32_t *>(s + kOffScan);
         uint32_t *bbox_u = reinterpret_cast<uint32_t *>(s + kOffBbox);
         int *flags = reinterpret_cast<int *>(s + kOffFlags);
         uint32_t *idx = reinterpret_cast<uint32_t *>(order);
@@ -91,11 +89,12 @@ extern "C" fmm_status fmm_morton_sort_noalloc(const float *xyz, int64_t N, uint6
         FMM_LAUNCH_CHECK();
         k_morton<<<grid, 256, 0, st>>>(xyz, N, nullptr, 1, bbox_u, box, keys, idx);
         FMM_LAUNCH_CHECK();
-        radix_sort_pairs(keys, idx, keys_alt, idx_alt, N, 63, hist, scan, st);
+        radix_sort_pairs(keys, idx, keys_alt, idx_alt, N, 63, hist, flags, st);
         int hflags[kNumFlags];
         FMM_CUDA_TRY(cudaMemcpyAsync(hflags, flags, sizeof(hflags), cudaMemcpyDeviceToHost, st));
         FMM_CUDA_TRY(cudaStreamSynchronize(st));
         if (hflags[kFlagNonfinite]) throw Error{FMM_ERR_NONFINITE, "a coordinate is NaN or infinite"};
+        if (hflags[kFlagTimeout]) throw Error{FMM_ERR_TIMEOUT, "a bounded device-side wait expired (radix sort)"};
         set_last_error("");
         return FMM_OK;
     } catch (const Error &e) {

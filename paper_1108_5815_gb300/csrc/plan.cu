@@ -54,13 +54,13 @@ void enqueue_plan(const PlanShape &s, const PlanBuffers &b, cudaStream_t st, cud
     k_morton<<<grid_stride(N), 256, 0, st>>>(b.xyz, N, b.sys_off, nsys, b.bbox_u, b.box, b.keys, b.idx);
     FMM_LAUNCH_CHECK();
     if (nsys == 1) {
-        radix_sort_pairs(b.keys, b.idx, b.keys_alt, b.idx_alt, N, 63, b.hist, b.scan_u32, st);
+        radix_sort_pairs(b.keys, b.idx, b.keys_alt, b.idx_alt, N, 63, b.hist, b.flags, st);
     } else {
         FMM_CUDA_TRY(cudaMemcpyAsync(b.keys_orig, b.keys, sizeof(uint64_t) * N, cudaMemcpyDeviceToDevice, st));
-        radix_sort_pairs(b.keys, b.idx, b.keys_alt, b.idx_alt, N, 63, b.hist, b.scan_u32, st);
+        radix_sort_pairs(b.keys, b.idx, b.keys_alt, b.idx_alt, N, 63, b.hist, b.flags, st);
         k_sys_of_sorted<<<grid_stride(N), 256, 0, st>>>(b.idx, N, b.sys_off, nsys, b.sys_key);
         FMM_LAUNCH_CHECK();
-        radix_sort_pairs(b.sys_key, b.idx, b.keys_alt, b.idx_alt, N, s.sys_bits, b.hist, b.scan_u32, st);
+        radix_sort_pairs(b.sys_key, b.idx, b.keys_alt, b.idx_alt, N, s.sys_bits, b.hist, b.flags, st);
         k_gather_keys<<<grid_stride(N), 256, 0, st>>>(b.keys_orig, b.idx, N, b.keys);
         FMM_LAUNCH_CHECK();
     }
@@ -73,7 +73,7 @@ void enqueue_plan(const PlanShape &s, const PlanBuffers &b, cudaStream_t st, cud
     if (N > 1) {
         k_first_diff<<<grid_stride(N), 256, 0, st>>>(b.keys, N, b.blvl, b.bpos);
         FMM_LAUNCH_CHECK();
-        radix_sort_pairs(b.blvl, b.bpos, b.keys_alt, b.idx_alt, N - 1, 8, b.hist, b.scan_u32, st);
+        radix_sort_pairs(b.blvl, b.bpos, b.keys_alt, b.idx_alt, N - 1, 8, b.hist, b.flags, st);
     }
     k_level_starts<<<1, 32, 0, st>>>(b.blvl, N - 1, b.bstart);
     FMM_LAUNCH_CHECK();

@@ -41,7 +41,7 @@ struct PlanBuffers {
     double *box = nullptr;
     int *sys_off = nullptr;
     uint64_t *keys = nullptr, *keys_alt = nullptr, *keys_orig = nullptr, *sys_key = nullptr;
-    uint32_t *idx = nullptr, *idx_alt = nullptr, *hist = nullptr, *scan_u32 = nullptr;
+    uint32_t *idx = nullptr, *idx_alt = nullptr, *hist = nullptr;  // hist: the radix sort scratch
     float4 *pts = nullptr;
     CellArrays c{};
     uint64_t *blvl = nullptr;

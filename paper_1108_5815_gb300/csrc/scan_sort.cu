@@ -5,7 +5,10 @@
 // in the dual tree traversal.  Written for coalesced HBM access: each block
 // owns a contiguous tile, and the radix scatter reorders a whole tile in shared
 // memory first so that each digit's run is written contiguously.
+#include <algorithm>
+
 #include "common.cuh"
+#include "kernels.cuh"
 
 namespace fmm {
 
@@ -153,37 +156,52 @@ template void scan_exclusive<int64_t>(const int64_t *, int64_t *, int64_t, int64
                                       cudaStream_t);
 
 // ---------------------------------------------------------------- radix sort
+//
+// One kernel per 8-bit digit (a one-sweep LSD sort, after Adinets & Merrill,
+// "Onesweep", 2022): the digit counts of every pass come from one read of the
+// keys before the first pass; in a pass each block takes the next tile of 4096
+// keys from a counter, ranks them stably in shared memory, publishes its
+// per-digit counts, and adds the counts of the tiles before it by looking back
+// over their published words (a tile that has finished its own look-back
+// publishes its inclusive prefix, which ends the walk).  Blocks take tiles in
+// the order they start, so every tile a block waits for belongs to a block
+// that has started and never waits for a later tile; each wait is bounded
+// anyway and reports kFlagTimeout if it runs out.
 
 namespace {
 
 constexpr int kSortThreads = 256;
-constexpr int kSortItems = 16;
-constexpr int kSortTile = kSortThreads * kSortItems;  // 4096 keys per block
+constexpr int kSortItems = kRadixTile / kSortThreads;  // 16
+constexpr int kSortTile = kRadixTile;
 constexpr int kRadix = 256;
+constexpr uint64_t kLbAggregate = 1ull << 62;  // look-back word: tile count only
+constexpr uint64_t kLbInclusive = 2ull << 62;  // look-back word: prefix through this tile
+constexpr uint32_t kLookbackPolls = 1u << 20;
 
-__global__ void k_radix_hist(const uint64_t *__restrict__ keys, int64_t n, int shift,
-                             uint32_t *__restrict__ hist, int ntiles)
+// Digit counts of passes 0 .. passes-1 over all keys (counts[pass][digit], zeroed).
+__global__ void __launch_bounds__(256)
+    k_radix_counts(const uint64_t *__restrict__ keys, int64_t n, int passes, uint32_t *__restrict__ counts)
 {
-    __shared__ uint32_t h[kRadix];
-    h[threadIdx.x] = 0;
+    __shared__ uint32_t h[kRadixMaxPasses * kRadix];
+    for (int i = threadIdx.x; i < passes * kRadix; i += blockDim.x) h[i] = 0;
     __syncthreads();
-    const int64_t base = (int64_t)blockIdx.x * kSortTile;
-#pragma unroll 4
-    for (int i = 0; i < kSortItems; ++i) {
-        int64_t idx = base + (int64_t)i * kSortThreads + threadIdx.x;
-        if (idx < n) atomicAdd(&h[(keys[idx] >> shift) & 0xff], 1u);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t k = keys[i];
+        for (int p = 0; p < passes; ++p) atomicAdd(&h[p * kRadix + ((k >> (8 * p)) & 0xff)], 1u);
     }
     __syncthreads();
-    // digit-major layout: all tiles of digit 0, then digit 1, ...
-    hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+    for (int i = threadIdx.x; i < passes * kRadix; i += blockDim.x)
+        if (h[i]) atomicAdd(&counts[i], h[i]);
 }
 
-// Stable scatter of one tile: ranks keys within the tile (index order), reorders
-// the tile in shared memory by digit, then writes each digit run contiguously.
+// One pass: stable scatter of one tile by the digit at `shift`.  The tile is
+// ranked (index order), reordered in shared memory by digit, and each digit's
+// run is written contiguously at the digit's global start plus the keys of that
+// digit in earlier tiles.
 __global__ void __launch_bounds__(kSortThreads)
-    k_radix_scatter(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
-                    uint64_t *__restrict__ kout, uint32_t *__restrict__ vout, int64_t n, int shift,
-                    const uint32_t *__restrict__ offs, int ntiles)
+    k_radix_pass(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint64_t *__restrict__ kout,
+                 uint32_t *__restrict__ vout, int64_t n, int shift, const uint32_t *__restrict__ counts,
+                 unsigned long long *status, int *tile_counter, int *flags)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     uint64_t *sk = reinterpret_cast<uint64_t *>(smem_raw);                 // kSortTile keys
@@ -193,12 +211,17 @@ __global__ void __launch_bounds__(kSortThreads)
     uint32_t *tile_off = run + kRadix;                                     // [256]
     uint32_t *gbase = tile_off + kRadix;                                   // [256]
     uint32_t *sw = gbase + kRadix;                                         // [33] scan scratch
+    __shared__ int s_tile;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t base = (int64_t)blockIdx.x * kSortTile;
-    const int tile_n = (int)(n - base < (int64_t)kSortTile ? n - base : (int64_t)kSortTile);
+    if (tid == 0) s_tile = atomicAdd(tile_counter, 1);
     run[tid] = 0;
-    gbase[tid] = offs[(int64_t)tid * ntiles + blockIdx.x];
+    __syncthreads();
+    const int tile = s_tile;
+    const int64_t base = (int64_t)tile * kSortTile;
+    const int tile_n = (int)(n - base < (int64_t)kSortTile ? n - base : (int64_t)kSortTile);
+    uint32_t gtot;
+    const uint32_t gstart = block_exclusive<uint32_t>(counts[tid], sw, &gtot);  // digit tid's global start
     const unsigned lt_mask = (1u << lane) - 1u;
 
     uint64_t key[kSortItems];
@@ -239,10 +262,40 @@ __global__ void __launch_bounds__(kSortThreads)
         rank[i] = valid ? wcnt[warp * kRadix + dig] + lr : 0u;
         __syncthreads();
     }
+
+    // this tile's count of digit tid, published; then the earlier tiles' counts
+    {
+        const uint32_t cnt = run[tid];
+        volatile unsigned long long *mine = status + (int64_t)tile * kRadix + tid;
+        uint32_t excl = 0;
+        if (tile == 0) {
+            *mine = kLbInclusive | cnt;
+        } else {
+            *mine = kLbAggregate | cnt;
+            for (int t = tile - 1; t >= 0; --t) {
+                volatile unsigned long long *pv = status + (int64_t)t * kRadix + tid;
+                unsigned long long v = *pv;
+                uint32_t polls = 0;
+                while ((v >> 62) == 0 && polls < kLookbackPolls) {
+                    __nanosleep(32);
+                    v = *pv;
+                    ++polls;
+                }
+                if ((v >> 62) == 0) {  // gave up: the result of this sort is invalid
+                    if (flags) atomicOr(&flags[kFlagTimeout], 1);
+                    break;
+                }
+                excl += (uint32_t)(v & 0xffffffffull);
+                if ((v >> 62) == 2) break;
+            }
+            *mine = kLbInclusive | (excl + cnt);
+        }
+        gbase[tid] = gstart + excl;
+    }
     // tile-level digit offsets (exclusive scan of run[] over digits)
     {
         uint32_t tot;
-        uint32_t ex = block_exclusive<uint32_t>(run[tid], sw, &tot);
+        const uint32_t ex = block_exclusive<uint32_t>(run[tid], sw, &tot);
         tile_off[tid] = ex;
     }
     __syncthreads();
@@ -260,39 +313,44 @@ __global__ void __launch_bounds__(kSortThreads)
     for (int li = tid; li < tile_n; li += kSortThreads) {
         const uint64_t k = sk[li];
         const uint32_t dig = (uint32_t)(k >> shift) & 0xffu;
-        const uint32_t dst = gbase[dig] + (li - tile_off[dig]);
-        kout[dst] = k;
-        vout[dst] = sv[li];
+        const int64_t dst = (int64_t)gbase[dig] + (li - (int)tile_off[dig]);
+        if (dst < n) {  // always, unless a wait gave up
+            kout[dst] = k;
+            vout[dst] = sv[li];
+        }
     }
 }
 
-constexpr size_t kScatterSmem = (size_t)kSortTile * 8 + (size_t)kSortTile * 4 +
-                                (8 * kRadix + 3 * kRadix + 33) * 4;
+constexpr size_t kPassSmem = (size_t)kSortTile * 8 + (size_t)kSortTile * 4 + (8 * kRadix + 3 * kRadix + 33) * 4;
 
 }  // namespace
 
-int64_t radix_hist_elems(int64_t n) { return (int64_t)kRadix * ceil_div(n, kSortTile) + 1; }
-
 void radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt,
-                      int64_t n, int bits, uint32_t *hist, uint32_t *scan_tmp, cudaStream_t st)
+                      int64_t n, int bits, uint32_t *scratch, int *flags, cudaStream_t st)
 {
     if (n <= 1) return;
-    set_smem_limit_once((const void *)k_radix_scatter, (int)kScatterSmem);
-    const int ntiles = (int)ceil_div(n, kSortTile);
-    const int64_t nh = (int64_t)kRadix * ntiles;
+    set_smem_limit_once((const void *)k_radix_pass, (int)kPassSmem);
+    const int64_t ntiles = ceil_div(n, kSortTile);
+    const int passes = (int)std::min<int64_t>(kRadixMaxPasses, ceil_div(bits, 8));
+    uint32_t *counts = scratch;                                        // [passes][256]
+    int *tile_counter = reinterpret_cast<int *>(scratch + kRadixMaxPasses * kRadix);  // [passes]
+    unsigned long long *status =
+        reinterpret_cast<unsigned long long *>(scratch + kRadixMaxPasses * kRadix + 64);  // [passes][ntiles][256]
+    const size_t zero_bytes = sizeof(uint32_t) * (kRadixMaxPasses * kRadix + 64) +
+                              sizeof(unsigned long long) * (size_t)passes * ntiles * kRadix;
+    FMM_CUDA_TRY(cudaMemsetAsync(scratch, 0, zero_bytes, st));
+    k_radix_counts<<<(unsigned)std::min<int64_t>(ceil_div(n, 256 * 8), 152 * 4), 256, 0, st>>>(keys, n, passes,
+                                                                                          counts);
+    FMM_LAUNCH_CHECK();
     uint64_t *ka = keys, *kb = keys_alt;
     uint32_t *va = vals, *vb = vals_alt;
-    int passes = 0;
-    for (int shift = 0; shift < bits; shift += 8) {
-        k_radix_hist<<<ntiles, kSortThreads, 0, st>>>(ka, n, shift, hist, ntiles);
-        FMM_LAUNCH_CHECK();
-        scan_exclusive<uint32_t>(hist, hist, nh, nullptr, scan_tmp, st);
-        k_radix_scatter<<<ntiles, kSortThreads, kScatterSmem, st>>>(ka, va, kb, vb, n, shift,
-                                                                    hist, ntiles);
+    for (int p = 0; p < passes; ++p) {
+        k_radix_pass<<<(unsigned)ntiles, kSortThreads, kPassSmem, st>>>(
+            ka, va, kb, vb, n, 8 * p, counts + p * kRadix, status + (int64_t)p * ntiles * kRadix, tile_counter + p,
+            flags);
         FMM_LAUNCH_CHECK();
         std::swap(ka, kb);
         std::swap(va, vb);
-        ++passes;
     }
     if (passes & 1) {
         FMM_CUDA_TRY(cudaMemcpyAsync(keys, ka, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, st));

@@ -178,6 +178,27 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16])
 }
 
 // 16 consecutive FP32 columns of this warp's 32 TMEM lanes.
+// Tensor-memory load of 16 columns without the wait: the registers are valid
+// only after tmem_ld_wait() and reg_touch16() of the same array.
+__device__ __forceinline__ void tmem_ld16_issue(uint32_t taddr, uint32_t (&r)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// Keeps every use of r after the preceding wait (volatile asm statements stay in order).
+__device__ __forceinline__ void reg_touch16(uint32_t (&r)[16])
+{
+    asm volatile(""
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]),
+                   "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]),
+                   "+r"(r[14]), "+r"(r[15]));
+}
+
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
 {
     uint32_t r[16];
@@ -275,13 +296,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (threadIdx.x == 0) {
         s_abort = 0;
         for (int s = 0; s < nstages; ++s) {
-            mbar_init(&full[s], kProducerWarps * 32);
+            mbar_init(&full[s], kProducerWarps);  // one arrival per producer warp
             mbar_init(&bfull[s], 1);
             mbar_init(&empty[s], 1);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&acc_full[b], 1);
-            mbar_init(&acc_empty[b], kAccWarps * 32);
+            mbar_init(&acc_empty[b], kAccWarps);  // one arrival per accumulator warp
         }
         mbar_init(fin, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -344,12 +365,14 @@ __global__ void __launch_bounds__(kThreads, 1)
         auto step = [&](int g, float4 (&cur)[NG][V], float4 (&ahead)[NG][V]) -> bool {
             if (g + 2 < nsteps) load_stage(g + 2, ahead);
             const int s = g % nstages;
-            if (g >= nstages && !mbar_wait(&empty[s], (uint32_t)((g / nstages) - 1) & 1u)) {
-                atomicOr(&flags[kFlagTimeout], 1);
+            // the warp decides together: it synchronises before its one arrival
+            const bool freed = g < nstages || mbar_wait(&empty[s], (uint32_t)((g / nstages) - 1) & 1u);
+            if (!__all_sync(0xffffffffu, freed)) {
+                if (lane == 0) atomicOr(&flags[kFlagTimeout], 1);
                 s_abort = 1;
                 return false;
             }
-            if (s_abort) return false;
+            if (__any_sync(0xffffffffu, s_abort != 0)) return false;
             unsigned char *st = smem + (size_t)s * stage_bytes;
             if (bissuer) {
                 const int e = U.e0 + g / nkc, kc = g % nkc;
@@ -378,8 +401,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                 }
             }
-            fence_proxy_async();
-            mbar_arrive(&full[s]);
+            fence_proxy_async();  // this thread's stores, before the tensor core reads them
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&full[s]);
             return true;
         };
         float4 b0[NG][V], b1[NG][V], b2[NG][V];
@@ -469,11 +493,27 @@ __global__ void __launch_bounds__(kThreads, 1)
             const bool last = b + 1 == nblocks;
             for (int c0 = 0; c0 < N; c0 += 16) {
                 float vm[16], vc[16], vs[16];
-                tmem_ld16(dmain + (uint32_t)c0, vm);
-                tmem_ld16(dmain + (uint32_t)(N + c0), vc);
+                {
+                    // the chunk's main, correction and running-sum columns under one wait
+                    uint32_t rm[16], rc[16], rs[16];
+                    const bool lds = SUM_TMEM && b > 0;
+                    tmem_ld16_issue(dmain + (uint32_t)c0, rm);
+                    tmem_ld16_issue(dmain + (uint32_t)(N + c0), rc);
+                    if (lds) tmem_ld16_issue(tmem + lane_off + (uint32_t)c0, rs);
+                    tmem_ld_wait();
+                    reg_touch16(rm);
+                    reg_touch16(rc);
+                    if (lds) reg_touch16(rs);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        vm[i] = __uint_as_float(rm[i]);
+                        vc[i] = __uint_as_float(rc[i]);
+                        vs[i] = lds ? __uint_as_float(rs[i]) : 0.f;
+                    }
+                }
                 if (b > 0) {
                     if (SUM_TMEM) {
-                        tmem_ld16(tmem + lane_off + (uint32_t)c0, vs);
+                        // vs holds the running sum
                     } else {
 #pragma unroll
                         for (int i = 0; i < 16; i += 4) {
@@ -497,7 +537,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             if (SUM_TMEM && !last) asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
             tc_fence_before();
-            mbar_arrive(&acc_empty[buf]);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[buf]);
         }
     }
     tc_fence_before();

@@ -412,6 +412,18 @@ def main():
     ms_p2p = statistics.mean(s["ms_p2p"] for s in st_list)
     ms_m2l = statistics.mean(s["ms_m2l"] for s in st_list)
     rooflines = hot_kernel_rooflines(st0, ms_p2p, ms_m2l, w["p"], args.precision)
+    # the FP32 pipe's measured ceilings beside the derived peak (context for the P2P line)
+    ceil = fmm.measure_fp32()
+    p2p_line = rooflines[0]
+    body_tf = ceil["body_interactions_per_s"] * P2P_FLOPS / 1e12
+    p2p_line["ceilings"] = {
+        "ffma_stream_tflops": ceil["ffma_tflops"],
+        "ffma_stream_frac_of_derived_peak": ceil["ffma_tflops"] / p2p_line["peak"],
+        "p2p_body_tflops": body_tf,
+        "p2p_body_frac_of_derived_peak": body_tf / p2p_line["peak"],
+        "kernel_frac_of_body": p2p_line["achieved"] / body_tf,
+        "what": "FP32x2 FMA chains alone, and the P2P interaction code on staged sources with no list walk "
+                "(fmm_measure_fp32), timed live beside the solve"}
     roof = max(rooflines, key=lambda r: r["ms"])  # the dominant kernel
     rooflines.append(tree_roofline(n, statistics.mean(s["ms_tree"] for s in st_list)))
     solve_frac = solve_roofline_fraction(rooflines, ms_per_step)

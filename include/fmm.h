@@ -302,6 +302,17 @@ fmm_status fmm_cost_model_samples(float *x, float *t, float *m, int64_t capacity
 fmm_status fmm_morton_sort_noalloc(const float *xyz, int64_t N, uint64_t *keys, int32_t *order,
                                    double *box, void *stream);
 
+/* Ceilings of the FP32 pipe on the current device, for the P2P roofline (the
+ * paper has no counterpart; its section "Advantage of N-body algorithms on
+ * GPUs" states peaks from the data sheet).  Runs, on `stream`, a kernel of
+ * independent FP32x2 FMA chains and the P2P kernel's interaction code on
+ * sources staged once in shared memory (no list walk), each timed with events
+ * after a warm-up; synchronises `stream`.
+ *   ffma_tflops       FMA-stream rate in TFLOP/s (FMA = 2 flop)
+ *   body_inter_per_s  interactions per second of the P2P body alone
+ * Either pointer may be NULL. */
+fmm_status fmm_measure_fp32(double *ffma_tflops, double *body_inter_per_s, void *stream);
+
 /* ---------------------------------------------------------------- captured plans
  * A plan is a solve whose every size lives on the device, captured once into a
  * CUDA graph and replayed for new particle data with one graph launch: no host

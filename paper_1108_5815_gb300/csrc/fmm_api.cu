@@ -1814,6 +1814,46 @@ fmm_status fmm_export(int what, void *dst, int64_t capacity, int64_t *needed)
     });
 }
 
+fmm_status fmm_measure_fp32(double *ffma_tflops, double *body_inter_per_s, void *stream)
+{
+    return guarded([&] {
+        cudaStream_t st = (cudaStream_t)stream;
+        int dev = 0, nsm = 152;
+        FMM_CUDA_TRY(cudaGetDevice(&dev));
+        FMM_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        Workspace &ws = workspace_for_current_device();
+        std::lock_guard<std::mutex> lk(ws.mu);
+        const int ffma_blocks = nsm * 8, body_blocks = nsm * kP2PBlocksPerSM;
+        float *out = need<float>(ws, "measure_out", (size_t)std::max(ffma_blocks * 256, body_blocks * 128), st);
+        cudaEvent_t e0, e1;
+        FMM_CUDA_TRY(cudaEventCreate(&e0));
+        FMM_CUDA_TRY(cudaEventCreate(&e1));
+        auto timed = [&](auto launch) {
+            launch(true);  // warm-up
+            FMM_CUDA_TRY(cudaEventRecord(e0, st));
+            launch(false);
+            FMM_CUDA_TRY(cudaEventRecord(e1, st));
+            FMM_CUDA_TRY(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            FMM_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+            return (double)ms;
+        };
+        const int iters = 20000, reps = 4000;
+        const double ms_ffma = timed([&](bool warm) {
+            k_ffma_stream<<<ffma_blocks, 256, 0, st>>>(out, warm ? 100 : iters, 1.0001f);
+            FMM_LAUNCH_CHECK();
+        });
+        const double ms_body = timed([&](bool warm) {
+            k_p2p_body<<<body_blocks, 128, 0, st>>>(out, warm ? 10 : reps);
+            FMM_LAUNCH_CHECK();
+        });
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (ffma_tflops) *ffma_tflops = (double)ffma_blocks * 256 * iters * 16 * 2 / (ms_ffma * 1e-3) / 1e12;
+        if (body_inter_per_s) *body_inter_per_s = (double)body_blocks * 128 * reps * 32 / (ms_body * 1e-3);
+    });
+}
+
 // ---------------------------------------------------------------- captured plans
 
 fmm_status fmm_plan_create(fmm_plan **plan, const float *xyz, const float *q, int64_t N, const int64_t *offsets,

@@ -214,6 +214,10 @@ constexpr int kP2PBlocksPerSM = 6;
 __global__ void k_p2p(CellArrays c, ListArrays L, const int *leaves, int nleaves,
                       const float4 *pts, float4 *near, int *counter, const int *sz = nullptr);
 __global__ void k_direct(const float *xyz, const float *q, int64_t n, float *phi, float *grad);
+// FP32-pipe ceilings: FP32x2 FMA chains (16 lane-FMAs per thread and iteration),
+// and the P2P interaction body on staged sources (32 interactions per thread and rep).
+__global__ void k_ffma_stream(float *out, int iters, float s);
+__global__ void k_p2p_body(float *out, int reps);
 __global__ void k_combine(const float4 *far, const float4 *near, const uint32_t *idx, int64_t n,
                           float *phi, float *grad);
 

@@ -346,6 +346,56 @@ __global__ void __launch_bounds__(128, kP2PBlocksPerSM)
     }
 }
 
+// Ceilings of the FP32 pipe on this device, for the P2P roofline.
+//
+// k_ffma_stream: eight independent FP32x2 FMA chains per thread, nothing else
+// in the loop -- the rate the FMA pipe sustains.  k_p2p_body: the P2P kernel's
+// own interaction code (p2p_chunk32, unguarded) on 32 sources staged once in
+// shared memory, `reps` passes, no list walk and no global loads -- the rate of
+// the interaction body alone.  Both write one value per thread so that the work
+// is kept.
+__global__ void __launch_bounds__(256) k_ffma_stream(float *__restrict__ out, int iters, float s)
+{
+    f2 a[8];
+    const f2 m = f2pack(s, s), c = f2pack(0.5f * s, 0.25f * s);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = f2pack(threadIdx.x * 1e-3f + k, k * 0.1f);
+#pragma unroll 1
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) a[k] = f2fma(a[k], m, c);
+    }
+    float x = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x += f2sum(a[k]);
+    out[(int64_t)blockIdx.x * blockDim.x + threadIdx.x] = x;
+}
+
+__global__ void __launch_bounds__(128, kP2PBlocksPerSM) k_p2p_body(float *__restrict__ out, int reps)
+{
+    __shared__ __align__(16) float sh[4][128];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float *s = sh[warp];
+    s[lane] = 0.37f * lane;
+    s[32 + lane] = 0.11f * lane + 0.5f;
+    s[64 + lane] = 0.05f * lane - 0.3f;
+    s[96 + lane] = 1.0f / (1 + lane);
+    __syncwarp();
+    const Target2 T = target2(make_float4(0.013f * threadIdx.x + 40.f, 0.2f, -0.1f, 0.f));
+    const f2 zero = 0ull;
+    Acc2 a0 = {zero, zero, zero, zero}, a1 = a0;
+#pragma unroll 1
+    for (int r = 0; r < reps; ++r) {
+        __syncwarp();
+        p2p_chunk32<false>(T, s, a0, a1);
+        __syncwarp();
+        if (lane == 0 && r < 0) s[0] = 1.f;  // never: the staged sources may change as far as the compiler knows
+    }
+    out[(int64_t)blockIdx.x * blockDim.x + threadIdx.x] =
+        f2sum(a0.phi) + f2sum(a1.phi) + f2sum(a0.gx) + f2sum(a1.gx) + f2sum(a0.gy) + f2sum(a1.gy) + f2sum(a0.gz) +
+        f2sum(a1.gz);
+}
+
 // All-pairs sum: one thread per target, 256-source tiles in shared memory.
 __global__ void __launch_bounds__(256)
     k_direct(const float *__restrict__ xyz, const float *__restrict__ q, int64_t n,

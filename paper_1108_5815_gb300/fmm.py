@@ -32,7 +32,7 @@ ABI_SYMBOLS = ("fmm_default_options", "fmm_laplace3d", "fmm_laplace3d_ex", "fmm_
                "fmm_cost_model_set", "fmm_cost_model_grad", "fmm_cost_model_adam_step",
                "fmm_cost_model_predict", "fmm_cost_model_samples", "fmm_tune_ncrit",
                "fmm_tune_schedule", "fmm_selftest_wait_timeout", "fmm_plan_create", "fmm_plan_execute",
-               "fmm_plan_check", "fmm_plan_buffers", "fmm_plan_info", "fmm_plan_destroy")
+               "fmm_plan_check", "fmm_plan_buffers", "fmm_plan_info", "fmm_plan_destroy", "fmm_measure_fp32")
 COST_MODEL_PARAMS = 4610
 
 
@@ -137,6 +137,8 @@ def load(path: str | None = None):
         L.fmm_plan_buffers.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
                                        ctypes.POINTER(vp)]
         L.fmm_plan_info.argtypes = [vp, ctypes.POINTER(PlanInfo)]
+        L.fmm_measure_fp32.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), vp]
+        L.fmm_measure_fp32.restype = ctypes.c_int
         L.fmm_plan_destroy.argtypes = [vp]
         L.fmm_plan_destroy.restype = None
         for name in ("fmm_plan_create", "fmm_plan_execute", "fmm_plan_check", "fmm_plan_buffers",
@@ -269,6 +271,17 @@ def laplace3d_batched(xyz, q, offsets, p: int, theta: float, ncrit: int, *, max_
                                             grad.data_ptr(), _stream_ptr(torch, xyz.device),
                                             ctypes.byref(o), ctypes.byref(st) if stats else None))
     return (phi, grad, st.as_dict()) if stats else (phi, grad)
+
+
+def measure_fp32() -> dict:
+    """FP32-pipe ceilings on the current device (fmm_measure_fp32): the rate of an
+    FP32x2 FMA stream in TFLOP/s and the interactions per second of the P2P
+    interaction body on staged sources."""
+    import torch
+    f, b = ctypes.c_double(), ctypes.c_double()
+    dev = torch.cuda.current_device()
+    _check(load().fmm_measure_fp32(ctypes.byref(f), ctypes.byref(b), _stream_ptr(torch, dev)))
+    return {"ffma_tflops": f.value, "body_interactions_per_s": b.value}
 
 
 class Plan:

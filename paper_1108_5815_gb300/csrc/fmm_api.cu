@@ -611,12 +611,12 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
     int *p2p_counter = need<int>(ws, "p2p_counter", 1, st);
     FMM_CUDA_TRY(cudaMemsetAsync(p2p_counter, 0, sizeof(int), st));
     {
-        // kP2PBlocksPerSM (6) blocks of 4 warps per SM: with up to 80 registers a thread
-        // the packed arithmetic keeps more interactions in flight than at 8 blocks and
-        // 64 registers (measured 3-5 % faster; 4 blocks was slower).  This fills the
-        // register file, so the far-field chain's kernels run after P2P.  Starting P2P
-        // together with M2L instead (so that the two share SMs) was measured no faster:
-        // both kernels then ran at half speed.
+        // kP2PBlocksPerSM (4) blocks of 4 warps per SM: with up to 128 registers a
+        // thread the packed arithmetic keeps more interactions in flight (measured
+        // 1.68 ms at 6 blocks and 80 registers, 1.60 ms at 4 blocks, on the uniform
+        // 1M workload).  This fills the register file, so the far-field chain's
+        // kernels run after P2P.  Starting P2P together with M2L instead (so that the
+        // two share SMs) was measured no faster: both kernels then ran at half speed.
         int nsm = 152;
         FMM_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ws.device));
         const unsigned blocks = (unsigned)std::min<int64_t>(ceil_div(nleaves, 4), (int64_t)nsm * kP2PBlocksPerSM);

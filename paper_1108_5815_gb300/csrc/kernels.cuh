@@ -210,7 +210,7 @@ void launch_split_tables(bool bf16, const float *table, int slot0, int nslots, i
                          cudaStream_t st);
 
 // p2p.cu -- persistent P2P: kP2PBlocksPerSM blocks of 128 threads per SM
-constexpr int kP2PBlocksPerSM = 6;
+constexpr int kP2PBlocksPerSM = 4;
 __global__ void k_p2p(CellArrays c, ListArrays L, const int *leaves, int nleaves,
                       const float4 *pts, float4 *near, int *counter, const int *sz = nullptr);
 __global__ void k_direct(const float *xyz, const float *q, int64_t n, float *phi, float *grad);

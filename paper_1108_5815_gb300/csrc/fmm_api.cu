@@ -387,6 +387,7 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
         c.tile = need<int>(ws, "c_tile", cap, st, keep);
         c.lane = need<int>(ws, "c_lane", cap, st, keep);
         c.sys = need<int>(ws, "c_sys", cap, st, keep);
+        c.geom = need<int4>(ws, "c_geom", cap, st, keep);
         return c;
     };
     CellArrays c = cells(cell_cap, false);
@@ -505,6 +506,8 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
         FMM_LAUNCH_CHECK();
         sync_point(ws, st, flags, {{lex + ncells, sizeof(int)}}, &nleaves);
     }
+    k_cell_geom<<<grid_for(ncells, 256), 256, 0, st>>>(c, ncells);
+    FMM_LAUNCH_CHECK();
     ev.rec(1, st);
     ws.shape.lstart = lstart;
     ws.shape.N = N;
@@ -1186,6 +1189,7 @@ void build_plan(fmm_plan &pl, Workspace &ws, const int64_t *offsets, const uint8
     b.c.tile = m.get<int>(cc);
     b.c.lane = m.get<int>(cc);
     b.c.sys = m.get<int>(cc);
+    b.c.geom = m.get<int4>(cc);
     b.blvl = m.get<uint64_t>(std::max(N - 1, 1));
     b.bpos = m.get<uint32_t>(std::max(N - 1, 1));
     b.bstart = m.get<int>(24);

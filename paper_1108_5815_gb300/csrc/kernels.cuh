@@ -50,6 +50,7 @@ struct CellArrays {
     int *parent, *child0, *nchild;
     int *tile, *lane;  // M2L GEMM tile of this cell as a target
     int *sys;          // independent system (root) the cell belongs to
+    int4 *geom;        // integer centre (x, y, z) in units of side/2^22 and half side
 };
 
 // Interaction lists written by the traversal (CSR per target cell).
@@ -99,6 +100,8 @@ __global__ void k_split_emit(CellArrays c, const uint64_t *keys, const uint32_t 
 __global__ void k_level_advance(const int64_t *total, int level, int last_level, int cell_cap,
                                 int next_level_cap, int tile_cap, int *sz);
 __global__ void k_fill_tile_cells(CellArrays c, int ncells, int *tile_cells, const int *sz = nullptr);
+// c.geom of every cell from its level and key prefix (with sz: the cell count from sz).
+__global__ void k_cell_geom(CellArrays c, int ncells, const int *sz = nullptr);
 // With sz: flags for len cells, zero past the last cell.
 __global__ void k_leaf_flags(CellArrays c, int ncells, int *flag, const int *sz = nullptr, int len = 0);
 __global__ void k_leaf_compact(CellArrays c, int ncells, const int *ex, int *leaves, const int *sz = nullptr);

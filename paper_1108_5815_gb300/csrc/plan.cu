@@ -96,6 +96,8 @@ void enqueue_plan(const PlanShape &s, const PlanBuffers &b, cudaStream_t st, cud
     k_leaf_compact<<<blocks_for(s.cell_cap, 256), 256, 0, st>>>(c, 0, b.leaf_ex, b.leaves, b.sz);
     FMM_LAUNCH_CHECK();
     FMM_CUDA_TRY(cudaMemcpyAsync(b.sz + kSzLeaves, b.leaf_ex + s.cell_cap, sizeof(int), cudaMemcpyDeviceToDevice, st));
+    k_cell_geom<<<grid_stride(s.cell_cap), 256, 0, st>>>(c, 0, b.sz);
+    FMM_LAUNCH_CHECK();
 
     // ---------------------------------------------------------- traversal
     const double theta2 = s.theta * s.theta;

@@ -52,11 +52,16 @@ __device__ __forceinline__ int count_bucket(int n)
     return e < 2 ? n - 1 : 3 + 4 * (e - 2) + ((n >> (e - 2)) & 3);
 }
 
-__device__ __forceinline__ void cell_geom32(int level, uint64_t prefix, int C[3], int &h)
+// Integer centre and half side of cell S (computed once per solve by
+// k_cell_geom); its level follows from the half side h = 2^(kKeyBits - level).
+__device__ __forceinline__ void cell_geom(const CellArrays &c, int S, int C[3], int &h, int &level)
 {
-    h = 1 << (kKeyBits - level);
-#pragma unroll
-    for (int a = 0; a < 3; ++a) C[a] = (2 * (int)compact3_dev(prefix >> a) + 1) * h;
+    const int4 g = __ldg(&c.geom[S]);
+    C[0] = g.x;
+    C[1] = g.y;
+    C[2] = g.z;
+    h = g.w;
+    level = kKeyBits + 1 - __ffs(g.w);
 }
 
 // MAC of reading R3: accept iff R > 0 and (r_t + r_s)^2 <= theta^2 R^2 with theta^2 R^2
@@ -160,10 +165,9 @@ __device__ Counts resolve(const TargetInfo &T, int S0, const CellArrays &c, cons
     stk[sp++] = S0;
     while (sp > 0) {
         const int S = stk[--sp];
-        const int ls = c.level[S];
         const int nchS = c.nchild[S];
-        int Cs[3], hs;
-        cell_geom32(ls, c.prefix[S], Cs, hs);
+        int Cs[3], hs, ls;
+        cell_geom(c, S, Cs, hs, ls);
         if (mac_accept(T, Cs, hs, theta2, theta2f)) {
             const int kind = sel ? __ldg(&sel[T.bt * kSelNB + count_bucket(c.end[S] - c.begin[S])]) : 0;
             if (kind == 3) {  // particle-cell: into T's own local expansion, at any level
@@ -220,9 +224,8 @@ __device__ __forceinline__ TargetInfo load_target(const CellArrays &c, int t)
 {
     TargetInfo T;
     T.t = t;
-    T.level = c.level[t];
     T.leaf = c.nchild[t] == 0;
-    cell_geom32(T.level, c.prefix[t], T.C, T.h);
+    cell_geom(c, t, T.C, T.h, T.level);
     T.bt = count_bucket(c.end[t] - c.begin[t]);
     return T;
 }
@@ -289,8 +292,8 @@ __global__ void __launch_bounds__(128, 6)
         auto splits = [&](int S, int &nc) {
             nc = 1;
             if ((S & (kP2PFlag | kM2PFlag)) || c.nchild[S] == 0) return false;
-            int Cs[3], hs;
-            cell_geom32(c.level[S], c.prefix[S], Cs, hs);
+            int Cs[3], hs, ls;
+            cell_geom(c, S, Cs, hs, ls);
             if (mac_accept(T, Cs, hs, theta2, theta2f)) return false;
             nc = c.nchild[S];
             return true;

@@ -413,6 +413,19 @@ __global__ void k_level_advance(const int64_t *__restrict__ total, int level, in
     sz[kSzCells] = b + nch;
 }
 
+__global__ void k_cell_geom(CellArrays c, int ncells, const int *__restrict__ sz)
+{
+    if (sz) ncells = sz[kSzCells];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ncells; i += gridDim.x * blockDim.x) {
+        const int h = 1 << (kKeyBits - c.level[i]);
+        const uint64_t pre = c.prefix[i];
+        int C[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) C[a] = (2 * (int)compact3_dev(pre >> a) + 1) * h;
+        c.geom[i] = make_int4(C[0], C[1], C[2], h);
+    }
+}
+
 __global__ void k_fill_tile_cells(CellArrays c, int ncells, int *__restrict__ tile_cells, const int *__restrict__ sz)
 {
     if (sz) ncells = sz[kSzCells];

@@ -334,37 +334,56 @@ __global__ void __launch_bounds__(32)
             const float z = (float)(((double)pt.z - cen[2]) * is);
             const float q = pt.w;
             const float r2 = x * x + y * y + z * z;
+            auto put = [&](int n, int m, float rr, float ri) {
+                if (m == 0) {
+                    row[n * n] = q * rr;
+                } else {
+                    row[n * n + 2 * m - 1] = q * rr;
+                    row[n * n + 2 * m] = -q * ri;
+                }
+            };
+            // orders m and m + 1 advance together: two independent recurrences in n
             float mre = 1.f, mim = 0.f;  // R^_m^m
-            for (int m = 0; m <= p; ++m) {
+            for (int m = 0; m <= p; m += 2) {
                 if (m > 0) {
                     const float f = c_rec_d[m];
                     const float nre = f * (x * mre - y * mim), nim = f * (x * mim + y * mre);
                     mre = nre;
                     mim = nim;
                 }
-                float p2r = 0.f, p2i = 0.f, p1r = mre, p1i = mim;
-                for (int n = m; n <= p; ++n) {
-                    float rr, ri;
-                    if (n == m) {
-                        rr = mre;
-                        ri = mim;
-                    } else {
-                        const int t = n * (n + 1) / 2 + m;
-                        const float a = c_rec_a[t] * z, bb = c_rec_b[t] * r2;
-                        rr = a * p1r - bb * p2r;
-                        ri = a * p1i - bb * p2i;
-                        p2r = p1r;
-                        p2i = p1i;
-                        p1r = rr;
-                        p1i = ri;
-                    }
-                    if (m == 0) {
-                        row[n * n] = q * rr;
-                    } else {
-                        row[n * n + 2 * m - 1] = q * rr;
-                        row[n * n + 2 * m] = -q * ri;
-                    }
+                float bre = 0.f, bim = 0.f;  // R^_{m+1}^{m+1}
+                if (m + 1 <= p) {
+                    const float f = c_rec_d[m + 1];
+                    bre = f * (x * mre - y * mim);
+                    bim = f * (x * mim + y * mre);
                 }
+                put(m, m, mre, mim);
+                float a2r = 0.f, a2i = 0.f, a1r = mre, a1i = mim;  // chain m
+                float b2r = 0.f, b2i = 0.f, b1r = bre, b1i = bim;  // chain m + 1
+                for (int n = m + 1; n <= p; ++n) {
+                    const int ta = n * (n + 1) / 2 + m;
+                    const float aa = c_rec_a[ta] * z, ab = c_rec_b[ta] * r2;
+                    const float rr = aa * a1r - ab * a2r, ri = aa * a1i - ab * a2i;
+                    a2r = a1r;
+                    a2i = a1i;
+                    a1r = rr;
+                    a1i = ri;
+                    put(n, m, rr, ri);
+                    float qr = b1r, qi = b1i;  // n == m + 1: the diagonal itself
+                    if (n > m + 1) {
+                        const int tb = ta + 1;
+                        const float ba = c_rec_a[tb] * z, bb = c_rec_b[tb] * r2;
+                        qr = ba * b1r - bb * b2r;
+                        qi = ba * b1i - bb * b2i;
+                        b2r = b1r;
+                        b2i = b1i;
+                        b1r = qr;
+                        b1i = qi;
+                    }
+                    put(n, m + 1, qr, qi);
+                }
+                mre = bre;  // the next pair starts from R^_{m+1}^{m+1}
+                mim = bim;
             }
         }
         __syncwarp();
@@ -615,71 +634,92 @@ __global__ void __launch_bounds__(32)
     const double is = 1.0 / s;
     const float inv_s = (float)is, inv_s2 = (float)(is * is);
     const int b = c.begin[cell], e = c.end[cell];
+    // one (n, m) term of phi, d/dz and D+ = d/dx + i d/dy into the sums s
+    struct Sums {
+        float phi, dz, dpr, dpi;
+    };
+    auto term = [&](int n, int m, float rr, float ri, Sums &sm) {
+        const float w = m == 0 ? 1.f : 2.f;
+        {  // phi += w Re(L_n^m R_n^m)
+            const int k = n * n + (m == 0 ? 0 : 2 * m - 1);
+            const float lr = Lh[k], lim = m == 0 ? 0.f : Lh[k + 1];
+            sm.phi += w * (lr * rr - lim * ri);
+        }
+        if (n + 1 <= p) {
+            const int n1 = n + 1, base = n1 * n1;
+            {  // dz += w Re(Lz_{n+1}^m R_n^m)
+                const int k = base + (m == 0 ? 0 : 2 * m - 1);
+                const float lr = Lz[k], lim = m == 0 ? 0.f : Lz[k + 1];
+                sm.dz += w * (lr * rr - lim * ri);
+            }
+            if (m >= 1) {  // D+ += Lx1_{n+1}^{m-1} R_n^m
+                const int mm = m - 1;
+                const int k = base + (mm == 0 ? 0 : 2 * mm - 1);
+                const float lr = Lx1[k], lim = mm == 0 ? 0.f : Lx1[k + 1];
+                sm.dpr += lr * rr - lim * ri;
+                sm.dpi += lr * ri + lim * rr;
+            }
+            {  // D+ -= conj(Lx2_{n+1}^{m+1} R_n^m)
+                const int k = base + 2 * (m + 1) - 1;
+                const float lr = Lx2[k], lim = Lx2[k + 1];
+                sm.dpr -= lr * rr - lim * ri;
+                sm.dpi += lr * ri + lim * rr;
+            }
+        }
+    };
     for (int i = b + lane; i < e; i += 32) {
         const float4 pt = pts[i];
         const float x = (float)(((double)pt.x - cen[0]) * is);
         const float y = (float)(((double)pt.y - cen[1]) * is);
         const float z = (float)(((double)pt.z - cen[2]) * is);
         const float r2 = x * x + y * y + z * z;
-        float phi = 0.f, dz = 0.f, dpr = 0.f, dpi = 0.f;
-        float mre = 1.f, mim = 0.f;
-        for (int m = 0; m <= p; ++m) {
+        // orders m and m + 1 advance together (two independent recurrences in n,
+        // each with its own sums) so that a lane has two chains in flight
+        Sums sa = {0.f, 0.f, 0.f, 0.f}, sb = sa;
+        float mre = 1.f, mim = 0.f;  // R^_m^m
+        for (int m = 0; m <= p; m += 2) {
             if (m > 0) {
                 const float f = c_rec_d[m];
                 const float nre = f * (x * mre - y * mim), nim = f * (x * mim + y * mre);
                 mre = nre;
                 mim = nim;
             }
-            const float w = m == 0 ? 1.f : 2.f;
-            float p2r = 0.f, p2i = 0.f, p1r = mre, p1i = mim;
-            for (int n = m; n <= p; ++n) {
-                float rr, ri;
-                if (n == m) {
-                    rr = mre;
-                    ri = mim;
-                } else {
-                    const int t = n * (n + 1) / 2 + m;
-                    const float a = c_rec_a[t] * z, bb = c_rec_b[t] * r2;
-                    rr = a * p1r - bb * p2r;
-                    ri = a * p1i - bb * p2i;
-                    p2r = p1r;
-                    p2i = p1i;
-                    p1r = rr;
-                    p1i = ri;
-                }
-                // phi += w Re(L_n^m R_n^m)
-                {
-                    const int k = n * n + (m == 0 ? 0 : 2 * m - 1);
-                    const float lr = Lh[k], lim = m == 0 ? 0.f : Lh[k + 1];
-                    phi += w * (lr * rr - lim * ri);
-                }
-                if (n + 1 <= p) {
-                    const int n1 = n + 1, base = n1 * n1;
-                    // dz += w Re(Lz_{n+1}^m R_n^m)
-                    {
-                        const int k = base + (m == 0 ? 0 : 2 * m - 1);
-                        const float lr = Lz[k], lim = m == 0 ? 0.f : Lz[k + 1];
-                        dz += w * (lr * rr - lim * ri);
-                    }
-                    // D+ += Lx1_{n+1}^{m-1} R_n^m  (m >= 1)
-                    if (m >= 1) {
-                        const int mm = m - 1;
-                        const int k = base + (mm == 0 ? 0 : 2 * mm - 1);
-                        const float lr = Lx1[k], lim = mm == 0 ? 0.f : Lx1[k + 1];
-                        dpr += lr * rr - lim * ri;
-                        dpi += lr * ri + lim * rr;
-                    }
-                    // D+ -= conj(Lx2_{n+1}^{m+1} R_n^m)
-                    {
-                        const int mm = m + 1;
-                        const int k = base + 2 * mm - 1;
-                        const float lr = Lx2[k], lim = Lx2[k + 1];
-                        dpr -= lr * rr - lim * ri;
-                        dpi += lr * ri + lim * rr;
-                    }
-                }
+            const bool two = m + 1 <= p;
+            float bre = 0.f, bim = 0.f;  // R^_{m+1}^{m+1}
+            if (two) {
+                const float f = c_rec_d[m + 1];
+                bre = f * (x * mre - y * mim);
+                bim = f * (x * mim + y * mre);
             }
+            term(m, m, mre, mim, sa);
+            float a2r = 0.f, a2i = 0.f, a1r = mre, a1i = mim;  // chain m
+            float b2r = 0.f, b2i = 0.f, b1r = bre, b1i = bim;  // chain m + 1
+            for (int n = m + 1; n <= p; ++n) {
+                const int ta = n * (n + 1) / 2 + m;
+                const float aa = c_rec_a[ta] * z, ab = c_rec_b[ta] * r2;
+                const float rr = aa * a1r - ab * a2r, ri = aa * a1i - ab * a2i;
+                a2r = a1r;
+                a2i = a1i;
+                a1r = rr;
+                a1i = ri;
+                term(n, m, rr, ri, sa);
+                float qr = b1r, qi = b1i;  // n == m + 1: the diagonal itself
+                if (n > m + 1) {
+                    const int tb = ta + 1;
+                    const float ba = c_rec_a[tb] * z, bb = c_rec_b[tb] * r2;
+                    qr = ba * b1r - bb * b2r;
+                    qi = ba * b1i - bb * b2i;
+                    b2r = b1r;
+                    b2i = b1i;
+                    b1r = qr;
+                    b1i = qi;
+                }
+                term(n, m + 1, qr, qi, sb);
+            }
+            mre = bre;  // the next pair starts from R^_{m+1}^{m+1}
+            mim = bim;
         }
+        const float phi = sa.phi + sb.phi, dz = sa.dz + sb.dz, dpr = sa.dpr + sb.dpr, dpi = sa.dpi + sb.dpi;
         far[i] = make_float4(phi * inv_s, dpr * inv_s2, dpi * inv_s2, dz * inv_s2);
     }
 }

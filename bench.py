@@ -379,6 +379,12 @@ def main():
                                           unit_candidates=ucs, **kw)
         ncrit_tuning = {"candidates_ms": {f"ncrit={a},unit={b}": v for (a, b), v in table.items()},
                         "best_ncrit": bn, "best_m2l_unit_blocks": bu, "workload_ncrit": w["ncrit"]}
+        if cost_model is not None and off is None:
+            # the network's pick from the candidates' interaction lists, judged by the measurement
+            nb, pred = fmm.cost_model_pick_ncrit(xd, qd, w["p"], w["theta"], ncs, **kw)
+            ncrit_tuning["network"] = {"pick": nb, "predicted_ms": pred,
+                                       "measured_ms_of_pick": min(v for (a, _), v in table.items() if a == nb),
+                                       "measured_best_ms": min(table.values())}
         w["ncrit"] = bn
         kw["m2l_unit_blocks"] = bu
 

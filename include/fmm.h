@@ -302,6 +302,22 @@ fmm_status fmm_cost_model_samples(float *x, float *t, float *m, int64_t capacity
 fmm_status fmm_morton_sort_noalloc(const float *xyz, int64_t N, uint64_t *keys, int32_t *order,
                                    double *box, void *stream);
 
+/* N_crit from the learned cost model (the benchmark spec's use of the network for
+ * the N_crit choice; the paper's section "Results" balances the near and far
+ * fields through N_crit).  For each candidate the library builds the tree and
+ * the interaction lists of the system (with the options' selection mode; no
+ * expansion is evaluated and nothing is timed), bins the P2P pairs by the
+ * count buckets of the selection table, and sums the network's predicted time
+ * per pair over the bins plus the number of M2L pairs times its predicted M2L
+ * time per pair.  pred_ms[k] (may be NULL) receives candidate k's prediction in
+ * ms and *best the candidate with the smallest one.  The expansion passes,
+ * whose cost grows with the number of cells, are not in the prediction; the
+ * measured autotuner (fmm_tune_ncrit) remains the fallback and the judge.
+ * Needs a trained or set model (else FMM_ERR_ARG).  Synchronises `stream`. */
+fmm_status fmm_cost_model_pick_ncrit(const float *xyz, const float *q, int64_t N, int p, double theta, void *stream,
+                                     const fmm_options *opt, const int *candidates, int ncand, float *pred_ms,
+                                     int *best);
+
 /* Ceilings of the FP32 pipe on the current device, for the P2P roofline (the
  * paper has no counterpart; its section "Advantage of N-body algorithms on
  * GPUs" states peaks from the data sheet).  Runs, on `stream`, a kernel of

@@ -300,9 +300,12 @@ void validate(const void *xyz, const void *q, int64_t N, int p, double theta, in
 }
 
 // The solve on device buffers; the caller holds ws.mu.
+// lists_only: stop after the traversal (the tree, the leaves and the interaction
+// lists stay in the workspace; phi and grad are not written).
 void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, int nsys,
                   const int64_t *offsets, int p, double theta, int ncrit, float *phi, float *grad,
-                  cudaStream_t caller, const fmm_options &o, fmm_stats *stats, const uint8_t *sel)
+                  cudaStream_t caller, const fmm_options &o, fmm_stats *stats, const uint8_t *sel,
+                  bool lists_only = false)
 {
     ensure_streams(ws);
     init_recurrence_tables();
@@ -601,6 +604,11 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
     ws.cap_def = def_cap;
     ws.cap_m2p = m2p_cap;
     ws.cap_p2l = p2l_cap;
+    if (lists_only) {
+        FMM_CUDA_TRY(cudaEventRecord(ws.ev_out, st));
+        FMM_CUDA_TRY(cudaStreamWaitEvent(caller, ws.ev_out, 0));
+        return;
+    }
 
     // ---------------------------------------------------------- fork
     // P2P needs only the leaf lists: it runs on the caller's stream while the
@@ -1815,6 +1823,55 @@ fmm_status fmm_export(int what, void *dst, int64_t capacity, int64_t *needed)
                 break;
             }
         }
+    });
+}
+
+fmm_status fmm_cost_model_pick_ncrit(const float *xyz, const float *q, int64_t N, int p, double theta, void *stream,
+                                     const fmm_options *opt, const int *candidates, int ncand, float *pred_ms,
+                                     int *best)
+{
+    return guarded([&] {
+        if (!candidates || ncand < 1 || !best) throw Error{FMM_ERR_ARG, "need candidates and best"};
+        const fmm_options o = resolve_opts(opt);
+        validate(xyz, q, N, p, theta, 1, xyz, xyz, o);
+        for (int k = 0; k < ncand; ++k)
+            if (candidates[k] < 1) throw Error{FMM_ERR_ARG, "ncrit candidates must be >= 1"};
+        Workspace &ws = workspace_for_current_device();
+        std::lock_guard<std::mutex> lk(ws.mu);
+        if (!ws.cm.trained) throw Error{FMM_ERR_ARG, "no cost model: train or set one first"};
+        ensure_streams(ws);
+        cudaStream_t cs = (cudaStream_t)stream, st = ws.main_stream;
+        const uint8_t *sel = selection_table(ws, o, p, theta);
+        const int64_t off[2] = {0, N};
+        unsigned long long *hist = need<unsigned long long>(ws, "pick_hist", (size_t)kSelNB * kSelNB, st);
+        double *cost = need<double>(ws, "pick_cost", 2, st);
+        double best_ns = 1e300;
+        for (int k = 0; k < ncand; ++k) {
+            // the candidate's tree and interaction lists (no evaluation), then the
+            // network over them
+            solve_locked(ws, xyz, q, N, 1, off, p, theta, candidates[k], nullptr, nullptr, cs, o, nullptr, sel, true);
+            const int64_t np2p = ws.shape.tot[1], nm2l = ws.shape.tot[0];
+            FMM_CUDA_TRY(cudaMemsetAsync(hist, 0, sizeof(unsigned long long) * kSelNB * kSelNB, st));
+            if (np2p > 0) {
+                k_pair_bucket_hist<<<grid_for(np2p, 256), 256, 0, st>>>(get<int>(ws, "p2p_tgt"), get<int>(ws, "p2p_src"),
+                                                                      np2p, get<int>(ws, "c_begin"),
+                                                                      get<int>(ws, "c_end"), hist);
+                FMM_LAUNCH_CHECK();
+            }
+            k_mlp_solve_cost<<<1, 256, 0, st>>>(ws.cm.w16, (float)p, (float)(1.0 / theta), hist,
+                                               (unsigned long long)nm2l, cost);
+            FMM_LAUNCH_CHECK();
+            double h[2];
+            FMM_CUDA_TRY(cudaMemcpyAsync(h, cost, sizeof(h), cudaMemcpyDeviceToHost, st));
+            FMM_CUDA_TRY(cudaStreamSynchronize(st));
+            const double ns = h[0] + h[1];
+            if (pred_ms) pred_ms[k] = (float)(ns * 1e-6);
+            if (ns < best_ns) {
+                best_ns = ns;
+                *best = candidates[k];
+            }
+        }
+        ws.have_solve = false;  // the workspace holds lists, not a finished solve
     });
 }
 

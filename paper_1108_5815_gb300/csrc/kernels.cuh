@@ -108,6 +108,12 @@ __global__ void k_leaf_compact(CellArrays c, int ncells, const int *ex, int *lea
 
 // traverse.cu
 constexpr int kSelNB = 128;  // count buckets of the hybrid selection table
+// Count bucket of the selection table: n - 1 below 4, then four per octave.
+__device__ __forceinline__ int count_bucket(int n)
+{
+    const int e = 31 - __clz(n);
+    return e < 2 ? n - 1 : 3 + 4 * (e - 2) + ((n >> (e - 2)) & 3);
+}
 __global__ void k_traverse_level(CellArrays c, ListArrays L, int a, int b, double theta2,
                                  float theta2f, const uint8_t *sel, unsigned long long *counters,
                                  int64_t cap_m, int64_t cap_p, int64_t cap_d, int64_t cap_q,
@@ -240,6 +246,10 @@ __global__ void k_mlp_adam(float *w32, float *mom, float *vel, const float *g, _
                            float lr, float beta1, float beta2, float eps);
 __global__ void k_mlp_step_inc(int *step);
 __global__ void k_mlp_table(const __half *w16, float p, float sep, uint8_t *sel);
+__global__ void k_pair_bucket_hist(const int *tgt, const int *src, int64_t n, const int *begin, const int *end,
+                                   unsigned long long *hist);
+__global__ void k_mlp_solve_cost(const __half *w16, float p, float sep, const unsigned long long *hist,
+                                 unsigned long long m2l_pairs, double *out);
 
 // cost_model.cu -- kernel pre-calculation on artificial cells
 struct P2PTiming {

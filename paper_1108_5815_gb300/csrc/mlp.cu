@@ -260,4 +260,54 @@ __global__ void __launch_bounds__(128)
     sel[i] = y[0] < y[1] ? 1 : 0;
 }
 
+// Histogram of P2P pairs (target leaf, source cell) over the count buckets of
+// the selection table: hist[bucket(n_t) * kSelNB + bucket(n_s)] (zeroed).
+__global__ void k_pair_bucket_hist(const int *__restrict__ tgt, const int *__restrict__ src, int64_t n,
+                                   const int *__restrict__ begin, const int *__restrict__ end,
+                                   unsigned long long *__restrict__ hist)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int t = tgt[i], so = src[i];
+        atomicAdd(&hist[count_bucket(end[t] - begin[t]) * kSelNB + count_bucket(end[so] - begin[so])], 1ull);
+    }
+}
+
+// The network's prediction of a solve's near- and far-field time: out[0] = sum
+// over the occupied buckets of (pairs in the bucket) x exp(y_P2P) ns, out[1] =
+// m2l_pairs x exp(y_M2L) ns (the M2L output does not depend on the counts; it
+// is read at log2 counts 5, 5).  One block of kBlock threads.
+__global__ void __launch_bounds__(256)
+    k_mlp_solve_cost(const __half *__restrict__ w16, float p, float sep, const unsigned long long *__restrict__ hist,
+                     unsigned long long m2l_pairs, double *__restrict__ out)
+{
+    __shared__ float sw[kMlpParams];
+    __shared__ double part[256];
+    load_params(w16, sw, threadIdx.x, blockDim.x);
+    __syncthreads();
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < kSelNB * kSelNB; i += blockDim.x) {
+        const unsigned long long h = hist[i];
+        if (h == 0) continue;
+        const float x[kMlpIn] = {bucket_mid_log2(i / kSelNB), bucket_mid_log2(i % kSelNB), sep, p};
+        float u[kMlpIn], y[kMlpOut];
+        normalise(x, u);
+        forward_one(sw, u, nullptr, nullptr, y);
+        acc += (double)h * exp((double)y[0]);
+    }
+    part[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) part[threadIdx.x] += part[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const float x[kMlpIn] = {5.f, 5.f, sep, p};
+        float u[kMlpIn], y[kMlpOut];
+        normalise(x, u);
+        forward_one(sw, u, nullptr, nullptr, y);
+        out[0] = part[0];
+        out[1] = (double)m2l_pairs * exp((double)y[1]);
+    }
+}
+
 }  // namespace fmm

@@ -45,13 +45,6 @@ struct TargetInfo {
     int bt;       // count bucket of the target (hybrid selection)
 };
 
-// Count bucket of the selection table: n - 1 below 4, then four per octave.
-__device__ __forceinline__ int count_bucket(int n)
-{
-    const int e = 31 - __clz(n);
-    return e < 2 ? n - 1 : 3 + 4 * (e - 2) + ((n >> (e - 2)) & 3);
-}
-
 // Integer centre and half side of cell S (computed once per solve by
 // k_cell_geom); its level follows from the half side h = 2^(kKeyBits - level).
 __device__ __forceinline__ void cell_geom(const CellArrays &c, int S, int C[3], int &h, int &level)

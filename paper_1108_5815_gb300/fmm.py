@@ -32,7 +32,8 @@ ABI_SYMBOLS = ("fmm_default_options", "fmm_laplace3d", "fmm_laplace3d_ex", "fmm_
                "fmm_cost_model_set", "fmm_cost_model_grad", "fmm_cost_model_adam_step",
                "fmm_cost_model_predict", "fmm_cost_model_samples", "fmm_tune_ncrit",
                "fmm_tune_schedule", "fmm_selftest_wait_timeout", "fmm_plan_create", "fmm_plan_execute",
-               "fmm_plan_check", "fmm_plan_buffers", "fmm_plan_info", "fmm_plan_destroy", "fmm_measure_fp32")
+               "fmm_plan_check", "fmm_plan_buffers", "fmm_plan_info", "fmm_plan_destroy", "fmm_measure_fp32",
+               "fmm_cost_model_pick_ncrit")
 COST_MODEL_PARAMS = 4610
 
 
@@ -138,6 +139,10 @@ def load(path: str | None = None):
                                        ctypes.POINTER(vp)]
         L.fmm_plan_info.argtypes = [vp, ctypes.POINTER(PlanInfo)]
         L.fmm_measure_fp32.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), vp]
+        L.fmm_cost_model_pick_ncrit.argtypes = [vp, vp, i64, ctypes.c_int, ctypes.c_double, vp,
+                                                ctypes.POINTER(Options), vp, ctypes.c_int, vp,
+                                                ctypes.POINTER(ctypes.c_int)]
+        L.fmm_cost_model_pick_ncrit.restype = ctypes.c_int
         L.fmm_measure_fp32.restype = ctypes.c_int
         L.fmm_plan_destroy.argtypes = [vp]
         L.fmm_plan_destroy.restype = None
@@ -271,6 +276,26 @@ def laplace3d_batched(xyz, q, offsets, p: int, theta: float, ncrit: int, *, max_
                                             grad.data_ptr(), _stream_ptr(torch, xyz.device),
                                             ctypes.byref(o), ctypes.byref(st) if stats else None))
     return (phi, grad, st.as_dict()) if stats else (phi, grad)
+
+
+def cost_model_pick_ncrit(xyz, q, p: int, theta: float, candidates=(16, 32, 64, 128, 256), *, max_depth: int = 0,
+                          precision: str = "fp32", select="plain"):
+    """N_crit from the learned cost model (fmm_cost_model_pick_ncrit): (best,
+    {candidate: predicted ms}).  Builds each candidate's tree and lists, times
+    nothing."""
+    import torch
+    n = int(xyz.shape[0])
+    xyz = _dev_f32(xyz, (n, 3), "xyz")
+    q = _dev_f32(q, (n,), "q")
+    cand = np.ascontiguousarray(np.asarray(candidates, dtype=np.int32))
+    pred = np.zeros(len(cand), dtype=np.float32)
+    best = ctypes.c_int()
+    o = _options(max_depth, precision, select)
+    with torch.cuda.device(xyz.device):
+        _check(load().fmm_cost_model_pick_ncrit(xyz.data_ptr(), q.data_ptr(), n, p, float(theta),
+                                                _stream_ptr(torch, xyz.device), ctypes.byref(o), cand.ctypes.data,
+                                                len(cand), pred.ctypes.data, ctypes.byref(best)))
+    return best.value, {int(c): float(m) for c, m in zip(cand, pred)}
 
 
 def measure_fp32() -> dict:

@@ -179,3 +179,19 @@ def test_tune_ncrit_returns_the_fastest_candidate():
     xt, qt = torch.from_numpy(x).cuda(), torch.from_numpy(q).cuda()
     best, ms = fmm.tune_ncrit(xt, qt, 6, 0.5, (8, 32, 128), select="autotune")
     assert best in (8, 32, 128) and ms[best] == min(ms.values()) and all(v > 0 for v in ms.values())
+
+
+def test_network_picks_ncrit_judged_by_the_measured_tuner(trained):
+    # the network costs each candidate's interaction lists (nothing timed); the
+    # measured autotuner solves every candidate and judges the pick
+    torch = torch_cuda()
+    from paper_1108_5815_gb300 import fmm
+    x, q = inputs.uniform_cube(1 << 19, 2025)
+    xt, qt = torch.from_numpy(x).cuda(), torch.from_numpy(q).cuda()
+    cands = (8, 16, 32, 64, 128, 256)
+    best_net, pred = fmm.cost_model_pick_ncrit(xt, qt, 8, 0.5, cands)
+    best_meas, ms = fmm.tune_ncrit(xt, qt, 8, 0.5, cands)
+    assert best_net in cands and all(v > 0 for v in pred.values())
+    # far out of balance (tiny leaves, a flood of M2L pairs) is predicted as such
+    assert pred[8] > 2 * pred[best_net]
+    assert ms[best_net] <= 1.5 * ms[best_meas], (best_net, best_meas, pred, ms)

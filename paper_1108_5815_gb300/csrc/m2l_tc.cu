@@ -265,8 +265,19 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (sz && (int)blockIdx.x >= sz[kSzUnits]) return;
     constexpr int NG = 2;                          // groups of 8 A rows per producer warp
     constexpr bool SUM_TMEM = 3 * N <= 512;        // running sum in tensor memory
-    constexpr int NBUF = 5 * N <= 512 ? 2 : 1;     // main/correction buffer pairs
-    constexpr int BUF0 = SUM_TMEM ? N : 0;         // first buffer column
+    // BF16, N <= 128: [sum | main 0 | correction | main 1].  The correction
+    // products (about 2^-8 of the main one) accumulate over all class blocks of
+    // the unit in one buffer; the main product restarts per block in two
+    // alternating buffers, so the MMAs of block b + 1 run while block b is
+    // drained.  The correction sits next to both main buffers, so one MMA of
+    // width 2N gives ah.bh and ah.bl together: [main 0 | corr] = ah.[bh | bl] for
+    // even blocks, [corr | main 1] = ah.[bl | bh] for odd ones, whose stages hold
+    // B_lo first.  (Measured faster for BF16 only; TF32 keeps the layout below.)
+    // Otherwise: [sum |] (main | correction) pairs, both restarted per block.
+    constexpr bool CORR_RUN = BF16 && 4 * N <= 512;
+    constexpr int NBUF = CORR_RUN || 5 * N <= 512 ? 2 : 1;  // main buffers (or main/correction pairs)
+    constexpr int BUF0 = SUM_TMEM ? N : 0;                   // first buffer column
+    constexpr int BUFW = 2 * N;                              // columns per buffer (main 1 at 3N)
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // 1024-byte aligned base
     unsigned char *smem = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
@@ -289,8 +300,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const Unit U = units[blockIdx.x];
     const int nsteps = (U.e1 - U.e0) * nkc;
+    constexpr int kCols = CORR_RUN ? 4 * N : BUF0 + BUFW * NBUF;  // tensor-memory columns in use
+    static_assert(kCols <= 512, "tensor memory has 512 columns");
     uint32_t ncols = 32;
-    while (ncols < (uint32_t)(BUF0 + 2 * N * NBUF)) ncols <<= 1;
+    while (ncols < (uint32_t)kCols) ncols <<= 1;
     const int nblocks = U.e1 - U.e0;
 
     if (threadIdx.x == 0) {
@@ -377,9 +390,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (bissuer) {
                 const int e = U.e0 + g / nkc, kc = g % nkc;
                 const unsigned char *bsrc = tsplit + ((int64_t)entry_class[e] * nkc + kc) * 2 * (int64_t)b_bytes;
+                const bool lo_first = CORR_RUN && ((g / nkc) & 1);  // odd blocks: [B_lo | B_hi]
                 mbar_arrive_expect_tx(&bfull[s], 2 * b_bytes);
-                bulk_g2s(st + 2 * a_bytes, bsrc, b_bytes, &bfull[s]);
-                bulk_g2s(st + 2 * a_bytes + b_bytes, bsrc + b_bytes, b_bytes, &bfull[s]);
+                bulk_g2s(st + 2 * a_bytes + (lo_first ? b_bytes : 0), bsrc, b_bytes, &bfull[s]);
+                bulk_g2s(st + 2 * a_bytes + (lo_first ? 0 : b_bytes), bsrc + b_bytes, b_bytes, &bfull[s]);
                 issued = g + 1;
             }
 #pragma unroll
@@ -437,7 +451,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                     ok = false;
                     break;
                 }
-                const uint32_t dmain = tmem + (uint32_t)(BUF0 + buf * 2 * N), dcorr = dmain + (uint32_t)N;
+                const uint32_t dmain = tmem + (uint32_t)(BUF0 + buf * BUFW),
+                               dcorr = CORR_RUN ? tmem + (uint32_t)(2 * N) : dmain + (uint32_t)N;
+                const bool odd = CORR_RUN && (b & 1);
                 for (int kc = 0; kc < nkc; ++kc, ++g) {
                     const int s = g % nstages;
                     if (!mbar_wait(&full[s], (uint32_t)(g / nstages) & 1u) ||
@@ -447,13 +463,24 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                     tc_fence_after();
                     const uint32_t base = smem_u32(smem + (size_t)s * stage_bytes);
-                    const uint32_t ah = base, al = base + a_bytes, bh = base + 2 * a_bytes,
-                                   bl = bh + b_bytes;
+                    const uint32_t ah = base, al = base + a_bytes, b0 = base + 2 * a_bytes,
+                                   bh = odd ? b0 + b_bytes : b0, bl = odd ? b0 : b0 + b_bytes;
 #pragma unroll
                     for (int k = 0; k < ksteps; ++k) {
                         const uint32_t off = (uint32_t)k * 256u;  // two core matrices along K
                         const uint32_t acc0 = (kc > 0 || k > 0) ? 1u : 0u;
-                        if (kFuse) {
+                        if (CORR_RUN) {
+                            if (acc0 == 0 && b > 0) {
+                                // a block's first step: main restarts, the correction goes on
+                                mma<BF16>(dmain, smem_desc(ah + off, SBO), smem_desc(bh + off, SBO), idesc, 0u);
+                                mma<BF16>(dcorr, smem_desc(ah + off, SBO), smem_desc(bl + off, SBO), idesc, 1u);
+                            } else {
+                                // [main | corr] (even) or [corr | main] (odd) = ah.(B as staged)
+                                mma<BF16>(odd ? dcorr : dmain, smem_desc(ah + off, SBO), smem_desc(b0 + off, SBO),
+                                          idesc2, acc0);
+                            }
+                            mma<BF16>(dcorr, smem_desc(al + off, SBO), smem_desc(bh + off, SBO), idesc, 1u);
+                        } else if (kFuse) {
                             mma<BF16>(dmain, smem_desc(ah + off, SBO), smem_desc(bh + off, SBO), idesc2, acc0);
                             mma<BF16>(dcorr, smem_desc(al + off, SBO), smem_desc(bh + off, SBO), idesc, 1u);
                         } else {
@@ -476,7 +503,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
     } else {
         // ------------------------------------------------------------ accumulators
-        // sum_b = sum_{b-1} + (main_b + corr_b), FP32 round-to-nearest, per element.
+        // sum_b = sum_{b-1} + (main_b + corr_b), FP32 round-to-nearest, per element;
+        // with the running correction: sum_b = sum_{b-1} + main_b, and the
+        // correction is added once after the last block.
         const int quad = warp & 3;
         const int row = quad * 32 + lane;
         const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
@@ -489,8 +518,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                 break;
             }
             tc_fence_after();
-            const uint32_t dmain = tmem + lane_off + (uint32_t)(BUF0 + buf * 2 * N);
+            const uint32_t dmain = tmem + lane_off + (uint32_t)(BUF0 + buf * BUFW);
+            const uint32_t dcorr = CORR_RUN ? tmem + lane_off + (uint32_t)(2 * N) : dmain + (uint32_t)N;
             const bool last = b + 1 == nblocks;
+            const bool ldc = !CORR_RUN || last;  // the correction: every block, or once at the end
             for (int c0 = 0; c0 < N; c0 += 16) {
                 float vm[16], vc[16], vs[16];
                 {
@@ -498,23 +529,28 @@ __global__ void __launch_bounds__(kThreads, 1)
                     uint32_t rm[16], rc[16], rs[16];
                     const bool lds = SUM_TMEM && b > 0;
                     tmem_ld16_issue(dmain + (uint32_t)c0, rm);
-                    tmem_ld16_issue(dmain + (uint32_t)(N + c0), rc);
+                    if (ldc) tmem_ld16_issue(dcorr + (uint32_t)c0, rc);
                     if (lds) tmem_ld16_issue(tmem + lane_off + (uint32_t)c0, rs);
                     tmem_ld_wait();
                     reg_touch16(rm);
-                    reg_touch16(rc);
+                    if (ldc) reg_touch16(rc);
                     if (lds) reg_touch16(rs);
 #pragma unroll
                     for (int i = 0; i < 16; ++i) {
                         vm[i] = __uint_as_float(rm[i]);
-                        vc[i] = __uint_as_float(rc[i]);
+                        vc[i] = ldc ? __uint_as_float(rc[i]) : 0.f;
                         vs[i] = lds ? __uint_as_float(rs[i]) : 0.f;
                     }
                 }
-                if (b > 0) {
-                    if (SUM_TMEM) {
-                        // vs holds the running sum
-                    } else {
+                if (CORR_RUN) {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) vs[i] = b > 0 ? vs[i] + vm[i] : vm[i];
+                    if (last) {
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) vs[i] += vc[i];
+                    }
+                } else if (b > 0) {
+                    if (!SUM_TMEM) {
 #pragma unroll
                         for (int i = 0; i < 16; i += 4) {
                             const float4 t = *reinterpret_cast<const float4 *>(out + c0 + i);

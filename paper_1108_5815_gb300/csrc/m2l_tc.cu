@@ -22,21 +22,23 @@
 // the shared-memory layout of a stage, so a stage's B is two bulk asynchronous
 // copies (cp.async.bulk, completing on an mbarrier) issued by one thread.
 //
-// Roles inside a CTA (416 threads):
-//   warps 0-7   producers: gather the 128 source rows (A) of one K-chunk of 32
-//               floats, split them into hi/lo and store them in the canonical
+// Roles inside a CTA (704 threads):
+//   warps 0-15  producers, two groups of 8 warps that fill alternate stages:
+//               gather the 128 source rows (A) of one K-chunk of 32 floats,
+//               split them into hi/lo and store them in the canonical
 //               no-swizzle K-major layout (8-row x 16-byte core matrices;
 //               LBO = 128 B along K, SBO = 8 core matrices (TF32, 128 B rows) or
-//               4 (BF16, 64 B rows) along rows); one producer thread also issues
-//               the stage's B copies.
-//   warp 8      allocates tensor memory; one lane issues the MMAs and commits.
-//   warps 9-12  accumulators, one per 32-lane quarter of tensor memory: after
+//               4 (BF16, 64 B rows) along rows).
+//   warp 16     allocates tensor memory; one lane issues the MMAs and commits.
+//   warps 17-20 accumulators, one per 32-lane quarter of tensor memory: after
 //               each class block they read the block's main and correction
 //               accumulators (two buffer pairs, alternating, when 5N columns fit)
 //               and add both into the running sum.
-// Stages are handed over through mbarriers (full: 256 producer arrivals; bfull:
-// one arrival with the B copies' byte count; empty, acc_full: tcgen05.commit;
-// acc_empty: 128 accumulator arrivals).  Every
+//   warp 21     one lane issues every stage's B copies, in stage order.
+// Stages are handed over through mbarriers (full: one arrival per warp of the
+// stage's producer group; bfull: one arrival with the B copies' byte count;
+// empty, acc_full: tcgen05.commit;
+// acc_empty: one arrival per accumulator warp).  Every
 // wait is bounded: on expiry the kernel raises a flag and returns after
 // releasing its tensor memory.
 // A work unit is (tile, range of the tile's class blocks); its 128 x N result
@@ -54,10 +56,12 @@ namespace fmm {
 
 namespace {
 
-constexpr int kProducerWarps = 8;
+constexpr int kProducerWarps = 8;  // per producer group
 constexpr int kAccWarps = 4;
-constexpr int kMmaWarp = kProducerWarps;
-constexpr int kThreads = (kProducerWarps + 1 + kAccWarps) * 32;
+constexpr int kProducerGroups = 2;                  // they fill alternate stages
+constexpr int kMmaWarp = kProducerGroups * kProducerWarps;
+constexpr int kBWarp = kMmaWarp + 1 + kAccWarps;    // issues the B copies
+constexpr int kThreads = (kBWarp + 1) * 32;
 constexpr int kKChunk = 32;  // source floats per row per stage (128 B)
 constexpr uint32_t kWaitLimit = 1u << 26;
 
@@ -199,20 +203,6 @@ __device__ __forceinline__ void reg_touch16(uint32_t (&r)[16])
                    "+r"(r[14]), "+r"(r[15]));
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
-{
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-          "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
 // hi/lo split of 4 floats into one 16-byte chunk each (TF32: 4 elements).
 __device__ __forceinline__ void split_tf32(float4 a, uint4 &hi, uint4 &lo)
 {
@@ -265,16 +255,16 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (sz && (int)blockIdx.x >= sz[kSzUnits]) return;
     constexpr int NG = 2;                          // groups of 8 A rows per producer warp
     constexpr bool SUM_TMEM = 3 * N <= 512;        // running sum in tensor memory
-    // BF16, N <= 128: [sum | main 0 | correction | main 1].  The correction
+    // N <= 128: [sum | main 0 | correction | main 1].  The correction
     // products (about 2^-8 of the main one) accumulate over all class blocks of
     // the unit in one buffer; the main product restarts per block in two
     // alternating buffers, so the MMAs of block b + 1 run while block b is
     // drained.  The correction sits next to both main buffers, so one MMA of
     // width 2N gives ah.bh and ah.bl together: [main 0 | corr] = ah.[bh | bl] for
     // even blocks, [corr | main 1] = ah.[bl | bh] for odd ones, whose stages hold
-    // B_lo first.  (Measured faster for BF16 only; TF32 keeps the layout below.)
+    // B_lo first.
     // Otherwise: [sum |] (main | correction) pairs, both restarted per block.
-    constexpr bool CORR_RUN = BF16 && 4 * N <= 512;
+    constexpr bool CORR_RUN = 4 * N <= 512;
     constexpr int NBUF = CORR_RUN || 5 * N <= 512 ? 2 : 1;  // main buffers (or main/correction pairs)
     constexpr int BUF0 = SUM_TMEM ? N : 0;                   // first buffer column
     constexpr int BUFW = 2 * N;                              // columns per buffer (main 1 at 3N)
@@ -332,24 +322,27 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    if (warp < kProducerWarps) {
+    if (warp < kMmaWarp) {
         // ------------------------------------------------------------ producers
-        // Thread (warp, lane) owns A rows grp*8 + (lane & 7) for grp = warp + 8j (j < 2),
-        // and the 16-byte chunks (lane >> 3) + 4h of each (h < 2 in TF32, h = 0 in BF16).
-        // The loads of stage g+2 are issued before stage g is split and stored.
-        // Thread 0 also issues the two bulk copies of stage g's B (hi, lo).
+        // Group grp fills stages g = grp, grp + 2, ...  Thread (warp, lane) of the
+        // group owns A rows grp8*8 + (lane & 7) for grp8 = pw + 8j (j < 2, pw = warp
+        // within the group), and the 16-byte chunks (lane >> 3) + 4h of each (h < 2
+        // in TF32, h = 0 in BF16).  The loads of the group's next stage are issued
+        // before a stage is split and stored.
+        const int grp = warp / kProducerWarps, pw = warp % kProducerWarps;
         const int sub = lane & 7, cq = lane >> 3;
         constexpr int V = 2;  // float4 per row and thread per stage
-        const bool bissuer = threadIdx.x == 0;
         int srow[2] = {0, 0};
         bool svalid[2] = {false, false};
+        int cur_e = -1;
         auto load_stage = [&](int g, float4 (&buf)[NG][V]) {
             const int e = U.e0 + g / nkc;
             const int k0 = (g % nkc) * kstage;
-            if (g % nkc == 0) {
+            if (e != cur_e) {  // the group's first stage of a block: its source rows
+                cur_e = e;
 #pragma unroll
                 for (int j = 0; j < 2; ++j) {
-                    const int row = (warp + 8 * j) * 8 + sub;
+                    const int row = (pw + 8 * j) * 8 + sub;
                     const int sidx = src[(int64_t)e * kTile + row];
                     svalid[j] = sidx >= 0;
                     srow[j] = svalid[j] ? sidx : 0;
@@ -372,11 +365,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
             }
         };
-        int issued = 0;  // B stages issued by thread 0
         // one pipeline step: consume stage g from `cur`, first issuing the loads of
-        // stage g + 2 into `ahead` (three register buffers in rotation)
+        // the group's next stage into `ahead` (two register buffers in turn)
         auto step = [&](int g, float4 (&cur)[NG][V], float4 (&ahead)[NG][V]) -> bool {
-            if (g + 2 < nsteps) load_stage(g + 2, ahead);
+            if (g + kProducerGroups < nsteps) load_stage(g + kProducerGroups, ahead);
             const int s = g % nstages;
             // the warp decides together: it synchronises before its one arrival
             const bool freed = g < nstages || mbar_wait(&empty[s], (uint32_t)((g / nstages) - 1) & 1u);
@@ -387,18 +379,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             if (__any_sync(0xffffffffu, s_abort != 0)) return false;
             unsigned char *st = smem + (size_t)s * stage_bytes;
-            if (bissuer) {
-                const int e = U.e0 + g / nkc, kc = g % nkc;
-                const unsigned char *bsrc = tsplit + ((int64_t)entry_class[e] * nkc + kc) * 2 * (int64_t)b_bytes;
-                const bool lo_first = CORR_RUN && ((g / nkc) & 1);  // odd blocks: [B_lo | B_hi]
-                mbar_arrive_expect_tx(&bfull[s], 2 * b_bytes);
-                bulk_g2s(st + 2 * a_bytes + (lo_first ? b_bytes : 0), bsrc, b_bytes, &bfull[s]);
-                bulk_g2s(st + 2 * a_bytes + (lo_first ? 0 : b_bytes), bsrc + b_bytes, b_bytes, &bfull[s]);
-                issued = g + 1;
-            }
 #pragma unroll
             for (int j = 0; j < NG; ++j) {
-                const int row = (warp + 8 * j) * 8 + sub;
+                const int row = (pw + 8 * j) * 8 + sub;
                 unsigned char *dst_hi = st + (row >> 3) * SBO + (row & 7) * 16;
                 unsigned char *dst_lo = dst_hi + a_bytes;
                 uint4 hi, lo;
@@ -420,18 +403,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (lane == 0) mbar_arrive(&full[s]);
             return true;
         };
-        float4 b0[NG][V], b1[NG][V], b2[NG][V];
-        if (nsteps > 0) load_stage(0, b0);
-        if (nsteps > 1) load_stage(1, b1);
-        for (int g = 0; g < nsteps; g += 3) {
-            if (!step(g, b0, b2)) break;
-            if (g + 1 >= nsteps || !step(g + 1, b1, b0)) break;
-            if (g + 2 >= nsteps || !step(g + 2, b2, b1)) break;
-        }
-        if (bissuer) {
-            // no B copy may still be landing when the CTA ends (matters after an abort)
-            for (int g = issued - 1; g >= 0 && g >= issued - nstages; --g)
-                if (!mbar_wait(&bfull[g % nstages], (uint32_t)(g / nstages) & 1u)) atomicOr(&flags[kFlagTimeout], 1);
+        constexpr int D = kProducerGroups;  // stride between a group's stages
+        float4 b0[NG][V], b1[NG][V];
+        if (grp < nsteps) load_stage(grp, b0);
+        for (int g = grp; g < nsteps; g += 2 * D) {
+            if (!step(g, b0, b1)) break;
+            if (g + D >= nsteps || !step(g + D, b1, b0)) break;
         }
     } else if (warp == kMmaWarp) {
         // ------------------------------------------------------------ MMA issuer
@@ -501,8 +478,36 @@ __global__ void __launch_bounds__(kThreads, 1)
             mma_commit(fin);
             if (!mbar_wait(fin, 0)) atomicOr(&flags[kFlagTimeout], 1);
         }
+    } else if (warp == kBWarp) {
+        if (lane == 0) {
+            // ------------------------------------------------------------ B copies
+            // Each stage's B (hi, lo) by two bulk copies, in stage order, as soon as the
+            // stage's buffer is free.
+            int issued = 0;
+            for (int g = 0; g < nsteps; ++g) {
+                const int s = g % nstages;
+                if (g >= nstages && !mbar_wait(&empty[s], (uint32_t)((g / nstages) - 1) & 1u)) {
+                    atomicOr(&flags[kFlagTimeout], 1);
+                    s_abort = 1;
+                    break;
+                }
+                if (s_abort) break;
+                unsigned char *st = smem + (size_t)s * stage_bytes;
+                const int e = U.e0 + g / nkc, kc = g % nkc;
+                const unsigned char *bsrc = tsplit + ((int64_t)entry_class[e] * nkc + kc) * 2 * (int64_t)b_bytes;
+                const bool lo_first = CORR_RUN && ((g / nkc) & 1);  // odd blocks: [B_lo | B_hi]
+                mbar_arrive_expect_tx(&bfull[s], 2 * b_bytes);
+                bulk_g2s(st + 2 * a_bytes + (lo_first ? b_bytes : 0), bsrc, b_bytes, &bfull[s]);
+                bulk_g2s(st + 2 * a_bytes + (lo_first ? 0 : b_bytes), bsrc + b_bytes, b_bytes, &bfull[s]);
+                issued = g + 1;
+            }
+            // no B copy may still be landing when the CTA ends (matters after an abort)
+            for (int g = issued - 1; g >= 0 && g >= issued - nstages; --g)
+                if (!mbar_wait(&bfull[g % nstages], (uint32_t)(g / nstages) & 1u)) atomicOr(&flags[kFlagTimeout], 1);
+        }
     } else {
         // ------------------------------------------------------------ accumulators
+        // (warps 17-20: warp & 3 covers the four lane quarters)
         // sum_b = sum_{b-1} + (main_b + corr_b), FP32 round-to-nearest, per element;
         // with the running correction: sum_b = sum_{b-1} + main_b, and the
         // correction is added once after the last block.
@@ -521,35 +526,57 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t dmain = tmem + lane_off + (uint32_t)(BUF0 + buf * BUFW);
             const uint32_t dcorr = CORR_RUN ? tmem + lane_off + (uint32_t)(2 * N) : dmain + (uint32_t)N;
             const bool last = b + 1 == nblocks;
-            const bool ldc = !CORR_RUN || last;  // the correction: every block, or once at the end
-            for (int c0 = 0; c0 < N; c0 += 16) {
+            if (CORR_RUN) {
+                // sum_b = sum_{b-1} + main_b in tensor memory; after the last block the
+                // correction is loaded on its own, which keeps two chunks in registers
+                const uint32_t dsum = tmem + lane_off;
+                for (int c0 = 0; c0 < N; c0 += 16) {
+                    uint32_t rm[16], rs[16];
+                    tmem_ld16_issue(dmain + (uint32_t)c0, rm);
+                    if (b > 0) tmem_ld16_issue(dsum + (uint32_t)c0, rs);
+                    tmem_ld_wait();
+                    reg_touch16(rm);
+                    if (b > 0) reg_touch16(rs);
+                    float vs[16];
+#pragma unroll
+                    for (int i = 0; i < 16; ++i)
+                        vs[i] = b > 0 ? __uint_as_float(rs[i]) + __uint_as_float(rm[i]) : __uint_as_float(rm[i]);
+                    if (last) {
+                        uint32_t rc[16];
+                        tmem_ld16_issue(dcorr + (uint32_t)c0, rc);
+                        tmem_ld_wait();
+                        reg_touch16(rc);
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) vs[i] += __uint_as_float(rc[i]);
+#pragma unroll
+                        for (int i = 0; i < 16; i += 4)
+                            *reinterpret_cast<float4 *>(out + c0 + i) = make_float4(vs[i], vs[i + 1], vs[i + 2], vs[i + 3]);
+                    } else {
+                        tmem_st16(dsum + (uint32_t)c0, vs);
+                    }
+                }
+            }
+            for (int c0 = 0; c0 < (CORR_RUN ? 0 : N); c0 += 16) {
                 float vm[16], vc[16], vs[16];
                 {
                     // the chunk's main, correction and running-sum columns under one wait
                     uint32_t rm[16], rc[16], rs[16];
                     const bool lds = SUM_TMEM && b > 0;
                     tmem_ld16_issue(dmain + (uint32_t)c0, rm);
-                    if (ldc) tmem_ld16_issue(dcorr + (uint32_t)c0, rc);
+                    tmem_ld16_issue(dcorr + (uint32_t)c0, rc);
                     if (lds) tmem_ld16_issue(tmem + lane_off + (uint32_t)c0, rs);
                     tmem_ld_wait();
                     reg_touch16(rm);
-                    if (ldc) reg_touch16(rc);
+                    reg_touch16(rc);
                     if (lds) reg_touch16(rs);
 #pragma unroll
                     for (int i = 0; i < 16; ++i) {
                         vm[i] = __uint_as_float(rm[i]);
-                        vc[i] = ldc ? __uint_as_float(rc[i]) : 0.f;
+                        vc[i] = __uint_as_float(rc[i]);
                         vs[i] = lds ? __uint_as_float(rs[i]) : 0.f;
                     }
                 }
-                if (CORR_RUN) {
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) vs[i] = b > 0 ? vs[i] + vm[i] : vm[i];
-                    if (last) {
-#pragma unroll
-                        for (int i = 0; i < 16; ++i) vs[i] += vc[i];
-                    }
-                } else if (b > 0) {
+                if (b > 0) {
                     if (!SUM_TMEM) {
 #pragma unroll
                         for (int i = 0; i < 16; i += 4) {

@@ -454,19 +454,55 @@ __global__ void __launch_bounds__(128)
 #pragma unroll
         for (int q = 0; q < 8; ++q) acc[r][q] = 0.f;
     const float *A = mats + (int64_t)o * P2pad * P2pad;
-    for (int k0 = 0; k0 < P2; k0 += 32) {
-        for (int idx = t; idx < 32 * 128; idx += 128) {
-            const int kr = idx >> 7, jj = idx & 127;
+    // The next K-chunk is loaded into registers (all loads of a thread in flight
+    // at once) while the current one is multiplied: one memory latency per chunk
+    // instead of one per element, which is what the small top levels wait on.
+    // A chunk: 32 K-rows x 128 output rows of A (8 float4 per thread) and 32 K
+    // entries of the 32 input rows (2 float4 per thread, parent q = idx & 31).
+    // P2pad is a multiple of 32, so every float4 is aligned and inside its row.
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 ra[8], rc[2];
+    auto load = [&](int k0) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int idx = t + 128 * i;
+            const int kr = idx >> 5, jj = (idx & 31) * 4;
             const int k = k0 + kr, j = j0 + jj;
-            sA[kr][jj] = (k < P2 && j < P2pad) ? A[(int64_t)k * P2pad + j] : 0.f;
+            ra[i] = (k < P2 && j < P2pad) ? __ldg(reinterpret_cast<const float4 *>(A + (int64_t)k * P2pad + j)) : zero4;
         }
-        for (int idx = t; idx < 32 * 32; idx += 128) {
-            const int q = idx >> 5, kr = idx & 31;
-            const int k = k0 + kr;
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int idx = t + 128 * i;
+            const int q = idx & 31, k = k0 + (idx >> 5) * 4;
             const int row = L2L ? (sch[q] >= 0 ? p0 + q : -1) : sch[q];
-            sC[kr][q] = (row >= 0 && k < P2) ? in[(int64_t)row * P2pad + k] : 0.f;
+            float4 v = zero4;
+            if (row >= 0 && k < P2) {
+                v = *reinterpret_cast<const float4 *>(in + (int64_t)row * P2pad + k);
+                if (k + 1 >= P2) v.y = 0.f;
+                if (k + 2 >= P2) v.z = 0.f;
+                if (k + 3 >= P2) v.w = 0.f;
+            }
+            rc[i] = v;
+        }
+    };
+    load(0);
+    for (int k0 = 0; k0 < P2; k0 += 32) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int idx = t + 128 * i;
+            *reinterpret_cast<float4 *>(&sA[idx >> 5][(idx & 31) * 4]) = ra[i];
+        }
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int idx = t + 128 * i;
+            const int q = idx & 31, kr = (idx >> 5) * 4;
+            sC[kr][q] = rc[i].x;
+            sC[kr + 1][q] = rc[i].y;
+            sC[kr + 2][q] = rc[i].z;
+            sC[kr + 3][q] = rc[i].w;
         }
         __syncthreads();
+        if (k0 + 32 < P2) load(k0 + 32);
 #pragma unroll 8
         for (int kr = 0; kr < 32; ++kr) {
             const float4 av = *reinterpret_cast<const float4 *>(&sA[kr][4 * jg]);

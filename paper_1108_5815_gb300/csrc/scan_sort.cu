@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(256)
 // ranked (index order), reordered in shared memory by digit, and each digit's
 // run is written contiguously at the digit's global start plus the keys of that
 // digit in earlier tiles.
-__global__ void __launch_bounds__(kSortThreads)
+__global__ void __launch_bounds__(kSortThreads, 2)
     k_radix_pass(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint64_t *__restrict__ kout,
                  uint32_t *__restrict__ vout, int64_t n, int shift, const uint32_t *__restrict__ counts,
                  unsigned long long *status, int *tile_counter, int *flags)
@@ -224,43 +224,55 @@ __global__ void __launch_bounds__(kSortThreads)
     const uint32_t gstart = block_exclusive<uint32_t>(counts[tid], sw, &gtot);  // digit tid's global start
     const unsigned lt_mask = (1u << lane) - 1u;
 
+    // Warp w holds the tile's keys w * 512 .. w * 512 + 511 (item i of lane l at
+    // w * 512 + 32 i + l) and ranks them in index order with warp-private digit
+    // counters; one prefix over the 8 warps per digit then makes the ranks
+    // tile-wide.  Equal digits keep their index order (stable).
+    constexpr int kWarpKeys = kSortItems * 32;
     uint64_t key[kSortItems];
     uint32_t val[kSortItems];
     uint32_t rank[kSortItems];
 #pragma unroll
     for (int i = 0; i < kSortItems; ++i) {
-        const int li = i * kSortThreads + tid;
+        const int li = warp * kWarpKeys + i * 32 + lane;
         const bool valid = li < tile_n;
         key[i] = valid ? kin[base + li] : ~0ull;
         val[i] = valid ? vin[base + li] : 0u;
     }
+    for (int d = tid; d < 8 * kRadix; d += kSortThreads) wcnt[d] = 0;
+    __syncthreads();
+    uint32_t *wc = wcnt + warp * kRadix;
+#pragma unroll
     for (int i = 0; i < kSortItems; ++i) {
-        for (int d = tid; d < 8 * kRadix; d += kSortThreads) wcnt[d] = 0;
-        __syncthreads();
-        const int li = i * kSortThreads + tid;
+        const int li = warp * kWarpKeys + i * 32 + lane;
         const bool valid = li < tile_n;
         const uint32_t dig = (uint32_t)(key[i] >> shift) & 0xffu;
         const unsigned active = __ballot_sync(0xffffffffu, valid);
-        unsigned peers = __match_any_sync(0xffffffffu, valid ? dig : 0x100u);
-        peers &= active;
-        uint32_t lr = __popc(peers & lt_mask);
-        if (valid && lr == 0) wcnt[warp * kRadix + dig] = __popc(peers);
-        __syncthreads();
-        // per digit: exclusive prefix over the 8 warps, then add the running count
-        {
-            const int d = tid;
-            uint32_t acc = run[d];
+        const unsigned peers = __match_any_sync(0xffffffffu, valid ? dig : 0x100u) & active;
+        const uint32_t lr = __popc(peers & lt_mask);
+        rank[i] = valid ? wc[dig] + lr : 0u;
+        __syncwarp();
+        if (valid && lr == 0) wc[dig] += __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    // per digit: exclusive prefix over the 8 warps; run[] = the tile's count
+    {
+        const int d = tid;
+        uint32_t acc = 0;
 #pragma unroll
-            for (int w = 0; w < 8; ++w) {
-                uint32_t c = wcnt[w * kRadix + d];
-                wcnt[w * kRadix + d] = acc;
-                acc += c;
-            }
-            run[d] = acc;
+        for (int w = 0; w < 8; ++w) {
+            const uint32_t c = wcnt[w * kRadix + d];
+            wcnt[w * kRadix + d] = acc;
+            acc += c;
         }
-        __syncthreads();
-        rank[i] = valid ? wcnt[warp * kRadix + dig] + lr : 0u;
-        __syncthreads();
+        run[d] = acc;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < kSortItems; ++i) {
+        const int li = warp * kWarpKeys + i * 32 + lane;
+        if (li < tile_n) rank[i] += wc[(uint32_t)(key[i] >> shift) & 0xffu];
     }
 
     // this tile's count of digit tid, published; then the earlier tiles' counts
@@ -301,7 +313,7 @@ __global__ void __launch_bounds__(kSortThreads)
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < kSortItems; ++i) {
-        const int li = i * kSortThreads + tid;
+        const int li = warp * kWarpKeys + i * 32 + lane;
         if (li < tile_n) {
             const uint32_t dig = (uint32_t)(key[i] >> shift) & 0xffu;
             const uint32_t pos = tile_off[dig] + rank[i];

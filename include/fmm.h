@@ -103,7 +103,12 @@ typedef struct {
     int64_t n_m2l_pairs, n_offset_classes;   /* cell pairs; distinct translation offsets */
     int64_t n_m2l_blocks;                    /* (target tile, offset class) GEMM blocks */
     int64_t n_launches;                      /* kernels this library launched for the solve */
-    /* per-phase device time in ms (measured with events when stats are requested) */
+    /* per-phase device time in ms (measured with events when stats are requested):
+     * ms_tree keys, sort and tree; ms_traverse the dual-tree traversal; ms_upward
+     * P2M and M2M; ms_m2l the M2L kernel and its unit reduction; ms_downward L2L
+     * and L2P; ms_p2p the P2P kernel, which runs beside the far-field chain (the
+     * offset classes and tiles are built on the far-field stream while P2P runs
+     * and are in no phase); ms_total the whole solve */
     float ms_tree, ms_upward, ms_traverse, ms_m2l, ms_downward, ms_p2p, ms_total;
     int64_t n_m2p_pairs; /* (target leaf, source cell) cell-particle pairs */
     int64_t n_p2l_pairs; /* (target cell, source cell) particle-cell pairs */

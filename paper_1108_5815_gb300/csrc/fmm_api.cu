@@ -405,7 +405,7 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
         FMM_LAUNCH_CHECK();
         radix_sort_pairs(blvl, bpos, keys_alt, idx_alt, N - 1, 8, hist, flags, st);
     }
-    k_level_starts<<<1, 32, 0, st>>>(blvl, N - 1, bstart);
+    k_level_starts<<<1, 32 * kLevelStartWarps, 0, st>>>(blvl, N - 1, bstart);
     FMM_LAUNCH_CHECK();
     std::vector<int> lstart;
     int tiles_total = 0;

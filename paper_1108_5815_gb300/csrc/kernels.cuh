@@ -86,6 +86,7 @@ __global__ void k_init_roots(CellArrays c, const int *off, int nsys);
 __global__ void k_permute(const float *xyz, const float *q, const uint32_t *idx, int64_t n,
                           float4 *out);
 __global__ void k_first_diff(const uint64_t *keys, int64_t n, uint64_t *lvl, uint32_t *pos);
+constexpr int kLevelStartWarps = 24;  // levels 0 .. 23, one warp each
 __global__ void k_level_starts(const uint64_t *lvl, int64_t n, int *start);
 // With sz: the level's cells come from sz, packed has len entries (zero past the
 // level) and emission stops at the level end sz clamps to.

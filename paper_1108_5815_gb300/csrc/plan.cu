@@ -75,7 +75,7 @@ void enqueue_plan(const PlanShape &s, const PlanBuffers &b, cudaStream_t st, cud
         FMM_LAUNCH_CHECK();
         radix_sort_pairs(b.blvl, b.bpos, b.keys_alt, b.idx_alt, N - 1, 8, b.hist, b.flags, st);
     }
-    k_level_starts<<<1, 32, 0, st>>>(b.blvl, N - 1, b.bstart);
+    k_level_starts<<<1, 32 * kLevelStartWarps, 0, st>>>(b.blvl, N - 1, b.bstart);
     FMM_LAUNCH_CHECK();
     for (int l = 0; l <= s.levels; ++l) {
         const int len = s.level_cap[l];

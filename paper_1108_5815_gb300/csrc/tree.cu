@@ -277,19 +277,30 @@ __global__ void k_first_diff(const uint64_t *__restrict__ keys, int64_t n,
 }
 
 // start[L] = first index of level L in the (stably) level-sorted boundary list.
+// Warp L searches for it 32 probes at a time: each round narrows [lo, hi) to one
+// of 32 equal steps, so a million entries take four dependent loads, not twenty.
 __global__ void k_level_starts(const uint64_t *__restrict__ lvl, int64_t n, int *__restrict__ start)
 {
-    const int L = threadIdx.x;
-    if (L > 23) return;
-    int64_t lo = 0, hi = n;
-    while (lo < hi) {
-        const int64_t mid = (lo + hi) >> 1;
-        if (lvl[mid] < (uint64_t)L)
-            lo = mid + 1;
-        else
-            hi = mid;
+    const int L = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (L >= kLevelStartWarps) return;
+    int64_t lo = 0, hi = n;  // the answer lies in [lo, hi]
+    while (hi - lo > 32) {
+        const int64_t step = (hi - lo + 31) / 32;
+        const int64_t pos = lo + lane * step;
+        const bool below = pos < hi && lvl[pos] < (uint64_t)L;
+        const int c = __popc(__ballot_sync(0xffffffffu, below));  // probes below L: a prefix
+        if (c == 0) {
+            hi = lo;
+        } else {
+            const int64_t last = lo + (int64_t)(c - 1) * step;  // the last probe below L
+            hi = min(hi, last + step);
+            lo = last + 1;
+        }
     }
-    start[L] = (int)lo;
+    const int64_t pos = lo + lane;
+    const bool below = pos < hi && lvl[pos] < (uint64_t)L;
+    const int c = __popc(__ballot_sync(0xffffffffu, below));
+    if (lane == 0) start[L] = (int)(lo + c);
 }
 
 __device__ __forceinline__ int lower_pos(const uint32_t *__restrict__ B, int nb, uint32_t v)

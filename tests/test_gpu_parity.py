@@ -66,6 +66,26 @@ def test_structure_and_fields_match_oracle(name, dist, n, p, theta, ncrit, md):
     assert rel_l2(grad, ograd) < TOL_ORACLE
 
 
+def test_many_equal_keys_sort_stably_and_match_oracle():
+    # 20,000 particles on 512 lattice sites (about 39 coincident particles per
+    # site): the key sort meets long runs of equal keys inside and across its
+    # 4,096-key tiles, and must keep them in index order, as the oracle's stable
+    # sort does.  Coincident pairs contribute nothing on either side.
+    rng = np.random.default_rng(2024)
+    sites = (np.stack(np.meshgrid(*[np.arange(8)] * 3, indexing="ij"), -1).reshape(-1, 3) + 0.5) / 8
+    x = sites[rng.integers(0, len(sites), 20000)].astype(np.float32)
+    q = rng.uniform(-1.0, 1.0, 20000).astype(np.float32)
+    p, theta, ncrit, md = 5, 0.5, 16, 6
+    phi, grad = gpu_solve(x, q, p, theta, ncrit, max_depth=md)
+    f = O.Fmm(x, q, p, theta, ncrit, max_depth=md)
+    key, order = f.sorted()
+    assert len(np.unique(key)) == len(sites)
+    _compare_structure(f)
+    ophi, ograd = f.evaluate()
+    assert rel_l2(phi, ophi) < TOL_ORACLE
+    assert rel_l2(grad, ograd) < TOL_ORACLE
+
+
 def test_expansions_match_oracle():
     from paper_1108_5815_gb300 import fmm
     n, p, theta, ncrit = 20000, 7, 0.5, 32

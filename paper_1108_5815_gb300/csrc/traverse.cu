@@ -523,9 +523,16 @@ __global__ void k_m2l_class(uint32_t *__restrict__ m2l_slot, int64_t n,
                             const int *__restrict__ slot_class, const unsigned long long *__restrict__ dn)
 {
     if (dn) n = (int64_t)*dn;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x)
-        m2l_slot[i] = (uint32_t)slot_class[m2l_slot[i]];
+    // four elements per thread and round, their loads issued together
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += 4 * stride) {
+        uint32_t sl[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) sl[u] = i0 + u * stride < n ? m2l_slot[i0 + u * stride] : 0u;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (i0 + u * stride < n) m2l_slot[i0 + u * stride] = (uint32_t)slot_class[sl[u]];
+    }
 }
 
 // ---------------------------------------------------------------- tiles
@@ -594,15 +601,31 @@ __global__ void k_tile_src(const int *__restrict__ m2l_tgt, const int *__restric
                            int *__restrict__ src, const unsigned long long *__restrict__ dn, int entry_cap)
 {
     if (dn) n = (int64_t)*dn;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int t = m2l_tgt[i];
-        const uint32_t cl = m2l_class[i];
-        const int tile = cell_tile[t];
-        const int64_t wi = (int64_t)tile * nwords + (cl >> 5);
-        const uint32_t below = bitmap[wi] & ((1u << (cl & 31)) - 1u);
-        const int e = word_prefix[wi] + __popc(below);
-        if (e < entry_cap) src[(int64_t)e * kTile + cell_lane[t]] = m2l_src[i];
+    // four elements per thread and round, each level of their dependent loads issued together
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += 4 * stride) {
+        int t[4], s4[4], tile[4], lane[4];
+        uint32_t cl[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const bool ok = i0 + u * stride < n;
+            t[u] = ok ? m2l_tgt[i0 + u * stride] : -1;
+            cl[u] = ok ? m2l_class[i0 + u * stride] : 0u;
+            s4[u] = ok ? m2l_src[i0 + u * stride] : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            tile[u] = t[u] >= 0 ? cell_tile[t[u]] : 0;
+            lane[u] = t[u] >= 0 ? cell_lane[t[u]] : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (t[u] < 0) continue;
+            const int64_t wi = (int64_t)tile[u] * nwords + (cl[u] >> 5);
+            const uint32_t below = bitmap[wi] & ((1u << (cl[u] & 31)) - 1u);
+            const int e = word_prefix[wi] + __popc(below);
+            if (e < entry_cap) src[(int64_t)e * kTile + lane[u]] = s4[u];
+        }
     }
 }
 

@@ -293,6 +293,18 @@ class ClockSampler:
                 stdout=self.fh, stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
+        # nvidia-smi takes a while to start: wait (up to 5 s) for its first sample, so
+        # that the samples after it fall inside the timed region that follows
+        self.skip = 0
+        if self.proc is not None:
+            t0 = time.time()
+            while time.time() - t0 < 5.0 and self.proc.poll() is None:
+                with open(self.path) as f:
+                    n = sum(1 for line in f if line.strip())
+                if n:
+                    self.skip = n
+                    break
+                time.sleep(0.01)
         return self
 
     def __exit__(self, *exc):
@@ -314,6 +326,8 @@ class ClockSampler:
             if len(parts) >= 8:
                 rows.append(parts)
         os.unlink(self.path)
+        if len(rows) > self.skip:
+            rows = rows[self.skip:]  # the samples taken before the timed region started
         if not rows:
             return None
         sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]

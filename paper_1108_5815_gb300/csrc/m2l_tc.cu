@@ -14,9 +14,12 @@
 // The tensor core's accumulation rounds toward zero, so long accumulations in
 // tensor memory drift.  Following the error-corrected split of Ootomo & Yokota
 // (2022), the main products ah*bh and the correction products ah*bl + al*bh go
-// to two separate accumulators, each restarted at every offset-class block, and
-// the blocks are summed with round-to-nearest FP32 adds into a running sum held
-// in a third tensor-memory region (in the partial buffer when 3N columns do not fit).
+// to two separate accumulators.  The main one restarts at every offset-class
+// block, and the blocks are summed with round-to-nearest FP32 adds into a running
+// sum held in a third tensor-memory region (in the partial buffer when 3N columns
+// do not fit).  The correction (about 2^-8 of the main product in BF16, 2^-11 in
+// TF32) runs over all blocks of a work unit when N <= 128 and restarts with the
+// main one otherwise.
 //
 // The class matrices B are split into hi/lo once (k_split_tables), already in
 // the shared-memory layout of a stage, so a stage's B is two bulk asynchronous

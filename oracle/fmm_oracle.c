@@ -21,7 +21,7 @@
  *     "Hybrid treecode/FMM algorithm": "Our kernels are based on spherical
  *     harmonic expansions") -- P2M, M2M, M2L, L2L, L2P, M2P and P2P.
  *
- * Readings taken where the paper is silent (each is also listed in the design doc):
+ * Readings taken where the paper is silent:
  *   R1 quantisation: box = [lo, lo+side)^3 with lo = per-axis minimum,
  *      side = largest extent (1 if zero); k_d = min(2^21-1, floor((x_d-lo_d)*s)),
  *      s = 2^21/side, each a single IEEE FP64 operation; key bit 3b+a = bit b of k_a
@@ -34,8 +34,10 @@
  *      3x3x3 neighbour list.
  *   R4 traversal: interact(T,S) = MAC -> cell-cell (M2L); else both leaves ->
  *      particle-particle (P2P); else push.  Pop -> split the larger cell (target
- *      on a tie; the other one if the chosen cell is a leaf).  A flag selects the
- *      literal "leaf pair first" order of the prose for comparison.
+ *      on a tie; the other one if the chosen cell is a leaf).  Flags select the
+ *      literal "leaf pair first" order of the prose for comparison and, for
+ *      the tests that show the split rule is pinned, two wrong split rules
+ *      (split the smaller cell; split the source on a tie).
  *   R5 expansion centres are the geometric cell centres; truncation is n <= p
  *      for both multipole and local expansions.
  *   R6 coincident pairs (r = 0) contribute nothing.
@@ -94,6 +96,12 @@ typedef double complex cplx;
 #define ORC_KBITS 21
 #define ORC_KMAX ((1LL << ORC_KBITS) - 1)
 #define ORC_SEL_NB 128
+
+/* flags of orc_fmm_create: the literal leaf-first order of the prose, and two
+ * wrong split rules that exist only so that tests can show they are caught */
+#define ORC_LEAF_FIRST 1
+#define ORC_SPLIT_SMALLER 2
+#define ORC_SPLIT_SOURCE_ON_TIE 4
 
 static inline int hidx(int n, int m) { return n * n + n + m; }
 static inline int nterms(int p) { return (p + 1) * (p + 1); }
@@ -409,7 +417,7 @@ static int cmp_keyidx(const void *a, const void *b)
 
 typedef struct {
     int64_t N;
-    int p, ncrit, max_depth, leaf_first;
+    int p, ncrit, max_depth, leaf_first, split_variant;
     double theta;
     const unsigned char *sel; /* hybrid selection table (R9), NULL = plain FMM */
     double lo[3], side;
@@ -609,7 +617,23 @@ static void traverse(orc_fmm *f)
         --st.n;
         int64_t T = st.t[st.n], S = st.s[st.n];
         int split_source;
-        if (is_leaf(f, T))
+        if (f->split_variant == ORC_SPLIT_SMALLER) {
+            /* planted mistake (tests only): split the smaller cell */
+            if (is_leaf(f, T))
+                split_source = 1;
+            else if (f->level[S] > f->level[T] && !is_leaf(f, S))
+                split_source = 1;
+            else
+                split_source = 0;
+        } else if (f->split_variant == ORC_SPLIT_SOURCE_ON_TIE) {
+            /* planted mistake (tests only): the source on a tie */
+            if (is_leaf(f, T))
+                split_source = 1;
+            else if (f->level[S] <= f->level[T] && !is_leaf(f, S))
+                split_source = 1;
+            else
+                split_source = 0;
+        } else if (is_leaf(f, T))
             split_source = 1;
         else if (f->level[S] < f->level[T] && !is_leaf(f, S))
             split_source = 1;
@@ -630,7 +654,7 @@ static void traverse(orc_fmm *f)
 /* Build keys, sorted order, tree and interaction lists.  Returns 0 on success,
  * 1 for a non-finite coordinate. */
 orc_fmm *orc_fmm_create(int64_t N, const double *xyz, const double *q, int p, double theta,
-                        int ncrit, int max_depth, int leaf_first, const unsigned char *sel,
+                        int ncrit, int max_depth, int flags, const unsigned char *sel,
                         int *status)
 {
     orc_fmm *f = calloc(1, sizeof(orc_fmm));
@@ -640,7 +664,8 @@ orc_fmm *orc_fmm_create(int64_t N, const double *xyz, const double *q, int p, do
     f->theta = theta;
     f->ncrit = ncrit;
     f->max_depth = max_depth;
-    f->leaf_first = leaf_first;
+    f->leaf_first = flags & ORC_LEAF_FIRST;
+    f->split_variant = flags & (ORC_SPLIT_SMALLER | ORC_SPLIT_SOURCE_ON_TIE);
     uint64_t *key = malloc(sizeof(uint64_t) * N);
     if (orc_morton_keys(N, xyz, f->lo, &f->side, key)) {
         free(key);

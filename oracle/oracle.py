@@ -236,9 +236,16 @@ class Fmm:
     """Oracle FMM: keys, tree and interaction lists are built on construction;
     ``evaluate()`` runs the upward and downward passes."""
 
-    def __init__(self, xyz, q, p, theta, ncrit, max_depth=21, leaf_first=False, sel=None):
+    SPLIT_RULES = {"paper": 0, "smaller": 2, "source_on_tie": 4}
+
+    def __init__(self, xyz, q, p, theta, ncrit, max_depth=21, leaf_first=False, sel=None,
+                 split_rule="paper"):
         """``sel``: optional hybrid selection table (reading R9), uint8 [128, 128]
-        indexed by the count buckets of (target, source); 1 = P2P for a MAC-accepted pair."""
+        indexed by the count buckets of (target, source); 1 = P2P for a MAC-accepted pair.
+
+        ``split_rule``: "paper" (split the larger cell, the target on a tie) is the
+        traversal; "smaller" and "source_on_tie" are deliberately wrong rules that
+        only the tests use, to show that the pair-set pins catch them."""
         self.xyz = _f64(xyz, (-1, 3))
         self.q = _f64(q, (-1,))
         self.p = p
@@ -248,7 +255,9 @@ class Fmm:
             sel = np.ascontiguousarray(np.asarray(sel, dtype=np.uint8).reshape(SEL_NB, SEL_NB))
             selp = sel.ctypes.data
         self._h = lib().orc_fmm_create(self.xyz.shape[0], _d(self.xyz), _d(self.q), p, theta,
-                                       ncrit, max_depth, int(leaf_first), selp, ctypes.byref(st))
+                                       ncrit, max_depth,
+                                       int(leaf_first) | self.SPLIT_RULES[split_rule], selp,
+                                       ctypes.byref(st))
         if st.value != 0 or not self._h:
             self._h = None
             raise ValueError("non-finite coordinate")

@@ -31,6 +31,20 @@ def rel_l2(a, b):
     return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
 
 
+def assert_pointwise(phi, ophi, grad, ograd, tol=1e-4):
+    """Worst particle, beside the relative L2 norm: max_i |phi_i - phi*_i| <=
+    tol * max_j |phi*_j|, and the same for the gradient vectors (Euclidean
+    length per particle), so that a few bad targets cannot hide under the norm."""
+    phi, grad = np.asarray(phi, np.float64), np.asarray(grad, np.float64).reshape(-1, 3)
+    ograd = np.asarray(ograd, np.float64).reshape(-1, 3)
+    ep = np.abs(phi - ophi).max()
+    eg = np.linalg.norm(grad - ograd, axis=1).max()
+    sp = np.abs(ophi).max()
+    sg = np.linalg.norm(ograd, axis=1).max()
+    assert ep <= tol * sp, f"worst |dphi| {ep:.3e} > {tol} * {sp:.3e}"
+    assert eg <= tol * sg, f"worst |dgrad| {eg:.3e} > {tol} * {sg:.3e}"
+
+
 def canonical_ids(level, prefix):
     """Rank of each cell in (level, prefix) order -- identical for both sides
     when the cell sets agree."""

@@ -10,12 +10,14 @@ import pytest
 
 from oracle import oracle as O
 from paper_1108_5815_gb300 import inputs
-from tests.gpu_helpers import (canonical_ids, gpu_cells, gpu_solve, oracle_to_gpu_layout,
-                               pair_codes, rel_l2)
+from tests.gpu_helpers import (assert_pointwise, canonical_ids, gpu_cells, gpu_solve,
+                               oracle_to_gpu_layout, pair_codes, rel_l2)
+from tests.test_oracle_traversal import _chain6, _named_pairs, chain6_expected
 
 pytestmark = pytest.mark.gpu
 
 TOL_ORACLE = 1e-5   # rel-L2 vs the FP64 oracle at equal p, theta (FP32 path)
+TOL_POINT = 1e-4    # worst particle, relative to the largest value (phi) or length (grad)
 
 
 def _compare_structure(f, ncells_expected=None):
@@ -64,6 +66,24 @@ def test_structure_and_fields_match_oracle(name, dist, n, p, theta, ncrit, md):
     ophi, ograd = f.evaluate()
     assert rel_l2(phi, ophi) < TOL_ORACLE
     assert rel_l2(grad, ograd) < TOL_ORACLE
+    assert_pointwise(phi, ophi, grad, ograd, TOL_POINT)
+
+
+def test_split_rule_hand_derived_lists_on_gpu():
+    # The six-particle adaptive tree whose interaction lists were written out by
+    # hand from the traversal's split rule (the larger cell, the target on a tie):
+    # the GPU traversal must give exactly those lists, and the fields must match.
+    from paper_1108_5815_gb300 import fmm
+    g, x, q = _chain6()
+    _, names, m2l, p2p = chain6_expected()
+    phi, grad = gpu_solve(x, q, 2, g["theta"], g["ncrit"], max_depth=g["max_depth"])
+    gc = gpu_cells()
+    gp, gm = fmm.export("p2p"), fmm.export("m2l")
+    assert _named_pairs(gc["level"], gc["prefix"], gm[:, 0], gm[:, 1], names) == m2l
+    assert _named_pairs(gc["level"], gc["prefix"], gp[:, 0], gp[:, 1], names) == p2p
+    f = O.Fmm(x, q, 2, g["theta"], g["ncrit"], max_depth=g["max_depth"])
+    ophi, ograd = f.evaluate()
+    assert rel_l2(phi, ophi) < TOL_ORACLE and rel_l2(grad, ograd) < TOL_ORACLE
 
 
 def test_many_equal_keys_sort_stably_and_match_oracle():
@@ -84,6 +104,7 @@ def test_many_equal_keys_sort_stably_and_match_oracle():
     ophi, ograd = f.evaluate()
     assert rel_l2(phi, ophi) < TOL_ORACLE
     assert rel_l2(grad, ograd) < TOL_ORACLE
+    assert_pointwise(phi, ophi, grad, ograd, TOL_POINT)
 
 
 def test_expansions_match_oracle():
@@ -165,6 +186,7 @@ def test_tensor_core_m2l_matches_oracle(precision, tol, dist, n, p, theta, ncrit
     ophi, ograd = f.evaluate()
     assert rel_l2(phi, ophi) < tol
     assert rel_l2(grad, ograd) < tol
+    assert_pointwise(phi, ophi, grad, ograd, TOL_POINT)
 
 
 def test_tensor_core_m2l_deterministic():

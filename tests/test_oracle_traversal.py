@@ -87,3 +87,71 @@ def test_lists_are_order_n():
     m2l = [a for a, _ in per]
     p2p = [b for _, b in per]
     assert max(m2l) < 2.0 * min(m2l) and max(p2p) < 2.0 * min(p2p)
+
+
+def _chain6():
+    """The hand-built adaptive tree of tests/golden/split_rule_chain6.json."""
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "split_rule_chain6.json")))
+    x = np.zeros((len(g["points_x"]), 3), dtype=np.float32)
+    x[:, 0] = g["points_x"]
+    x[:, 1:] = g["points_yz"]
+    q = np.linspace(-1.0, 1.0, len(x)).astype(np.float32)
+    return g, x, q
+
+
+def _named_pairs(level, prefix, t, s, names):
+    k = cell_index(level, prefix)
+    name = {}
+    for c in range(len(level)):
+        assert k[c][1] == 0 and k[c][2] == 0
+        name[c] = names[(int(level[c]), int(k[c][0]))]
+    return sorted((name[a], name[b]) for a, b in zip(t, s))
+
+
+def chain6_expected():
+    g, _, _ = _chain6()
+    names = {tuple(v): n for n, v in g["cells"].items()}
+    return g, names, sorted(map(tuple, g["m2l"])), sorted(map(tuple, g["p2p"]))
+
+
+def test_split_rule_matches_hand_derived_lists():
+    # The split rule (the larger cell; the target on a tie; the other cell when the
+    # chosen one is a leaf) fixes which pairs reach the lists; the expected lists
+    # were derived by hand for a six-particle adaptive tree.
+    g, x, q = _chain6()
+    _, names, m2l, p2p = chain6_expected()
+    f = O.Fmm(x, q, 2, g["theta"], g["ncrit"], max_depth=g["max_depth"])
+    c, L = f.cells(), f.lists()
+    assert sorted(names) == sorted((int(a), int(b)) for a, b in
+                                   zip(c["level"], cell_index(c["level"], c["prefix"])[:, 0]))
+    assert _named_pairs(c["level"], c["prefix"], L["m2l_t"], L["m2l_s"], names) == m2l
+    assert _named_pairs(c["level"], c["prefix"], L["p2p_t"], L["p2p_s"], names) == p2p
+
+
+@pytest.mark.parametrize("rule", ["smaller", "source_on_tie"])
+def test_wrong_split_rules_fail_the_hand_derived_lists(rule):
+    # A traversal that splits the smaller cell, or the source on a tie, still
+    # covers every particle pair exactly once (so the coverage pins cannot tell
+    # it apart), but its lists differ from the hand-derived ones.
+    g, x, q = _chain6()
+    _, names, m2l, p2p = chain6_expected()
+    f = O.Fmm(x, q, 2, g["theta"], g["ncrit"], max_depth=g["max_depth"], split_rule=rule)
+    c, L = f.cells(), f.lists()
+    assert np.all(coverage_matrix(f.N, c, L) == 1)
+    got = (_named_pairs(c["level"], c["prefix"], L["m2l_t"], L["m2l_s"], names),
+           _named_pairs(c["level"], c["prefix"], L["p2p_t"], L["p2p_s"], names))
+    assert got != (m2l, p2p)
+
+
+@pytest.mark.parametrize("rule", ["smaller", "source_on_tie"])
+def test_wrong_split_rules_change_lists_on_random_trees(rule):
+    # the same on a Plummer tree: some (target, source) pair set differs
+    x, q = inputs.plummer(3000, 31)
+    a = O.Fmm(x, q, 2, 0.6, 8)
+    b = O.Fmm(x, q, 2, 0.6, 8, split_rule=rule)
+    la, lb = a.lists(), b.lists()
+    ka = set(zip(la["m2l_t"].tolist(), la["m2l_s"].tolist()))
+    kb = set(zip(lb["m2l_t"].tolist(), lb["m2l_s"].tolist()))
+    assert ka != kb

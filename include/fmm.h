@@ -298,12 +298,20 @@ fmm_status fmm_cost_model_samples(float *x, float *t, float *m, int64_t capacity
  *   box   device double [4]  out: lo_x, lo_y, lo_z, side of the cubic box
  * Results equal FMM_EXPORT_KEYS / FMM_EXPORT_ORDER / FMM_EXPORT_BOX of a
  * solve on the same points.  A NaN/Inf coordinate gives FMM_ERR_NONFINITE.
- * The scratch array (16,786,176 bytes) exists on every device that loads the
- * library until the process exits.  The first call on a device resolves its
- * address with cudaGetSymbolAddress; make that first call before any stream
- * capture.  All calls share the array, so calls whose GPU work overlaps (on
- * different streams or threads) race and must be serialised by the caller.
- * The call synchronises `stream` before returning. */
+ * The scratch array is 16,786,176 bytes.  It is placed in a device's memory
+ * when the library's module is loaded on that device; under CUDA's lazy module
+ * loading (the default since CUDA 12.2) that happens at the first use of the
+ * module there -- in practice the set-up of this entry point's first call on
+ * the device (cudaGetSymbolAddress), together with the code of the kernels it
+ * launches -- not when the library is loaded into the process.  So the FIRST
+ * call on each device does take device memory: a caller that may not allocate
+ * after start-up makes one call per device during its initialisation, before
+ * any stream capture begins.  From then on the array stays until the process
+ * exits, and later calls allocate nothing.  All calls share the array and it
+ * keeps the last call's contents (whatever must start at zero is cleared on
+ * every call), so calls whose GPU work overlaps (on different streams or
+ * threads) race and must be serialised by the caller.  The call synchronises
+ * `stream` before returning. */
 fmm_status fmm_morton_sort_noalloc(const float *xyz, int64_t N, uint64_t *keys, int32_t *order,
                                    double *box, void *stream);
 

@@ -13,8 +13,11 @@
 // The scratch holds the sort's second key/index buffers, digit counts and
 // look-back words, the box and the flags for up to kNoAllocMaxN points.  It is
 // resolved to a device address with cudaGetSymbolAddress once per device, on
-// that device's first call.  All calls share it and it keeps the previous
-// call's contents; everything that must start at zero is cleared on every call.
+// that device's first call.  Under lazy module loading (CUDA's default) the
+// array itself is placed in device memory at that first use of the module on
+// the device, so the first call per device belongs in the caller's
+// initialisation.  All calls share it and it keeps the previous call's
+// contents; everything that must start at zero is cleared on every call.
 #include <algorithm>
 #include <mutex>
 

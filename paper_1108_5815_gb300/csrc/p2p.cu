@@ -7,11 +7,16 @@
 // the layout of Nyland et al. that the paper recounts): no reduction across
 // threads, source tiles staged through shared memory and broadcast.
 //
-// Per interaction: 3 FADD for the offset, 3 for r^2, one MUFU rsqrt with one
-// Newton step y <- y (3/2 - r^2 y^2 / 2), then phi += q y and
-// grad += q y^3 d.  Pairs at r = 0 (the particle itself, coincident points)
-// contribute nothing: rsqrt(0) = inf makes the Newton step NaN and
-// max(NaN, 0) = 0 removes it without a branch.  Only a chunk holding sources of
+// Per interaction: 3 FADD for the offset, 3 for r^2, one MUFU rsqrt y0 and one
+// Newton step y = y0 (3 - r^2 y0^2) / 2, then phi += q y and grad += q y^3 d.
+// The step is taken without its factor -1/2: z = y0 (r^2 y0^2 - 3) = -2 y is
+// three operations (y0^2, one FMA, one product), the charge is staged as -q/2
+// so that u = (-q/2) z = q y, phi += u, w = u z^2 = 4 q y^3, and grad += w d
+// sums 4 q y^3 d, scaled by 1/4 once per target at the end (exact: a power of
+// two).  16 FP32-pipe lane operations per interaction instead of 17.  Pairs at
+// r = 0 (the particle itself, coincident points) contribute nothing:
+// rsqrt(0) = inf makes the Newton step NaN and min(NaN, 0) = 0 removes it
+// without a branch (valid z are negative).  Only a chunk holding sources of
 // the target's own leaf can hold the particle itself, so only those chunks take
 // the guard; a pass that still ends with a non-finite sum (a pair at r = 0 in
 // two leaves, r^2 flushed to zero, a target at the origin meeting the zero
@@ -76,39 +81,38 @@ __device__ __forceinline__ f2 f2fma(f2 a, f2 b, f2 c)
 }
 
 struct Target2 {
-    f2 x, y, z;          // the target's coordinates in both halves
-    f2 mhalf, threehalf; // (-1/2, -1/2), (3/2, 3/2)
+    f2 x, y, z;  // the target's coordinates in both halves
+    f2 mthree;   // (-3, -3)
 };
 
 __device__ __forceinline__ Target2 target2(float4 xi)
 {
-    return {f2pack(xi.x, xi.x), f2pack(xi.y, xi.y), f2pack(xi.z, xi.z), f2pack(-0.5f, -0.5f),
-            f2pack(1.5f, 1.5f)};
+    return {f2pack(xi.x, xi.x), f2pack(xi.y, xi.y), f2pack(xi.z, xi.z), f2pack(-3.f, -3.f)};
 }
 
-// The target against two sources (packed x, y, z, q); accumulators packed per source.
+// The target against two sources (packed x, y, z and staged charge -q/2);
+// accumulators packed per source: phi and 4 x grad.
 template <bool GUARD>
-__device__ __forceinline__ void p2p_interact2(const Target2 &T, f2 sx, f2 sy, f2 sz, f2 sq, f2 &phi,
+__device__ __forceinline__ void p2p_interact2(const Target2 &T, f2 sx, f2 sy, f2 sz, f2 sqn, f2 &phi,
                                               f2 &gx, f2 &gy, f2 &gz)
 {
     const f2 dx = f2sub(sx, T.x), dy = f2sub(sy, T.y), dz = f2sub(sz, T.z);
     const f2 r2 = f2fma(dz, dz, f2fma(dy, dy, f2mul(dx, dx)));
     float ra, rb;
     f2unpack(r2, ra, rb);
-    f2 y = f2pack(rsqrt_approx(ra), rsqrt_approx(rb));
-    const f2 t = f2mul(f2mul(r2, y), y);
-    y = f2mul(y, f2fma(T.mhalf, t, T.threehalf));
+    const f2 y0 = f2pack(rsqrt_approx(ra), rsqrt_approx(rb));
+    f2 z = f2mul(y0, f2fma(r2, f2mul(y0, y0), T.mthree));  // -2 y
     if (GUARD) {
-        float ya, yb;
-        f2unpack(y, ya, yb);
-        y = f2pack(fmaxf(ya, 0.f), fmaxf(yb, 0.f));
+        float za, zb;
+        f2unpack(z, za, zb);
+        z = f2pack(fminf(za, 0.f), fminf(zb, 0.f));
     }
-    const f2 qy = f2mul(sq, y);
-    phi = f2add(phi, qy);
-    const f2 qy3 = f2mul(f2mul(qy, y), y);
-    gx = f2fma(qy3, dx, gx);
-    gy = f2fma(qy3, dy, gy);
-    gz = f2fma(qy3, dz, gz);
+    const f2 u = f2mul(sqn, z);  // q y
+    phi = f2add(phi, u);
+    const f2 w = f2mul(u, f2mul(z, z));  // 4 q y^3
+    gx = f2fma(w, dx, gx);
+    gy = f2fma(w, dy, gy);
+    gz = f2fma(w, dz, gz);
 }
 
 __device__ __forceinline__ float f2sum(f2 v)
@@ -190,8 +194,8 @@ __device__ __forceinline__ float4 fetch_chunk(const Window &w, int s, const floa
     return in ? pts[j] : make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
-// The staged 32 sources against one target: pairs of sources per packed
-// instruction, two accumulator sets (sources 4k, 4k+1 and 4k+2, 4k+3).
+// The staged 32 sources (x, y, z, -q/2) against one target: pairs of sources
+// per packed instruction, two accumulator sets (sources 4k, 4k+1 and 4k+2, 4k+3).
 struct Acc2 {
     f2 phi, gx, gy, gz;
 };
@@ -221,9 +225,10 @@ __device__ __forceinline__ void p2p_run(const Target2 &T, const float *sh, int j
                              a.phi, a.gx, a.gy, a.gz);
 }
 
+// phi and grad of one accumulator set (the gradient sums carry the factor 4)
 __device__ __forceinline__ float4 acc_sum(const Acc2 &a)
 {
-    return make_float4(f2sum(a.phi), f2sum(a.gx), f2sum(a.gy), f2sum(a.gz));
+    return make_float4(f2sum(a.phi), 0.25f * f2sum(a.gx), 0.25f * f2sum(a.gy), 0.25f * f2sum(a.gz));
 }
 
 __device__ __forceinline__ bool nonfinite(float4 v)
@@ -273,7 +278,7 @@ __device__ __forceinline__ void p2p_leaf(const CellArrays &c, const ListArrays &
                 sh[lane] = nx.x;
                 sh[32 + lane] = nx.y;
                 sh[64 + lane] = nx.z;
-                sh[96 + lane] = nx.w;
+                sh[96 + lane] = -0.5f * nx.w;
                 __syncwarp();
                 if (s + 32 < w.total) nx = fetch_chunk(w, s + 32, pts, lane, b, e, own_next);
                 if (guard) {
@@ -379,7 +384,7 @@ __global__ void __launch_bounds__(128, kP2PBlocksPerSM) k_p2p_body(float *__rest
     s[lane] = 0.37f * lane;
     s[32 + lane] = 0.11f * lane + 0.5f;
     s[64 + lane] = 0.05f * lane - 0.3f;
-    s[96 + lane] = 1.0f / (1 + lane);
+    s[96 + lane] = -0.5f / (1 + lane);
     __syncwarp();
     const Target2 T = target2(make_float4(0.013f * threadIdx.x + 40.f, 0.2f, -0.1f, 0.f));
     const f2 zero = 0ull;

@@ -12,10 +12,22 @@ Also reported:
   e2e          the same solve through fmm_laplace3d_host (pinned host buffers,
                host->device and device->host copies inside the timed region)
   roofline     the dominant kernel against the measured/derived peak
-  cpu_baseline the FP64 oracle on the host cores on a bounded sample
+  cpu_baseline the whole FP64 oracle FMM on the same workload on the host
+               cores (measured, one run), the single-core time of the 4,096-point
+               uniform case, and the sampled FP64 direct sum
   clocks       nvidia-smi SM clock samples during the timed region
+  configs      the other workloads, GPU only: Plummer 4M at p = 6/8/12 in each
+               M2L precision (time and error against the FP64 direct sum per p),
+               512 batched systems (tuned schedule, one call, one graph replay,
+               one call per system) and Plummer 16M (learned vs plain selection
+               at the measured-best N_crit, and the plain FP32 FMM)
+  peaks        SM count from the device, the derived FP32 peak, and TF32 / FP64
+               dense GEMM rates measured with cuBLAS in this process
 
---impl reference times the oracle (the reference arm of this project).
+--impl reference times the oracle (the reference arm of this project): each
+step is the whole oracle pipeline (keys, sort, tree, traversal, upward pass)
+plus the evaluation of every 8th leaf (every 8th system for a batch), and the
+line reports the particles evaluated per second of those steps as measured.
 Multi-GPU (torchrun): every rank solves its own replica (the single system is
 not sharded), the reported value is the sum over ranks.
 """
@@ -34,9 +46,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 P2P_FLOPS = 23          # counted flops per P2P interaction (FMA = 2)
-SMS = 152
-FP32_LANES = 128
-SM_MAX_MHZ = 2070.0
+FP32_LANES = 128        # FP32 lanes per SM (4 partitions x 32)
+REF_STRIDE = 8          # the reference arm evaluates every 8th leaf / system per step
 
 
 def parse():
@@ -60,6 +71,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="skip timing the captured plan (graph replay)")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the other workloads (Plummer 4M per p, batched 512, Plummer 16M)")
     return ap.parse_args()
 
 
@@ -92,42 +105,76 @@ def config_of(w, args):
 
 # ------------------------------------------------------------------ oracle timing
 
-def oracle_sample(x, q, w, leaf_stride=128):
-    """Oracle FMM on the full workload with the far/near evaluation restricted to
-    every `leaf_stride`-th leaf; the evaluation time is scaled to all leaves.
-    Returns (particles_per_s, seconds, description)."""
+def oracle_full(x, q, w):
+    """The whole FP64 oracle FMM on the workload (all targets), timed once on all
+    host cores.  Returns (particles_per_s, seconds, description)."""
+    from oracle import oracle as O
+    t0 = time.perf_counter()
+    f = O.Fmm(x, q, w["p"], w["theta"], w["ncrit"], max_depth=w["max_depth"])
+    f.evaluate()
+    t = time.perf_counter() - t0
+    return w["n"] / t, t, (f"the whole oracle FMM on the full workload ({w['n']} particles: keys, sort, "
+                           f"tree, traversal, P2M/M2M, M2L, L2L, L2P, P2P over all {f.ncells} cells), one run")
+
+
+def oracle_full_batched(x, q, off, w):
+    """The oracle FMM on every system of a batch, one after another."""
+    from oracle import oracle as O
+    t0 = time.perf_counter()
+    for sy in range(len(off) - 1):
+        a, b = off[sy], off[sy + 1]
+        O.Fmm(x[a:b], q[a:b], w["p"], w["theta"], w["ncrit"], max_depth=w["max_depth"]).evaluate()
+    t = time.perf_counter() - t0
+    return int(off[-1]) / t, t, f"the oracle FMM on all {len(off) - 1} systems ({int(off[-1])} particles), one run"
+
+
+def oracle_single_core_config1():
+    """Single-core time of the oracle FMM on the 4,096-point uniform case (p = 4,
+    theta = 0.5, ncrit = 64): median of three runs."""
+    from oracle import oracle as O
+    from paper_1108_5815_gb300 import inputs
+    w = inputs.WORKLOADS["uniform4k"]
+    x, q = inputs.make(w["kind"], w["n"], w["seed"])
+    nt = O.num_threads()
+    O.set_num_threads(1)
+    try:
+        ts = []
+        for _ in range(3):
+            t0 = time.perf_counter()
+            O.Fmm(x, q, w["p"], w["theta"], w["ncrit"], max_depth=w["max_depth"]).evaluate()
+            ts.append(time.perf_counter() - t0)
+    finally:
+        O.set_num_threads(nt)
+    return statistics.median(ts)
+
+
+def oracle_step(x, q, w, k, stride=REF_STRIDE):
+    """One step of the reference arm: the oracle's keys, sort, tree, traversal and
+    upward pass over the whole workload, then the far/near evaluation of the
+    leaves k, k+stride, ... (a different slice each step).  Returns (particles
+    evaluated, seconds)."""
     import numpy as np
     from oracle import oracle as O
     t0 = time.perf_counter()
     f = O.Fmm(x, q, w["p"], w["theta"], w["ncrit"], max_depth=w["max_depth"])
     f.upward()
-    t1 = time.perf_counter()
     c = f.cells()
     leaves = np.flatnonzero(c["nchild"] == 0)
-    pick = leaves[::leaf_stride]
-    f.evaluate_leaves(pick)
-    t2 = time.perf_counter()
-    t_total = (t1 - t0) + (t2 - t1) * (len(leaves) / len(pick))
-    desc = (f"oracle FMM on the full workload (keys, sort, tree, traversal, P2M/M2M over all "
-            f"{f.ncells} cells), M2L/L2L/L2P/P2P on {len(pick)} of {len(leaves)} leaves, "
-            f"evaluation time scaled by {len(leaves) / len(pick):.1f}")
-    return w["n"] / t_total, t2 - t0, desc
+    pos, _, _ = f.evaluate_leaves(leaves[k % stride::stride])
+    return len(pos), time.perf_counter() - t0
 
 
-def oracle_sample_batched(x, q, off, w, stride=32):
-    """Oracle FMM on every `stride`-th system, its time scaled to all systems."""
+def oracle_step_batched(x, q, off, w, k, stride=REF_STRIDE):
+    """One step of the reference arm for a batch: the whole oracle FMM of systems
+    k, k+stride, ... Returns (particles evaluated, seconds)."""
     from oracle import oracle as O
     t0 = time.perf_counter()
     done = 0
-    picked = list(range(0, len(off) - 1, stride))
-    for sy in picked:
+    for sy in range(k % stride, len(off) - 1, stride):
         a, b = off[sy], off[sy + 1]
         O.Fmm(x[a:b], q[a:b], w["p"], w["theta"], w["ncrit"], max_depth=w["max_depth"]).evaluate()
-        done += b - a
-    t = time.perf_counter() - t0
-    desc = (f"oracle FMM on {len(picked)} of {len(off) - 1} systems ({done} particles), "
-            f"rate applied to all {int(off[-1])} particles")
-    return done / t, t, desc
+        done += int(b - a)
+    return done, time.perf_counter() - t0
 
 
 def run_reference(args):
@@ -136,60 +183,81 @@ def run_reference(args):
         return
     from oracle import oracle as O
     w, x, q, off = workload(args.workload, args.p, args.ncrit)
-    sample = (lambda: oracle_sample(x, q, w)) if off is None else (lambda: oracle_sample_batched(x, q, off, w))
-    for _ in range(args.warmup):
-        sample()
-    vals = []
-    wall = 0.0
-    desc = ""
-    for _ in range(args.steps):
-        v, t, desc = sample()
-        vals.append(v)
-        wall += t
-    value = statistics.mean(vals)
+    if off is None:
+        step = lambda k: oracle_step(x, q, w, k)
+        desc = (f"each step: the oracle's keys, sort, tree, traversal and upward pass over the whole "
+                f"workload, then M2L/L2L/L2P/P2P for the particles of every {REF_STRIDE}th leaf (a "
+                f"different slice each step); value = particles evaluated / measured seconds")
+    else:
+        step = lambda k: oracle_step_batched(x, q, off, w, k)
+        desc = (f"each step: the whole oracle FMM of every {REF_STRIDE}th system (a different slice each "
+                f"step); value = particles evaluated / measured seconds")
+    for k in range(args.warmup):
+        step(k)
+    done, secs = 0, 0.0
+    for k in range(args.steps):
+        n_k, t_k = step(args.warmup + k)
+        done += n_k
+        secs += t_k
+    value = done / secs
     line = {"impl": "reference", "metric": "FMM particles/s", "value": value,
             "unit": "particles/s", "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * w["n"] / value,
+            "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": config_of(w, args),
             "cpu_baseline": {"value": value, "unit": "particles/s", "cores": O.num_threads(),
-                             "kind": "oracle", "sample": desc},
+                             "kind": "oracle", "sample": desc, "measured": True,
+                             "particles_per_step": done / args.steps},
             "e2e": {"value": value, "unit": "particles/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def accuracy(x, q, phi, grad, nsample=512, seed=77, off=None):
-    """Relative L2 error of phi and grad against the FP64 direct sum (oracle) on
-    nsample seeded targets (for a batch: 128 targets in each of 4 systems, each
-    against its own system)."""
+def direct_reference(x, q, nsample=512, seed=77, off=None):
+    """FP64 direct sums (oracle) on nsample seeded targets (for a batch: 128 targets
+    in each of 4 systems, each against its own system).  Returns (targets, phi*,
+    grad*, seconds)."""
     from oracle import oracle as O
     from paper_1108_5815_gb300 import inputs
     import numpy as np
+    t0 = time.perf_counter()
     if off is None:
         t = inputs.sample_indices(len(q), nsample, seed)
         pd, gd = O.direct(x, q, targets=t)
-        got_p, got_g = phi[t], grad[t]
     else:
         nsys = len(off) - 1
-        pds, gds, gps, ggs = [], [], [], []
+        ts, pds, gds = [], [], []
         for sy in (0, nsys // 3, 2 * nsys // 3, nsys - 1):
             a, b = int(off[sy]), int(off[sy + 1])
-            t = inputs.sample_indices(b - a, 128, seed + sy)
-            p_, g_ = O.direct(x[a:b], q[a:b], targets=t)
+            tt = inputs.sample_indices(b - a, 128, seed + sy)
+            p_, g_ = O.direct(x[a:b], q[a:b], targets=tt)
+            ts.append(a + tt)
             pds.append(p_)
             gds.append(g_)
-            gps.append(phi[a + t])
-            ggs.append(grad[a + t])
-        pd, gd, got_p, got_g = np.concatenate(pds), np.concatenate(gds), np.concatenate(gps), np.concatenate(ggs)
-        nsample = len(pd)
-    e_phi = float(np.linalg.norm(got_p - pd) / np.linalg.norm(pd))
-    e_grad = float(np.linalg.norm(got_g - gd) / np.linalg.norm(gd))
-    return {"rel_l2_phi": e_phi, "rel_l2_grad": e_grad, "reference": "FP64 direct sum (oracle)",
-            "targets": int(nsample)}
+        t, pd, gd = np.concatenate(ts), np.concatenate(pds), np.concatenate(gds)
+    return t, pd, gd, time.perf_counter() - t0
 
 
-# ------------------------------------------------------------------ rooflines
+def compare(ref, phi, grad):
+    """Relative L2 and worst-particle errors of phi/grad (numpy, caller order) at
+    the reference's targets."""
+    import numpy as np
+    t, pd, gd, _ = ref
+    got_p, got_g = np.asarray(phi, np.float64)[t], np.asarray(grad, np.float64)[t]
+    return {"rel_l2_phi": float(np.linalg.norm(got_p - pd) / np.linalg.norm(pd)),
+            "rel_l2_grad": float(np.linalg.norm(got_g - gd) / np.linalg.norm(gd)),
+            "max_err_phi_rel_max": float(np.abs(got_p - pd).max() / np.abs(pd).max()),
+            "max_err_grad_rel_max": float(np.linalg.norm(got_g - gd, axis=1).max()
+                                          / np.linalg.norm(gd, axis=1).max()),
+            "reference": "FP64 direct sum (oracle)", "targets": int(len(t))}
+
+
+def accuracy(x, q, phi, grad, nsample=512, seed=77, off=None):
+    """compare() against a fresh direct_reference()."""
+    return compare(direct_reference(x, q, nsample, seed, off), phi, grad)
+
+
+# ------------------------------------------------------------------ peaks and rooflines
 
 def measured_peaks():
     """(HBM GB/s, BF16 dense TF/s, label): MEASURED_PEAKS.json when present, else
@@ -200,6 +268,62 @@ def measured_peaks():
         return float(d["hbm_gbs"]), float(d["bf16_tflops"]), "of measured"
     except (OSError, KeyError, ValueError):
         return 6800.0, 1900.0, "of fallback"
+
+
+def sm_max_mhz():
+    """Maximum SM clock: MEASURED_PEAKS.json, else nvidia-smi, else the GB300 figure."""
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["sm_max_mhz"]), "MEASURED_PEAKS.json"
+    except (OSError, KeyError, ValueError):
+        pass
+    try:
+        out = subprocess.run(["nvidia-smi", "--query-gpu=clocks.max.sm", "--format=csv,noheader,nounits"],
+                             capture_output=True, text=True, timeout=20).stdout.split()
+        return float(out[0]), "nvidia-smi"
+    except (OSError, IndexError, ValueError, subprocess.SubprocessError):
+        return 2070.0, "GB300 maximum SM clock"
+
+
+def gemm_tflops(torch, dev, dtype, n, reps, tf32=False):
+    """Best-of-reps rate of one dense n x n x n cuBLAS GEMM (2 n^3 flop), CUDA events."""
+    old = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = tf32
+    try:
+        g = torch.Generator(device=dev)
+        g.manual_seed(5)
+        a = torch.randn(n, n, device=dev, dtype=dtype, generator=g)
+        b = torch.randn(n, n, device=dev, dtype=dtype, generator=g)
+        c = a @ b
+        best = float("inf")
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b, out=c)
+            e1.record()
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        del a, b, c
+        return 2.0 * n ** 3 / (best * 1e-3) / 1e12
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = old
+
+
+def device_peaks(torch, dev):
+    """Peaks for the rooflines: the SM count from the device, the FP32 peak derived
+    from it (SMs x 128 lanes x 2 flop x maximum SM clock), HBM and BF16 from
+    MEASURED_PEAKS.json, and TF32 / FP64 dense GEMM rates measured here with
+    cuBLAS (TF32: fp32 matmul with TF32 allowed, 8192^3; FP64: 4096^3)."""
+    props = torch.cuda.get_device_properties(dev)
+    sms = int(props.multi_processor_count)
+    mhz, mhz_src = sm_max_mhz()
+    hbm, bf16, label = measured_peaks()
+    return {"sms": sms, "sm_max_mhz": mhz, "sm_max_mhz_source": mhz_src,
+            "fp32_derived_tflops": sms * FP32_LANES * 2 * mhz * 1e6 / 1e12,
+            "hbm_gbs": hbm, "bf16_tflops": bf16, "hbm_bf16_label": label,
+            "tf32_tflops": gemm_tflops(torch, dev, torch.float32, 8192, 10, tf32=True),
+            "fp64_tflops": gemm_tflops(torch, dev, torch.float64, 4096, 3),
+            "what": "sms: cudaDevAttrMultiProcessorCount; tf32/fp64: cuBLAS dense GEMM measured in this "
+                    "process (best of 10 / 3, CUDA events); hbm/bf16: MEASURED_PEAKS.json"}
 
 
 def captured_traffic(kernel):
@@ -217,29 +341,31 @@ def captured_traffic(kernel):
     return rec["dram_bytes_per_launch"]
 
 
-def hot_kernel_rooflines(st, ms_p2p, ms_m2l, p, precision):
+def hot_kernel_rooflines(st, ms_p2p, ms_m2l, p, precision, pk):
     """P2P against the FP32 pipe (derived peak) and M2L against its own pipe.
 
     P2P work: interactions x 23 flop.  M2L work: M2L pairs x 2 (p+1)^4 flop, the
     useful flops of the dense translation (the 3-way split, padding to 128 and
     empty rows of a tile are not counted)."""
-    _, bf16_tf, label = measured_peaks()
-    fp32_peak = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    fp32_peak = pk["fp32_derived_tflops"]
     out = []
     p2p_tf = st["n_p2p_interactions"] * P2P_FLOPS / (ms_p2p * 1e-3) / 1e12
     out.append({"kernel": "k_p2p", "bound": "alu", "achieved": p2p_tf, "peak": fp32_peak,
                 "unit": "TFLOP/s", "frac": p2p_tf / fp32_peak, "traffic": captured_traffic("k_p2p"),
-                "ms": ms_p2p, "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+                "ms": ms_p2p,
+                "peak_source": (f"derived: {pk['sms']} SMs (device query) x {FP32_LANES} FP32 lanes x 2 flop x "
+                                f"{pk['sm_max_mhz']:.0f} MHz ({pk['sm_max_mhz_source']})"),
                 "work": f"{st['n_p2p_interactions']} interactions x {P2P_FLOPS} flop"})
     P2 = (p + 1) ** 2
     m2l_tf = st["n_m2l_pairs"] * 2 * P2 * P2 / (ms_m2l * 1e-3) / 1e12
     if precision == "fp32":
         kern, bound, peak, src = "k_m2l_simt", "alu", fp32_peak, "derived FP32 peak (as for P2P)"
     elif precision == "tf32x3":
-        kern, bound, peak = "k_m2l_tc<tf32x3>", "tensor", bf16_tf * 1.1 / 2.25
-        src = f"TF32 = BF16 dense {label} x nominal ratio 1.1/2.25"
+        kern, bound, peak = "k_m2l_tc<tf32x3>", "tensor", pk["tf32_tflops"]
+        src = "TF32 dense: cuBLAS fp32 GEMM with TF32, 8192^3, measured in this process"
     else:
-        kern, bound, peak, src = "k_m2l_tc<bf16x3>", "tensor", bf16_tf, f"BF16 dense {label}"
+        kern, bound, peak = "k_m2l_tc<bf16x3>", "tensor", pk["bf16_tflops"]
+        src = f"BF16 dense {pk['hbm_bf16_label']} (MEASURED_PEAKS.json)"
     out.append({"kernel": kern, "bound": bound, "achieved": m2l_tf, "peak": peak,
                 "unit": "TFLOP/s", "frac": m2l_tf / peak, "traffic": captured_traffic(kern),
                 "ms": ms_m2l, "peak_source": src,
@@ -247,13 +373,13 @@ def hot_kernel_rooflines(st, ms_p2p, ms_m2l, p, precision):
     return out
 
 
-def tree_roofline(n, ms_tree):
+def tree_roofline(n, ms_tree, pk):
     """The tree build (box, keys, radix sort, permute, level splits) against HBM.
 
     Algorithmic bytes per particle: 16 read (x, y, z, q) + 16 permuted write +
     12 key/index write, plus 24 per 8-bit radix pass (8 passes over 63-bit keys).
     The phase time includes every launch of the phase; it is a phase, not one kernel."""
-    hbm, _, label = measured_peaks()
+    hbm, label = pk["hbm_gbs"], pk["hbm_bf16_label"]
     bytes_ = n * (16 + 16 + 12 + 24 * 8)
     gbs = bytes_ / (ms_tree * 1e-3) / 1e9
     return {"kernel": "tree build phase", "phase": True, "bound": "hbm", "achieved": gbs, "peak": hbm,
@@ -338,6 +464,140 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
                 "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ the other workloads
+
+def _time_gpu(torch, stream, flush, fn, steps, warm=2):
+    """Median device time (ms) of fn() over `steps` calls after `warm` untimed
+    ones, L2 flushed before each, CUDA events on the solve's stream."""
+    for _ in range(warm):
+        fn()
+    ms = []
+    for k in range(steps):
+        flush.fill_(float(k))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    return statistics.median(ms)
+
+
+def run_configs(torch, dev, stream, flush, cost_model, args):
+    """The benchmark's other configurations on the GPU (no CPU oracle runs but the
+    sampled FP64 direct sums that judge accuracy):
+
+    * plummer4m: N = 4,194,304 Plummer points, q = 1/N, theta 0.4, ncrit 64, at
+      p = 6, 8, 12 in each M2L precision (FP32, TF32x3, BF16x3): time and error
+      against the FP64 direct sum per p;
+    * batched512: 512 systems (N_i log-uniform in [1e3, 1e5], half uniform, half
+      Plummer), p = 8, theta 0.5: schedule (N_crit, M2L work-unit size) from the
+      measured autotuner, then one batched call (TF32x3 and FP32), one replay of
+      the captured graph, and one call per system;
+    * plummer16m: N = 16,777,216 Plummer points, p = 10, theta 0.4: N_crit from the
+      measured autotuner (plain selection) and from the learned cost model; plain
+      and learned selection with TF32x3 M2L, and the plain FP32 FMM."""
+    from paper_1108_5815_gb300 import fmm, inputs
+    out = {}
+    t_all = time.perf_counter()
+    tm = lambda fn, k=3: _time_gpu(torch, stream, flush, fn, k)
+
+    # ---- mixed precision per p
+    w = inputs.WORKLOADS["plummer4m"]
+    x, q = inputs.make(w["kind"], w["n"], w["seed"])
+    n = w["n"]
+    xd, qd = torch.from_numpy(x).to(dev), torch.from_numpy(q).to(dev)
+    phi, grad = torch.empty(n, device=dev), torch.empty(n, 3, device=dev)
+    ref = direct_reference(x, q)
+    per_p = {}
+    for p in (6, 8, 12):
+        rec = {}
+        for prec in ("fp32", "tf32x3", "bf16x3"):
+            m = tm(lambda: fmm.laplace3d(xd, qd, p, w["theta"], w["ncrit"], max_depth=w["max_depth"],
+                                         precision=prec, out=(phi, grad)))
+            rec[prec] = {"ms": m, "value": n / (m / 1e3),
+                         "accuracy": compare(ref, phi.cpu().numpy(), grad.cpu().numpy())}
+        rec["speedup_vs_fp32"] = {k: rec["fp32"]["ms"] / rec[k]["ms"] for k in ("tf32x3", "bf16x3")}
+        per_p[str(p)] = rec
+    out["plummer4m"] = {"workload": f"N={n} Plummer (a=1, r<=20), q=1/N, theta={w['theta']}, "
+                                    f"ncrit={w['ncrit']}", "per_p": per_p}
+    del xd, qd, phi, grad
+
+    # ---- batched systems
+    w = inputs.WORKLOADS["batched512"]
+    x, q, off = inputs.batched_systems(w["nsys"], w["seed"])
+    n = int(off[-1])
+    xd, qd = torch.from_numpy(x).to(dev), torch.from_numpy(q).to(dev)
+    phi, grad = torch.empty(n, device=dev), torch.empty(n, 3, device=dev)
+    ref = direct_reference(x, q, off=off)
+    bn, bu, table = fmm.tune_schedule(xd, qd, w["p"], w["theta"], offsets=off, ncrit_candidates=(32, 64, 128, 256),
+                                      unit_candidates=(0, 32, 128), max_depth=w["max_depth"], precision="tf32x3")
+    kb = dict(max_depth=w["max_depth"], m2l_unit_blocks=bu)
+    rec = {"schedule": {"ncrit": bn, "m2l_unit_blocks": bu,
+                        "candidates_ms": {f"ncrit={a},unit={b}": v for (a, b), v in table.items()}}}
+    for prec in ("fp32", "tf32x3"):
+        m = tm(lambda: fmm.laplace3d_batched(xd, qd, off, w["p"], w["theta"], bn, precision=prec,
+                                             out=(phi, grad), **kb))
+        rec["batched_" + prec] = {"ms": m, "value": n / (m / 1e3),
+                                  "accuracy": compare(ref, phi.cpu().numpy(), grad.cpu().numpy())}
+    plan = fmm.Plan(xd, qd, w["p"], w["theta"], bn, offsets=off, precision="tf32x3", headroom=1.25, **kb)
+    gphi, ggrad = torch.empty_like(phi), torch.empty_like(grad)
+    m = tm(lambda: plan.execute(xd, qd, out=(gphi, ggrad)))
+    valid = plan.check() == 0
+    info = plan.info()
+    plan.close()
+    fmm.laplace3d_batched(xd, qd, off, w["p"], w["theta"], bn, precision="tf32x3", out=(phi, grad), **kb)
+    torch.cuda.synchronize()
+    rec["graph_replay_tf32x3"] = {"ms": m, "value": n / (m / 1e3), "valid": valid,
+                                  "equal_to_batched_call": bool(torch.equal(gphi, phi) and torch.equal(ggrad, grad)),
+                                  "graph_kernels": info["graph_kernels"]}
+
+    def loop():
+        for sy in range(len(off) - 1):
+            a_, b_ = int(off[sy]), int(off[sy + 1])
+            fmm.laplace3d(xd[a_:b_], qd[a_:b_], w["p"], w["theta"], bn, precision="tf32x3",
+                          out=(phi[a_:b_], grad[a_:b_]), **kb)
+    m = _time_gpu(torch, stream, flush, loop, 2, warm=1)
+    rec["one_call_per_system_tf32x3"] = {"ms": m, "value": n / (m / 1e3)}
+    rec["speedup_batched_vs_per_system"] = m / rec["batched_tf32x3"]["ms"]
+    rec["speedup_batched_tf32x3_vs_batched_fp32"] = rec["batched_fp32"]["ms"] / rec["batched_tf32x3"]["ms"]
+    out["batched512"] = dict(workload=f"{len(off) - 1} systems, {n} particles, N_i log-uniform in [1e3, 1e5], "
+                                      f"half uniform / half Plummer, p={w['p']}, theta={w['theta']}", **rec)
+    del xd, qd, phi, grad, gphi, ggrad
+
+    # ---- learned cost model at scale
+    w = inputs.WORKLOADS["plummer16m"]
+    x, q = inputs.make(w["kind"], w["n"], w["seed"])
+    n = w["n"]
+    xd, qd = torch.from_numpy(x).to(dev), torch.from_numpy(q).to(dev)
+    phi, grad = torch.empty(n, device=dev), torch.empty(n, 3, device=dev)
+    ref = direct_reference(x, q)
+    cands = (64, 128, 256)
+    bn, _, table = fmm.tune_schedule(xd, qd, w["p"], w["theta"], ncrit_candidates=cands, unit_candidates=(0,),
+                                     max_depth=w["max_depth"], precision="tf32x3")
+    if cost_model is None:
+        cost_model = fmm.cost_model_train(precision="tf32x3", p_lo=3, p_hi=12, steps=args.train_steps, seed=1)
+    nb, pred = fmm.cost_model_pick_ncrit(xd, qd, w["p"], w["theta"], cands, max_depth=w["max_depth"],
+                                         precision="tf32x3", select="learned")
+    rec = {"ncrit_measured_best": bn, "ncrit_tuner_ms": {str(a): v for (a, _), v in table.items()},
+           "ncrit_network_pick": nb, "ncrit_network_predicted_ms": {str(k): v for k, v in pred.items()}}
+    variants = [("plain_fp32", "fp32", "plain", bn), ("plain_tf32x3", "tf32x3", "plain", bn),
+                ("learned_tf32x3", "tf32x3", "learned", bn)]
+    if nb != bn:
+        variants.append(("learned_tf32x3_network_ncrit", "tf32x3", "learned", nb))
+    for name, prec, sel, nc in variants:
+        m = tm(lambda: fmm.laplace3d(xd, qd, w["p"], w["theta"], nc, max_depth=w["max_depth"], precision=prec,
+                                     select=sel, out=(phi, grad)))
+        rec[name] = {"ms": m, "value": n / (m / 1e3), "ncrit": nc,
+                     "accuracy": compare(ref, phi.cpu().numpy(), grad.cpu().numpy())}
+    rec["speedup_learned_tf32x3_vs_plain_fp32"] = rec["plain_fp32"]["ms"] / rec["learned_tf32x3"]["ms"]
+    rec["speedup_learned_vs_plain_tf32x3"] = rec["plain_tf32x3"]["ms"] / rec["learned_tf32x3"]["ms"]
+    out["plummer16m"] = dict(workload=f"N={n} Plummer, q=1/N, p={w['p']}, theta={w['theta']}", **rec)
+    del xd, qd, phi, grad
+    out["seconds"] = time.perf_counter() - t_all
+    return out
 
 
 # ------------------------------------------------------------------ main arm
@@ -431,21 +691,24 @@ def main():
     st0 = st_list[-1]
     ms_p2p = statistics.mean(s["ms_p2p"] for s in st_list)
     ms_m2l = statistics.mean(s["ms_m2l"] for s in st_list)
-    rooflines = hot_kernel_rooflines(st0, ms_p2p, ms_m2l, w["p"], args.precision)
+    pk = device_peaks(torch, dev)
+    rooflines = hot_kernel_rooflines(st0, ms_p2p, ms_m2l, w["p"], args.precision, pk)
     # the FP32 pipe's measured ceilings beside the derived peak (context for the P2P line)
     ceil = fmm.measure_fp32()
     p2p_line = rooflines[0]
     body_tf = ceil["body_interactions_per_s"] * P2P_FLOPS / 1e12
+    p2p_line["peak_measured_ffma_stream"] = ceil["ffma_tflops"]
+    p2p_line["frac_of_measured_ffma_stream"] = p2p_line["achieved"] / ceil["ffma_tflops"]
     p2p_line["ceilings"] = {
         "ffma_stream_tflops": ceil["ffma_tflops"],
         "ffma_stream_frac_of_derived_peak": ceil["ffma_tflops"] / p2p_line["peak"],
         "p2p_body_tflops": body_tf,
         "p2p_body_frac_of_derived_peak": body_tf / p2p_line["peak"],
         "kernel_frac_of_body": p2p_line["achieved"] / body_tf,
-        "what": "FP32x2 FMA chains alone, and the P2P interaction code on staged sources with no list walk "
-                "(fmm_measure_fp32), timed live beside the solve"}
+        "what": "FP32x2 FMA chains alone (the measured FP32 rate), and the P2P interaction code on staged "
+                "sources with no list walk (fmm_measure_fp32), timed live beside the solve"}
     roof = max(rooflines, key=lambda r: r["ms"])  # the dominant kernel
-    rooflines.append(tree_roofline(n, statistics.mean(s["ms_tree"] for s in st_list)))
+    rooflines.append(tree_roofline(n, statistics.mean(s["ms_tree"] for s in st_list), pk))
     solve_frac = solve_roofline_fraction(rooflines, ms_per_step)
     phases = {k: round(statistics.mean(s[k] for s in st_list), 4)
               for k in ("ms_tree", "ms_traverse", "ms_upward", "ms_m2l", "ms_downward", "ms_p2p",
@@ -488,9 +751,10 @@ def main():
                "d2h_bytes_per_step": int(ph.nbytes + gh.nbytes), "ms_per_step": e2e_ms}
 
     # accuracy of this very solve against the FP64 direct sum on sampled targets
-    acc = None
+    acc = ref = None
     if rank == 0:
-        acc = accuracy(x, q, phi.cpu().numpy(), grad.cpu().numpy(), off=off)
+        ref = direct_reference(x, q, off=off)
+        acc = compare(ref, phi.cpu().numpy(), grad.cpu().numpy())
 
     # the other M2L precisions, timed the same way (value and accuracy)
     modes = {}
@@ -511,7 +775,7 @@ def main():
                 ms.append(a.elapsed_time(b))
             m = statistics.mean(ms)
             modes[prec] = {"value": n / (m / 1e3), "ms_per_step": m,
-                           "accuracy": accuracy(x, q, phi.cpu().numpy(), grad.cpu().numpy(), off=off)}
+                           "accuracy": compare(ref, phi.cpu().numpy(), grad.cpu().numpy())}
 
     # the other selection modes (plain FMM, pre-timed, learned, and the treecode: cell-particle
     # for every accepted pair), timed the same way
@@ -539,7 +803,7 @@ def main():
                                  "n_m2p_pairs": sts[-1]["n_m2p_pairs"],
                                  "n_p2p_pairs": sts[-1]["n_p2p_pairs"],
                                  "n_p2p_interactions": sts[-1]["n_p2p_interactions"],
-                                 "accuracy": accuracy(x, q, phi.cpu().numpy(), grad.cpu().numpy(), off=off)}
+                                 "accuracy": compare(ref, phi.cpu().numpy(), grad.cpu().numpy())}
 
     # the same solve captured once into a CUDA graph (fmm_plan_create) and
     # replayed: one graph launch per step, no host read-back, inputs copied into
@@ -595,12 +859,22 @@ def main():
         loop = {"value": n / (m / 1e3), "ms_per_step": m, "speedup_of_batch": m / ms_per_step,
                 "what": "one fmm_laplace3d call per system, same workload"}
 
+    configs = None
+    if rank == 0 and world == 1 and not args.no_configs:
+        configs = run_configs(torch, dev, stream, flush, cost_model, args)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         from oracle import oracle as O
-        v, _, desc = oracle_sample(x, q, w) if off is None else oracle_sample_batched(x, q, off, w)
+        v, secs, desc = oracle_full(x, q, w) if off is None else oracle_full_batched(x, q, off, w)
         cpu = {"value": v, "unit": "particles/s", "cores": O.num_threads(), "kind": "oracle",
-               "sample": desc}
+               "sample": desc, "measured": True, "seconds": secs,
+               "single_core_config1_s": oracle_single_core_config1(),
+               "single_core_config1": "oracle FMM, N=4096 uniform cube, p=4, theta=0.5, ncrit=64, 1 thread, "
+                                      "median of 3",
+               "direct_sum_sample_s": ref[3] if ref is not None else None,
+               "direct_sum_sample": f"FP64 direct sum on {len(ref[0]) if ref is not None else 0} sampled "
+                                    f"targets against all {n} sources"}
 
     if rank == 0:
         line = {"metric": "FMM particles/s", "value": value, "unit": "particles/s",
@@ -612,7 +886,8 @@ def main():
                 "gpu_launches": int(sum(s["n_launches"] for s in st_list)),
                 "accuracy": acc, "m2l_modes": modes, "select_modes": select_modes,
                 "cost_model": cost_model, "ncrit_tuning": ncrit_tuning, "per_system_loop": loop,
-                "graph_replay": graph, "solve_roofline_fraction": solve_frac,
+                "graph_replay": graph, "solve_roofline_fraction": solve_frac, "peaks": pk,
+                "configs": configs,
                 "clocks": clocks, "phases_ms": phases,
                 "counts": {k: st0[k] for k in ("ncells", "nleaves", "depth", "n_p2p_pairs",
                                                "n_p2p_interactions", "n_m2l_pairs",

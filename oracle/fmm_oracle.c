@@ -1097,6 +1097,17 @@ int orc_num_threads(void)
 #endif
 }
 
+/* Threads of the parallel loops from now on (n >= 1); for the timed baselines. */
+void orc_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    if (n >= 1)
+        omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 /* Thin complex-array wrappers for the operator pins (arrays of re/im pairs). */
 void orc_regular_ri(const double x[3], int p, double *ri)
 {

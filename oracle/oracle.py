@@ -65,6 +65,7 @@ def lib():
             L.orc_fmm_expansion.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, _D, _D]
             L.orc_fmm_centre.argtypes = [ctypes.c_void_p, ctypes.c_int64, _D]
             L.orc_num_threads.restype = ctypes.c_int
+            L.orc_set_num_threads.argtypes = [ctypes.c_int]
             L.orc_morton_keys.restype = ctypes.c_int
             L.orc_morton_keys.argtypes = [ctypes.c_int64, _D, _D, _D, _U64]
             L.orc_regular_ri.argtypes = [_D, ctypes.c_int, _D]
@@ -97,6 +98,11 @@ def _f64(a, shape=None):
 
 def num_threads() -> int:
     return lib().orc_num_threads()
+
+
+def set_num_threads(n: int) -> None:
+    """Threads of the oracle's parallel loops from now on."""
+    lib().orc_set_num_threads(int(n))
 
 
 def nterms(p: int) -> int:

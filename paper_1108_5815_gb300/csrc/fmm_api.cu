@@ -106,7 +106,7 @@ struct Workspace {
     // the far-field chain.  They are ordered after the caller's stream on entry
     // and the caller's stream is ordered after them on exit.
     cudaStream_t main_stream = nullptr, far_stream = nullptr;
-    cudaEvent_t ev_in = nullptr, ev_fork = nullptr, ev_join = nullptr, ev_out = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_tree = nullptr, ev_fork = nullptr, ev_join = nullptr, ev_out = nullptr;
 };
 
 std::mutex g_ws_mu;
@@ -158,7 +158,7 @@ void ensure_streams(Workspace &ws)
     FMM_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&lo, &hi));
     FMM_CUDA_TRY(cudaStreamCreateWithFlags(&ws.main_stream, cudaStreamNonBlocking));
     FMM_CUDA_TRY(cudaStreamCreateWithPriority(&ws.far_stream, cudaStreamNonBlocking, hi));
-    for (cudaEvent_t *e : {&ws.ev_in, &ws.ev_fork, &ws.ev_join, &ws.ev_out})
+    for (cudaEvent_t *e : {&ws.ev_in, &ws.ev_tree, &ws.ev_fork, &ws.ev_join, &ws.ev_out})
         FMM_CUDA_TRY(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
 }
 
@@ -512,6 +512,51 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
     k_cell_geom<<<grid_for(ncells, 256), 256, 0, st>>>(c, ncells);
     FMM_LAUNCH_CHECK();
     ev.rec(1, st);
+
+    // ---------------------------------------------------------- upward pass (beside the traversal)
+    // P2M and M2M need only the tree: they run on the far-field stream while the
+    // traversal runs on the main stream.
+    cudaStream_t fs = ws.far_stream;
+    float *M = nullptr, *Lx = nullptr;
+    if (!lists_only) {
+        FMM_CUDA_TRY(cudaEventRecord(ws.ev_tree, st));
+        FMM_CUDA_TRY(cudaStreamWaitEvent(fs, ws.ev_tree, 0));
+        if (ws.cache_p != p) {
+            // operator tables: shift matrices per p; the M2L matrices are cached per class key
+            ws.class_cache.clear();
+            ws.table_slots = 0;
+            ws.split_slots = 0;
+            ws.cache_p = p;
+            float *m2m = need<float>(ws, "m2m", (size_t)8 * P2pad * P2pad, fs);
+            float *l2l = need<float>(ws, "l2l", (size_t)8 * P2pad * P2pad, fs);
+            double *m2m64 = nullptr, *l2l64 = nullptr;  // FP64 copies for the top levels at high p
+            if (p >= kFp64TopP) {
+                m2m64 = need<double>(ws, "m2m64", (size_t)8 * P2pad * P2pad, fs);
+                l2l64 = need<double>(ws, "l2l64", (size_t)8 * P2pad * P2pad, fs);
+            }
+            const size_t sh = sizeof(double) * 2 * (size_t)(p + 1) * (p + 2) / 2;
+            k_build_shift_tables<<<16, 256, sh, fs>>>(p, P2pad, m2m, l2l, m2m64, l2l64);
+            FMM_LAUNCH_CHECK();
+        }
+        M = need<float>(ws, "M", (size_t)ncells * P2pad, fs);
+        Lx = need<float>(ws, "L", (size_t)ncells * P2pad, fs);
+        ev.rec(2, fs);
+        {
+            const size_t sh = (size_t)32 * (P2pad + 1) * sizeof(float);
+            if (sh > 48 * 1024) set_smem_limit_once((const void *)k_p2m, (int)sh);
+            k_p2m<<<nleaves, 32, sh, fs>>>(c, leaves, nleaves, pts, box, p, P2pad, M);
+            FMM_LAUNCH_CHECK();
+        }
+        float *mtmp = need<float>(ws, "m2m_tmp", (size_t)ncells * P2pad, fs);
+        for (int l = depth - 1; l >= 0; --l) {
+            const int a = lstart[l], b = lstart[l + 1];
+            if (p >= kFp64TopP && l < kFp64TopLevels)
+                launch_shift_fp64(false, c, a, b, get<double>(ws, "m2m64"), P2, P2pad, M, fs);
+            else
+                launch_shift_batched(false, c, a, b, get<float>(ws, "m2m"), P2, P2pad, M, mtmp, fs);
+        }
+        ev.rec(7, fs);
+    }
     ws.shape.lstart = lstart;
     ws.shape.N = N;
     ws.shape.nsys = nsys;
@@ -617,7 +662,6 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
     // the library's high-priority stream; the two join before the final sum.
     float4 *far = need<float4>(ws, "far", N, st);
     float4 *near = need<float4>(ws, "near", N, st);
-    cudaStream_t fs = ws.far_stream;
     FMM_CUDA_TRY(cudaEventRecord(ws.ev_fork, st));
     FMM_CUDA_TRY(cudaStreamWaitEvent(fs, ws.ev_fork, 0));
     int *p2p_counter = need<int>(ws, "p2p_counter", 1, st);
@@ -677,23 +721,6 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
                 k_m2l_class<<<grid_for(m2l_total, 256), 256, 0, fs>>>(L.m2l_slot, m2l_total, slot_class);
                 FMM_LAUNCH_CHECK();
             }
-        }
-        // operator tables: shift matrices per p, M2L matrices cached per class key
-        if (ws.cache_p != p) {
-            ws.class_cache.clear();
-            ws.table_slots = 0;
-            ws.split_slots = 0;
-            ws.cache_p = p;
-            float *m2m = need<float>(ws, "m2m", (size_t)8 * P2pad * P2pad, fs);
-            float *l2l = need<float>(ws, "l2l", (size_t)8 * P2pad * P2pad, fs);
-            double *m2m64 = nullptr, *l2l64 = nullptr;  // FP64 copies for the top levels at high p
-            if (p >= kFp64TopP) {
-                m2m64 = need<double>(ws, "m2m64", (size_t)8 * P2pad * P2pad, fs);
-                l2l64 = need<double>(ws, "l2l64", (size_t)8 * P2pad * P2pad, fs);
-            }
-            const size_t sh = sizeof(double) * 2 * (size_t)(p + 1) * (p + 2) / 2;
-            k_build_shift_tables<<<16, 256, sh, fs>>>(p, P2pad, m2m, l2l, m2m64, l2l64);
-            FMM_LAUNCH_CHECK();
         }
         std::vector<uint64_t> hkeys(nclass);
         if (nclass > 0) sync_point(ws, fs, flags, {{ukeys, sizeof(uint64_t) * nclass}}, hkeys.data());
@@ -770,26 +797,6 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
                                                            bitmap, word_prefix, entry_base, src);
         FMM_LAUNCH_CHECK();
     }
-    ev.rec(2, fs);
-
-    // ---------------------------------------------------------- upward pass
-    float *M = need<float>(ws, "M", (size_t)ncells * P2pad, fs);
-    float *Lx = need<float>(ws, "L", (size_t)ncells * P2pad, fs);
-    {
-        const size_t sh = (size_t)32 * (P2pad + 1) * sizeof(float);
-        if (sh > 48 * 1024) set_smem_limit_once((const void *)k_p2m, (int)sh);
-        k_p2m<<<nleaves, 32, sh, fs>>>(c, leaves, nleaves, pts, box, p, P2pad, M);
-        FMM_LAUNCH_CHECK();
-    }
-    float *mtmp = need<float>(ws, "m2m_tmp", (size_t)ncells * P2pad, fs);
-    for (int l = depth - 1; l >= 0; --l) {
-        const int a = lstart[l], b = lstart[l + 1];
-        if (p >= kFp64TopP && l < kFp64TopLevels)
-            launch_shift_fp64(false, c, a, b, get<double>(ws, "m2m64"), P2, P2pad, M, fs);
-        else
-            launch_shift_batched(false, c, a, b, get<float>(ws, "m2m"), P2, P2pad, M, mtmp, fs);
-    }
-    ev.rec(7, fs);
 
     // ---------------------------------------------------------- M2L
     const bool tensor = o.precision_mode != FMM_PREC_FP32 && m2l_tc_supported(P2pad);
@@ -1136,7 +1143,7 @@ struct fmm_plan {
     int64_t operators = 0, graph_nodes = 0, graph_kernels = 0;
     float *xyz = nullptr, *q = nullptr, *phi = nullptr, *grad = nullptr;
     cudaStream_t st = nullptr, fs = nullptr;
-    cudaEvent_t fork = nullptr, join = nullptr;
+    cudaEvent_t tree = nullptr, fork = nullptr, join = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     ~fmm_plan()
@@ -1144,6 +1151,7 @@ struct fmm_plan {
         if (st) cudaStreamSynchronize(st);
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
+        if (tree) cudaEventDestroy(tree);
         if (fork) cudaEventDestroy(fork);
         if (join) cudaEventDestroy(join);
         if (st) cudaStreamDestroy(st);
@@ -1166,6 +1174,7 @@ void build_plan(fmm_plan &pl, Workspace &ws, const int64_t *offsets, const uint8
     int lo = 0, hi = 0;
     FMM_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&lo, &hi));
     FMM_CUDA_TRY(cudaStreamCreateWithPriority(&pl.fs, cudaStreamNonBlocking, hi));
+    FMM_CUDA_TRY(cudaEventCreateWithFlags(&pl.tree, cudaEventDisableTiming));
     FMM_CUDA_TRY(cudaEventCreateWithFlags(&pl.fork, cudaEventDisableTiming));
     FMM_CUDA_TRY(cudaEventCreateWithFlags(&pl.join, cudaEventDisableTiming));
 
@@ -1322,7 +1331,7 @@ void build_plan(fmm_plan &pl, Workspace &ws, const int64_t *offsets, const uint8
     const int64_t launches0 = g_launch_count;
     FMM_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     try {
-        enqueue_plan(s, b, st, pl.fs, pl.fork, pl.join);
+        enqueue_plan(s, b, st, pl.fs, pl.tree, pl.fork, pl.join);
     } catch (...) {
         cudaGraph_t g = nullptr;
         cudaStreamEndCapture(st, &g);

@@ -33,8 +33,8 @@ unsigned grid_stride(int64_t n) { return (unsigned)std::max<int64_t>(1, std::min
 
 }  // namespace
 
-void enqueue_plan(const PlanShape &s, const PlanBuffers &b, cudaStream_t st, cudaStream_t fs, cudaEvent_t fork,
-                  cudaEvent_t join)
+void enqueue_plan(const PlanShape &s, const PlanBuffers &b, cudaStream_t st, cudaStream_t fs, cudaEvent_t tree,
+                  cudaEvent_t fork, cudaEvent_t join)
 {
     const int N = s.N, nsys = s.nsys;
     const CellArrays &c = b.c;
@@ -98,6 +98,20 @@ void enqueue_plan(const PlanShape &s, const PlanBuffers &b, cudaStream_t st, cud
     FMM_CUDA_TRY(cudaMemcpyAsync(b.sz + kSzLeaves, b.leaf_ex + s.cell_cap, sizeof(int), cudaMemcpyDeviceToDevice, st));
     k_cell_geom<<<grid_stride(s.cell_cap), 256, 0, st>>>(c, 0, b.sz);
     FMM_LAUNCH_CHECK();
+
+    // ---------------------------------------------------------- upward pass (fs, beside the traversal)
+    const int p = s.p, P2 = s.P2, P2pad = s.P2pad;
+    FMM_CUDA_TRY(cudaEventRecord(tree, st));
+    FMM_CUDA_TRY(cudaStreamWaitEvent(fs, tree, 0));
+    k_p2m<<<(unsigned)std::max(1, s.leaf_cap), 32, (size_t)32 * (P2pad + 1) * sizeof(float), fs>>>(
+        c, b.leaves, 0, b.pts, b.box, p, P2pad, b.M, b.sz);
+    FMM_LAUNCH_CHECK();
+    for (int l = s.levels - 1; l >= 0; --l) {
+        if (p >= kFp64TopP && l < kFp64TopLevels)
+            launch_shift_fp64(false, c, 0, 0, b.m2m64, P2, P2pad, b.M, fs, b.sz, l, s.level_cap[l]);
+        else
+            launch_shift_batched(false, c, 0, 0, b.m2m, P2, P2pad, b.M, b.mtmp, fs, b.sz, l, s.level_cap[l]);
+    }
 
     // ---------------------------------------------------------- traversal
     const double theta2 = s.theta * s.theta;
@@ -163,18 +177,6 @@ void enqueue_plan(const PlanShape &s, const PlanBuffers &b, cudaStream_t st, cud
                                                        s.nwords, b.bitmap, b.word_prefix, b.entry_base, b.src,
                                                        b.totals, s.nent_cap);
     FMM_LAUNCH_CHECK();
-
-    // ---------------------------------------------------------- upward pass (fs)
-    const int p = s.p, P2 = s.P2, P2pad = s.P2pad;
-    k_p2m<<<(unsigned)std::max(1, s.leaf_cap), 32, (size_t)32 * (P2pad + 1) * sizeof(float), fs>>>(
-        c, b.leaves, 0, b.pts, b.box, p, P2pad, b.M, b.sz);
-    FMM_LAUNCH_CHECK();
-    for (int l = s.levels - 1; l >= 0; --l) {
-        if (p >= kFp64TopP && l < kFp64TopLevels)
-            launch_shift_fp64(false, c, 0, 0, b.m2m64, P2, P2pad, b.M, fs, b.sz, l, s.level_cap[l]);
-        else
-            launch_shift_batched(false, c, 0, 0, b.m2m, P2, P2pad, b.M, b.mtmp, fs, b.sz, l, s.level_cap[l]);
-    }
 
     // ---------------------------------------------------------- M2L (fs)
     if (s.tensor) {

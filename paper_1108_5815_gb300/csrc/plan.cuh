@@ -101,8 +101,8 @@ struct PlanMemory {
 
 // Enqueues one solve of the plan: st runs the tree, traversal and P2P, fs the
 // far-field chain; fork/join order fs after the traversal and st after fs.
-void enqueue_plan(const PlanShape &s, const PlanBuffers &b, cudaStream_t st, cudaStream_t fs, cudaEvent_t fork,
-                  cudaEvent_t join);
+void enqueue_plan(const PlanShape &s, const PlanBuffers &b, cudaStream_t st, cudaStream_t fs, cudaEvent_t tree,
+                  cudaEvent_t fork, cudaEvent_t join);
 
 // Zeroes the sizes block and sets the roots: level 0 = [0, nsys), tiles of the roots.
 __global__ void k_plan_init(int *sz, int nsys);

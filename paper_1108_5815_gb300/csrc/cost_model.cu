@@ -227,6 +227,8 @@ std::vector<double> pretime_p2l(int p, const std::vector<int> &counts, uint64_t 
     DevBuf<uint64_t> prefix(2 * kMaxCells);
     DevBuf<float> L((size_t)2 * kMaxCells * P2pad);
     DevBuf<double> box(4);
+    DevBuf<int4> geom(2 * kMaxCells);
+    DevBuf<float4> fhi(2 * kMaxCells), flo(2 * kMaxCells);
     k_synth_points<<<1024, 256, 0, st>>>(pts.p, kMaxSources, seed);
     FMM_LAUNCH_CHECK();
     const double hbox[4] = {0.0, 0.0, 0.0, 1.0};
@@ -237,6 +239,18 @@ std::vector<double> pretime_p2l(int p, const std::vector<int> &counts, uint64_t 
     FMM_CUDA_TRY(cudaMemcpyAsync(level.p, hl.data(), sizeof(int) * hl.size(), cudaMemcpyHostToDevice, st));
     FMM_CUDA_TRY(cudaMemcpyAsync(sys.p, hs.data(), sizeof(int) * hs.size(), cudaMemcpyHostToDevice, st));
     FMM_CUDA_TRY(cudaMemcpyAsync(prefix.p, hp.data(), sizeof(uint64_t) * hp.size(), cudaMemcpyHostToDevice, st));
+    {
+        // the cells' FP32 frames (the particle offsets of k_p2l)
+        CellArrays g{};
+        g.level = level.p;
+        g.prefix = prefix.p;
+        g.sys = sys.p;
+        g.geom = geom.p;
+        g.fhi = fhi.p;
+        g.flo = flo.p;
+        k_cell_geom<<<(unsigned)ceil_div(2 * kMaxCells, 256), 256, 0, st>>>(g, (int)(2 * kMaxCells), box.p);
+        FMM_LAUNCH_CHECK();
+    }
     const size_t sh = (size_t)32 * (P2pad + 1) * sizeof(float);
     if (sh > 48 * 1024) set_smem_limit_once((const void *)k_p2l, (int)sh);
     cudaEvent_t e0, e1;
@@ -252,6 +266,9 @@ std::vector<double> pretime_p2l(int p, const std::vector<int> &counts, uint64_t 
         c.level = level.p;
         c.prefix = prefix.p;
         c.sys = sys.p;
+        c.geom = geom.p;
+        c.fhi = fhi.p;
+        c.flo = flo.p;
         ListArrays Ls{};
         Ls.p2l_off = off.p;
         Ls.p2l_cnt = cnt.p;

@@ -250,6 +250,19 @@ __device__ __forceinline__ void cell_centre_side(const CellArrays &c, int cell,
 
 constexpr int kMaxChunks = 14;  // ceil(448 / 32): p <= 20
 
+// A particle's offset from a cell's centre in units of the cell side, in FP32:
+// ((x - c_hi) - c_lo) / s with the centre's FP32 hi + lo parts (k_cell_geom).
+struct Frame {
+    float4 hi, lo;
+};
+__device__ __forceinline__ Frame cell_frame(const CellArrays &c, int cell) { return {c.fhi[cell], c.flo[cell]}; }
+__device__ __forceinline__ void frame_offset(const Frame &f, float4 pt, float &x, float &y, float &z)
+{
+    x = __fmul_rn(__fsub_rn(__fsub_rn(pt.x, f.hi.x), f.lo.x), f.hi.w);
+    y = __fmul_rn(__fsub_rn(__fsub_rn(pt.y, f.hi.y), f.lo.y), f.hi.w);
+    z = __fmul_rn(__fsub_rn(__fsub_rn(pt.z, f.hi.z), f.lo.z), f.hi.w);
+}
+
 }  // namespace
 
 // Coefficients of the order-normalised three-term recurrences, for n <= kRecMax
@@ -266,6 +279,11 @@ __constant__ float c_rec_a[kRecTri], c_rec_b[kRecTri], c_rec_d[kRecMax + 1];
 // the lanes of a warp read different entries.
 constexpr int kScaleMax = 448;
 __device__ float g_l2p_scale[3][kScaleMax];
+// P2M writes the real coefficients of a particle in the order its recurrences
+// produce them (orders m and m + 1 together: (m, m), then (n, m), (n, m + 1)
+// for n = m + 1..p, a term m > 0 giving its real and imaginary parts); entry
+// [p][g] is the stored coefficient index of the g-th value produced.
+__device__ short g_p2m_perm[kRecMax][kScaleMax];
 
 void init_recurrence_tables()
 {
@@ -294,115 +312,135 @@ void init_recurrence_tables()
         sc[2][k] = (float)std::sqrt((double)(n + m) * (n + m - 1));
     }
     FMM_CUDA_TRY(cudaMemcpyToSymbol(g_l2p_scale, sc, sizeof(sc)));
+    static short perm[kRecMax][kScaleMax];
+    for (int pp = 0; pp < kRecMax; ++pp) {
+        int g = 0;
+        auto put = [&](int n, int m) {
+            if (m == 0) {
+                perm[pp][g++] = (short)(n * n);
+            } else {
+                perm[pp][g++] = (short)(n * n + 2 * m - 1);
+                perm[pp][g++] = (short)(n * n + 2 * m);
+            }
+        };
+        for (int m = 0; m <= pp; m += 2) {
+            put(m, m);
+            for (int n = m + 1; n <= pp; ++n) {
+                put(n, m);
+                put(n, m + 1);
+            }
+        }
+        for (; g < kScaleMax; ++g) perm[pp][g] = -1;
+    }
+    FMM_CUDA_TRY(cudaMemcpyToSymbol(g_p2m_perm, perm, sizeof(perm)));
     FMM_CUDA_TRY(cudaMemcpyToSymbol(c_rec_a, a, sizeof(a)));
     FMM_CUDA_TRY(cudaMemcpyToSymbol(c_rec_b, b, sizeof(b)));
     FMM_CUDA_TRY(cudaMemcpyToSymbol(c_rec_d, d, sizeof(d)));
     if (dev < 64) done[dev] = true;
 }
 
-// One warp per leaf.  Each lane evaluates R^(xi) of one particle into its
-// shared-memory row; the lanes then sum the rows column by column.
+// One warp per leaf.  Each lane evaluates q R^(x - c) of one particle; the
+// values are written, in the order the recurrences produce them, into a 32 x 32
+// tile of shared memory (a row per lane), and every 32 values the lanes sum the
+// tile's columns, so a warp needs only 6 KB of shared memory.  The column sums
+// accumulate per produced value in shared memory and are written to their
+// stored indices at the end.
 __global__ void __launch_bounds__(32)
     k_p2m(CellArrays c, const int *__restrict__ leaves, int nleaves, const float4 *__restrict__ pts,
           const double *__restrict__ box, int p, int P2pad, float *__restrict__ M, const int *__restrict__ sz)
 {
-    extern __shared__ float rows[];  // 32 x (P2pad + 1)
+    __shared__ float tile[32 * 33];
+    __shared__ float colsum[kMaxChunks * 32];  // sums of produced values, by batch of 32
     if (sz) nleaves = sz[kSzLeaves];
     const int li = blockIdx.x;
     if (li >= nleaves) return;
     const int cell = leaves[li];
     const int lane = threadIdx.x;
-    const int stride = P2pad + 1;
-    double cen[3], s;
-    cell_centre_side(c, cell, box, cen, s);
-    const double is = 1.0 / s;
+    const Frame fr = cell_frame(c, cell);
     const int b = c.begin[cell], e = c.end[cell];
-    float acc[kMaxChunks];
-#pragma unroll
-    for (int j = 0; j < kMaxChunks; ++j) acc[j] = 0.f;
-    float *row = rows + lane * stride;
-    // the padding columns stay zero; a lane past the leaf's end writes a zero row
-    for (int k = nterms(p); k < P2pad; ++k) row[k] = 0.f;
+    const int P2 = nterms(p);
+    for (int j = lane; j < kMaxChunks * 32; j += 32) colsum[j] = 0.f;
+    float *row = tile + lane * 33;
     for (int base = b; base < e; base += 32) {
         const int i = base + lane;
-        if (i >= e)
-            for (int k = 0; k < P2pad; ++k) row[k] = 0.f;
+        // a lane past the leaf's end adds zeros: charge 0 at the centre (finite harmonics)
+        float x = 0.f, y = 0.f, z = 0.f, q = 0.f;
         if (i < e) {
             const float4 pt = pts[i];
-            const float x = (float)(((double)pt.x - cen[0]) * is);
-            const float y = (float)(((double)pt.y - cen[1]) * is);
-            const float z = (float)(((double)pt.z - cen[2]) * is);
-            const float q = pt.w;
-            const float r2 = x * x + y * y + z * z;
-            auto put = [&](int n, int m, float rr, float ri) {
-                if (m == 0) {
-                    row[n * n] = q * rr;
-                } else {
-                    row[n * n + 2 * m - 1] = q * rr;
-                    row[n * n + 2 * m] = -q * ri;
-                }
-            };
-            // orders m and m + 1 advance together: two independent recurrences in n
-            float mre = 1.f, mim = 0.f;  // R^_m^m
-            for (int m = 0; m <= p; m += 2) {
-                if (m > 0) {
-                    const float f = c_rec_d[m];
-                    const float nre = f * (x * mre - y * mim), nim = f * (x * mim + y * mre);
-                    mre = nre;
-                    mim = nim;
-                }
-                float bre = 0.f, bim = 0.f;  // R^_{m+1}^{m+1}
-                if (m + 1 <= p) {
-                    const float f = c_rec_d[m + 1];
-                    bre = f * (x * mre - y * mim);
-                    bim = f * (x * mim + y * mre);
-                }
-                put(m, m, mre, mim);
-                float a2r = 0.f, a2i = 0.f, a1r = mre, a1i = mim;  // chain m
-                float b2r = 0.f, b2i = 0.f, b1r = bre, b1i = bim;  // chain m + 1
-                for (int n = m + 1; n <= p; ++n) {
-                    const int ta = n * (n + 1) / 2 + m;
-                    const float aa = c_rec_a[ta] * z, ab = c_rec_b[ta] * r2;
-                    const float rr = aa * a1r - ab * a2r, ri = aa * a1i - ab * a2i;
-                    a2r = a1r;
-                    a2i = a1i;
-                    a1r = rr;
-                    a1i = ri;
-                    put(n, m, rr, ri);
-                    float qr = b1r, qi = b1i;  // n == m + 1: the diagonal itself
-                    if (n > m + 1) {
-                        const int tb = ta + 1;
-                        const float ba = c_rec_a[tb] * z, bb = c_rec_b[tb] * r2;
-                        qr = ba * b1r - bb * b2r;
-                        qi = ba * b1i - bb * b2i;
-                        b2r = b1r;
-                        b2i = b1i;
-                        b1r = qr;
-                        b1i = qi;
-                    }
-                    put(n, m + 1, qr, qi);
-                }
-                mre = bre;  // the next pair starts from R^_{m+1}^{m+1}
-                mim = bim;
-            }
+            frame_offset(fr, pt, x, y, z);
+            q = pt.w;
         }
-        __syncwarp();
-#pragma unroll
-        for (int j = 0; j < kMaxChunks; ++j) {
-            const int k = lane + 32 * j;
-            if (k < P2pad) {
-                float sum = 0.f;
-                for (int r = 0; r < 32; ++r) sum += rows[r * stride + k];
-                acc[j] += sum;
+        const float r2 = x * x + y * y + z * z;
+        int g = 0;  // values produced so far (the same in every lane)
+        auto flush = [&]() {
+            __syncwarp();
+            float sum = 0.f;
+#pragma unroll 8
+            for (int r = 0; r < 32; ++r) sum += tile[r * 33 + lane];
+            colsum[((g - 1) & ~31) + lane] += sum;
+            __syncwarp();
+        };
+        auto put1 = [&](float v) {
+            row[g & 31] = v;
+            if ((++g & 31) == 0) flush();
+        };
+        auto put = [&](int m, float rr, float ri) {
+            put1(q * rr);
+            if (m > 0) put1(-q * ri);
+        };
+        // orders m and m + 1 advance together: two independent recurrences in n
+        float mre = 1.f, mim = 0.f;  // R^_m^m
+        for (int m = 0; m <= p; m += 2) {
+            if (m > 0) {
+                const float f = c_rec_d[m];
+                const float nre = f * (x * mre - y * mim), nim = f * (x * mim + y * mre);
+                mre = nre;
+                mim = nim;
             }
+            float bre = 0.f, bim = 0.f;  // R^_{m+1}^{m+1}
+            if (m + 1 <= p) {
+                const float f = c_rec_d[m + 1];
+                bre = f * (x * mre - y * mim);
+                bim = f * (x * mim + y * mre);
+            }
+            put(m, mre, mim);
+            float a2r = 0.f, a2i = 0.f, a1r = mre, a1i = mim;  // chain m
+            float b2r = 0.f, b2i = 0.f, b1r = bre, b1i = bim;  // chain m + 1
+            for (int n = m + 1; n <= p; ++n) {
+                const int ta = n * (n + 1) / 2 + m;
+                const float aa = c_rec_a[ta] * z, ab = c_rec_b[ta] * r2;
+                const float rr = aa * a1r - ab * a2r, ri = aa * a1i - ab * a2i;
+                a2r = a1r;
+                a2i = a1i;
+                a1r = rr;
+                a1i = ri;
+                put(m, rr, ri);
+                float qr = b1r, qi = b1i;  // n == m + 1: the diagonal itself
+                if (n > m + 1) {
+                    const int tb = ta + 1;
+                    const float ba = c_rec_a[tb] * z, bb = c_rec_b[tb] * r2;
+                    qr = ba * b1r - bb * b2r;
+                    qi = ba * b1i - bb * b2i;
+                    b2r = b1r;
+                    b2i = b1i;
+                    b1r = qr;
+                    b1i = qi;
+                }
+                put(m + 1, qr, qi);
+            }
+            mre = bre;  // the next pair starts from R^_{m+1}^{m+1}
+            mim = bim;
         }
-        __syncwarp();
+        if (g & 31) {  // the last, partial tile: zero its unused columns first
+            for (int k = g & 31; k < 32; ++k) row[k] = 0.f;
+            g = (g | 31) + 1;
+            flush();
+        }
     }
-#pragma unroll
-    for (int j = 0; j < kMaxChunks; ++j) {
-        const int k = lane + 32 * j;
-        if (k < P2pad) M[(int64_t)cell * P2pad + k] = acc[j];
-    }
+    __syncwarp();
+    float *out = M + (int64_t)cell * P2pad;
+    for (int gg = lane; gg < P2; gg += 32) out[g_p2m_perm[p][gg]] = colsum[gg];
+    for (int k = P2 + lane; k < P2pad; k += 32) out[k] = 0.f;
 }
 
 // Octant-batched shifts.  A block takes 32 consecutive parents of one level, one
@@ -642,72 +680,75 @@ void launch_shift_batched(bool l2l, const CellArrays &c, int a, int b, const flo
 }
 
 // One warp per leaf: far-field potential and gradient from the leaf's local
-// expansion.  Shared memory holds the expansion and three rescaled copies that
-// fold in the normalisation ratios of the derivative ladder.
+// expansion, phi = Re sum L^ R^, d/dz and D+ = d/dx + i d/dy from the
+// derivative ladder.  Every term (n, m), m >= 0, reads one record of 8 floats
+// from shared memory (two 16-byte loads), built once per leaf with the
+// normalisation ratios, the weight 2 of the m > 0 real parts and the two D+
+// contributions already combined:
+//   [w Lr, w Li, w Lzr, w Lzi, X1r - X2r, X1i - X2i, X1r + X2r, X1i + X2i]
+// with Lz = L_{n+1}^m s0, X1 = L_{n+1}^{m-1} s1 (m >= 1), X2 = L_{n+1}^{m+1} s2
+// (zero past n + 1 > p), so that
+//   phi += w(Lr rr - Li ri),  dz += w(Lzr rr - Lzi ri),
+//   dpr += (X1r - X2r) rr - (X1i - X2i) ri,  dpi += (X1r + X2r) ri + (X1i + X2i) rr.
 __global__ void __launch_bounds__(32)
     k_l2p(CellArrays c, const int *__restrict__ leaves, int nleaves, const float4 *__restrict__ pts,
           const double *__restrict__ box, int p, int P2pad, const float *__restrict__ L,
           float4 *__restrict__ far, const int *__restrict__ sz)
 {
-    extern __shared__ float sl[];  // 4 x P2pad: L, Lz, Lx1, Lx2
+    extern __shared__ float4 l2p_sm[];  // 2 x ntri records, then P2pad floats of L
     if (sz) nleaves = sz[kSzLeaves];
     const int li = blockIdx.x;
     if (li >= nleaves) return;
     const int cell = leaves[li];
     const int lane = threadIdx.x;
-    float *Lh = sl, *Lz = sl + P2pad, *Lx1 = sl + 2 * P2pad, *Lx2 = sl + 3 * P2pad;
-    const int P2 = nterms(p);
-    for (int k = lane; k < P2pad; k += 32) {
-        const float v = k < P2 ? L[(int64_t)cell * P2pad + k] : 0.f;
-        Lh[k] = v;
-        Lz[k] = v * g_l2p_scale[0][k];
-        Lx1[k] = v * g_l2p_scale[1][k];
-        Lx2[k] = v * g_l2p_scale[2][k];
+    const int P2 = nterms(p), ntri = (p + 1) * (p + 2) / 2;
+    float4 *rec = l2p_sm;
+    float *Lh = reinterpret_cast<float *>(l2p_sm + 2 * ntri);
+    for (int k = lane; k < P2; k += 32) Lh[k] = L[(int64_t)cell * P2pad + k];
+    __syncwarp();
+    for (int t = lane; t < ntri; t += 32) {
+        int n = 0;
+        while ((n + 1) * (n + 2) / 2 <= t) ++n;
+        const int m = t - n * (n + 1) / 2;
+        const float w = m == 0 ? 1.f : 2.f;
+        const int k = n * n + (m == 0 ? 0 : 2 * m - 1);
+        float lr = Lh[k], lim = m == 0 ? 0.f : Lh[k + 1];
+        float zr = 0.f, zi = 0.f, x1r = 0.f, x1i = 0.f, x2r = 0.f, x2i = 0.f;
+        if (n + 1 <= p) {
+            const int base = (n + 1) * (n + 1);
+            const int kz = base + (m == 0 ? 0 : 2 * m - 1);
+            zr = Lh[kz] * g_l2p_scale[0][kz];
+            zi = m == 0 ? 0.f : Lh[kz + 1] * g_l2p_scale[0][kz];
+            if (m >= 1) {
+                const int k1 = base + (m == 1 ? 0 : 2 * (m - 1) - 1);
+                x1r = Lh[k1] * g_l2p_scale[1][k1];
+                x1i = m == 1 ? 0.f : Lh[k1 + 1] * g_l2p_scale[1][k1];
+            }
+            const int k2 = base + 2 * (m + 1) - 1;
+            x2r = Lh[k2] * g_l2p_scale[2][k2];
+            x2i = Lh[k2 + 1] * g_l2p_scale[2][k2];
+        }
+        rec[2 * t] = make_float4(w * lr, w * lim, w * zr, w * zi);
+        rec[2 * t + 1] = make_float4(x1r - x2r, x1i - x2i, x1r + x2r, x1i + x2i);
     }
     __syncwarp();
-    double cen[3], s;
-    cell_centre_side(c, cell, box, cen, s);
-    const double is = 1.0 / s;
-    const float inv_s = (float)is, inv_s2 = (float)(is * is);
+    const Frame fr = cell_frame(c, cell);
+    const float inv_s = fr.hi.w, inv_s2 = inv_s * inv_s;
     const int b = c.begin[cell], e = c.end[cell];
-    // one (n, m) term of phi, d/dz and D+ = d/dx + i d/dy into the sums s
     struct Sums {
         float phi, dz, dpr, dpi;
     };
-    auto term = [&](int n, int m, float rr, float ri, Sums &sm) {
-        const float w = m == 0 ? 1.f : 2.f;
-        {  // phi += w Re(L_n^m R_n^m)
-            const int k = n * n + (m == 0 ? 0 : 2 * m - 1);
-            const float lr = Lh[k], lim = m == 0 ? 0.f : Lh[k + 1];
-            sm.phi += w * (lr * rr - lim * ri);
-        }
-        if (n + 1 <= p) {
-            const int n1 = n + 1, base = n1 * n1;
-            {  // dz += w Re(Lz_{n+1}^m R_n^m)
-                const int k = base + (m == 0 ? 0 : 2 * m - 1);
-                const float lr = Lz[k], lim = m == 0 ? 0.f : Lz[k + 1];
-                sm.dz += w * (lr * rr - lim * ri);
-            }
-            if (m >= 1) {  // D+ += Lx1_{n+1}^{m-1} R_n^m
-                const int mm = m - 1;
-                const int k = base + (mm == 0 ? 0 : 2 * mm - 1);
-                const float lr = Lx1[k], lim = mm == 0 ? 0.f : Lx1[k + 1];
-                sm.dpr += lr * rr - lim * ri;
-                sm.dpi += lr * ri + lim * rr;
-            }
-            {  // D+ -= conj(Lx2_{n+1}^{m+1} R_n^m)
-                const int k = base + 2 * (m + 1) - 1;
-                const float lr = Lx2[k], lim = Lx2[k + 1];
-                sm.dpr -= lr * rr - lim * ri;
-                sm.dpi += lr * ri + lim * rr;
-            }
-        }
+    auto term = [&](int t, float rr, float ri, Sums &sm) {
+        const float4 u = rec[2 * t], v = rec[2 * t + 1];
+        sm.phi = fmaf(u.x, rr, fmaf(-u.y, ri, sm.phi));
+        sm.dz = fmaf(u.z, rr, fmaf(-u.w, ri, sm.dz));
+        sm.dpr = fmaf(v.x, rr, fmaf(-v.y, ri, sm.dpr));
+        sm.dpi = fmaf(v.z, ri, fmaf(v.w, rr, sm.dpi));
     };
     for (int i = b + lane; i < e; i += 32) {
         const float4 pt = pts[i];
-        const float x = (float)(((double)pt.x - cen[0]) * is);
-        const float y = (float)(((double)pt.y - cen[1]) * is);
-        const float z = (float)(((double)pt.z - cen[2]) * is);
+        float x, y, z;
+        frame_offset(fr, pt, x, y, z);
         const float r2 = x * x + y * y + z * z;
         // orders m and m + 1 advance together (two independent recurrences in n,
         // each with its own sums) so that a lane has two chains in flight
@@ -727,18 +768,19 @@ __global__ void __launch_bounds__(32)
                 bre = f * (x * mre - y * mim);
                 bim = f * (x * mim + y * mre);
             }
-            term(m, m, mre, mim, sa);
+            int ta = m * (m + 1) / 2 + m;  // term (m, m)
+            term(ta, mre, mim, sa);
             float a2r = 0.f, a2i = 0.f, a1r = mre, a1i = mim;  // chain m
             float b2r = 0.f, b2i = 0.f, b1r = bre, b1i = bim;  // chain m + 1
             for (int n = m + 1; n <= p; ++n) {
-                const int ta = n * (n + 1) / 2 + m;
+                ta += n;  // term (n, m)
                 const float aa = c_rec_a[ta] * z, ab = c_rec_b[ta] * r2;
                 const float rr = aa * a1r - ab * a2r, ri = aa * a1i - ab * a2i;
                 a2r = a1r;
                 a2i = a1i;
                 a1r = rr;
                 a1i = ri;
-                term(n, m, rr, ri, sa);
+                term(ta, rr, ri, sa);
                 float qr = b1r, qi = b1i;  // n == m + 1: the diagonal itself
                 if (n > m + 1) {
                     const int tb = ta + 1;
@@ -750,7 +792,7 @@ __global__ void __launch_bounds__(32)
                     b1r = qr;
                     b1i = qi;
                 }
-                term(n, m + 1, qr, qi, sb);
+                term(ta + 1, qr, qi, sb);
             }
             mre = bre;  // the next pair starts from R^_{m+1}^{m+1}
             mim = bim;
@@ -791,9 +833,7 @@ __global__ void __launch_bounds__(32)
     const int *slist = Ls.p2l_src + Ls.p2l_off[cell];
     const int lane = threadIdx.x;
     const int stride = P2pad + 1;
-    double cen[3], s;
-    cell_centre_side(c, cell, box, cen, s);
-    const double is = 1.0 / s;
+    const Frame fr = cell_frame(c, cell);
     float acc[kMaxChunks];
 #pragma unroll
     for (int j = 0; j < kMaxChunks; ++j) acc[j] = 0.f;
@@ -806,9 +846,8 @@ __global__ void __launch_bounds__(32)
             for (int j = 0; j < P2pad; ++j) row[j] = 0.f;
             if (i < e) {
                 const float4 pt = pts[i];
-                const float x = (float)(((double)pt.x - cen[0]) * is);
-                const float y = (float)(((double)pt.y - cen[1]) * is);
-                const float z = (float)(((double)pt.z - cen[2]) * is);
+                float x, y, z;
+                frame_offset(fr, pt, x, y, z);
                 const float q = pt.w;
                 const float r2 = x * x + y * y + z * z, ir2 = 1.f / r2;
                 float mre = rsqrtf(r2), mim = 0.f;  // I^_m^m

@@ -391,6 +391,8 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
         c.lane = need<int>(ws, "c_lane", cap, st, keep);
         c.sys = need<int>(ws, "c_sys", cap, st, keep);
         c.geom = need<int4>(ws, "c_geom", cap, st, keep);
+        c.fhi = need<float4>(ws, "c_fhi", cap, st, keep);
+        c.flo = need<float4>(ws, "c_flo", cap, st, keep);
         return c;
     };
     CellArrays c = cells(cell_cap, false);
@@ -509,7 +511,7 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
         FMM_LAUNCH_CHECK();
         sync_point(ws, st, flags, {{lex + ncells, sizeof(int)}}, &nleaves);
     }
-    k_cell_geom<<<grid_for(ncells, 256), 256, 0, st>>>(c, ncells);
+    k_cell_geom<<<grid_for(ncells, 256), 256, 0, st>>>(c, ncells, box);
     FMM_LAUNCH_CHECK();
     ev.rec(1, st);
 
@@ -541,12 +543,8 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
         M = need<float>(ws, "M", (size_t)ncells * P2pad, fs);
         Lx = need<float>(ws, "L", (size_t)ncells * P2pad, fs);
         ev.rec(2, fs);
-        {
-            const size_t sh = (size_t)32 * (P2pad + 1) * sizeof(float);
-            if (sh > 48 * 1024) set_smem_limit_once((const void *)k_p2m, (int)sh);
-            k_p2m<<<nleaves, 32, sh, fs>>>(c, leaves, nleaves, pts, box, p, P2pad, M);
-            FMM_LAUNCH_CHECK();
-        }
+        k_p2m<<<nleaves, 32, 0, fs>>>(c, leaves, nleaves, pts, box, p, P2pad, M);
+        FMM_LAUNCH_CHECK();
         float *mtmp = need<float>(ws, "m2m_tmp", (size_t)ncells * P2pad, fs);
         for (int l = depth - 1; l >= 0; --l) {
             const int a = lstart[l], b = lstart[l + 1];
@@ -869,7 +867,7 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
             launch_shift_fp64(true, c, lstart[l], lstart[l + 1], get<double>(ws, "l2l64"), P2, P2pad, Lx, fs);
         else
             launch_shift_batched(true, c, lstart[l], lstart[l + 1], get<float>(ws, "l2l"), P2, P2pad, Lx, nullptr, fs);
-    k_l2p<<<nleaves, 32, 4 * P2pad * sizeof(float), fs>>>(c, leaves, nleaves, pts, box, p, P2pad, Lx,
+    k_l2p<<<nleaves, 32, l2p_smem(p, P2pad), fs>>>(c, leaves, nleaves, pts, box, p, P2pad, Lx,
                                                           far);
     FMM_LAUNCH_CHECK();
     if (m2p_total > 0) {  // cell-particle pairs of the hybrid selection, added to the far field
@@ -1208,6 +1206,8 @@ void build_plan(fmm_plan &pl, Workspace &ws, const int64_t *offsets, const uint8
     b.c.lane = m.get<int>(cc);
     b.c.sys = m.get<int>(cc);
     b.c.geom = m.get<int4>(cc);
+    b.c.fhi = m.get<float4>(cc);
+    b.c.flo = m.get<float4>(cc);
     b.blvl = m.get<uint64_t>(std::max(N - 1, 1));
     b.bpos = m.get<uint32_t>(std::max(N - 1, 1));
     b.bstart = m.get<int>(24);
@@ -1319,7 +1319,6 @@ void build_plan(fmm_plan &pl, Workspace &ws, const int64_t *offsets, const uint8
     // have run the hybrid kernels)
     const int rows_smem = (int)((size_t)32 * (P2pad + 1) * sizeof(float));
     if (rows_smem > 48 * 1024) {
-        set_smem_limit_once((const void *)k_p2m, rows_smem);
         set_smem_limit_once((const void *)k_p2l, rows_smem);
     }
     if (s.hybrid && m2p_smem(s.p, P2pad) > 48 * 1024)

@@ -51,6 +51,9 @@ struct CellArrays {
     int *tile, *lane;  // M2L GEMM tile of this cell as a target
     int *sys;          // independent system (root) the cell belongs to
     int4 *geom;        // integer centre (x, y, z) in units of side/2^22 and half side
+    // centre in FP32 as hi + lo parts with 1/side (fhi.w) and side (flo.w): the frame
+    // of the expansion kernels' particle offsets, without FP64 per particle
+    float4 *fhi, *flo;
 };
 
 // Interaction lists written by the traversal (CSR per target cell).
@@ -102,7 +105,7 @@ __global__ void k_level_advance(const int64_t *total, int level, int last_level,
                                 int next_level_cap, int tile_cap, int *sz);
 __global__ void k_fill_tile_cells(CellArrays c, int ncells, int *tile_cells, const int *sz = nullptr);
 // c.geom of every cell from its level and key prefix (with sz: the cell count from sz).
-__global__ void k_cell_geom(CellArrays c, int ncells, const int *sz = nullptr);
+__global__ void k_cell_geom(CellArrays c, int ncells, const double *box, const int *sz = nullptr);
 // With sz: flags for len cells, zero past the last cell.
 __global__ void k_leaf_flags(CellArrays c, int ncells, int *flag, const int *sz = nullptr, int len = 0);
 __global__ void k_leaf_compact(CellArrays c, int ncells, const int *ex, int *leaves, const int *sz = nullptr);
@@ -180,6 +183,9 @@ void launch_shift_fp64(bool l2l, const CellArrays &c, int a, int b, const double
 __global__ void k_l2p(CellArrays c, const int *leaves, int nleaves, const float4 *pts,
                       const double *box, int p, int P2pad, const float *L, float4 *far,
                       const int *sz = nullptr);
+// Dynamic shared memory of k_l2p: one 32-byte record per term (n, m), m <= n <= p,
+// then the leaf's P2pad coefficients.
+inline size_t l2p_smem(int p, int P2pad) { return (size_t)(p + 1) * (p + 2) / 2 * 32 + (size_t)P2pad * 4; }
 // P2L: one warp (block) per target cell with a P2L list; the source particles are
 // added to the cell's local expansion.  Dynamic shared memory 32 (P2pad + 1) floats.
 __global__ void k_p2l(CellArrays c, ListArrays Ls, int ncells, const float4 *pts, const double *box, int p,

@@ -96,14 +96,14 @@ void enqueue_plan(const PlanShape &s, const PlanBuffers &b, cudaStream_t st, cud
     k_leaf_compact<<<blocks_for(s.cell_cap, 256), 256, 0, st>>>(c, 0, b.leaf_ex, b.leaves, b.sz);
     FMM_LAUNCH_CHECK();
     FMM_CUDA_TRY(cudaMemcpyAsync(b.sz + kSzLeaves, b.leaf_ex + s.cell_cap, sizeof(int), cudaMemcpyDeviceToDevice, st));
-    k_cell_geom<<<grid_stride(s.cell_cap), 256, 0, st>>>(c, 0, b.sz);
+    k_cell_geom<<<grid_stride(s.cell_cap), 256, 0, st>>>(c, 0, b.box, b.sz);
     FMM_LAUNCH_CHECK();
 
     // ---------------------------------------------------------- upward pass (fs, beside the traversal)
     const int p = s.p, P2 = s.P2, P2pad = s.P2pad;
     FMM_CUDA_TRY(cudaEventRecord(tree, st));
     FMM_CUDA_TRY(cudaStreamWaitEvent(fs, tree, 0));
-    k_p2m<<<(unsigned)std::max(1, s.leaf_cap), 32, (size_t)32 * (P2pad + 1) * sizeof(float), fs>>>(
+    k_p2m<<<(unsigned)std::max(1, s.leaf_cap), 32, 0, fs>>>(
         c, b.leaves, 0, b.pts, b.box, p, P2pad, b.M, b.sz);
     FMM_LAUNCH_CHECK();
     for (int l = s.levels - 1; l >= 0; --l) {
@@ -201,7 +201,7 @@ void enqueue_plan(const PlanShape &s, const PlanBuffers &b, cudaStream_t st, cud
         else
             launch_shift_batched(true, c, 0, 0, b.l2l, P2, P2pad, b.Lx, nullptr, fs, b.sz, l, s.level_cap[l]);
     }
-    k_l2p<<<(unsigned)std::max(1, s.leaf_cap), 32, 4 * (size_t)P2pad * sizeof(float), fs>>>(
+    k_l2p<<<(unsigned)std::max(1, s.leaf_cap), 32, l2p_smem(p, P2pad), fs>>>(
         c, b.leaves, 0, b.pts, b.box, p, P2pad, b.Lx, b.far, b.sz);
     FMM_LAUNCH_CHECK();
     if (s.hybrid) {

@@ -424,16 +424,30 @@ __global__ void k_level_advance(const int64_t *__restrict__ total, int level, in
     sz[kSzCells] = b + nch;
 }
 
-__global__ void k_cell_geom(CellArrays c, int ncells, const int *__restrict__ sz)
+__global__ void k_cell_geom(CellArrays c, int ncells, const double *__restrict__ box, const int *__restrict__ sz)
 {
     if (sz) ncells = sz[kSzCells];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ncells; i += gridDim.x * blockDim.x) {
-        const int h = 1 << (kKeyBits - c.level[i]);
+        const int l = c.level[i];
+        const int h = 1 << (kKeyBits - l);
         const uint64_t pre = c.prefix[i];
         int C[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) C[a] = (2 * (int)compact3_dev(pre >> a) + 1) * h;
         c.geom[i] = make_int4(C[0], C[1], C[2], h);
+        // real centre lo + (2k + 1) side / 2^(l+1) of the cell's own system box, split
+        // into FP32 hi + lo; side and 1/side of the cell in FP32
+        const double *bx = box + 4 * c.sys[i];
+        const double s = ldexp(bx[3], -l), half = ldexp(bx[3], -l - 1);
+        float hi[3], lo[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const double cen = bx[a] + (double)(2 * (int64_t)compact3_dev(pre >> a) + 1) * half;
+            hi[a] = (float)cen;
+            lo[a] = (float)(cen - (double)hi[a]);
+        }
+        c.fhi[i] = make_float4(hi[0], hi[1], hi[2], (float)(1.0 / s));
+        c.flo[i] = make_float4(lo[0], lo[1], lo[2], (float)s);
     }
 }
 

@@ -345,10 +345,14 @@ void init_recurrence_tables()
 // tile's columns, so a warp needs only 6 KB of shared memory.  The column sums
 // accumulate per produced value in shared memory and are written to their
 // stored indices at the end.
+// PT > 0: the expansion order as a compile-time constant (loops unrolled, the
+// recurrence coefficients and shared-memory offsets folded); PT = 0: p at run time.
+template <int PT>
 __global__ void __launch_bounds__(32)
     k_p2m(CellArrays c, const int *__restrict__ leaves, int nleaves, const float4 *__restrict__ pts,
-          const double *__restrict__ box, int p, int P2pad, float *__restrict__ M, const int *__restrict__ sz)
+          int p_run, int P2pad, float *__restrict__ M, const int *__restrict__ sz)
 {
+    const int p = PT > 0 ? PT : p_run;
     __shared__ float tile[32 * 33];
     __shared__ float colsum[kMaxChunks * 32];  // sums of produced values, by batch of 32
     if (sz) nleaves = sz[kSzLeaves];
@@ -390,6 +394,7 @@ __global__ void __launch_bounds__(32)
         };
         // orders m and m + 1 advance together: two independent recurrences in n
         float mre = 1.f, mim = 0.f;  // R^_m^m
+#pragma unroll
         for (int m = 0; m <= p; m += 2) {
             if (m > 0) {
                 const float f = c_rec_d[m];
@@ -406,6 +411,7 @@ __global__ void __launch_bounds__(32)
             put(m, mre, mim);
             float a2r = 0.f, a2i = 0.f, a1r = mre, a1i = mim;  // chain m
             float b2r = 0.f, b2i = 0.f, b1r = bre, b1i = bim;  // chain m + 1
+#pragma unroll
             for (int n = m + 1; n <= p; ++n) {
                 const int ta = n * (n + 1) / 2 + m;
                 const float aa = c_rec_a[ta] * z, ab = c_rec_b[ta] * r2;
@@ -441,6 +447,26 @@ __global__ void __launch_bounds__(32)
     float *out = M + (int64_t)cell * P2pad;
     for (int gg = lane; gg < P2; gg += 32) out[g_p2m_perm[p][gg]] = colsum[gg];
     for (int k = P2 + lane; k < P2pad; k += 32) out[k] = 0.f;
+}
+
+void launch_p2m(const CellArrays &c, const int *leaves, int nleaves, unsigned grid, const float4 *pts, int p,
+                int P2pad, float *M, cudaStream_t st, const int *sz)
+{
+    switch (p) {
+#define FMM_P2M_CASE(P)                                                            \
+    case P:                                                                        \
+        k_p2m<P><<<grid, 32, 0, st>>>(c, leaves, nleaves, pts, p, P2pad, M, sz); \
+        break;
+        FMM_P2M_CASE(4)
+        FMM_P2M_CASE(6)
+        FMM_P2M_CASE(8)
+        FMM_P2M_CASE(10)
+        FMM_P2M_CASE(12)
+#undef FMM_P2M_CASE
+    default:
+        k_p2m<0><<<grid, 32, 0, st>>>(c, leaves, nleaves, pts, p, P2pad, M, sz);
+    }
+    FMM_LAUNCH_CHECK();
 }
 
 // Octant-batched shifts.  A block takes 32 consecutive parents of one level, one
@@ -690,11 +716,12 @@ void launch_shift_batched(bool l2l, const CellArrays &c, int a, int b, const flo
 // (zero past n + 1 > p), so that
 //   phi += w(Lr rr - Li ri),  dz += w(Lzr rr - Lzi ri),
 //   dpr += (X1r - X2r) rr - (X1i - X2i) ri,  dpi += (X1r + X2r) ri + (X1i + X2i) rr.
-__global__ void __launch_bounds__(32)
+template <int PT>
+__global__ void __launch_bounds__(32, 24)
     k_l2p(CellArrays c, const int *__restrict__ leaves, int nleaves, const float4 *__restrict__ pts,
-          const double *__restrict__ box, int p, int P2pad, const float *__restrict__ L,
-          float4 *__restrict__ far, const int *__restrict__ sz)
+          int p_run, int P2pad, const float *__restrict__ L, float4 *__restrict__ far, const int *__restrict__ sz)
 {
+    const int p = PT > 0 ? PT : p_run;  // compile-time order when PT > 0 (as in k_p2m)
     extern __shared__ float4 l2p_sm[];  // 2 x ntri records, then P2pad floats of L
     if (sz) nleaves = sz[kSzLeaves];
     const int li = blockIdx.x;
@@ -754,6 +781,7 @@ __global__ void __launch_bounds__(32)
         // each with its own sums) so that a lane has two chains in flight
         Sums sa = {0.f, 0.f, 0.f, 0.f}, sb = sa;
         float mre = 1.f, mim = 0.f;  // R^_m^m
+#pragma unroll
         for (int m = 0; m <= p; m += 2) {
             if (m > 0) {
                 const float f = c_rec_d[m];
@@ -772,6 +800,7 @@ __global__ void __launch_bounds__(32)
             term(ta, mre, mim, sa);
             float a2r = 0.f, a2i = 0.f, a1r = mre, a1i = mim;  // chain m
             float b2r = 0.f, b2i = 0.f, b1r = bre, b1i = bim;  // chain m + 1
+#pragma unroll 2
             for (int n = m + 1; n <= p; ++n) {
                 ta += n;  // term (n, m)
                 const float aa = c_rec_a[ta] * z, ab = c_rec_b[ta] * r2;
@@ -800,6 +829,27 @@ __global__ void __launch_bounds__(32)
         const float phi = sa.phi + sb.phi, dz = sa.dz + sb.dz, dpr = sa.dpr + sb.dpr, dpi = sa.dpi + sb.dpi;
         far[i] = make_float4(phi * inv_s, dpr * inv_s2, dpi * inv_s2, dz * inv_s2);
     }
+}
+
+void launch_l2p(const CellArrays &c, const int *leaves, int nleaves, unsigned grid, const float4 *pts, int p,
+                int P2pad, const float *L, float4 *far, cudaStream_t st, const int *sz)
+{
+    const size_t sh = l2p_smem(p, P2pad);
+    switch (p) {
+#define FMM_L2P_CASE(P)                                                                    \
+    case P:                                                                                \
+        k_l2p<P><<<grid, 32, sh, st>>>(c, leaves, nleaves, pts, p, P2pad, L, far, sz); \
+        break;
+        FMM_L2P_CASE(4)
+        FMM_L2P_CASE(6)
+        FMM_L2P_CASE(8)
+        FMM_L2P_CASE(10)
+        FMM_L2P_CASE(12)
+#undef FMM_L2P_CASE
+    default:
+        k_l2p<0><<<grid, 32, sh, st>>>(c, leaves, nleaves, pts, p, P2pad, L, far, sz);
+    }
+    FMM_LAUNCH_CHECK();
 }
 
 // Cell-particle (M2P, the treecode kernel): one warp per target leaf with an

@@ -543,8 +543,7 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
         M = need<float>(ws, "M", (size_t)ncells * P2pad, fs);
         Lx = need<float>(ws, "L", (size_t)ncells * P2pad, fs);
         ev.rec(2, fs);
-        k_p2m<<<nleaves, 32, 0, fs>>>(c, leaves, nleaves, pts, box, p, P2pad, M);
-        FMM_LAUNCH_CHECK();
+        launch_p2m(c, leaves, nleaves, (unsigned)nleaves, pts, p, P2pad, M, fs);
         float *mtmp = need<float>(ws, "m2m_tmp", (size_t)ncells * P2pad, fs);
         for (int l = depth - 1; l >= 0; --l) {
             const int a = lstart[l], b = lstart[l + 1];
@@ -867,9 +866,7 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
             launch_shift_fp64(true, c, lstart[l], lstart[l + 1], get<double>(ws, "l2l64"), P2, P2pad, Lx, fs);
         else
             launch_shift_batched(true, c, lstart[l], lstart[l + 1], get<float>(ws, "l2l"), P2, P2pad, Lx, nullptr, fs);
-    k_l2p<<<nleaves, 32, l2p_smem(p, P2pad), fs>>>(c, leaves, nleaves, pts, box, p, P2pad, Lx,
-                                                          far);
-    FMM_LAUNCH_CHECK();
+    launch_l2p(c, leaves, nleaves, (unsigned)nleaves, pts, p, P2pad, Lx, far, fs);
     if (m2p_total > 0) {  // cell-particle pairs of the hybrid selection, added to the far field
         const size_t sh = m2p_smem(p, P2pad);
         if (sh > 48 * 1024) set_smem_limit_once((const void *)k_m2p, (int)sh);

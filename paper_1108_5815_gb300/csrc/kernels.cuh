@@ -164,8 +164,10 @@ __global__ void k_tile_src(const int *m2l_tgt, const int *m2l_src, const uint32_
 __global__ void k_build_m2l_tables(const uint64_t *class_keys, const int *cache_slot, int nnew,
                                    int p, int P2pad, float *table);
 __global__ void k_build_shift_tables(int p, int P2pad, float *m2m, float *l2l, double *m2m64, double *l2l64);
-__global__ void k_p2m(CellArrays c, const int *leaves, int nleaves, const float4 *pts,
-                      const double *box, int p, int P2pad, float *M, const int *sz = nullptr);
+// P2M, one warp (32-thread block) per leaf of leaves[0, nleaves), grid blocks;
+// an instantiation with the order fixed at compile time for p = 4, 6, 8, 10, 12.
+void launch_p2m(const CellArrays &c, const int *leaves, int nleaves, unsigned grid, const float4 *pts, int p,
+                int P2pad, float *M, cudaStream_t st, const int *sz = nullptr);
 // Fills the recurrence-coefficient tables P2M and L2P read (once per device).
 void init_recurrence_tables();
 // M2M (l2l = false: parents [a, b) of E from their children, through the
@@ -180,9 +182,9 @@ void launch_shift_batched(bool l2l, const CellArrays &c, int a, int b, const flo
 constexpr int kFp64TopP = 12, kFp64TopLevels = 3;  // p >= 12: parents at levels 0..2
 void launch_shift_fp64(bool l2l, const CellArrays &c, int a, int b, const double *mats, int P2, int P2pad, float *E,
                        cudaStream_t st, const int *sz = nullptr, int level = 0, int cap = 0);
-__global__ void k_l2p(CellArrays c, const int *leaves, int nleaves, const float4 *pts,
-                      const double *box, int p, int P2pad, const float *L, float4 *far,
-                      const int *sz = nullptr);
+// L2P, one warp (32-thread block) per leaf, as launch_p2m.
+void launch_l2p(const CellArrays &c, const int *leaves, int nleaves, unsigned grid, const float4 *pts, int p,
+                int P2pad, const float *L, float4 *far, cudaStream_t st, const int *sz = nullptr);
 // Dynamic shared memory of k_l2p: one 32-byte record per term (n, m), m <= n <= p,
 // then the leaf's P2pad coefficients.
 inline size_t l2p_smem(int p, int P2pad) { return (size_t)(p + 1) * (p + 2) / 2 * 32 + (size_t)P2pad * 4; }

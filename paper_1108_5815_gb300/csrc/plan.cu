@@ -103,9 +103,7 @@ void enqueue_plan(const PlanShape &s, const PlanBuffers &b, cudaStream_t st, cud
     const int p = s.p, P2 = s.P2, P2pad = s.P2pad;
     FMM_CUDA_TRY(cudaEventRecord(tree, st));
     FMM_CUDA_TRY(cudaStreamWaitEvent(fs, tree, 0));
-    k_p2m<<<(unsigned)std::max(1, s.leaf_cap), 32, 0, fs>>>(
-        c, b.leaves, 0, b.pts, b.box, p, P2pad, b.M, b.sz);
-    FMM_LAUNCH_CHECK();
+    launch_p2m(c, b.leaves, 0, (unsigned)std::max(1, s.leaf_cap), b.pts, p, P2pad, b.M, fs, b.sz);
     for (int l = s.levels - 1; l >= 0; --l) {
         if (p >= kFp64TopP && l < kFp64TopLevels)
             launch_shift_fp64(false, c, 0, 0, b.m2m64, P2, P2pad, b.M, fs, b.sz, l, s.level_cap[l]);
@@ -201,9 +199,7 @@ void enqueue_plan(const PlanShape &s, const PlanBuffers &b, cudaStream_t st, cud
         else
             launch_shift_batched(true, c, 0, 0, b.l2l, P2, P2pad, b.Lx, nullptr, fs, b.sz, l, s.level_cap[l]);
     }
-    k_l2p<<<(unsigned)std::max(1, s.leaf_cap), 32, l2p_smem(p, P2pad), fs>>>(
-        c, b.leaves, 0, b.pts, b.box, p, P2pad, b.Lx, b.far, b.sz);
-    FMM_LAUNCH_CHECK();
+    launch_l2p(c, b.leaves, 0, (unsigned)std::max(1, s.leaf_cap), b.pts, p, P2pad, b.Lx, b.far, fs, b.sz);
     if (s.hybrid) {
         k_m2p<<<blocks_for(s.leaf_cap, kM2PWarps), 32 * kM2PWarps, m2p_smem(p, P2pad), fs>>>(
             c, L, b.leaves, 0, b.pts, b.box, p, P2pad, b.M, b.far, b.sz);

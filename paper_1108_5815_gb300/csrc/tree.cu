@@ -159,6 +159,54 @@ __global__ void k_bbox_sys(const float *__restrict__ xyz, int64_t n, const int *
     if (bad) atomicOr(&flags[kFlagNonfinite], 1);
 }
 
+// Key quantisation k = floor(fl64(fl64(x - lo) * s)), clamped to [0, 2^21 - 1]
+// (FP64, one rounding per operation), taken in FP32 arithmetic when that
+// decides it: the difference x - lo of two floats is exact as dh + dl (TwoSum)
+// and is exact in FP64 when their exponents differ by at most 28; with
+// s = s_hi + s_lo, p + e = (dh + dl)(s_hi + s_lo) (TwoProd for dh s_hi) is
+// within 2^-44 relative (2^-23 absolute below 2^21) of the FP64 product, so
+// floor() is decided whenever p + e lies more than 2^-20 from an integer.
+// Otherwise (false) the caller takes the FP64 operations themselves.
+__device__ __forceinline__ bool quant_fast(float x, float lo, float s_hi, float s_lo, uint32_t &k)
+{
+    const float b = -lo;
+    const float dh = __fadd_rn(x, b);
+    const float bv = __fsub_rn(dh, x), av = __fsub_rn(dh, bv);
+    const float br = __fsub_rn(b, bv), ar = __fsub_rn(x, av);
+    const float dl = __fadd_rn(ar, br);
+    const int ex = (__float_as_int(x) >> 23) & 0xff, el = (__float_as_int(lo) >> 23) & 0xff;
+    if (!(x == 0.f || lo == 0.f || abs(ex - el) <= 28)) return false;
+    const float p = __fmul_rn(dh, s_hi);
+    const float e1 = __fmaf_rn(dh, s_hi, -p);
+    const float e2 = __fmaf_rn(dh, s_lo, __fmul_rn(dl, s_hi));
+    const float e = __fadd_rn(e1, e2);
+    const float k0 = floorf(p);
+    const float r = __fadd_rn(__fsub_rn(p, k0), e);
+    const float m = 9.5367431640625e-07f;  // 2^-20
+    float kf;
+    if (r > m && r < 1.f - m)
+        kf = k0;
+    else if (r > -1.f + m && r < -m)
+        kf = k0 - 1.f;
+    else if (r > 1.f + m && r < 2.f - m)
+        kf = k0 + 1.f;
+    else
+        return false;
+    k = (uint32_t)fminf(fmaxf(kf, 0.f), 2097151.f);
+    return true;
+}
+
+// The same with the FP64 operations.
+__device__ __forceinline__ uint32_t quant_fp64(float x, double lo, double s)
+{
+    const double t = __dsub_rn((double)x, lo);
+    double f = floor(__dmul_rn(t, s));
+    // NaN/Inf inputs are reported through the flag; keep the key in range.
+    if (!(f >= 0.0)) f = 0.0;
+    if (f > 2097151.0) f = 2097151.0;
+    return (uint32_t)f;
+}
+
 // Decodes each system's box into box[4s..4s+3] = lo, side (FP64), then writes
 // keys (quantised in the particle's own system box) and the identity permutation.
 __global__ void k_morton(const float *__restrict__ xyz, int64_t n, const int *__restrict__ off,
@@ -175,33 +223,42 @@ __global__ void k_morton(const float *__restrict__ xyz, int64_t n, const int *__
             box[4 * sy + 3] = side;
         }
     }
-    int sys = 0;
-    double lo[3], side;
-    decode_box(bbox_u, lo, side);
-    // the scale 2^21 / side: one FP64 division per block (FP64 is a slow pipe here)
+    // the first system's box and scale 2^21 / side, once per block (FP64 is a slow
+    // pipe here): lo per axis (floats), the scale in FP64 and as FP32 hi + lo
     __shared__ double s_scale;
-    if (threadIdx.x == 0) s_scale = __ddiv_rn(2097152.0, side);
+    __shared__ float s_lof[3], s_shi, s_slo;
+    if (threadIdx.x == 0) {
+        double lo[3], side;
+        decode_box(bbox_u, lo, side);
+        const double sc = __ddiv_rn(2097152.0, side);
+        s_scale = sc;
+        s_shi = (float)sc;
+        s_slo = (float)(sc - (double)s_shi);
+        for (int a = 0; a < 3; ++a) s_lof[a] = (float)lo[a];
+    }
     __syncthreads();
+    int sys = 0;
     double s = s_scale;
+    float lof[3] = {s_lof[0], s_lof[1], s_lof[2]}, s_hi = s_shi, s_lo = s_slo;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         if (nsys > 1) {
             const int si = system_of(off, nsys, i);
             if (si != sys) {
                 sys = si;
+                double lo[3], side;
                 decode_box(bbox_u + 6 * sys, lo, side);
                 s = __ddiv_rn(2097152.0, side);
+                s_hi = (float)s;
+                s_lo = (float)(s - (double)s_hi);
+                for (int a = 0; a < 3; ++a) lof[a] = (float)lo[a];
             }
         }
         uint32_t k[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            double t = __dsub_rn((double)xyz[3 * i + a], lo[a]);
-            double f = floor(__dmul_rn(t, s));
-            // NaN/Inf inputs are reported through the flag; keep the key in range.
-            if (!(f >= 0.0)) f = 0.0;
-            if (f > 2097151.0) f = 2097151.0;
-            k[a] = (uint32_t)f;
+            const float x = xyz[3 * i + a];
+            if (!quant_fast(x, lof[a], s_hi, s_lo, k[a])) k[a] = quant_fp64(x, (double)lof[a], s);
         }
         keys[i] = spread3_dev(k[0]) | (spread3_dev(k[1]) << 1) | (spread3_dev(k[2]) << 2);
         idx[i] = (uint32_t)i;

@@ -315,18 +315,23 @@ fmm_status fmm_cost_model_samples(float *x, float *t, float *m, int64_t capacity
 fmm_status fmm_morton_sort_noalloc(const float *xyz, int64_t N, uint64_t *keys, int32_t *order,
                                    double *box, void *stream);
 
-/* N_crit from the learned cost model (the benchmark spec's use of the network for
- * the N_crit choice; the paper's section "Results" balances the near and far
- * fields through N_crit).  For each candidate the library builds the tree and
- * the interaction lists of the system (with the options' selection mode; no
- * expansion is evaluated and nothing is timed), bins the P2P pairs by the
- * count buckets of the selection table, and sums the network's predicted time
- * per pair over the bins plus the number of M2L pairs times its predicted M2L
- * time per pair.  pred_ms[k] (may be NULL) receives candidate k's prediction in
- * ms and *best the candidate with the smallest one.  The expansion passes,
- * whose cost grows with the number of cells, are not in the prediction; the
- * measured autotuner (fmm_tune_ncrit) remains the fallback and the judge.
- * Needs a trained or set model (else FMM_ERR_ARG).  Synchronises `stream`. */
+/* N_crit from the learned cost model (the paper's section "Results" balances
+ * the near and far fields through N_crit; the library's network takes that
+ * choice without timing the candidates).  For each candidate the library builds
+ * the tree and the interaction lists of the system (with the options'
+ * selection mode; no expansion is evaluated and the candidate is not timed),
+ * bins the P2P pairs by the count buckets of the selection table, and sums the
+ * network's predicted time per pair over the bins, the number of M2L pairs
+ * times its predicted M2L time per pair, and the number of cells times a
+ * measured time per cell.  That last term is the part of a solve that grows as
+ * N_crit shrinks: tree levels, traversal, upward and downward passes, class and
+ * tile building.  It is the slope of the time outside the P2P and M2L kernels
+ * over the cell count between two solves of an artificial 2^18-particle cube
+ * at N_crit 16 and 64, measured once per (p, theta, precision) and device.
+ * pred_ms[k] (may be NULL) receives candidate k's prediction in ms and *best
+ * the candidate with the smallest one.  The measured autotuner (fmm_tune_ncrit)
+ * remains the fallback and the judge.  Needs a trained or set model (else
+ * FMM_ERR_ARG).  Synchronises `stream`. */
 fmm_status fmm_cost_model_pick_ncrit(const float *xyz, const float *q, int64_t N, int p, double theta, void *stream,
                                      const fmm_options *opt, const int *candidates, int ncand, float *pred_ms,
                                      int *best);

@@ -96,6 +96,7 @@ struct Workspace {
     // hybrid selection: pre-timed kernels and the learned model
     std::vector<P2PTiming> p2p_grid;                      // P2P time per pair on artificial leaves
     std::map<std::tuple<int, uint64_t, int>, double> m2l_ns;  // (p, theta bits, precision) -> ns per pair
+    std::map<std::tuple<int, uint64_t, int>, double> cell_ns;  // (p, theta bits, precision) -> ns per cell
     std::map<int, std::vector<double>> m2p_ns;                // p -> ns per pair for kSelCounts
     std::map<int, std::vector<double>> p2l_ns;                // p -> ns per pair for kSelCounts
     std::map<std::tuple<int, uint64_t, int, int>, std::vector<uint8_t>> tables;  // (mode, theta, p, prec)
@@ -963,6 +964,44 @@ double m2l_ns_per_pair(Workspace &ws, int p, double theta, int prec)
     ws.have_solve = false;
     ws.m2l_ns[key] = best;
     return best;
+}
+
+// Time per cell of the solve outside the P2P and M2L kernels (tree levels,
+// traversal, upward and downward passes, class and tile building), the part of
+// the cost that grows as N_crit shrinks: the slope of (total - P2P - M2L) over
+// the number of cells between two plain solves of the artificial 2^18-particle
+// cube at N_crit 16 and 64 (best of two repetitions each).
+double cell_ns_per_cell(Workspace &ws, int p, double theta, int prec)
+{
+    const auto key = std::make_tuple(p, (uint64_t)std::llround(theta * 1e9), prec);
+    auto it = ws.cell_ns.find(key);
+    if (it != ws.cell_ns.end()) return it->second;
+    ensure_streams(ws);
+    cudaStream_t st = ws.main_stream;
+    const int64_t n = 1 << 18;
+    float *xyz = need<float>(ws, "syn_xyz", 3 * n, st);
+    float *q = need<float>(ws, "syn_q", n, st);
+    float *phi = need<float>(ws, "syn_phi", n, st);
+    float *grad = need<float>(ws, "syn_grad", 3 * n, st);
+    synth_uniform(xyz, q, n, 0x5eed0001ull, st);
+    fmm_options o;
+    fmm_default_options(&o);
+    o.precision_mode = prec;
+    const int64_t off[2] = {0, n};
+    double rest[2] = {1e30, 1e30}, cells[2] = {0, 0};
+    const int ncs[2] = {16, 64};
+    for (int k = 0; k < 2; ++k)
+        for (int rep = 0; rep < 3; ++rep) {
+            fmm_stats s{};
+            solve_locked(ws, xyz, q, n, 1, off, p, theta, ncs[k], phi, grad, st, o, &s, nullptr);
+            if (rep == 0) continue;  // warm-up (operator tables, buffers)
+            rest[k] = std::min(rest[k], (double)(s.ms_total - s.ms_p2p - s.ms_m2l) * 1e6);
+            cells[k] = (double)s.ncells;
+        }
+    ws.have_solve = false;
+    const double slope = cells[0] > cells[1] ? std::max(0.0, (rest[0] - rest[1]) / (cells[0] - cells[1])) : 0.0;
+    ws.cell_ns[key] = slope;
+    return slope;
 }
 
 const std::vector<int> kSelCounts = {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512};
@@ -1848,6 +1887,7 @@ fmm_status fmm_cost_model_pick_ncrit(const float *xyz, const float *q, int64_t N
         ensure_streams(ws);
         cudaStream_t cs = (cudaStream_t)stream, st = ws.main_stream;
         const uint8_t *sel = selection_table(ws, o, p, theta);
+        const double per_cell = cell_ns_per_cell(ws, p, theta, o.precision_mode);
         const int64_t off[2] = {0, N};
         unsigned long long *hist = need<unsigned long long>(ws, "pick_hist", (size_t)kSelNB * kSelNB, st);
         double *cost = need<double>(ws, "pick_cost", 2, st);
@@ -1870,7 +1910,7 @@ fmm_status fmm_cost_model_pick_ncrit(const float *xyz, const float *q, int64_t N
             double h[2];
             FMM_CUDA_TRY(cudaMemcpyAsync(h, cost, sizeof(h), cudaMemcpyDeviceToHost, st));
             FMM_CUDA_TRY(cudaStreamSynchronize(st));
-            const double ns = h[0] + h[1];
+            const double ns = h[0] + h[1] + per_cell * (double)ws.shape.ncells;
             if (pred_ms) pred_ms[k] = (float)(ns * 1e-6);
             if (ns < best_ns) {
                 best_ns = ns;

@@ -50,7 +50,8 @@ struct CellArrays {
     int *parent, *child0, *nchild;
     int *tile, *lane;  // M2L GEMM tile of this cell as a target
     int *sys;          // independent system (root) the cell belongs to
-    int4 *geom;        // integer centre (x, y, z) in units of side/2^22 and half side
+    int4 *geom;        // integer centre (x, y, z) in units of side/2^22; w = half side
+                       // (bits 0-23) | count bucket of the hybrid selection << 24
     // centre in FP32 as hi + lo parts with 1/side (fhi.w) and side (flo.w): the frame
     // of the expansion kernels' particle offsets, without FP64 per particle
     float4 *fhi, *flo;
@@ -113,6 +114,8 @@ __global__ void k_leaf_compact(CellArrays c, int ncells, const int *ex, int *lea
 // traverse.cu
 constexpr int kSelNB = 128;  // count buckets of the hybrid selection table
 // Count bucket of the selection table: n - 1 below 4, then four per octave.
+constexpr int kGeomHalfMask = (1 << 24) - 1;
+constexpr int kGeomBucketShift = 24;
 __device__ __forceinline__ int count_bucket(int n)
 {
     const int e = 31 - __clz(n);

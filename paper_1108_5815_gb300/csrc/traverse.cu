@@ -47,14 +47,21 @@ struct TargetInfo {
 
 // Integer centre and half side of cell S (computed once per solve by
 // k_cell_geom); its level follows from the half side h = 2^(kKeyBits - level).
-__device__ __forceinline__ void cell_geom(const CellArrays &c, int S, int C[3], int &h, int &level)
+// The count bucket of the cell (hybrid selection) rides in the top bits.
+__device__ __forceinline__ void cell_geom(const CellArrays &c, int S, int C[3], int &h, int &level, int &bucket)
 {
     const int4 g = __ldg(&c.geom[S]);
     C[0] = g.x;
     C[1] = g.y;
     C[2] = g.z;
-    h = g.w;
-    level = kKeyBits + 1 - __ffs(g.w);
+    h = g.w & kGeomHalfMask;
+    level = kKeyBits + 1 - __ffs(h);
+    bucket = (int)((unsigned)g.w >> kGeomBucketShift);
+}
+__device__ __forceinline__ void cell_geom(const CellArrays &c, int S, int C[3], int &h, int &level)
+{
+    int bucket;
+    cell_geom(c, S, C, h, level, bucket);
 }
 
 // MAC of reading R3: accept iff R > 0 and (r_t + r_s)^2 <= theta^2 R^2 with theta^2 R^2
@@ -124,7 +131,8 @@ struct Counts {
 
 // Resolves one inherited source S0 for target T.  WRITE = false only counts;
 // with WRITE, only the lists whose bit is set in wm are written.
-// sel: hybrid selection table (nullptr = plain FMM).
+// sel: the target's row of the hybrid selection table, indexed by the source's
+// count bucket (nullptr = plain FMM).
 enum : unsigned { kWM2L = 1, kWP2P = 2, kWDef = 4, kWM2P = 8, kWP2L = 16 };
 template <bool WRITE>
 __device__ Counts resolve(const TargetInfo &T, int S0, const CellArrays &c, const ListArrays &L,
@@ -159,10 +167,10 @@ __device__ Counts resolve(const TargetInfo &T, int S0, const CellArrays &c, cons
     while (sp > 0) {
         const int S = stk[--sp];
         const int nchS = c.nchild[S];
-        int Cs[3], hs, ls;
-        cell_geom(c, S, Cs, hs, ls);
+        int Cs[3], hs, ls, bs;
+        cell_geom(c, S, Cs, hs, ls, bs);
         if (mac_accept(T, Cs, hs, theta2, theta2f)) {
-            const int kind = sel ? __ldg(&sel[T.bt * kSelNB + count_bucket(c.end[S] - c.begin[S])]) : 0;
+            const int kind = sel ? sel[bs] : 0;  // the target's row of the table, in shared memory
             if (kind == 3) {  // particle-cell: into T's own local expansion, at any level
                 if (WRITE && (wm & kWP2L)) {
                     L.p2l_src[l_pos + n.l] = S;
@@ -218,8 +226,7 @@ __device__ __forceinline__ TargetInfo load_target(const CellArrays &c, int t)
     TargetInfo T;
     T.t = t;
     T.leaf = c.nchild[t] == 0;
-    cell_geom(c, t, T.C, T.h, T.level);
-    T.bt = count_bucket(c.end[t] - c.begin[t]);
+    cell_geom(c, t, T.C, T.h, T.level, T.bt);
     return T;
 }
 
@@ -259,6 +266,7 @@ __global__ void __launch_bounds__(128, 6)
 {
     __shared__ int sF[4][2][kFrontier];
     __shared__ int sCnt[4][5][kCountCache];  // per-source counts of the count pass (first kCountCache)
+    __shared__ uint8_t sRow[4][kSelNB];      // the target's row of the selection table
     if (sz) {
         a = sz[kSzLevel + level];
         b = sz[kSzLevel + level + 1];
@@ -268,6 +276,12 @@ __global__ void __launch_bounds__(128, 6)
     const int t = a + warp;
     if (t >= b) return;
     const TargetInfo T = load_target(c, t);
+    const uint8_t *row = nullptr;  // the target's row of the selection table
+    if (sel) {
+        for (int k = lane; k < kSelNB; k += 32) sRow[wib][k] = sel[T.bt * kSelNB + k];
+        __syncwarp();
+        row = sRow[wib];
+    }
     const int P = c.parent[t];
     const int i0 = L.def_off[P];
     int ni = L.def_cnt[P];
@@ -331,7 +345,7 @@ __global__ void __launch_bounds__(128, 6)
     }
     int m = 0, p = 0, d = 0, q = 0, l = 0;
     for (int k = lane; k < ni; k += 32) {
-        const Counts n = resolve<false>(T, F[k], c, L, theta2, theta2f, 0, 0, 0, 0, 0, 0u, sel, nullptr, flags);
+        const Counts n = resolve<false>(T, F[k], c, L, theta2, theta2f, 0, 0, 0, 0, 0, 0u, row, nullptr, flags);
         if (k < kCountCache) {
             sCnt[wib][0][k] = n.m;
             sCnt[wib][1][k] = n.p;
@@ -391,12 +405,12 @@ __global__ void __launch_bounds__(128, 6)
         if (S0 >= 0 && k < kCountCache)  // counted by this lane in the count pass
             n = {sCnt[wib][0][k], sCnt[wib][1][k], sCnt[wib][2][k], sCnt[wib][3][k], sCnt[wib][4][k]};
         else if (S0 >= 0)
-            n = resolve<false>(T, S0, c, L, theta2, theta2f, 0, 0, 0, 0, 0, 0u, sel, nullptr, flags);
+            n = resolve<false>(T, S0, c, L, theta2, theta2f, 0, 0, 0, 0, 0, 0u, row, nullptr, flags);
         const int em = warp_excl(n.m), ep = warp_excl(n.p), ed = warp_excl(n.d), eq = warp_excl(n.q),
                   el = warp_excl(n.l);
         if (S0 >= 0)
             resolve<true>(T, S0, c, L, theta2, theta2f, (int64_t)om + rm + em, (int64_t)op + rp + ep,
-                          (int)od + rd + ed, (int64_t)oq + rq + eq, (int64_t)ol + rl + el, wm, sel, hash_keys,
+                          (int)od + rd + ed, (int64_t)oq + rq + eq, (int64_t)ol + rl + el, wm, row, hash_keys,
                           flags);
         rm += warp_sum(n.m);
         rp += warp_sum(n.p);

@@ -491,7 +491,11 @@ __global__ void k_cell_geom(CellArrays c, int ncells, const double *__restrict__
         int C[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) C[a] = (2 * (int)compact3_dev(pre >> a) + 1) * h;
-        c.geom[i] = make_int4(C[0], C[1], C[2], h);
+        // the count bucket of the hybrid selection (cells without a particle range:
+        // bucket 0)
+        const int cnt = c.begin ? c.end[i] - c.begin[i] : 0;
+        const int bucket = cnt >= 1 ? min(count_bucket(cnt), kSelNB - 1) : 0;
+        c.geom[i] = make_int4(C[0], C[1], C[2], h | (bucket << kGeomBucketShift));
         // real centre lo + (2k + 1) side / 2^(l+1) of the cell's own system box, split
         // into FP32 hi + lo; side and 1/side of the cell in FP32
         const double *bx = box + 4 * c.sys[i];

@@ -158,6 +158,9 @@ def _timed(xt, qt, p, theta, ncrit, select, reps=5):
 
 
 def test_learned_selection_gains_where_the_fmm_is_out_of_balance(trained):
+    # the paper's experiment with a too-small N_crit (section "Results", Fig. gpu2):
+    # the plain FMM floods the far field with cell-cell pairs, the hybrid moves the
+    # cheap ones to P2P
     torch = torch_cuda()
     n, p, theta, ncrit = 1 << 20, 8, 0.5, 4
     x, q = inputs.uniform_cube(n, 2024)
@@ -194,4 +197,28 @@ def test_network_picks_ncrit_judged_by_the_measured_tuner(trained):
     assert best_net in cands and all(v > 0 for v in pred.values())
     # far out of balance (tiny leaves, a flood of M2L pairs) is predicted as such
     assert pred[8] > 2 * pred[best_net]
-    assert ms[best_net] <= 1.5 * ms[best_meas], (best_net, best_meas, pred, ms)
+    assert ms[best_net] <= 1.15 * ms[best_meas], (best_net, best_meas, pred, ms)
+
+
+@pytest.mark.parametrize("dist,seed", [("plummer", 2031), ("shell", 2032)])
+def test_learned_with_its_own_ncrit_keeps_pace_with_tuned_plain(trained, dist, seed):
+    # The learned form end to end -- the network's N_crit (nothing timed) and its
+    # selection table -- against the plain FMM at the N_crit the measured tuner
+    # finds best among the same candidates: no slower (5 % timing margin), at the
+    # same accuracy against the FP64 direct sum.
+    torch = torch_cuda()
+    from paper_1108_5815_gb300 import fmm
+    n, p, theta = 1 << 20, 8, 0.5
+    x, q = inputs.make(dist, n, seed)
+    xt, qt = torch.from_numpy(x).cuda(), torch.from_numpy(q).cuda()
+    cands = (16, 32, 64, 128, 256)
+    best_meas, _ = fmm.tune_ncrit(xt, qt, p, theta, cands)
+    best_net, pred = fmm.cost_model_pick_ncrit(xt, qt, p, theta, cands, select="learned")
+    t_plain, (phi0, _) = _timed(xt, qt, p, theta, best_meas, "plain")
+    t_learn, (phi1, _) = _timed(xt, qt, p, theta, best_net, "learned")
+    assert t_learn <= 1.05 * t_plain, (best_net, best_meas, t_learn, t_plain, pred)
+    idx = inputs.sample_indices(n, 256, 6)
+    dphi, _ = O.direct(x, q, targets=idx)
+    e0 = rel_l2(phi0.cpu().numpy()[idx], dphi)
+    e1 = rel_l2(phi1.cpu().numpy()[idx], dphi)
+    assert e1 <= 1.5 * e0 + 1e-6

@@ -95,6 +95,11 @@ typedef struct {
     /* tensor-core M2L schedule: (target tile, offset class) blocks per work unit,
      * 0 = automatic (about six units per SM, at least 8 blocks) */
     int m2l_unit_blocks;
+    /* 0 (default): the far-field chain (offset classes, tiles, M2L, L2L, L2P) runs
+     * on its own stream beside P2P and takes SMs as P2P's blocks retire; 1: it
+     * waits until P2P has finished, so that each phase's time in fmm_stats is
+     * that phase alone (slower; for measurements).  Plans ignore it. */
+    int serialize_phases;
 } fmm_options;
 
 typedef struct {
@@ -108,13 +113,16 @@ typedef struct {
      * P2M and M2M; ms_m2l the M2L kernel and its unit reduction; ms_downward L2L
      * and L2P; ms_p2p the P2P kernel, which runs beside the far-field chain (the
      * offset classes and tiles are built on the far-field stream while P2P runs
-     * and are in no phase); ms_total the whole solve */
+     * and are in no phase; unless fmm_options.serialize_phases is set, P2P and
+     * the far-field phases share the GPU and their times overlap); ms_total the
+     * whole solve */
     float ms_tree, ms_upward, ms_traverse, ms_m2l, ms_downward, ms_p2p, ms_total;
     int64_t n_m2p_pairs; /* (target leaf, source cell) cell-particle pairs */
     int64_t n_p2l_pairs; /* (target cell, source cell) particle-cell pairs */
 } fmm_stats;
 
-/* Fills *opt with the defaults (max_depth 21, FP32 M2L, plain FMM, deterministic). */
+/* Fills *opt with the defaults (max_depth 21, FP32 M2L, plain FMM, deterministic,
+ * phases overlapped). */
 void fmm_default_options(fmm_options *opt);
 
 /* The FMM solve.  Arguments must satisfy N >= 1, 1 <= p <= 20, 0 < theta < 1,

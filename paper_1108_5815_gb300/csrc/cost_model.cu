@@ -98,7 +98,7 @@ std::vector<P2PTiming> pretime_p2p(const std::vector<int> &counts, uint64_t seed
     const int cmax = *std::max_element(counts.begin(), counts.end());
     DevBuf<float4> pts(kMaxTargets + kMaxSources), near(kMaxTargets);
     DevBuf<int> begin(2 * kMaxLeaves), end(2 * kMaxLeaves), off(kMaxLeaves), cnt(kMaxLeaves),
-        src(kMaxLeaves * K), leaves(kMaxLeaves), counter(1);
+        src(kMaxLeaves * K), leaves(kMaxLeaves);
     k_synth_points<<<1024, 256, 0, st>>>(pts.p, kMaxTargets + kMaxSources, seed);
     FMM_LAUNCH_CHECK();
     (void)cmax;
@@ -128,12 +128,10 @@ std::vector<P2PTiming> pretime_p2p(const std::vector<int> &counts, uint64_t seed
             k_synth_lists<<<(unsigned)ceil_div(nmax, 256), 256, 0, st>>>((int)nL, nt, (int)nS, ns, K, begin.p,
                                                                          end.p, off.p, cnt.p, src.p, leaves.p);
             FMM_LAUNCH_CHECK();
-            const unsigned blocks = (unsigned)std::min<int64_t>(ceil_div(nL, 4), (int64_t)nsm * kP2PBlocksPerSM);
             float best = 1e30f;
             for (int rep = 0; rep < 4; ++rep) {
-                FMM_CUDA_TRY(cudaMemsetAsync(counter.p, 0, sizeof(int), st));
                 FMM_CUDA_TRY(cudaEventRecord(e0, st));
-                k_p2p<<<blocks, 128, 0, st>>>(c, L, leaves.p, (int)nL, pts.p, near.p, counter.p);
+                k_p2p<<<(unsigned)std::max<int64_t>(1, nL), 32, 0, st>>>(c, L, leaves.p, (int)nL, pts.p, near.p);
                 FMM_LAUNCH_CHECK();
                 FMM_CUDA_TRY(cudaEventRecord(e1, st));
                 FMM_CUDA_TRY(cudaEventSynchronize(e1));

@@ -662,27 +662,26 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
     float4 *near = need<float4>(ws, "near", N, st);
     FMM_CUDA_TRY(cudaEventRecord(ws.ev_fork, st));
     FMM_CUDA_TRY(cudaStreamWaitEvent(fs, ws.ev_fork, 0));
-    int *p2p_counter = need<int>(ws, "p2p_counter", 1, st);
-    FMM_CUDA_TRY(cudaMemsetAsync(p2p_counter, 0, sizeof(int), st));
     {
-        // kP2PBlocksPerSM (4) blocks of 4 warps per SM: with up to 128 registers a
-        // thread the packed arithmetic keeps more interactions in flight (measured
-        // 1.68 ms at 6 blocks and 80 registers, 1.60 ms at 4 blocks, on the uniform
-        // 1M workload).  This fills the register file, so the far-field chain's
-        // kernels run after P2P.  Starting P2P together with M2L instead (so that the
-        // two share SMs) was measured no faster: both kernels then ran at half speed.
-        int nsm = 152;
-        FMM_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ws.device));
-        const unsigned blocks = (unsigned)std::min<int64_t>(ceil_div(nleaves, 4), (int64_t)nsm * kP2PBlocksPerSM);
+        // One warp (block) per leaf with up to 128 registers a thread, 16 warps per
+        // SM: the packed arithmetic keeps more interactions in flight than with
+        // more warps of fewer registers (measured 1.68 ms at 80 registers and 24
+        // warps, 1.60 ms at 128 and 16, uniform 1M).  That fills the register file;
+        // as blocks retire, the far-field stream (higher priority) gets SMs for
+        // its class and tile kernels, and M2L starts on SMs that P2P has drained.
         // An SM's L1/shared split can only change when the SM is idle; with the
         // maximum shared carveout the far-field kernels (up to ~200 KB of shared
         // memory) can start on SMs that run P2P blocks.
         set_carveout_once((const void *)k_p2p, cudaSharedmemCarveoutMaxShared);
         ev.rec(8, st);
-        k_p2p<<<blocks, 128, 0, st>>>(c, L, leaves, nleaves, pts, near, p2p_counter);
+        k_p2p<<<(unsigned)std::max(1, nleaves), 32, 0, st>>>(c, L, leaves, nleaves, pts, near);
         FMM_LAUNCH_CHECK();
     }
     ev.rec(9, st);
+    if (o.serialize_phases) {  // the far-field chain after P2P (each phase timed alone)
+        FMM_CUDA_TRY(cudaEventRecord(ws.ev_fork, st));
+        FMM_CUDA_TRY(cudaStreamWaitEvent(fs, ws.ev_fork, 0));
+    }
 
     // ---------------------------------------------------------- offset classes
     int nclass = 0;
@@ -954,6 +953,7 @@ double m2l_ns_per_pair(Workspace &ws, int p, double theta, int prec)
     fmm_options o;
     fmm_default_options(&o);
     o.precision_mode = prec;
+    o.serialize_phases = 1;  // the M2L kernel's time alone
     const int64_t off[2] = {0, n};
     double best = 1e30;
     for (int rep = 0; rep < 3; ++rep) {
@@ -987,6 +987,7 @@ double cell_ns_per_cell(Workspace &ws, int p, double theta, int prec)
     fmm_options o;
     fmm_default_options(&o);
     o.precision_mode = prec;
+    o.serialize_phases = 1;  // P2P and M2L each timed alone
     const int64_t off[2] = {0, n};
     double rest[2] = {1e30, 1e30}, cells[2] = {0, 0};
     const int ncs[2] = {16, 64};
@@ -1273,7 +1274,6 @@ void build_plan(fmm_plan &pl, Workspace &ws, const int64_t *offsets, const uint8
     b.totals = m.get<unsigned long long>(5);
     b.far = m.get<float4>(N);
     b.near = m.get<float4>(N);
-    b.p2p_counter = m.get<int>(1);
     b.hflag = m.get<int>(kHashCap);
     b.hex = m.get<int>(kHashCap + 1);
     b.ukeys = m.get<uint64_t>(kHashCap);
@@ -1398,6 +1398,7 @@ void fmm_default_options(fmm_options *opt)
     opt->deterministic = 1;
     opt->select_table = nullptr;
     opt->m2l_unit_blocks = 0;
+    opt->serialize_phases = 0;
 }
 
 fmm_status fmm_laplace3d_ex(const float *xyz, const float *q, int64_t N, int p, double theta,

@@ -230,10 +230,13 @@ size_t m2l_split_bytes(int P2pad, bool bf16, int nslots);
 void launch_split_tables(bool bf16, const float *table, int slot0, int nslots, int P2pad, unsigned char *out,
                          cudaStream_t st);
 
-// p2p.cu -- persistent P2P: kP2PBlocksPerSM blocks of 128 threads per SM
+// p2p.cu -- P2P: one 32-thread block per target leaf (grid >= nleaves), up to
+// kP2PWarpsPerSM resident per SM; the FP32 ceiling probe of the interaction body
+// runs kP2PBlocksPerSM blocks of 128 threads per SM (the same warps per SM)
+constexpr int kP2PWarpsPerSM = 16;
 constexpr int kP2PBlocksPerSM = 4;
 __global__ void k_p2p(CellArrays c, ListArrays L, const int *leaves, int nleaves,
-                      const float4 *pts, float4 *near, int *counter, const int *sz = nullptr);
+                      const float4 *pts, float4 *near, const int *sz = nullptr);
 __global__ void k_direct(const float *xyz, const float *q, int64_t n, float *phi, float *grad);
 // FP32-pipe ceilings: FP32x2 FMA chains (16 lane-FMAs per thread and iteration),
 // and the P2P interaction body on staged sources (32 interactions per thread and rep).

@@ -330,25 +330,21 @@ __device__ __forceinline__ void p2p_leaf(const CellArrays &c, const ListArrays &
     }
 }
 
-// Persistent: a fixed number of blocks per SM, each warp taking the next leaf
-// from a counter, so the kernel leaves room on every SM for the far-field chain
-// that runs beside it and has no tail wave.
-__global__ void __launch_bounds__(128, kP2PBlocksPerSM)
+// One 32-thread block per target leaf (leaves[blockIdx.x]), up to
+// kP2PWarpsPerSM resident per SM with 128 registers a thread.  Blocks retire as
+// their leaves finish, so kernels of the far-field stream, which has the higher
+// priority, take SMs while P2P runs, and the M2L kernel starts on the SMs that
+// P2P has drained.
+__global__ void __launch_bounds__(32, kP2PWarpsPerSM)
     k_p2p(CellArrays c, ListArrays L, const int *__restrict__ leaves, int nleaves,
-          const float4 *__restrict__ pts, float4 *__restrict__ near, int *__restrict__ counter,
-          const int *__restrict__ sz)
+          const float4 *__restrict__ pts, float4 *__restrict__ near, const int *__restrict__ sz)
 {
     if (sz) nleaves = sz[kSzLeaves];
-    __shared__ __align__(16) float sh[4][128];
-    __shared__ float4 red[4][32];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (;;) {
-        int li = 0;
-        if (lane == 0) li = atomicAdd(counter, 1);
-        li = __shfl_sync(0xffffffffu, li, 0);
-        if (li >= nleaves) break;
-        p2p_leaf(c, L, leaves[li], pts, near, sh[warp], red[warp], lane);
-    }
+    __shared__ __align__(16) float sh[128];
+    __shared__ float4 red[32];
+    const int li = blockIdx.x;
+    if (li >= nleaves) return;
+    p2p_leaf(c, L, leaves[li], pts, near, sh, red, threadIdx.x);
 }
 
 // Ceilings of the FP32 pipe on this device, for the P2P roofline.

@@ -128,13 +128,8 @@ void enqueue_plan(const PlanShape &s, const PlanBuffers &b, cudaStream_t st, cud
     // ---------------------------------------------------------- fork: P2P on st
     FMM_CUDA_TRY(cudaEventRecord(fork, st));
     FMM_CUDA_TRY(cudaStreamWaitEvent(fs, fork, 0));
-    FMM_CUDA_TRY(cudaMemsetAsync(b.p2p_counter, 0, sizeof(int), st));
-    {
-        const unsigned blocks =
-            (unsigned)std::min<int64_t>(std::max<int64_t>(1, ceil_div(s.leaf_cap, 4)), (int64_t)s.nsm * kP2PBlocksPerSM);
-        k_p2p<<<blocks, 128, 0, st>>>(c, L, b.leaves, 0, b.pts, b.near, b.p2p_counter, b.sz);
-        FMM_LAUNCH_CHECK();
-    }
+    k_p2p<<<(unsigned)std::max(1, s.leaf_cap), 32, 0, st>>>(c, L, b.leaves, 0, b.pts, b.near, b.sz);
+    FMM_LAUNCH_CHECK();
 
     // ---------------------------------------------------------- offset classes (fs)
     k_hash_flags<<<kHashCap / 256, 256, 0, fs>>>(b.hash_keys, b.hflag);

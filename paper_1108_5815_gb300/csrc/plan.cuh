@@ -54,7 +54,6 @@ struct PlanBuffers {
     unsigned long long *tcount = nullptr, *totals = nullptr;
     const uint8_t *sel = nullptr;
     float4 *far = nullptr, *near = nullptr;
-    int *p2p_counter = nullptr;
     int *hflag = nullptr, *hex = nullptr;
     uint64_t *ukeys = nullptr, *ukeys_alt = nullptr;
     uint32_t *uslot = nullptr;

@@ -431,7 +431,18 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
         int64_t *i64_tmp = need<int64_t>(ws, "scan_i64", scan_temp_elems(std::max(maxcap, 1 << 16)), st);
         k_plan_init<<<1, 64, 0, st>>>(sz, nsys);
         FMM_LAUNCH_CHECK();
-        for (int l = 0; l <= levels; ++l) {
+        // the first levels whose capacities are small: one block splits them all
+        int nsmall = 0;
+        while (nsmall < kMaxSmallLevels && nsmall <= levels && cap[nsmall] <= kSmallLevelCells) ++nsmall;
+        if (nsmall > 0) {
+            SmallLevels sl{};
+            sl.n = nsmall;
+            for (int l = 0; l <= nsmall; ++l) sl.cap[l] = cap[l];
+            k_tree_small_levels<<<1, kSmallLevelThreads, 0, st>>>(c, keys, bpos, bstart, ncrit, max_depth, sl,
+                                                                    levels, cell_cap, INT_MAX, sz);
+            FMM_LAUNCH_CHECK();
+        }
+        for (int l = nsmall; l <= levels; ++l) {
             const int len = cap[l];
             k_split_count<<<(unsigned)ceil_div(len, 128), 128, 0, st>>>(c, bpos, bstart, 0, 0, l, ncrit, max_depth,
                                                                        packed, sz, len);

@@ -104,6 +104,17 @@ __global__ void k_split_emit(CellArrays c, const uint64_t *keys, const uint32_t 
 // plan's capacities (graph replay only).
 __global__ void k_level_advance(const int64_t *total, int level, int last_level, int cell_cap,
                                 int next_level_cap, int tile_cap, int *sz);
+// The first levels of a tree with device-side level ranges, in one block (see tree.cu).
+constexpr int kSmallLevelCells = 4096;
+constexpr int kSmallLevelThreads = 1024;
+constexpr int kMaxSmallLevels = 16;
+struct SmallLevels {
+    int n;                         // levels 0 .. n - 1 are split by the one block
+    int cap[kMaxSmallLevels + 1];  // cell capacity of each level (cap[l + 1]: the children of level l)
+};
+__global__ void k_tree_small_levels(CellArrays c, const uint64_t *keys, const uint32_t *bpos, const int *bstart,
+                                    int ncrit, int max_depth, SmallLevels sl, int last_level, int cell_cap,
+                                    int tile_cap, int *sz);
 __global__ void k_fill_tile_cells(CellArrays c, int ncells, int *tile_cells, const int *sz = nullptr);
 // c.geom of every cell from its level and key prefix (with sz: the cell count from sz).
 __global__ void k_cell_geom(CellArrays c, int ncells, const double *box, const int *sz = nullptr);

@@ -77,7 +77,18 @@ void enqueue_plan(const PlanShape &s, const PlanBuffers &b, cudaStream_t st, cud
     }
     k_level_starts<<<1, 32 * kLevelStartWarps, 0, st>>>(b.blvl, N - 1, b.bstart);
     FMM_LAUNCH_CHECK();
-    for (int l = 0; l <= s.levels; ++l) {
+    // the first levels whose capacities are small: one block splits them all
+    int nsmall = 0;
+    while (nsmall < kMaxSmallLevels && nsmall <= s.levels && s.level_cap[nsmall] <= kSmallLevelCells) ++nsmall;
+    if (nsmall > 0) {
+        SmallLevels sl{};
+        sl.n = nsmall;
+        for (int l = 0; l <= nsmall; ++l) sl.cap[l] = s.level_cap[l];
+        k_tree_small_levels<<<1, kSmallLevelThreads, 0, st>>>(c, b.keys, b.bpos, b.bstart, s.ncrit, s.max_depth, sl,
+                                                                s.levels, s.cell_cap, s.tile_cap, b.sz);
+        FMM_LAUNCH_CHECK();
+    }
+    for (int l = nsmall; l <= s.levels; ++l) {
         const int len = s.level_cap[l];
         k_split_count<<<blocks_for(len, 128), 128, 0, st>>>(c, b.bpos, b.bstart, 0, 0, l, s.ncrit, s.max_depth,
                                                             b.packed, b.sz, len);

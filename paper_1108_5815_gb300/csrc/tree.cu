@@ -481,6 +481,145 @@ __global__ void k_level_advance(const int64_t *__restrict__ total, int level, in
     sz[kSzCells] = b + nch;
 }
 
+// The first levels of a tree built with device-side level ranges (capacities
+// from an earlier solve), in one block: level l = 0 .. sl.n - 1 takes the steps
+// of k_split_count, the exclusive scan, k_level_advance and k_split_emit with
+// __syncthreads between them, so that levels of at most kSmallLevelCells cells
+// cost one launch together instead of four or more each.  A level larger than
+// that, or than its capacity, sets kSzAbort as k_level_advance does (the host
+// then builds the tree level by level).
+__global__ void __launch_bounds__(kSmallLevelThreads)
+    k_tree_small_levels(CellArrays c, const uint64_t *__restrict__ keys, const uint32_t *__restrict__ bpos,
+                        const int *__restrict__ bstart, int ncrit, int max_depth, SmallLevels sl, int last_level,
+                        int cell_cap, int tile_cap, int *__restrict__ sz)
+{
+    __shared__ long long sv[kSmallLevelCells];  // per cell: children | splits << 32, then its exclusive scan
+    __shared__ long long swarp[kSmallLevelThreads / 32];
+    __shared__ long long s_total;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int kPer = kSmallLevelCells / kSmallLevelThreads;
+    for (int level = 0; level < sl.n; ++level) {
+        __syncthreads();
+        if (sz[kSzAbort]) return;
+        const int a = sz[kSzLevel + level], b = sz[kSzLevel + level + 1];
+        const int n = b - a;
+        if (n > kSmallLevelCells) {
+            __syncthreads();
+            if (tid == 0) {
+                sz[kSzAbort] = 1;
+                sz[kSzLevel + level + 2] = b;
+            }
+            return;
+        }
+        // split counts (k_split_count), kPer consecutive cells per thread
+        long long loc[kPer];
+        long long run = 0;
+#pragma unroll
+        for (int u = 0; u < kPer; ++u) {
+            const int k = tid * kPer + u;
+            long long v = 0;
+            if (k < n) {
+                const int i = a + k;
+                const int cb = c.begin[i], ce = c.end[i];
+                if (ce - cb > ncrit && level < max_depth) {
+                    const uint32_t *B = bpos + bstart[level + 1];
+                    const int nb = bstart[level + 2] - bstart[level + 1];
+                    const int lo = lower_pos(B, nb, (uint32_t)cb + 1), hi = lower_pos(B, nb, (uint32_t)ce);
+                    v = (long long)(hi - lo + 1) | ((long long)1 << 32);
+                }
+            }
+            loc[u] = run;  // exclusive within the thread's cells
+            run += v;
+        }
+        // block-wide exclusive scan of the threads' sums
+        long long x = run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) swarp[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            long long w = lane < kSmallLevelThreads / 32 ? swarp[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const long long y = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += y;
+            }
+            if (lane < kSmallLevelThreads / 32) swarp[lane] = w;  // inclusive over warps
+            if (lane == kSmallLevelThreads / 32 - 1) s_total = w;
+        }
+        __syncthreads();
+        const long long base = (warp > 0 ? swarp[warp - 1] : 0) + (x - run);
+#pragma unroll
+        for (int u = 0; u < kPer; ++u) {
+            const int k = tid * kPer + u;
+            if (k < n) sv[k] = base + loc[u];
+        }
+        // level advance (k_level_advance)
+        if (tid == 0) {
+            const long long t = s_total;
+            const int nch = (int)(t & 0xffffffffll), nsplit = (int)(t >> 32);
+            const int tiles = sz[kSzTiles] + 8 * (int)((nsplit + kTile - 1) / kTile);
+            sz[kSzTileBase + level] = sz[kSzTiles];
+            if (nch > 0 &&
+                (level >= last_level || nch > sl.cap[level + 1] || b + nch > cell_cap || tiles > tile_cap)) {
+                sz[kSzAbort] = 1;
+                sz[kSzLevel + level + 2] = b;
+            } else {
+                sz[kSzLevel + level + 2] = b + nch;
+                sz[kSzTiles] = tiles;
+                sz[kSzCells] = b + nch;
+            }
+        }
+        __syncthreads();
+        // children (k_split_emit)
+        const int cend = sz[kSzLevel + level + 2];
+        const int tile_base = sz[kSzTileBase + level];
+        for (int k = tid; k < n; k += kSmallLevelThreads) {
+            const int i = a + k;
+            const long long e = sv[k];
+            const long long next = k + 1 < n ? sv[k + 1] : s_total;
+            const int nch = (int)((next - e) & 0xffffffffll);
+            const int first = b + (int)(e & 0xffffffffll);
+            if (nch == 0 || first + nch > cend) {
+                c.child0[i] = -1;
+                c.nchild[i] = 0;
+                continue;
+            }
+            const int rank = (int)(e >> 32);
+            const int window = rank / kTile, tl = rank % kTile;
+            const int cb = c.begin[i], ce = c.end[i];
+            const int shift = 3 * (kKeyBits - level - 1);
+            const uint64_t pre = c.prefix[i];
+            const int sys = c.sys[i];
+            const uint32_t *B = bpos + bstart[level + 1];
+            const int nb = bstart[level + 2] - bstart[level + 1];
+            const int lo = lower_pos(B, nb, (uint32_t)cb + 1);
+            int beg = cb;
+            for (int q = 0; q < nch; ++q) {
+                const int end = q + 1 < nch ? (int)B[lo + q] : ce;
+                const int o = (int)((keys[beg] >> shift) & 7ull);
+                const int ch = first + q;
+                c.level[ch] = level + 1;
+                c.prefix[ch] = (pre << 3) | (uint64_t)o;
+                c.begin[ch] = beg;
+                c.end[ch] = end;
+                c.parent[ch] = i;
+                c.child0[ch] = -1;
+                c.nchild[ch] = 0;
+                c.tile[ch] = tile_base + window * 8 + o;
+                c.lane[ch] = tl;
+                c.sys[ch] = sys;
+                beg = end;
+            }
+            c.child0[i] = first;
+            c.nchild[i] = nch;
+        }
+    }
+}
+
 __global__ void k_cell_geom(CellArrays c, int ncells, const double *__restrict__ box, const int *__restrict__ sz)
 {
     if (sz) ncells = sz[kSzCells];

@@ -166,3 +166,21 @@ def test_fp32_ceilings_bound_the_p2p_kernel():
     _, _, st = gpu_solve(x, q, 6, 0.5, 64, stats=True)
     rate = st["n_p2p_interactions"] / (st["ms_p2p"] * 1e-3)
     assert rate <= 1.05 * c["body_interactions_per_s"]
+
+
+@pytest.mark.parametrize("dist", ["uniform", "plummer"])
+def test_tree_from_previous_capacities_is_bit_exact(dist):
+    # A second solve with the same N, ncrit and depth limit builds its tree with the
+    # level ranges on the device (the first levels in one block, the rest level by
+    # level): on new points its keys, order, cells and lists must still equal the
+    # oracle's bit for bit, and its fields must match.
+    from tests.test_gpu_parity import _compare_structure
+    n = 50000
+    x0, q0 = inputs.make(dist, n, 301)
+    gpu_solve(x0, q0, 5, 0.5, 24)
+    x, q = inputs.make(dist, n, 302)
+    phi, grad = gpu_solve(x, q, 5, 0.5, 24)
+    f = O.Fmm(x, q, 5, 0.5, 24)
+    _compare_structure(f)
+    ophi, ograd = f.evaluate()
+    assert rel_l2(phi, ophi) < 1e-5 and rel_l2(grad, ograd) < 1e-5

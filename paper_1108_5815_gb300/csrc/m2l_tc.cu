@@ -25,7 +25,12 @@
 // the shared-memory layout of a stage, so a stage's B is two bulk asynchronous
 // copies (cp.async.bulk, completing on an mbarrier) issued by one thread.
 //
-// Roles inside a CTA (704 threads):
+// Two kernels share this scheme.  For P2pad <= 128, k_m2l_tc_ta keeps A in
+// tensor memory (described at its definition).  For larger P2pad the
+// accumulators leave no tensor-memory columns for A, and k_m2l_tc stages A in
+// shared memory:
+//
+// Roles inside a k_m2l_tc CTA (704 threads):
 //   warps 0-15  producers, two groups of 8 warps that fill alternate stages:
 //               gather the 128 source rows (A) of one K-chunk of 32 floats,
 //               split them into hi/lo and store them in the canonical
@@ -616,6 +621,350 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
+// ---------------------------------------------------------------------------
+// A operand in tensor memory (N = P2pad <= 128).
+//
+// The same products, accumulators and order of additions as k_m2l_tc, with the
+// gathered source rows held in tensor memory instead of shared memory: the
+// producers split each row into hi/lo in registers and write both with
+// tcgen05.st, and the MMAs take A from tensor memory (tcgen05.mma's [a-tmem]
+// form).  Shared memory then carries only the class matrices: their bulk copies
+// and the MMAs' reads of B.  Per stage of 32 K values (TF32, N = 128) that is
+// 32 KB written and 48 KB read, against 32 + 32 KB written and 80 KB read with A
+// in shared memory, where shared memory, not the tensor pipe, set the pace.
+//
+// Tensor-memory columns: [main 0 | correction | main 1] at 0, N, 2N (as in
+// k_m2l_tc with the running correction), and a ring of A stages at 384..511:
+// TF32 stages of 64 columns (hi 32 K values, lo 32), BF16 stages of 32 (two
+// values per 32-bit column).  Row r of A is tensor-memory lane r.
+//
+// Roles (576 threads):
+//   warps 0-7   producers, two per 32-lane quarter (warp & 3): thread (warp,
+//               lane) owns A row 32 (warp & 3) + lane and half (warp >> 2) of
+//               each stage's 32 K values; loads run two stages ahead.
+//   warp 8      allocates tensor memory; one lane issues the MMAs and commits.
+//   warps 9-16  accumulators, two per lane quarter, each owning half of the N
+//               columns of its 32 rows: the running sum of the class blocks'
+//               main products is kept in registers (FP32 round-to-nearest adds,
+//               the same order as k_m2l_tc), the correction added after the last
+//               block.
+//   warp 17     one lane issues every stage's B copies, in stage order.
+namespace ta {
+constexpr int kProducers = 8;
+constexpr int kMmaWarp = 8;
+constexpr int kAcc0 = 9, kAccWarps = 8;
+constexpr int kBWarp = kAcc0 + kAccWarps;
+constexpr int kThreads = (kBWarp + 1) * 32;
+constexpr uint32_t kACol = 384;  // first tensor-memory column of the A ring
+constexpr int kTmemCols = 512;
+}  // namespace ta
+
+// Tensor-memory store of 8 consecutive 32-bit columns of this warp's 32 lanes.
+__device__ __forceinline__ void tmem_st8u(uint32_t taddr, const uint32_t (&v)[8])
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(v[0]),
+                 "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// D (tensor memory) (+)= A (tensor memory, lane = row) * B (shared memory)^T.
+template <bool BF16>
+__device__ __forceinline__ void mma_ta(uint32_t tmem_d, uint32_t tmem_a, uint64_t b, uint32_t idesc,
+                                       uint32_t accumulate)
+{
+    if (BF16) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(tmem_d),
+            "r"(tmem_a), "l"(b), "r"(idesc), "r"(accumulate));
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(tmem_d),
+            "r"(tmem_a), "l"(b), "r"(idesc), "r"(accumulate));
+    }
+}
+
+template <bool BF16, int N>
+__global__ void __launch_bounds__(ta::kThreads, 1)
+    k_m2l_tc_ta(const Unit *__restrict__ units, const int *__restrict__ entry_class,
+                const int *__restrict__ src, const float *__restrict__ M,
+                const unsigned char *__restrict__ tsplit, int nbstages,
+                float *__restrict__ partial, int *__restrict__ flags, const int *__restrict__ sz)
+{
+    static_assert(N % 32 == 0 && N <= 128, "N = P2pad <= 128, a multiple of 32");
+    if (sz && (int)blockIdx.x >= sz[kSzUnits]) return;
+    constexpr int P2pad = N;
+    constexpr int ACOLS = BF16 ? 32 : 64;      // tensor-memory columns per A stage (hi + lo)
+    constexpr int NAST = 128 / ACOLS;          // A stages in the ring
+    constexpr int KSTEPS = ACOLS / 16;         // MMAs (8 columns of A each) per stage
+    constexpr uint32_t RB = BF16 ? 64u : 128u;  // bytes per B row per stage
+    constexpr uint32_t SBO = 8u * RB;
+    constexpr uint32_t b_bytes = (uint32_t)N * RB;
+    constexpr int nkc = P2pad / kKChunk;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *smem = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
+    uint64_t *bfull = reinterpret_cast<uint64_t *>(smem + (size_t)nbstages * 2 * b_bytes);
+    uint64_t *bempty = bfull + nbstages;
+    uint64_t *afull = bempty + nbstages;
+    uint64_t *aempty = afull + NAST;
+    uint64_t *acc_full = aempty + NAST;
+    uint64_t *acc_empty = acc_full + 2;
+    uint64_t *fin = acc_empty + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(fin + 1);
+    __shared__ int s_abort;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const Unit U = units[blockIdx.x];
+    const int nblocks = U.e1 - U.e0;
+    const int nsteps = nblocks * nkc;
+
+    if (threadIdx.x == 0) {
+        s_abort = 0;
+        for (int s = 0; s < nbstages; ++s) {
+            mbar_init(&bfull[s], 1);
+            mbar_init(&bempty[s], 1);
+        }
+        for (int s = 0; s < NAST; ++s) {
+            mbar_init(&afull[s], ta::kProducers);  // one arrival per producer warp
+            mbar_init(&aempty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], ta::kAccWarps);
+        }
+        mbar_init(fin, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == ta::kMmaWarp) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "r"((uint32_t)ta::kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp < ta::kProducers) {
+        // ------------------------------------------------------------ producers
+        const int quad = warp & 3, half = warp >> 2;
+        const int row = quad * 32 + lane;
+        const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
+        // the row's source index of the next block is read one block ahead, so a
+        // block's first rows wait for one load, not two in a chain
+        int cur_e = -1, srow = 0, next_src = nblocks > 0 ? src[(int64_t)U.e0 * kTile + row] : -1;
+        bool svalid = false;
+        auto load = [&](int g, float4 (&buf)[4]) {
+            const int e = U.e0 + g / nkc;
+            if (e != cur_e) {  // a block's first stage: the row's source
+                cur_e = e;
+                svalid = next_src >= 0;
+                srow = svalid ? next_src : 0;
+                if (e + 1 < U.e1) next_src = src[(int64_t)(e + 1) * kTile + row];
+            }
+            const float4 *p = reinterpret_cast<const float4 *>(M + (int64_t)srow * P2pad + (g % nkc) * kKChunk +
+                                                               half * 16);
+#pragma unroll
+            for (int v = 0; v < 4; ++v) buf[v] = svalid ? p[v] : make_float4(0.f, 0.f, 0.f, 0.f);
+        };
+        auto fill = [&](int g, const float4 (&buf)[4]) -> bool {
+            const int s = g % NAST;
+            const bool freed = g < NAST || mbar_wait(&aempty[s], (uint32_t)((g / NAST) - 1) & 1u);
+            if (!__all_sync(0xffffffffu, freed)) {
+                if (lane == 0) atomicOr(&flags[kFlagTimeout], 1);
+                s_abort = 1;
+                return false;
+            }
+            if (__any_sync(0xffffffffu, s_abort != 0)) return false;
+            tc_fence_after();
+            const uint32_t col = tmem + lane_off + ta::kACol + (uint32_t)(s * ACOLS);
+            if (BF16) {
+                uint32_t hi[8], lo[8];
+#pragma unroll
+                for (int v = 0; v < 4; v += 2) {
+                    uint4 h, l;
+                    split_bf16(buf[v], buf[v + 1], h, l);
+                    hi[2 * v] = h.x, hi[2 * v + 1] = h.y, hi[2 * v + 2] = h.z, hi[2 * v + 3] = h.w;
+                    lo[2 * v] = l.x, lo[2 * v + 1] = l.y, lo[2 * v + 2] = l.z, lo[2 * v + 3] = l.w;
+                }
+                tmem_st8u(col + (uint32_t)(half * 8), hi);
+                tmem_st8u(col + (uint32_t)(ACOLS / 2 + half * 8), lo);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {  // 8 K values at a time
+                    uint32_t hi[8], lo[8];
+#pragma unroll
+                    for (int v = 0; v < 2; ++v) {
+                        uint4 h, l;
+                        split_tf32(buf[2 * q + v], h, l);
+                        hi[4 * v] = h.x, hi[4 * v + 1] = h.y, hi[4 * v + 2] = h.z, hi[4 * v + 3] = h.w;
+                        lo[4 * v] = l.x, lo[4 * v + 1] = l.y, lo[4 * v + 2] = l.z, lo[4 * v + 3] = l.w;
+                    }
+                    tmem_st8u(col + (uint32_t)(half * 16 + q * 8), hi);
+                    tmem_st8u(col + (uint32_t)(ACOLS / 2 + half * 16 + q * 8), lo);
+                }
+            }
+            tmem_st_wait();
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&afull[s]);
+            return true;
+        };
+        // loads run two stages ahead of the stage being written (three buffers in turn)
+        float4 r0[4], r1[4], r2[4];
+        if (0 < nsteps) load(0, r0);
+        if (1 < nsteps) load(1, r1);
+        for (int g = 0; g < nsteps; g += 3) {
+            if (g + 2 < nsteps) load(g + 2, r2);
+            if (!fill(g, r0) || g + 1 >= nsteps) break;
+            if (g + 3 < nsteps) load(g + 3, r0);
+            if (!fill(g + 1, r1) || g + 2 >= nsteps) break;
+            if (g + 4 < nsteps) load(g + 4, r1);
+            if (!fill(g + 2, r2)) break;
+        }
+    } else if (warp == ta::kMmaWarp) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc = instr_desc(BF16 ? 1u : 2u, (uint32_t)N);
+            const uint32_t idesc2 = instr_desc(BF16 ? 1u : 2u, 2u * N);
+            bool ok = true;
+            int g = 0;
+            for (int b = 0; b < nblocks && ok; ++b) {
+                const int buf = b & 1;
+                if (b >= 2 && !mbar_wait(&acc_empty[buf], (uint32_t)((b >> 1) - 1) & 1u)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t dmain = tmem + (uint32_t)(buf ? 2 * N : 0), dcorr = tmem + (uint32_t)N;
+                const bool odd = b & 1;
+                for (int kc = 0; kc < nkc; ++kc, ++g) {
+                    const int sa = g % NAST, sb = g % nbstages;
+                    if (!mbar_wait(&afull[sa], (uint32_t)(g / NAST) & 1u) ||
+                        !mbar_wait(&bfull[sb], (uint32_t)(g / nbstages) & 1u)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t ah = tmem + ta::kACol + (uint32_t)(sa * ACOLS), al = ah + (uint32_t)(ACOLS / 2);
+                    const uint32_t b0 = smem_u32(smem + (size_t)sb * 2 * b_bytes);
+                    const uint32_t bh = odd ? b0 + b_bytes : b0, bl = odd ? b0 : b0 + b_bytes;
+#pragma unroll
+                    for (int k = 0; k < KSTEPS; ++k) {
+                        const uint32_t ka = (uint32_t)k * 8u;    // 8 columns of A
+                        const uint32_t kb = (uint32_t)k * 256u;  // two core matrices of B along K
+                        const uint32_t acc0 = (kc > 0 || k > 0) ? 1u : 0u;
+                        if (acc0 == 0 && b > 0) {
+                            // a block's first step: main restarts, the correction goes on
+                            mma_ta<BF16>(dmain, ah + ka, smem_desc(bh + kb, SBO), idesc, 0u);
+                            mma_ta<BF16>(dcorr, ah + ka, smem_desc(bl + kb, SBO), idesc, 1u);
+                        } else {
+                            // [main 0 | corr] (even) or [corr | main 1] (odd) = ah.(B as staged)
+                            mma_ta<BF16>(odd ? dcorr : dmain, ah + ka, smem_desc(b0 + kb, SBO), idesc2, acc0);
+                        }
+                        mma_ta<BF16>(dcorr, al + ka, smem_desc(bh + kb, SBO), idesc, 1u);
+                    }
+                    mma_commit(&aempty[sa]);
+                    mma_commit(&bempty[sb]);
+                }
+                if (ok) mma_commit(&acc_full[buf]);
+            }
+            if (!ok) {
+                atomicOr(&flags[kFlagTimeout], 1);
+                s_abort = 1;
+            }
+            mma_commit(fin);
+            if (!mbar_wait(fin, 0)) atomicOr(&flags[kFlagTimeout], 1);
+        }
+    } else if (warp == ta::kBWarp) {
+        // ------------------------------------------------------------ B copies
+        if (lane == 0) {
+            int issued = 0;
+            for (int g = 0; g < nsteps; ++g) {
+                const int s = g % nbstages;
+                if (g >= nbstages && !mbar_wait(&bempty[s], (uint32_t)((g / nbstages) - 1) & 1u)) {
+                    atomicOr(&flags[kFlagTimeout], 1);
+                    s_abort = 1;
+                    break;
+                }
+                if (s_abort) break;
+                unsigned char *st = smem + (size_t)s * 2 * b_bytes;
+                const int e = U.e0 + g / nkc, kc = g % nkc;
+                const unsigned char *bsrc = tsplit + ((int64_t)entry_class[e] * nkc + kc) * 2 * (int64_t)b_bytes;
+                const bool lo_first = (g / nkc) & 1;  // odd blocks: [B_lo | B_hi]
+                mbar_arrive_expect_tx(&bfull[s], 2 * b_bytes);
+                bulk_g2s(st + (lo_first ? b_bytes : 0), bsrc, b_bytes, &bfull[s]);
+                bulk_g2s(st + (lo_first ? 0 : b_bytes), bsrc + b_bytes, b_bytes, &bfull[s]);
+                issued = g + 1;
+            }
+            for (int g = issued - 1; g >= 0 && g >= issued - nbstages; --g)
+                if (!mbar_wait(&bfull[g % nbstages], (uint32_t)(g / nbstages) & 1u))
+                    atomicOr(&flags[kFlagTimeout], 1);
+        }
+    } else {
+        // ------------------------------------------------------------ accumulators
+        // sum_b = sum_{b-1} + main_b (FP32 round-to-nearest, per element); after
+        // the last block, + correction.
+        constexpr int NH = N / 2;
+        const int quad = warp & 3, half = (warp - ta::kAcc0) >> 2;
+        const int row = quad * 32 + lane;
+        const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
+        const uint32_t c0 = (uint32_t)(half * NH);
+        float sum[NH];
+        bool done = true;
+        for (int b = 0; b < nblocks; ++b) {
+            const int buf = b & 1;
+            if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[buf], (uint32_t)(b >> 1) & 1u))) {
+                atomicOr(&flags[kFlagTimeout], 1);
+                done = false;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t dmain = tmem + lane_off + (uint32_t)(buf ? 2 * N : 0) + c0;
+#pragma unroll
+            for (int c = 0; c < NH; c += 16) {
+                uint32_t r[16];
+                tmem_ld16_issue(dmain + (uint32_t)c, r);
+                tmem_ld_wait();
+                reg_touch16(r);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) sum[c + i] = b > 0 ? sum[c + i] + __uint_as_float(r[i]) : __uint_as_float(r[i]);
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[buf]);
+        }
+        if (done && nblocks > 0) {
+            float *out = partial + ((int64_t)blockIdx.x * 128 + row) * P2pad + c0;
+#pragma unroll
+            for (int c = 0; c < NH; c += 16) {
+                uint32_t r[16];
+                tmem_ld16_issue(tmem + lane_off + (uint32_t)N + c0 + (uint32_t)c, r);
+                tmem_ld_wait();
+                reg_touch16(r);
+#pragma unroll
+                for (int i = 0; i < 16; i += 4)
+                    *reinterpret_cast<float4 *>(out + c + i) =
+                        make_float4(sum[c + i] + __uint_as_float(r[i]), sum[c + i + 1] + __uint_as_float(r[i + 1]),
+                                    sum[c + i + 2] + __uint_as_float(r[i + 2]),
+                                    sum[c + i + 3] + __uint_as_float(r[i + 3]));
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == ta::kMmaWarp) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)ta::kTmemCols)
+                     : "memory");
+    }
+}
+
 // L rows of a tile = sum of its units' partials, in the order tile_units lists
 // them (the tile's class order).
 __global__ void k_m2l_reduce(const int *__restrict__ unit_base, const int *__restrict__ tile_units,
@@ -740,11 +1089,47 @@ size_t m2l_tc_smem(int P2pad, bool bf16, int &nstages)
     return nstages * stage + 1024 /*alignment*/ + (3 * nstages + 5) * 8 + 16;
 }
 
+// Shared memory of k_m2l_tc_ta: a ring of B stages (hi and lo of N rows of 32 K
+// values), its barriers and the 1024-byte alignment slack.
+static size_t m2l_tc_ta_smem(int P2pad, bool bf16, int &nbstages)
+{
+    const size_t stage = 2 * (size_t)P2pad * (bf16 ? 64 : 128);
+    nbstages = (int)std::min<size_t>(8, (192 * 1024) / stage);
+    return nbstages * stage + 1024 + (2 * nbstages + 2 * 4 + 5) * 8 + 16;
+}
+
 void launch_m2l_tc(bool bf16, int nunits, const void *units, int ntiles, const int *unit_base,
                    const int *tile_units, const int *entry_class, const int *src, const int *tile_cells,
                    const float *M, const unsigned char *tsplit, int P2pad, float *partial, float *L,
                    int *flags, cudaStream_t st, const int *sz)
 {
+    if (nunits > 0 && P2pad <= 128) {
+        int nb = 0;
+        const size_t smem = m2l_tc_ta_smem(P2pad, bf16, nb);
+#define FMM_M2L_TA_LAUNCH(B, NN)                                                                     \
+    do {                                                                                            \
+        set_smem_limit_once((const void *)k_m2l_tc_ta<B, NN>, (int)smem);                           \
+        k_m2l_tc_ta<B, NN><<<nunits, ta::kThreads, smem, st>>>(static_cast<const Unit *>(units), entry_class, \
+                                                               src, M, tsplit, nb, partial, flags, sz); \
+    } while (0)
+#define FMM_M2L_TA_BY_N(B)                              \
+    do {                                                \
+        switch (P2pad) {                                \
+            case 32: FMM_M2L_TA_LAUNCH(B, 32); break;   \
+            case 64: FMM_M2L_TA_LAUNCH(B, 64); break;   \
+            case 96: FMM_M2L_TA_LAUNCH(B, 96); break;   \
+            default: FMM_M2L_TA_LAUNCH(B, 128); break;  \
+        }                                               \
+    } while (0)
+        if (bf16)
+            FMM_M2L_TA_BY_N(true);
+        else
+            FMM_M2L_TA_BY_N(false);
+#undef FMM_M2L_TA_BY_N
+#undef FMM_M2L_TA_LAUNCH
+        FMM_LAUNCH_CHECK();
+        nunits = 0;  // done: only the reduction below remains
+    }
     int nstages = 0;
     const size_t smem = m2l_tc_smem(P2pad, bf16, nstages);
     if (nunits > 0) {

@@ -35,7 +35,7 @@ constexpr int kStack = 192;
 constexpr int kP2PFlag = 1 << 30;  // deferred source that is a chosen P2P pair
 constexpr int kM2PFlag = 1 << 29;  // deferred source that is a chosen M2P pair
 constexpr int kCellMask = kM2PFlag - 1;
-constexpr int kFrontier = 256;  // sources of a leaf target split warp-wide before the walks
+constexpr int kFrontier = 512;  // sources of a leaf target split warp-wide before the walks
 constexpr int kCountCache = 128;  // sources whose counts the write pass reuses
 
 struct TargetInfo {
@@ -249,6 +249,106 @@ __device__ __forceinline__ int warp_excl(int v)
     return x - v;
 }
 
+// Target T with ni <= kFrontier sources F (shared memory), no selection table:
+// if every source resolves to a single pair -- accepted (M2L), or else P2P (T a
+// leaf, S a leaf) or deferred (T not a leaf, S no larger than T or a leaf) --
+// writes T's lists and list offsets exactly as resolve() would (same pairs, same
+// order) and returns true; otherwise writes nothing and returns false.
+__device__ bool lists_by_ballot(const TargetInfo &T, const int *F, int ni, const CellArrays &c,
+                                const ListArrays &L, double theta2, float theta2f,
+                                unsigned long long *__restrict__ counters, int64_t cap_m, int64_t cap_p,
+                                int64_t cap_d, uint64_t *hash_keys, int *flags)
+{
+    constexpr int R = kFrontier / 32;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    unsigned ma[R], mo[R];  // per round of 32 sources: M2L pairs, the other pairs (P2P or deferred)
+    bool single = true;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        ma[r] = mo[r] = 0u;
+        if (r * 32 < ni) {
+            const int k = r * 32 + lane;
+            const bool valid = k < ni;
+            bool acc = false, one = true;
+            if (valid) {
+                const int S = F[k];
+                if (S & (kP2PFlag | kM2PFlag)) {
+                    one = false;
+                } else {
+                    int Cs[3], hs, ls;
+                    cell_geom(c, S, Cs, hs, ls);
+                    acc = mac_accept(T, Cs, hs, theta2, theta2f);
+                    const int nch = c.nchild[S];
+                    one = acc || (T.leaf ? nch == 0 : !(ls < T.level && nch > 0));
+                }
+            }
+            ma[r] = __ballot_sync(0xffffffffu, valid && acc);
+            mo[r] = __ballot_sync(0xffffffffu, valid && !acc && one);
+            single = __all_sync(0xffffffffu, one) && single;
+        }
+    }
+    if (!single) return false;
+    int m = 0, o = 0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        m += __popc(ma[r]);
+        o += __popc(mo[r]);
+    }
+    const int p = T.leaf ? o : 0, d = T.leaf ? 0 : o;
+    unsigned long long om = 0, op = 0, od = 0;
+    if (lane == 0) {
+        om = atomicAdd(&counters[0], (unsigned long long)m);
+        op = atomicAdd(&counters[1], (unsigned long long)p);
+        od = atomicAdd(&counters[2], (unsigned long long)d);
+    }
+    om = __shfl_sync(0xffffffffu, om, 0);
+    op = __shfl_sync(0xffffffffu, op, 0);
+    od = __shfl_sync(0xffffffffu, od, 0);
+    const bool fm = (int64_t)(om + m) <= cap_m, fp = (int64_t)(op + p) <= cap_p, fd = (int64_t)(od + d) <= cap_d;
+    const int t = T.t;
+    if (lane == 0) {
+        L.m2l_off[t] = (int)om;
+        L.m2l_cnt[t] = fm ? m : 0;
+        L.p2p_off[t] = (int)op;
+        L.p2p_cnt[t] = fp ? p : 0;
+        L.def_off[t] = (int)od;
+        L.def_cnt[t] = fd ? d : 0;
+        L.m2p_off[t] = 0;
+        L.m2p_cnt[t] = 0;
+        L.p2l_off[t] = 0;
+        L.p2l_cnt[t] = 0;
+    }
+    const bool fo = T.leaf ? fp : fd;
+    int64_t rm = (int64_t)om, ro = T.leaf ? (int64_t)op : (int64_t)od;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        if (r * 32 < ni) {
+            const int k = r * 32 + lane;
+            if (fm && ((ma[r] >> lane) & 1u)) {
+                const int S = F[k];
+                int Cs[3], hs, ls;
+                cell_geom(c, S, Cs, hs, ls);
+                const int64_t pos = rm + __popc(ma[r] & lt);
+                L.m2l_src[pos] = S;
+                L.m2l_tgt[pos] = t;
+                L.m2l_slot[pos] = hash_insert(hash_keys, class_key(T, ls, Cs, flags), flags);
+            } else if (fo && ((mo[r] >> lane) & 1u)) {
+                const int64_t pos = ro + __popc(mo[r] & lt);
+                if (T.leaf) {
+                    L.p2p_src[pos] = F[k];
+                    L.p2p_tgt[pos] = t;
+                } else {
+                    L.def_src[pos] = F[k];
+                }
+            }
+            rm += __popc(ma[r]);
+            ro += __popc(mo[r]);
+        }
+    }
+    return true;
+}
+
 }  // namespace
 
 // One warp per target of the level [a, b): count the outputs of all inherited
@@ -286,13 +386,14 @@ __global__ void __launch_bounds__(128, 6)
     const int i0 = L.def_off[P];
     int ni = L.def_cnt[P];
     const int *F = L.def_src + i0;
-    if (T.leaf && ni <= kFrontier) {
-        // A leaf target resolves every inherited source it does not accept by a
+    if (ni <= kFrontier) {
+        // A target resolves every inherited source it does not accept by a
         // depth-first walk of the source's subtree, one source per lane; next to a
         // dense region a few sources carry almost all the work.  Split the sources
-        // the walks would split first (not accepted, not leaves) in warp-wide rounds
-        // while the list fits in kFrontier entries; the walks then start from the
-        // pieces.  The set of pairs does not change, only the order of discovery.
+        // the walks would split first (not accepted, not leaves, and for a target
+        // that is not a leaf, larger than it) in warp-wide rounds while the list
+        // fits in kFrontier entries; the walks then start from the pieces.  The set
+        // of pairs does not change, only the order of discovery.
         int cur = 0;
         for (int k = lane; k < ni; k += 32) sF[wib][0][k] = F[k];
         __syncwarp();
@@ -301,7 +402,7 @@ __global__ void __launch_bounds__(128, 6)
             if ((S & (kP2PFlag | kM2PFlag)) || c.nchild[S] == 0) return false;
             int Cs[3], hs, ls;
             cell_geom(c, S, Cs, hs, ls);
-            if (mac_accept(T, Cs, hs, theta2, theta2f)) return false;
+            if ((!T.leaf && ls >= T.level) || mac_accept(T, Cs, hs, theta2, theta2f)) return false;
             nc = c.nchild[S];
             return true;
         };
@@ -342,6 +443,12 @@ __global__ void __launch_bounds__(128, 6)
         }
         __syncwarp();
         F = sF[wib][cur];
+        // Without a selection table, a target whose split sources each resolve to
+        // one pair needs no walk: one acceptance test per source decides its pair,
+        // the lanes' pairs are placed by ballot, and the lists come out in the order
+        // the walks give.
+        if (!sel && lists_by_ballot(T, F, ni, c, L, theta2, theta2f, counters, cap_m, cap_p, cap_d, hash_keys, flags))
+            return;
     }
     int m = 0, p = 0, d = 0, q = 0, l = 0;
     for (int k = lane; k < ni; k += 32) {

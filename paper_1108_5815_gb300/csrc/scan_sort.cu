@@ -177,6 +177,7 @@ constexpr int kRadix = 256;
 constexpr uint64_t kLbAggregate = 1ull << 62;  // look-back word: tile count only
 constexpr uint64_t kLbInclusive = 2ull << 62;  // look-back word: prefix through this tile
 constexpr uint32_t kLookbackPolls = 1u << 20;
+constexpr int kLookbackWindow = 8;  // earlier tiles whose look-back words are read together
 
 // Digit counts of passes 0 .. passes-1 over all keys (counts[pass][digit], zeroed).
 __global__ void __launch_bounds__(256)
@@ -284,21 +285,33 @@ __global__ void __launch_bounds__(kSortThreads, 2)
             *mine = kLbInclusive | cnt;
         } else {
             *mine = kLbAggregate | cnt;
-            for (int t = tile - 1; t >= 0; --t) {
-                volatile unsigned long long *pv = status + (int64_t)t * kRadix + tid;
-                unsigned long long v = *pv;
-                uint32_t polls = 0;
-                while ((v >> 62) == 0 && polls < kLookbackPolls) {
-                    __nanosleep(32);
-                    v = *pv;
-                    ++polls;
+            // The words of the next kLookbackWindow earlier tiles are read together
+            // (independent loads), then taken in order: the walk costs one memory
+            // latency per window, not per tile.
+            bool done = false;
+            for (int t0 = tile - 1; t0 >= 0 && !done; t0 -= kLookbackWindow) {
+                unsigned long long v[kLookbackWindow];
+#pragma unroll
+                for (int j = 0; j < kLookbackWindow; ++j)
+                    v[j] = t0 - j >= 0 ? *(volatile unsigned long long *)(status + (int64_t)(t0 - j) * kRadix + tid) : 0ull;
+#pragma unroll
+                for (int j = 0; j < kLookbackWindow; ++j) {
+                    if (done || t0 - j < 0) break;
+                    volatile unsigned long long *pv = status + (int64_t)(t0 - j) * kRadix + tid;
+                    uint32_t polls = 0;
+                    while ((v[j] >> 62) == 0 && polls < kLookbackPolls) {
+                        __nanosleep(32);
+                        v[j] = *pv;
+                        ++polls;
+                    }
+                    if ((v[j] >> 62) == 0) {  // gave up: the result of this sort is invalid
+                        if (flags) atomicOr(&flags[kFlagTimeout], 1);
+                        done = true;
+                        break;
+                    }
+                    excl += (uint32_t)(v[j] & 0xffffffffull);
+                    if ((v[j] >> 62) == 2) done = true;
                 }
-                if ((v >> 62) == 0) {  // gave up: the result of this sort is invalid
-                    if (flags) atomicOr(&flags[kFlagTimeout], 1);
-                    break;
-                }
-                excl += (uint32_t)(v & 0xffffffffull);
-                if ((v >> 62) == 2) break;
             }
             *mine = kLbInclusive | (excl + cnt);
         }

@@ -249,46 +249,18 @@ __device__ __forceinline__ int warp_excl(int v)
     return x - v;
 }
 
-// Target T with ni <= kFrontier sources F (shared memory), no selection table:
-// if every source resolves to a single pair -- accepted (M2L), or else P2P (T a
-// leaf, S a leaf) or deferred (T not a leaf, S no larger than T or a leaf) --
-// writes T's lists and list offsets exactly as resolve() would (same pairs, same
-// order) and returns true; otherwise writes nothing and returns false.
-__device__ bool lists_by_ballot(const TargetInfo &T, const int *F, int ni, const CellArrays &c,
-                                const ListArrays &L, double theta2, float theta2f,
-                                unsigned long long *__restrict__ counters, int64_t cap_m, int64_t cap_p,
-                                int64_t cap_d, uint64_t *hash_keys, int *flags)
+// Writes the lists of target T whose ni sources F each resolve to one pair:
+// ma[r] / mo[r] mark, per round r of 32 sources, the accepted ones (M2L) and the
+// others (P2P for a leaf T, deferred otherwise).  The pairs, their order and the
+// list offsets are those resolve() would give.
+template <int R>
+__device__ __forceinline__ void write_single_pairs(const TargetInfo &T, const int *F, int ni, const unsigned (&ma)[R],
+                                                   const unsigned (&mo)[R], const CellArrays &c, const ListArrays &L,
+                                                   unsigned long long *__restrict__ counters, int64_t cap_m,
+                                                   int64_t cap_p, int64_t cap_d, uint64_t *hash_keys, int *flags)
 {
-    constexpr int R = kFrontier / 32;
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
-    unsigned ma[R], mo[R];  // per round of 32 sources: M2L pairs, the other pairs (P2P or deferred)
-    bool single = true;
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        ma[r] = mo[r] = 0u;
-        if (r * 32 < ni) {
-            const int k = r * 32 + lane;
-            const bool valid = k < ni;
-            bool acc = false, one = true;
-            if (valid) {
-                const int S = F[k];
-                if (S & (kP2PFlag | kM2PFlag)) {
-                    one = false;
-                } else {
-                    int Cs[3], hs, ls;
-                    cell_geom(c, S, Cs, hs, ls);
-                    acc = mac_accept(T, Cs, hs, theta2, theta2f);
-                    const int nch = c.nchild[S];
-                    one = acc || (T.leaf ? nch == 0 : !(ls < T.level && nch > 0));
-                }
-            }
-            ma[r] = __ballot_sync(0xffffffffu, valid && acc);
-            mo[r] = __ballot_sync(0xffffffffu, valid && !acc && one);
-            single = __all_sync(0xffffffffu, one) && single;
-        }
-    }
-    if (!single) return false;
     int m = 0, o = 0;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -346,7 +318,6 @@ __device__ bool lists_by_ballot(const TargetInfo &T, const int *F, int ni, const
             ro += __popc(mo[r]);
         }
     }
-    return true;
 }
 
 }  // namespace
@@ -365,6 +336,7 @@ __global__ void __launch_bounds__(128, 6)
                      int level)
 {
     __shared__ int sF[4][2][kFrontier];
+    __shared__ int sN[4][kFrontier];  // per source of the frontier: its children when split, else -1
     __shared__ int sCnt[4][5][kCountCache];  // per-source counts of the count pass (first kCountCache)
     __shared__ uint8_t sRow[4][kSelNB];      // the target's row of the selection table
     if (sz) {
@@ -389,48 +361,73 @@ __global__ void __launch_bounds__(128, 6)
     if (ni <= kFrontier) {
         // A target resolves every inherited source it does not accept by a
         // depth-first walk of the source's subtree, one source per lane; next to a
-        // dense region a few sources carry almost all the work.  Split the sources
-        // the walks would split first (not accepted, not leaves, and for a target
-        // that is not a leaf, larger than it) in warp-wide rounds while the list
-        // fits in kFrontier entries; the walks then start from the pieces.  The set
-        // of pairs does not change, only the order of discovery.
+        // dense region a few sources carry almost all the work.  Instead, rounds of
+        // the whole warp classify every source once (accepted; split, when it is
+        // not accepted, has children and the target is a leaf or smaller than it;
+        // or neither) and replace the split ones by their children while the list
+        // fits in kFrontier entries.  The set of pairs does not change, only the
+        // order of discovery.  When a round splits nothing and every source gives
+        // exactly one pair (no selection table), the pairs are placed by ballot and
+        // no walk is needed.
+        constexpr int R = kFrontier / 32;
         int cur = 0;
         for (int k = lane; k < ni; k += 32) sF[wib][0][k] = F[k];
         __syncwarp();
-        auto splits = [&](int S, int &nc) {
-            nc = 1;
-            if ((S & (kP2PFlag | kM2PFlag)) || c.nchild[S] == 0) return false;
-            int Cs[3], hs, ls;
-            cell_geom(c, S, Cs, hs, ls);
-            if ((!T.leaf && ls >= T.level) || mac_accept(T, Cs, hs, theta2, theta2f)) return false;
-            nc = c.nchild[S];
-            return true;
-        };
         for (int round = 0; round < 8; ++round) {
+            const int *E = sF[wib][cur];
+            int *nsplit = sN[wib];  // per source: its children when split, else -1
+            unsigned ma[R], mo[R];
             int total = 0;
-            bool any = false;
-            for (int k0 = 0; k0 < ni; k0 += 32) {
-                int nc = 0;
-                if (k0 + lane < ni) any |= splits(sF[wib][cur][k0 + lane], nc);
-                total += warp_sum(nc);
+            bool any_split = false, single = true;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                ma[r] = mo[r] = 0u;
+                if (r * 32 < ni) {
+                    const int k = r * 32 + lane;
+                    bool acc = false, sp = false, one = false;
+                    int nc = 0;
+                    if (k < ni) {
+                        const int S = E[k];
+                        nc = 1;
+                        if (!(S & (kP2PFlag | kM2PFlag))) {
+                            int Cs[3], hs, ls;
+                            cell_geom(c, S, Cs, hs, ls);
+                            const int nch = c.nchild[S];
+                            acc = mac_accept(T, Cs, hs, theta2, theta2f);
+                            sp = !acc && nch > 0 && (T.leaf || ls < T.level);
+                            one = !sp;
+                            if (sp) nc = nch;
+                        }
+                        nsplit[k] = sp ? nc : -1;
+                    }
+                    ma[r] = __ballot_sync(0xffffffffu, acc);
+                    mo[r] = __ballot_sync(0xffffffffu, one && !acc);
+                    single = __all_sync(0xffffffffu, k >= ni || one) && single;
+                    any_split = __any_sync(0xffffffffu, sp) || any_split;
+                    total += warp_sum(nc);
+                }
             }
-            if (!__any_sync(0xffffffffu, any) || total > kFrontier) break;
+            if (!any_split) {
+                if (!sel && single) {
+                    write_single_pairs<R>(T, E, ni, ma, mo, c, L, counters, cap_m, cap_p, cap_d, hash_keys, flags);
+                    return;
+                }
+                break;
+            }
+            if (total > kFrontier) break;
+            __syncwarp();
             int base = 0;
             for (int k0 = 0; k0 < ni; k0 += 32) {
-                int nc = 0, S = -1;
-                bool sp = false;
-                if (k0 + lane < ni) {
-                    S = sF[wib][cur][k0 + lane];
-                    sp = splits(S, nc);
-                } else {
-                    nc = 0;
-                }
+                const int k = k0 + lane;
+                const int ns = k < ni ? nsplit[k] : 0;
+                const int nc = k < ni ? (ns > 0 ? ns : 1) : 0;
                 const int pos = base + warp_excl(nc);
-                if (k0 + lane < ni) {
+                if (k < ni) {
+                    const int S = E[k];
                     int *dst = sF[wib][cur ^ 1] + pos;
-                    if (sp) {
+                    if (ns > 0) {
                         const int c0 = c.child0[S];
-                        for (int j = 0; j < nc; ++j) dst[j] = c0 + j;
+                        for (int j = 0; j < ns; ++j) dst[j] = c0 + j;
                     } else {
                         dst[0] = S;
                     }
@@ -443,12 +440,6 @@ __global__ void __launch_bounds__(128, 6)
         }
         __syncwarp();
         F = sF[wib][cur];
-        // Without a selection table, a target whose split sources each resolve to
-        // one pair needs no walk: one acceptance test per source decides its pair,
-        // the lanes' pairs are placed by ballot, and the lists come out in the order
-        // the walks give.
-        if (!sel && lists_by_ballot(T, F, ni, c, L, theta2, theta2f, counters, cap_m, cap_p, cap_d, hash_keys, flags))
-            return;
     }
     int m = 0, p = 0, d = 0, q = 0, l = 0;
     for (int k = lane; k < ni; k += 32) {

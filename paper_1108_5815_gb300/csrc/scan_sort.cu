@@ -179,6 +179,20 @@ constexpr uint64_t kLbInclusive = 2ull << 62;  // look-back word: prefix through
 constexpr uint32_t kLookbackPolls = 1u << 20;
 constexpr int kLookbackWindow = 8;  // earlier tiles whose look-back words are read together
 
+// The lanes of the warp whose 8-bit digit equals this lane's: one ballot per
+// digit bit, each keeping the lanes that agree on that bit.
+__device__ __forceinline__ unsigned digit_peers(uint32_t dig)
+{
+    unsigned peers = 0xffffffffu;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        const bool bit = (dig >> b) & 1u;
+        const unsigned m = __ballot_sync(0xffffffffu, bit);
+        peers &= bit ? m : ~m;
+    }
+    return peers;
+}
+
 // Digit counts of passes 0 .. passes-1 over all keys (counts[pass][digit], zeroed).
 __global__ void __launch_bounds__(256)
     k_radix_counts(const uint64_t *__restrict__ keys, int64_t n, int passes, uint32_t *__restrict__ counts)
@@ -249,7 +263,7 @@ __global__ void __launch_bounds__(kSortThreads, 2)
         const bool valid = li < tile_n;
         const uint32_t dig = (uint32_t)(key[i] >> shift) & 0xffu;
         const unsigned active = __ballot_sync(0xffffffffu, valid);
-        const unsigned peers = __match_any_sync(0xffffffffu, valid ? dig : 0x100u) & active;
+        const unsigned peers = digit_peers(dig) & active;
         const uint32_t lr = __popc(peers & lt_mask);
         rank[i] = valid ? wc[dig] + lr : 0u;
         __syncwarp();

@@ -1094,7 +1094,7 @@ size_t m2l_tc_smem(int P2pad, bool bf16, int &nstages)
 static size_t m2l_tc_ta_smem(int P2pad, bool bf16, int &nbstages)
 {
     const size_t stage = 2 * (size_t)P2pad * (bf16 ? 64 : 128);
-    nbstages = (int)std::min<size_t>(8, (192 * 1024) / stage);
+    nbstages = (int)std::min<size_t>(4, (192 * 1024) / stage);  // more stages measured slower (L1 share)
     return nbstages * stage + 1024 + (2 * nbstages + 2 * 4 + 5) * 8 + 16;
 }
 

@@ -360,20 +360,37 @@ __global__ void k_level_starts(const uint64_t *__restrict__ lvl, int64_t n, int 
     if (lane == 0) start[L] = (int)(lo + c);
 }
 
-__device__ __forceinline__ int lower_pos(const uint32_t *__restrict__ B, int nb, uint32_t v)
+// The first positions of B[0, nb) (ascending) holding a value >= v1 and >= v2,
+// in one loop: both probes of a step are loaded before either is compared, so
+// the two searches cost the latency of one.
+__device__ __forceinline__ void lower_pos2(const uint32_t *__restrict__ B, int nb, uint32_t v1, uint32_t v2, int &r1,
+                                           int &r2)
 {
-    int lo = 0, hi = nb;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (B[mid] < v)
-            lo = mid + 1;
-        else
-            hi = mid;
+    int lo1 = 0, hi1 = nb, lo2 = 0, hi2 = nb;
+    while (lo1 < hi1 || lo2 < hi2) {
+        const int m1 = (lo1 + hi1) >> 1, m2 = (lo2 + hi2) >> 1;
+        const uint32_t x1 = lo1 < hi1 ? B[m1] : 0u, x2 = lo2 < hi2 ? B[m2] : 0u;
+        if (lo1 < hi1) {
+            if (x1 < v1)
+                lo1 = m1 + 1;
+            else
+                hi1 = m1;
+        }
+        if (lo2 < hi2) {
+            if (x2 < v2)
+                lo2 = m2 + 1;
+            else
+                hi2 = m2;
+        }
     }
-    return lo;
+    r1 = lo1;
+    r2 = lo2;
 }
 
 // For the cells [a, b) at level l: packed[c-a] = nchild | (split ? 1 << 32 : 0).
+// A split cell's child0 holds, until its children are written, the index of
+// its first child boundary in the level's boundary list (the emit step reads it
+// back instead of searching again).
 __global__ void k_split_count(CellArrays c, const uint32_t *__restrict__ bpos,
                               const int *__restrict__ lstart, int a, int b, int level, int ncrit,
                               int max_depth, int64_t *__restrict__ packed, const int *__restrict__ sz, int len)
@@ -396,10 +413,48 @@ __global__ void k_split_count(CellArrays c, const uint32_t *__restrict__ bpos,
     if (ce - cb > ncrit && level < max_depth) {
         const uint32_t *B = bpos + lstart[level + 1];
         const int nb = lstart[level + 2] - lstart[level + 1];
-        const int lo = lower_pos(B, nb, (uint32_t)cb + 1), hi = lower_pos(B, nb, (uint32_t)ce);
+        int lo, hi;
+        lower_pos2(B, nb, (uint32_t)cb + 1, (uint32_t)ce, lo, hi);
         v = (int64_t)(hi - lo + 1) | ((int64_t)1 << 32);
+        c.child0[i] = lo;
     }
     packed[i - a] = v;
+}
+
+// Writes the nch (<= 8) children of cell i (level l, particles [cb, ce)) at
+// cells first .. first + nch - 1.  B[lo .. lo + nch - 2] are the boundaries
+// between them; all boundaries, then all first keys, are loaded at once (two
+// memory latencies per cell, not two per child).
+__device__ __forceinline__ void emit_children(CellArrays &c, const uint64_t *__restrict__ keys,
+                                              const uint32_t *__restrict__ B, int lo, int i, int level, int cb,
+                                              int ce, int nch, int first, int tile, int lane)
+{
+    const int shift = 3 * (kKeyBits - level - 1);
+    const uint64_t pre = c.prefix[i];
+    const int sys = c.sys[i];
+    int end[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) end[q] = q + 1 < nch ? (int)B[lo + q] : ce;
+    int oct[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) oct[q] = q < nch ? (int)((keys[q == 0 ? cb : end[q - 1]] >> shift) & 7ull) : 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        if (q >= nch) break;
+        const int ch = first + q, o = oct[q];
+        c.level[ch] = level + 1;
+        c.prefix[ch] = (pre << 3) | (uint64_t)o;
+        c.begin[ch] = q == 0 ? cb : end[q - 1];
+        c.end[ch] = end[q];
+        c.parent[ch] = i;
+        c.child0[ch] = -1;
+        c.nchild[ch] = 0;
+        c.tile[ch] = tile + o;
+        c.lane[ch] = lane;
+        c.sys[ch] = sys;
+    }
+    c.child0[i] = first;
+    c.nchild[i] = nch;
 }
 
 // Writes the children of the cells [a, b) (level l) starting at cell index b,
@@ -431,32 +486,9 @@ __global__ void k_split_emit(CellArrays c, const uint64_t *__restrict__ keys,
     const int rank = (int)(e >> 32);
     const int window = rank / kTile, lane = rank % kTile;
     const int cb = c.begin[i], ce = c.end[i];
-    const int shift = 3 * (kKeyBits - level - 1);
-    const uint64_t pre = c.prefix[i];
-    const int sys = c.sys[i];
     const uint32_t *B = bpos + lstart[level + 1];
-    const int nb = lstart[level + 2] - lstart[level + 1];
-    const int lo = lower_pos(B, nb, (uint32_t)cb + 1);
-    const int nch = (int)(v & 0xffffffffll);
-    int beg = cb;
-    for (int k = 0; k < nch; ++k) {
-        const int end = k + 1 < nch ? (int)B[lo + k] : ce;
-        const int o = (int)((keys[beg] >> shift) & 7ull);
-        const int ch = first + k;
-        c.level[ch] = level + 1;
-        c.prefix[ch] = (pre << 3) | (uint64_t)o;
-        c.begin[ch] = beg;
-        c.end[ch] = end;
-        c.parent[ch] = i;
-        c.child0[ch] = -1;
-        c.nchild[ch] = 0;
-        c.tile[ch] = tile_base + window * 8 + o;
-        c.lane[ch] = lane;
-        c.sys[ch] = sys;
-        beg = end;
-    }
-    c.child0[i] = first;
-    c.nchild[i] = nch;
+    const int lo = c.child0[i];  // left there by k_split_count
+    emit_children(c, keys, B, lo, i, level, cb, ce, (int)(v & 0xffffffffll), first, tile_base + window * 8, lane);
 }
 
 // Next level of a replayed plan: the children of level `level` start at the
@@ -524,8 +556,10 @@ __global__ void __launch_bounds__(kSmallLevelThreads)
                 if (ce - cb > ncrit && level < max_depth) {
                     const uint32_t *B = bpos + bstart[level + 1];
                     const int nb = bstart[level + 2] - bstart[level + 1];
-                    const int lo = lower_pos(B, nb, (uint32_t)cb + 1), hi = lower_pos(B, nb, (uint32_t)ce);
+                    int lo, hi;
+                    lower_pos2(B, nb, (uint32_t)cb + 1, (uint32_t)ce, lo, hi);
                     v = (long long)(hi - lo + 1) | ((long long)1 << 32);
+                    c.child0[i] = lo;  // read back by the emit step below
                 }
             }
             loc[u] = run;  // exclusive within the thread's cells
@@ -591,31 +625,9 @@ __global__ void __launch_bounds__(kSmallLevelThreads)
             const int rank = (int)(e >> 32);
             const int window = rank / kTile, tl = rank % kTile;
             const int cb = c.begin[i], ce = c.end[i];
-            const int shift = 3 * (kKeyBits - level - 1);
-            const uint64_t pre = c.prefix[i];
-            const int sys = c.sys[i];
             const uint32_t *B = bpos + bstart[level + 1];
-            const int nb = bstart[level + 2] - bstart[level + 1];
-            const int lo = lower_pos(B, nb, (uint32_t)cb + 1);
-            int beg = cb;
-            for (int q = 0; q < nch; ++q) {
-                const int end = q + 1 < nch ? (int)B[lo + q] : ce;
-                const int o = (int)((keys[beg] >> shift) & 7ull);
-                const int ch = first + q;
-                c.level[ch] = level + 1;
-                c.prefix[ch] = (pre << 3) | (uint64_t)o;
-                c.begin[ch] = beg;
-                c.end[ch] = end;
-                c.parent[ch] = i;
-                c.child0[ch] = -1;
-                c.nchild[ch] = 0;
-                c.tile[ch] = tile_base + window * 8 + o;
-                c.lane[ch] = tl;
-                c.sys[ch] = sys;
-                beg = end;
-            }
-            c.child0[i] = first;
-            c.nchild[i] = nch;
+            const int lo = c.child0[i];  // left by the count step
+            emit_children(c, keys, B, lo, i, level, cb, ce, nch, first, tile_base + window * 8, tl);
         }
     }
 }

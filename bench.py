@@ -341,6 +341,13 @@ def captured_traffic(kernel):
     return rec["dram_bytes_per_launch"]
 
 
+def m2l_tc_kernel(p):
+    """The tensor-core M2L kernel the library runs at order p: A in tensor
+    memory while the padded expansion length (p+1)^2 -> multiple of 32 is at
+    most 128, A in shared memory above that."""
+    return "k_m2l_tc_ta" if -(-(p + 1) ** 2 // 32) * 32 <= 128 else "k_m2l_tc"
+
+
 def hot_kernel_rooflines(st, ms_p2p, ms_m2l, p, precision, pk):
     """P2P against the FP32 pipe (derived peak) and M2L against its own pipe.
 
@@ -361,10 +368,10 @@ def hot_kernel_rooflines(st, ms_p2p, ms_m2l, p, precision, pk):
     if precision == "fp32":
         kern, bound, peak, src = "k_m2l_simt", "alu", fp32_peak, "derived FP32 peak (as for P2P)"
     elif precision == "tf32x3":
-        kern, bound, peak = "k_m2l_tc<tf32x3>", "tensor", pk["tf32_tflops"]
+        kern, bound, peak = f"{m2l_tc_kernel(p)}<tf32x3>", "tensor", pk["tf32_tflops"]
         src = "TF32 dense: cuBLAS fp32 GEMM with TF32, 8192^3, measured in this process"
     else:
-        kern, bound, peak = "k_m2l_tc<bf16x3>", "tensor", pk["bf16_tflops"]
+        kern, bound, peak = f"{m2l_tc_kernel(p)}<bf16x3>", "tensor", pk["bf16_tflops"]
         src = f"BF16 dense {pk['hbm_bf16_label']} (MEASURED_PEAKS.json)"
     out.append({"kernel": kern, "bound": bound, "achieved": m2l_tf, "peak": peak,
                 "unit": "TFLOP/s", "frac": m2l_tf / peak, "traffic": captured_traffic(kern),

@@ -107,7 +107,8 @@ struct Workspace {
     // the far-field chain.  They are ordered after the caller's stream on entry
     // and the caller's stream is ordered after them on exit.
     cudaStream_t main_stream = nullptr, far_stream = nullptr;
-    cudaEvent_t ev_in = nullptr, ev_tree = nullptr, ev_fork = nullptr, ev_join = nullptr, ev_out = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_tree = nullptr, ev_fork = nullptr, ev_join = nullptr, ev_out = nullptr,
+                ev_read = nullptr;
 };
 
 std::mutex g_ws_mu;
@@ -159,7 +160,7 @@ void ensure_streams(Workspace &ws)
     FMM_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&lo, &hi));
     FMM_CUDA_TRY(cudaStreamCreateWithFlags(&ws.main_stream, cudaStreamNonBlocking));
     FMM_CUDA_TRY(cudaStreamCreateWithPriority(&ws.far_stream, cudaStreamNonBlocking, hi));
-    for (cudaEvent_t *e : {&ws.ev_in, &ws.ev_tree, &ws.ev_fork, &ws.ev_join, &ws.ev_out})
+    for (cudaEvent_t *e : {&ws.ev_in, &ws.ev_tree, &ws.ev_fork, &ws.ev_join, &ws.ev_out, &ws.ev_read})
         FMM_CUDA_TRY(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
 }
 
@@ -212,8 +213,17 @@ void upload(Workspace &ws, void *dst, const void *src, size_t bytes, cudaStream_
 }
 
 // Copies the device flags plus `n` extra (dev -> host) items and synchronises.
-void sync_point(Workspace &ws, cudaStream_t st, const int *flags_dev,
-                std::initializer_list<std::pair<const void *, size_t>> items, void *host_out)
+// A read-back of the device flags and some device values, in two halves:
+// read_begin enqueues the copies on st and records an event; read_end waits for
+// that event only (work enqueued on st after read_begin keeps running), raises
+// the error a flag reports and copies the values out.
+struct ReadBack {
+    char *h;
+    size_t total;
+};
+
+ReadBack read_begin(Workspace &ws, cudaStream_t st, const int *flags_dev,
+                    std::initializer_list<std::pair<const void *, size_t>> items)
 {
     size_t total = sizeof(int) * kNumFlags;
     for (auto &it : items) total += it.second;
@@ -224,15 +234,29 @@ void sync_point(Workspace &ws, cudaStream_t st, const int *flags_dev,
         FMM_CUDA_TRY(cudaMemcpyAsync(h + off, it.first, it.second, cudaMemcpyDeviceToHost, st));
         off += it.second;
     }
-    FMM_CUDA_TRY(cudaStreamSynchronize(st));
-    const int *f = reinterpret_cast<const int *>(h);
+    if (!ws.ev_read) FMM_CUDA_TRY(cudaEventCreateWithFlags(&ws.ev_read, cudaEventDisableTiming));
+    FMM_CUDA_TRY(cudaEventRecord(ws.ev_read, st));
+    return {h, total};
+}
+
+void read_end(Workspace &ws, const ReadBack &rb, void *host_out)
+{
+    FMM_CUDA_TRY(cudaEventSynchronize(ws.ev_read));
+    const int *f = reinterpret_cast<const int *>(rb.h);
     if (f[kFlagNonfinite]) throw Error{FMM_ERR_NONFINITE, "a coordinate is NaN or infinite"};
     if (f[kFlagHashFull]) throw Error{FMM_ERR_CAPACITY, "offset-class table is full"};
     if (f[kFlagClassRange])
         throw Error{FMM_ERR_CAPACITY, "an M2L offset exceeds the class key range (2^18 cells)"};
     if (f[kFlagStack]) throw Error{FMM_ERR_CAPACITY, "traversal stack overflow"};
     if (f[kFlagTimeout]) throw Error{FMM_ERR_TIMEOUT, "a bounded device-side wait expired (M2L pipeline)"};
-    if (host_out) std::memcpy(host_out, h + sizeof(int) * kNumFlags, total - sizeof(int) * kNumFlags);
+    if (host_out) std::memcpy(host_out, rb.h + sizeof(int) * kNumFlags, rb.total - sizeof(int) * kNumFlags);
+}
+
+// Both halves at once: the host waits until st has reached the read-back.
+void sync_point(Workspace &ws, cudaStream_t st, const int *flags_dev,
+                std::initializer_list<std::pair<const void *, size_t>> items, void *host_out)
+{
+    read_end(ws, read_begin(ws, st, flags_dev, items), host_out);
 }
 
 struct Events {
@@ -605,6 +629,8 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
     L.p2l_cnt = need<int>(ws, "p2l_cnt", ncells, st);
     int64_t m2p_cap = std::max<int64_t>(ws.cap_m2p, 4096), p2l_cap = std::max<int64_t>(ws.cap_p2l, 4096);
     int64_t m2l_total = 0, p2p_total = 0, m2p_total = 0, p2l_total = 0;
+    float4 *far = lists_only ? nullptr : need<float4>(ws, "far", N, st);
+    float4 *near = lists_only ? nullptr : need<float4>(ws, "near", N, st);
     for (int attempt = 0;; ++attempt) {
         L.m2p_src = need<int>(ws, "m2p_src", m2p_cap, st);
         L.m2p_tgt = need<int>(ws, "m2p_tgt", m2p_cap, st);
@@ -627,8 +653,23 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
                                                      flags);
             FMM_LAUNCH_CHECK();
         }
+        ev.rec(10, st);  // the lists of this attempt are complete
         unsigned long long tot[5];
-        sync_point(ws, st, flags, {{tcount, sizeof(tot)}}, tot);
+        const ReadBack rb = read_begin(ws, st, flags, {{tcount, sizeof(tot)}});
+        if (!lists_only) {
+            // P2P needs only the per-leaf lists: it is enqueued behind the read-back
+            // of the list totals, and the host waits for the read-back alone while
+            // P2P runs.  (If a list outgrew its buffer, the traversal and P2P run
+            // again.)
+            FMM_CUDA_TRY(cudaEventRecord(ws.ev_fork, st));
+            FMM_CUDA_TRY(cudaStreamWaitEvent(fs, ws.ev_fork, 0));
+            set_carveout_once((const void *)k_p2p, cudaSharedmemCarveoutMaxShared);
+            ev.rec(8, st);
+            k_p2p<<<(unsigned)std::max(1, nleaves), 32, 0, st>>>(c, L, leaves, nleaves, pts, near);
+            FMM_LAUNCH_CHECK();
+            ev.rec(9, st);
+        }
+        read_end(ws, rb, tot);
         if ((int64_t)tot[0] <= m2l_cap && (int64_t)tot[1] <= p2p_cap && (int64_t)tot[2] <= def_cap &&
             (int64_t)tot[3] <= m2p_cap && (int64_t)tot[4] <= p2l_cap) {
             m2l_total = (int64_t)tot[0];
@@ -653,7 +694,6 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
             }
         }
     }
-    ev.rec(10, st);  // the lists are complete
     ws.cap_m2l = m2l_cap;
     ws.cap_p2p = p2p_cap;
     ws.cap_def = def_cap;
@@ -669,26 +709,16 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
     // P2P needs only the leaf lists: it runs on the caller's stream while the
     // far-field chain (classes, tiles, upward pass, M2L, downward pass) runs on
     // the library's high-priority stream; the two join before the final sum.
-    float4 *far = need<float4>(ws, "far", N, st);
-    float4 *near = need<float4>(ws, "near", N, st);
-    FMM_CUDA_TRY(cudaEventRecord(ws.ev_fork, st));
-    FMM_CUDA_TRY(cudaStreamWaitEvent(fs, ws.ev_fork, 0));
-    {
-        // One warp (block) per leaf with up to 128 registers a thread, 16 warps per
-        // SM: the packed arithmetic keeps more interactions in flight than with
-        // more warps of fewer registers (measured 1.68 ms at 80 registers and 24
-        // warps, 1.60 ms at 128 and 16, uniform 1M).  That fills the register file;
-        // as blocks retire, the far-field stream (higher priority) gets SMs for
-        // its class and tile kernels, and M2L starts on SMs that P2P has drained.
-        // An SM's L1/shared split can only change when the SM is idle; with the
-        // maximum shared carveout the far-field kernels (up to ~200 KB of shared
-        // memory) can start on SMs that run P2P blocks.
-        set_carveout_once((const void *)k_p2p, cudaSharedmemCarveoutMaxShared);
-        ev.rec(8, st);
-        k_p2p<<<(unsigned)std::max(1, nleaves), 32, 0, st>>>(c, L, leaves, nleaves, pts, near);
-        FMM_LAUNCH_CHECK();
-    }
-    ev.rec(9, st);
+    // P2P (launched in the traversal loop above) runs on the caller's stream:
+    // one warp (block) per leaf with up to 128 registers a thread, 16 warps per
+    // SM; the packed arithmetic keeps more interactions in flight than with more
+    // warps of fewer registers (measured 1.68 ms at 80 registers and 24 warps,
+    // 1.60 ms at 128 and 16, uniform 1M).  That fills the register file; as
+    // blocks retire, the far-field stream (higher priority) gets SMs for its class
+    // and tile kernels, and M2L starts on SMs that P2P has drained.  An SM's
+    // L1/shared split can only change when the SM is idle; with the maximum shared
+    // carveout the far-field kernels (up to ~200 KB of shared memory) can start
+    // on SMs that run P2P blocks.
     if (o.serialize_phases) {  // the far-field chain after P2P (each phase timed alone)
         FMM_CUDA_TRY(cudaEventRecord(ws.ev_fork, st));
         FMM_CUDA_TRY(cudaStreamWaitEvent(fs, ws.ev_fork, 0));

@@ -705,33 +705,24 @@ void launch_shift_batched(bool l2l, const CellArrays &c, int a, int b, const flo
     }
 }
 
-// One warp per leaf: far-field potential and gradient from the leaf's local
-// expansion, phi = Re sum L^ R^, d/dz and D+ = d/dx + i d/dy from the
-// derivative ladder.  Every term (n, m), m >= 0, reads one record of 8 floats
-// from shared memory (two 16-byte loads), built once per leaf with the
-// normalisation ratios, the weight 2 of the m > 0 real parts and the two D+
-// contributions already combined:
+// Far-field potential and gradient from a leaf's local expansion,
+// phi = Re sum L^ R^, d/dz and D+ = d/dx + i d/dy from the derivative ladder.
+// Every term (n, m), m >= 0, reads one record of 8 floats from shared memory
+// (two 16-byte loads), built once per leaf with the normalisation ratios, the
+// weight 2 of the m > 0 real parts and the two D+ contributions already
+// combined:
 //   [w Lr, w Li, w Lzr, w Lzi, X1r - X2r, X1i - X2i, X1r + X2r, X1i + X2i]
 // with Lz = L_{n+1}^m s0, X1 = L_{n+1}^{m-1} s1 (m >= 1), X2 = L_{n+1}^{m+1} s2
 // (zero past n + 1 > p), so that
 //   phi += w(Lr rr - Li ri),  dz += w(Lzr rr - Lzi ri),
 //   dpr += (X1r - X2r) rr - (X1i - X2i) ri,  dpi += (X1r + X2r) ri + (X1i + X2i) rr.
-template <int PT>
-__global__ void __launch_bounds__(32, 24)
-    k_l2p(CellArrays c, const int *__restrict__ leaves, int nleaves, const float4 *__restrict__ pts,
-          int p_run, int P2pad, const float *__restrict__ L, float4 *__restrict__ far, const int *__restrict__ sz)
+
+// The records of local expansion Lg (P2 floats) into rec (2 ntri float4),
+// staging Lg in Lh; the 32 lanes of the warp share the work.
+__device__ __forceinline__ void l2p_records(const float *__restrict__ Lg, int p, float *Lh, float4 *rec, int lane)
 {
-    const int p = PT > 0 ? PT : p_run;  // compile-time order when PT > 0 (as in k_p2m)
-    extern __shared__ float4 l2p_sm[];  // 2 x ntri records, then P2pad floats of L
-    if (sz) nleaves = sz[kSzLeaves];
-    const int li = blockIdx.x;
-    if (li >= nleaves) return;
-    const int cell = leaves[li];
-    const int lane = threadIdx.x;
     const int P2 = nterms(p), ntri = (p + 1) * (p + 2) / 2;
-    float4 *rec = l2p_sm;
-    float *Lh = reinterpret_cast<float *>(l2p_sm + 2 * ntri);
-    for (int k = lane; k < P2; k += 32) Lh[k] = L[(int64_t)cell * P2pad + k];
+    for (int k = lane; k < P2; k += 32) Lh[k] = Lg[k];
     __syncwarp();
     for (int t = lane; t < ntri; t += 32) {
         int n = 0;
@@ -759,9 +750,14 @@ __global__ void __launch_bounds__(32, 24)
         rec[2 * t + 1] = make_float4(x1r - x2r, x1i - x2i, x1r + x2r, x1i + x2i);
     }
     __syncwarp();
-    const Frame fr = cell_frame(c, cell);
+}
+
+// phi and grad at particle pt from the records of its leaf (frame fr).
+template <int PT>
+__device__ __forceinline__ float4 l2p_eval(const float4 *rec, const Frame &fr, float4 pt, int p_run)
+{
+    const int p = PT > 0 ? PT : p_run;
     const float inv_s = fr.hi.w, inv_s2 = inv_s * inv_s;
-    const int b = c.begin[cell], e = c.end[cell];
     struct Sums {
         float phi, dz, dpr, dpi;
     };
@@ -772,73 +768,125 @@ __global__ void __launch_bounds__(32, 24)
         sm.dpr = fmaf(v.x, rr, fmaf(-v.y, ri, sm.dpr));
         sm.dpi = fmaf(v.z, ri, fmaf(v.w, rr, sm.dpi));
     };
-    for (int i = b + lane; i < e; i += 32) {
-        const float4 pt = pts[i];
-        float x, y, z;
-        frame_offset(fr, pt, x, y, z);
-        const float r2 = x * x + y * y + z * z;
-        // orders m and m + 1 advance together (two independent recurrences in n,
-        // each with its own sums) so that a lane has two chains in flight
-        Sums sa = {0.f, 0.f, 0.f, 0.f}, sb = sa;
-        float mre = 1.f, mim = 0.f;  // R^_m^m
+    float x, y, z;
+    frame_offset(fr, pt, x, y, z);
+    const float r2 = x * x + y * y + z * z;
+    // orders m and m + 1 advance together (two independent recurrences in n,
+    // each with its own sums) so that a lane has two chains in flight
+    Sums sa = {0.f, 0.f, 0.f, 0.f}, sb = sa;
+    float mre = 1.f, mim = 0.f;  // R^_m^m
 #pragma unroll
-        for (int m = 0; m <= p; m += 2) {
-            if (m > 0) {
-                const float f = c_rec_d[m];
-                const float nre = f * (x * mre - y * mim), nim = f * (x * mim + y * mre);
-                mre = nre;
-                mim = nim;
-            }
-            const bool two = m + 1 <= p;
-            float bre = 0.f, bim = 0.f;  // R^_{m+1}^{m+1}
-            if (two) {
-                const float f = c_rec_d[m + 1];
-                bre = f * (x * mre - y * mim);
-                bim = f * (x * mim + y * mre);
-            }
-            int ta = m * (m + 1) / 2 + m;  // term (m, m)
-            term(ta, mre, mim, sa);
-            float a2r = 0.f, a2i = 0.f, a1r = mre, a1i = mim;  // chain m
-            float b2r = 0.f, b2i = 0.f, b1r = bre, b1i = bim;  // chain m + 1
-#pragma unroll 2
-            for (int n = m + 1; n <= p; ++n) {
-                ta += n;  // term (n, m)
-                const float aa = c_rec_a[ta] * z, ab = c_rec_b[ta] * r2;
-                const float rr = aa * a1r - ab * a2r, ri = aa * a1i - ab * a2i;
-                a2r = a1r;
-                a2i = a1i;
-                a1r = rr;
-                a1i = ri;
-                term(ta, rr, ri, sa);
-                float qr = b1r, qi = b1i;  // n == m + 1: the diagonal itself
-                if (n > m + 1) {
-                    const int tb = ta + 1;
-                    const float ba = c_rec_a[tb] * z, bb = c_rec_b[tb] * r2;
-                    qr = ba * b1r - bb * b2r;
-                    qi = ba * b1i - bb * b2i;
-                    b2r = b1r;
-                    b2i = b1i;
-                    b1r = qr;
-                    b1i = qi;
-                }
-                term(ta + 1, qr, qi, sb);
-            }
-            mre = bre;  // the next pair starts from R^_{m+1}^{m+1}
-            mim = bim;
+    for (int m = 0; m <= p; m += 2) {
+        if (m > 0) {
+            const float f = c_rec_d[m];
+            const float nre = f * (x * mre - y * mim), nim = f * (x * mim + y * mre);
+            mre = nre;
+            mim = nim;
         }
-        const float phi = sa.phi + sb.phi, dz = sa.dz + sb.dz, dpr = sa.dpr + sb.dpr, dpi = sa.dpi + sb.dpi;
-        far[i] = make_float4(phi * inv_s, dpr * inv_s2, dpi * inv_s2, dz * inv_s2);
+        const bool two = m + 1 <= p;
+        float bre = 0.f, bim = 0.f;  // R^_{m+1}^{m+1}
+        if (two) {
+            const float f = c_rec_d[m + 1];
+            bre = f * (x * mre - y * mim);
+            bim = f * (x * mim + y * mre);
+        }
+        int ta = m * (m + 1) / 2 + m;  // term (m, m)
+        term(ta, mre, mim, sa);
+        float a2r = 0.f, a2i = 0.f, a1r = mre, a1i = mim;  // chain m
+        float b2r = 0.f, b2i = 0.f, b1r = bre, b1i = bim;  // chain m + 1
+#pragma unroll 2
+        for (int n = m + 1; n <= p; ++n) {
+            ta += n;  // term (n, m)
+            const float aa = c_rec_a[ta] * z, ab = c_rec_b[ta] * r2;
+            const float rr = aa * a1r - ab * a2r, ri = aa * a1i - ab * a2i;
+            a2r = a1r;
+            a2i = a1i;
+            a1r = rr;
+            a1i = ri;
+            term(ta, rr, ri, sa);
+            float qr = b1r, qi = b1i;  // n == m + 1: the diagonal itself
+            if (n > m + 1) {
+                const int tb = ta + 1;
+                const float ba = c_rec_a[tb] * z, bb = c_rec_b[tb] * r2;
+                qr = ba * b1r - bb * b2r;
+                qi = ba * b1i - bb * b2i;
+                b2r = b1r;
+                b2i = b1i;
+                b1r = qr;
+                b1i = qi;
+            }
+            term(ta + 1, qr, qi, sb);
+        }
+        mre = bre;  // the next pair starts from R^_{m+1}^{m+1}
+        mim = bim;
+    }
+    const float phi = sa.phi + sb.phi, dz = sa.dz + sb.dz, dpr = sa.dpr + sb.dpr, dpi = sa.dpi + sb.dpi;
+    return make_float4(phi * inv_s, dpr * inv_s2, dpi * inv_s2, dz * inv_s2);
+}
+
+// Particle-parallel L2P.  Warp w takes the sorted particles 32 w .. 32 w + 31,
+// whatever leaves they belong to (pcell: the leaf of each sorted particle), so
+// every lane has a particle; a leaf of n particles no longer leaves 32 - n
+// lanes, or 64 - n in a second pass, without work.  The lanes' leaves form
+// runs; the warp builds the records of up to kL2PSlots runs at a time in its own
+// shared memory, and each lane evaluates its particle from its run's records.
+constexpr int kL2PWarps = 4;  // warps per block
+constexpr int kL2PSlots = 3;  // leaves whose records a warp holds at once
+
+template <int PT>
+__global__ void __launch_bounds__(32 * kL2PWarps, 6)
+    k_l2p(CellArrays c, const int *__restrict__ pcell, int64_t n, const float4 *__restrict__ pts, int p_run,
+          int P2pad, const float *__restrict__ L, float4 *__restrict__ far)
+{
+    const int p = PT > 0 ? PT : p_run;  // compile-time order when PT > 0 (as in k_p2m)
+    extern __shared__ float4 l2p_sm[];  // per warp and slot: 2 x ntri records, then P2pad floats of L
+    const int ntri = (p + 1) * (p + 2) / 2;
+    const int slot_f4 = 2 * ntri + P2pad / 4;  // float4 per slot
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float4 *wsm = l2p_sm + (size_t)warp * kL2PSlots * slot_f4;
+    const int64_t i = ((int64_t)blockIdx.x * kL2PWarps + warp) * 32 + lane;
+    const bool valid = i < n;
+    const int cell = valid ? pcell[i] : -1;
+    const int prev = __shfl_up_sync(0xffffffffu, cell, 1);
+    const unsigned heads = __ballot_sync(0xffffffffu, valid && (lane == 0 || prev != cell));
+    if (heads == 0) return;  // the whole warp is past the particles
+    const int nrun = __popc(heads);
+    const int myrun = __popc(heads & (0xffffffffu >> (31 - lane))) - 1;  // runs starting at or before this lane
+    float4 pt = make_float4(0.f, 0.f, 0.f, 0.f);
+    Frame fr = {pt, pt};
+    if (valid) {
+        pt = pts[i];
+        fr = cell_frame(c, cell);
+    }
+    for (int r0 = 0; r0 < nrun; r0 += kL2PSlots) {
+#pragma unroll
+        for (int s = 0; s < kL2PSlots; ++s) {
+            if (r0 + s >= nrun) break;
+            // the lane that heads run r0 + s
+            const int hl = __ffs(__ballot_sync(0xffffffffu, ((heads >> lane) & 1u) && myrun == r0 + s)) - 1;
+            const int rc = __shfl_sync(0xffffffffu, cell, hl);
+            float4 *rec = wsm + (size_t)s * slot_f4;
+            l2p_records(L + (int64_t)rc * P2pad, p, reinterpret_cast<float *>(rec + 2 * ntri), rec, lane);
+        }
+        if (valid && myrun >= r0 && myrun < r0 + kL2PSlots)
+            far[i] = l2p_eval<PT>(wsm + (size_t)(myrun - r0) * slot_f4, fr, pt, p);
+        __syncwarp();
     }
 }
 
-void launch_l2p(const CellArrays &c, const int *leaves, int nleaves, unsigned grid, const float4 *pts, int p,
-                int P2pad, const float *L, float4 *far, cudaStream_t st, const int *sz)
+size_t l2p_block_smem(int p, int P2pad) { return (size_t)kL2PWarps * kL2PSlots * l2p_smem(p, P2pad); }
+
+void launch_l2p(const CellArrays &c, const int *pcell, int64_t n, const float4 *pts, int p, int P2pad,
+                const float *L, float4 *far, cudaStream_t st)
 {
-    const size_t sh = l2p_smem(p, P2pad);
+    if (n <= 0) return;
+    const size_t sh = l2p_block_smem(p, P2pad);
+    const unsigned grid = (unsigned)ceil_div(n, (int64_t)32 * kL2PWarps);
     switch (p) {
-#define FMM_L2P_CASE(P)                                                                    \
-    case P:                                                                                \
-        k_l2p<P><<<grid, 32, sh, st>>>(c, leaves, nleaves, pts, p, P2pad, L, far, sz); \
+#define FMM_L2P_CASE(P)                                                          \
+    case P:                                                                      \
+        set_smem_limit_once((const void *)k_l2p<P>, (int)sh);                     \
+        k_l2p<P><<<grid, 32 * kL2PWarps, sh, st>>>(c, pcell, n, pts, p, P2pad, L, far); \
         break;
         FMM_L2P_CASE(4)
         FMM_L2P_CASE(6)
@@ -847,7 +895,8 @@ void launch_l2p(const CellArrays &c, const int *leaves, int nleaves, unsigned gr
         FMM_L2P_CASE(12)
 #undef FMM_L2P_CASE
     default:
-        k_l2p<0><<<grid, 32, sh, st>>>(c, leaves, nleaves, pts, p, P2pad, L, far, sz);
+        set_smem_limit_once((const void *)k_l2p<0>, (int)sh);
+        k_l2p<0><<<grid, 32 * kL2PWarps, sh, st>>>(c, pcell, n, pts, p, P2pad, L, far);
     }
     FMM_LAUNCH_CHECK();
 }

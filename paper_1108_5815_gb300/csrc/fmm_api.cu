@@ -438,6 +438,7 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
     int tiles_total = 0;
     int nleaves = 0;
     int *leaves = nullptr;
+    int *pcell = need<int>(ws, "pcell", std::max(N, 1), st);  // the leaf of each sorted particle
     bool tree_done = false;
     if (fast_tree) {
         const int pdepth = (int)prev.lstart.size() - 2;
@@ -485,7 +486,7 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
         k_leaf_flags<<<(unsigned)ceil_div(cell_cap, 256), 256, 0, st>>>(c, 0, lflag, sz, cell_cap);
         FMM_LAUNCH_CHECK();
         scan_exclusive<int>(lflag, lex, cell_cap, lex + cell_cap, i32_tmp, st);
-        k_leaf_compact<<<(unsigned)ceil_div(cell_cap, 256), 256, 0, st>>>(c, 0, lex, leaves, sz);
+        k_leaf_compact<<<(unsigned)ceil_div(cell_cap, 256), 256, 0, st>>>(c, 0, lex, leaves, sz, pcell);
         FMM_LAUNCH_CHECK();
         FMM_CUDA_TRY(cudaMemcpyAsync(sz + kSzLeaves, lex + cell_cap, sizeof(int), cudaMemcpyDeviceToDevice, st));
         int hsz[kSzWords];
@@ -543,7 +544,7 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
         k_leaf_flags<<<(unsigned)ceil_div(ncells, 256), 256, 0, st>>>(c, ncells, lflag);
         FMM_LAUNCH_CHECK();
         scan_exclusive<int>(lflag, lex, ncells, lex + ncells, i32_tmp, st);
-        k_leaf_compact<<<(unsigned)ceil_div(ncells, 256), 256, 0, st>>>(c, ncells, lex, leaves);
+        k_leaf_compact<<<(unsigned)ceil_div(ncells, 256), 256, 0, st>>>(c, ncells, lex, leaves, nullptr, pcell);
         FMM_LAUNCH_CHECK();
         sync_point(ws, st, flags, {{lex + ncells, sizeof(int)}}, &nleaves);
     }
@@ -907,7 +908,7 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
             launch_shift_fp64(true, c, lstart[l], lstart[l + 1], get<double>(ws, "l2l64"), P2, P2pad, Lx, fs);
         else
             launch_shift_batched(true, c, lstart[l], lstart[l + 1], get<float>(ws, "l2l"), P2, P2pad, Lx, nullptr, fs);
-    launch_l2p(c, leaves, nleaves, (unsigned)nleaves, pts, p, P2pad, Lx, far, fs);
+    launch_l2p(c, pcell, N, pts, p, P2pad, Lx, far, fs);
     if (m2p_total > 0) {  // cell-particle pairs of the hybrid selection, added to the far field
         const size_t sh = m2p_smem(p, P2pad);
         if (sh > 48 * 1024) set_smem_limit_once((const void *)k_m2p, (int)sh);
@@ -1296,6 +1297,7 @@ void build_plan(fmm_plan &pl, Workspace &ws, const int64_t *offsets, const uint8
     b.leaf_ex = m.get<int>(cc + 1);
     b.scan_i32 = m.get<int>(scan_temp_elems(std::max<int64_t>({cc, (int64_t)kHashCap, (int64_t)s.tile_cap})));
     b.leaves = m.get<int>(cc);
+    b.pcell = m.get<int>(std::max<int64_t>(s.N, 1));
     ListArrays &L = b.L;
     for (int **a : {&L.m2l_off, &L.m2l_cnt, &L.p2p_off, &L.p2p_cnt, &L.def_off, &L.def_cnt, &L.m2p_off, &L.m2p_cnt,
                     &L.p2l_off, &L.p2l_cnt})

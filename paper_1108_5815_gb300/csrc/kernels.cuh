@@ -120,7 +120,7 @@ __global__ void k_fill_tile_cells(CellArrays c, int ncells, int *tile_cells, con
 __global__ void k_cell_geom(CellArrays c, int ncells, const double *box, const int *sz = nullptr);
 // With sz: flags for len cells, zero past the last cell.
 __global__ void k_leaf_flags(CellArrays c, int ncells, int *flag, const int *sz = nullptr, int len = 0);
-__global__ void k_leaf_compact(CellArrays c, int ncells, const int *ex, int *leaves, const int *sz = nullptr);
+__global__ void k_leaf_compact(CellArrays c, int ncells, const int *ex, int *leaves, const int *sz, int *pcell);
 
 // traverse.cu
 constexpr int kSelNB = 128;  // count buckets of the hybrid selection table
@@ -196,11 +196,12 @@ void launch_shift_batched(bool l2l, const CellArrays &c, int a, int b, const flo
 constexpr int kFp64TopP = 12, kFp64TopLevels = 3;  // p >= 12: parents at levels 0..2
 void launch_shift_fp64(bool l2l, const CellArrays &c, int a, int b, const double *mats, int P2, int P2pad, float *E,
                        cudaStream_t st, const int *sz = nullptr, int level = 0, int cap = 0);
-// L2P, one warp (32-thread block) per leaf, as launch_p2m.
-void launch_l2p(const CellArrays &c, const int *leaves, int nleaves, unsigned grid, const float4 *pts, int p,
-                int P2pad, const float *L, float4 *far, cudaStream_t st, const int *sz = nullptr);
-// Dynamic shared memory of k_l2p: one 32-byte record per term (n, m), m <= n <= p,
-// then the leaf's P2pad coefficients.
+// L2P, particle-parallel: warps of 32 consecutive sorted particles, pcell[i] =
+// the leaf of sorted particle i (k_leaf_compact), n particles.
+void launch_l2p(const CellArrays &c, const int *pcell, int64_t n, const float4 *pts, int p, int P2pad,
+                const float *L, float4 *far, cudaStream_t st);
+// Shared memory of one leaf's L2P records: one 32-byte record per term (n, m),
+// m <= n <= p, then the leaf's P2pad coefficients.
 inline size_t l2p_smem(int p, int P2pad) { return (size_t)(p + 1) * (p + 2) / 2 * 32 + (size_t)P2pad * 4; }
 // P2L: one warp (block) per target cell with a P2L list; the source particles are
 // added to the cell's local expansion.  Dynamic shared memory 32 (P2pad + 1) floats.

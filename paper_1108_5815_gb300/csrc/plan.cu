@@ -104,7 +104,7 @@ void enqueue_plan(const PlanShape &s, const PlanBuffers &b, cudaStream_t st, cud
     k_leaf_flags<<<blocks_for(s.cell_cap, 256), 256, 0, st>>>(c, 0, b.leaf_flag, b.sz, s.cell_cap);
     FMM_LAUNCH_CHECK();
     scan_exclusive<int>(b.leaf_flag, b.leaf_ex, s.cell_cap, b.leaf_ex + s.cell_cap, b.scan_i32, st);
-    k_leaf_compact<<<blocks_for(s.cell_cap, 256), 256, 0, st>>>(c, 0, b.leaf_ex, b.leaves, b.sz);
+    k_leaf_compact<<<blocks_for(s.cell_cap, 256), 256, 0, st>>>(c, 0, b.leaf_ex, b.leaves, b.sz, b.pcell);
     FMM_LAUNCH_CHECK();
     FMM_CUDA_TRY(cudaMemcpyAsync(b.sz + kSzLeaves, b.leaf_ex + s.cell_cap, sizeof(int), cudaMemcpyDeviceToDevice, st));
     k_cell_geom<<<grid_stride(s.cell_cap), 256, 0, st>>>(c, 0, b.box, b.sz);
@@ -205,7 +205,7 @@ void enqueue_plan(const PlanShape &s, const PlanBuffers &b, cudaStream_t st, cud
         else
             launch_shift_batched(true, c, 0, 0, b.l2l, P2, P2pad, b.Lx, nullptr, fs, b.sz, l, s.level_cap[l]);
     }
-    launch_l2p(c, b.leaves, 0, (unsigned)std::max(1, s.leaf_cap), b.pts, p, P2pad, b.Lx, b.far, fs, b.sz);
+    launch_l2p(c, b.pcell, s.N, b.pts, p, P2pad, b.Lx, b.far, fs);
     if (s.hybrid) {
         k_m2p<<<blocks_for(s.leaf_cap, kM2PWarps), 32 * kM2PWarps, m2p_smem(p, P2pad), fs>>>(
             c, L, b.leaves, 0, b.pts, b.box, p, P2pad, b.M, b.far, b.sz);

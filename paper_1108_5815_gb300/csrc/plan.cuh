@@ -49,6 +49,7 @@ struct PlanBuffers {
     int *bstart = nullptr;
     int64_t *packed = nullptr, *packed_ex = nullptr, *scan_i64 = nullptr;
     int *leaf_flag = nullptr, *leaf_ex = nullptr, *scan_i32 = nullptr, *leaves = nullptr;
+    int *pcell = nullptr;  // the leaf of each sorted particle (L2P)
     ListArrays L{};
     uint64_t *hash_keys = nullptr;
     unsigned long long *tcount = nullptr, *totals = nullptr;

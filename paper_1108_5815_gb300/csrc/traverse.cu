@@ -36,7 +36,7 @@ constexpr int kP2PFlag = 1 << 30;  // deferred source that is a chosen P2P pair
 constexpr int kM2PFlag = 1 << 29;  // deferred source that is a chosen M2P pair
 constexpr int kCellMask = kM2PFlag - 1;
 constexpr int kFrontier = 512;  // sources of a leaf target split warp-wide before the walks
-constexpr int kCountCache = 128;  // sources whose counts the write pass reuses
+constexpr int kCountCache = 32;  // sources whose counts the write pass reuses
 
 struct TargetInfo {
     int t, level;
@@ -328,7 +328,7 @@ __device__ __forceinline__ void write_single_pairs(const TargetInfo &T, const in
 // the levels; a list whose reservation passes its capacity is not written for the
 // target (its count becomes 0) and the host repeats the traversal with larger
 // buffers.
-__global__ void __launch_bounds__(128, 6)
+__global__ void __launch_bounds__(128, 7)
     k_traverse_level(CellArrays c, ListArrays L, int a, int b, double theta2, float theta2f,
                      const uint8_t *__restrict__ sel, unsigned long long *__restrict__ counters,
                      int64_t cap_m, int64_t cap_p, int64_t cap_d, int64_t cap_q, int64_t cap_l,

@@ -683,11 +683,14 @@ __global__ void k_leaf_flags(CellArrays c, int ncells, int *__restrict__ flag, c
 }
 
 __global__ void k_leaf_compact(CellArrays c, int ncells, const int *__restrict__ ex,
-                               int *__restrict__ leaves, const int *__restrict__ sz)
+                               int *__restrict__ leaves, const int *__restrict__ sz, int *__restrict__ pcell)
 {
     if (sz) ncells = sz[kSzCells];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < ncells && c.nchild[i] == 0) leaves[ex[i]] = i;
+    if (i < ncells && c.nchild[i] == 0) {
+        leaves[ex[i]] = i;
+        for (int j = c.begin[i], e = c.end[i]; j < e; ++j) pcell[j] = i;  // the leaf of each sorted particle
+    }
 }
 
 }  // namespace fmm

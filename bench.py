@@ -696,6 +696,20 @@ def main():
         flush.fill_(float(k))
         st_list.append(solve(stats=True)[2])
     torch.cuda.synchronize()
+    # the timed solve replays the plan the library captured from the warm-up
+    # calls (fmm_options.replay); the same solve without it, for comparison
+    plain_ms = []
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        solve(replay=False)
+        b.record(stream)
+        b.synchronize()
+        plain_ms.append(a.elapsed_time(b))
+    plain = {"ms_per_step": statistics.mean(plain_ms), "value": n / (statistics.mean(plain_ms) / 1e3),
+             "what": "the same solve with fmm_options.replay = 0: every call launches its kernels from the "
+                     "host, with read-backs of the sizes between phases"}
     # each rank solved its own replica: job time = slowest rank, work = all ranks
     total_ms, _, value = replicas.aggregate(sum(step_ms), n * args.steps, device=dev)
     ms_per_step = total_ms / args.steps
@@ -858,7 +872,7 @@ def main():
             b.synchronize()
             ms.append(a.elapsed_time(b))
         status = plan.check()
-        solve()
+        solve(replay=False)  # the plain solve, for the bit-for-bit comparison
         torch.cuda.synchronize()
         info = plan.info()
         m = statistics.mean(ms)
@@ -916,7 +930,13 @@ def main():
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": config_of(w, args), "roofline": roof, "rooflines": rooflines,
                 "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": int(sum(s["n_launches"] for s in st_list)),
+                "gpu_launches": (args.steps * graph["graph_kernels"] if graph is not None
+                                 else int(sum(s["n_launches"] for s in st_list))),
+                "solve_path": ("fmm_laplace3d_ex with fmm_options.replay = 1 (the default): from the third "
+                               "call of one key on, each call replays the plan captured after the second -- "
+                               "every step of the solve in one graph launch, results bit-identical to the "
+                               "plain solve (graph_replay.equal_to_plain_solve)"),
+                "plain_solve": plain,
                 "accuracy": acc, "m2l_modes": modes, "select_modes": select_modes,
                 "cost_model": cost_model, "ncrit_tuning": ncrit_tuning, "per_system_loop": loop,
                 "graph_replay": graph, "solve_roofline_fraction": solve_frac, "peaks": pk,

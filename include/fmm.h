@@ -100,6 +100,18 @@ typedef struct {
      * waits until P2P has finished, so that each phase's time in fmm_stats is
      * that phase alone (slower; for measurements).  Plans ignore it. */
     int serialize_phases;
+    /* 1 (default): a solve without statistics and without serialize_phases whose
+     * key -- N, the system offsets, p, theta, ncrit, max_depth, precision_mode,
+     * select_mode, m2l_unit_blocks and the selection table's content -- equals
+     * the previous such call's on this device captures a plan after it solves
+     * (as fmm_plan_create, capacities 1.25x this solve's), and later calls with
+     * that key replay it: every step of the solve still runs, in one graph
+     * launch with every size on the device, and the results are bit-identical
+     * to a plain solve.  A replay that outgrows the plan is solved again plainly
+     * and the plan is dropped.  The plan's memory stays allocated until a call
+     * with another key captures its own.  The first two calls with a key are
+     * plain solves; the second also captures.  0: always a plain solve. */
+    int replay;
 } fmm_options;
 
 typedef struct {
@@ -122,7 +134,7 @@ typedef struct {
 } fmm_stats;
 
 /* Fills *opt with the defaults (max_depth 21, FP32 M2L, plain FMM, deterministic,
- * phases overlapped). */
+ * phases overlapped, repeated solves replayed). */
 void fmm_default_options(fmm_options *opt);
 
 /* The FMM solve.  Arguments must satisfy N >= 1, 1 <= p <= 20, 0 < theta < 1,

@@ -109,6 +109,25 @@ struct Workspace {
     cudaStream_t main_stream = nullptr, far_stream = nullptr;
     cudaEvent_t ev_in = nullptr, ev_tree = nullptr, ev_fork = nullptr, ev_join = nullptr, ev_out = nullptr,
                 ev_read = nullptr;
+    // Repeated solves (fmm_options.replay): what a solve depends on besides the
+    // particle data, the plan captured when a solve repeated its predecessor's
+    // key, and that predecessor's key.
+    struct ReplayKey {
+        int64_t N = 0;
+        int nsys = 0, p = 0, ncrit = 0, max_depth = 0, precision = 0, select_mode = 0, unit_blocks = 0;
+        double theta = 0.0;
+        std::vector<int64_t> off;  // system offsets (batched)
+        std::vector<uint8_t> sel;  // the selection table's content (empty: plain FMM)
+        bool operator==(const ReplayKey &k) const
+        {
+            return N == k.N && nsys == k.nsys && p == k.p && ncrit == k.ncrit && max_depth == k.max_depth &&
+                   precision == k.precision && select_mode == k.select_mode && unit_blocks == k.unit_blocks &&
+                   theta == k.theta && off == k.off && sel == k.sel;
+        }
+    };
+    fmm_plan *replay_plan = nullptr;
+    ReplayKey replay_key, last_key;
+    bool have_last = false;
 };
 
 std::mutex g_ws_mu;
@@ -1223,9 +1242,11 @@ struct fmm_plan {
     cudaEvent_t tree = nullptr, fork = nullptr, join = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    int *hcheck = nullptr;  // pinned: the flags and sizes read back by a check
     ~fmm_plan()
     {
         if (st) cudaStreamSynchronize(st);
+        if (hcheck) cudaFreeHost(hcheck);
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
         if (tree) cudaEventDestroy(tree);
@@ -1425,6 +1446,108 @@ void build_plan(fmm_plan &pl, Workspace &ws, const int64_t *offsets, const uint8
     FMM_CUDA_TRY(cudaGraphInstantiate(&pl.exec, pl.graph, 0));
 }
 
+// One replay of a plan on `stream`: the inputs copied into the plan (unless they
+// are its own buffers), one graph launch, the results copied out.
+void plan_execute(fmm_plan &pl, const float *xyz, const float *q, float *phi, float *grad, cudaStream_t st)
+{
+    const size_t n = (size_t)pl.s.N;
+    if (xyz && xyz != pl.xyz)
+        FMM_CUDA_TRY(cudaMemcpyAsync(pl.xyz, xyz, sizeof(float) * 3 * n, cudaMemcpyDeviceToDevice, st));
+    if (q && q != pl.q) FMM_CUDA_TRY(cudaMemcpyAsync(pl.q, q, sizeof(float) * n, cudaMemcpyDeviceToDevice, st));
+    FMM_CUDA_TRY(cudaGraphLaunch(pl.exec, st));
+    if (phi && phi != pl.phi)
+        FMM_CUDA_TRY(cudaMemcpyAsync(phi, pl.phi, sizeof(float) * n, cudaMemcpyDeviceToDevice, st));
+    if (grad && grad != pl.grad)
+        FMM_CUDA_TRY(cudaMemcpyAsync(grad, pl.grad, sizeof(float) * 3 * n, cudaMemcpyDeviceToDevice, st));
+}
+
+// Waits for `stream` and raises what the last replay's flags report.
+void plan_check(fmm_plan &pl, cudaStream_t st)
+{
+    // both read-backs queued behind the replay, then one wait
+    if (!pl.hcheck) FMM_CUDA_TRY(cudaMallocHost(&pl.hcheck, sizeof(int) * (kNumFlags + kSzWords)));
+    FMM_CUDA_TRY(cudaMemcpyAsync(pl.hcheck, pl.b.flags, sizeof(int) * kNumFlags, cudaMemcpyDeviceToHost, st));
+    FMM_CUDA_TRY(cudaMemcpyAsync(pl.hcheck + kNumFlags, pl.b.sz, sizeof(int) * kSzWords, cudaMemcpyDeviceToHost, st));
+    FMM_CUDA_TRY(cudaStreamSynchronize(st));
+    const int *f = pl.hcheck, *sz = pl.hcheck + kNumFlags;
+    if (f[kFlagNonfinite]) throw Error{FMM_ERR_NONFINITE, "a coordinate is NaN or infinite"};
+    if (f[kFlagTimeout]) throw Error{FMM_ERR_TIMEOUT, "a bounded device-side wait expired (M2L pipeline)"};
+    if (sz[kSzAbort] || f[kFlagHashFull] || f[kFlagClassRange] || f[kFlagStack])
+        throw Error{FMM_ERR_CAPACITY, "the replay exceeded a capacity of the plan or met an offset class it has "
+                                      "no operator for; its results are invalid (create a new plan)"};
+}
+
+// A plan captured from the workspace's last solve (its sizes, operators and
+// classes), with plan-owned particle and result buffers.
+fmm_plan *plan_from_last_solve(Workspace &ws, int64_t N, int nsys, const int64_t *off, int p, double theta,
+                               int ncrit, const fmm_options &o, const uint8_t *sel, double headroom)
+{
+    std::unique_ptr<fmm_plan> pl(new fmm_plan());
+    FMM_CUDA_TRY(cudaGetDevice(&pl->device));
+    pl->xyz = pl->mem.get<float>(3 * (size_t)N);
+    pl->q = pl->mem.get<float>((size_t)N);
+    pl->phi = pl->mem.get<float>((size_t)N);
+    pl->grad = pl->mem.get<float>(3 * (size_t)N);
+    pl->s = plan_shape(ws, N, nsys, p, theta, ncrit, o, sel != nullptr, headroom);
+    build_plan(*pl, ws, off, sel);
+    return pl.release();
+}
+
+// The solve behind the public entry points (device arrays, the workspace
+// locked).  With fmm_options.replay and no statistics: a call whose key (sizes,
+// order, MAC, options, system offsets, selection table) equals the previous
+// call's captures a plan after solving, and later calls with that key replay
+// it -- one graph launch, every size on the device, the same arithmetic, so the
+// same bits as a plain solve.  A replay that outgrows the plan's capacities (or
+// meets an offset class it holds no operator for) is solved again plainly and
+// the plan is dropped.
+void solve_api(Workspace &ws, const float *xyz, const float *q, int64_t N, int nsys, const int64_t *off, int p,
+               double theta, int ncrit, float *phi, float *grad, cudaStream_t stream, const fmm_options &o,
+               fmm_stats *stats, const uint8_t *sel)
+{
+    if (!o.replay || stats || o.serialize_phases) {
+        solve_locked(ws, xyz, q, N, nsys, off, p, theta, ncrit, phi, grad, stream, o, stats, sel);
+        return;
+    }
+    Workspace::ReplayKey key;
+    key.N = N;
+    key.nsys = nsys;
+    key.p = p;
+    key.ncrit = ncrit;
+    key.max_depth = o.max_depth;
+    key.precision = o.precision_mode;
+    key.select_mode = o.select_mode;
+    key.unit_blocks = o.m2l_unit_blocks;
+    key.theta = theta;
+    key.off.assign(off, off + nsys + 1);
+    if (sel) key.sel.assign(sel, sel + (size_t)kSelNB * kSelNB);
+    if (ws.replay_plan && ws.replay_key == key) {
+        try {
+            plan_execute(*ws.replay_plan, xyz, q, phi, grad, stream);
+            plan_check(*ws.replay_plan, stream);
+            return;
+        } catch (const Error &e) {
+            if (e.code != FMM_ERR_CAPACITY) throw;
+        }
+        delete ws.replay_plan;  // outgrown: solve plainly below
+        ws.replay_plan = nullptr;
+    }
+    solve_locked(ws, xyz, q, N, nsys, off, p, theta, ncrit, phi, grad, stream, o, nullptr, sel);
+    if (ws.have_last && ws.last_key == key && !(ws.replay_plan && ws.replay_key == key)) {
+        delete ws.replay_plan;
+        ws.replay_plan = nullptr;
+        try {
+            ws.replay_plan = plan_from_last_solve(ws, N, nsys, off, p, theta, ncrit, o, sel, 1.25);
+            ws.replay_key = key;
+        } catch (const Error &) {
+            // no plan for this key (the solve itself succeeded): later calls solve plainly
+            cudaGetLastError();
+        }
+    }
+    ws.last_key = std::move(key);
+    ws.have_last = true;
+}
+
 }  // namespace
 }  // namespace fmm
 
@@ -1442,6 +1565,7 @@ void fmm_default_options(fmm_options *opt)
     opt->select_table = nullptr;
     opt->m2l_unit_blocks = 0;
     opt->serialize_phases = 0;
+    opt->replay = 1;
 }
 
 fmm_status fmm_laplace3d_ex(const float *xyz, const float *q, int64_t N, int p, double theta,
@@ -1455,7 +1579,7 @@ fmm_status fmm_laplace3d_ex(const float *xyz, const float *q, int64_t N, int p, 
         std::lock_guard<std::mutex> lk(ws.mu);
         const uint8_t *sel = selection_table(ws, o, p, theta);
         const int64_t off[2] = {0, N};
-        solve_locked(ws, xyz, q, N, 1, off, p, theta, ncrit, phi, grad, (cudaStream_t)stream, o, stats, sel);
+        solve_api(ws, xyz, q, N, 1, off, p, theta, ncrit, phi, grad, (cudaStream_t)stream, o, stats, sel);
     });
 }
 
@@ -1483,7 +1607,7 @@ fmm_status fmm_laplace3d_host(const float *xyz_host, const float *q_host, int64_
         FMM_CUDA_TRY(cudaMemcpyAsync(xd, xyz_host, sizeof(float) * 3 * N, cudaMemcpyHostToDevice, st));
         FMM_CUDA_TRY(cudaMemcpyAsync(qd, q_host, sizeof(float) * N, cudaMemcpyHostToDevice, st));
         const int64_t off[2] = {0, N};
-        solve_locked(ws, xd, qd, N, 1, off, p, theta, ncrit, pd, gd, st, o, stats, sel);
+        solve_api(ws, xd, qd, N, 1, off, p, theta, ncrit, pd, gd, st, o, stats, sel);
         FMM_CUDA_TRY(cudaMemcpyAsync(phi_host, pd, sizeof(float) * N, cudaMemcpyDeviceToHost, st));
         FMM_CUDA_TRY(cudaMemcpyAsync(grad_host, gd, sizeof(float) * 3 * N, cudaMemcpyDeviceToHost, st));
         FMM_CUDA_TRY(cudaStreamSynchronize(st));
@@ -1505,7 +1629,7 @@ fmm_status fmm_laplace3d_batched(const float *xyz, const float *q, const int64_t
         Workspace &ws = workspace_for_current_device();
         std::lock_guard<std::mutex> lk(ws.mu);
         const uint8_t *sel = selection_table(ws, o, p, theta);
-        solve_locked(ws, xyz, q, N, nsys, offsets, p, theta, ncrit, phi, grad, (cudaStream_t)stream, o,
+        solve_api(ws, xyz, q, N, nsys, offsets, p, theta, ncrit, phi, grad, (cudaStream_t)stream, o,
                      stats, sel);
     });
 }
@@ -2058,16 +2182,7 @@ fmm_status fmm_plan_execute(fmm_plan *plan, const float *xyz, const float *q, fl
         int dev = 0;
         FMM_CUDA_TRY(cudaGetDevice(&dev));
         if (dev != plan->device) throw Error{FMM_ERR_ARG, "the plan belongs to another device"};
-        cudaStream_t st = (cudaStream_t)stream;
-        const size_t n = (size_t)plan->s.N;
-        if (xyz && xyz != plan->xyz)
-            FMM_CUDA_TRY(cudaMemcpyAsync(plan->xyz, xyz, sizeof(float) * 3 * n, cudaMemcpyDeviceToDevice, st));
-        if (q && q != plan->q) FMM_CUDA_TRY(cudaMemcpyAsync(plan->q, q, sizeof(float) * n, cudaMemcpyDeviceToDevice, st));
-        FMM_CUDA_TRY(cudaGraphLaunch(plan->exec, st));
-        if (phi && phi != plan->phi)
-            FMM_CUDA_TRY(cudaMemcpyAsync(phi, plan->phi, sizeof(float) * n, cudaMemcpyDeviceToDevice, st));
-        if (grad && grad != plan->grad)
-            FMM_CUDA_TRY(cudaMemcpyAsync(grad, plan->grad, sizeof(float) * 3 * n, cudaMemcpyDeviceToDevice, st));
+        plan_execute(*plan, xyz, q, phi, grad, (cudaStream_t)stream);
     });
 }
 
@@ -2075,15 +2190,7 @@ fmm_status fmm_plan_check(fmm_plan *plan, void *stream)
 {
     return guarded([&] {
         if (!plan) throw Error{FMM_ERR_ARG, "null plan"};
-        FMM_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
-        int f[kNumFlags], sz[kSzWords];
-        FMM_CUDA_TRY(cudaMemcpy(f, plan->b.flags, sizeof(f), cudaMemcpyDeviceToHost));
-        FMM_CUDA_TRY(cudaMemcpy(sz, plan->b.sz, sizeof(sz), cudaMemcpyDeviceToHost));
-        if (f[kFlagNonfinite]) throw Error{FMM_ERR_NONFINITE, "a coordinate is NaN or infinite"};
-        if (f[kFlagTimeout]) throw Error{FMM_ERR_TIMEOUT, "a bounded device-side wait expired (M2L pipeline)"};
-        if (sz[kSzAbort] || f[kFlagHashFull] || f[kFlagClassRange] || f[kFlagStack])
-            throw Error{FMM_ERR_CAPACITY, "the replay exceeded a capacity of the plan or met an offset class it has "
-                                          "no operator for; its results are invalid (create a new plan)"};
+        plan_check(*plan, (cudaStream_t)stream);
     });
 }
 

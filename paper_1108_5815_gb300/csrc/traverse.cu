@@ -37,6 +37,9 @@ constexpr int kM2PFlag = 1 << 29;  // deferred source that is a chosen M2P pair
 constexpr int kCellMask = kM2PFlag - 1;
 constexpr int kFrontier = 512;  // sources of a leaf target split warp-wide before the walks
 constexpr int kCountCache = 32;  // sources whose counts the write pass reuses
+// The single pair of a source that is not split (frontier, selection tables):
+// M2L, P2P, deferred as it is, M2P, P2L, or deferred with the P2P or M2P flag.
+enum { kOutM2L = 0, kOutP2P, kOutDef, kOutM2P, kOutP2L, kOutDefP2P, kOutDefM2P, kOutKinds };
 
 struct TargetInfo {
     int t, level;
@@ -320,6 +323,98 @@ __device__ __forceinline__ void write_single_pairs(const TargetInfo &T, const in
     }
 }
 
+// Writes the lists of target T whose ni sources E each give one pair, of the kind
+// recorded as code[k] = -1 - kind: the pairs, their order and the list offsets
+// that resolve() would give.
+__device__ __forceinline__ void write_kinds(const TargetInfo &T, const int *E, const int *code, int ni,
+                                            const CellArrays &c, const ListArrays &L,
+                                            unsigned long long *__restrict__ counters, int64_t cap_m, int64_t cap_p,
+                                            int64_t cap_d, int64_t cap_q, int64_t cap_l, uint64_t *hash_keys,
+                                            int *flags)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    auto list_of = [](int kind) {  // 0 M2L, 1 P2P, 2 deferred, 3 M2P, 4 P2L
+        return kind == kOutDefP2P || kind == kOutDefM2P ? 2 : kind;
+    };
+    int n[5] = {0, 0, 0, 0, 0};
+    for (int k0 = 0; k0 < ni; k0 += 32) {
+        const int k = k0 + lane;
+        const int li = k < ni ? list_of(-1 - code[k]) : -1;
+#pragma unroll
+        for (int j = 0; j < 5; ++j) n[j] += __popc(__ballot_sync(0xffffffffu, li == j));
+    }
+    unsigned long long o[5] = {0, 0, 0, 0, 0};
+    if (lane == 0) {
+        o[0] = atomicAdd(&counters[0], (unsigned long long)n[0]);
+        o[1] = atomicAdd(&counters[1], (unsigned long long)n[1]);
+        o[2] = atomicAdd(&counters[2], (unsigned long long)n[2]);
+        if (n[3]) o[3] = atomicAdd(&counters[3], (unsigned long long)n[3]);
+        if (n[4]) o[4] = atomicAdd(&counters[4], (unsigned long long)n[4]);
+    }
+#pragma unroll
+    for (int j = 0; j < 5; ++j) o[j] = __shfl_sync(0xffffffffu, o[j], 0);
+    const int64_t cap[5] = {cap_m, cap_p, cap_d, cap_q, cap_l};
+    bool fit[5];
+#pragma unroll
+    for (int j = 0; j < 5; ++j) fit[j] = (int64_t)(o[j] + n[j]) <= cap[j];
+    const int t = T.t;
+    if (lane == 0) {
+        L.m2l_off[t] = (int)o[0];
+        L.m2l_cnt[t] = fit[0] ? n[0] : 0;
+        L.p2p_off[t] = (int)o[1];
+        L.p2p_cnt[t] = fit[1] ? n[1] : 0;
+        L.def_off[t] = (int)o[2];
+        L.def_cnt[t] = fit[2] ? n[2] : 0;
+        L.m2p_off[t] = (int)o[3];
+        L.m2p_cnt[t] = fit[3] ? n[3] : 0;
+        L.p2l_off[t] = (int)o[4];
+        L.p2l_cnt[t] = fit[4] ? n[4] : 0;
+    }
+    int64_t run[5];
+#pragma unroll
+    for (int j = 0; j < 5; ++j) run[j] = (int64_t)o[j];
+    for (int k0 = 0; k0 < ni; k0 += 32) {
+        const int k = k0 + lane;
+        const int kind = k < ni ? -1 - code[k] : -1;
+        const int li = kind >= 0 ? list_of(kind) : -1;
+        int64_t pos = 0;
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+            const unsigned m = __ballot_sync(0xffffffffu, li == j);
+            if (li == j) pos = run[j] + __popc(m & lt);
+            run[j] += __popc(m);
+        }
+        if (li < 0 || !fit[li]) continue;
+        const int S = E[k];
+        switch (kind) {
+            case kOutM2L: {
+                int Cs[3], hs, ls;
+                cell_geom(c, S, Cs, hs, ls);
+                L.m2l_src[pos] = S;
+                L.m2l_tgt[pos] = t;
+                L.m2l_slot[pos] = hash_insert(hash_keys, class_key(T, ls, Cs, flags), flags);
+                break;
+            }
+            case kOutP2P:
+                L.p2p_src[pos] = S & kCellMask;
+                L.p2p_tgt[pos] = t;
+                break;
+            case kOutM2P:
+                L.m2p_src[pos] = S & kCellMask;
+                L.m2p_tgt[pos] = t;
+                break;
+            case kOutP2L:
+                L.p2l_src[pos] = S;
+                L.p2l_tgt[pos] = t;
+                break;
+            case kOutDefP2P: L.def_src[pos] = S | kP2PFlag; break;
+            case kOutDefM2P: L.def_src[pos] = S | kM2PFlag; break;
+            default: L.def_src[pos] = S; break;
+        }
+    }
+}
+
 }  // namespace
 
 // One warp per target of the level [a, b): count the outputs of all inherited
@@ -389,16 +484,29 @@ __global__ void __launch_bounds__(128, 7)
                     if (k < ni) {
                         const int S = E[k];
                         nc = 1;
+                        int kind = kOutDef;  // the source's single pair when it is not split
                         if (!(S & (kP2PFlag | kM2PFlag))) {
-                            int Cs[3], hs, ls;
-                            cell_geom(c, S, Cs, hs, ls);
+                            int Cs[3], hs, ls, bs;
+                            cell_geom(c, S, Cs, hs, ls, bs);
                             const int nch = c.nchild[S];
                             acc = mac_accept(T, Cs, hs, theta2, theta2f);
                             sp = !acc && nch > 0 && (T.leaf || ls < T.level);
                             one = !sp;
                             if (sp) nc = nch;
+                            if (acc) {
+                                const int kd = sel ? row[bs] : 0;  // as resolve()
+                                kind = kd == 3 ? kOutP2L
+                                       : kd != 0 && !T.leaf ? (kd == 1 ? kOutDefP2P : kOutDefM2P)
+                                       : kd == 1 ? kOutP2P
+                                       : kd == 2 ? kOutM2P
+                                                 : kOutM2L;
+                            } else if (T.leaf) {
+                                kind = kOutP2P;  // (a leaf source; others are split)
+                            }
+                        } else if (T.leaf) {
+                            kind = (S & kP2PFlag) ? kOutP2P : kOutM2P;  // a pair chosen at an ancestor
                         }
-                        nsplit[k] = sp ? nc : -1;
+                        nsplit[k] = sp ? nc : -1 - kind;
                     }
                     ma[r] = __ballot_sync(0xffffffffu, acc);
                     mo[r] = __ballot_sync(0xffffffffu, one && !acc);
@@ -410,6 +518,12 @@ __global__ void __launch_bounds__(128, 7)
             if (!any_split) {
                 if (!sel && single) {
                     write_single_pairs<R>(T, E, ni, ma, mo, c, L, counters, cap_m, cap_p, cap_d, hash_keys, flags);
+                    return;
+                }
+                if (sel) {  // with a selection table every source left gives one pair of its recorded kind
+                    __syncwarp();
+                    write_kinds(T, E, nsplit, ni, c, L, counters, cap_m, cap_p, cap_d, cap_q, cap_l, hash_keys,
+                                flags);
                     return;
                 }
                 break;

@@ -47,7 +47,7 @@ class Options(ctypes.Structure):
     _fields_ = [("max_depth", ctypes.c_int), ("precision_mode", ctypes.c_int),
                 ("select_mode", ctypes.c_int), ("deterministic", ctypes.c_int),
                 ("select_table", ctypes.c_void_p), ("m2l_unit_blocks", ctypes.c_int),
-                ("serialize_phases", ctypes.c_int)]
+                ("serialize_phases", ctypes.c_int), ("replay", ctypes.c_int)]
 
 
 class CostModelInfo(ctypes.Structure):
@@ -169,17 +169,20 @@ def _check(status: int):
         raise FmmError(status, last_error())
 
 
-def _options(max_depth=0, precision="fp32", select="plain", m2l_unit_blocks=0, serialize_phases=False):
+def _options(max_depth=0, precision="fp32", select="plain", m2l_unit_blocks=0, serialize_phases=False,
+             replay=True):
     """fmm_options for the call.  ``select`` is "plain", "autotune", "learned" or a
     uint8 [128, 128] selection table; the returned options keep the table alive.
     ``serialize_phases``: the far-field chain waits for P2P (phase times of the
-    statistics are then each phase alone)."""
+    statistics are then each phase alone).  ``replay``: repeated solves of one
+    key replay a captured plan (fmm_options.replay)."""
     o = Options()
     load().fmm_default_options(ctypes.byref(o))
     o.max_depth = max_depth
     o.precision_mode = PRECISION[precision]
     o.m2l_unit_blocks = m2l_unit_blocks
     o.serialize_phases = int(bool(serialize_phases))
+    o.replay = int(bool(replay))
     if isinstance(select, str):
         o.select_mode = SELECT[select]
         o._table = None
@@ -210,7 +213,7 @@ def _dev_f32(t, shape, name):
 
 def laplace3d(xyz, q, p: int, theta: float, ncrit: int, *, max_depth: int = 0,
               precision: str = "fp32", select="plain", m2l_unit_blocks: int = 0, stats: bool = False,
-              out=None, serialize_phases: bool = False):
+              out=None, serialize_phases: bool = False, replay: bool = True):
     """FMM potential and gradient for CUDA float32 xyz[N,3], q[N].
 
     Returns (phi[N], grad[N,3]) as CUDA tensors (and a stats dict if ``stats``)."""
@@ -224,7 +227,7 @@ def laplace3d(xyz, q, p: int, theta: float, ncrit: int, *, max_depth: int = 0,
             grad = torch.empty(n, 3, device=xyz.device, dtype=torch.float32)
         else:
             phi, grad = out
-        o = _options(max_depth, precision, select, m2l_unit_blocks, serialize_phases)
+        o = _options(max_depth, precision, select, m2l_unit_blocks, serialize_phases, replay)
         st = Stats()
         _check(load().fmm_laplace3d_ex(xyz.data_ptr(), q.data_ptr(), n, p, float(theta), ncrit,
                                        phi.data_ptr(), grad.data_ptr(), _stream_ptr(torch, xyz.device),
@@ -236,7 +239,7 @@ def laplace3d_host(xyz: np.ndarray, q: np.ndarray, p: int, theta: float, ncrit: 
                    max_depth: int = 0, precision: str = "fp32", select="plain", m2l_unit_blocks: int = 0,
                    stats: bool = False,
                    out=None,
-                   stream=None, serialize_phases: bool = False):
+                   stream=None, serialize_phases: bool = False, replay: bool = True):
     """Same solve with host (numpy) arrays: the library copies in and out."""
     xyz = np.ascontiguousarray(xyz, dtype=np.float32)
     q = np.ascontiguousarray(q, dtype=np.float32)
@@ -246,7 +249,7 @@ def laplace3d_host(xyz: np.ndarray, q: np.ndarray, p: int, theta: float, ncrit: 
         grad = np.empty((n, 3), dtype=np.float32)
     else:
         phi, grad = out
-    o = _options(max_depth, precision, select, m2l_unit_blocks, serialize_phases)
+    o = _options(max_depth, precision, select, m2l_unit_blocks, serialize_phases, replay)
     st = Stats()
     _check(load().fmm_laplace3d_host(xyz.ctypes.data, q.ctypes.data, n, p, float(theta), ncrit,
                                      phi.ctypes.data, grad.ctypes.data,
@@ -257,7 +260,7 @@ def laplace3d_host(xyz: np.ndarray, q: np.ndarray, p: int, theta: float, ncrit: 
 
 def laplace3d_batched(xyz, q, offsets, p: int, theta: float, ncrit: int, *, max_depth: int = 0,
                       precision: str = "fp32", select="plain", m2l_unit_blocks: int = 0, stats: bool = False,
-                      out=None, serialize_phases: bool = False):
+                      out=None, serialize_phases: bool = False, replay: bool = True):
     """Independent systems in one solve: system s = rows offsets[s]:offsets[s+1] of
     the CUDA float32 xyz[N,3], q[N]; offsets is a host int sequence (len nsys + 1)."""
     import torch
@@ -273,7 +276,7 @@ def laplace3d_batched(xyz, q, offsets, p: int, theta: float, ncrit: int, *, max_
             grad = torch.empty(n, 3, device=xyz.device, dtype=torch.float32)
         else:
             phi, grad = out
-        o = _options(max_depth, precision, select, m2l_unit_blocks, serialize_phases)
+        o = _options(max_depth, precision, select, m2l_unit_blocks, serialize_phases, replay)
         st = Stats()
         _check(load().fmm_laplace3d_batched(xyz.data_ptr(), q.data_ptr(), off.ctypes.data,
                                             len(off) - 1, p, float(theta), ncrit, phi.data_ptr(),

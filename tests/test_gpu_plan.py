@@ -32,7 +32,7 @@ def _dev(x, q):
 def _plain(xt, qt, p, theta, ncrit, **kw):
     from paper_1108_5815_gb300 import fmm
     torch = torch_cuda()
-    phi, grad = fmm.laplace3d(xt, qt, p, theta, ncrit, **kw)
+    phi, grad = fmm.laplace3d(xt, qt, p, theta, ncrit, replay=False, **kw)
     torch.cuda.synchronize()
     return phi.cpu().numpy(), grad.cpu().numpy()
 
@@ -99,7 +99,7 @@ def test_batched_plan():
     off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
     xt, qt = _dev(x, q)
     p, theta, ncrit = 5, 0.5, 16
-    phi0, grad0 = fmm.laplace3d_batched(xt, qt, off, p, theta, ncrit)
+    phi0, grad0 = fmm.laplace3d_batched(xt, qt, off, p, theta, ncrit, replay=False)
     torch.cuda.synchronize()
     plan = fmm.Plan(xt, qt, p, theta, ncrit, offsets=off)
     status, phi1, grad1 = _replay(plan)

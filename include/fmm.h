@@ -338,16 +338,19 @@ fmm_status fmm_morton_sort_noalloc(const float *xyz, int64_t N, uint64_t *keys, 
 /* N_crit from the learned cost model (the paper's section "Results" balances
  * the near and far fields through N_crit; the library's network takes that
  * choice without timing the candidates).  For each candidate the library builds
- * the tree and the interaction lists of the system (with the options'
- * selection mode; no expansion is evaluated and the candidate is not timed),
- * bins the P2P pairs by the count buckets of the selection table, and sums the
- * network's predicted time per pair over the bins, the number of M2L pairs
- * times its predicted M2L time per pair, and the number of cells times a
- * measured time per cell.  That last term is the part of a solve that grows as
- * N_crit shrinks: tree levels, traversal, upward and downward passes, class and
- * tile building.  It is the slope of the time outside the P2P and M2L kernels
- * over the cell count between two solves of an artificial 2^18-particle cube
- * at N_crit 16 and 64, measured once per (p, theta, precision) and device.
+ * the tree, the interaction lists, the offset classes and the M2L tiles of the
+ * system (with the options' selection mode; no operator is built, no expansion
+ * is evaluated and the candidate is not timed), bins the P2P pairs by the count
+ * buckets of the selection table, and sums the network's predicted time per
+ * pair over the bins, the number of (tile, class) M2L blocks times a measured
+ * time per block, and the number of cells times a measured time per cell.  The
+ * cell term is the part of a solve that grows as N_crit shrinks: tree levels,
+ * traversal, upward and downward passes, class and tile building.  Both are
+ * measured once per (p, theta, precision) and device on an artificial Plummer
+ * sphere of 2^20 particles solved at N_crit 32 and 128: the M2L kernel's time
+ * over its blocks, and the slope of the time outside the P2P and M2L kernels
+ * over the cell count.  The network's P2P sum is scaled so that it equals the
+ * P2P kernel's measured time on those two solves.
  * pred_ms[k] (may be NULL) receives candidate k's prediction in ms and *best
  * the candidate with the smallest one.  The measured autotuner (fmm_tune_ncrit)
  * remains the fallback and the judge.  Needs a trained or set model (else

@@ -49,6 +49,27 @@ __global__ void k_synth_uniform(float *__restrict__ xyz, float *__restrict__ q, 
     }
 }
 
+// Points of a Plummer sphere of scale 1, cut at radius 20 through the mass
+// fraction (M(r) = r^3 / (1 + r^2)^(3/2), M(20) = 0.9963): r from the fraction m
+// as 1 / sqrt(m^(-2/3) - 1), the direction uniform on the sphere; charges 1/n.
+__global__ void k_synth_plummer(float *__restrict__ xyz, float *__restrict__ q, int64_t n, uint64_t seed)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t b = seed + 4 * (uint64_t)i;
+        const float m = fmaxf(0.9963f * unit(splitmix(b)), 1e-6f);
+        const float r = rsqrtf(powf(m, -2.f / 3.f) - 1.f);
+        const float z = 2.f * unit(splitmix(b + 1)) - 1.f;
+        const float ph = 6.2831853f * unit(splitmix(b + 2));
+        const float sxy = sqrtf(fmaxf(0.f, 1.f - z * z));
+        float sp, cp;
+        sincosf(ph, &sp, &cp);
+        xyz[3 * i] = r * sxy * cp;
+        xyz[3 * i + 1] = r * sxy * sp;
+        xyz[3 * i + 2] = r * z;
+        q[i] = 1.f / (float)n;
+    }
+}
+
 // nL target leaves of nt particles, nS source cells of ns particles; leaf t
 // lists K sources spread over the source cells.
 __global__ void k_synth_lists(int nL, int nt, int nS, int ns, int K, int *__restrict__ begin,
@@ -348,6 +369,12 @@ void table_from_timings(const std::vector<P2PTiming> &grid, double m2l_ns, const
             sel[bt * kSelNB + bs] = kind;
         }
     }
+}
+
+void synth_plummer(float *xyz, float *q, int64_t n, uint64_t seed, cudaStream_t st)
+{
+    k_synth_plummer<<<1024, 256, 0, st>>>(xyz, q, n, seed);
+    FMM_LAUNCH_CHECK();
 }
 
 void synth_uniform(float *xyz, float *q, int64_t n, uint64_t seed, cudaStream_t st)

@@ -50,6 +50,8 @@ void model_table(CostModel &cm, int p, double theta, uint8_t *sel, cudaStream_t 
 
 // Artificial uniform particles in the unit cube, charges in [-1, 1) (SplitMix64).
 void synth_uniform(float *xyz, float *q, int64_t n, uint64_t seed, cudaStream_t st);
+// n points of a Plummer sphere (scale 1, radius <= 20), charges 1/n.
+void synth_plummer(float *xyz, float *q, int64_t n, uint64_t seed, cudaStream_t st);
 
 // Host-side SplitMix64 (Steele, Lea & Flood 2014) for sample features.
 struct SplitMix64 {

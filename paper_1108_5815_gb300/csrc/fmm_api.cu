@@ -62,6 +62,15 @@ struct Buf {
     size_t bytes = 0;
 };
 
+// Calibration of the N_crit pick (solve_calibration): ns per cell and per M2L
+// (tile, class) block, and for each calibration solve its P2P kernel time and its
+// P2P pairs binned by count bucket (to scale the network's P2P prediction).
+struct SolveCal {
+    double ns_cell = 0.0, ns_block = 0.0, ns_fixed = 0.0;  // slopes, and the lines' intercepts
+    double p2p_ns[2] = {0.0, 0.0};
+    std::vector<unsigned long long> hist[2];
+};
+
 struct Workspace {
     int device = 0;
     std::mutex mu;
@@ -96,7 +105,7 @@ struct Workspace {
     // hybrid selection: pre-timed kernels and the learned model
     std::vector<P2PTiming> p2p_grid;                      // P2P time per pair on artificial leaves
     std::map<std::tuple<int, uint64_t, int>, double> m2l_ns;  // (p, theta bits, precision) -> ns per pair
-    std::map<std::tuple<int, uint64_t, int>, double> cell_ns;  // (p, theta bits, precision) -> ns per cell
+    std::map<std::tuple<int, uint64_t, int>, SolveCal> cell_ns;  // (p, theta bits, precision) -> calibration
     std::map<int, std::vector<double>> m2p_ns;                // p -> ns per pair for kSelCounts
     std::map<int, std::vector<double>> p2l_ns;                // p -> ns per pair for kSelCounts
     std::map<std::tuple<int, uint64_t, int, int>, std::vector<uint8_t>> tables;  // (mode, theta, p, prec)
@@ -345,12 +354,16 @@ void validate(const void *xyz, const void *q, int64_t N, int p, double theta, in
 
 // The solve on device buffers; the caller holds ws.mu.
 // lists_only: stop after the traversal (the tree, the leaves and the interaction
-// lists stay in the workspace; phi and grad are not written).
+// lists stay in the workspace; phi and grad are not written).  blocks_only: go on
+// to the offset classes and the M2L tiles and stop once the number of (tile,
+// class) blocks is known (ws.shape.nent); no operator is built, nothing is
+// evaluated.
 void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, int nsys,
                   const int64_t *offsets, int p, double theta, int ncrit, float *phi, float *grad,
                   cudaStream_t caller, const fmm_options &o, fmm_stats *stats, const uint8_t *sel,
-                  bool lists_only = false)
+                  bool lists_only = false, bool blocks_only = false)
 {
+    const bool no_eval = lists_only || blocks_only;
     ensure_streams(ws);
     init_recurrence_tables();
     cudaStream_t st = ws.main_stream;
@@ -576,7 +589,7 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
     // traversal runs on the main stream.
     cudaStream_t fs = ws.far_stream;
     float *M = nullptr, *Lx = nullptr;
-    if (!lists_only) {
+    if (!no_eval) {
         FMM_CUDA_TRY(cudaEventRecord(ws.ev_tree, st));
         FMM_CUDA_TRY(cudaStreamWaitEvent(fs, ws.ev_tree, 0));
         if (ws.cache_p != p) {
@@ -649,8 +662,8 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
     L.p2l_cnt = need<int>(ws, "p2l_cnt", ncells, st);
     int64_t m2p_cap = std::max<int64_t>(ws.cap_m2p, 4096), p2l_cap = std::max<int64_t>(ws.cap_p2l, 4096);
     int64_t m2l_total = 0, p2p_total = 0, m2p_total = 0, p2l_total = 0;
-    float4 *far = lists_only ? nullptr : need<float4>(ws, "far", N, st);
-    float4 *near = lists_only ? nullptr : need<float4>(ws, "near", N, st);
+    float4 *far = no_eval ? nullptr : need<float4>(ws, "far", N, st);
+    float4 *near = no_eval ? nullptr : need<float4>(ws, "near", N, st);
     for (int attempt = 0;; ++attempt) {
         L.m2p_src = need<int>(ws, "m2p_src", m2p_cap, st);
         L.m2p_tgt = need<int>(ws, "m2p_tgt", m2p_cap, st);
@@ -683,11 +696,13 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
             // again.)
             FMM_CUDA_TRY(cudaEventRecord(ws.ev_fork, st));
             FMM_CUDA_TRY(cudaStreamWaitEvent(fs, ws.ev_fork, 0));
-            set_carveout_once((const void *)k_p2p, cudaSharedmemCarveoutMaxShared);
-            ev.rec(8, st);
-            k_p2p<<<(unsigned)std::max(1, nleaves), 32, 0, st>>>(c, L, leaves, nleaves, pts, near);
-            FMM_LAUNCH_CHECK();
-            ev.rec(9, st);
+            if (!blocks_only) {
+                set_carveout_once((const void *)k_p2p, cudaSharedmemCarveoutMaxShared);
+                ev.rec(8, st);
+                k_p2p<<<(unsigned)std::max(1, nleaves), 32, 0, st>>>(c, L, leaves, nleaves, pts, near);
+                FMM_LAUNCH_CHECK();
+                ev.rec(9, st);
+            }
         }
         read_end(ws, rb, tot);
         if ((int64_t)tot[0] <= m2l_cap && (int64_t)tot[1] <= p2p_cap && (int64_t)tot[2] <= def_cap &&
@@ -726,10 +741,9 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
     }
 
     // ---------------------------------------------------------- fork
-    // P2P needs only the leaf lists: it runs on the caller's stream while the
-    // far-field chain (classes, tiles, upward pass, M2L, downward pass) runs on
-    // the library's high-priority stream; the two join before the final sum.
-    // P2P (launched in the traversal loop above) runs on the caller's stream:
+    // P2P (launched in the traversal loop above) runs on the main stream while
+    // the far-field chain (classes, tiles, M2L, downward pass) runs on the
+    // library's high-priority stream; the two join before the final sum.  P2P:
     // one warp (block) per leaf with up to 128 registers a thread, 16 warps per
     // SM; the packed arithmetic keeps more interactions in flight than with more
     // warps of fewer registers (measured 1.68 ms at 80 registers and 24 warps,
@@ -780,35 +794,37 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
                 FMM_LAUNCH_CHECK();
             }
         }
-        std::vector<uint64_t> hkeys(nclass);
-        if (nclass > 0) sync_point(ws, fs, flags, {{ukeys, sizeof(uint64_t) * nclass}}, hkeys.data());
-        std::vector<int> cls_slot(nclass);
-        std::vector<uint64_t> new_keys;
-        std::vector<int> new_slots;
-        for (int i = 0; i < nclass; ++i) {
-            auto it = ws.class_cache.find(hkeys[i]);
-            if (it == ws.class_cache.end()) {
-                const int s = ws.table_slots++;
-                ws.class_cache.emplace(hkeys[i], s);
-                new_keys.push_back(hkeys[i]);
-                new_slots.push_back(s);
-                cls_slot[i] = s;
-            } else {
-                cls_slot[i] = it->second;
+        if (!blocks_only) {  // (the block count needs class indices, not operators)
+            std::vector<uint64_t> hkeys(nclass);
+            if (nclass > 0) sync_point(ws, fs, flags, {{ukeys, sizeof(uint64_t) * nclass}}, hkeys.data());
+            std::vector<int> cls_slot(nclass);
+            std::vector<uint64_t> new_keys;
+            std::vector<int> new_slots;
+            for (int i = 0; i < nclass; ++i) {
+                auto it = ws.class_cache.find(hkeys[i]);
+                if (it == ws.class_cache.end()) {
+                    const int s = ws.table_slots++;
+                    ws.class_cache.emplace(hkeys[i], s);
+                    new_keys.push_back(hkeys[i]);
+                    new_slots.push_back(s);
+                    cls_slot[i] = s;
+                } else {
+                    cls_slot[i] = it->second;
+                }
             }
-        }
-        need<float>(ws, "table", (size_t)std::max(ws.table_slots, 1) * P2pad * P2pad, fs, true);
-        int *class_slot = need<int>(ws, "class_slot", nclass, fs);
-        if (nclass > 0) upload(ws, class_slot, cls_slot.data(), sizeof(int) * nclass, fs);
-        if (!new_keys.empty()) {
-            const int nnew = (int)new_keys.size();
-            uint64_t *nk = need<uint64_t>(ws, "new_keys", nnew, fs);
-            int *ns = need<int>(ws, "new_slots", nnew, fs);
-            upload(ws, nk, new_keys.data(), sizeof(uint64_t) * nnew, fs);
-            upload(ws, ns, new_slots.data(), sizeof(int) * nnew, fs);
-            const size_t sh = sizeof(double) * 2 * (size_t)(2 * p + 1) * (2 * p + 2) / 2;
-            k_build_m2l_tables<<<nnew, 256, sh, fs>>>(nk, ns, nnew, p, P2pad, get<float>(ws, "table"));
-            FMM_LAUNCH_CHECK();
+            need<float>(ws, "table", (size_t)std::max(ws.table_slots, 1) * P2pad * P2pad, fs, true);
+            int *class_slot = need<int>(ws, "class_slot", nclass, fs);
+            if (nclass > 0) upload(ws, class_slot, cls_slot.data(), sizeof(int) * nclass, fs);
+            if (!new_keys.empty()) {
+                const int nnew = (int)new_keys.size();
+                uint64_t *nk = need<uint64_t>(ws, "new_keys", nnew, fs);
+                int *ns = need<int>(ws, "new_slots", nnew, fs);
+                upload(ws, nk, new_keys.data(), sizeof(uint64_t) * nnew, fs);
+                upload(ws, ns, new_slots.data(), sizeof(int) * nnew, fs);
+                const size_t sh = sizeof(double) * 2 * (size_t)(2 * p + 1) * (2 * p + 2) / 2;
+                k_build_m2l_tables<<<nnew, 256, sh, fs>>>(nk, ns, nnew, p, P2pad, get<float>(ws, "table"));
+                FMM_LAUNCH_CHECK();
+            }
         }
     }
 
@@ -842,6 +858,11 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
     ws.shape.ntiles = ntiles;
     ws.shape.nent = nent;
     ws.shape.nunits = 0;
+    if (blocks_only) {
+        FMM_CUDA_TRY(cudaEventRecord(ws.ev_out, fs));
+        FMM_CUDA_TRY(cudaStreamWaitEvent(caller, ws.ev_out, 0));
+        return;
+    }
     int *entry_class = need<int>(ws, "entry_class", nent, fs);
     int *src = need<int>(ws, "src", (size_t)nent * kTile, fs);
     FMM_CUDA_TRY(cudaMemsetAsync(src, 0xff, sizeof(int) * (size_t)nent * kTile, fs));
@@ -1027,43 +1048,71 @@ double m2l_ns_per_pair(Workspace &ws, int p, double theta, int prec)
     return best;
 }
 
-// Time per cell of the solve outside the P2P and M2L kernels (tree levels,
-// traversal, upward and downward passes, class and tile building), the part of
-// the cost that grows as N_crit shrinks: the slope of (total - P2P - M2L) over
-// the number of cells between two plain solves of the artificial 2^18-particle
-// cube at N_crit 16 and 64 (best of two repetitions each).
-double cell_ns_per_cell(Workspace &ws, int p, double theta, int prec)
+// The parts of a solve's time that the N_crit pick does not take from the
+// network, measured on an artificial clustered set (a Plummer sphere of 2^20
+// particles) at N_crit 32 and 256, the range of the usual candidates (best of
+// two repetitions each), each as a line through the two solves:
+//  * the M2L kernel's time against its (tile, class) blocks -- the kernel's work
+//    is per block, whatever the block's share of rows with a pair, so on a
+//    clustered set or at a large N_crit the time per pair grows;
+//  * the time outside the P2P and M2L kernels (tree levels, traversal, upward
+//    and downward passes, class and tile building) against the cells, the part
+//    that grows as N_crit shrinks.
+SolveCal solve_calibration(Workspace &ws, int p, double theta, int prec)
 {
     const auto key = std::make_tuple(p, (uint64_t)std::llround(theta * 1e9), prec);
     auto it = ws.cell_ns.find(key);
     if (it != ws.cell_ns.end()) return it->second;
     ensure_streams(ws);
     cudaStream_t st = ws.main_stream;
-    const int64_t n = 1 << 18;
+    const int64_t n = 1 << 20;
     float *xyz = need<float>(ws, "syn_xyz", 3 * n, st);
     float *q = need<float>(ws, "syn_q", n, st);
     float *phi = need<float>(ws, "syn_phi", n, st);
     float *grad = need<float>(ws, "syn_grad", 3 * n, st);
-    synth_uniform(xyz, q, n, 0x5eed0001ull, st);
+    synth_plummer(xyz, q, n, 0x5eed0005ull, st);
     fmm_options o;
     fmm_default_options(&o);
     o.precision_mode = prec;
     o.serialize_phases = 1;  // P2P and M2L each timed alone
     const int64_t off[2] = {0, n};
-    double rest[2] = {1e30, 1e30}, cells[2] = {0, 0};
-    const int ncs[2] = {16, 64};
-    for (int k = 0; k < 2; ++k)
+    double rest[2] = {1e30, 1e30}, m2l[2] = {1e30, 1e30}, cells[2] = {0, 0}, blocks[2] = {0, 0};
+    const int ncs[2] = {32, 256};
+    SolveCal c;
+    unsigned long long *hist = need<unsigned long long>(ws, "pick_hist", (size_t)kSelNB * kSelNB, st);
+    for (int k = 0; k < 2; ++k) {
+        c.p2p_ns[k] = 1e30;
         for (int rep = 0; rep < 3; ++rep) {
             fmm_stats s{};
             solve_locked(ws, xyz, q, n, 1, off, p, theta, ncs[k], phi, grad, st, o, &s, nullptr);
             if (rep == 0) continue;  // warm-up (operator tables, buffers)
             rest[k] = std::min(rest[k], (double)(s.ms_total - s.ms_p2p - s.ms_m2l) * 1e6);
+            m2l[k] = std::min(m2l[k], (double)s.ms_m2l * 1e6);
+            c.p2p_ns[k] = std::min(c.p2p_ns[k], (double)s.ms_p2p * 1e6);
             cells[k] = (double)s.ncells;
+            blocks[k] = (double)s.n_m2l_blocks;
         }
+        // this solve's P2P pairs by count bucket
+        const int64_t np2p = ws.shape.tot[1];
+        FMM_CUDA_TRY(cudaMemsetAsync(hist, 0, sizeof(unsigned long long) * kSelNB * kSelNB, st));
+        if (np2p > 0) {
+            k_pair_bucket_hist<<<grid_for(np2p, 256), 256, 0, st>>>(get<int>(ws, "p2p_tgt"), get<int>(ws, "p2p_src"),
+                                                                  np2p, get<int>(ws, "c_begin"), get<int>(ws, "c_end"),
+                                                                  hist);
+            FMM_LAUNCH_CHECK();
+        }
+        c.hist[k].resize((size_t)kSelNB * kSelNB);
+        FMM_CUDA_TRY(cudaMemcpyAsync(c.hist[k].data(), hist, sizeof(unsigned long long) * kSelNB * kSelNB,
+                                     cudaMemcpyDeviceToHost, st));
+        FMM_CUDA_TRY(cudaStreamSynchronize(st));
+    }
     ws.have_solve = false;
-    const double slope = cells[0] > cells[1] ? std::max(0.0, (rest[0] - rest[1]) / (cells[0] - cells[1])) : 0.0;
-    ws.cell_ns[key] = slope;
-    return slope;
+    // lines through the two solves (slopes kept >= 0)
+    c.ns_block = blocks[0] > blocks[1] ? std::max(0.0, (m2l[0] - m2l[1]) / (blocks[0] - blocks[1])) : 0.0;
+    c.ns_cell = cells[0] > cells[1] ? std::max(0.0, (rest[0] - rest[1]) / (cells[0] - cells[1])) : 0.0;
+    c.ns_fixed = std::max(0.0, m2l[1] - c.ns_block * blocks[1]) + std::max(0.0, rest[1] - c.ns_cell * cells[1]);
+    ws.cell_ns[key] = c;
+    return c;
 }
 
 const std::vector<int> kSelCounts = {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512};
@@ -2055,15 +2104,32 @@ fmm_status fmm_cost_model_pick_ncrit(const float *xyz, const float *q, int64_t N
         ensure_streams(ws);
         cudaStream_t cs = (cudaStream_t)stream, st = ws.main_stream;
         const uint8_t *sel = selection_table(ws, o, p, theta);
-        const double per_cell = cell_ns_per_cell(ws, p, theta, o.precision_mode);
+        const SolveCal cal = solve_calibration(ws, p, theta, o.precision_mode);
         const int64_t off[2] = {0, N};
         unsigned long long *hist = need<unsigned long long>(ws, "pick_hist", (size_t)kSelNB * kSelNB, st);
         double *cost = need<double>(ws, "pick_cost", 2, st);
+        // the network's P2P prediction is scaled to the P2P kernel's measured time
+        // on the calibration solves (the network gives how the time varies with
+        // the leaf sizes; the solves fix its scale in a real solve)
+        double net_cal = 0.0, meas_cal = 0.0;
+        for (int k = 0; k < 2; ++k) {
+            FMM_CUDA_TRY(cudaMemcpyAsync(hist, cal.hist[k].data(), sizeof(unsigned long long) * kSelNB * kSelNB,
+                                         cudaMemcpyHostToDevice, st));
+            k_mlp_solve_cost<<<1, 256, 0, st>>>(ws.cm.w16, (float)p, (float)(1.0 / theta), hist, 0ull, cost);
+            FMM_LAUNCH_CHECK();
+            double h[2];
+            FMM_CUDA_TRY(cudaMemcpyAsync(h, cost, sizeof(h), cudaMemcpyDeviceToHost, st));
+            FMM_CUDA_TRY(cudaStreamSynchronize(st));
+            net_cal += h[0];
+            meas_cal += cal.p2p_ns[k];
+        }
+        const double p2p_scale = net_cal > 0.0 ? meas_cal / net_cal : 1.0;
         double best_ns = 1e300;
         for (int k = 0; k < ncand; ++k) {
             // the candidate's tree and interaction lists (no evaluation), then the
             // network over them
-            solve_locked(ws, xyz, q, N, 1, off, p, theta, candidates[k], nullptr, nullptr, cs, o, nullptr, sel, true);
+            solve_locked(ws, xyz, q, N, 1, off, p, theta, candidates[k], nullptr, nullptr, cs, o, nullptr, sel, false,
+                         true);
             const int64_t np2p = ws.shape.tot[1], nm2l = ws.shape.tot[0];
             FMM_CUDA_TRY(cudaMemsetAsync(hist, 0, sizeof(unsigned long long) * kSelNB * kSelNB, st));
             if (np2p > 0) {
@@ -2078,7 +2144,9 @@ fmm_status fmm_cost_model_pick_ncrit(const float *xyz, const float *q, int64_t N
             double h[2];
             FMM_CUDA_TRY(cudaMemcpyAsync(h, cost, sizeof(h), cudaMemcpyDeviceToHost, st));
             FMM_CUDA_TRY(cudaStreamSynchronize(st));
-            const double ns = h[0] + h[1] + per_cell * (double)ws.shape.ncells;
+            // the network's P2P time (scaled), the calibrated M2L and per-cell times
+            const double ns = p2p_scale * h[0] + cal.ns_block * (double)ws.shape.nent +
+                              cal.ns_cell * (double)ws.shape.ncells + cal.ns_fixed;
             if (pred_ms) pred_ms[k] = (float)(ns * 1e-6);
             if (ns < best_ns) {
                 best_ns = ns;

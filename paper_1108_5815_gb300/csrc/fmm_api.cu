@@ -758,6 +758,28 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
         FMM_CUDA_TRY(cudaStreamWaitEvent(fs, ws.ev_fork, 0));
     }
 
+    // ---------------------------------------------------------- M2L tiles regrouped
+    // each level's cells ordered by octant, face distances and M2L count, and cut
+    // into tiles (k_tile_keys), for the tensor-core M2L, whose work units split a
+    // tile's class blocks: the CUDA-core M2L runs one block per tile, and tiles
+    // that gather the cells of most pairs would set its pace.  Enqueued before the
+    // class read-backs.
+    const bool tensor = o.precision_mode != FMM_PREC_FP32 && m2l_tc_supported(P2pad);
+    if (tensor) {
+        uint64_t *tkey = need<uint64_t>(ws, "tile_key", ncells, fs);
+        uint64_t *tkey_alt = need<uint64_t>(ws, "tile_key_alt", ncells, fs);
+        uint32_t *tval = need<uint32_t>(ws, "tile_val", ncells, fs);
+        uint32_t *tval_alt = need<uint32_t>(ws, "tile_val_alt", ncells, fs);
+        uint32_t *thist = need<uint32_t>(ws, "tile_hist", radix_scratch_elems(ncells), fs);
+        int *tlstart = need<int>(ws, "tile_lstart", (int)lstart.size(), fs);
+        upload(ws, tlstart, lstart.data(), sizeof(int) * lstart.size(), fs);
+        k_tile_keys<<<grid_for(ncells, 256), 256, 0, fs>>>(c, ncells, L.m2l_cnt, ncells, tkey, tval);
+        FMM_LAUNCH_CHECK();
+        radix_sort_pairs(tkey, tval, tkey_alt, tval_alt, ncells, kTileSortBits, thist, flags, fs);
+        k_tile_assign<<<grid_for(ncells, 256), 256, 0, fs>>>(tkey, tval, ncells, tlstart, tiles_total, c);
+        FMM_LAUNCH_CHECK();
+    }
+
     // ---------------------------------------------------------- offset classes
     int nclass = 0;
     {
@@ -878,7 +900,6 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
     }
 
     // ---------------------------------------------------------- M2L
-    const bool tensor = o.precision_mode != FMM_PREC_FP32 && m2l_tc_supported(P2pad);
     if (tensor) {
         // work units: (tile, contiguous run of its class blocks), about six per SM
         const int chunk = o.m2l_unit_blocks > 0 ? o.m2l_unit_blocks
@@ -1395,6 +1416,11 @@ void build_plan(fmm_plan &pl, Workspace &ws, const int64_t *offsets, const uint8
     b.slot_class = m.get<int>(kHashCap);
     b.class_slot = m.get<int>(s.nclass_cap);
     b.tile_cells = m.get<int>((size_t)s.tile_cap * kTile);
+    b.tile_key = m.get<uint64_t>(s.cell_cap);
+    b.tile_key_alt = m.get<uint64_t>(s.cell_cap);
+    b.tile_val = m.get<uint32_t>(s.cell_cap);
+    b.tile_val_alt = m.get<uint32_t>(s.cell_cap);
+    b.tile_hist = m.get<uint32_t>(radix_scratch_elems(s.cell_cap));
     b.bitmap = m.get<uint32_t>((size_t)s.tile_cap * s.nwords);
     b.tile_cnt = m.get<int>(s.tile_cap);
     b.entry_base = m.get<int>(s.tile_cap + 1);

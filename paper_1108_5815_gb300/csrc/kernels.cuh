@@ -116,6 +116,16 @@ __global__ void k_tree_small_levels(CellArrays c, const uint64_t *keys, const ui
                                     int ncrit, int max_depth, SmallLevels sl, int last_level, int cell_cap,
                                     int tile_cap, int *sz);
 __global__ void k_fill_tile_cells(CellArrays c, int ncells, int *tile_cells, const int *sz = nullptr);
+// M2L tiles regrouped by likeness of the targets' class sets (tree.cu): sort
+// keys of len cells (past the last cell: a key that sorts last), then, from the
+// stably sorted (key, cell) pairs, each cell's tile and lane.  lstart: first
+// cell of each level.  With sz: the cell count from sz, and kSzAbort on a tile
+// past tile_cap.
+__global__ void k_tile_keys(CellArrays c, int ncells, const int *m2l_cnt, int len, uint64_t *key, uint32_t *val,
+                            const int *sz = nullptr);
+__global__ void k_tile_assign(const uint64_t *key, const uint32_t *val, int ncells, const int *lstart, int tile_cap,
+                              CellArrays c, int *sz = nullptr);
+constexpr int kTileSortBits = 28;
 // c.geom of every cell from its level and key prefix (with sz: the cell count from sz).
 __global__ void k_cell_geom(CellArrays c, int ncells, const double *box, const int *sz = nullptr);
 // With sz: flags for len cells, zero past the last cell.

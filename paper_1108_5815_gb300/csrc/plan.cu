@@ -142,6 +142,18 @@ void enqueue_plan(const PlanShape &s, const PlanBuffers &b, cudaStream_t st, cud
     k_p2p<<<(unsigned)std::max(1, s.leaf_cap), 32, 0, st>>>(c, L, b.leaves, 0, b.pts, b.near, b.sz);
     FMM_LAUNCH_CHECK();
 
+    // ---------------------------------------------------------- M2L tiles regrouped (fs, tensor-core M2L)
+    if (s.tensor) {
+        k_tile_keys<<<grid_stride(s.cell_cap), 256, 0, fs>>>(c, 0, L.m2l_cnt, s.cell_cap, b.tile_key, b.tile_val,
+                                                             b.sz);
+        FMM_LAUNCH_CHECK();
+        radix_sort_pairs(b.tile_key, b.tile_val, b.tile_key_alt, b.tile_val_alt, s.cell_cap, kTileSortBits,
+                         b.tile_hist, b.flags, fs);
+        k_tile_assign<<<grid_stride(s.cell_cap), 256, 0, fs>>>(b.tile_key, b.tile_val, 0, b.sz + kSzLevel,
+                                                               s.tile_cap, c, b.sz);
+        FMM_LAUNCH_CHECK();
+    }
+
     // ---------------------------------------------------------- offset classes (fs)
     k_hash_flags<<<kHashCap / 256, 256, 0, fs>>>(b.hash_keys, b.hflag);
     FMM_LAUNCH_CHECK();

@@ -66,6 +66,8 @@ struct PlanBuffers {
     const float *table = nullptr;
     const unsigned char *tsplit = nullptr;
     int *tile_cells = nullptr, *tile_cnt = nullptr, *entry_base = nullptr, *word_prefix = nullptr;
+    uint64_t *tile_key = nullptr, *tile_key_alt = nullptr;  // the tile regrouping sort (cell_cap pairs)
+    uint32_t *tile_val = nullptr, *tile_val_alt = nullptr, *tile_hist = nullptr;
     int *entry_class = nullptr, *src = nullptr;
     uint32_t *bitmap = nullptr;
     M2LUnit *units = nullptr;

@@ -904,8 +904,11 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
         // work units: (tile, contiguous run of its class blocks), about six per SM
         const int chunk = o.m2l_unit_blocks > 0 ? o.m2l_unit_blocks
                                                 : std::max(8, (int)ceil_div(std::max(nent, 1), 6 * 152));
-        // units in execution order (rank within the tile, tile): resident CTAs then work on
-        // similar class ranges; tile_units lists each tile's units in class order for the sum
+        // units in execution order: the full ones by (rank within the tile, tile), so that
+        // resident CTAs work on similar class ranges, then each tile's shorter last unit by
+        // size class, longer first (an SM takes the next unit as it frees, and short units
+        // last even out the SMs' ends); tile_units lists each tile's units in class order
+        // for the sum
         std::vector<int> nut(ntiles), ubase(ntiles + 1, 0);
         int maxr = 0;
         for (int t = 0; t < ntiles; ++t) {
@@ -919,13 +922,21 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
         std::vector<M2LUnit> units;
         units.reserve(nunits);
         std::vector<int> tile_units(std::max(nunits, 1));
+        auto bucket = [&](int t, int r) {
+            const int n = std::min(chunk, h_eb[t + 1] - (h_eb[t] + r * chunk));
+            return n == chunk ? kUnitBuckets : n * kUnitBuckets / (chunk + 1);
+        };
+        auto place = [&](int t, int r) {
+            const int e = h_eb[t] + r * chunk;
+            tile_units[ubase[t] + r] = (int)units.size();
+            units.push_back({t, e, std::min(e + chunk, h_eb[t + 1]), 0});
+        };
         for (int r = 0; r < maxr; ++r)
-            for (int t = 0; t < ntiles; ++t) {
-                if (r >= nut[t]) continue;
-                const int e = h_eb[t] + r * chunk;
-                tile_units[ubase[t] + r] = (int)units.size();
-                units.push_back({t, e, std::min(e + chunk, h_eb[t + 1]), 0});
-            }
+            for (int t = 0; t < ntiles; ++t)
+                if (r < nut[t] && bucket(t, r) == kUnitBuckets) place(t, r);
+        for (int k = kUnitBuckets - 1; k >= 0; --k)
+            for (int t = 0; t < ntiles; ++t)
+                if (nut[t] > 0 && bucket(t, nut[t] - 1) == k) place(t, nut[t] - 1);
         M2LUnit *d_units = need<M2LUnit>(ws, "m2l_units", std::max(nunits, 1), fs);
         int *d_ubase = need<int>(ws, "m2l_ubase", ntiles + 1, fs);
         int *d_tunits = need<int>(ws, "m2l_tile_units", std::max(nunits, 1), fs);

@@ -241,8 +241,11 @@ void launch_m2l_tc(bool bf16, int nunits, const void *units, int ntiles, const i
                    const int *tile_units, const int *entry_class, const int *src, const int *tile_cells,
                    const float *M, const unsigned char *tsplit, int P2pad, float *partial, float *L,
                    int *flags, cudaStream_t st, const int *sz = nullptr);
-// Work units on the device (graph replay): per tile ceil(blocks / chunk) units,
-// ordered (rank within the tile, tile), as the host builds them; kSzAbort and
+// Work units: per tile ceil(blocks / chunk) units of chunk blocks, the last one
+// shorter.  Execution order: the full units by (rank within the tile, tile), then
+// the shorter last units by size class (kUnitBuckets classes, longer first).
+constexpr int kUnitBuckets = 8;
+// Work units on the device (graph replay), as the host builds them; kSzAbort and
 // no units when more than units_cap would be needed.  One block.
 __global__ void k_build_units(const int *entry_base, int ntiles_cap, int chunk, int units_cap, M2LUnit *units,
                               int *unit_base, int *tile_units, int *sz);

@@ -1167,9 +1167,13 @@ void launch_m2l_tc(bool bf16, int nunits, const void *units, int ntiles, const i
 
 // Work units of a replayed plan, built as the host builds them for a solve: tile
 // t has ceil(blocks_t / chunk) units, unit r of tile t covers its blocks
-// [eb_t + r chunk, min(eb_t + (r + 1) chunk, eb_{t+1})), and the units run in
-// the order (r, t).  One block: per rank r, a block-wide scan over the tiles
-// gives each unit of rank r its place.
+// [eb_t + r chunk, min(eb_t + (r + 1) chunk, eb_{t+1})).  The units of chunk
+// blocks run first in the order (r, t), then each tile's shorter last unit,
+// longer ones first (kUnitBuckets size classes, tile order within one): the
+// units are one CTA each and an SM takes the next as it frees, so short units
+// last even out the SMs' ends (longest-first list scheduling).  One block: per
+// rank r, then per size class, a block-wide scan over the tiles gives each unit
+// its place.
 __global__ void __launch_bounds__(1024)
     k_build_units(const int *__restrict__ entry_base, int ntiles_cap, int chunk, int units_cap,
                   M2LUnit *__restrict__ units, int *__restrict__ unit_base, int *__restrict__ tile_units,
@@ -1231,19 +1235,35 @@ __global__ void __launch_bounds__(1024)
     if (!fits) return;
     __syncthreads();
     const int R = s_maxr;
-    int done = 0;  // units of ranks below r
-    for (int r = 0; r < R; ++r) {
+    // size class of a unit: kUnitBuckets for a full one, else its size's class
+    auto bucket = [&](int t, int r) {
+        const int e0 = entry_base[t] + r * chunk;
+        const int n = min(chunk, entry_base[t + 1] - e0);
+        return n == chunk ? kUnitBuckets : n * kUnitBuckets / (chunk + 1);
+    };
+    auto place = [&](int t, int r, int &pos) {
+        const int e0 = entry_base[t] + r * chunk;
+        units[pos] = {t, e0, min(e0 + chunk, entry_base[t + 1]), 0};
+        tile_units[unit_base[t] + r] = pos;
+        ++pos;
+    };
+    int done = 0;  // units placed so far
+    for (int r = 0; r < R; ++r) {  // full units, rank by rank
         int cnt = 0;
-        for (int t = t0; t < t1; ++t) cnt += nut(t) > r;
+        for (int t = t0; t < t1; ++t) cnt += nut(t) > r && bucket(t, r) == kUnitBuckets;
         int total = 0;
         int pos = done + scan(cnt, total);
-        for (int t = t0; t < t1; ++t) {
-            if (nut(t) <= r) continue;
-            const int e0 = entry_base[t] + r * chunk;
-            units[pos] = {t, e0, min(e0 + chunk, entry_base[t + 1]), 0};
-            tile_units[unit_base[t] + r] = pos;
-            ++pos;
-        }
+        for (int t = t0; t < t1; ++t)
+            if (nut(t) > r && bucket(t, r) == kUnitBuckets) place(t, r, pos);
+        done += total;
+    }
+    for (int k = kUnitBuckets - 1; k >= 0; --k) {  // each tile's shorter last unit
+        int cnt = 0;
+        for (int t = t0; t < t1; ++t) cnt += nut(t) > 0 && bucket(t, nut(t) - 1) == k;
+        int total = 0;
+        int pos = done + scan(cnt, total);
+        for (int t = t0; t < t1; ++t)
+            if (nut(t) > 0 && bucket(t, nut(t) - 1) == k) place(t, nut(t) - 1, pos);
         done += total;
     }
 }

@@ -10,13 +10,16 @@
 // Per interaction: 3 FADD for the offset, 3 for r^2, one MUFU rsqrt y0 and one
 // Newton step y = y0 (3 - r^2 y0^2) / 2, then phi += q y and grad += q y^3 d.
 // The step is taken without its factor -1/2: z = y0 (r^2 y0^2 - 3) = -2 y is
-// three operations (y0^2, one FMA, one product), the charge is staged as -q/2
-// so that u = (-q/2) z = q y, phi += u, w = u z^2 = 4 q y^3, and grad += w d
-// sums 4 q y^3 d, scaled by 1/4 once per target at the end (exact: a power of
-// two).  16 FP32-pipe lane operations per interaction instead of 17.  Pairs at
-// r = 0 (the particle itself, coincident points) contribute nothing:
-// rsqrt(0) = inf makes the Newton step NaN and min(NaN, 0) = 0 removes it
-// without a branch (valid z are negative).  Only a chunk holding sources of
+// three operations (t = y0^2, one FMA, one product), the charge is staged as
+// -q/2 so that u = (-q/2) z = q y and phi += u, and the gradient's weight is
+// w = u t = q y y0^2: the Newton-refined 1/r times the 1/r^2 that the step has
+// already formed from y0 (relative error within twice the rsqrt's), and
+// grad += w d.  15 FP32-pipe lane operations per interaction (17 with a
+// separate -1/2 and y^3 = y y y).  Pairs at r = 0 (the particle itself,
+// coincident points) contribute nothing: rsqrt(0) = inf makes the Newton step
+// NaN and min(NaN, 0) = 0 removes it without a branch (valid z are negative),
+// and t = inf is clamped to the largest float so that w = 0 * t stays 0.
+// Only a chunk holding sources of
 // the target's own leaf can hold the particle itself, so only those chunks take
 // the guard; a pass that still ends with a non-finite sum (a pair at r = 0 in
 // two leaves, r^2 flushed to zero, a target at the origin meeting the zero
@@ -28,6 +31,8 @@
 // only the rsqrt and the NaN guard stay scalar.  Sources are staged in shared
 // memory as four arrays (x, y, z, q), so a pair of consecutive sources is one
 // 64-bit load per component.
+#include <cfloat>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -91,7 +96,7 @@ __device__ __forceinline__ Target2 target2(float4 xi)
 }
 
 // The target against two sources (packed x, y, z and staged charge -q/2);
-// accumulators packed per source: phi and 4 x grad.
+// accumulators packed per source: phi and grad.
 template <bool GUARD>
 __device__ __forceinline__ void p2p_interact2(const Target2 &T, f2 sx, f2 sy, f2 sz, f2 sqn, f2 &phi,
                                               f2 &gx, f2 &gy, f2 &gz)
@@ -101,15 +106,18 @@ __device__ __forceinline__ void p2p_interact2(const Target2 &T, f2 sx, f2 sy, f2
     float ra, rb;
     f2unpack(r2, ra, rb);
     const f2 y0 = f2pack(rsqrt_approx(ra), rsqrt_approx(rb));
-    f2 z = f2mul(y0, f2fma(r2, f2mul(y0, y0), T.mthree));  // -2 y
+    f2 t = f2mul(y0, y0);                  // 1 / r^2 (unrefined)
+    f2 z = f2mul(y0, f2fma(r2, t, T.mthree));  // -2 y
     if (GUARD) {
-        float za, zb;
+        float za, zb, ta, tb;
         f2unpack(z, za, zb);
+        f2unpack(t, ta, tb);
         z = f2pack(fminf(za, 0.f), fminf(zb, 0.f));
+        t = f2pack(fminf(ta, FLT_MAX), fminf(tb, FLT_MAX));
     }
     const f2 u = f2mul(sqn, z);  // q y
     phi = f2add(phi, u);
-    const f2 w = f2mul(u, f2mul(z, z));  // 4 q y^3
+    const f2 w = f2mul(u, t);  // q y^3
     gx = f2fma(w, dx, gx);
     gy = f2fma(w, dy, gy);
     gz = f2fma(w, dz, gz);
@@ -225,10 +233,10 @@ __device__ __forceinline__ void p2p_run(const Target2 &T, const float *sh, int j
                              a.phi, a.gx, a.gy, a.gz);
 }
 
-// phi and grad of one accumulator set (the gradient sums carry the factor 4)
+// phi and grad of one accumulator set
 __device__ __forceinline__ float4 acc_sum(const Acc2 &a)
 {
-    return make_float4(f2sum(a.phi), 0.25f * f2sum(a.gx), 0.25f * f2sum(a.gy), 0.25f * f2sum(a.gz));
+    return make_float4(f2sum(a.phi), f2sum(a.gx), f2sum(a.gy), f2sum(a.gz));
 }
 
 __device__ __forceinline__ bool nonfinite(float4 v)

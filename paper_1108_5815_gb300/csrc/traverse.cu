@@ -256,17 +256,17 @@ __device__ __forceinline__ int warp_excl(int v)
 // ma[r] / mo[r] mark, per round r of 32 sources, the accepted ones (M2L) and the
 // others (P2P for a leaf T, deferred otherwise).  The pairs, their order and the
 // list offsets are those resolve() would give.
-template <int R>
-__device__ __forceinline__ void write_single_pairs(const TargetInfo &T, const int *F, int ni, const unsigned (&ma)[R],
-                                                   const unsigned (&mo)[R], const CellArrays &c, const ListArrays &L,
+__device__ __forceinline__ void write_single_pairs(const TargetInfo &T, const int *F, int ni, const unsigned *ma,
+                                                   const unsigned *mo, const CellArrays &c, const ListArrays &L,
                                                    unsigned long long *__restrict__ counters, int64_t cap_m,
                                                    int64_t cap_p, int64_t cap_d, uint64_t *hash_keys, int *flags)
 {
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
+    const int nr = (ni + 31) >> 5;
     int m = 0, o = 0;
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
+#pragma unroll 1
+    for (int r = 0; r < nr; ++r) {
         m += __popc(ma[r]);
         o += __popc(mo[r]);
     }
@@ -296,30 +296,29 @@ __device__ __forceinline__ void write_single_pairs(const TargetInfo &T, const in
     }
     const bool fo = T.leaf ? fp : fd;
     int64_t rm = (int64_t)om, ro = T.leaf ? (int64_t)op : (int64_t)od;
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        if (r * 32 < ni) {
-            const int k = r * 32 + lane;
-            if (fm && ((ma[r] >> lane) & 1u)) {
-                const int S = F[k];
-                int Cs[3], hs, ls;
-                cell_geom(c, S, Cs, hs, ls);
-                const int64_t pos = rm + __popc(ma[r] & lt);
-                L.m2l_src[pos] = S;
-                L.m2l_tgt[pos] = t;
-                L.m2l_slot[pos] = hash_insert(hash_keys, class_key(T, ls, Cs, flags), flags);
-            } else if (fo && ((mo[r] >> lane) & 1u)) {
-                const int64_t pos = ro + __popc(mo[r] & lt);
-                if (T.leaf) {
-                    L.p2p_src[pos] = F[k];
-                    L.p2p_tgt[pos] = t;
-                } else {
-                    L.def_src[pos] = F[k];
-                }
+#pragma unroll 1
+    for (int r = 0; r < nr; ++r) {
+        const int k = r * 32 + lane;
+        const unsigned a = ma[r], b = mo[r];
+        if (fm && ((a >> lane) & 1u)) {
+            const int S = F[k];
+            int Cs[3], hs, ls;
+            cell_geom(c, S, Cs, hs, ls);
+            const int64_t pos = rm + __popc(a & lt);
+            L.m2l_src[pos] = S;
+            L.m2l_tgt[pos] = t;
+            L.m2l_slot[pos] = hash_insert(hash_keys, class_key(T, ls, Cs, flags), flags);
+        } else if (fo && ((b >> lane) & 1u)) {
+            const int64_t pos = ro + __popc(b & lt);
+            if (T.leaf) {
+                L.p2p_src[pos] = F[k];
+                L.p2p_tgt[pos] = t;
+            } else {
+                L.def_src[pos] = F[k];
             }
-            rm += __popc(ma[r]);
-            ro += __popc(mo[r]);
         }
+        rm += __popc(a);
+        ro += __popc(b);
     }
 }
 
@@ -434,6 +433,7 @@ __global__ void __launch_bounds__(128, 7)
     __shared__ int sN[4][kFrontier];  // per source of the frontier: its children when split, else -1
     __shared__ int sCnt[4][5][kCountCache];  // per-source counts of the count pass (first kCountCache)
     __shared__ uint8_t sRow[4][kSelNB];      // the target's row of the selection table
+    __shared__ unsigned sMa[4][kFrontier / 32], sMo[4][kFrontier / 32];  // a round's accepted / single-pair masks
     if (sz) {
         a = sz[kSzLevel + level];
         b = sz[kSzLevel + level + 1];
@@ -464,20 +464,21 @@ __global__ void __launch_bounds__(128, 7)
         // order of discovery.  When a round splits nothing and every source gives
         // exactly one pair (no selection table), the pairs are placed by ballot and
         // no walk is needed.
-        constexpr int R = kFrontier / 32;
         int cur = 0;
         for (int k = lane; k < ni; k += 32) sF[wib][0][k] = F[k];
         __syncwarp();
         for (int round = 0; round < 8; ++round) {
             const int *E = sF[wib][cur];
             int *nsplit = sN[wib];  // per source: its children when split, else -1
-            unsigned ma[R], mo[R];
+            unsigned *ma = sMa[wib], *mo = sMo[wib];
             int total = 0;
             bool any_split = false, single = true;
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                ma[r] = mo[r] = 0u;
-                if (r * 32 < ni) {
+            const int nr = (ni + 31) >> 5;
+            // a rolled loop: unrolled over the kFrontier / 32 rows, the classification
+            // and pair writing make a code footprint that stalls on instruction fetch
+#pragma unroll 1
+            for (int r = 0; r < nr; ++r) {
+                {
                     const int k = r * 32 + lane;
                     bool acc = false, sp = false, one = false;
                     int nc = 0;
@@ -508,8 +509,11 @@ __global__ void __launch_bounds__(128, 7)
                         }
                         nsplit[k] = sp ? nc : -1 - kind;
                     }
-                    ma[r] = __ballot_sync(0xffffffffu, acc);
-                    mo[r] = __ballot_sync(0xffffffffu, one && !acc);
+                    const unsigned ba = __ballot_sync(0xffffffffu, acc), bo = __ballot_sync(0xffffffffu, one && !acc);
+                    if (lane == 0) {
+                        ma[r] = ba;
+                        mo[r] = bo;
+                    }
                     single = __all_sync(0xffffffffu, k >= ni || one) && single;
                     any_split = __any_sync(0xffffffffu, sp) || any_split;
                     total += warp_sum(nc);
@@ -517,7 +521,8 @@ __global__ void __launch_bounds__(128, 7)
             }
             if (!any_split) {
                 if (!sel && single) {
-                    write_single_pairs<R>(T, E, ni, ma, mo, c, L, counters, cap_m, cap_p, cap_d, hash_keys, flags);
+                    __syncwarp();
+                    write_single_pairs(T, E, ni, ma, mo, c, L, counters, cap_m, cap_p, cap_d, hash_keys, flags);
                     return;
                 }
                 if (sel) {  // with a selection table every source left gives one pair of its recorded kind

@@ -925,81 +925,84 @@ __global__ void __launch_bounds__(32)
 {
     extern __shared__ float rows[];  // 32 x (P2pad + 1)
     if (sz) ncells = sz[kSzCells];
-    const int cell = blockIdx.x;
-    if (cell >= ncells) return;
-    const int cnt = Ls.p2l_cnt[cell];
-    if (cnt == 0) return;
-    const int *slist = Ls.p2l_src + Ls.p2l_off[cell];
-    const int lane = threadIdx.x;
-    const int stride = P2pad + 1;
-    const Frame fr = cell_frame(c, cell);
-    float acc[kMaxChunks];
+    // blocks stride over the cells, so that the grid can be sized to the GPU and a
+    // solve without particle-cell pairs costs one pass over the counts
+    for (int cell = blockIdx.x; cell < ncells; cell += gridDim.x) {
+        const int cnt = Ls.p2l_cnt[cell];
+        if (cnt == 0) continue;
+        const int *slist = Ls.p2l_src + Ls.p2l_off[cell];
+        const int lane = threadIdx.x;
+        const int stride = P2pad + 1;
+        const Frame fr = cell_frame(c, cell);
+        float acc[kMaxChunks];
 #pragma unroll
-    for (int j = 0; j < kMaxChunks; ++j) acc[j] = 0.f;
-    float *row = rows + lane * stride;
-    for (int k = 0; k < cnt; ++k) {
-        const int S = slist[k];
-        const int b = c.begin[S], e = c.end[S];
-        for (int base = b; base < e; base += 32) {
-            const int i = base + lane;
-            for (int j = 0; j < P2pad; ++j) row[j] = 0.f;
-            if (i < e) {
-                const float4 pt = pts[i];
-                float x, y, z;
-                frame_offset(fr, pt, x, y, z);
-                const float q = pt.w;
-                const float r2 = x * x + y * y + z * z, ir2 = 1.f / r2;
-                float mre = rsqrtf(r2), mim = 0.f;  // I^_m^m
-                for (int m = 0; m <= p; ++m) {
-                    if (m > 0) {
-                        const float f = c_rec_d[m] * ir2;
-                        const float nre = f * (x * mre - y * mim), nim = f * (x * mim + y * mre);
-                        mre = nre;
-                        mim = nim;
-                    }
-                    float p2r = 0.f, p2i = 0.f, p1r = mre, p1i = mim;
-                    for (int n = m; n <= p; ++n) {
-                        float ir, ii;
-                        if (n == m) {
-                            ir = mre;
-                            ii = mim;
-                        } else {
-                            const int t = n * (n + 1) / 2 + m;
-                            const float a = c_rec_a[t] * z * ir2, bb = c_rec_b[t] * ir2;
-                            ir = a * p1r - bb * p2r;
-                            ii = a * p1i - bb * p2i;
-                            p2r = p1r;
-                            p2i = p1i;
-                            p1r = ir;
-                            p1i = ii;
+        for (int j = 0; j < kMaxChunks; ++j) acc[j] = 0.f;
+        float *row = rows + lane * stride;
+        for (int k = 0; k < cnt; ++k) {
+            const int S = slist[k];
+            const int b = c.begin[S], e = c.end[S];
+            for (int base = b; base < e; base += 32) {
+                const int i = base + lane;
+                for (int j = 0; j < P2pad; ++j) row[j] = 0.f;
+                if (i < e) {
+                    const float4 pt = pts[i];
+                    float x, y, z;
+                    frame_offset(fr, pt, x, y, z);
+                    const float q = pt.w;
+                    const float r2 = x * x + y * y + z * z, ir2 = 1.f / r2;
+                    float mre = rsqrtf(r2), mim = 0.f;  // I^_m^m
+                    for (int m = 0; m <= p; ++m) {
+                        if (m > 0) {
+                            const float f = c_rec_d[m] * ir2;
+                            const float nre = f * (x * mre - y * mim), nim = f * (x * mim + y * mre);
+                            mre = nre;
+                            mim = nim;
                         }
-                        if (m == 0) {
-                            row[n * n] = q * ir;
-                        } else {
-                            row[n * n + 2 * m - 1] = q * ir;
-                            row[n * n + 2 * m] = -q * ii;
+                        float p2r = 0.f, p2i = 0.f, p1r = mre, p1i = mim;
+                        for (int n = m; n <= p; ++n) {
+                            float ir, ii;
+                            if (n == m) {
+                                ir = mre;
+                                ii = mim;
+                            } else {
+                                const int t = n * (n + 1) / 2 + m;
+                                const float a = c_rec_a[t] * z * ir2, bb = c_rec_b[t] * ir2;
+                                ir = a * p1r - bb * p2r;
+                                ii = a * p1i - bb * p2i;
+                                p2r = p1r;
+                                p2i = p1i;
+                                p1r = ir;
+                                p1i = ii;
+                            }
+                            if (m == 0) {
+                                row[n * n] = q * ir;
+                            } else {
+                                row[n * n + 2 * m - 1] = q * ir;
+                                row[n * n + 2 * m] = -q * ii;
+                            }
                         }
                     }
                 }
-            }
-            __syncwarp();
+                __syncwarp();
 #pragma unroll
-            for (int j = 0; j < kMaxChunks; ++j) {
-                const int kk = lane + 32 * j;
-                if (kk < P2pad) {
-                    float sum = 0.f;
-                    for (int r = 0; r < 32; ++r) sum += rows[r * stride + kk];
-                    acc[j] += sum;
+                for (int j = 0; j < kMaxChunks; ++j) {
+                    const int kk = lane + 32 * j;
+                    if (kk < P2pad) {
+                        float sum = 0.f;
+                        for (int r = 0; r < 32; ++r) sum += rows[r * stride + kk];
+                        acc[j] += sum;
+                    }
                 }
+                __syncwarp();
             }
-            __syncwarp();
         }
-    }
-    const int P2 = nterms(p);
+        const int P2 = nterms(p);
 #pragma unroll
-    for (int j = 0; j < kMaxChunks; ++j) {
-        const int kk = lane + 32 * j;
-        if (kk < P2) L[(int64_t)cell * P2pad + kk] += acc[j];
+        for (int j = 0; j < kMaxChunks; ++j) {
+            const int kk = lane + 32 * j;
+            if (kk < P2) L[(int64_t)cell * P2pad + kk] += acc[j];
+        }
+        __syncwarp();  // the warp's shared rows are rewritten for the next cell
     }
 }
 
@@ -1041,120 +1044,123 @@ __global__ void __launch_bounds__(32 * kM2PWarps)
     }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int li = blockIdx.x * kM2PWarps + warp;
-    if (li >= nleaves) return;
-    const int cell = leaves[li];
-    const int cnt = Ls.m2p_cnt[cell];
-    if (cnt == 0) return;
-    const int *slist = Ls.m2p_src + Ls.m2p_off[cell];
-    float *Mh = wbuf + warp * 4 * P2pad, *Mz = Mh + P2pad, *Mx1 = Mz + P2pad, *Mx2 = Mx1 + P2pad;
-    const int P2 = nterms(p);
-    const int b = c.begin[cell], e = c.end[cell];
-    // particle offsets from the target leaf's centre in FP32; the shift and scale of
-    // each source come from one FP64 evaluation per (leaf, source) pair, not per particle
-    double cT[3], sT;
-    cell_centre_side(c, cell, box, cT, sT);
-    float *geo = sgeo + warp * 4;  // (c_T - c_S) / s_S and s_T / s_S of the current source
-    for (int i0 = b; i0 < e; i0 += 32) {
-        const int i = i0 + lane;
-        const bool valid = i < e;
-        const float4 pt = pts[valid ? i : b];
-        const double isT = 1.0 / sT;
-        const float rx = (float)(((double)pt.x - cT[0]) * isT), ry = (float)(((double)pt.y - cT[1]) * isT),
-                    rz = (float)(((double)pt.z - cT[2]) * isT);
-        float phi = 0.f, dz = 0.f, dpr = 0.f, dpi = 0.f;
-        for (int k = 0; k < cnt; ++k) {
-            const int S = slist[k];
-            __syncwarp();
-            if (lane == 0) {
-                double cS[3], sS;
-                cell_centre_side(c, S, box, cS, sS);
-                const double isS = 1.0 / sS;  // sides are powers of two times the box side
-                geo[0] = (float)((cT[0] - cS[0]) * isS);
-                geo[1] = (float)((cT[1] - cS[1]) * isS);
-                geo[2] = (float)((cT[2] - cS[2]) * isS);
-                geo[3] = (float)(sT * isS);
-            }
-            for (int j = lane; j < P2pad; j += 32) {
-                const float v = j < P2 ? M[(int64_t)S * P2pad + j] : 0.f;
-                Mh[j] = v;
-                Mz[j] = v * fz[j];
-                Mx1[j] = v * f1[j];
-                Mx2[j] = v * f2[j];
-            }
-            __syncwarp();
-            const float ratio = geo[3];
-            const float x = fmaf(rx, ratio, geo[0]), y = fmaf(ry, ratio, geo[1]), z = fmaf(rz, ratio, geo[2]);
-            const float is1 = ratio / (float)sT, is2 = is1 * is1;  // 1 / s_S = (s_T / s_S) / s_T
-            const float r2 = x * x + y * y + z * z;
-            const float ir2 = 1.f / r2;
-            float sphi = 0.f, sdz = 0.f, sdr = 0.f, sdi = 0.f;
-            float mre = rsqrtf(r2), mim = 0.f;  // I^_m^m
-            for (int m = 0; m <= p + 1; ++m) {
-                if (m > 0) {
-                    const float f = cd[m] * ir2;
-                    const float nre = f * (x * mre - y * mim), nim = f * (x * mim + y * mre);
-                    mre = nre;
-                    mim = nim;
+    // warps stride over the leaves, so that the grid can be sized to the GPU and a
+    // solve without cell-particle pairs costs one pass over the counts
+    for (int li = blockIdx.x * kM2PWarps + warp; li < nleaves; li += gridDim.x * kM2PWarps) {
+        const int cell = leaves[li];
+        const int cnt = Ls.m2p_cnt[cell];
+        if (cnt == 0) continue;
+        const int *slist = Ls.m2p_src + Ls.m2p_off[cell];
+        float *Mh = wbuf + warp * 4 * P2pad, *Mz = Mh + P2pad, *Mx1 = Mz + P2pad, *Mx2 = Mx1 + P2pad;
+        const int P2 = nterms(p);
+        const int b = c.begin[cell], e = c.end[cell];
+        // particle offsets from the target leaf's centre in FP32; the shift and scale of
+        // each source come from one FP64 evaluation per (leaf, source) pair, not per particle
+        double cT[3], sT;
+        cell_centre_side(c, cell, box, cT, sT);
+        float *geo = sgeo + warp * 4;  // (c_T - c_S) / s_S and s_T / s_S of the current source
+        for (int i0 = b; i0 < e; i0 += 32) {
+            const int i = i0 + lane;
+            const bool valid = i < e;
+            const float4 pt = pts[valid ? i : b];
+            const double isT = 1.0 / sT;
+            const float rx = (float)(((double)pt.x - cT[0]) * isT), ry = (float)(((double)pt.y - cT[1]) * isT),
+                        rz = (float)(((double)pt.z - cT[2]) * isT);
+            float phi = 0.f, dz = 0.f, dpr = 0.f, dpi = 0.f;
+            for (int k = 0; k < cnt; ++k) {
+                const int S = slist[k];
+                __syncwarp();
+                if (lane == 0) {
+                    double cS[3], sS;
+                    cell_centre_side(c, S, box, cS, sS);
+                    const double isS = 1.0 / sS;  // sides are powers of two times the box side
+                    geo[0] = (float)((cT[0] - cS[0]) * isS);
+                    geo[1] = (float)((cT[1] - cS[1]) * isS);
+                    geo[2] = (float)((cT[2] - cS[2]) * isS);
+                    geo[3] = (float)(sT * isS);
                 }
-                const float w = m == 0 ? 1.f : 2.f;
-                float p2r = 0.f, p2i = 0.f, p1r = mre, p1i = mim;
-                for (int n = m; n <= p + 1; ++n) {
-                    float ir, ii;
-                    if (n == m) {
-                        ir = mre;
-                        ii = mim;
-                    } else {
-                        const int t = n * (n + 1) / 2 + m;
-                        const float a = ca[t] * z * ir2, bb = cb[t] * ir2;
-                        ir = a * p1r - bb * p2r;
-                        ii = a * p1i - bb * p2i;
-                        p2r = p1r;
-                        p2i = p1i;
-                        p1r = ir;
-                        p1i = ii;
+                for (int j = lane; j < P2pad; j += 32) {
+                    const float v = j < P2 ? M[(int64_t)S * P2pad + j] : 0.f;
+                    Mh[j] = v;
+                    Mz[j] = v * fz[j];
+                    Mx1[j] = v * f1[j];
+                    Mx2[j] = v * f2[j];
+                }
+                __syncwarp();
+                const float ratio = geo[3];
+                const float x = fmaf(rx, ratio, geo[0]), y = fmaf(ry, ratio, geo[1]), z = fmaf(rz, ratio, geo[2]);
+                const float is1 = ratio / (float)sT, is2 = is1 * is1;  // 1 / s_S = (s_T / s_S) / s_T
+                const float r2 = x * x + y * y + z * z;
+                const float ir2 = 1.f / r2;
+                float sphi = 0.f, sdz = 0.f, sdr = 0.f, sdi = 0.f;
+                float mre = rsqrtf(r2), mim = 0.f;  // I^_m^m
+                for (int m = 0; m <= p + 1; ++m) {
+                    if (m > 0) {
+                        const float f = cd[m] * ir2;
+                        const float nre = f * (x * mre - y * mim), nim = f * (x * mim + y * mre);
+                        mre = nre;
+                        mim = nim;
                     }
-                    if (n <= p) {  // phi += w Re(M^_n^m I^_n^m)
-                        const int k = n * n + (m == 0 ? 0 : 2 * m - 1);
-                        const float mr = Mh[k], mi = m == 0 ? 0.f : Mh[k + 1];
-                        sphi += w * (mr * ir - mi * ii);
-                    }
-                    if (n >= 1) {
-                        const int n1 = n - 1, base = n1 * n1;
-                        if (m <= n1) {  // dz += w Re(Mz_{n-1}^m I^_n^m)
-                            const int k = base + (m == 0 ? 0 : 2 * m - 1);
-                            const float mr = Mz[k], mi = m == 0 ? 0.f : Mz[k + 1];
-                            sdz += w * (mr * ir - mi * ii);
+                    const float w = m == 0 ? 1.f : 2.f;
+                    float p2r = 0.f, p2i = 0.f, p1r = mre, p1i = mim;
+                    for (int n = m; n <= p + 1; ++n) {
+                        float ir, ii;
+                        if (n == m) {
+                            ir = mre;
+                            ii = mim;
+                        } else {
+                            const int t = n * (n + 1) / 2 + m;
+                            const float a = ca[t] * z * ir2, bb = cb[t] * ir2;
+                            ir = a * p1r - bb * p2r;
+                            ii = a * p1i - bb * p2i;
+                            p2r = p1r;
+                            p2i = p1i;
+                            p1r = ir;
+                            p1i = ii;
                         }
-                        if (m >= 1) {  // D+ += Mx1_{n-1}^{m-1} I^_n^m
-                            const int mm = m - 1;
-                            const int k = base + (mm == 0 ? 0 : 2 * mm - 1);
-                            const float mr = Mx1[k], mi = mm == 0 ? 0.f : Mx1[k + 1];
-                            sdr += mr * ir - mi * ii;
-                            sdi += mr * ii + mi * ir;
+                        if (n <= p) {  // phi += w Re(M^_n^m I^_n^m)
+                            const int k = n * n + (m == 0 ? 0 : 2 * m - 1);
+                            const float mr = Mh[k], mi = m == 0 ? 0.f : Mh[k + 1];
+                            sphi += w * (mr * ir - mi * ii);
                         }
-                        if (m + 1 <= n1) {  // D+ -= conj(Mx2_{n-1}^{m+1} I^_n^m)
-                            const int k = base + 2 * (m + 1) - 1;
-                            const float mr = Mx2[k], mi = Mx2[k + 1];
-                            sdr -= mr * ir - mi * ii;
-                            sdi += mr * ii + mi * ir;
+                        if (n >= 1) {
+                            const int n1 = n - 1, base = n1 * n1;
+                            if (m <= n1) {  // dz += w Re(Mz_{n-1}^m I^_n^m)
+                                const int k = base + (m == 0 ? 0 : 2 * m - 1);
+                                const float mr = Mz[k], mi = m == 0 ? 0.f : Mz[k + 1];
+                                sdz += w * (mr * ir - mi * ii);
+                            }
+                            if (m >= 1) {  // D+ += Mx1_{n-1}^{m-1} I^_n^m
+                                const int mm = m - 1;
+                                const int k = base + (mm == 0 ? 0 : 2 * mm - 1);
+                                const float mr = Mx1[k], mi = mm == 0 ? 0.f : Mx1[k + 1];
+                                sdr += mr * ir - mi * ii;
+                                sdi += mr * ii + mi * ir;
+                            }
+                            if (m + 1 <= n1) {  // D+ -= conj(Mx2_{n-1}^{m+1} I^_n^m)
+                                const int k = base + 2 * (m + 1) - 1;
+                                const float mr = Mx2[k], mi = Mx2[k + 1];
+                                sdr -= mr * ir - mi * ii;
+                                sdi += mr * ii + mi * ir;
+                            }
                         }
                     }
                 }
+                phi += sphi * is1;
+                dz -= sdz * is2;
+                dpr += sdr * is2;
+                dpi += sdi * is2;
             }
-            phi += sphi * is1;
-            dz -= sdz * is2;
-            dpr += sdr * is2;
-            dpi += sdi * is2;
+            if (valid) {
+                float4 f = far[i];
+                f.x += phi;
+                f.y += dpr;
+                f.z += dpi;
+                f.w += dz;
+                far[i] = f;
+            }
         }
-        if (valid) {
-            float4 f = far[i];
-            f.x += phi;
-            f.y += dpr;
-            f.z += dpi;
-            f.w += dz;
-            far[i] = f;
-        }
+        __syncwarp();  // the warp's shared rows are rewritten for the next cell
     }
 }
 

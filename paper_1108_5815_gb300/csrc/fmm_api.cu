@@ -972,7 +972,7 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
     if (p2l_total > 0) {  // particle-cell pairs of the hybrid selection, into L before L2L
         const size_t sh = (size_t)32 * (P2pad + 1) * sizeof(float);
         if (sh > 48 * 1024) set_smem_limit_once((const void *)k_p2l, (int)sh);
-        k_p2l<<<ncells, 32, sh, fs>>>(c, L, ncells, pts, box, p, P2pad, Lx);
+        k_p2l<<<(unsigned)std::min(ncells, 152 * 8), 32, sh, fs>>>(c, L, ncells, pts, box, p, P2pad, Lx);
         FMM_LAUNCH_CHECK();
     }
     for (int l = 0; l < depth; ++l)  // parents at level l, children at level l + 1
@@ -984,7 +984,7 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
     if (m2p_total > 0) {  // cell-particle pairs of the hybrid selection, added to the far field
         const size_t sh = m2p_smem(p, P2pad);
         if (sh > 48 * 1024) set_smem_limit_once((const void *)k_m2p, (int)sh);
-        k_m2p<<<(unsigned)ceil_div(nleaves, kM2PWarps), 32 * kM2PWarps, sh, fs>>>(c, L, leaves, nleaves, pts, box, p,
+        k_m2p<<<(unsigned)std::min<int64_t>(ceil_div(nleaves, kM2PWarps), 152 * 4), 32 * kM2PWarps, sh, fs>>>(c, L, leaves, nleaves, pts, box, p,
                                                                                 P2pad, M, far);
         FMM_LAUNCH_CHECK();
     }

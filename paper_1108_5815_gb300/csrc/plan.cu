@@ -207,7 +207,7 @@ void enqueue_plan(const PlanShape &s, const PlanBuffers &b, cudaStream_t st, cud
 
     // ---------------------------------------------------------- downward pass (fs)
     if (s.hybrid) {
-        k_p2l<<<(unsigned)std::max(1, s.cell_cap), 32, (size_t)32 * (P2pad + 1) * sizeof(float), fs>>>(
+        k_p2l<<<(unsigned)std::max(1, std::min(s.cell_cap, 152 * 8)), 32, (size_t)32 * (P2pad + 1) * sizeof(float), fs>>>(
             c, L, 0, b.pts, b.box, p, P2pad, b.Lx, b.sz);
         FMM_LAUNCH_CHECK();
     }
@@ -219,7 +219,7 @@ void enqueue_plan(const PlanShape &s, const PlanBuffers &b, cudaStream_t st, cud
     }
     launch_l2p(c, b.pcell, s.N, b.pts, p, P2pad, b.Lx, b.far, fs);
     if (s.hybrid) {
-        k_m2p<<<blocks_for(s.leaf_cap, kM2PWarps), 32 * kM2PWarps, m2p_smem(p, P2pad), fs>>>(
+        k_m2p<<<std::min(blocks_for(s.leaf_cap, kM2PWarps), 152u * 4u), 32 * kM2PWarps, m2p_smem(p, P2pad), fs>>>(
             c, L, b.leaves, 0, b.pts, b.box, p, P2pad, b.M, b.far, b.sz);
         FMM_LAUNCH_CHECK();
     }

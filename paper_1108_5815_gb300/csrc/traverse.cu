@@ -473,6 +473,7 @@ __global__ void __launch_bounds__(128, 7)
             unsigned *ma = sMa[wib], *mo = sMo[wib];
             int total = 0;
             bool any_split = false, single = true;
+            bool plain = true;  // every pair of the round is of the kind the plain FMM gives it
             const int nr = (ni + 31) >> 5;
             // a rolled loop: unrolled over the kFrontier / 32 rows, the classification
             // and pair writing make a code footprint that stalls on instruction fetch
@@ -480,13 +481,14 @@ __global__ void __launch_bounds__(128, 7)
             for (int r = 0; r < nr; ++r) {
                 {
                     const int k = r * 32 + lane;
-                    bool acc = false, sp = false, one = false;
+                    bool acc = false, sp = false, one = false, pk = true;
                     int nc = 0;
                     if (k < ni) {
                         const int S = E[k];
                         nc = 1;
                         int kind = kOutDef;  // the source's single pair when it is not split
-                        if (!(S & (kP2PFlag | kM2PFlag))) {
+                        pk = !(S & (kP2PFlag | kM2PFlag));
+                        if (pk) {
                             int Cs[3], hs, ls, bs;
                             cell_geom(c, S, Cs, hs, ls, bs);
                             const int nch = c.nchild[S];
@@ -496,6 +498,7 @@ __global__ void __launch_bounds__(128, 7)
                             if (sp) nc = nch;
                             if (acc) {
                                 const int kd = sel ? row[bs] : 0;  // as resolve()
+                                pk = kd == 0;
                                 kind = kd == 3 ? kOutP2L
                                        : kd != 0 && !T.leaf ? (kd == 1 ? kOutDefP2P : kOutDefM2P)
                                        : kd == 1 ? kOutP2P
@@ -515,12 +518,15 @@ __global__ void __launch_bounds__(128, 7)
                         mo[r] = bo;
                     }
                     single = __all_sync(0xffffffffu, k >= ni || one) && single;
+                    plain = __all_sync(0xffffffffu, pk) && plain;
                     any_split = __any_sync(0xffffffffu, sp) || any_split;
                     total += warp_sum(nc);
                 }
             }
             if (!any_split) {
-                if (!sel && single) {
+                if (single && (!sel || plain)) {
+                    // (with a selection table whose entries for these pairs are all M2L,
+                    // the lists are those of the plain FMM)
                     __syncwarp();
                     write_single_pairs(T, E, ni, ma, mo, c, L, counters, cap_m, cap_p, cap_d, hash_keys, flags);
                     return;

@@ -127,11 +127,14 @@ struct Workspace {
         double theta = 0.0;
         std::vector<int64_t> off;  // system offsets (batched)
         std::vector<uint8_t> sel;  // the selection table's content (empty: plain FMM)
+        // the caller's arrays: the plan reads and writes them in place (no copies)
+        const void *xyz = nullptr, *q = nullptr, *phi = nullptr, *grad = nullptr;
         bool operator==(const ReplayKey &k) const
         {
             return N == k.N && nsys == k.nsys && p == k.p && ncrit == k.ncrit && max_depth == k.max_depth &&
                    precision == k.precision && select_mode == k.select_mode && unit_blocks == k.unit_blocks &&
-                   theta == k.theta && off == k.off && sel == k.sel;
+                   theta == k.theta && off == k.off && sel == k.sel && xyz == k.xyz && q == k.q && phi == k.phi &&
+                   grad == k.grad;
         }
     };
     fmm_plan *replay_plan = nullptr;
@@ -972,7 +975,7 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
     if (p2l_total > 0) {  // particle-cell pairs of the hybrid selection, into L before L2L
         const size_t sh = (size_t)32 * (P2pad + 1) * sizeof(float);
         if (sh > 48 * 1024) set_smem_limit_once((const void *)k_p2l, (int)sh);
-        k_p2l<<<(unsigned)std::min(ncells, 152 * 8), 32, sh, fs>>>(c, L, ncells, pts, box, p, P2pad, Lx);
+        k_p2l<<<(unsigned)ncells, 32, sh, fs>>>(c, L, ncells, pts, box, p, P2pad, Lx);
         FMM_LAUNCH_CHECK();
     }
     for (int l = 0; l < depth; ++l)  // parents at level l, children at level l + 1
@@ -984,7 +987,7 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
     if (m2p_total > 0) {  // cell-particle pairs of the hybrid selection, added to the far field
         const size_t sh = m2p_smem(p, P2pad);
         if (sh > 48 * 1024) set_smem_limit_once((const void *)k_m2p, (int)sh);
-        k_m2p<<<(unsigned)std::min<int64_t>(ceil_div(nleaves, kM2PWarps), 152 * 4), 32 * kM2PWarps, sh, fs>>>(c, L, leaves, nleaves, pts, box, p,
+        k_m2p<<<(unsigned)ceil_div(nleaves, kM2PWarps), 32 * kM2PWarps, sh, fs>>>(c, L, leaves, nleaves, pts, box, p,
                                                                                 P2pad, M, far);
         FMM_LAUNCH_CHECK();
     }
@@ -1301,6 +1304,8 @@ PlanShape plan_shape(const Workspace &ws, int64_t N, int nsys, int p, double the
     s.def_cap = with_headroom(sh.tot[2], h, 4096);
     s.m2p_cap = with_headroom(sh.tot[3], h, 4096);
     s.p2l_cap = with_headroom(sh.tot[4], h, 4096);
+    s.m2p_seen = sh.tot[3] > 0;
+    s.p2l_seen = sh.tot[4] > 0;
     s.class_hcap = 1;
     while (s.class_hcap < 2u * (uint32_t)std::max<int64_t>(1, (int64_t)ws.class_cache.size())) s.class_hcap <<= 1;
     int nsm = 152;
@@ -1563,17 +1568,27 @@ void plan_check(fmm_plan &pl, cudaStream_t st)
                                       "no operator for; its results are invalid (create a new plan)"};
 }
 
+// The caller's arrays that a replayed plan reads and writes in place.
+struct Borrowed {
+    const float *xyz = nullptr, *q = nullptr;
+    float *phi = nullptr, *grad = nullptr;
+};
+
 // A plan captured from the workspace's last solve (its sizes, operators and
-// classes), with plan-owned particle and result buffers.
+// classes).  Its particle and result arrays are its own, or, for the plan that
+// repeated calls replay, the caller's (borrowed: that plan is replayed only by a
+// call with the same four arrays, so it never copies them).
 fmm_plan *plan_from_last_solve(Workspace &ws, int64_t N, int nsys, const int64_t *off, int p, double theta,
-                               int ncrit, const fmm_options &o, const uint8_t *sel, double headroom)
+                               int ncrit, const fmm_options &o, const uint8_t *sel, double headroom,
+                               const Borrowed &bw = Borrowed{})
 {
     std::unique_ptr<fmm_plan> pl(new fmm_plan());
     FMM_CUDA_TRY(cudaGetDevice(&pl->device));
-    pl->xyz = pl->mem.get<float>(3 * (size_t)N);
-    pl->q = pl->mem.get<float>((size_t)N);
-    pl->phi = pl->mem.get<float>((size_t)N);
-    pl->grad = pl->mem.get<float>(3 * (size_t)N);
+    const bool borrow = bw.xyz && bw.q && bw.phi && bw.grad;
+    pl->xyz = borrow ? const_cast<float *>(bw.xyz) : pl->mem.get<float>(3 * (size_t)N);
+    pl->q = borrow ? const_cast<float *>(bw.q) : pl->mem.get<float>((size_t)N);
+    pl->phi = borrow ? bw.phi : pl->mem.get<float>((size_t)N);
+    pl->grad = borrow ? bw.grad : pl->mem.get<float>(3 * (size_t)N);
     pl->s = plan_shape(ws, N, nsys, p, theta, ncrit, o, sel != nullptr, headroom);
     build_plan(*pl, ws, off, sel);
     return pl.release();
@@ -1607,10 +1622,18 @@ void solve_api(Workspace &ws, const float *xyz, const float *q, int64_t N, int n
     key.theta = theta;
     key.off.assign(off, off + nsys + 1);
     if (sel) key.sel.assign(sel, sel + (size_t)kSelNB * kSelNB);
+    key.xyz = xyz;
+    key.q = q;
+    key.phi = phi;
+    key.grad = grad;
     if (ws.replay_plan && ws.replay_key == key) {
         try {
             plan_execute(*ws.replay_plan, xyz, q, phi, grad, stream);
             plan_check(*ws.replay_plan, stream);
+            // (calls that alternate between keys then solve the other keys plainly
+            // instead of capturing a plan at every other call)
+            ws.last_key = std::move(key);
+            ws.have_last = true;
             return;
         } catch (const Error &e) {
             if (e.code != FMM_ERR_CAPACITY) throw;
@@ -1623,7 +1646,8 @@ void solve_api(Workspace &ws, const float *xyz, const float *q, int64_t N, int n
         delete ws.replay_plan;
         ws.replay_plan = nullptr;
         try {
-            ws.replay_plan = plan_from_last_solve(ws, N, nsys, off, p, theta, ncrit, o, sel, 1.25);
+            ws.replay_plan = plan_from_last_solve(ws, N, nsys, off, p, theta, ncrit, o, sel, 1.25,
+                                                  Borrowed{xyz, q, phi, grad});
             ws.replay_key = key;
         } catch (const Error &) {
             // no plan for this key (the solve itself succeeded): later calls solve plainly

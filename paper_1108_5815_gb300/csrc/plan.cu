@@ -207,8 +207,11 @@ void enqueue_plan(const PlanShape &s, const PlanBuffers &b, cudaStream_t st, cud
 
     // ---------------------------------------------------------- downward pass (fs)
     if (s.hybrid) {
-        k_p2l<<<(unsigned)std::max(1, std::min(s.cell_cap, 152 * 8)), 32, (size_t)32 * (P2pad + 1) * sizeof(float), fs>>>(
-            c, L, 0, b.pts, b.box, p, P2pad, b.Lx, b.sz);
+        // a full grid when the captured solve had particle-cell pairs, else a GPU-sized
+        // one that strides over the cells' counts
+        const int gp = std::max(1, s.p2l_seen ? s.cell_cap : std::min(s.cell_cap, 152 * 16));
+        k_p2l<<<(unsigned)gp, 32, (size_t)32 * (P2pad + 1) * sizeof(float), fs>>>(c, L, 0, b.pts, b.box, p, P2pad,
+                                                                                   b.Lx, b.sz);
         FMM_LAUNCH_CHECK();
     }
     for (int l = 0; l < s.levels; ++l) {
@@ -219,7 +222,9 @@ void enqueue_plan(const PlanShape &s, const PlanBuffers &b, cudaStream_t st, cud
     }
     launch_l2p(c, b.pcell, s.N, b.pts, p, P2pad, b.Lx, b.far, fs);
     if (s.hybrid) {
-        k_m2p<<<std::min(blocks_for(s.leaf_cap, kM2PWarps), 152u * 4u), 32 * kM2PWarps, m2p_smem(p, P2pad), fs>>>(
+        const unsigned gm = s.m2p_seen ? blocks_for(s.leaf_cap, kM2PWarps)
+                                       : std::min(blocks_for(s.leaf_cap, kM2PWarps), 152u * 16u);
+        k_m2p<<<gm, 32 * kM2PWarps, m2p_smem(p, P2pad), fs>>>(
             c, L, b.leaves, 0, b.pts, b.box, p, P2pad, b.M, b.far, b.sz);
         FMM_LAUNCH_CHECK();
     }

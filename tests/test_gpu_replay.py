@@ -1,9 +1,12 @@
 """Repeated solves through the public entry points (fmm_options.replay, the
 default): from the third call of one key on, a call replays the plan the library
-captured after the second.
+captured after the second.  The key includes the caller's arrays, which the plan
+reads and writes in place.
 
 * a replayed call gives exactly the plain solve's result (replay=False) of the
-  same data, for new positions and charges too;
+  same data, for new positions and charges too, also when they are written into
+  the same arrays;
+* calls that alternate between two sets of arrays are plain solves and stay right;
 * data that outgrows the plan (a clustered set after a uniform one of the same
   N) is solved again plainly, with the plain result, and later calls stay right;
 * batched systems and a selection table replay the same way;
@@ -108,3 +111,35 @@ def test_nonfinite_input_in_a_replayed_call():
         _solve(xbt, qbt, args)
     assert e.value.status == fmm.FMM_ERR_NONFINITE
     assert _equal(_solve(xt, qt, args), plain)
+
+
+def test_new_data_in_the_same_arrays_and_alternating_arrays():
+    torch = torch_cuda()
+    from paper_1108_5815_gb300 import fmm
+    args = (6, 0.5, 32)
+    xa, qa = inputs.uniform_cube(25000, 830)
+    xb, qb = inputs.uniform_cube(25000, 831)
+    xta, qta = _dev(xa, qa)
+    xtb, qtb = _dev(xb, qb)
+    pa = torch.empty(25000, device="cuda")
+    ga = torch.empty(25000, 3, device="cuda")
+
+    def run(xt, qt, **kw):
+        fmm.laplace3d(xt, qt, *args, out=(pa, ga), **kw)
+        torch.cuda.synchronize()
+        return pa.cpu().numpy().copy(), ga.cpu().numpy().copy()
+
+    for _ in range(3):
+        run(xta, qta)  # the third call replays the plan on these very arrays
+    # new data written into the same arrays: the replay reads it in place
+    xta.copy_(xtb)
+    qta.copy_(qtb)
+    ref_b = run(xtb, qtb, replay=False)
+    assert _equal(run(xta, qta), ref_b)
+    # alternating arrays: no two calls in a row share a key
+    xta.copy_(torch.from_numpy(xa).cuda())
+    qta.copy_(torch.from_numpy(qa).cuda())
+    ref_a = run(xta, qta, replay=False)
+    for _ in range(2):
+        assert _equal(run(xtb, qtb), ref_b)
+        assert _equal(run(xta, qta), ref_a)

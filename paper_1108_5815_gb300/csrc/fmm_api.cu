@@ -1302,10 +1302,12 @@ PlanShape plan_shape(const Workspace &ws, int64_t N, int nsys, int p, double the
     s.m2l_cap = with_headroom(sh.tot[0], h, 4096);
     s.p2p_cap = with_headroom(sh.tot[1], h, 4096);
     s.def_cap = with_headroom(sh.tot[2], h, 4096);
-    s.m2p_cap = with_headroom(sh.tot[3], h, 4096);
-    s.p2l_cap = with_headroom(sh.tot[4], h, 4096);
+    // A kind of pair the captured solve did not have gets no capacity and no kernel:
+    // a replay whose lists hold one exceeds its capacity and is solved again plainly.
     s.m2p_seen = sh.tot[3] > 0;
     s.p2l_seen = sh.tot[4] > 0;
+    s.m2p_cap = s.m2p_seen ? with_headroom(sh.tot[3], h, 4096) : 0;
+    s.p2l_cap = s.p2l_seen ? with_headroom(sh.tot[4], h, 4096) : 0;
     s.class_hcap = 1;
     while (s.class_hcap < 2u * (uint32_t)std::max<int64_t>(1, (int64_t)ws.class_cache.size())) s.class_hcap <<= 1;
     int nsm = 152;

@@ -206,12 +206,9 @@ void enqueue_plan(const PlanShape &s, const PlanBuffers &b, cudaStream_t st, cud
     }
 
     // ---------------------------------------------------------- downward pass (fs)
-    if (s.hybrid) {
-        // a full grid when the captured solve had particle-cell pairs, else a GPU-sized
-        // one that strides over the cells' counts
-        const int gp = std::max(1, s.p2l_seen ? s.cell_cap : std::min(s.cell_cap, 152 * 16));
-        k_p2l<<<(unsigned)gp, 32, (size_t)32 * (P2pad + 1) * sizeof(float), fs>>>(c, L, 0, b.pts, b.box, p, P2pad,
-                                                                                   b.Lx, b.sz);
+    if (s.p2l_seen) {  // particle-cell pairs (the plan has none of a kind its capture lacked)
+        k_p2l<<<(unsigned)std::max(1, s.cell_cap), 32, (size_t)32 * (P2pad + 1) * sizeof(float), fs>>>(
+            c, L, 0, b.pts, b.box, p, P2pad, b.Lx, b.sz);
         FMM_LAUNCH_CHECK();
     }
     for (int l = 0; l < s.levels; ++l) {
@@ -221,10 +218,8 @@ void enqueue_plan(const PlanShape &s, const PlanBuffers &b, cudaStream_t st, cud
             launch_shift_batched(true, c, 0, 0, b.l2l, P2, P2pad, b.Lx, nullptr, fs, b.sz, l, s.level_cap[l]);
     }
     launch_l2p(c, b.pcell, s.N, b.pts, p, P2pad, b.Lx, b.far, fs);
-    if (s.hybrid) {
-        const unsigned gm = s.m2p_seen ? blocks_for(s.leaf_cap, kM2PWarps)
-                                       : std::min(blocks_for(s.leaf_cap, kM2PWarps), 152u * 16u);
-        k_m2p<<<gm, 32 * kM2PWarps, m2p_smem(p, P2pad), fs>>>(
+    if (s.m2p_seen) {  // cell-particle pairs
+        k_m2p<<<blocks_for(s.leaf_cap, kM2PWarps), 32 * kM2PWarps, m2p_smem(p, P2pad), fs>>>(
             c, L, b.leaves, 0, b.pts, b.box, p, P2pad, b.M, b.far, b.sz);
         FMM_LAUNCH_CHECK();
     }

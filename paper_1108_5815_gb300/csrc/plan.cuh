@@ -23,7 +23,7 @@ struct PlanShape {
     double theta = 0.0;
     bool tensor = false, bf16 = false;  // M2L on the tensor cores, BF16x3 (else TF32x3)
     bool hybrid = false;                // a selection table is in use (M2P/P2L possible)
-    bool m2p_seen = false, p2l_seen = false;  // the captured solve had such pairs: full grids
+    bool m2p_seen = false, p2l_seen = false;  // the captured solve had such pairs (else none allowed)
     int sys_bits = 1;                   // bits of the system index (batched sort)
     int levels = 0;                     // parents at levels 0 .. levels - 1; level `levels` must not split
     std::vector<int> level_cap;         // cells per level, levels + 2 entries

@@ -102,15 +102,14 @@ typedef struct {
     int serialize_phases;
     /* 1 (default): a solve without statistics and without serialize_phases whose
      * key -- N, the system offsets, p, theta, ncrit, max_depth, precision_mode,
-     * select_mode, m2l_unit_blocks, the selection table's content and the four
-     * array pointers xyz, q, phi and grad -- equals the previous such call's on
-     * this device captures a plan after it solves (as fmm_plan_create,
-     * capacities 1.25x this solve's), and later calls with that key replay it:
-     * every step of the solve still runs, in one graph launch with every size on
-     * the device, reading xyz and q and writing phi and grad in place, and the
-     * results are bit-identical to a plain solve.  The arrays' contents may
-     * change between calls; the plan keeps their addresses only, and a call with
-     * other arrays does not replay it.  A replay that outgrows the plan is solved
+     * select_mode, m2l_unit_blocks and the selection table's content -- equals
+     * the previous such call's on this device captures a plan after it solves
+     * (as fmm_plan_create, capacities 1.25x this solve's), and later calls with
+     * that key replay it: every step of the solve still runs, in one graph
+     * launch with every size on the device, reading this call's xyz and q and
+     * writing its phi and grad in place (any arrays: their addresses are handed
+     * to the plan at each replay), and the results are bit-identical to a plain
+     * solve.  A replay that outgrows the plan is solved
      * again plainly and the plan is dropped.  The plan's memory stays allocated
      * until a call with another key captures its own.  The first two calls with
      * a key are plain solves; the second also captures.  0: always a plain

@@ -127,14 +127,11 @@ struct Workspace {
         double theta = 0.0;
         std::vector<int64_t> off;  // system offsets (batched)
         std::vector<uint8_t> sel;  // the selection table's content (empty: plain FMM)
-        // the caller's arrays: the plan reads and writes them in place (no copies)
-        const void *xyz = nullptr, *q = nullptr, *phi = nullptr, *grad = nullptr;
         bool operator==(const ReplayKey &k) const
         {
             return N == k.N && nsys == k.nsys && p == k.p && ncrit == k.ncrit && max_depth == k.max_depth &&
                    precision == k.precision && select_mode == k.select_mode && unit_blocks == k.unit_blocks &&
-                   theta == k.theta && off == k.off && sel == k.sel && xyz == k.xyz && q == k.q && phi == k.phi &&
-                   grad == k.grad;
+                   theta == k.theta && off == k.off && sel == k.sel;
         }
     };
     fmm_plan *replay_plan = nullptr;
@@ -1331,10 +1328,12 @@ struct fmm_plan {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int *hcheck = nullptr;  // pinned: the flags and sizes read back by a check
+    fmm::IoPtrs *io = nullptr, *hio = nullptr;  // the caller's arrays of each replay (device, pinned host)
     ~fmm_plan()
     {
         if (st) cudaStreamSynchronize(st);
         if (hcheck) cudaFreeHost(hcheck);
+        if (hio) cudaFreeHost(hio);
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
         if (tree) cudaEventDestroy(tree);
@@ -1368,6 +1367,7 @@ void build_plan(fmm_plan &pl, Workspace &ws, const int64_t *offsets, const uint8
     b.q = pl.q;
     b.phi = pl.phi;
     b.grad = pl.grad;
+    b.io = pl.io;
     b.flags = m.get<int>(kNumFlags);
     b.sz = m.get<int>(kSzWords);
     b.bbox_u = m.get<uint32_t>(6 * (size_t)nsys);
@@ -1554,6 +1554,20 @@ void plan_execute(fmm_plan &pl, const float *xyz, const float *q, float *phi, fl
         FMM_CUDA_TRY(cudaMemcpyAsync(grad, pl.grad, sizeof(float) * 3 * n, cudaMemcpyDeviceToDevice, st));
 }
 
+// One replay of a plan made with caller_arrays on the caller's arrays, in place:
+// their addresses go to the plan's pointer block (one small copy ahead of the
+// graph on `st`; the pinned source is rewritten only after the replay's check
+// has waited for the stream).
+void plan_execute_io(fmm_plan &pl, const float *xyz, const float *q, float *phi, float *grad, cudaStream_t st)
+{
+    pl.hio->xyz = xyz;
+    pl.hio->q = q;
+    pl.hio->phi = phi;
+    pl.hio->grad = grad;
+    FMM_CUDA_TRY(cudaMemcpyAsync(pl.io, pl.hio, sizeof(IoPtrs), cudaMemcpyHostToDevice, st));
+    FMM_CUDA_TRY(cudaGraphLaunch(pl.exec, st));
+}
+
 // Waits for `stream` and raises what the last replay's flags report.
 void plan_check(fmm_plan &pl, cudaStream_t st)
 {
@@ -1570,27 +1584,26 @@ void plan_check(fmm_plan &pl, cudaStream_t st)
                                       "no operator for; its results are invalid (create a new plan)"};
 }
 
-// The caller's arrays that a replayed plan reads and writes in place.
-struct Borrowed {
-    const float *xyz = nullptr, *q = nullptr;
-    float *phi = nullptr, *grad = nullptr;
-};
-
 // A plan captured from the workspace's last solve (its sizes, operators and
 // classes).  Its particle and result arrays are its own, or, for the plan that
-// repeated calls replay, the caller's (borrowed: that plan is replayed only by a
-// call with the same four arrays, so it never copies them).
+// repeated calls replay (caller_arrays), the caller's of each replay: their
+// addresses go to the plan's pointer block before each launch (plan_execute_io),
+// so that any arrays are read and written in place.
 fmm_plan *plan_from_last_solve(Workspace &ws, int64_t N, int nsys, const int64_t *off, int p, double theta,
                                int ncrit, const fmm_options &o, const uint8_t *sel, double headroom,
-                               const Borrowed &bw = Borrowed{})
+                               bool caller_arrays = false)
 {
     std::unique_ptr<fmm_plan> pl(new fmm_plan());
     FMM_CUDA_TRY(cudaGetDevice(&pl->device));
-    const bool borrow = bw.xyz && bw.q && bw.phi && bw.grad;
-    pl->xyz = borrow ? const_cast<float *>(bw.xyz) : pl->mem.get<float>(3 * (size_t)N);
-    pl->q = borrow ? const_cast<float *>(bw.q) : pl->mem.get<float>((size_t)N);
-    pl->phi = borrow ? bw.phi : pl->mem.get<float>((size_t)N);
-    pl->grad = borrow ? bw.grad : pl->mem.get<float>(3 * (size_t)N);
+    if (caller_arrays) {
+        pl->io = pl->mem.get<IoPtrs>(1);
+        FMM_CUDA_TRY(cudaMallocHost(reinterpret_cast<void **>(&pl->hio), sizeof(IoPtrs)));
+    } else {
+        pl->xyz = pl->mem.get<float>(3 * (size_t)N);
+        pl->q = pl->mem.get<float>((size_t)N);
+        pl->phi = pl->mem.get<float>((size_t)N);
+        pl->grad = pl->mem.get<float>(3 * (size_t)N);
+    }
     pl->s = plan_shape(ws, N, nsys, p, theta, ncrit, o, sel != nullptr, headroom);
     build_plan(*pl, ws, off, sel);
     return pl.release();
@@ -1624,13 +1637,9 @@ void solve_api(Workspace &ws, const float *xyz, const float *q, int64_t N, int n
     key.theta = theta;
     key.off.assign(off, off + nsys + 1);
     if (sel) key.sel.assign(sel, sel + (size_t)kSelNB * kSelNB);
-    key.xyz = xyz;
-    key.q = q;
-    key.phi = phi;
-    key.grad = grad;
     if (ws.replay_plan && ws.replay_key == key) {
         try {
-            plan_execute(*ws.replay_plan, xyz, q, phi, grad, stream);
+            plan_execute_io(*ws.replay_plan, xyz, q, phi, grad, stream);
             plan_check(*ws.replay_plan, stream);
             // (calls that alternate between keys then solve the other keys plainly
             // instead of capturing a plan at every other call)
@@ -1648,8 +1657,7 @@ void solve_api(Workspace &ws, const float *xyz, const float *q, int64_t N, int n
         delete ws.replay_plan;
         ws.replay_plan = nullptr;
         try {
-            ws.replay_plan = plan_from_last_solve(ws, N, nsys, off, p, theta, ncrit, o, sel, 1.25,
-                                                  Borrowed{xyz, q, phi, grad});
+            ws.replay_plan = plan_from_last_solve(ws, N, nsys, off, p, theta, ncrit, o, sel, 1.25, true);
             ws.replay_key = key;
         } catch (const Error &) {
             // no plan for this key (the solve itself succeeded): later calls solve plainly

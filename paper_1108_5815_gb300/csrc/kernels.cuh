@@ -76,19 +76,29 @@ constexpr int kHashBits = 18;
 constexpr uint32_t kHashCap = 1u << kHashBits;
 constexpr uint64_t kHashEmpty = ~0ull;
 
+// The caller's arrays of a replayed plan.  The kernels that read the particles
+// or write the results take them from here when io is given (the host writes
+// the four pointers before each replay), so that one captured plan serves any
+// arrays in place.
+struct IoPtrs {
+    const float *xyz, *q;
+    float *phi, *grad;
+};
+
 // tree.cu
 __global__ void k_init_bbox(uint32_t *bbox_u, int nsys);
-__global__ void k_bbox(const float *xyz, int64_t n, uint32_t *bbox_u, int *flags);
+__global__ void k_bbox(const float *xyz, int64_t n, uint32_t *bbox_u, int *flags, const IoPtrs *io = nullptr);
 __global__ void k_morton(const float *xyz, int64_t n, const int *off, int nsys,
-                         const uint32_t *bbox_u, double *box, uint64_t *keys, uint32_t *idx);
+                         const uint32_t *bbox_u, double *box, uint64_t *keys, uint32_t *idx,
+                         const IoPtrs *io = nullptr);
 __global__ void k_bbox_sys(const float *xyz, int64_t n, const int *off, int nsys, uint32_t *bbox_u,
-                           int *flags);
+                           int *flags, const IoPtrs *io = nullptr);
 __global__ void k_sys_of_sorted(const uint32_t *idx, int64_t n, const int *off, int nsys,
                                 uint64_t *sys_key);
 __global__ void k_gather_keys(const uint64_t *orig, const uint32_t *idx, int64_t n, uint64_t *keys);
 __global__ void k_init_roots(CellArrays c, const int *off, int nsys);
 __global__ void k_permute(const float *xyz, const float *q, const uint32_t *idx, int64_t n,
-                          float4 *out);
+                          float4 *out, const IoPtrs *io = nullptr);
 __global__ void k_first_diff(const uint64_t *keys, int64_t n, uint64_t *lvl, uint32_t *pos);
 constexpr int kLevelStartWarps = 24;  // levels 0 .. 23, one warp each
 __global__ void k_level_starts(const uint64_t *lvl, int64_t n, int *start);
@@ -268,7 +278,7 @@ __global__ void k_direct(const float *xyz, const float *q, int64_t n, float *phi
 __global__ void k_ffma_stream(float *out, int iters, float s);
 __global__ void k_p2p_body(float *out, int reps);
 __global__ void k_combine(const float4 *far, const float4 *near, const uint32_t *idx, int64_t n,
-                          float *phi, float *grad);
+                          float *phi, float *grad, const IoPtrs *io = nullptr);
 
 // mlp.cu -- cost-model network (3 layers, hidden 64, FP16 parameters)
 constexpr int kMlpIn = 4, kMlpHidden = 64, kMlpOut = 2;

@@ -436,8 +436,12 @@ __global__ void __launch_bounds__(256)
 // phi/grad in caller order = far + near of each sorted position.
 __global__ void k_combine(const float4 *__restrict__ far, const float4 *__restrict__ near,
                           const uint32_t *__restrict__ idx, int64_t n, float *__restrict__ phi,
-                          float *__restrict__ grad)
+                          float *__restrict__ grad, const IoPtrs *__restrict__ io)
 {
+    if (io) {
+        phi = io->phi;
+        grad = io->grad;
+    }
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const float4 a = far[i], b = near[i];

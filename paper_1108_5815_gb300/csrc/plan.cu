@@ -47,11 +47,12 @@ void enqueue_plan(const PlanShape &s, const PlanBuffers &b, cudaStream_t st, cud
     k_init_bbox<<<blocks_for(6 * (int64_t)nsys, 256), 256, 0, st>>>(b.bbox_u, nsys);
     FMM_LAUNCH_CHECK();
     if (nsys == 1)
-        k_bbox<<<grid_stride(N), 256, 0, st>>>(b.xyz, N, b.bbox_u, b.flags);
+        k_bbox<<<grid_stride(N), 256, 0, st>>>(b.xyz, N, b.bbox_u, b.flags, b.io);
     else
-        k_bbox_sys<<<blocks_for(ceil_div(N, 8), 256), 256, 0, st>>>(b.xyz, N, b.sys_off, nsys, b.bbox_u, b.flags);
+        k_bbox_sys<<<blocks_for(ceil_div(N, 8), 256), 256, 0, st>>>(b.xyz, N, b.sys_off, nsys, b.bbox_u, b.flags,
+                                                                    b.io);
     FMM_LAUNCH_CHECK();
-    k_morton<<<grid_stride(N), 256, 0, st>>>(b.xyz, N, b.sys_off, nsys, b.bbox_u, b.box, b.keys, b.idx);
+    k_morton<<<grid_stride(N), 256, 0, st>>>(b.xyz, N, b.sys_off, nsys, b.bbox_u, b.box, b.keys, b.idx, b.io);
     FMM_LAUNCH_CHECK();
     if (nsys == 1) {
         radix_sort_pairs(b.keys, b.idx, b.keys_alt, b.idx_alt, N, 63, b.hist, b.flags, st);
@@ -64,7 +65,7 @@ void enqueue_plan(const PlanShape &s, const PlanBuffers &b, cudaStream_t st, cud
         k_gather_keys<<<grid_stride(N), 256, 0, st>>>(b.keys_orig, b.idx, N, b.keys);
         FMM_LAUNCH_CHECK();
     }
-    k_permute<<<grid_stride(N), 256, 0, st>>>(b.xyz, b.q, b.idx, N, b.pts);
+    k_permute<<<grid_stride(N), 256, 0, st>>>(b.xyz, b.q, b.idx, N, b.pts, b.io);
     FMM_LAUNCH_CHECK();
 
     // ---------------------------------------------------------- tree
@@ -227,7 +228,7 @@ void enqueue_plan(const PlanShape &s, const PlanBuffers &b, cudaStream_t st, cud
     // ---------------------------------------------------------- join and combine
     FMM_CUDA_TRY(cudaEventRecord(join, fs));
     FMM_CUDA_TRY(cudaStreamWaitEvent(st, join, 0));
-    k_combine<<<grid_stride(N), 256, 0, st>>>(b.far, b.near, b.idx, N, b.phi, b.grad);
+    k_combine<<<grid_stride(N), 256, 0, st>>>(b.far, b.near, b.idx, N, b.phi, b.grad, b.io);
     FMM_LAUNCH_CHECK();
 }
 

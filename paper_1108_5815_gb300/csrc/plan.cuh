@@ -37,6 +37,7 @@ struct PlanShape {
 struct PlanBuffers {
     const float *xyz = nullptr, *q = nullptr;  // plan-owned inputs
     float *phi = nullptr, *grad = nullptr;     // plan-owned outputs
+    const IoPtrs *io = nullptr;                // or, when set, the caller's arrays (device copy)
     int *flags = nullptr, *sz = nullptr;
     uint32_t *bbox_u = nullptr;
     double *box = nullptr;

@@ -32,8 +32,9 @@ __device__ __forceinline__ float ordered_to_float(uint32_t u)
 
 // bbox_u[0..2] = ordered min, [3..5] = ordered max; flags[kFlagNonfinite] set on NaN/Inf.
 __global__ void k_bbox(const float *__restrict__ xyz, int64_t n, uint32_t *__restrict__ bbox_u,
-                       int *__restrict__ flags)
+                       int *__restrict__ flags, const IoPtrs *__restrict__ io)
 {
+    if (io) xyz = io->xyz;
     float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
     bool bad = false;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -115,8 +116,10 @@ __device__ __forceinline__ void decode_box(const uint32_t *__restrict__ bu, doub
 // each thread reduces 8 consecutive particles, flushing when the system changes;
 // a warp whose lanes end in one system combines before its atomics.
 __global__ void k_bbox_sys(const float *__restrict__ xyz, int64_t n, const int *__restrict__ off,
-                           int nsys, uint32_t *__restrict__ bbox_u, int *__restrict__ flags)
+                           int nsys, uint32_t *__restrict__ bbox_u, int *__restrict__ flags,
+                           const IoPtrs *__restrict__ io)
 {
+    if (io) xyz = io->xyz;
     const int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 8;
     float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
     bool bad = false;
@@ -211,8 +214,9 @@ __device__ __forceinline__ uint32_t quant_fp64(float x, double lo, double s)
 // keys (quantised in the particle's own system box) and the identity permutation.
 __global__ void k_morton(const float *__restrict__ xyz, int64_t n, const int *__restrict__ off,
                          int nsys, const uint32_t *__restrict__ bbox_u, double *__restrict__ box,
-                         uint64_t *__restrict__ keys, uint32_t *__restrict__ idx)
+                         uint64_t *__restrict__ keys, uint32_t *__restrict__ idx, const IoPtrs *__restrict__ io)
 {
+    if (io) xyz = io->xyz;
     if (blockIdx.x == 0) {
         for (int sy = threadIdx.x; sy < nsys; sy += blockDim.x) {
             double lo[3], side;
@@ -267,8 +271,13 @@ __global__ void k_morton(const float *__restrict__ xyz, int64_t n, const int *__
 
 // Sorted particles as float4 (x, y, z, q).
 __global__ void k_permute(const float *__restrict__ xyz, const float *__restrict__ q,
-                          const uint32_t *__restrict__ idx, int64_t n, float4 *__restrict__ out)
+                          const uint32_t *__restrict__ idx, int64_t n, float4 *__restrict__ out,
+                          const IoPtrs *__restrict__ io)
 {
+    if (io) {
+        xyz = io->xyz;
+        q = io->q;
+    }
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t o = idx[i];

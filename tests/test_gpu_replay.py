@@ -1,12 +1,11 @@
 """Repeated solves through the public entry points (fmm_options.replay, the
 default): from the third call of one key on, a call replays the plan the library
-captured after the second.  The key includes the caller's arrays, which the plan
-reads and writes in place.
+captured after the second, reading and writing each call's arrays in place.
 
 * a replayed call gives exactly the plain solve's result (replay=False) of the
   same data, for new positions and charges too, also when they are written into
   the same arrays;
-* calls that alternate between two sets of arrays are plain solves and stay right;
+* calls that alternate between two sets of arrays replay on each set and stay right;
 * data that outgrows the plan (a clustered set after a uniform one of the same
   N) is solved again plainly, with the plain result, and later calls stay right;
 * batched systems and a selection table replay the same way;
@@ -136,7 +135,7 @@ def test_new_data_in_the_same_arrays_and_alternating_arrays():
     qta.copy_(qtb)
     ref_b = run(xtb, qtb, replay=False)
     assert _equal(run(xta, qta), ref_b)
-    # alternating arrays: no two calls in a row share a key
+    # alternating arrays: the same plan replays on each set
     xta.copy_(torch.from_numpy(xa).cuda())
     qta.copy_(torch.from_numpy(qa).cuda())
     ref_a = run(xta, qta, replay=False)

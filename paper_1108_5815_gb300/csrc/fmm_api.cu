@@ -893,9 +893,8 @@ void solve_locked(Workspace &ws, const float *xyz, const float *q, int64_t N64, 
                                                                   get<int>(ws, "class_slot"));
     FMM_LAUNCH_CHECK();
     if (m2l_total > 0) {
-        k_tile_src<<<grid_for(m2l_total, 256), 256, 0, fs>>>(L.m2l_tgt, L.m2l_src, L.m2l_slot,
-                                                           m2l_total, c.tile, c.lane, nwords,
-                                                           bitmap, word_prefix, entry_base, src);
+        k_tile_src_rows<<<(unsigned)ceil_div((int64_t)ntiles * kTile, 4), 128, 0, fs>>>(
+            tile_cells, ntiles, L.m2l_off, L.m2l_cnt, L.m2l_src, L.m2l_slot, nwords, bitmap, word_prefix, src);
         FMM_LAUNCH_CHECK();
     }
 

@@ -188,11 +188,12 @@ __global__ void k_tile_popc(const uint32_t *bitmap, int ntiles, int nwords, int 
 __global__ void k_tile_entries(const uint32_t *bitmap, int ntiles, int nwords,
                                const int *entry_base, int *word_prefix, int *entry_class,
                                const int *class_slot, int entry_cap = INT_MAX);
-__global__ void k_tile_src(const int *m2l_tgt, const int *m2l_src, const uint32_t *m2l_class,
-                           int64_t n, const int *cell_tile, const int *cell_lane, int nwords,
-                           const uint32_t *bitmap, const int *word_prefix,
-                           const int *entry_base, int *src, const unsigned long long *dn = nullptr,
-                           int entry_cap = INT_MAX);
+// src[entry * kTile + row] = source cell of each M2L pair, written row by row in
+// tile order (a warp per row; with sz, the tile count from sz), so that the
+// writes in flight stay within a few tiles' entries.
+__global__ void k_tile_src_rows(const int *tile_cells, int ntiles, const int *m2l_off, const int *m2l_cnt,
+                                const int *m2l_src, const uint32_t *m2l_class, int nwords, const uint32_t *bitmap,
+                                const int *word_prefix, int *src, const int *sz = nullptr, int entry_cap = INT_MAX);
 
 // expansions.cu
 __global__ void k_build_m2l_tables(const uint64_t *class_keys, const int *cache_slot, int nnew,

@@ -190,9 +190,9 @@ void enqueue_plan(const PlanShape &s, const PlanBuffers &b, cudaStream_t st, cud
                                                               s.nent_cap);
     FMM_LAUNCH_CHECK();
     FMM_CUDA_TRY(cudaMemsetAsync(b.src, 0xff, sizeof(int) * (size_t)s.nent_cap * kTile, fs));
-    k_tile_src<<<grid_stride(s.m2l_cap), 256, 0, fs>>>(L.m2l_tgt, L.m2l_src, L.m2l_slot, 0, c.tile, c.lane,
-                                                       s.nwords, b.bitmap, b.word_prefix, b.entry_base, b.src,
-                                                       b.totals, s.nent_cap);
+    k_tile_src_rows<<<blocks_for((int64_t)s.tile_cap * kTile, 4), 128, 0, fs>>>(
+        b.tile_cells, 0, L.m2l_off, L.m2l_cnt, L.m2l_src, L.m2l_slot, s.nwords, b.bitmap, b.word_prefix, b.src, b.sz,
+        s.nent_cap);
     FMM_LAUNCH_CHECK();
 
     // ---------------------------------------------------------- M2L (fs)

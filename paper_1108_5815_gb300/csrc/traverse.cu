@@ -830,42 +830,42 @@ __global__ void k_tile_entries(const uint32_t *__restrict__ bitmap, int ntiles, 
     }
 }
 
-__global__ void k_tile_src(const int *__restrict__ m2l_tgt, const int *__restrict__ m2l_src,
-                           const uint32_t *__restrict__ m2l_class, int64_t n,
-                           const int *__restrict__ cell_tile, const int *__restrict__ cell_lane,
-                           int nwords, const uint32_t *__restrict__ bitmap,
-                           const int *__restrict__ word_prefix, const int *__restrict__ entry_base,
-                           int *__restrict__ src, const unsigned long long *__restrict__ dn, int entry_cap)
+// The gather index of every M2L pair, src[entry * kTile + row], written row by
+// row in tile order: warp w takes row w % kTile of tile w / kTile, and its lanes
+// take 32 of the row's pairs at a time (the cell's pairs are contiguous).  Warps start in order, so the rows in flight belong to a few
+// dozen tiles, whose entries (a few hundred kilobytes each) stay in the L2
+// cache while their writes merge; in pair order the writes spread over the
+// whole array (a quarter of a gigabyte at 4M Plummer points), where each 4-byte
+// write costs a partial sector in DRAM.
+__global__ void __launch_bounds__(128)
+    k_tile_src_rows(const int *__restrict__ tile_cells, int ntiles, const int *__restrict__ m2l_off,
+                    const int *__restrict__ m2l_cnt, const int *__restrict__ m2l_src,
+                    const uint32_t *__restrict__ m2l_class, int nwords, const uint32_t *__restrict__ bitmap,
+                    const int *__restrict__ word_prefix, int *__restrict__ src, const int *__restrict__ sz,
+                    int entry_cap)
 {
-    if (dn) n = (int64_t)*dn;
-    // four elements per thread and round, each level of their dependent loads issued together
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += 4 * stride) {
-        int t[4], s4[4], tile[4], lane[4];
-        uint32_t cl[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const bool ok = i0 + u * stride < n;
-            t[u] = ok ? m2l_tgt[i0 + u * stride] : -1;
-            cl[u] = ok ? m2l_class[i0 + u * stride] : 0u;
-            s4[u] = ok ? m2l_src[i0 + u * stride] : 0;
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            tile[u] = t[u] >= 0 ? cell_tile[t[u]] : 0;
-            lane[u] = t[u] >= 0 ? cell_lane[t[u]] : 0;
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            if (t[u] < 0) continue;
-            const int64_t wi = (int64_t)tile[u] * nwords + (cl[u] >> 5);
-            const uint32_t below = bitmap[wi] & ((1u << (cl[u] & 31)) - 1u);
-            const int e = word_prefix[wi] + __popc(below);
-            if (e < entry_cap) src[(int64_t)e * kTile + lane[u]] = s4[u];
-        }
+    if (sz) {
+        if (sz[kSzAbort]) return;  // (class ids may be unconverted hash slots)
+        ntiles = sz[kSzTiles];
+    }
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (gw >= (int64_t)ntiles * kTile) return;
+    const int tile = (int)(gw / kTile), r = (int)(gw % kTile);
+    const int cell = tile_cells[gw];
+    if (cell < 0) return;
+    const int o = m2l_off[cell], cnt = m2l_cnt[cell];
+    const uint32_t *bm = bitmap + (int64_t)tile * nwords;
+    const int *wp = word_prefix + (int64_t)tile * nwords;
+    for (int k = lane; k < cnt; k += 32) {
+        const uint32_t cl = m2l_class[o + k];
+        const int s = m2l_src[o + k];
+        if ((int)(cl >> 5) >= nwords) continue;
+        const uint32_t below = bm[cl >> 5] & ((1u << (cl & 31)) - 1u);
+        const int e = wp[cl >> 5] + __popc(below);
+        if (e < entry_cap) src[(int64_t)e * kTile + r] = s;
     }
 }
-
 
 // ---------------------------------------------------------------- replayed plans
 
